@@ -1,0 +1,165 @@
+/*
+ * binodeg -- exact degree of the C*-solution set of a binomial system on GB300 (sm_103a).
+ *
+ * C ABI of libbinodeg.so.  Plain pointers and sizes only.  Unless stated otherwise every
+ * pointer is a HOST pointer owned by the caller; the library copies what it needs and
+ * never keeps a caller pointer after a call returns.  Integer matrices are row-major.
+ * Every function returns a status code (BD_OK on success) and never throws; the message
+ * of the last failure on the calling thread is available from bd_last_error().
+ *
+ * Method (Chen & Mehta, "Parallel degree computation for solution space of binomial
+ * systems ...", arXiv 1501.02237):
+ *   x^A = b with A in Z^{n x m} (Sec. 2, Eq. standard-form);  Smith form P A Q = D
+ *   (Sec. 2, Eq. smith; Sec. 3);  the solution set has |prod d_j| components of dimension
+ *   d = n - rank A (Prop. 1), each of degree d! Vol_d(conv{columns of P_0, 0}) (Prop. 4,
+ *   Eq. deg-vol), computed as the sum of |det| over the cells of a regular triangulation
+ *   obtained from generic lift heights (Sec. 4.1, Eq. lower-face, strict form of Sec. 5).
+ */
+#ifndef BINODEG_H
+#define BINODEG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define BD_OK 0
+#define BD_ERR_ARG 1       /* invalid argument (sizes, null pointers, limits) */
+#define BD_ERR_OVERFLOW 2  /* an exact value would not fit: Smith form entries above 2^100,
+                              or the Hadamard bound of the lifted minors above 2^126 */
+#define BD_ERR_TIES 3      /* every one of the allowed liftings produced a tie */
+#define BD_ERR_CUDA 4      /* a CUDA runtime call failed (message in bd_last_error) */
+#define BD_ERR_TIMEOUT 5   /* a bounded device-side wait ran out */
+#define BD_ERR_NOMEM 6     /* host or device allocation failed */
+#define BD_ERR_STATE 7     /* call not valid in the object's current state */
+
+/* flags reported in outputs */
+#define BD_FLAG_DEGENERATE 1   /* points not full-dimensional: volume 0 */
+#define BD_FLAG_INT128 2       /* the 128-bit kernel path was used */
+#define BD_FLAG_INCONSISTENT 4 /* b^{Q_0} != 1: empty solution set, degree 0 */
+
+/* limits: K <= BD_KMAX lattice dimension, N <= BD_NMAX points (the origin included) */
+#define BD_KMAX 14
+#define BD_NMAX 64
+
+typedef struct {
+  uint64_t nvol_lo, nvol_hi; /* NVol_k(conv points) = k! Vol_k, exact unsigned 128-bit */
+  uint64_t cells;            /* accepted cells (lower facets) of the final lifting */
+  uint64_t singular;         /* (k+1)-subsets with zero simplex determinant */
+  uint64_t ties;             /* tie subsets of the final lifting (0 whenever BD_OK) */
+  uint64_t subsets;          /* C(npts, k+1): subsets tested per lifting */
+  int32_t relifts;           /* liftings discarded because of ties */
+  int32_t flags;             /* BD_FLAG_* */
+  int32_t max_abs_coord;     /* largest |coordinate| of the input points */
+  int32_t bound_bits;        /* ceil(log2) of the Hadamard bound that chose the int path */
+} bd_volume_out;
+
+typedef struct {
+  uint64_t degree_lo, degree_hi; /* degree of the solution set = torsion * nvol (Props. 1, 4) */
+  uint64_t nvol_lo, nvol_hi;     /* degree of one component, NVol_d(conv{P_0 columns, 0}) */
+  uint64_t torsion;              /* number of components |prod d_j| (Prop. 1) */
+  int32_t rank, dim;             /* rank A and d = n - rank A */
+  int32_t consistent;            /* 1 unless coefficients were given and b^{Q_0} != 1 */
+  int32_t relifts;
+  uint64_t subsets, cells;
+  int32_t flags;
+  int32_t max_abs_coord;         /* largest |coordinate| of the reduced kernel points */
+} bd_degree_out;
+
+/* Message of the last failed call on this thread ("" if none). Owned by the library. */
+const char* bd_last_error(void);
+
+/* CUDA stream (a cudaStream_t, or NULL for the legacy default stream) used by the
+ * synchronous calls below on this thread.  The library does not take ownership. */
+int bd_set_stream(void* stream);
+
+/*
+ * Degree of V(x^A - b) (Props. 1, 2, 4).
+ *   A    : n x m integers, column i = alpha_i - beta_i (Eq. standard-form); 1 <= n < BD_NMAX,
+ *          0 <= m <= 256.
+ *   coef : NULL (generic coefficients: the system is taken as consistent) or 4*m integers,
+ *          binomial i -> (num1, den1, num2, den2) = c_{i,1}, c_{i,2} as fractions,
+ *          b_i = -c_{i,2}/c_{i,1}; the consistency condition b^{Q_0} = 1 (Eq. consistency)
+ *          is decided exactly.  Denominators and numerators must be nonzero.
+ *   seed : lift seed; the result does not depend on it.
+ * Host reduction (Smith form, LLL-reduced kernel basis, torsion) runs on the CPU; the
+ * volume on the GPU.  dim = 0 gives degree = torsion.  Errors: BD_ERR_ARG, BD_ERR_OVERFLOW,
+ * BD_ERR_TIES, BD_ERR_CUDA, BD_ERR_NOMEM.
+ */
+int bd_degree(const int64_t* A, int32_t n, int32_t m, const int64_t* coef, uint64_t seed,
+              bd_degree_out* out);
+
+/*
+ * Host front end of bd_degree only (no GPU): Smith form, torsion, consistency and the
+ * LLL-reduced kernel points.  points receives (n + 1) x d integers (row i = point i, the
+ * last row the origin) and must hold (n + 1) * n entries.  info receives 8 int64:
+ * {rank, dim, torsion, consistent, max_abs_coord, 0, 0, 0}.
+ */
+int bd_reduce(const int64_t* A, int32_t n, int32_t m, const int64_t* coef, int64_t* points,
+              int64_t* info);
+
+/*
+ * NVol_k(conv points) = k! Vol_k (Sec. 4, Eq. deg-nvol), exact.
+ *   points : npts x k integers (row = point), k+1 <= npts <= BD_NMAX, 1 <= k <= BD_KMAX.
+ *            The origin is NOT added.  Not full-dimensional -> volume 0, BD_FLAG_DEGENERATE.
+ *   seed   : lift seed; ties are re-lifted (up to 8 liftings, then BD_ERR_TIES).
+ */
+int bd_volume(const int64_t* points, int32_t npts, int32_t k, uint64_t seed, bd_volume_out* out);
+
+/* As bd_volume with caller-given lift heights (npts values, |lift| < 2^40) and no re-lift:
+ * a tie is reported in out->ties and the call returns BD_ERR_TIES. */
+int bd_volume_lifted(const int64_t* points, const int64_t* lifts, int32_t npts, int32_t k,
+                     bd_volume_out* out);
+
+/*
+ * Lower-facet status of `count` given (k+1)-subsets (each k+1 strictly increasing uint8
+ * indices, back to back) under the given lifts, on the GPU (Eq. lower-face, strict form).
+ *   status[i] : 0 singular (zero determinant), 1 rejected (a point strictly below),
+ *               2 accepted (every other point strictly above), 3 tie (none below, one on).
+ *   absdet[i] : |det(a_{s_1} - a_{s_0}, .., a_{s_k} - a_{s_0})| as int64 (0 if singular,
+ *               -1 if it needs more than 63 bits).
+ */
+int bd_classify(const int64_t* points, const int64_t* lifts, int32_t npts, int32_t k,
+                const uint8_t* subsets, int32_t count, int32_t* status, int64_t* absdet);
+
+/* ---- device-resident plans (the timed path of the benchmark) ------------------------- */
+
+typedef struct bd_plan bd_plan;
+
+typedef struct {
+  int32_t warps_per_block;  /* 0: choose from shared-memory capacity */
+  int32_t blocks_per_sm;    /* 0: occupancy calculator */
+  int64_t item_subsets;     /* split prefixes until each holds at most this many subsets; 0: auto */
+  int32_t force_int128;     /* 1: use the 128-bit path even when 64 bits suffice */
+  int32_t reserved[3];
+} bd_plan_opts;
+
+/* Copies the points to device memory and builds the work list.  opts may be NULL. */
+int bd_plan_create(const int64_t* points, int32_t npts, int32_t k, const bd_plan_opts* opts,
+                   bd_plan** plan);
+/* Enqueue one pass over all subsets with lifting (seed, attempt) on `stream` (NULL: the
+ * thread's stream).  Asynchronous: nothing is copied to or from the host. */
+int bd_plan_launch(bd_plan* plan, uint64_t seed, int32_t attempt, void* stream);
+/* Wait for the last launch on its stream and read its result. */
+int bd_plan_read(bd_plan* plan, bd_volume_out* out);
+/* The full volume (launch, read, re-lift on ties) with inputs already on the device. */
+int bd_plan_volume(bd_plan* plan, uint64_t seed, bd_volume_out* out);
+/* Number of work items, kernel launch geometry and path: {items, blocks, warps_per_block,
+ * shared_bytes_per_block, int128, slots_per_warp, 0, 0}. */
+int bd_plan_info(const bd_plan* plan, int64_t* info);
+int bd_plan_destroy(bd_plan* plan);
+
+/* ---- host emulation (CPU tests and the native CPU baseline; never used by the calls above) */
+
+/* Runs the same lower-facet enumeration as the GPU kernel on `threads` CPU threads, with
+ * the given lifts (no re-lift).  Returns BD_ERR_TIES when the lifting has a tie. */
+int bd_host_volume_lifted(const int64_t* points, const int64_t* lifts, int32_t npts, int32_t k,
+                          int32_t threads, bd_volume_out* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BINODEG_H */

@@ -1,0 +1,149 @@
+"""Exact degree of binomial-system solution sets on GB300 (Chen & Mehta, arXiv 1501.02237).
+
+Python face of libbinodeg.so, with the same names as the C ABI (include/binodeg.h).
+Every computation runs in the library: the host front end (Smith form, kernel basis)
+in C++ and the lower-facet enumeration in CUDA.  If the library is missing, calls raise.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+from typing import Optional, Sequence
+
+import numpy as np
+
+from ._lib import (BD_FLAG_DEGENERATE, BD_FLAG_INCONSISTENT, BD_FLAG_INT128, KMAX, NMAX,  # noqa: F401
+                   BinodegError, DegreeOut, PlanOpts, VolumeOut, check, i64, lib, ptr)
+from ._lib import I32P, U8P
+
+__all__ = ["degree", "volume", "volume_lifted", "classify", "reduce", "Plan", "set_stream",
+           "host_volume_lifted", "BinodegError", "lib"]
+
+
+def set_stream(stream) -> None:
+    """Stream for the synchronous calls on this thread: a torch.cuda.Stream, a raw handle or None."""
+    handle = getattr(stream, "cuda_stream", stream)
+    check(lib().bd_set_stream(C.c_void_p(handle or 0)))
+
+
+def _coef_array(coef, m: int) -> Optional[np.ndarray]:
+    if coef is None:
+        return None
+    c = i64(coef).reshape(m, 4)
+    return np.ascontiguousarray(c)
+
+
+def degree(A, coef=None, seed: int = 0) -> dict:
+    """bd_degree: degree of V(x^A - b); A is n x m (column i = alpha_i - beta_i).
+    coef: None or m x 2 x 2 / m x 4 integers (num, den) of c_{i,1}, c_{i,2}."""
+    A = i64(A)
+    n, m = A.shape
+    c = _coef_array(coef, m)
+    out = DegreeOut()
+    check(lib().bd_degree(ptr(A), n, m, ptr(c) if c is not None else None, C.c_uint64(seed), C.byref(out)))
+    return out.as_dict()
+
+
+def reduce(A, coef=None) -> dict:
+    """bd_reduce: host front end only -> kernel points (n+1 x d, origin last), rank, torsion."""
+    A = i64(A)
+    n, m = A.shape
+    c = _coef_array(coef, m)
+    pts = np.zeros((n + 1) * n, dtype=np.int64)
+    info = np.zeros(8, dtype=np.int64)
+    check(lib().bd_reduce(ptr(A), n, m, ptr(c) if c is not None else None, ptr(pts), ptr(info)))
+    d = int(info[1])
+    return dict(points=pts[: (n + 1) * d].reshape(n + 1, d), rank=int(info[0]), dim=d, torsion=int(info[2]),
+                consistent=bool(info[3]), max_abs_coord=int(info[4]))
+
+
+def volume(points, seed: int = 0) -> dict:
+    """bd_volume: exact NVol_k(conv points), points npts x k (the origin is not added)."""
+    P = i64(points)
+    npts, k = P.shape
+    out = VolumeOut()
+    check(lib().bd_volume(ptr(P), npts, k, C.c_uint64(seed), C.byref(out)))
+    return out.as_dict()
+
+
+def volume_lifted(points, lifts) -> dict:
+    """bd_volume_lifted: the same with caller-given lift heights and no re-lift."""
+    P, W = i64(points), i64(lifts)
+    npts, k = P.shape
+    out = VolumeOut()
+    rc = lib().bd_volume_lifted(ptr(P), ptr(W), npts, k, C.byref(out))
+    res = out.as_dict()
+    res["status"] = rc
+    if rc not in (0, 3):
+        check(rc)
+    return res
+
+
+def classify(points, lifts, subsets) -> tuple:
+    """bd_classify: (status, absdet) arrays for the given (k+1)-subsets (rows of indices)."""
+    P, W = i64(points), i64(lifts)
+    npts, k = P.shape
+    S = np.ascontiguousarray(np.asarray(subsets, dtype=np.uint8).reshape(-1, k + 1))
+    cnt = S.shape[0]
+    status = np.zeros(cnt, dtype=np.int32)
+    absdet = np.zeros(cnt, dtype=np.int64)
+    check(lib().bd_classify(ptr(P), ptr(W), npts, k, S.ctypes.data_as(U8P), cnt, status.ctypes.data_as(I32P),
+                            ptr(absdet)))
+    return status, absdet
+
+
+def host_volume_lifted(points, lifts, threads: int = 1) -> dict:
+    """bd_host_volume_lifted: CPU emulation of the enumeration (CPU tests and the native baseline)."""
+    P, W = i64(points), i64(lifts)
+    npts, k = P.shape
+    out = VolumeOut()
+    rc = lib().bd_host_volume_lifted(ptr(P), ptr(W), npts, k, threads, C.byref(out))
+    res = out.as_dict()
+    res["status"] = rc
+    if rc not in (0, 3):
+        check(rc)
+    return res
+
+
+class Plan:
+    """bd_plan_*: device-resident enumeration of one point set."""
+
+    def __init__(self, points, warps_per_block: int = 0, blocks_per_sm: int = 0, item_subsets: int = 0,
+                 force_int128: bool = False):
+        P = i64(points)
+        self.npts, self.k = P.shape
+        opts = PlanOpts(warps_per_block, blocks_per_sm, item_subsets, int(force_int128))
+        h = C.c_void_p()
+        check(lib().bd_plan_create(ptr(P), self.npts, self.k, C.byref(opts), C.byref(h)))
+        self.handle = h
+
+    def launch(self, seed: int = 0, attempt: int = 0, stream=None) -> None:
+        s = getattr(stream, "cuda_stream", stream)
+        check(lib().bd_plan_launch(self.handle, C.c_uint64(seed), attempt, C.c_void_p(s or 0)))
+
+    def read(self) -> dict:
+        out = VolumeOut()
+        check(lib().bd_plan_read(self.handle, C.byref(out)))
+        return out.as_dict()
+
+    def volume(self, seed: int = 0) -> dict:
+        out = VolumeOut()
+        check(lib().bd_plan_volume(self.handle, C.c_uint64(seed), C.byref(out)))
+        return out.as_dict()
+
+    def info(self) -> dict:
+        a = np.zeros(8, dtype=np.int64)
+        check(lib().bd_plan_info(self.handle, ptr(a)))
+        return dict(items=int(a[0]), blocks=int(a[1]), warps_per_block=int(a[2]), smem=int(a[3]),
+                    int128=bool(a[4]), slots=int(a[5]))
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            lib().bd_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

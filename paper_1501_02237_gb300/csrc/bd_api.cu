@@ -1,0 +1,467 @@
+// C ABI of libbinodeg.so (declarations and contracts in include/binodeg.h).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/binodeg.h"
+#include "bd_host.h"
+#include "bd_kernels.cuh"
+#include "bd_lifts.h"
+
+using bd::i128;
+using bd::u128;
+
+namespace {
+
+thread_local std::string g_err;
+thread_local cudaStream_t g_stream = nullptr;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+  return fail(BD_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define BD_CUDA(call)                                   \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+constexpr int MAX_LIFTINGS = 8;
+constexpr double INT64_BITS = 62.99;   // |minor| < 2^63
+constexpr double INT128_BITS = 126.99; // |minor| < 2^127
+
+int sm_count() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  return sms;
+}
+
+int check_points(const int64_t* points, int32_t npts, int32_t k) {
+  if (!points) return fail(BD_ERR_ARG, "points is NULL");
+  if (k < 1 || k > BD_KMAX) return fail(BD_ERR_ARG, "k must be in [1, BD_KMAX]");
+  if (npts < 1 || npts > BD_NMAX) return fail(BD_ERR_ARG, "npts must be in [1, BD_NMAX]");
+  for (int64_t i = 0; i < (int64_t)npts * k; ++i)
+    if (points[i] >= ((int64_t)1 << 40) || points[i] <= -((int64_t)1 << 40))
+      return fail(BD_ERR_ARG, "|coordinate| must be below 2^40");
+  return BD_OK;
+}
+
+void set_u128(uint64_t& lo, uint64_t& hi, u128 v) {
+  lo = (uint64_t)v;
+  hi = (uint64_t)(v >> 64);
+}
+
+}  // namespace
+
+struct bd_plan {
+  int N = 0, K = 0;
+  bool wide = false;
+  double bound = 0;
+  int64_t max_abs = 0;
+  std::vector<bd::Item> items;
+  int64_t* d_pts = nullptr;
+  int64_t* d_lifts = nullptr;  // explicit lifts (optional)
+  bd::Item* d_items = nullptr;
+  unsigned char* d_state = nullptr;  // [DevAcc][counter]
+  bd::DevAcc* h_acc = nullptr;       // pinned
+  bd::LaunchShape shape;
+  cudaStream_t stream = nullptr;
+  bool launched = false;
+  int attempt = 0;
+};
+
+namespace {
+
+size_t state_bytes() { return sizeof(bd::DevAcc) + 16; }
+
+void plan_free(bd_plan* p) {
+  if (!p) return;
+  cudaFree(p->d_pts);
+  cudaFree(p->d_lifts);
+  cudaFree(p->d_items);
+  cudaFree(p->d_state);
+  cudaFreeHost(p->h_acc);
+  delete p;
+}
+
+int plan_make(const int64_t* points, const int64_t* lifts, int32_t npts, int32_t k, const bd_plan_opts* opts,
+              bd_plan** out) {
+  int rc = check_points(points, npts, k);
+  if (rc) return rc;
+  if (npts < k + 1) return fail(BD_ERR_ARG, "a plan needs at least k+1 points");
+  bd_plan* p = new (std::nothrow) bd_plan();
+  if (!p) return fail(BD_ERR_NOMEM, "host allocation");
+  p->N = npts;
+  p->K = k;
+  for (int64_t i = 0; i < (int64_t)npts * k; ++i) p->max_abs = std::max<int64_t>(p->max_abs, std::llabs(points[i]));
+  int64_t spread = (1 << 20) - 1;
+  if (lifts) {
+    int64_t lo = lifts[0], hi = lifts[0];
+    for (int i = 0; i < npts; ++i) {
+      if (lifts[i] >= ((int64_t)1 << 40) || lifts[i] <= -((int64_t)1 << 40)) {
+        delete p;
+        return fail(BD_ERR_ARG, "|lift| must be below 2^40");
+      }
+      lo = std::min(lo, lifts[i]);
+      hi = std::max(hi, lifts[i]);
+    }
+    spread = hi - lo;
+  }
+  p->bound = bd::hadamard_log2(points, lifts, npts, k, spread);
+  if (p->bound >= INT128_BITS) {
+    delete p;
+    return fail(BD_ERR_OVERFLOW, "Hadamard bound of the lifted minors exceeds 2^127");
+  }
+  p->wide = p->bound >= INT64_BITS || (opts && opts->force_int128);
+  const int sms = sm_count();
+  cudaError_t e;
+  p->shape = bd::enum_shape(npts, k, p->wide, opts ? opts->warps_per_block : 0, opts ? opts->blocks_per_sm : 0,
+                            sms, &e);
+  if (e != cudaSuccess) {
+    delete p;
+    return cuda_fail(e, "launch shape");
+  }
+  const uint64_t total = bd::binom(npts, k + 1);
+  int64_t thr = opts && opts->item_subsets > 0 ? opts->item_subsets : 0;
+  if (!thr) {
+    const uint64_t warps = (uint64_t)p->shape.blocks * p->shape.warps;
+    thr = (int64_t)(total / (warps * 4 + 1));
+    thr = std::max<int64_t>(thr, 256);
+    thr = std::min<int64_t>(thr, (int64_t)1 << 22);
+  }
+  p->items = bd::build_items(npts, k, (uint64_t)thr);
+  std::vector<int64_t> P(points, points + (size_t)npts * k);
+#define PLAN_CUDA(call)                  \
+  do {                                   \
+    cudaError_t e_ = (call);             \
+    if (e_ != cudaSuccess) {             \
+      plan_free(p);                      \
+      return cuda_fail(e_, #call);       \
+    }                                    \
+  } while (0)
+  PLAN_CUDA(cudaMalloc(&p->d_pts, sizeof(int64_t) * P.size()));
+  PLAN_CUDA(cudaMemcpy(p->d_pts, P.data(), sizeof(int64_t) * P.size(), cudaMemcpyHostToDevice));
+  if (lifts) {
+    PLAN_CUDA(cudaMalloc(&p->d_lifts, sizeof(int64_t) * npts));
+    PLAN_CUDA(cudaMemcpy(p->d_lifts, lifts, sizeof(int64_t) * npts, cudaMemcpyHostToDevice));
+  }
+  PLAN_CUDA(cudaMalloc(&p->d_items, sizeof(bd::Item) * std::max<size_t>(1, p->items.size())));
+  if (!p->items.empty())
+    PLAN_CUDA(cudaMemcpy(p->d_items, p->items.data(), sizeof(bd::Item) * p->items.size(), cudaMemcpyHostToDevice));
+  PLAN_CUDA(cudaMalloc(&p->d_state, state_bytes()));
+  PLAN_CUDA(cudaMallocHost(&p->h_acc, sizeof(bd::DevAcc)));
+#undef PLAN_CUDA
+  *out = p;
+  return BD_OK;
+}
+
+int plan_launch(bd_plan* p, uint64_t seed, int attempt, cudaStream_t st) {
+  BD_CUDA(cudaMemsetAsync(p->d_state, 0, state_bytes(), st));
+  bd::EnumParams ep{};
+  ep.pts = p->d_pts;
+  ep.lifts = p->d_lifts;
+  ep.lift_seed = bd::lift_stream_seed(seed, (uint32_t)attempt);
+  ep.items = p->d_items;
+  ep.nitems = (int)p->items.size();
+  ep.N = p->N;
+  ep.K = p->K;
+  ep.acc = reinterpret_cast<bd::DevAcc*>(p->d_state);
+  ep.counter = reinterpret_cast<unsigned int*>(p->d_state + sizeof(bd::DevAcc));
+  BD_CUDA(bd::launch_enumerate(ep, p->shape, p->wide, st));
+  BD_CUDA(cudaMemcpyAsync(p->h_acc, p->d_state, sizeof(bd::DevAcc), cudaMemcpyDeviceToHost, st));
+  p->stream = st;
+  p->launched = true;
+  p->attempt = attempt;
+  return BD_OK;
+}
+
+int plan_read(bd_plan* p, bd_volume_out* out) {
+  if (!p->launched) return fail(BD_ERR_STATE, "plan has not been launched");
+  BD_CUDA(cudaStreamSynchronize(p->stream));
+  std::memset(out, 0, sizeof(*out));
+  const bd::DevAcc& a = *p->h_acc;
+  out->nvol_lo = a.nvol_lo;
+  out->nvol_hi = a.nvol_hi;
+  out->cells = a.cells;
+  out->singular = a.singular;
+  out->ties = a.ties;
+  out->subsets = bd::binom(p->N, p->K + 1);
+  out->relifts = p->attempt;
+  out->flags = (p->wide ? BD_FLAG_INT128 : 0) | ((a.nvol_lo | a.nvol_hi) == 0 ? BD_FLAG_DEGENERATE : 0);
+  out->max_abs_coord = (int32_t)std::min<int64_t>(p->max_abs, INT32_MAX);
+  out->bound_bits = (int32_t)std::ceil(p->bound);
+  if (a.items_done != p->items.size()) return fail(BD_ERR_CUDA, "enumeration did not process every work item");
+  return BD_OK;
+}
+
+int plan_volume(bd_plan* p, uint64_t seed, cudaStream_t st, bd_volume_out* out) {
+  const int tries = p->d_lifts ? 1 : MAX_LIFTINGS;
+  for (int attempt = 0; attempt < tries; ++attempt) {
+    int rc = plan_launch(p, seed, attempt, st);
+    if (rc) return rc;
+    rc = plan_read(p, out);
+    if (rc) return rc;
+    if (out->ties == 0) return BD_OK;
+  }
+  return fail(BD_ERR_TIES, p->d_lifts ? "the given lifting has ties" : "every allowed lifting had ties");
+}
+
+void degenerate_volume(int32_t npts, int32_t k, const int64_t* points, bd_volume_out* out) {
+  std::memset(out, 0, sizeof(*out));
+  out->flags = BD_FLAG_DEGENERATE;
+  out->subsets = bd::binom(npts, k + 1);
+  int64_t mx = 0;
+  for (int64_t i = 0; i < (int64_t)npts * k; ++i) mx = std::max<int64_t>(mx, std::llabs(points[i]));
+  out->max_abs_coord = (int32_t)std::min<int64_t>(mx, INT32_MAX);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* bd_last_error(void) { return g_err.c_str(); }
+
+int bd_set_stream(void* stream) {
+  g_stream = reinterpret_cast<cudaStream_t>(stream);
+  return BD_OK;
+}
+
+int bd_plan_create(const int64_t* points, int32_t npts, int32_t k, const bd_plan_opts* opts, bd_plan** plan) {
+  if (!plan) return fail(BD_ERR_ARG, "plan is NULL");
+  return plan_make(points, nullptr, npts, k, opts, plan);
+}
+
+int bd_plan_launch(bd_plan* plan, uint64_t seed, int32_t attempt, void* stream) {
+  if (!plan) return fail(BD_ERR_ARG, "plan is NULL");
+  return plan_launch(plan, seed, attempt, stream ? reinterpret_cast<cudaStream_t>(stream) : g_stream);
+}
+
+int bd_plan_read(bd_plan* plan, bd_volume_out* out) {
+  if (!plan || !out) return fail(BD_ERR_ARG, "NULL argument");
+  return plan_read(plan, out);
+}
+
+int bd_plan_volume(bd_plan* plan, uint64_t seed, bd_volume_out* out) {
+  if (!plan || !out) return fail(BD_ERR_ARG, "NULL argument");
+  return plan_volume(plan, seed, g_stream, out);
+}
+
+int bd_plan_info(const bd_plan* plan, int64_t* info) {
+  if (!plan || !info) return fail(BD_ERR_ARG, "NULL argument");
+  info[0] = (int64_t)plan->items.size();
+  info[1] = plan->shape.blocks;
+  info[2] = plan->shape.warps;
+  info[3] = (int64_t)plan->shape.smem;
+  info[4] = plan->wide ? 1 : 0;
+  info[5] = plan->shape.slots;
+  info[6] = 0;
+  info[7] = 0;
+  return BD_OK;
+}
+
+int bd_plan_destroy(bd_plan* plan) {
+  plan_free(plan);
+  return BD_OK;
+}
+
+int bd_volume(const int64_t* points, int32_t npts, int32_t k, uint64_t seed, bd_volume_out* out) {
+  if (!out) return fail(BD_ERR_ARG, "out is NULL");
+  int rc = check_points(points, npts, k);
+  if (rc) return rc;
+  if (npts < k + 1) {
+    degenerate_volume(npts, k, points, out);
+    return BD_OK;
+  }
+  bd_plan* p = nullptr;
+  rc = plan_make(points, nullptr, npts, k, nullptr, &p);
+  if (rc) return rc;
+  rc = plan_volume(p, seed, g_stream, out);
+  plan_free(p);
+  return rc;
+}
+
+int bd_volume_lifted(const int64_t* points, const int64_t* lifts, int32_t npts, int32_t k, bd_volume_out* out) {
+  if (!out || !lifts) return fail(BD_ERR_ARG, "NULL argument");
+  int rc = check_points(points, npts, k);
+  if (rc) return rc;
+  if (npts < k + 1) {
+    degenerate_volume(npts, k, points, out);
+    return BD_OK;
+  }
+  bd_plan* p = nullptr;
+  rc = plan_make(points, lifts, npts, k, nullptr, &p);
+  if (rc) return rc;
+  rc = plan_volume(p, 0, g_stream, out);
+  plan_free(p);
+  return rc;
+}
+
+int bd_reduce(const int64_t* A, int32_t n, int32_t m, const int64_t* coef, int64_t* points, int64_t* info) {
+  if (!A && m > 0) return fail(BD_ERR_ARG, "A is NULL");
+  if (!points || !info) return fail(BD_ERR_ARG, "NULL output");
+  if (n < 1 || n >= BD_NMAX || m < 0 || m > 256) return fail(BD_ERR_ARG, "need 1 <= n < BD_NMAX, 0 <= m <= 256");
+  bd::Reduction r;
+  std::string err;
+  int rc = bd::reduce_system(A, n, m, coef, r, err);
+  if (rc) return fail(rc, err);
+  std::memcpy(points, r.points.data(), sizeof(int64_t) * r.points.size());
+  info[0] = r.rank;
+  info[1] = r.dim;
+  info[2] = (int64_t)r.torsion;
+  info[3] = r.consistent ? 1 : 0;
+  info[4] = r.max_abs_coord;
+  info[5] = info[6] = info[7] = 0;
+  return BD_OK;
+}
+
+int bd_degree(const int64_t* A, int32_t n, int32_t m, const int64_t* coef, uint64_t seed, bd_degree_out* out) {
+  if (!out) return fail(BD_ERR_ARG, "out is NULL");
+  if (!A && m > 0) return fail(BD_ERR_ARG, "A is NULL");
+  if (n < 1 || n >= BD_NMAX || m < 0 || m > 256) return fail(BD_ERR_ARG, "need 1 <= n < BD_NMAX, 0 <= m <= 256");
+  std::memset(out, 0, sizeof(*out));
+  bd::Reduction r;
+  std::string err;
+  int rc = bd::reduce_system(A, n, m, coef, r, err);
+  if (rc) return fail(rc, err);
+  out->rank = r.rank;
+  out->dim = r.dim;
+  out->torsion = r.torsion;
+  out->consistent = r.consistent ? 1 : 0;
+  out->max_abs_coord = (int32_t)r.max_abs_coord;
+  if (!r.consistent) {
+    out->flags = BD_FLAG_INCONSISTENT;
+    return BD_OK;
+  }
+  if (r.dim == 0) {  // isolated points (Prop. 1)
+    set_u128(out->nvol_lo, out->nvol_hi, 1);
+    set_u128(out->degree_lo, out->degree_hi, r.torsion);
+    return BD_OK;
+  }
+  if (r.dim > BD_KMAX) return fail(BD_ERR_ARG, "solution dimension exceeds BD_KMAX");
+  bd_volume_out v;
+  rc = bd_volume(r.points.data(), n + 1, r.dim, seed, &v);
+  if (rc) return rc;
+  const u128 nvol = ((u128)v.nvol_hi << 64) | v.nvol_lo;
+  const u128 deg = nvol * r.torsion;
+  if (r.torsion && deg / r.torsion != nvol) return fail(BD_ERR_OVERFLOW, "degree exceeds 2^128");
+  set_u128(out->nvol_lo, out->nvol_hi, nvol);
+  set_u128(out->degree_lo, out->degree_hi, deg);
+  out->relifts = v.relifts;
+  out->subsets = v.subsets;
+  out->cells = v.cells;
+  out->flags = v.flags;
+  return BD_OK;
+}
+
+int bd_classify(const int64_t* points, const int64_t* lifts, int32_t npts, int32_t k, const uint8_t* subsets,
+                int32_t count, int32_t* status, int64_t* absdet) {
+  int rc = check_points(points, npts, k);
+  if (rc) return rc;
+  if (!lifts || !subsets || !status || !absdet || count < 0) return fail(BD_ERR_ARG, "NULL argument");
+  if (npts < k + 1) return fail(BD_ERR_ARG, "need at least k+1 points");
+  for (int64_t i = 0; i < (int64_t)count; ++i) {
+    const uint8_t* s = subsets + i * (k + 1);
+    for (int j = 0; j <= k; ++j)
+      if (s[j] >= npts || (j && s[j] <= s[j - 1])) return fail(BD_ERR_ARG, "subset indices must increase and be < npts");
+  }
+  if (count == 0) return BD_OK;
+  int64_t lo = lifts[0], hi = lifts[0];
+  for (int i = 0; i < npts; ++i) {
+    lo = std::min(lo, lifts[i]);
+    hi = std::max(hi, lifts[i]);
+  }
+  const double bound = bd::hadamard_log2(points, lifts, npts, k, hi - lo);
+  if (bound >= INT128_BITS) return fail(BD_ERR_OVERFLOW, "Hadamard bound exceeds 2^127");
+  const bool wide = bound >= INT64_BITS;
+  cudaStream_t st = g_stream;
+  int64_t *d_pts = nullptr, *d_lifts = nullptr, *d_abs = nullptr;
+  uint8_t* d_sub = nullptr;
+  int32_t* d_status = nullptr;
+  auto cleanup = [&]() {
+    cudaFree(d_pts);
+    cudaFree(d_lifts);
+    cudaFree(d_abs);
+    cudaFree(d_sub);
+    cudaFree(d_status);
+  };
+  cudaError_t e = cudaSuccess;
+  const char* where = "";
+#define CL(call)                 \
+  if (e == cudaSuccess) {        \
+    e = (call);                  \
+    if (e != cudaSuccess) where = #call; \
+  }
+  CL(cudaMalloc(&d_pts, sizeof(int64_t) * npts * k));
+  CL(cudaMalloc(&d_lifts, sizeof(int64_t) * npts));
+  CL(cudaMalloc(&d_abs, sizeof(int64_t) * count));
+  CL(cudaMalloc(&d_sub, (size_t)count * (k + 1)));
+  CL(cudaMalloc(&d_status, sizeof(int32_t) * count));
+  CL(cudaMemcpyAsync(d_pts, points, sizeof(int64_t) * npts * k, cudaMemcpyHostToDevice, st));
+  CL(cudaMemcpyAsync(d_lifts, lifts, sizeof(int64_t) * npts, cudaMemcpyHostToDevice, st));
+  CL(cudaMemcpyAsync(d_sub, subsets, (size_t)count * (k + 1), cudaMemcpyHostToDevice, st));
+  CL(bd::launch_classify(d_pts, d_lifts, npts, k, d_sub, count, d_status, d_abs, wide, st));
+  CL(cudaMemcpyAsync(status, d_status, sizeof(int32_t) * count, cudaMemcpyDeviceToHost, st));
+  CL(cudaMemcpyAsync(absdet, d_abs, sizeof(int64_t) * count, cudaMemcpyDeviceToHost, st));
+  CL(cudaStreamSynchronize(st));
+#undef CL
+  cleanup();
+  if (e != cudaSuccess) return cuda_fail(e, where);
+  return BD_OK;
+}
+
+int bd_host_volume_lifted(const int64_t* points, const int64_t* lifts, int32_t npts, int32_t k, int32_t threads,
+                          bd_volume_out* out) {
+  if (!out || !lifts) return fail(BD_ERR_ARG, "NULL argument");
+  int rc = check_points(points, npts, k);
+  if (rc) return rc;
+  if (npts < k + 1) {
+    degenerate_volume(npts, k, points, out);
+    return BD_OK;
+  }
+  int64_t lo = lifts[0], hi = lifts[0];
+  for (int i = 0; i < npts; ++i) {
+    lo = std::min(lo, lifts[i]);
+    hi = std::max(hi, lifts[i]);
+  }
+  const double bound = bd::hadamard_log2(points, lifts, npts, k, hi - lo);
+  if (bound >= INT128_BITS) return fail(BD_ERR_OVERFLOW, "Hadamard bound exceeds 2^127");
+  const bool wide = bound >= INT64_BITS;
+  std::vector<int64_t> P((size_t)(k + 1) * npts);
+  for (int q = 0; q < npts; ++q) {
+    for (int c = 0; c < k; ++c) P[(size_t)c * npts + q] = points[(size_t)q * k + c];
+    P[(size_t)k * npts + q] = lifts[q];
+  }
+  const auto items = bd::build_items(npts, k, 4096);
+  bd::Acc acc{};
+  if (wide) bd::host_enumerate<i128>(P.data(), npts, k, items, std::max(1, threads), acc);
+  else bd::host_enumerate<int64_t>(P.data(), npts, k, items, std::max(1, threads), acc);
+  std::memset(out, 0, sizeof(*out));
+  set_u128(out->nvol_lo, out->nvol_hi, acc.nvol);
+  out->cells = acc.cells;
+  out->singular = acc.singular;
+  out->ties = acc.ties;
+  out->subsets = bd::binom(npts, k + 1);
+  out->flags = (wide ? BD_FLAG_INT128 : 0) | (acc.nvol == 0 ? BD_FLAG_DEGENERATE : 0);
+  int64_t mx = 0;
+  for (int64_t i = 0; i < (int64_t)npts * k; ++i) mx = std::max<int64_t>(mx, std::llabs(points[i]));
+  out->max_abs_coord = (int32_t)std::min<int64_t>(mx, INT32_MAX);
+  out->bound_bits = (int32_t)std::ceil(bound);
+  if (acc.ties) return fail(BD_ERR_TIES, "the given lifting has ties");
+  return BD_OK;
+}
+
+}  // extern "C"

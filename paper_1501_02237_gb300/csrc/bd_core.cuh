@@ -1,0 +1,306 @@
+// Exact lower-facet enumeration core, shared by the CUDA warp kernel and its host emulation.
+//
+// Method (Sec. 4, Eq. lower-face; strict form Sec. 5, Eq. lower-d-face-again): for a lifted
+// point set S^ = {(a_q, w_q)} in Z^{K+1}, a (K+1)-subset {s_0 < .. < s_K} is a lower facet iff
+// its coordinate simplex is full-dimensional (D0 = det(a_{s_j} - a_{s_0}) != 0) and every
+// other lifted point lies strictly above the hyperplane through the lifted subset.  With
+// M = [a_{s_j} - a_{s_0}], w = [w_{s_j} - w_{s_0}] and z_q = (a_q - a_{s_0}, w_q - w_{s_0}),
+//     s(q) = det [[M, w], [z_q]]  =  D0 * (height of q above the hyperplane),
+// so q is strictly above iff sign s(q) = sign D0.  NVol = sum |D0| over accepted cells
+// (Eq. simplex-vol read as |det|).
+//
+// Evaluation order (this file's own design, not the paper's LP traversal):
+//   * subsets are enumerated depth-first in lexicographic order; level j fixes s_j;
+//   * the state at level j is the fraction-free (Bareiss) reduction of EVERY point's
+//     lifted difference row z_q against the pivot rows of s_1..s_j: an entry of state j at
+//     a surviving column c equals the (j+1)x(j+1) minor det(rows s_1..s_j, q ; pivot cols, c)
+//     (Sylvester's identity), so each level costs one update per point and surviving column
+//     and is shared by the whole subtree below it;
+//   * pivots are taken in coordinate columns only; a pivot row with no nonzero coordinate
+//     entry means every subset extending the prefix has D0 = 0 (counted as singular, skipped);
+//   * after K-1 levels each point q carries two numbers (C_q, L_q): the K x K minors with the
+//     last coordinate column and with the lift column.  For the last point p,
+//         D0 = sigma * C_p,   s(q) = sigma * (C_p L_q - C_q L_p) / p_{K-1},
+//     (sigma = column-permutation sign, common to both) so the test of q is one more
+//     Bareiss step and a sign compare;
+//   * a warp owns one subtree; lane l holds points l, l+32, ...; a warp vote decides each cell.
+//
+// Exactness: entries are minors bounded by a Hadamard bound checked on the host, so each fits
+// the entry type (int64 or int128).  The Bareiss division (a p - b r) / d is exact; it is done
+// modulo 2^64 (2^128) as in T. Jebelean, "An algorithm for exact division", J. Symbolic
+// Computation 15 (1993): drop the t trailing zero bits of d (t = ctz d, using the high product
+// bits when t > 0) and multiply by the inverse of the odd part of d modulo 2^64, obtained by
+// Newton-Hensel lifting x <- x (2 - d x).
+#pragma once
+
+#include <stdint.h>
+
+#ifdef __CUDACC__
+#define BD_HD __host__ __device__ __forceinline__
+#else
+#define BD_HD inline
+#endif
+
+namespace bd {
+
+typedef __int128 i128;
+typedef unsigned __int128 u128;
+
+BD_HD int ctz64(uint64_t x) {
+#ifdef __CUDA_ARCH__
+  return __ffsll((long long)x) - 1;
+#else
+  return __builtin_ctzll(x);
+#endif
+}
+
+BD_HD int ctz128(u128 x) {
+  uint64_t lo = (uint64_t)x;
+  return lo ? ctz64(lo) : 64 + ctz64((uint64_t)(x >> 64));
+}
+
+// ---------------------------------------------------------------------------------------------
+// exact division by a fixed nonzero divisor
+// ---------------------------------------------------------------------------------------------
+struct Div64 {
+  uint64_t inv;  // inverse of the odd part of d modulo 2^64
+  int shift;     // number of trailing zero bits of d
+};
+
+BD_HD Div64 make_div(int64_t d) {
+  Div64 r;
+  r.shift = ctz64((uint64_t)d);
+  uint64_t odd = (uint64_t)(d >> r.shift);  // exact: 2^shift divides d
+  uint64_t x = odd;                          // odd*odd = 1 mod 8: 3 correct bits
+  for (int i = 0; i < 5; ++i) x *= 2u - odd * x;  // 6, 12, 24, 48, 96 bits
+  r.inv = x;
+  return r;
+}
+
+struct Div128 {
+  u128 inv;
+  int shift;
+};
+
+BD_HD Div128 make_div(i128 d) {
+  Div128 r;
+  r.shift = ctz128((u128)d);
+  u128 odd = (u128)(d >> r.shift);
+  u128 x = odd;
+  for (int i = 0; i < 6; ++i) x *= (u128)2 - odd * x;  // ... 192 bits
+  r.inv = x;
+  return r;
+}
+
+// (a*p - b*r) / d, exact, for a quotient that fits int64.
+BD_HD int64_t bareiss(int64_t a, int64_t p, int64_t b, int64_t r, const Div64& D) {
+  if (D.shift == 0) {
+    uint64_t v = (uint64_t)a * (uint64_t)p - (uint64_t)b * (uint64_t)r;  // mod 2^64
+    return (int64_t)(v * D.inv);
+  }
+  i128 v = (i128)a * p - (i128)b * r;  // |a p|, |b r| < 2^126: exact
+  uint64_t lo = (uint64_t)(v >> D.shift);
+  return (int64_t)(lo * D.inv);
+}
+
+// signed 128 x 128 -> 256 product as (hi, lo)
+BD_HD void mul_wide(i128 a, i128 b, u128& hi, u128& lo) {
+  u128 ua = (u128)a, ub = (u128)b;
+  uint64_t a0 = (uint64_t)ua, a1 = (uint64_t)(ua >> 64);
+  uint64_t b0 = (uint64_t)ub, b1 = (uint64_t)(ub >> 64);
+  u128 p00 = (u128)a0 * b0, p01 = (u128)a0 * b1, p10 = (u128)a1 * b0, p11 = (u128)a1 * b1;
+  u128 mid = (p00 >> 64) + (uint64_t)p01 + (uint64_t)p10;
+  lo = (u128)(uint64_t)p00 | ((u128)(uint64_t)mid << 64);
+  hi = p11 + (p01 >> 64) + (p10 >> 64) + (mid >> 64);
+  if (a < 0) hi -= ub;  // two's-complement correction of the unsigned product
+  if (b < 0) hi -= ua;
+}
+
+// (a*p - b*r) / d, exact, for a quotient that fits int128.
+BD_HD i128 bareiss(i128 a, i128 p, i128 b, i128 r, const Div128& D) {
+  if (D.shift == 0) {
+    u128 v = (u128)a * (u128)p - (u128)b * (u128)r;  // mod 2^128
+    return (i128)(v * D.inv);
+  }
+  u128 h1, l1, h2, l2;
+  mul_wide(a, p, h1, l1);
+  mul_wide(b, r, h2, l2);
+  u128 lo = l1 - l2;
+  u128 hi = h1 - h2 - (u128)(l1 < l2);
+  int t = D.shift;  // 0 < t < 127
+  u128 q = (lo >> t) | (hi << (128 - t));
+  return (i128)(q * D.inv);
+}
+
+// ---------------------------------------------------------------------------------------------
+// work items and per-team accumulators
+// ---------------------------------------------------------------------------------------------
+constexpr int KMAX = 14;           // largest lattice dimension K (a work item is 16 bytes)
+constexpr int NMAX = 64;           // largest number of points (one 64-bit membership mask)
+
+struct Item {                      // a subset prefix s_0 < .. < s_{L-1}, 1 <= L <= K
+  uint8_t len;
+  uint8_t idx[15];
+};
+
+struct Acc {
+  u128 nvol;         // sum of |D0| over accepted cells
+  uint64_t cells;    // accepted cells
+  uint64_t singular; // subsets with D0 = 0
+  uint64_t ties;     // subsets with no point below and at least one point on the hyperplane
+};
+
+BD_HD uint64_t binom(int n, int k) {
+  if (k < 0 || n < k) return 0;
+  if (k > n - k) k = n - k;
+  uint64_t r = 1;
+  for (int i = 1; i <= k; ++i) r = r * (uint64_t)(n - k + i) / (uint64_t)i;
+  return r;
+}
+
+// number of (K+1)-subsets below a prefix whose last index is `last` and length `len`
+BD_HD uint64_t subtree_size(int N, int K, int last, int len) { return binom(N - 1 - last, K + 1 - len); }
+
+// offset of level j inside a point's stack: sum_{i<j} (K+1-i)
+BD_HD int level_offset(int K, int j) { return j * (K + 1) - (j * (j - 1)) / 2; }
+BD_HD int stack_entries(int K) { return level_offset(K, K); }
+
+template <class T> struct DivOf;
+template <> struct DivOf<int64_t> { typedef Div64 type; };
+template <> struct DivOf<i128> { typedef Div128 type; };
+
+template <class T> BD_HD T tabs(T x) { return x < 0 ? -x : x; }
+
+// ---------------------------------------------------------------------------------------------
+// The DFS state of one team (a warp on the GPU, one thread in the host emulation).
+//
+// Team provides lane(), lanes(), any(bool), sync().  Points are owned round-robin by lanes;
+// `st` is this team's stack: entry (level j, column e, point q) at st[(off_j + e) * SLOTS + q].
+// `P` holds the lifted points column-major: P[c * N + q], c < K coordinates, c = K the lift.
+// ---------------------------------------------------------------------------------------------
+enum { ST_SINGULAR = 0, ST_REJECTED = 1, ST_ACCEPTED = 2, ST_TIE = 3 };
+
+template <class T, class Team>
+struct Walker {
+  typedef typename DivOf<T>::type Div;
+  Team& tm;
+  const int64_t* P;
+  int N, K, SLOTS;
+  T* st;
+  int s[KMAX + 1];  // chosen indices s_0 .. s_j
+  Div dv[KMAX];     // exact divider by the pivot of each level (dv[0]: by 1)
+
+  BD_HD Walker(Team& t, const int64_t* P_, int N_, int K_, int SLOTS_, T* st_)
+      : tm(t), P(P_), N(N_), K(K_), SLOTS(SLOTS_), st(st_) {}
+
+  // state 0: lifted differences z_q = (a_q - a_{s_0}, w_q - w_{s_0})
+  BD_HD void start(int s0) {
+    tm.sync();  // the previous item's readers are done with the stack
+    s[0] = s0;
+    for (int q = tm.lane(); q < N; q += tm.lanes())
+      for (int c = 0; c <= K; ++c) st[c * SLOTS + q] = (T)(P[c * N + q] - P[c * N + s0]);
+    dv[0] = make_div((T)1);
+    tm.sync();
+  }
+
+  // state j from state j-1 with pivot point c (s_j = c); false if the pivot row has no
+  // nonzero coordinate entry (every subset extending the prefix is singular)
+  BD_HD bool build(int j, int c) {
+    const int po = level_offset(K, j - 1), no = level_offset(K, j);
+    const int ncoord = K - j + 1;  // coordinate entries of state j-1; its lift is at index ncoord
+    int pi = -1;
+    for (int e = 0; e < ncoord; ++e)
+      if (st[(po + e) * SLOTS + c] != 0) { pi = e; break; }
+    if (pi < 0) return false;
+    const T pj = st[(po + pi) * SLOTS + c];
+    const Div D = dv[j - 1];
+    tm.sync();  // readers of the old state j (a sibling's subtree) are done
+    for (int q = tm.lane(); q < N; q += tm.lanes()) {
+      const T bq = st[(po + pi) * SLOTS + q];
+      for (int e = 0; e < ncoord; ++e) {  // state j: K-j coordinates + lift = ncoord entries
+        const int ep = e < pi ? e : e + 1;
+        st[(no + e) * SLOTS + q] = bareiss(st[(po + ep) * SLOTS + q], pj, bq, st[(po + ep) * SLOTS + c], D);
+      }
+    }
+    dv[j] = make_div(pj);
+    s[j] = c;
+    tm.sync();
+    return true;
+  }
+
+  BD_HD uint64_t member_mask() const {
+    uint64_t mask = 0;
+    for (int i = 0; i < K; ++i) mask |= 1ull << s[i];
+    return mask;
+  }
+
+  // status of the cell {s_0 .. s_{K-1}, p}; |D0| in absdet.  Uniform across the team.
+  BD_HD int leaf(int p, uint64_t mask, T& absdet) {
+    const int lo = level_offset(K, K - 1);
+    const T Cp = st[lo * SLOTS + p];
+    const T Lp = st[(lo + 1) * SLOTS + p];
+    absdet = tabs(Cp);
+    if (Cp == 0) return ST_SINGULAR;
+    const Div D = dv[K - 1];
+    bool below = false, on = false;
+    for (int q = tm.lane(); q < N; q += tm.lanes()) {
+      if (((mask >> q) & 1ull) || q == p) continue;
+      const T sq = bareiss(st[(lo + 1) * SLOTS + q], Cp, st[lo * SLOTS + q], Lp, D);
+      if (sq == 0) on = true;
+      else if ((sq < 0) != (Cp < 0)) below = true;
+    }
+    const bool any_below = tm.any(below);
+    const bool any_on = tm.any(on);
+    return any_below ? ST_REJECTED : (any_on ? ST_TIE : ST_ACCEPTED);
+  }
+
+  // every (K+1)-subset extending the prefix it.idx[0 .. it.len-1]
+  BD_HD void run_item(const Item& it, Acc& acc) {
+    const int L = it.len;
+    start(it.idx[0]);
+    for (int j = 1; j < L; ++j) {
+      if (!build(j, it.idx[j])) {
+        acc.singular += subtree_size(N, K, it.idx[L - 1], L);
+        return;
+      }
+    }
+    int cur[KMAX + 1];
+    int j = L;
+    cur[j] = it.idx[L - 1];
+    for (;;) {
+      if (j == K) {
+        const uint64_t mask = member_mask();
+        for (int p = s[K - 1] + 1; p < N; ++p) {
+          T ad;
+          const int stt = leaf(p, mask, ad);
+          if (stt == ST_ACCEPTED) { acc.cells += 1; acc.nvol += (u128)ad; }
+          else if (stt == ST_SINGULAR) acc.singular += 1;
+          else if (stt == ST_TIE) acc.ties += 1;
+        }
+        if (--j < L) break;
+        continue;
+      }
+      const int c = ++cur[j];
+      if (c > N - 1 - (K - j)) {
+        if (--j < L) break;
+        continue;
+      }
+      if (!build(j, c)) {
+        acc.singular += binom(N - 1 - c, K - j);
+        continue;
+      }
+      ++j;
+      cur[j] = c;
+    }
+  }
+
+  // status of one given subset sub[0] < .. < sub[K]
+  BD_HD int classify(const uint8_t* sub, T& absdet) {
+    start(sub[0]);
+    for (int j = 1; j < K; ++j)
+      if (!build(j, sub[j])) { absdet = 0; return ST_SINGULAR; }
+    return leaf(sub[K], member_mask(), absdet);
+  }
+};
+
+}  // namespace bd

@@ -1,0 +1,387 @@
+// Host front end of the degree computation (Sec. 2-3 of the paper) and the CPU emulation of
+// the GPU enumeration.  Plain C++17, no CUDA.
+#include "bd_host.h"
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdlib>
+#include <thread>
+
+#include "../../include/binodeg.h"
+
+namespace bd {
+
+namespace {
+
+const i128 ENTRY_LIMIT = (i128)1 << 62;  // Smith-form entries stay below 2^62 so products fit i128
+
+struct Mat {
+  int r = 0, c = 0;
+  std::vector<i128> a;
+  Mat() {}
+  Mat(int r_, int c_) : r(r_), c(c_), a((size_t)r_ * c_, 0) {}
+  i128& at(int i, int j) { return a[(size_t)i * c + j]; }
+  i128 at(int i, int j) const { return a[(size_t)i * c + j]; }
+  static Mat eye(int n) {
+    Mat m(n, n);
+    for (int i = 0; i < n; ++i) m.at(i, i) = 1;
+    return m;
+  }
+};
+
+i128 iabs(i128 x) { return x < 0 ? -x : x; }
+
+// extended Euclid: g = s a + t b = gcd(a, b) >= 0
+void xgcd(i128 a, i128 b, i128& g, i128& s, i128& t) {
+  i128 r0 = a, r1 = b, s0 = 1, s1 = 0, t0 = 0, t1 = 1;
+  while (r1 != 0) {
+    i128 q = r0 / r1;
+    i128 tmp = r0 - q * r1; r0 = r1; r1 = tmp;
+    tmp = s0 - q * s1; s0 = s1; s1 = tmp;
+    tmp = t0 - q * t1; t0 = t1; t1 = tmp;
+  }
+  if (r0 < 0) { r0 = -r0; s0 = -s0; t0 = -t0; }
+  g = r0; s = s0; t = t0;
+}
+
+// unimodular [[s, t], [u, v]] sending (a1, a2) to (g, 0) (Sec. 3); plain elimination when a1 | a2
+void bezout2(i128 a1, i128 a2, i128& s, i128& t, i128& u, i128& v) {
+  if (a2 % a1 == 0) { s = 1; t = 0; u = -(a2 / a1); v = 1; return; }
+  i128 g;
+  xgcd(a1, a2, g, s, t);
+  u = -(a2 / g);
+  v = a1 / g;
+}
+
+bool rows_op(Mat& X, int i, int j, i128 s, i128 t, i128 u, i128 v) {
+  for (int c = 0; c < X.c; ++c) {
+    i128 x = X.at(i, c), y = X.at(j, c);
+    i128 nx = s * x + t * y, ny = u * x + v * y;
+    if (iabs(nx) >= ENTRY_LIMIT || iabs(ny) >= ENTRY_LIMIT) return false;
+    X.at(i, c) = nx; X.at(j, c) = ny;
+  }
+  return true;
+}
+
+bool cols_op(Mat& X, int i, int j, i128 s, i128 t, i128 u, i128 v) {
+  for (int r = 0; r < X.r; ++r) {
+    i128 x = X.at(r, i), y = X.at(r, j);
+    i128 nx = s * x + t * y, ny = u * x + v * y;
+    if (iabs(nx) >= ENTRY_LIMIT || iabs(ny) >= ENTRY_LIMIT) return false;
+    X.at(r, i) = nx; X.at(r, j) = ny;
+  }
+  return true;
+}
+
+// Smith form by Bezout row and column reductions (Sec. 3): P A Q = diag(d_1..d_r, 0..).
+// M is overwritten by the diagonal form.  The divisibility chain is not produced.
+bool smith(Mat& M, Mat& P, Mat& Q, int& rank) {
+  const int n = M.r, m = M.c;
+  P = Mat::eye(n);
+  Q = Mat::eye(m);
+  int t = 0;
+  for (; t < std::min(n, m); ++t) {
+    int bi = -1, bj = -1;
+    for (int i = t; i < n; ++i)
+      for (int j = t; j < m; ++j)
+        if (M.at(i, j) != 0 && (bi < 0 || iabs(M.at(i, j)) < iabs(M.at(bi, bj)))) { bi = i; bj = j; }
+    if (bi < 0) break;
+    if (bi != t) {
+      for (int c = 0; c < m; ++c) std::swap(M.at(t, c), M.at(bi, c));
+      for (int c = 0; c < n; ++c) std::swap(P.at(t, c), P.at(bi, c));
+    }
+    if (bj != t) {
+      for (int r = 0; r < n; ++r) std::swap(M.at(r, t), M.at(r, bj));
+      for (int r = 0; r < m; ++r) std::swap(Q.at(r, t), Q.at(r, bj));
+    }
+    for (;;) {
+      bool dirty = false;
+      for (int i = t + 1; i < n; ++i) {
+        if (M.at(i, t) == 0) continue;
+        i128 s, tt, u, v;
+        bezout2(M.at(t, t), M.at(i, t), s, tt, u, v);
+        if (!rows_op(M, t, i, s, tt, u, v) || !rows_op(P, t, i, s, tt, u, v)) return false;
+        dirty = true;
+      }
+      for (int j = t + 1; j < m; ++j) {
+        if (M.at(t, j) == 0) continue;
+        i128 s, tt, u, v;
+        bezout2(M.at(t, t), M.at(t, j), s, tt, u, v);
+        if (!cols_op(M, t, j, s, tt, u, v) || !cols_op(Q, t, j, s, tt, u, v)) return false;
+        dirty = true;
+      }
+      if (!dirty) break;
+    }
+  }
+  rank = t;
+  return true;
+}
+
+u128 ugcd(u128 a, u128 b) {
+  while (b) { u128 r = a % b; a = b; b = r; }
+  return a;
+}
+
+// b^{Q_0} == 1 exactly (Eq. consistency), b_i = -c_{i,2} / c_{i,1}.  Numbers are split over a
+// coprime base (repeated gcd refinement), so exponents can be compared without factoring.
+bool consistent(const int64_t* coef, int m, const Mat& Q, int rank, std::string& err, bool& ok) {
+  std::vector<u128> num(m), den(m);
+  std::vector<int> neg(m);
+  for (int i = 0; i < m; ++i) {
+    const int64_t n1 = coef[4 * i], d1 = coef[4 * i + 1], n2 = coef[4 * i + 2], d2 = coef[4 * i + 3];
+    if (n1 == 0 || d1 == 0 || n2 == 0 || d2 == 0) { err = "coefficients and denominators must be nonzero"; return false; }
+    i128 p = -(i128)n2 * d1, q = (i128)d2 * n1;  // b_i = p / q
+    neg[i] = (p < 0) != (q < 0);
+    u128 up = (u128)iabs(p), uq = (u128)iabs(q);
+    u128 g = ugcd(up, uq);
+    num[i] = up / g;
+    den[i] = uq / g;
+  }
+  std::vector<u128> base;
+  for (int i = 0; i < m; ++i) {
+    if (num[i] > 1) base.push_back(num[i]);
+    if (den[i] > 1) base.push_back(den[i]);
+  }
+  for (bool changed = true; changed;) {
+    changed = false;
+    std::sort(base.begin(), base.end());
+    base.erase(std::unique(base.begin(), base.end()), base.end());
+    for (size_t i = 0; i < base.size() && !changed; ++i)
+      for (size_t j = i + 1; j < base.size() && !changed; ++j) {
+        u128 g = ugcd(base[i], base[j]);
+        if (g > 1) {
+          u128 x = base[i] / g, y = base[j] / g;
+          base.erase(base.begin() + j);
+          base.erase(base.begin() + i);
+          if (x > 1) base.push_back(x);
+          if (y > 1) base.push_back(y);
+          base.push_back(g);
+          changed = true;
+        }
+      }
+  }
+  auto val = [](u128 x, u128 b) {
+    int v = 0;
+    while (x % b == 0) { x /= b; ++v; }
+    return v;
+  };
+  ok = true;
+  for (int j = rank; j < m && ok; ++j) {
+    i128 sgn = 0;
+    for (int i = 0; i < m; ++i)
+      if (neg[i]) sgn += Q.at(i, j);
+    if (sgn % 2 != 0) ok = false;
+    for (size_t b = 0; b < base.size() && ok; ++b) {
+      i128 e = 0;
+      for (int i = 0; i < m; ++i) {
+        const int v = val(num[i], base[b]) - val(den[i], base[b]);
+        if (v) e += Q.at(i, j) * v;
+      }
+      if (e != 0) ok = false;
+    }
+  }
+  return true;
+}
+
+// LLL reduction (delta = 0.99) of the rows of B (d x n), exact integer row operations, Gram-
+// Schmidt data in double only to take decisions (any outcome is a basis of the same lattice).
+bool lll(std::vector<i128>& B, int d, int n) {
+  if (d <= 1) return true;
+  std::vector<double> mu((size_t)d * d), bn(d);
+  auto gso = [&]() {
+    std::vector<double> bs((size_t)d * n);
+    for (int i = 0; i < d; ++i) {
+      for (int c = 0; c < n; ++c) bs[(size_t)i * n + c] = (double)B[(size_t)i * n + c];
+      for (int j = 0; j < i; ++j) {
+        double dot = 0;
+        for (int c = 0; c < n; ++c) dot += (double)B[(size_t)i * n + c] * bs[(size_t)j * n + c];
+        const double m = bn[j] > 0 ? dot / bn[j] : 0.0;
+        mu[(size_t)i * d + j] = m;
+        for (int c = 0; c < n; ++c) bs[(size_t)i * n + c] -= m * bs[(size_t)j * n + c];
+      }
+      double s = 0;
+      for (int c = 0; c < n; ++c) s += bs[(size_t)i * n + c] * bs[(size_t)i * n + c];
+      bn[i] = s;
+    }
+  };
+  gso();
+  int k = 1;
+  long guard = 0;
+  while (k < d && guard++ < 200000) {
+    for (int j = k - 1; j >= 0; --j) {
+      const double m = mu[(size_t)k * d + j];
+      if (std::fabs(m) <= 0.5) continue;
+      const i128 q = (i128)std::llround(m);
+      for (int c = 0; c < n; ++c) {
+        const i128 v = B[(size_t)k * n + c] - q * B[(size_t)j * n + c];
+        if (iabs(v) >= ENTRY_LIMIT) return false;
+        B[(size_t)k * n + c] = v;
+      }
+      for (int l = 0; l < j; ++l) mu[(size_t)k * d + l] -= (double)q * mu[(size_t)j * d + l];
+      mu[(size_t)k * d + j] -= (double)q;
+    }
+    const double m = mu[(size_t)k * d + k - 1];
+    if (bn[k] < (0.99 - m * m) * bn[k - 1]) {
+      for (int c = 0; c < n; ++c) std::swap(B[(size_t)k * n + c], B[(size_t)(k - 1) * n + c]);
+      gso();
+      k = std::max(k - 1, 1);
+    } else {
+      ++k;
+    }
+  }
+  return true;
+}
+
+}  // namespace
+
+int reduce_system(const int64_t* A, int n, int m, const int64_t* coef, Reduction& out, std::string& err) {
+  Mat M(n, m);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < m; ++j) M.at(i, j) = A[(size_t)i * m + j];
+  Mat P, Q;
+  int rank = 0;
+  if (m > 0) {
+    if (!smith(M, P, Q, rank)) { err = "Smith form entries exceed 2^62"; return BD_ERR_OVERFLOW; }
+  } else {
+    P = Mat::eye(n);
+    Q = Mat(0, 0);
+  }
+  // Prop. 1: |prod d_j| components
+  u128 tors = 1;
+  for (int j = 0; j < rank; ++j) {
+    tors *= (u128)iabs(M.at(j, j));
+    if (tors >> 63) { err = "torsion exceeds 2^63"; return BD_ERR_OVERFLOW; }
+  }
+  out.rank = rank;
+  out.dim = n - rank;
+  out.torsion = (uint64_t)tors;
+  out.consistent = true;
+  if (coef && rank < m) {
+    bool ok = true;
+    if (!consistent(coef, m, Q, rank, err, ok)) return BD_ERR_ARG;
+    out.consistent = ok;
+  }
+  const int d = out.dim;
+  out.points.assign((size_t)(n + 1) * d, 0);
+  out.max_abs_coord = 0;
+  if (d == 0) return BD_OK;
+  // Eq. rank-decomp: P_0 = rows rank..n-1 of P; its columns are the points (Prop. 4)
+  std::vector<i128> B((size_t)d * n);
+  for (int i = 0; i < d; ++i)
+    for (int c = 0; c < n; ++c) B[(size_t)i * n + c] = P.at(rank + i, c);
+  if (!lll(B, d, n)) { err = "kernel basis entries exceed 2^62 during reduction"; return BD_ERR_OVERFLOW; }
+  for (int q = 0; q < n; ++q)
+    for (int i = 0; i < d; ++i) {
+      const i128 v = B[(size_t)i * n + q];
+      if (iabs(v) >= ((i128)1 << 40)) { err = "kernel point coordinate exceeds 2^40"; return BD_ERR_OVERFLOW; }
+      out.points[(size_t)q * d + i] = (int64_t)v;
+      out.max_abs_coord = std::max<int64_t>(out.max_abs_coord, (int64_t)iabs(v));
+    }
+  return BD_OK;
+}
+
+double hadamard_log2(const int64_t* pts, const int64_t* lifts, int npts, int k, int64_t max_lift_spread) {
+  // Column-wise Hadamard bound for the (K+1) x (K+1) lifted difference matrices: for column c
+  // and base point s, the K+1 largest squared differences |a_q[c] - a_s[c]|^2 bound the
+  // squared column norm; the bound is the product over columns of the worst base point.
+  double total = 0;
+  std::vector<double> sq(npts);
+  for (int c = 0; c <= k; ++c) {
+    double best = 1.0;
+    for (int s = 0; s < npts; ++s) {
+      for (int q = 0; q < npts; ++q) {
+        double diff;
+        if (c < k) diff = (double)(pts[(size_t)q * k + c] - pts[(size_t)s * k + c]);
+        else if (lifts) diff = (double)(lifts[q] - lifts[s]);
+        else diff = (double)max_lift_spread;
+        sq[q] = diff * diff;
+      }
+      std::sort(sq.begin(), sq.end(), [](double a, double b) { return a > b; });
+      double sum = 0;
+      for (int i = 0; i < std::min(k + 1, npts); ++i) sum += sq[i];
+      best = std::max(best, sum);
+    }
+    total += 0.5 * std::log2(best);
+  }
+  return total;
+}
+
+std::vector<Item> build_items(int N, int K, uint64_t max_subsets) {
+  std::vector<Item> items;
+  if (K < 1 || N < K + 1) return items;
+  std::vector<int> pre(K + 1);
+  int len = 1;
+  pre[0] = 0;
+  for (;;) {
+    const uint64_t T = subtree_size(N, K, pre[len - 1], len);
+    if (T > max_subsets && len < K) {  // split: descend to the first child
+      pre[len] = pre[len - 1] + 1;
+      ++len;
+      continue;
+    }
+    if (T > 0) {
+      Item x{};
+      x.len = (uint8_t)len;
+      for (int i = 0; i < len; ++i) x.idx[i] = (uint8_t)pre[i];
+      items.push_back(x);
+    }
+    // next sibling, backtracking as needed; position i admits indices up to N-1-(K-i)
+    for (;;) {
+      const int nxt = pre[len - 1] + 1;
+      if (nxt <= N - 1 - (K - (len - 1))) { pre[len - 1] = nxt; break; }
+      if (--len == 0) break;
+    }
+    if (len == 0) break;
+  }
+  std::stable_sort(items.begin(), items.end(), [&](const Item& a, const Item& b) {
+    return subtree_size(N, K, a.idx[a.len - 1], a.len) > subtree_size(N, K, b.idx[b.len - 1], b.len);
+  });
+  return items;
+}
+
+namespace {
+struct HostTeam {
+  int lane() const { return 0; }
+  int lanes() const { return 1; }
+  bool any(bool b) const { return b; }
+  void sync() const {}
+};
+}  // namespace
+
+template <class T>
+void host_enumerate(const int64_t* P, int N, int K, const std::vector<Item>& items, int threads, Acc& acc) {
+  std::atomic<size_t> next(0);
+  std::vector<Acc> part(std::max(1, threads));
+  auto work = [&](int tid) {
+    HostTeam tm;
+    std::vector<T> st((size_t)N * stack_entries(K));
+    Walker<T, HostTeam> W(tm, P, N, K, N, st.data());
+    Acc a{};
+    for (;;) {
+      const size_t i = next.fetch_add(1);
+      if (i >= items.size()) break;
+      W.run_item(items[i], a);
+    }
+    part[tid] = a;
+  };
+  if (threads <= 1) {
+    work(0);
+  } else {
+    std::vector<std::thread> th;
+    for (int t = 0; t < threads; ++t) th.emplace_back(work, t);
+    for (auto& t : th) t.join();
+  }
+  acc = Acc{};
+  for (auto& a : part) {
+    acc.nvol += a.nvol;
+    acc.cells += a.cells;
+    acc.singular += a.singular;
+    acc.ties += a.ties;
+  }
+}
+
+template void host_enumerate<int64_t>(const int64_t*, int, int, const std::vector<Item>&, int, Acc&);
+template void host_enumerate<i128>(const int64_t*, int, int, const std::vector<Item>&, int, Acc&);
+
+}  // namespace bd

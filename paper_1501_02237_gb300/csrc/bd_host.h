@@ -1,0 +1,39 @@
+// Host front end: Smith form, consistency, LLL-reduced kernel points, Hadamard bound,
+// work-list construction.  Plain C++ (no CUDA), shared by the C ABI and the host emulation.
+#pragma once
+
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "bd_core.cuh"
+
+namespace bd {
+
+struct Reduction {
+  int rank = 0, dim = 0;
+  uint64_t torsion = 1;
+  bool consistent = true;
+  std::vector<int64_t> points;  // (n + 1) x dim, row-major; last row the origin
+  int64_t max_abs_coord = 0;
+};
+
+// Returns BD_OK or an error code; message in `err`.
+int reduce_system(const int64_t* A, int n, int m, const int64_t* coef, Reduction& out, std::string& err);
+
+// ceil(log2) of a Hadamard bound on every minor of the lifted difference matrices
+// [a_q - a_s, w_q - w_s] (rows q, K+1 of them) that the enumeration forms.
+double hadamard_log2(const int64_t* pts, const int64_t* lifts_maxdiff_or_null, int npts, int k,
+                     int64_t max_lift_spread);
+
+// Prefix work list: every (k+1)-subset of {0..npts-1} lies below exactly one item; items are
+// split until each holds at most `max_subsets` subsets (or reaches length k), then sorted by
+// decreasing size.
+std::vector<Item> build_items(int npts, int k, uint64_t max_subsets);
+
+// Host emulation of the warp enumeration on `threads` CPU threads.
+template <class T>
+void host_enumerate(const int64_t* P, int N, int K, const std::vector<Item>& items, int threads, Acc& acc);
+
+}  // namespace bd

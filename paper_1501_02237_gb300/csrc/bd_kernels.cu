@@ -1,0 +1,182 @@
+// CUDA kernels of the lower-facet enumeration (sm_103a).
+//
+// k_enumerate is persistent: every warp repeatedly takes the next work item (a subset prefix,
+// largest first) from a global counter and walks all (K+1)-subsets below it with the exact
+// level-by-level Bareiss state of bd_core.cuh.  The lifted points sit in shared memory
+// (column-major, one int64 per coordinate); each warp has its own stack of reduced rows in
+// shared memory, laid out [level entry][point] so that lane l touches consecutive 8-byte
+// (16-byte for the wide path) words and a pivot row is a broadcast read.  Per-warp results
+// stay in registers and are added once to the global accumulators at the end (128-bit sum
+// by two 64-bit atomics with carry).
+#include "bd_kernels.cuh"
+#include "bd_lifts.h"
+
+namespace bd {
+
+namespace {
+
+struct WarpTeam {
+  BD_HD int lane() const {
+#ifdef __CUDA_ARCH__
+    return threadIdx.x & 31;
+#else
+    return 0;
+#endif
+  }
+  BD_HD int lanes() const { return 32; }
+  BD_HD bool any(bool b) const {
+#ifdef __CUDA_ARCH__
+    return __any_sync(0xffffffffu, b);
+#else
+    return b;
+#endif
+  }
+  BD_HD void sync() const {
+#ifdef __CUDA_ARCH__
+    __syncwarp();
+#endif
+  }
+};
+
+__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+__host__ __device__ inline int round32(int x) { return (x + 31) & ~31; }
+
+__device__ void load_points(int64_t* P, const EnumParams& p) {
+  const int N = p.N, K = p.K;
+  for (int i = threadIdx.x; i < N * K; i += blockDim.x) {
+    const int q = i / K, c = i - q * K;
+    P[c * N + q] = p.pts[i];
+  }
+  for (int q = threadIdx.x; q < N; q += blockDim.x)
+    P[K * N + q] = p.lifts ? p.lifts[q] : lift_height(p.lift_seed, q);
+  __syncthreads();
+}
+
+__device__ void flush(const Acc& a, DevAcc* g, unsigned long long items) {
+  const unsigned long long lo = (unsigned long long)(uint64_t)a.nvol;
+  const unsigned long long hi = (unsigned long long)(uint64_t)(a.nvol >> 64);
+  const unsigned long long old = atomicAdd(&g->nvol_lo, lo);
+  const unsigned long long carry = (old + lo < old) ? 1ull : 0ull;
+  if (hi + carry) atomicAdd(&g->nvol_hi, hi + carry);
+  if (a.cells) atomicAdd(&g->cells, (unsigned long long)a.cells);
+  if (a.singular) atomicAdd(&g->singular, (unsigned long long)a.singular);
+  if (a.ties) atomicAdd(&g->ties, (unsigned long long)a.ties);
+  if (items) atomicAdd(&g->items_done, items);
+}
+
+template <class T>
+__global__ void k_enumerate(EnumParams p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  int64_t* P = reinterpret_cast<int64_t*>(smem);
+  const int N = p.N, K = p.K;
+  const int slots = round32(N);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  T* st = reinterpret_cast<T*>(smem + align16((size_t)(K + 1) * N * sizeof(int64_t))) +
+          (size_t)warp * slots * stack_entries(K);
+  load_points(P, p);
+
+  WarpTeam tm;
+  Walker<T, WarpTeam> W(tm, P, N, K, slots, st);
+  Acc acc{};
+  unsigned long long done = 0;
+  for (;;) {
+    unsigned int i = 0;
+    if (lane == 0) i = atomicAdd(p.counter, 1u);
+    i = __shfl_sync(0xffffffffu, i, 0);
+    if (i >= (unsigned int)p.nitems) break;
+    const Item it = p.items[i];
+    W.run_item(it, acc);
+    ++done;
+  }
+  if (lane == 0) flush(acc, p.acc, done);
+}
+
+template <class T>
+__global__ void k_classify(const int64_t* pts, const int64_t* lifts, int N, int K, const uint8_t* subsets,
+                           int count, int32_t* status, int64_t* absdet) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  int64_t* P = reinterpret_cast<int64_t*>(smem);
+  EnumParams p{};
+  p.pts = pts;
+  p.lifts = lifts;
+  p.N = N;
+  p.K = K;
+  load_points(P, p);
+  const int slots = round32(N);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, warps = blockDim.x >> 5;
+  T* st = reinterpret_cast<T*>(smem + align16((size_t)(K + 1) * N * sizeof(int64_t))) +
+          (size_t)warp * slots * stack_entries(K);
+  WarpTeam tm;
+  Walker<T, WarpTeam> W(tm, P, N, K, slots, st);
+  for (int i = blockIdx.x * warps + warp; i < count; i += gridDim.x * warps) {
+    T ad = 0;
+    const int s = W.classify(subsets + (size_t)i * (K + 1), ad);
+    if (lane == 0) {
+      status[i] = s;
+      absdet[i] = (ad >> 63) != 0 ? -1 : (int64_t)ad;
+    }
+  }
+}
+
+template <class T>
+cudaError_t configure(int smem) {
+  cudaError_t e = cudaFuncSetAttribute(k_enumerate<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_classify<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+
+}  // namespace
+
+size_t enum_smem_bytes(int N, int K, int warps, bool wide) {
+  const size_t pts = align16((size_t)(K + 1) * N * sizeof(int64_t));
+  const size_t per_warp = (size_t)round32(N) * stack_entries(K) * (wide ? 16 : 8);
+  return pts + per_warp * warps;
+}
+
+LaunchShape enum_shape(int N, int K, bool wide, int warps_req, int blocks_per_sm_req, int sms,
+                       cudaError_t* err) {
+  LaunchShape s;
+  *err = cudaSuccess;
+  int dev = 0, max_optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  int warps = warps_req > 0 ? warps_req : 4;
+  while (warps > 1 && enum_smem_bytes(N, K, warps, wide) > (size_t)max_optin) warps /= 2;
+  s.warps = warps;
+  s.smem = enum_smem_bytes(N, K, warps, wide);
+  s.slots = round32(N);
+  if (s.smem > (size_t)max_optin) { *err = cudaErrorInvalidConfiguration; return s; }
+  cudaError_t e = wide ? configure<i128>((int)s.smem) : configure<int64_t>((int)s.smem);
+  if (e != cudaSuccess) { *err = e; return s; }
+  int per_sm = blocks_per_sm_req;
+  if (per_sm <= 0) {
+    e = wide ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_enumerate<i128>, warps * 32, s.smem)
+             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_enumerate<int64_t>, warps * 32, s.smem);
+    if (e != cudaSuccess) { *err = e; return s; }
+    if (per_sm < 1) per_sm = 1;
+  }
+  s.blocks = per_sm * sms;
+  return s;
+}
+
+cudaError_t launch_enumerate(const EnumParams& p, const LaunchShape& s, bool wide, cudaStream_t st) {
+  if (wide) k_enumerate<i128><<<s.blocks, s.warps * 32, s.smem, st>>>(p);
+  else k_enumerate<int64_t><<<s.blocks, s.warps * 32, s.smem, st>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_classify(const int64_t* pts, const int64_t* lifts, int N, int K, const uint8_t* subsets,
+                            int count, int32_t* status, int64_t* absdet, bool wide, cudaStream_t st) {
+  const int warps = 4;
+  const size_t smem = enum_smem_bytes(N, K, warps, wide);
+  cudaError_t e = wide ? configure<i128>((int)smem) : configure<int64_t>((int)smem);
+  if (e != cudaSuccess) return e;
+  int blocks = (count + warps - 1) / warps;
+  if (blocks > 4096) blocks = 4096;
+  if (blocks < 1) blocks = 1;
+  if (wide) k_classify<i128><<<blocks, warps * 32, smem, st>>>(pts, lifts, N, K, subsets, count, status, absdet);
+  else k_classify<int64_t><<<blocks, warps * 32, smem, st>>>(pts, lifts, N, K, subsets, count, status, absdet);
+  return cudaGetLastError();
+}
+
+}  // namespace bd

@@ -1,0 +1,45 @@
+// Device-side declarations shared by the C ABI translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "bd_core.cuh"
+
+namespace bd {
+
+// Global accumulators of one enumeration (one system).
+struct DevAcc {
+  unsigned long long nvol_lo, nvol_hi;  // sum |D0| as unsigned 128-bit
+  unsigned long long cells, singular, ties;
+  unsigned long long items_done;
+};
+
+struct EnumParams {
+  const int64_t* pts;     // N x K coordinates, row-major (device)
+  const int64_t* lifts;   // N explicit lift heights (device) or nullptr: use (lift_seed, attempt)
+  uint64_t lift_seed;     // stream seed (see bd_lifts.h)
+  const Item* items;
+  int nitems;
+  int N, K;
+  unsigned int* counter;  // next item (reset to 0 before the launch)
+  DevAcc* acc;            // reset to 0 before the launch
+};
+
+struct LaunchShape {
+  int blocks = 0, warps = 0;
+  size_t smem = 0;       // dynamic shared memory per block
+  int slots = 0;         // points per warp stack (multiple of 32)
+};
+
+// Shared memory of one block: lifted points + one stack per warp.
+size_t enum_smem_bytes(int N, int K, int warps, bool wide);
+LaunchShape enum_shape(int N, int K, bool wide, int warps_req, int blocks_per_sm_req, int sms,
+                       cudaError_t* err);
+cudaError_t launch_enumerate(const EnumParams& p, const LaunchShape& s, bool wide, cudaStream_t st);
+
+// One warp per given subset: status (0 singular, 1 rejected, 2 accepted, 3 tie) and |D0|.
+cudaError_t launch_classify(const int64_t* pts, const int64_t* lifts, int N, int K, const uint8_t* subsets,
+                            int count, int32_t* status, int64_t* absdet, bool wide, cudaStream_t st);
+
+}  // namespace bd

@@ -1,0 +1,110 @@
+"""CPU checks of the native library: it loads, exports every symbol the public header declares,
+and its host emulation of the GPU enumeration (same source as the kernel's walker, run by one
+CPU thread per team) agrees with the oracle.  No GPU needed."""
+
+import os
+import random
+import re
+
+import numpy as np
+import pytest
+
+import paper_1501_02237_gb300 as bd
+from paper_1501_02237_gb300._lib import SIGNATURES, lib
+from oracle.lifts import lifts as oracle_lifts
+from oracle.lower_facet import nvol_lifting_bruteforce
+from oracle.snf import BinomialStructure
+from oracle.volume import nvol_placing
+from workloads import config_system, master_space_system
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+GOLD = __import__("json").load(open(os.path.join(ROOT, "tests", "golden", "oracle_volumes.json")))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "binodeg.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(bd_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol():
+    names = declared_functions()
+    assert len(names) >= 14
+    L = lib()
+    for n in names:
+        assert hasattr(L, n), n
+    assert set(names) == set(SIGNATURES)
+
+
+@pytest.mark.parametrize("seed", range(60))
+def test_host_walker_matches_oracle_random(seed):
+    rng = random.Random(seed)
+    k = rng.randint(1, 5)
+    npts = rng.randint(k + 1, 14)
+    pts = [tuple(rng.randint(-3, 3) for _ in range(k)) for _ in range(npts)]
+    lf = oracle_lifts(npts, seed)
+    r = bd.host_volume_lifted(np.array(pts), np.array(lf))
+    assert r["status"] == 0
+    assert r["nvol"] == nvol_placing(pts)
+    assert r["subsets"] == __import__("math").comb(npts, k + 1)
+
+
+@pytest.mark.parametrize("seed", range(15))
+def test_host_walker_counts_match_bruteforce(seed):
+    # the number of accepted cells and singular subsets are fixed by the lifting
+    rng = random.Random(1000 + seed)
+    k = rng.randint(1, 3)
+    npts = rng.randint(k + 1, 8)
+    pts = [tuple(rng.randint(-2, 2) for _ in range(k)) for _ in range(npts)]
+    lf = oracle_lifts(npts, seed)
+    total, acc, sing, ties = nvol_lifting_bruteforce(pts, lf)
+    r = bd.host_volume_lifted(np.array(pts), np.array(lf))
+    assert (r["nvol"], r["cells"], r["singular"], r["ties"]) == (total, acc, sing, ties)
+
+
+def test_host_walker_reports_ties():
+    S = np.array([(0, 0), (0, 1), (1, 1), (1, 0)])
+    r = bd.host_volume_lifted(S, np.array([0, 1, 2, 1]))
+    assert r["status"] == 3 and r["ties"] == 4
+
+
+def test_reduce_matches_oracle_structure():
+    for name in ["small_n10_k4", "single_n24_k8"]:
+        s = config_system(name)
+        red = bd.reduce(s.A)
+        ref = BinomialStructure(s.A.tolist())
+        assert (red["rank"], red["dim"], red["torsion"]) == (ref.rank, ref.dim, ref.torsion)
+        # the reduced points span the same lattice: volumes agree (GL_k(Z) invariance)
+        assert nvol_placing([tuple(p) for p in red["points"]]) == GOLD["configs"][name]["nvol"]
+
+
+def test_host_walker_config_small():
+    s = config_system("small_n10_k4")
+    P = bd.reduce(s.A)["points"]
+    r = bd.host_volume_lifted(P, np.array(oracle_lifts(len(P), 0)))
+    assert r["nvol"] == GOLD["configs"]["small_n10_k4"]["nvol"]
+
+
+@pytest.mark.parametrize("mk,deg", [((2, 2), 14), ((2, 3), 92), ((1, 6), 32), ((2, 4), 584)])
+def test_host_walker_master_space(mk, deg):
+    s = master_space_system(*mk)
+    red = bd.reduce(s.A, s.coef.reshape(-1, 4))
+    assert red["consistent"] and red["torsion"] == 1
+    r = bd.host_volume_lifted(red["points"], np.array(oracle_lifts(len(red["points"]), 3)), threads=4)
+    assert r["nvol"] == deg
+
+
+def test_reduce_consistency_matches_oracle():
+    A = np.array([[1, 1]])
+    assert not bd.reduce(A, [[1, 1, -2, 1], [1, 1, -3, 1]])["consistent"]
+    assert bd.reduce(A, [[1, 1, -2, 1], [1, 2, -1, 1]])["consistent"]
+    A2 = np.array([[2, 1]])
+    assert bd.reduce(A2, [[1, 1, -4, 1], [1, 1, 2, 1]])["consistent"]
+    assert not bd.reduce(A2, [[1, 1, -4, 1], [1, 1, -3, 1]])["consistent"]
+
+
+def test_argument_errors_raise():
+    with pytest.raises(bd.BinodegError):
+        bd.host_volume_lifted(np.zeros((3, 15), dtype=np.int64), np.zeros(3, dtype=np.int64))
+    with pytest.raises(bd.BinodegError):
+        bd.host_volume_lifted(np.array([[1 << 41, 0], [0, 1], [1, 1]]), np.array([1, 2, 3]))
