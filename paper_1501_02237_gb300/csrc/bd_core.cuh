@@ -33,6 +33,7 @@
 // Newton-Hensel lifting x <- x (2 - d x).
 #pragma once
 
+#include <math.h>
 #include <stdint.h>
 
 #ifdef __CUDACC__
@@ -70,9 +71,16 @@ struct Div64 {
 BD_HD Div64 make_div(int64_t d) {
   Div64 r;
   r.shift = ctz64((uint64_t)d);
-  uint64_t odd = (uint64_t)(d >> r.shift);  // exact: 2^shift divides d
-  uint64_t x = odd;                          // odd*odd = 1 mod 8: 3 correct bits
-  for (int i = 0; i < 5; ++i) x *= 2u - odd * x;  // 6, 12, 24, 48, 96 bits
+  const uint64_t odd = (uint64_t)(d >> r.shift);  // exact: 2^shift divides d
+  // (3 odd) xor 2 is an inverse modulo 2^5; each Newton-Hensel step doubles the correct bits:
+  // three 32-bit steps reach 40 >= 32 bits, one 64-bit step reaches 64
+  const uint32_t o32 = (uint32_t)odd;
+  uint32_t y = (3u * o32) ^ 2u;
+  y *= 2u - o32 * y;
+  y *= 2u - o32 * y;
+  y *= 2u - o32 * y;
+  uint64_t x = y;
+  x *= 2u - odd * x;
   r.inv = x;
   return r;
 }
@@ -85,9 +93,10 @@ struct Div128 {
 BD_HD Div128 make_div(i128 d) {
   Div128 r;
   r.shift = ctz128((u128)d);
-  u128 odd = (u128)(d >> r.shift);
-  u128 x = odd;
-  for (int i = 0; i < 6; ++i) x *= (u128)2 - odd * x;  // ... 192 bits
+  const u128 odd = (u128)(d >> r.shift);
+  const Div64 lo = make_div((int64_t)(uint64_t)odd);  // inverse modulo 2^64 (odd: shift 0)
+  u128 x = lo.inv;
+  x *= (u128)2 - odd * x;  // 128 bits
   r.inv = x;
   return r;
 }
@@ -130,6 +139,36 @@ BD_HD i128 bareiss(i128 a, i128 p, i128 b, i128 r, const Div128& D) {
   int t = D.shift;  // 0 < t < 127
   u128 q = (lo >> t) | (hi << (128 - t));
   return (i128)(q * D.inv);
+}
+
+// sign of a*b - c*d, exact (-1, 0, 1)
+BD_HD int cross_sign(int64_t a, int64_t b, int64_t c, int64_t d) {
+  const i128 v = (i128)a * b - (i128)c * d;  // |a b|, |c d| < 2^126
+  return (v > 0) - (v < 0);
+}
+
+BD_HD int cross_sign(i128 a, i128 b, i128 c, i128 d) {
+  u128 h1, l1, h2, l2;
+  mul_wide(a, b, h1, l1);
+  mul_wide(c, d, h2, l2);
+  const u128 lo = l1 - l2;
+  const i128 hi = (i128)(h1 - h2 - (u128)(l1 < l2));
+  if (hi != 0) return hi > 0 ? 1 : -1;
+  return lo != 0 ? 1 : 0;
+}
+
+// Sign of a*b - c*d from single-precision copies (af = fl(a) etc.), or 2 when the rounded
+// value is too close to zero to decide.  Each copy has relative error <= 2^-24, each product
+// and the fused difference add at most 2^-24 more, so the computed value is within
+// 2^-21 (|ab| + |cd|) of the exact one; a larger magnitude fixes the sign.  Copies of values
+// below 2^63 keep every product below 2^126 < FLT_MAX.
+BD_HD int cross_sign_filtered(float af, float bf, float cf, float df) {
+  const float p = af * bf;
+  const float v = fmaf(-cf, df, p);
+  const float bound = 4.8e-7f * (fabsf(p) + fabsf(cf * df));  // 2^-21 ~ 4.77e-7
+  if (v > bound) return 1;
+  if (v < -bound) return -1;
+  return 2;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -187,11 +226,13 @@ struct Walker {
   const int64_t* P;
   int N, K, SLOTS;
   T* st;
+  float* fl;        // single-precision copies of the two level K-1 entries: fl[q], fl[SLOTS + q]
   int s[KMAX + 1];  // chosen indices s_0 .. s_j
   Div dv[KMAX];     // exact divider by the pivot of each level (dv[0]: by 1)
+  int psign;        // sign of the level K-1 pivot p_{K-1}
 
-  BD_HD Walker(Team& t, const int64_t* P_, int N_, int K_, int SLOTS_, T* st_)
-      : tm(t), P(P_), N(N_), K(K_), SLOTS(SLOTS_), st(st_) {}
+  BD_HD Walker(Team& t, const int64_t* P_, int N_, int K_, int SLOTS_, T* st_, float* fl_)
+      : tm(t), P(P_), N(N_), K(K_), SLOTS(SLOTS_), st(st_), fl(fl_) {}
 
   // state 0: lifted differences z_q = (a_q - a_{s_0}, w_q - w_{s_0})
   BD_HD void start(int s0) {
@@ -214,18 +255,33 @@ struct Walker {
     if (pi < 0) return false;
     const T pj = st[(po + pi) * SLOTS + c];
     const Div D = dv[j - 1];
+    const bool last = (j == K - 1);
     tm.sync();  // readers of the old state j (a sibling's subtree) are done
     for (int q = tm.lane(); q < N; q += tm.lanes()) {
       const T bq = st[(po + pi) * SLOTS + q];
       for (int e = 0; e < ncoord; ++e) {  // state j: K-j coordinates + lift = ncoord entries
         const int ep = e < pi ? e : e + 1;
-        st[(no + e) * SLOTS + q] = bareiss(st[(po + ep) * SLOTS + q], pj, bq, st[(po + ep) * SLOTS + c], D);
+        const T v = bareiss(st[(po + ep) * SLOTS + q], pj, bq, st[(po + ep) * SLOTS + c], D);
+        st[(no + e) * SLOTS + q] = v;
+        if (last) fl[e * SLOTS + q] = (float)v;
       }
     }
-    dv[j] = make_div(pj);
+    if (last) psign = pj < 0 ? -1 : 1;  // the leaf test needs only the sign of p_{K-1}
+    else dv[j] = make_div(pj);
     s[j] = c;
     tm.sync();
     return true;
+  }
+
+  // level 0 is the last level when K = 1: its float copies and pivot sign (p_0 = 1)
+  BD_HD void finish_level0() {
+    if (K != 1) return;
+    for (int q = tm.lane(); q < N; q += tm.lanes()) {
+      fl[q] = (float)st[q];
+      fl[SLOTS + q] = (float)st[SLOTS + q];
+    }
+    psign = 1;
+    tm.sync();
   }
 
   BD_HD uint64_t member_mask() const {
@@ -235,29 +291,33 @@ struct Walker {
   }
 
   // status of the cell {s_0 .. s_{K-1}, p}; |D0| in absdet.  Uniform across the team.
+  // s(q) = sigma (C_p L_q - C_q L_p) / p_{K-1} and D0 = sigma C_p, so q lies strictly below
+  // the lifted hyperplane iff  sign(C_p) sign(p_{K-1}) (C_p L_q - C_q L_p) < 0.
   BD_HD int leaf(int p, uint64_t mask, T& absdet) {
     const int lo = level_offset(K, K - 1);
     const T Cp = st[lo * SLOTS + p];
-    const T Lp = st[(lo + 1) * SLOTS + p];
     absdet = tabs(Cp);
     if (Cp == 0) return ST_SINGULAR;
-    const Div D = dv[K - 1];
+    const T Lp = st[(lo + 1) * SLOTS + p];
+    const float Cpf = fl[p], Lpf = fl[SLOTS + p];
+    const int sig = (Cp < 0 ? -1 : 1) * psign;
     bool below = false, on = false;
     for (int q = tm.lane(); q < N; q += tm.lanes()) {
       if (((mask >> q) & 1ull) || q == p) continue;
-      const T sq = bareiss(st[(lo + 1) * SLOTS + q], Cp, st[lo * SLOTS + q], Lp, D);
-      if (sq == 0) on = true;
-      else if ((sq < 0) != (Cp < 0)) below = true;
+      int sg = sizeof(T) == 8 ? cross_sign_filtered(Cpf, fl[SLOTS + q], fl[q], Lpf) : 2;
+      if (sg == 2) sg = cross_sign(Cp, st[(lo + 1) * SLOTS + q], st[lo * SLOTS + q], Lp);
+      if (sg == 0) on = true;
+      else if (sg != sig) below = true;
     }
-    const bool any_below = tm.any(below);
-    const bool any_on = tm.any(on);
-    return any_below ? ST_REJECTED : (any_on ? ST_TIE : ST_ACCEPTED);
+    if (tm.any(below)) return ST_REJECTED;
+    return tm.any(on) ? ST_TIE : ST_ACCEPTED;
   }
 
   // every (K+1)-subset extending the prefix it.idx[0 .. it.len-1]
   BD_HD void run_item(const Item& it, Acc& acc) {
     const int L = it.len;
     start(it.idx[0]);
+    finish_level0();
     for (int j = 1; j < L; ++j) {
       if (!build(j, it.idx[j])) {
         acc.singular += subtree_size(N, K, it.idx[L - 1], L);
@@ -297,6 +357,7 @@ struct Walker {
   // status of one given subset sub[0] < .. < sub[K]
   BD_HD int classify(const uint8_t* sub, T& absdet) {
     start(sub[0]);
+    finish_level0();
     for (int j = 1; j < K; ++j)
       if (!build(j, sub[j])) { absdet = 0; return ST_SINGULAR; }
     return leaf(sub[K], member_mask(), absdet);

@@ -74,50 +74,6 @@ bool cols_op(Mat& X, int i, int j, i128 s, i128 t, i128 u, i128 v) {
   return true;
 }
 
-// Smith form by Bezout row and column reductions (Sec. 3): P A Q = diag(d_1..d_r, 0..).
-// M is overwritten by the diagonal form.  The divisibility chain is not produced.
-bool smith(Mat& M, Mat& P, Mat& Q, int& rank) {
-  const int n = M.r, m = M.c;
-  P = Mat::eye(n);
-  Q = Mat::eye(m);
-  int t = 0;
-  for (; t < std::min(n, m); ++t) {
-    int bi = -1, bj = -1;
-    for (int i = t; i < n; ++i)
-      for (int j = t; j < m; ++j)
-        if (M.at(i, j) != 0 && (bi < 0 || iabs(M.at(i, j)) < iabs(M.at(bi, bj)))) { bi = i; bj = j; }
-    if (bi < 0) break;
-    if (bi != t) {
-      for (int c = 0; c < m; ++c) std::swap(M.at(t, c), M.at(bi, c));
-      for (int c = 0; c < n; ++c) std::swap(P.at(t, c), P.at(bi, c));
-    }
-    if (bj != t) {
-      for (int r = 0; r < n; ++r) std::swap(M.at(r, t), M.at(r, bj));
-      for (int r = 0; r < m; ++r) std::swap(Q.at(r, t), Q.at(r, bj));
-    }
-    for (;;) {
-      bool dirty = false;
-      for (int i = t + 1; i < n; ++i) {
-        if (M.at(i, t) == 0) continue;
-        i128 s, tt, u, v;
-        bezout2(M.at(t, t), M.at(i, t), s, tt, u, v);
-        if (!rows_op(M, t, i, s, tt, u, v) || !rows_op(P, t, i, s, tt, u, v)) return false;
-        dirty = true;
-      }
-      for (int j = t + 1; j < m; ++j) {
-        if (M.at(t, j) == 0) continue;
-        i128 s, tt, u, v;
-        bezout2(M.at(t, t), M.at(t, j), s, tt, u, v);
-        if (!cols_op(M, t, j, s, tt, u, v) || !cols_op(Q, t, j, s, tt, u, v)) return false;
-        dirty = true;
-      }
-      if (!dirty) break;
-    }
-  }
-  rank = t;
-  return true;
-}
-
 u128 ugcd(u128 a, u128 b) {
   while (b) { u128 r = a % b; a = b; b = r; }
   return a;
@@ -125,7 +81,7 @@ u128 ugcd(u128 a, u128 b) {
 
 // b^{Q_0} == 1 exactly (Eq. consistency), b_i = -c_{i,2} / c_{i,1}.  Numbers are split over a
 // coprime base (repeated gcd refinement), so exponents can be compared without factoring.
-bool consistent(const int64_t* coef, int m, const Mat& Q, int rank, std::string& err, bool& ok) {
+bool consistent(const int64_t* coef, int m, const Mat& R, std::string& err, bool& ok) {
   std::vector<u128> num(m), den(m);
   std::vector<int> neg(m);
   for (int i = 0; i < m; ++i) {
@@ -167,16 +123,16 @@ bool consistent(const int64_t* coef, int m, const Mat& Q, int rank, std::string&
     return v;
   };
   ok = true;
-  for (int j = rank; j < m && ok; ++j) {
+  for (int j = 0; j < R.r && ok; ++j) {
     i128 sgn = 0;
     for (int i = 0; i < m; ++i)
-      if (neg[i]) sgn += Q.at(i, j);
+      if (neg[i]) sgn += R.at(j, i);
     if (sgn % 2 != 0) ok = false;
     for (size_t b = 0; b < base.size() && ok; ++b) {
       i128 e = 0;
       for (int i = 0; i < m; ++i) {
         const int v = val(num[i], base[b]) - val(den[i], base[b]);
-        if (v) e += Q.at(i, j) * v;
+        if (v) e += R.at(j, i) * v;
       }
       if (e != 0) ok = false;
     }
@@ -233,47 +189,207 @@ bool lll(std::vector<i128>& B, int d, int n) {
   return true;
 }
 
+// checked i128 arithmetic
+bool mul_ok(i128 a, i128 b, i128& r) { return !__builtin_mul_overflow(a, b, &r); }
+bool add_ok(i128 a, i128 b, i128& r) { return !__builtin_add_overflow(a, b, &r); }
+
+// Basis (rows of U, d x rows) of the lattice {p in Z^rows : p M = 0} for M (rows x cols).
+// Column by column: the values v = U m_j of the current basis are sent to (g, 0, .., 0) by the
+// unimodular 2x2 Bezout steps of Sec. 3 applied to the basis rows; the row carrying g leaves
+// the basis, the others span exactly the vectors of the old lattice orthogonal to m_j.  The
+// basis is LLL-reduced after every column, which keeps its entries small.  The result is
+// saturated: it is a basis of ker(M) intersected with Z^rows.
+bool kernel_rows(const Mat& M, Mat& U, std::string& err) {
+  const int n = M.r, m = M.c;
+  std::vector<std::vector<i128>> B(n, std::vector<i128>(n, 0));
+  for (int i = 0; i < n; ++i) B[i][i] = 1;
+  for (int j = 0; j < m && !B.empty(); ++j) {
+    const int d = (int)B.size();
+    std::vector<i128> v(d, 0);
+    for (int i = 0; i < d; ++i)
+      for (int t = 0; t < n; ++t) {
+        i128 pr;
+        if (!mul_ok(B[i][t], M.at(t, j), pr) || !add_ok(v[i], pr, v[i])) { err = "kernel values overflow"; return false; }
+      }
+    int first = -1;
+    for (int i = 0; i < d; ++i)
+      if (v[i] != 0) { first = i; break; }
+    if (first < 0) continue;
+    std::swap(B[0], B[first]);
+    std::swap(v[0], v[first]);
+    for (int i = 1; i < d; ++i) {
+      if (v[i] == 0) continue;
+      i128 s, t, u, w;
+      bezout2(v[0], v[i], s, t, u, w);
+      for (int c = 0; c < n; ++c) {
+        i128 x = B[0][c], y = B[i][c], a1, a2, b1, b2;
+        if (!mul_ok(s, x, a1) || !mul_ok(t, y, a2) || !mul_ok(u, x, b1) || !mul_ok(w, y, b2) ||
+            !add_ok(a1, a2, B[0][c]) || !add_ok(b1, b2, B[i][c])) { err = "kernel basis overflow"; return false; }
+      }
+      const i128 nv0 = s * v[0] + t * v[i];
+      v[i] = 0;
+      v[0] = nv0;
+    }
+    B.erase(B.begin());
+    if (!B.empty()) {
+      std::vector<i128> flat;
+      for (auto& row : B) flat.insert(flat.end(), row.begin(), row.end());
+      if (!lll(flat, (int)B.size(), n)) { err = "kernel basis entries exceed 2^62"; return false; }
+      for (size_t i = 0; i < B.size(); ++i)
+        for (int c = 0; c < n; ++c) B[i][c] = flat[i * n + c];
+    }
+  }
+  U = Mat((int)B.size(), n);
+  for (size_t i = 0; i < B.size(); ++i)
+    for (int c = 0; c < n; ++c) {
+      if (iabs(B[i][c]) >= ENTRY_LIMIT) { err = "kernel basis entries exceed 2^62"; return false; }
+      U.at((int)i, c) = B[i][c];
+    }
+  return true;
+}
+
+Mat transpose(const Mat& A) {
+  Mat T(A.c, A.r);
+  for (int i = 0; i < A.r; ++i)
+    for (int j = 0; j < A.c; ++j) T.at(j, i) = A.at(i, j);
+  return T;
+}
+
+// exact determinant of a k x k i128 matrix (fraction-free elimination, overflow-checked)
+bool det_exact(std::vector<i128> a, int k, i128& det) {
+  i128 prev = 1;
+  int sign = 1;
+  for (int c = 0; c < k; ++c) {
+    int p = -1;
+    for (int r = c; r < k; ++r)
+      if (a[(size_t)r * k + c] != 0) { p = r; break; }
+    if (p < 0) { det = 0; return true; }
+    if (p != c) {
+      for (int j = 0; j < k; ++j) std::swap(a[(size_t)c * k + j], a[(size_t)p * k + j]);
+      sign = -sign;
+    }
+    for (int r = c + 1; r < k; ++r) {
+      for (int j = c + 1; j < k; ++j) {
+        i128 x, y;
+        if (!mul_ok(a[(size_t)r * k + j], a[(size_t)c * k + c], x) || !mul_ok(a[(size_t)r * k + c], a[(size_t)c * k + j], y))
+          return false;
+        a[(size_t)r * k + j] = (x - y) / prev;  // exact (Bareiss)
+      }
+      a[(size_t)r * k + c] = 0;
+    }
+    prev = a[(size_t)c * k + c];
+  }
+  det = sign * a[(size_t)(k - 1) * k + (k - 1)];
+  if (k == 0) det = 1;
+  return true;
+}
+
+// rows I and columns J of an r x r submatrix of A that is nonsingular modulo a prime
+bool pivot_sets(const Mat& A, int r, std::vector<int>& I, std::vector<int>& J) {
+  const uint64_t primes[4] = {2305843009213693951ull, 4611686018427387847ull, 1000000000000000003ull,
+                              999999999999999989ull};
+  for (uint64_t pr : primes) {
+    const int n = A.r, m = A.c;
+    std::vector<uint64_t> M((size_t)n * m);
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < m; ++j) {
+        i128 x = A.at(i, j) % (i128)pr;
+        if (x < 0) x += pr;
+        M[(size_t)i * m + j] = (uint64_t)x;
+      }
+    auto mulmod = [pr](uint64_t a, uint64_t b) { return (uint64_t)((u128)a * b % pr); };
+    auto inv = [&](uint64_t a) {
+      uint64_t r = 1, e = pr - 2;
+      while (e) { if (e & 1) r = mulmod(r, a); a = mulmod(a, a); e >>= 1; }
+      return r;
+    };
+    std::vector<int> used(n, 0);
+    I.clear();
+    J.clear();
+    for (int c = 0; c < m && (int)I.size() < r; ++c) {
+      int p = -1;
+      for (int i = 0; i < n; ++i)
+        if (!used[i] && M[(size_t)i * m + c]) { p = i; break; }
+      if (p < 0) continue;
+      used[p] = 1;
+      I.push_back(p);
+      J.push_back(c);
+      const uint64_t ip = inv(M[(size_t)p * m + c]);
+      for (int i = 0; i < n; ++i) {
+        if (used[i] || !M[(size_t)i * m + c]) continue;
+        const uint64_t f = mulmod(M[(size_t)i * m + c], ip);
+        for (int cc = c; cc < m; ++cc)
+          M[(size_t)i * m + cc] = (M[(size_t)i * m + cc] + pr - mulmod(f, M[(size_t)p * m + cc])) % pr;
+      }
+    }
+    if ((int)I.size() == r) {
+      std::sort(I.begin(), I.end());
+      return true;
+    }
+  }
+  return false;
+}
+
 }  // namespace
 
+// The invariants of the Smith form P A Q = D (Eq. smith) that the degree needs, computed
+// without forming P and Q (whose entries can grow to hundreds of bits):
+//   * P_0: any basis of the saturated left kernel {p : p A = 0} (the rows of P_0 in
+//     Eq. rank-decomp are one such basis; Prop. 4's volume is the same for every basis);
+//   * rank r = n - dim of that kernel;
+//   * Q_0: a basis of the right kernel {q : A q = 0}, for the consistency test b^{Q_0} = 1;
+//   * |prod d_j| = gcd of the r x r minors of A (Prop. 1).  With X a basis of the saturated
+//     column lattice (n x r) and S of the saturated row lattice (r x m), A = X Y and Y = T S
+//     with T r x r integer, so by Cauchy-Binet, for any nonsingular A_{I,J}:
+//         |prod d_j| = |det T| = |det A_{I,J}| / (|det X_I| |det S_J|).
 int reduce_system(const int64_t* A, int n, int m, const int64_t* coef, Reduction& out, std::string& err) {
   Mat M(n, m);
   for (int i = 0; i < n; ++i)
     for (int j = 0; j < m; ++j) M.at(i, j) = A[(size_t)i * m + j];
-  Mat P, Q;
-  int rank = 0;
-  if (m > 0) {
-    if (!smith(M, P, Q, rank)) { err = "Smith form entries exceed 2^62"; return BD_ERR_OVERFLOW; }
-  } else {
-    P = Mat::eye(n);
-    Q = Mat(0, 0);
-  }
-  // Prop. 1: |prod d_j| components
-  u128 tors = 1;
-  for (int j = 0; j < rank; ++j) {
-    tors *= (u128)iabs(M.at(j, j));
-    if (tors >> 63) { err = "torsion exceeds 2^63"; return BD_ERR_OVERFLOW; }
-  }
+  Mat P0, R;
+  if (!kernel_rows(M, P0, err)) return BD_ERR_OVERFLOW;
+  const int d = P0.r, rank = n - d;
+  if (!kernel_rows(transpose(M), R, err)) return BD_ERR_OVERFLOW;
+  if (R.r != m - rank) { err = "inconsistent kernel dimensions"; return BD_ERR_OVERFLOW; }
   out.rank = rank;
-  out.dim = n - rank;
-  out.torsion = (uint64_t)tors;
+  out.dim = d;
+  out.torsion = 1;
+  if (rank > 0) {
+    Mat X, S;
+    if (!kernel_rows(transpose(P0), X, err)) return BD_ERR_OVERFLOW;  // {y : P_0 y = 0}
+    if (!kernel_rows(transpose(R), S, err)) return BD_ERR_OVERFLOW;   // {x : R x = 0}
+    std::vector<int> I, J;
+    if (X.r != rank || S.r != rank || !pivot_sets(M, rank, I, J)) { err = "rank selection failed"; return BD_ERR_OVERFLOW; }
+    std::vector<i128> a((size_t)rank * rank), x((size_t)rank * rank), sm((size_t)rank * rank);
+    for (int u = 0; u < rank; ++u)
+      for (int v = 0; v < rank; ++v) {
+        a[(size_t)u * rank + v] = M.at(I[u], J[v]);
+        x[(size_t)u * rank + v] = X.at(u, I[v]);
+        sm[(size_t)u * rank + v] = S.at(u, J[v]);
+      }
+    i128 da, dx, ds;
+    if (!det_exact(a, rank, da) || !det_exact(x, rank, dx) || !det_exact(sm, rank, ds)) {
+      err = "torsion determinants exceed 2^127";
+      return BD_ERR_OVERFLOW;
+    }
+    if (da == 0 || dx == 0 || ds == 0 || da % (dx * ds) != 0) { err = "torsion identity failed"; return BD_ERR_OVERFLOW; }
+    const i128 t = iabs(da / (dx * ds));
+    if (t >> 63) { err = "torsion exceeds 2^63"; return BD_ERR_OVERFLOW; }
+    out.torsion = (uint64_t)t;
+  }
   out.consistent = true;
   if (coef && rank < m) {
     bool ok = true;
-    if (!consistent(coef, m, Q, rank, err, ok)) return BD_ERR_ARG;
+    if (!consistent(coef, m, R, err, ok)) return BD_ERR_ARG;
     out.consistent = ok;
   }
-  const int d = out.dim;
   out.points.assign((size_t)(n + 1) * d, 0);
   out.max_abs_coord = 0;
   if (d == 0) return BD_OK;
-  // Eq. rank-decomp: P_0 = rows rank..n-1 of P; its columns are the points (Prop. 4)
-  std::vector<i128> B((size_t)d * n);
-  for (int i = 0; i < d; ++i)
-    for (int c = 0; c < n; ++c) B[(size_t)i * n + c] = P.at(rank + i, c);
-  if (!lll(B, d, n)) { err = "kernel basis entries exceed 2^62 during reduction"; return BD_ERR_OVERFLOW; }
+  // the points are the columns of the (LLL-reduced) kernel basis (Prop. 4), then the origin
   for (int q = 0; q < n; ++q)
     for (int i = 0; i < d; ++i) {
-      const i128 v = B[(size_t)i * n + q];
+      const i128 v = P0.at(i, q);
       if (iabs(v) >= ((i128)1 << 40)) { err = "kernel point coordinate exceeds 2^40"; return BD_ERR_OVERFLOW; }
       out.points[(size_t)q * d + i] = (int64_t)v;
       out.max_abs_coord = std::max<int64_t>(out.max_abs_coord, (int64_t)iabs(v));
@@ -356,7 +472,8 @@ void host_enumerate(const int64_t* P, int N, int K, const std::vector<Item>& ite
   auto work = [&](int tid) {
     HostTeam tm;
     std::vector<T> st((size_t)N * stack_entries(K));
-    Walker<T, HostTeam> W(tm, P, N, K, N, st.data());
+    std::vector<float> fl((size_t)2 * N);
+    Walker<T, HostTeam> W(tm, P, N, K, N, st.data(), fl.data());
     Acc a{};
     for (;;) {
       const size_t i = next.fetch_add(1);

@@ -41,6 +41,12 @@ struct WarpTeam {
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 __host__ __device__ inline int round32(int x) { return (x + 31) & ~31; }
 
+// one warp's shared memory: its stack of reduced rows and two float rows for the last level
+template <class T>
+__host__ __device__ inline size_t warp_bytes(int slots, int K) {
+  return align16((size_t)slots * stack_entries(K) * sizeof(T) + (size_t)2 * slots * sizeof(float));
+}
+
 __device__ void load_points(int64_t* P, const EnumParams& p) {
   const int N = p.N, K = p.K;
   for (int i = threadIdx.x; i < N * K; i += blockDim.x) {
@@ -71,12 +77,14 @@ __global__ void k_enumerate(EnumParams p) {
   const int N = p.N, K = p.K;
   const int slots = round32(N);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  T* st = reinterpret_cast<T*>(smem + align16((size_t)(K + 1) * N * sizeof(int64_t))) +
-          (size_t)warp * slots * stack_entries(K);
+  unsigned char* wbase = smem + align16((size_t)(K + 1) * N * sizeof(int64_t)) +
+                         (size_t)warp * warp_bytes<T>(slots, K);
+  T* st = reinterpret_cast<T*>(wbase);
+  float* fl = reinterpret_cast<float*>(wbase + (size_t)slots * stack_entries(K) * sizeof(T));
   load_points(P, p);
 
   WarpTeam tm;
-  Walker<T, WarpTeam> W(tm, P, N, K, slots, st);
+  Walker<T, WarpTeam> W(tm, P, N, K, slots, st, fl);
   Acc acc{};
   unsigned long long done = 0;
   for (;;) {
@@ -104,10 +112,12 @@ __global__ void k_classify(const int64_t* pts, const int64_t* lifts, int N, int 
   load_points(P, p);
   const int slots = round32(N);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, warps = blockDim.x >> 5;
-  T* st = reinterpret_cast<T*>(smem + align16((size_t)(K + 1) * N * sizeof(int64_t))) +
-          (size_t)warp * slots * stack_entries(K);
+  unsigned char* wbase = smem + align16((size_t)(K + 1) * N * sizeof(int64_t)) +
+                         (size_t)warp * warp_bytes<T>(slots, K);
+  T* st = reinterpret_cast<T*>(wbase);
+  float* fl = reinterpret_cast<float*>(wbase + (size_t)slots * stack_entries(K) * sizeof(T));
   WarpTeam tm;
-  Walker<T, WarpTeam> W(tm, P, N, K, slots, st);
+  Walker<T, WarpTeam> W(tm, P, N, K, slots, st, fl);
   for (int i = blockIdx.x * warps + warp; i < count; i += gridDim.x * warps) {
     T ad = 0;
     const int s = W.classify(subsets + (size_t)i * (K + 1), ad);
@@ -129,7 +139,7 @@ cudaError_t configure(int smem) {
 
 size_t enum_smem_bytes(int N, int K, int warps, bool wide) {
   const size_t pts = align16((size_t)(K + 1) * N * sizeof(int64_t));
-  const size_t per_warp = (size_t)round32(N) * stack_entries(K) * (wide ? 16 : 8);
+  const size_t per_warp = wide ? warp_bytes<i128>(round32(N), K) : warp_bytes<int64_t>(round32(N), K);
   return pts + per_warp * warps;
 }
 

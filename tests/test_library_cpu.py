@@ -108,3 +108,47 @@ def test_argument_errors_raise():
         bd.host_volume_lifted(np.zeros((3, 15), dtype=np.int64), np.zeros(3, dtype=np.int64))
     with pytest.raises(bd.BinodegError):
         bd.host_volume_lifted(np.array([[1 << 41, 0], [0, 1], [1, 1]]), np.array([1, 2, 3]))
+
+
+def _rand_matrix(rng, n, m, lo=-3, hi=3):
+    A = [[rng.randint(lo, hi) for _ in range(m)] for _ in range(n)]
+    if n >= 3 and rng.random() < 0.4:  # rank deficiency
+        A[0] = [2 * a - b for a, b in zip(A[1], A[2])]
+    if rng.random() < 0.3:  # torsion: scale a row-combination
+        A[-1] = [3 * x for x in A[-1]]
+    return A
+
+
+@pytest.mark.parametrize("seed", range(80))
+def test_reduce_invariants_random_matrices(seed):
+    rng = random.Random(seed)
+    n, m = rng.randint(1, 7), rng.randint(0, 6)
+    A = _rand_matrix(rng, n, m) if m else [[] for _ in range(n)]
+    ref = BinomialStructure(A)
+    red = bd.reduce(np.array(A, dtype=np.int64).reshape(n, m))
+    assert (red["rank"], red["dim"], red["torsion"]) == (ref.rank, ref.dim, ref.torsion)
+    if ref.dim:
+        P = red["points"][:n]
+        # points are a kernel basis: P^T A = 0, and they give the oracle's volume
+        assert not (P.T @ np.array(A, dtype=np.int64).reshape(n, m)).any()
+        want = nvol_placing(ref.kernel_points() + [tuple([0] * ref.dim)])
+        assert nvol_placing([tuple(p) for p in red["points"]]) == want
+
+
+def test_reduce_batch_systems_match_oracle():
+    from workloads import batch_systems
+    gold = GOLD["batch_first_256"]
+    for s, g in zip(batch_systems(96), gold):
+        red = bd.reduce(s.A)
+        ref = BinomialStructure(s.A.tolist())
+        assert (red["rank"], red["torsion"]) == (ref.rank, ref.torsion), s.name
+        P = red["points"][:-1]
+        assert not (P.T @ s.A).any()
+
+
+@pytest.mark.parametrize("idx", [0, 2, 25, 39])
+def test_reduce_batch_volume_equals_oracle(idx):
+    from workloads import batch_systems
+    s = batch_systems(idx + 1)[idx]
+    P = bd.reduce(s.A)["points"]
+    assert nvol_placing([tuple(p) for p in P]) == GOLD["batch_first_256"][idx]["nvol"]
