@@ -146,15 +146,17 @@ int bd_plan_launch(bd_plan* plan, uint64_t seed, int32_t attempt, void* stream);
 int bd_plan_read(bd_plan* plan, bd_volume_out* out);
 /* The full volume (launch, read, re-lift on ties) with inputs already on the device. */
 int bd_plan_volume(bd_plan* plan, uint64_t seed, bd_volume_out* out);
-/* Number of work items, kernel launch geometry and path: {items, blocks, warps_per_block,
- * shared_bytes_per_block, int128, slots_per_warp, 0, 0}. */
+/* Number of work items, kernel launch geometry and integer path: {items, blocks, warps_per_block,
+ * shared_bytes_per_block, path (0: int32 coordinate / int64 lift minors, 1: int64, 2: int128),
+ * slots_per_warp, 0, 0}. */
 int bd_plan_info(const bd_plan* plan, int64_t* info);
 int bd_plan_destroy(bd_plan* plan);
 
 /* ---- host emulation (CPU tests and the native CPU baseline; never used by the calls above) */
 
-/* Runs the same lower-facet enumeration as the GPU kernel on `threads` CPU threads, with
- * the given lifts (no re-lift).  Returns BD_ERR_TIES when the lifting has a tie. */
+/* Runs the same lower-facet enumeration as the GPU kernel on |threads| CPU threads, with
+ * the given lifts (no re-lift); a negative count forces the 128-bit path.  Returns
+ * BD_ERR_TIES when the lifting has a tie. */
 int bd_host_volume_lifted(const int64_t* points, const int64_t* lifts, int32_t npts, int32_t k,
                           int32_t threads, bd_volume_out* out);
 

@@ -92,12 +92,14 @@ def classify(points, lifts, subsets) -> tuple:
     return status, absdet
 
 
-def host_volume_lifted(points, lifts, threads: int = 1) -> dict:
-    """bd_host_volume_lifted: CPU emulation of the enumeration (CPU tests and the native baseline)."""
+def host_volume_lifted(points, lifts, threads: int = 1, force_int128: bool = False) -> dict:
+    """bd_host_volume_lifted: CPU emulation of the enumeration (CPU tests and the native baseline).
+    force_int128 runs the 128-bit walker (a negative thread count at the C ABI)."""
     P, W = i64(points), i64(lifts)
     npts, k = P.shape
     out = VolumeOut()
-    rc = lib().bd_host_volume_lifted(ptr(P), ptr(W), npts, k, threads, C.byref(out))
+    t = -max(1, threads) if force_int128 else threads
+    rc = lib().bd_host_volume_lifted(ptr(P), ptr(W), npts, k, t, C.byref(out))
     res = out.as_dict()
     res["status"] = rc
     if rc not in (0, 3):
@@ -135,7 +137,7 @@ class Plan:
         a = np.zeros(8, dtype=np.int64)
         check(lib().bd_plan_info(self.handle, ptr(a)))
         return dict(items=int(a[0]), blocks=int(a[1]), warps_per_block=int(a[2]), smem=int(a[3]),
-                    int128=bool(a[4]), slots=int(a[5]))
+                    path=("int32/int64", "int64", "int128")[int(a[4])], int128=int(a[4]) == 2, slots=int(a[5]))
 
     def close(self) -> None:
         if getattr(self, "handle", None):

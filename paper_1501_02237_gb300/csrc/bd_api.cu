@@ -36,8 +36,6 @@ int cuda_fail(cudaError_t e, const char* where) {
   } while (0)
 
 constexpr int MAX_LIFTINGS = 8;
-constexpr double INT64_BITS = 62.99;   // |minor| < 2^63
-constexpr double INT128_BITS = 126.99; // |minor| < 2^127
 
 int sm_count() {
   static int sms = 0;
@@ -69,7 +67,7 @@ void set_u128(uint64_t& lo, uint64_t& hi, u128 v) {
 
 struct bd_plan {
   int N = 0, K = 0;
-  bool wide = false;
+  int path = 0;  // bd::PATH_NARROW / MID / WIDE
   double bound = 0;
   int64_t max_abs = 0;
   std::vector<bd::Item> items;
@@ -121,15 +119,17 @@ int plan_make(const int64_t* points, const int64_t* lifts, int32_t npts, int32_t
     }
     spread = hi - lo;
   }
-  p->bound = bd::hadamard_log2(points, lifts, npts, k, spread);
-  if (p->bound >= INT128_BITS) {
+  double coord_bits = 0;
+  p->bound = bd::hadamard_log2(points, lifts, npts, k, spread, &coord_bits);
+  p->path = bd::choose_path(coord_bits, p->bound);
+  if (p->path < 0) {
     delete p;
     return fail(BD_ERR_OVERFLOW, "Hadamard bound of the lifted minors exceeds 2^127");
   }
-  p->wide = p->bound >= INT64_BITS || (opts && opts->force_int128);
+  if (opts && opts->force_int128) p->path = bd::PATH_WIDE;
   const int sms = sm_count();
   cudaError_t e;
-  p->shape = bd::enum_shape(npts, k, p->wide, opts ? opts->warps_per_block : 0, opts ? opts->blocks_per_sm : 0,
+  p->shape = bd::enum_shape(npts, k, p->path, opts ? opts->warps_per_block : 0, opts ? opts->blocks_per_sm : 0,
                             sms, &e);
   if (e != cudaSuccess) {
     delete p;
@@ -181,7 +181,7 @@ int plan_launch(bd_plan* p, uint64_t seed, int attempt, cudaStream_t st) {
   ep.K = p->K;
   ep.acc = reinterpret_cast<bd::DevAcc*>(p->d_state);
   ep.counter = reinterpret_cast<unsigned int*>(p->d_state + sizeof(bd::DevAcc));
-  BD_CUDA(bd::launch_enumerate(ep, p->shape, p->wide, st));
+  BD_CUDA(bd::launch_enumerate(ep, p->shape, p->path, st));
   BD_CUDA(cudaMemcpyAsync(p->h_acc, p->d_state, sizeof(bd::DevAcc), cudaMemcpyDeviceToHost, st));
   p->stream = st;
   p->launched = true;
@@ -201,7 +201,7 @@ int plan_read(bd_plan* p, bd_volume_out* out) {
   out->ties = a.ties;
   out->subsets = bd::binom(p->N, p->K + 1);
   out->relifts = p->attempt;
-  out->flags = (p->wide ? BD_FLAG_INT128 : 0) | ((a.nvol_lo | a.nvol_hi) == 0 ? BD_FLAG_DEGENERATE : 0);
+  out->flags = (p->path == bd::PATH_WIDE ? BD_FLAG_INT128 : 0) | ((a.nvol_lo | a.nvol_hi) == 0 ? BD_FLAG_DEGENERATE : 0);
   out->max_abs_coord = (int32_t)std::min<int64_t>(p->max_abs, INT32_MAX);
   out->bound_bits = (int32_t)std::ceil(p->bound);
   if (a.items_done != p->items.size()) return fail(BD_ERR_CUDA, "enumeration did not process every work item");
@@ -266,7 +266,7 @@ int bd_plan_info(const bd_plan* plan, int64_t* info) {
   info[1] = plan->shape.blocks;
   info[2] = plan->shape.warps;
   info[3] = (int64_t)plan->shape.smem;
-  info[4] = plan->wide ? 1 : 0;
+  info[4] = plan->path;
   info[5] = plan->shape.slots;
   info[6] = 0;
   info[7] = 0;
@@ -384,9 +384,10 @@ int bd_classify(const int64_t* points, const int64_t* lifts, int32_t npts, int32
     lo = std::min(lo, lifts[i]);
     hi = std::max(hi, lifts[i]);
   }
-  const double bound = bd::hadamard_log2(points, lifts, npts, k, hi - lo);
-  if (bound >= INT128_BITS) return fail(BD_ERR_OVERFLOW, "Hadamard bound exceeds 2^127");
-  const bool wide = bound >= INT64_BITS;
+  double coord_bits = 0;
+  const double bound = bd::hadamard_log2(points, lifts, npts, k, hi - lo, &coord_bits);
+  const int path = bd::choose_path(coord_bits, bound);
+  if (path < 0) return fail(BD_ERR_OVERFLOW, "Hadamard bound exceeds 2^127");
   cudaStream_t st = g_stream;
   int64_t *d_pts = nullptr, *d_lifts = nullptr, *d_abs = nullptr;
   uint8_t* d_sub = nullptr;
@@ -413,7 +414,7 @@ int bd_classify(const int64_t* points, const int64_t* lifts, int32_t npts, int32
   CL(cudaMemcpyAsync(d_pts, points, sizeof(int64_t) * npts * k, cudaMemcpyHostToDevice, st));
   CL(cudaMemcpyAsync(d_lifts, lifts, sizeof(int64_t) * npts, cudaMemcpyHostToDevice, st));
   CL(cudaMemcpyAsync(d_sub, subsets, (size_t)count * (k + 1), cudaMemcpyHostToDevice, st));
-  CL(bd::launch_classify(d_pts, d_lifts, npts, k, d_sub, count, d_status, d_abs, wide, st));
+  CL(bd::launch_classify(d_pts, d_lifts, npts, k, d_sub, count, d_status, d_abs, path, st));
   CL(cudaMemcpyAsync(status, d_status, sizeof(int32_t) * count, cudaMemcpyDeviceToHost, st));
   CL(cudaMemcpyAsync(absdet, d_abs, sizeof(int64_t) * count, cudaMemcpyDeviceToHost, st));
   CL(cudaStreamSynchronize(st));
@@ -437,9 +438,14 @@ int bd_host_volume_lifted(const int64_t* points, const int64_t* lifts, int32_t n
     lo = std::min(lo, lifts[i]);
     hi = std::max(hi, lifts[i]);
   }
-  const double bound = bd::hadamard_log2(points, lifts, npts, k, hi - lo);
-  if (bound >= INT128_BITS) return fail(BD_ERR_OVERFLOW, "Hadamard bound exceeds 2^127");
-  const bool wide = bound >= INT64_BITS;
+  double coord_bits = 0;
+  const double bound = bd::hadamard_log2(points, lifts, npts, k, hi - lo, &coord_bits);
+  int path = bd::choose_path(coord_bits, bound);
+  if (path < 0) return fail(BD_ERR_OVERFLOW, "Hadamard bound exceeds 2^127");
+  if (threads < 0) {  // a negative thread count forces the 128-bit path (tests of the wide walker)
+    path = bd::PATH_WIDE;
+    threads = -threads;
+  }
   std::vector<int64_t> P((size_t)(k + 1) * npts);
   for (int q = 0; q < npts; ++q) {
     for (int c = 0; c < k; ++c) P[(size_t)c * npts + q] = points[(size_t)q * k + c];
@@ -447,15 +453,14 @@ int bd_host_volume_lifted(const int64_t* points, const int64_t* lifts, int32_t n
   }
   const auto items = bd::build_items(npts, k, 4096);
   bd::Acc acc{};
-  if (wide) bd::host_enumerate<i128>(P.data(), npts, k, items, std::max(1, threads), acc);
-  else bd::host_enumerate<int64_t>(P.data(), npts, k, items, std::max(1, threads), acc);
+  bd::host_enumerate(path, P.data(), npts, k, items, std::max(1, threads), acc);
   std::memset(out, 0, sizeof(*out));
   set_u128(out->nvol_lo, out->nvol_hi, acc.nvol);
   out->cells = acc.cells;
   out->singular = acc.singular;
   out->ties = acc.ties;
   out->subsets = bd::binom(npts, k + 1);
-  out->flags = (wide ? BD_FLAG_INT128 : 0) | (acc.nvol == 0 ? BD_FLAG_DEGENERATE : 0);
+  out->flags = (path == bd::PATH_WIDE ? BD_FLAG_INT128 : 0) | (acc.nvol == 0 ? BD_FLAG_DEGENERATE : 0);
   int64_t mx = 0;
   for (int64_t i = 0; i < (int64_t)npts * k; ++i) mx = std::max<int64_t>(mx, std::llabs(points[i]));
   out->max_abs_coord = (int32_t)std::min<int64_t>(mx, INT32_MAX);

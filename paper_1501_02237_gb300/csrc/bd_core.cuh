@@ -55,6 +55,14 @@ BD_HD int ctz64(uint64_t x) {
 #endif
 }
 
+BD_HD int popc64(uint64_t x) {
+#ifdef __CUDA_ARCH__
+  return __popcll(x);
+#else
+  return __builtin_popcountll(x);
+#endif
+}
+
 BD_HD int ctz128(u128 x) {
   uint64_t lo = (uint64_t)x;
   return lo ? ctz64(lo) : 64 + ctz64((uint64_t)(x >> 64));
@@ -110,6 +118,45 @@ BD_HD int64_t bareiss(int64_t a, int64_t p, int64_t b, int64_t r, const Div64& D
   i128 v = (i128)a * p - (i128)b * r;  // |a p|, |b r| < 2^126: exact
   uint64_t lo = (uint64_t)(v >> D.shift);
   return (int64_t)(lo * D.inv);
+}
+
+// divider for 32-bit coordinate minors, also usable for the 64-bit lift minors
+struct Div32 {
+  uint32_t inv32;  // inverse of the odd part modulo 2^32
+  uint64_t inv64;  // the same odd part (sign-extended) inverted modulo 2^64
+  int shift;
+};
+
+BD_HD Div32 make_div(int32_t d) {
+  Div32 r;
+  r.shift = ctz64((uint64_t)(uint32_t)d);
+  const int64_t odd = (int64_t)(d >> r.shift);
+  const uint32_t o32 = (uint32_t)odd;
+  uint32_t y = (3u * o32) ^ 2u;  // 5 bits
+  y *= 2u - o32 * y;             // 10
+  y *= 2u - o32 * y;             // 20
+  y *= 2u - o32 * y;             // 40 >= 32
+  r.inv32 = y;
+  uint64_t x = y;
+  x *= 2u - (uint64_t)odd * x;   // 80 >= 64
+  r.inv64 = x;
+  return r;
+}
+
+// (a*p - b*r) / d for 32-bit minors: the products are exact in 64 bits
+BD_HD int32_t bareiss(int32_t a, int32_t p, int32_t b, int32_t r, const Div32& D) {
+  const int64_t v = (int64_t)a * p - (int64_t)b * r;
+  return (int32_t)((uint32_t)(v >> D.shift) * D.inv32);
+}
+
+// (a*p - b*r) / d for a 64-bit lift minor a, r with 32-bit coordinate minors p, b, d
+BD_HD int64_t bareiss(int64_t a, int32_t p, int32_t b, int64_t r, const Div32& D) {
+  if (D.shift == 0) {
+    const uint64_t v = (uint64_t)a * (uint64_t)(int64_t)p - (uint64_t)(int64_t)b * (uint64_t)r;
+    return (int64_t)(v * D.inv64);
+  }
+  const i128 v = (i128)a * p - (i128)b * r;  // < 2^95 in magnitude
+  return (int64_t)((uint64_t)(v >> D.shift) * D.inv64);
 }
 
 // signed 128 x 128 -> 256 product as (hi, lo)
@@ -187,6 +234,9 @@ struct Acc {
   uint64_t cells;    // accepted cells
   uint64_t singular; // subsets with D0 = 0
   uint64_t ties;     // subsets with no point below and at least one point on the hyperplane
+#ifdef BD_COUNT
+  uint64_t builds[KMAX + 1], fails[KMAX + 1], leaves, leaf_singular, exact_fallbacks;
+#endif
 };
 
 BD_HD uint64_t binom(int n, int k) {
@@ -200,11 +250,13 @@ BD_HD uint64_t binom(int n, int k) {
 // number of (K+1)-subsets below a prefix whose last index is `last` and length `len`
 BD_HD uint64_t subtree_size(int N, int K, int last, int len) { return binom(N - 1 - last, K + 1 - len); }
 
-// offset of level j inside a point's stack: sum_{i<j} (K+1-i)
-BD_HD int level_offset(int K, int j) { return j * (K + 1) - (j * (j - 1)) / 2; }
+// offset of level j inside a point's coordinate stack: sum_{i<j} (K-i) (level j keeps K-j
+// coordinate minors; the lift minor of level j is kept apart, one per level)
+BD_HD int level_offset(int K, int j) { return j * K - (j * (j - 1)) / 2; }
 BD_HD int stack_entries(int K) { return level_offset(K, K); }
 
 template <class T> struct DivOf;
+template <> struct DivOf<int32_t> { typedef Div32 type; };
 template <> struct DivOf<int64_t> { typedef Div64 type; };
 template <> struct DivOf<i128> { typedef Div128 type; };
 
@@ -219,69 +271,108 @@ template <class T> BD_HD T tabs(T x) { return x < 0 ? -x : x; }
 // ---------------------------------------------------------------------------------------------
 enum { ST_SINGULAR = 0, ST_REJECTED = 1, ST_ACCEPTED = 2, ST_TIE = 3 };
 
-template <class T, class Team>
+template <class TC, class TL, class Team>
 struct Walker {
-  typedef typename DivOf<T>::type Div;
+  typedef typename DivOf<TC>::type Div;
   Team& tm;
   const int64_t* P;
   int N, K, SLOTS;
-  T* st;
-  float* fl;        // single-precision copies of the two level K-1 entries: fl[q], fl[SLOTS + q]
+  TC* sc;           // coordinate minors: (level j, entry e, point q) at sc[(off_j + e) * SLOTS + q]
+  TL* sl;           // lift minor of level j for point q at sl[j * SLOTS + q]
+  float* fl;        // single-precision copies of the level K-1 minors: C at fl[q], L at fl[SLOTS + q]
   int s[KMAX + 1];  // chosen indices s_0 .. s_j
   Div dv[KMAX];     // exact divider by the pivot of each level (dv[0]: by 1)
   int psign;        // sign of the level K-1 pivot p_{K-1}
+#ifdef BD_COUNT
+  Acc* cnt = nullptr;
+#endif
 
-  BD_HD Walker(Team& t, const int64_t* P_, int N_, int K_, int SLOTS_, T* st_, float* fl_)
-      : tm(t), P(P_), N(N_), K(K_), SLOTS(SLOTS_), st(st_), fl(fl_) {}
+  BD_HD Walker(Team& t, const int64_t* P_, int N_, int K_, int SLOTS_, TC* sc_, TL* sl_, float* fl_)
+      : tm(t), P(P_), N(N_), K(K_), SLOTS(SLOTS_), sc(sc_), sl(sl_), fl(fl_) {}
 
   // state 0: lifted differences z_q = (a_q - a_{s_0}, w_q - w_{s_0})
   BD_HD void start(int s0) {
     tm.sync();  // the previous item's readers are done with the stack
     s[0] = s0;
-    for (int q = tm.lane(); q < N; q += tm.lanes())
-      for (int c = 0; c <= K; ++c) st[c * SLOTS + q] = (T)(P[c * N + q] - P[c * N + s0]);
-    dv[0] = make_div((T)1);
+    for (int q = tm.lane(); q < N; q += tm.lanes()) {
+      for (int c = 0; c < K; ++c) sc[c * SLOTS + q] = (TC)(P[c * N + q] - P[c * N + s0]);
+      sl[q] = (TL)(P[K * N + q] - P[K * N + s0]);
+    }
+    dv[0] = make_div((TC)1);
+    psign = 1;
     tm.sync();
   }
 
-  // state j from state j-1 with pivot point c (s_j = c); false if the pivot row has no
-  // nonzero coordinate entry (every subset extending the prefix is singular)
-  BD_HD bool build(int j, int c) {
+  // the float copies of the last level (K-1) for the leaf filter
+  BD_HD void copy_floats(int j) {
+    const int o = level_offset(K, j);
+    for (int q = tm.lane(); q < N; q += tm.lanes()) {
+      fl[q] = (float)sc[o * SLOTS + q];
+      fl[SLOTS + q] = (float)sl[j * SLOTS + q];
+    }
+  }
+
+  // Bareiss step: state j from state j-1 with pivot point c (s_j = c).  Returns false when the
+  // pivot row has no nonzero coordinate minor (every extension is singular).  At the last level
+  // the coordinate minors come first; the lift minors are formed only when some candidate last
+  // point p > c has a nonzero coordinate minor (lazy: *live = 0 means nothing left to test).
+  BD_HD bool build(int j, int c, uint64_t* live = nullptr) {
     const int po = level_offset(K, j - 1), no = level_offset(K, j);
-    const int ncoord = K - j + 1;  // coordinate entries of state j-1; its lift is at index ncoord
+    const int ncoord = K - j + 1;  // coordinate minors of state j-1
     int pi = -1;
     for (int e = 0; e < ncoord; ++e)
-      if (st[(po + e) * SLOTS + c] != 0) { pi = e; break; }
+      if (sc[(po + e) * SLOTS + c] != 0) { pi = e; break; }
+#ifdef BD_COUNT
+    if (cnt) { if (pi < 0) cnt->fails[j]++; else cnt->builds[j]++; }
+#endif
     if (pi < 0) return false;
-    const T pj = st[(po + pi) * SLOTS + c];
+    const TC pj = sc[(po + pi) * SLOTS + c];
+    const TL rl = sl[(j - 1) * SLOTS + c];
     const Div D = dv[j - 1];
     const bool last = (j == K - 1);
     tm.sync();  // readers of the old state j (a sibling's subtree) are done
+    uint64_t mine = 0;
     for (int q = tm.lane(); q < N; q += tm.lanes()) {
-      const T bq = st[(po + pi) * SLOTS + q];
-      for (int e = 0; e < ncoord; ++e) {  // state j: K-j coordinates + lift = ncoord entries
+      const TC bq = sc[(po + pi) * SLOTS + q];
+      for (int e = 0; e < ncoord - 1; ++e) {
         const int ep = e < pi ? e : e + 1;
-        const T v = bareiss(st[(po + ep) * SLOTS + q], pj, bq, st[(po + ep) * SLOTS + c], D);
-        st[(no + e) * SLOTS + q] = v;
-        if (last) fl[e * SLOTS + q] = (float)v;
+        const TC v = bareiss(sc[(po + ep) * SLOTS + q], pj, bq, sc[(po + ep) * SLOTS + c], D);
+        sc[(no + e) * SLOTS + q] = v;
+        if (last && v != 0 && q > c) mine |= 1ull << q;
+      }
+      if (!last) sl[j * SLOTS + q] = bareiss(sl[(j - 1) * SLOTS + q], pj, bq, rl, D);
+    }
+    s[j] = c;
+    if (!last) {
+      dv[j] = make_div(pj);
+      tm.sync();
+      return true;
+    }
+    psign = pj < 0 ? -1 : 1;  // the leaf test needs only the sign of p_{K-1}
+    const uint64_t cand = tm.or_all(mine);
+    *live = cand;
+    if (cand) {
+      for (int q = tm.lane(); q < N; q += tm.lanes()) {
+        const TC bq = sc[(po + pi) * SLOTS + q];
+        const TL v = bareiss(sl[(j - 1) * SLOTS + q], pj, bq, rl, D);
+        sl[j * SLOTS + q] = v;
+        fl[q] = (float)sc[no * SLOTS + q];
+        fl[SLOTS + q] = (float)v;
       }
     }
-    if (last) psign = pj < 0 ? -1 : 1;  // the leaf test needs only the sign of p_{K-1}
-    else dv[j] = make_div(pj);
-    s[j] = c;
     tm.sync();
     return true;
   }
 
-  // level 0 is the last level when K = 1: its float copies and pivot sign (p_0 = 1)
-  BD_HD void finish_level0() {
-    if (K != 1) return;
-    for (int q = tm.lane(); q < N; q += tm.lanes()) {
-      fl[q] = (float)st[q];
-      fl[SLOTS + q] = (float)st[SLOTS + q];
-    }
-    psign = 1;
+  // level 0 is the last level when K = 1
+  BD_HD uint64_t finish_level0() {
+    uint64_t mine = 0;
+    for (int q = tm.lane(); q < N; q += tm.lanes())
+      if (q > s[0] && sc[q] != 0) mine |= 1ull << q;
+    copy_floats(0);
+    const uint64_t cand = tm.or_all(mine);
     tm.sync();
+    return cand;
   }
 
   BD_HD uint64_t member_mask() const {
@@ -290,22 +381,30 @@ struct Walker {
     return mask;
   }
 
-  // status of the cell {s_0 .. s_{K-1}, p}; |D0| in absdet.  Uniform across the team.
-  // s(q) = sigma (C_p L_q - C_q L_p) / p_{K-1} and D0 = sigma C_p, so q lies strictly below
-  // the lifted hyperplane iff  sign(C_p) sign(p_{K-1}) (C_p L_q - C_q L_p) < 0.
-  BD_HD int leaf(int p, uint64_t mask, T& absdet) {
+  // status of the cell {s_0 .. s_{K-1}, p} (its coordinate minor C_p is nonzero); |D0| in
+  // absdet.  s(q) = sigma (C_p L_q - C_q L_p) / p_{K-1} and D0 = sigma C_p, so q lies strictly
+  // below the lifted hyperplane iff sign(C_p) sign(p_{K-1}) (C_p L_q - C_q L_p) < 0.
+  BD_HD int leaf(int p, uint64_t mask, TL& absdet) {
     const int lo = level_offset(K, K - 1);
-    const T Cp = st[lo * SLOTS + p];
+    const TL Cp = (TL)sc[lo * SLOTS + p];
+    const TL Lp = sl[(K - 1) * SLOTS + p];
     absdet = tabs(Cp);
+#ifdef BD_COUNT
+    if (cnt) cnt->leaves++;
+#endif
     if (Cp == 0) return ST_SINGULAR;
-    const T Lp = st[(lo + 1) * SLOTS + p];
     const float Cpf = fl[p], Lpf = fl[SLOTS + p];
     const int sig = (Cp < 0 ? -1 : 1) * psign;
     bool below = false, on = false;
     for (int q = tm.lane(); q < N; q += tm.lanes()) {
       if (((mask >> q) & 1ull) || q == p) continue;
-      int sg = sizeof(T) == 8 ? cross_sign_filtered(Cpf, fl[SLOTS + q], fl[q], Lpf) : 2;
-      if (sg == 2) sg = cross_sign(Cp, st[(lo + 1) * SLOTS + q], st[lo * SLOTS + q], Lp);
+      int sg = sizeof(TL) == 8 ? cross_sign_filtered(Cpf, fl[SLOTS + q], fl[q], Lpf) : 2;
+      if (sg == 2) {
+#ifdef BD_COUNT
+        if (cnt) cnt->exact_fallbacks++;
+#endif
+        sg = cross_sign(Cp, sl[(K - 1) * SLOTS + q], (TL)sc[lo * SLOTS + q], Lp);
+      }
       if (sg == 0) on = true;
       else if (sg != sig) below = true;
     }
@@ -313,13 +412,26 @@ struct Walker {
     return tm.any(on) ? ST_TIE : ST_ACCEPTED;
   }
 
+  BD_HD void leaves(uint64_t cand, Acc& acc) {
+    const uint64_t mask = member_mask();
+    while (cand) {
+      const int p = ctz64(cand);
+      cand &= cand - 1;
+      TL ad;
+      const int stt = leaf(p, mask, ad);
+      if (stt == ST_ACCEPTED) { acc.cells += 1; acc.nvol += (u128)ad; }
+      else if (stt == ST_TIE) acc.ties += 1;
+    }
+  }
+
   // every (K+1)-subset extending the prefix it.idx[0 .. it.len-1]
   BD_HD void run_item(const Item& it, Acc& acc) {
     const int L = it.len;
     start(it.idx[0]);
-    finish_level0();
+    uint64_t live = 0;
+    if (K == 1) live = finish_level0();
     for (int j = 1; j < L; ++j) {
-      if (!build(j, it.idx[j])) {
+      if (!build(j, it.idx[j], &live)) {
         acc.singular += subtree_size(N, K, it.idx[L - 1], L);
         return;
       }
@@ -329,14 +441,10 @@ struct Walker {
     cur[j] = it.idx[L - 1];
     for (;;) {
       if (j == K) {
-        const uint64_t mask = member_mask();
-        for (int p = s[K - 1] + 1; p < N; ++p) {
-          T ad;
-          const int stt = leaf(p, mask, ad);
-          if (stt == ST_ACCEPTED) { acc.cells += 1; acc.nvol += (u128)ad; }
-          else if (stt == ST_SINGULAR) acc.singular += 1;
-          else if (stt == ST_TIE) acc.ties += 1;
-        }
+        // candidates with a zero coordinate minor are singular cells
+        const int s_last = s[K - 1];
+        acc.singular += (uint64_t)(N - 1 - s_last) - (uint64_t)popc64(live);
+        leaves(live, acc);
         if (--j < L) break;
         continue;
       }
@@ -345,7 +453,7 @@ struct Walker {
         if (--j < L) break;
         continue;
       }
-      if (!build(j, c)) {
+      if (!build(j, c, &live)) {
         acc.singular += binom(N - 1 - c, K - j);
         continue;
       }
@@ -355,11 +463,13 @@ struct Walker {
   }
 
   // status of one given subset sub[0] < .. < sub[K]
-  BD_HD int classify(const uint8_t* sub, T& absdet) {
+  BD_HD int classify(const uint8_t* sub, TL& absdet) {
     start(sub[0]);
-    finish_level0();
+    uint64_t live = 0;
+    if (K == 1) live = finish_level0();
     for (int j = 1; j < K; ++j)
-      if (!build(j, sub[j])) { absdet = 0; return ST_SINGULAR; }
+      if (!build(j, sub[j], &live)) { absdet = 0; return ST_SINGULAR; }
+    if (!((live >> sub[K]) & 1ull)) { absdet = 0; return ST_SINGULAR; }
     return leaf(sub[K], member_mask(), absdet);
   }
 };

@@ -7,6 +7,9 @@
 #include <cmath>
 #include <cstdlib>
 #include <thread>
+#ifdef BD_DEBUG
+#include <cstdio>
+#endif
 
 #include "../../include/binodeg.h"
 
@@ -140,48 +143,63 @@ bool consistent(const int64_t* coef, int m, const Mat& R, std::string& err, bool
   return true;
 }
 
-// LLL reduction (delta = 0.99) of the rows of B (d x n), exact integer row operations, Gram-
-// Schmidt data in double only to take decisions (any outcome is a basis of the same lattice).
+// LLL reduction (delta = 0.99) of the rows of B (d x n).  Row operations are exact integer
+// operations; Gram-Schmidt data is kept in double only to steer them (every operation is
+// unimodular, so the rows always span the same lattice whatever the doubles decide).  To keep
+// the doubles trustworthy with large entries, the coefficients of row k are recomputed from the
+// exact integer row before each use and size reduction is repeated until it makes only small
+// corrections (the usual floating-point LLL safeguard).
 bool lll(std::vector<i128>& B, int d, int n) {
   if (d <= 1) return true;
-  std::vector<double> mu((size_t)d * d), bn(d);
-  auto gso = [&]() {
-    std::vector<double> bs((size_t)d * n);
-    for (int i = 0; i < d; ++i) {
-      for (int c = 0; c < n; ++c) bs[(size_t)i * n + c] = (double)B[(size_t)i * n + c];
-      for (int j = 0; j < i; ++j) {
+  std::vector<double> bs((size_t)d * n), bn(d, 0.0), mu((size_t)d * d, 0.0);
+  auto row = [&](int i) { return &B[(size_t)i * n]; };
+  auto set_row = [&](int k) -> bool {  // size-reduce b_k, then b*_k and |b*_k|^2
+    for (int iter = 0; iter < 100; ++iter) {
+      for (int j = 0; j < k; ++j) {
         double dot = 0;
-        for (int c = 0; c < n; ++c) dot += (double)B[(size_t)i * n + c] * bs[(size_t)j * n + c];
-        const double m = bn[j] > 0 ? dot / bn[j] : 0.0;
-        mu[(size_t)i * d + j] = m;
-        for (int c = 0; c < n; ++c) bs[(size_t)i * n + c] -= m * bs[(size_t)j * n + c];
+        for (int c = 0; c < n; ++c) dot += (double)row(k)[c] * bs[(size_t)j * n + c];
+        mu[(size_t)k * d + j] = bn[j] > 0 ? dot / bn[j] : 0.0;
       }
-      double s = 0;
-      for (int c = 0; c < n; ++c) s += bs[(size_t)i * n + c] * bs[(size_t)i * n + c];
-      bn[i] = s;
+      bool large = false;
+      for (int j = k - 1; j >= 0; --j) {
+        const double m = mu[(size_t)k * d + j];
+        if (std::fabs(m) <= 0.51) continue;
+        if (std::fabs(m) > 4e18) return false;
+        const i128 q = (i128)std::llround(m);
+        for (int c = 0; c < n; ++c) {
+          i128 t;
+          if (__builtin_mul_overflow(q, row(j)[c], &t)) return false;
+          const i128 v = row(k)[c] - t;
+          if (iabs(v) >= ENTRY_LIMIT) return false;
+          row(k)[c] = v;
+        }
+        for (int l = 0; l < j; ++l) mu[(size_t)k * d + l] -= (double)q * mu[(size_t)j * d + l];
+        mu[(size_t)k * d + j] -= (double)q;
+        if (iabs(q) > ((i128)1 << 20)) large = true;
+      }
+      if (!large) break;
     }
+    for (int c = 0; c < n; ++c) {
+      double v = (double)row(k)[c];
+      for (int j = 0; j < k; ++j) v -= mu[(size_t)k * d + j] * bs[(size_t)j * n + c];
+      bs[(size_t)k * n + c] = v;
+    }
+    double s2 = 0;
+    for (int c = 0; c < n; ++c) s2 += bs[(size_t)k * n + c] * bs[(size_t)k * n + c];
+    bn[k] = s2;
+    return true;
   };
-  gso();
+  if (!set_row(0)) return false;
   int k = 1;
   long guard = 0;
-  while (k < d && guard++ < 200000) {
-    for (int j = k - 1; j >= 0; --j) {
-      const double m = mu[(size_t)k * d + j];
-      if (std::fabs(m) <= 0.5) continue;
-      const i128 q = (i128)std::llround(m);
-      for (int c = 0; c < n; ++c) {
-        const i128 v = B[(size_t)k * n + c] - q * B[(size_t)j * n + c];
-        if (iabs(v) >= ENTRY_LIMIT) return false;
-        B[(size_t)k * n + c] = v;
-      }
-      for (int l = 0; l < j; ++l) mu[(size_t)k * d + l] -= (double)q * mu[(size_t)j * d + l];
-      mu[(size_t)k * d + j] -= (double)q;
-    }
+  while (k < d) {
+    if (++guard > 2000000) return true;  // still a basis of the same lattice
+    if (!set_row(k)) return false;
     const double m = mu[(size_t)k * d + k - 1];
     if (bn[k] < (0.99 - m * m) * bn[k - 1]) {
-      for (int c = 0; c < n; ++c) std::swap(B[(size_t)k * n + c], B[(size_t)(k - 1) * n + c]);
-      gso();
+      for (int c = 0; c < n; ++c) std::swap(row(k)[c], row(k - 1)[c]);
       k = std::max(k - 1, 1);
+      if (k == 1 && !set_row(0)) return false;
     } else {
       ++k;
     }
@@ -211,27 +229,68 @@ bool kernel_rows(const Mat& M, Mat& U, std::string& err) {
         i128 pr;
         if (!mul_ok(B[i][t], M.at(t, j), pr) || !add_ok(v[i], pr, v[i])) { err = "kernel values overflow"; return false; }
       }
-    int first = -1;
+    // Euclid on the value vector: reduce every value modulo the smallest nonzero one (row
+    // operations b_i -= q b_min) until a single nonzero value g = gcd remains; this keeps the
+    // multipliers no larger than the values themselves.  If the rows still grow, LLL-reduce
+    // them (a unimodular change of basis; the values are recomputed) and continue.
+    bool all_zero = true;
     for (int i = 0; i < d; ++i)
-      if (v[i] != 0) { first = i; break; }
-    if (first < 0) continue;
-    std::swap(B[0], B[first]);
-    std::swap(v[0], v[first]);
-    for (int i = 1; i < d; ++i) {
-      if (v[i] == 0) continue;
-      i128 s, t, u, w;
-      bezout2(v[0], v[i], s, t, u, w);
-      for (int c = 0; c < n; ++c) {
-        i128 x = B[0][c], y = B[i][c], a1, a2, b1, b2;
-        if (!mul_ok(s, x, a1) || !mul_ok(t, y, a2) || !mul_ok(u, x, b1) || !mul_ok(w, y, b2) ||
-            !add_ok(a1, a2, B[0][c]) || !add_ok(b1, b2, B[i][c])) { err = "kernel basis overflow"; return false; }
+      if (v[i] != 0) all_zero = false;
+    if (all_zero) continue;  // the whole current lattice is orthogonal to this column
+    for (int guard = 0;; ++guard) {
+      int piv = -1, nz = 0;
+      for (int i = 0; i < d; ++i)
+        if (v[i] != 0) {
+          ++nz;
+          if (piv < 0 || iabs(v[i]) < iabs(v[piv])) piv = i;
+        }
+      if (nz <= 1) {
+        std::swap(B[0], B[piv]);
+        std::swap(v[0], v[piv]);
+        break;
       }
-      const i128 nv0 = s * v[0] + t * v[i];
-      v[i] = 0;
-      v[0] = nv0;
+      i128 big = 0;
+      for (int i = 0; i < d; ++i) {
+        if (i == piv || v[i] == 0) continue;
+        i128 q = v[i] / v[piv];  // truncation; the remainder is smaller than |v_piv|
+        const i128 r = v[i] - q * v[piv];
+        if (2 * iabs(r) > iabs(v[piv])) q += ((r > 0) == (v[piv] > 0)) ? 1 : -1;  // nearest quotient
+        for (int c = 0; c < n; ++c) {
+          i128 t;
+          if (!mul_ok(q, B[piv][c], t) || !add_ok(B[i][c], -t, B[i][c])) { err = "kernel basis overflow"; return false; }
+          big = std::max(big, iabs(B[i][c]));
+        }
+        v[i] -= q * v[piv];
+      }
+      if (big > ((i128)1 << 40) || guard > 4000) {
+        std::vector<i128> flat;
+        for (auto& row : B) flat.insert(flat.end(), row.begin(), row.end());
+        if (!lll(flat, d, n)) { err = "kernel basis entries exceed 2^62"; return false; }
+        for (int i = 0; i < d; ++i) {
+          v[i] = 0;
+          for (int c = 0; c < n; ++c) {
+            B[i][c] = flat[(size_t)i * n + c];
+            i128 pr;
+            if (!mul_ok(B[i][c], M.at(c, j), pr) || !add_ok(v[i], pr, v[i])) { err = "kernel values overflow"; return false; }
+          }
+        }
+        if (guard > 8000) { err = "kernel elimination did not converge"; return false; }
+      }
     }
     B.erase(B.begin());
-    if (!B.empty()) {
+    i128 big = 0;
+    for (auto& r : B)
+      for (i128 x : r) big = std::max(big, iabs(x));
+    const bool last_col = (j == m - 1);
+#ifdef BD_DEBUG
+    {
+      double lb = 0;
+      for (auto& r : B) for (i128 x : r) lb = std::max(lb, (double)iabs(x));
+      double vb = 0;
+      fprintf(stderr, "kernel_rows %dx%d col %d d=%zu big=%.3g\n", n, m, j, B.size(), lb);
+    }
+#endif
+    if (!B.empty() && (big > ((i128)1 << 16) || last_col)) {
       std::vector<i128> flat;
       for (auto& row : B) flat.insert(flat.end(), row.begin(), row.end());
       if (!lll(flat, (int)B.size(), n)) { err = "kernel basis entries exceed 2^62"; return false; }
@@ -397,11 +456,13 @@ int reduce_system(const int64_t* A, int n, int m, const int64_t* coef, Reduction
   return BD_OK;
 }
 
-double hadamard_log2(const int64_t* pts, const int64_t* lifts, int npts, int k, int64_t max_lift_spread) {
+double hadamard_log2(const int64_t* pts, const int64_t* lifts, int npts, int k, int64_t max_lift_spread,
+                     double* coord) {
   // Column-wise Hadamard bound for the (K+1) x (K+1) lifted difference matrices: for column c
   // and base point s, the K+1 largest squared differences |a_q[c] - a_s[c]|^2 bound the
-  // squared column norm; the bound is the product over columns of the worst base point.
-  double total = 0;
+  // squared column norm; the bound is the product over columns of the worst base point
+  // (each factor at least 1, so it also bounds every smaller minor).
+  double total = 0, coords = 0;
   std::vector<double> sq(npts);
   for (int c = 0; c <= k; ++c) {
     double best = 1.0;
@@ -419,8 +480,19 @@ double hadamard_log2(const int64_t* pts, const int64_t* lifts, int npts, int k, 
       best = std::max(best, sum);
     }
     total += 0.5 * std::log2(best);
+    if (c < k) coords = total;
   }
+  if (coord) *coord = coords;
   return total;
+}
+
+int choose_path(double coord_bits, double full_bits) {
+  // margins cover the rounding of the double-precision logarithms
+  if (full_bits < 126.99) {
+    if (full_bits < 62.99) return coord_bits < 30.99 ? 0 : 1;
+    return 2;
+  }
+  return -1;
 }
 
 std::vector<Item> build_items(int N, int K, uint64_t max_subsets) {
@@ -462,18 +534,20 @@ struct HostTeam {
   int lanes() const { return 1; }
   bool any(bool b) const { return b; }
   void sync() const {}
+  uint64_t or_all(uint64_t x) const { return x; }
 };
 }  // namespace
 
-template <class T>
-void host_enumerate(const int64_t* P, int N, int K, const std::vector<Item>& items, int threads, Acc& acc) {
+template <class TC, class TL>
+void host_run(const int64_t* P, int N, int K, const std::vector<Item>& items, int threads, Acc& acc) {
   std::atomic<size_t> next(0);
   std::vector<Acc> part(std::max(1, threads));
   auto work = [&](int tid) {
     HostTeam tm;
-    std::vector<T> st((size_t)N * stack_entries(K));
+    std::vector<TC> sc((size_t)N * stack_entries(K));
+    std::vector<TL> sl((size_t)N * K);
     std::vector<float> fl((size_t)2 * N);
-    Walker<T, HostTeam> W(tm, P, N, K, N, st.data(), fl.data());
+    Walker<TC, TL, HostTeam> W(tm, P, N, K, N, sc.data(), sl.data(), fl.data());
     Acc a{};
     for (;;) {
       const size_t i = next.fetch_add(1);
@@ -498,7 +572,10 @@ void host_enumerate(const int64_t* P, int N, int K, const std::vector<Item>& ite
   }
 }
 
-template void host_enumerate<int64_t>(const int64_t*, int, int, const std::vector<Item>&, int, Acc&);
-template void host_enumerate<i128>(const int64_t*, int, int, const std::vector<Item>&, int, Acc&);
+void host_enumerate(int path, const int64_t* P, int N, int K, const std::vector<Item>& items, int threads, Acc& acc) {
+  if (path == 0) host_run<int32_t, int64_t>(P, N, K, items, threads, acc);
+  else if (path == 1) host_run<int64_t, int64_t>(P, N, K, items, threads, acc);
+  else host_run<i128, i128>(P, N, K, items, threads, acc);
+}
 
 }  // namespace bd

@@ -22,18 +22,23 @@ struct Reduction {
 // Returns BD_OK or an error code; message in `err`.
 int reduce_system(const int64_t* A, int n, int m, const int64_t* coef, Reduction& out, std::string& err);
 
-// ceil(log2) of a Hadamard bound on every minor of the lifted difference matrices
-// [a_q - a_s, w_q - w_s] (rows q, K+1 of them) that the enumeration forms.
-double hadamard_log2(const int64_t* pts, const int64_t* lifts_maxdiff_or_null, int npts, int k,
-                     int64_t max_lift_spread);
+// log2 of Hadamard bounds on every minor of the lifted difference matrices [a_q - a_s, w_q - w_s]
+// (K+1 rows) that the enumeration forms: `coord` for minors of coordinate columns only, the
+// return value for all minors (lift column included).  lifts == nullptr: lift differences are
+// bounded by max_lift_spread.
+double hadamard_log2(const int64_t* pts, const int64_t* lifts, int npts, int k, int64_t max_lift_spread,
+                     double* coord = nullptr);
+
+// Integer path for the bounds: 0 (int32 coordinate minors, int64 lift minors), 1 (int64, int64),
+// 2 (int128), -1 (too large).
+int choose_path(double coord_bits, double full_bits);
 
 // Prefix work list: every (k+1)-subset of {0..npts-1} lies below exactly one item; items are
 // split until each holds at most `max_subsets` subsets (or reaches length k), then sorted by
 // decreasing size.
 std::vector<Item> build_items(int npts, int k, uint64_t max_subsets);
 
-// Host emulation of the warp enumeration on `threads` CPU threads.
-template <class T>
-void host_enumerate(const int64_t* P, int N, int K, const std::vector<Item>& items, int threads, Acc& acc);
+// Host emulation of the warp enumeration on `threads` CPU threads, for an integer path.
+void host_enumerate(int path, const int64_t* P, int N, int K, const std::vector<Item>& items, int threads, Acc& acc);
 
 }  // namespace bd

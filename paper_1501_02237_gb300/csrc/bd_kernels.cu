@@ -36,16 +36,42 @@ struct WarpTeam {
     __syncwarp();
 #endif
   }
+  BD_HD uint64_t or_all(uint64_t x) const {
+#ifdef __CUDA_ARCH__
+    const unsigned lo = __reduce_or_sync(0xffffffffu, (unsigned)x);
+    const unsigned hi = __reduce_or_sync(0xffffffffu, (unsigned)(x >> 32));
+    return ((uint64_t)hi << 32) | lo;
+#else
+    return x;
+#endif
+  }
 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 __host__ __device__ inline int round32(int x) { return (x + 31) & ~31; }
 
-// one warp's shared memory: its stack of reduced rows and two float rows for the last level
-template <class T>
+// one warp's shared memory: its coordinate-minor stack, lift-minor stack and the two float rows
+// of the last level, each 16-byte aligned
+template <class TC, class TL>
 __host__ __device__ inline size_t warp_bytes(int slots, int K) {
-  return align16((size_t)slots * stack_entries(K) * sizeof(T) + (size_t)2 * slots * sizeof(float));
+  return align16((size_t)slots * stack_entries(K) * sizeof(TC)) + align16((size_t)slots * K * sizeof(TL)) +
+         align16((size_t)2 * slots * sizeof(float));
 }
+
+template <class TC, class TL>
+struct WarpMem {
+  TC* sc;
+  TL* sl;
+  float* fl;
+  __device__ WarpMem(unsigned char* smem, int N, int K, int slots, int warp) {
+    unsigned char* b = smem + align16((size_t)(K + 1) * N * sizeof(int64_t)) + (size_t)warp * warp_bytes<TC, TL>(slots, K);
+    sc = reinterpret_cast<TC*>(b);
+    b += align16((size_t)slots * stack_entries(K) * sizeof(TC));
+    sl = reinterpret_cast<TL*>(b);
+    b += align16((size_t)slots * K * sizeof(TL));
+    fl = reinterpret_cast<float*>(b);
+  }
+};
 
 __device__ void load_points(int64_t* P, const EnumParams& p) {
   const int N = p.N, K = p.K;
@@ -70,21 +96,18 @@ __device__ void flush(const Acc& a, DevAcc* g, unsigned long long items) {
   if (items) atomicAdd(&g->items_done, items);
 }
 
-template <class T>
+template <class TC, class TL>
 __global__ void k_enumerate(EnumParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
   int64_t* P = reinterpret_cast<int64_t*>(smem);
   const int N = p.N, K = p.K;
   const int slots = round32(N);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  unsigned char* wbase = smem + align16((size_t)(K + 1) * N * sizeof(int64_t)) +
-                         (size_t)warp * warp_bytes<T>(slots, K);
-  T* st = reinterpret_cast<T*>(wbase);
-  float* fl = reinterpret_cast<float*>(wbase + (size_t)slots * stack_entries(K) * sizeof(T));
+  WarpMem<TC, TL> m(smem, N, K, slots, warp);
   load_points(P, p);
 
   WarpTeam tm;
-  Walker<T, WarpTeam> W(tm, P, N, K, slots, st, fl);
+  Walker<TC, TL, WarpTeam> W(tm, P, N, K, slots, m.sc, m.sl, m.fl);
   Acc acc{};
   unsigned long long done = 0;
   for (;;) {
@@ -99,7 +122,7 @@ __global__ void k_enumerate(EnumParams p) {
   if (lane == 0) flush(acc, p.acc, done);
 }
 
-template <class T>
+template <class TC, class TL>
 __global__ void k_classify(const int64_t* pts, const int64_t* lifts, int N, int K, const uint8_t* subsets,
                            int count, int32_t* status, int64_t* absdet) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -112,14 +135,11 @@ __global__ void k_classify(const int64_t* pts, const int64_t* lifts, int N, int 
   load_points(P, p);
   const int slots = round32(N);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, warps = blockDim.x >> 5;
-  unsigned char* wbase = smem + align16((size_t)(K + 1) * N * sizeof(int64_t)) +
-                         (size_t)warp * warp_bytes<T>(slots, K);
-  T* st = reinterpret_cast<T*>(wbase);
-  float* fl = reinterpret_cast<float*>(wbase + (size_t)slots * stack_entries(K) * sizeof(T));
+  WarpMem<TC, TL> m(smem, N, K, slots, warp);
   WarpTeam tm;
-  Walker<T, WarpTeam> W(tm, P, N, K, slots, st, fl);
+  Walker<TC, TL, WarpTeam> W(tm, P, N, K, slots, m.sc, m.sl, m.fl);
   for (int i = blockIdx.x * warps + warp; i < count; i += gridDim.x * warps) {
-    T ad = 0;
+    TL ad = 0;
     const int s = W.classify(subsets + (size_t)i * (K + 1), ad);
     if (lane == 0) {
       status[i] = s;
@@ -128,40 +148,52 @@ __global__ void k_classify(const int64_t* pts, const int64_t* lifts, int N, int 
   }
 }
 
-template <class T>
+template <class TC, class TL>
 cudaError_t configure(int smem) {
-  cudaError_t e = cudaFuncSetAttribute(k_enumerate<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaError_t e = cudaFuncSetAttribute(k_enumerate<TC, TL>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_classify<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  return cudaFuncSetAttribute(k_classify<TC, TL>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+
+cudaError_t configure_path(int path, int smem) {
+  if (path == PATH_NARROW) return configure<int32_t, int64_t>(smem);
+  if (path == PATH_MID) return configure<int64_t, int64_t>(smem);
+  return configure<i128, i128>(smem);
 }
 
 }  // namespace
 
-size_t enum_smem_bytes(int N, int K, int warps, bool wide) {
+size_t enum_smem_bytes(int N, int K, int warps, int path) {
   const size_t pts = align16((size_t)(K + 1) * N * sizeof(int64_t));
-  const size_t per_warp = wide ? warp_bytes<i128>(round32(N), K) : warp_bytes<int64_t>(round32(N), K);
+  const int slots = round32(N);
+  const size_t per_warp = path == PATH_NARROW ? warp_bytes<int32_t, int64_t>(slots, K)
+                          : path == PATH_MID  ? warp_bytes<int64_t, int64_t>(slots, K)
+                                              : warp_bytes<i128, i128>(slots, K);
   return pts + per_warp * warps;
 }
 
-LaunchShape enum_shape(int N, int K, bool wide, int warps_req, int blocks_per_sm_req, int sms,
-                       cudaError_t* err) {
+LaunchShape enum_shape(int N, int K, int path, int warps_req, int blocks_per_sm_req, int sms, cudaError_t* err) {
   LaunchShape s;
   *err = cudaSuccess;
   int dev = 0, max_optin = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   int warps = warps_req > 0 ? warps_req : 4;
-  while (warps > 1 && enum_smem_bytes(N, K, warps, wide) > (size_t)max_optin) warps /= 2;
+  while (warps > 1 && enum_smem_bytes(N, K, warps, path) > (size_t)max_optin) warps /= 2;
   s.warps = warps;
-  s.smem = enum_smem_bytes(N, K, warps, wide);
+  s.smem = enum_smem_bytes(N, K, warps, path);
   s.slots = round32(N);
   if (s.smem > (size_t)max_optin) { *err = cudaErrorInvalidConfiguration; return s; }
-  cudaError_t e = wide ? configure<i128>((int)s.smem) : configure<int64_t>((int)s.smem);
+  cudaError_t e = configure_path(path, (int)s.smem);
   if (e != cudaSuccess) { *err = e; return s; }
   int per_sm = blocks_per_sm_req;
   if (per_sm <= 0) {
-    e = wide ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_enumerate<i128>, warps * 32, s.smem)
-             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_enumerate<int64_t>, warps * 32, s.smem);
+    if (path == PATH_NARROW)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_enumerate<int32_t, int64_t>, warps * 32, s.smem);
+    else if (path == PATH_MID)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_enumerate<int64_t, int64_t>, warps * 32, s.smem);
+    else
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_enumerate<i128, i128>, warps * 32, s.smem);
     if (e != cudaSuccess) { *err = e; return s; }
     if (per_sm < 1) per_sm = 1;
   }
@@ -169,23 +201,28 @@ LaunchShape enum_shape(int N, int K, bool wide, int warps_req, int blocks_per_sm
   return s;
 }
 
-cudaError_t launch_enumerate(const EnumParams& p, const LaunchShape& s, bool wide, cudaStream_t st) {
-  if (wide) k_enumerate<i128><<<s.blocks, s.warps * 32, s.smem, st>>>(p);
-  else k_enumerate<int64_t><<<s.blocks, s.warps * 32, s.smem, st>>>(p);
+cudaError_t launch_enumerate(const EnumParams& p, const LaunchShape& s, int path, cudaStream_t st) {
+  if (path == PATH_NARROW) k_enumerate<int32_t, int64_t><<<s.blocks, s.warps * 32, s.smem, st>>>(p);
+  else if (path == PATH_MID) k_enumerate<int64_t, int64_t><<<s.blocks, s.warps * 32, s.smem, st>>>(p);
+  else k_enumerate<i128, i128><<<s.blocks, s.warps * 32, s.smem, st>>>(p);
   return cudaGetLastError();
 }
 
 cudaError_t launch_classify(const int64_t* pts, const int64_t* lifts, int N, int K, const uint8_t* subsets,
-                            int count, int32_t* status, int64_t* absdet, bool wide, cudaStream_t st) {
+                            int count, int32_t* status, int64_t* absdet, int path, cudaStream_t st) {
   const int warps = 4;
-  const size_t smem = enum_smem_bytes(N, K, warps, wide);
-  cudaError_t e = wide ? configure<i128>((int)smem) : configure<int64_t>((int)smem);
+  const size_t smem = enum_smem_bytes(N, K, warps, path);
+  cudaError_t e = configure_path(path, (int)smem);
   if (e != cudaSuccess) return e;
   int blocks = (count + warps - 1) / warps;
   if (blocks > 4096) blocks = 4096;
   if (blocks < 1) blocks = 1;
-  if (wide) k_classify<i128><<<blocks, warps * 32, smem, st>>>(pts, lifts, N, K, subsets, count, status, absdet);
-  else k_classify<int64_t><<<blocks, warps * 32, smem, st>>>(pts, lifts, N, K, subsets, count, status, absdet);
+  if (path == PATH_NARROW)
+    k_classify<int32_t, int64_t><<<blocks, warps * 32, smem, st>>>(pts, lifts, N, K, subsets, count, status, absdet);
+  else if (path == PATH_MID)
+    k_classify<int64_t, int64_t><<<blocks, warps * 32, smem, st>>>(pts, lifts, N, K, subsets, count, status, absdet);
+  else
+    k_classify<i128, i128><<<blocks, warps * 32, smem, st>>>(pts, lifts, N, K, subsets, count, status, absdet);
   return cudaGetLastError();
 }
 

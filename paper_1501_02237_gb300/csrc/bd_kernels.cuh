@@ -32,14 +32,16 @@ struct LaunchShape {
   int slots = 0;         // points per warp stack (multiple of 32)
 };
 
+// Integer paths: coordinate minors / lift minors in (int32, int64), (int64, int64), (int128, int128)
+enum { PATH_NARROW = 0, PATH_MID = 1, PATH_WIDE = 2 };
+
 // Shared memory of one block: lifted points + one stack per warp.
-size_t enum_smem_bytes(int N, int K, int warps, bool wide);
-LaunchShape enum_shape(int N, int K, bool wide, int warps_req, int blocks_per_sm_req, int sms,
-                       cudaError_t* err);
-cudaError_t launch_enumerate(const EnumParams& p, const LaunchShape& s, bool wide, cudaStream_t st);
+size_t enum_smem_bytes(int N, int K, int warps, int path);
+LaunchShape enum_shape(int N, int K, int path, int warps_req, int blocks_per_sm_req, int sms, cudaError_t* err);
+cudaError_t launch_enumerate(const EnumParams& p, const LaunchShape& s, int path, cudaStream_t st);
 
 // One warp per given subset: status (0 singular, 1 rejected, 2 accepted, 3 tie) and |D0|.
 cudaError_t launch_classify(const int64_t* pts, const int64_t* lifts, int N, int K, const uint8_t* subsets,
-                            int count, int32_t* status, int64_t* absdet, bool wide, cudaStream_t st);
+                            int count, int32_t* status, int64_t* absdet, int path, cudaStream_t st);
 
 }  // namespace bd

@@ -133,6 +133,16 @@ def test_int128_path_forced_equals_int64():
 
 
 @pytest.mark.parametrize("seed", range(6))
+def test_int64_path_medium_coordinates(seed):
+    # |x| ~ 2^10 in k = 3: coordinate minors beyond 32 bits, lifted minors within 64
+    rng = random.Random(70 + seed)
+    pts = [tuple(rng.randint(-1024, 1024) for _ in range(3)) for _ in range(12)]
+    p = bd.Plan(np.array(pts))
+    assert p.info()["path"] == "int64"
+    assert p.volume(seed=seed)["nvol"] == nvol_placing(pts)
+
+
+@pytest.mark.parametrize("seed", range(6))
 def test_int128_path_large_coordinates(seed):
     # coordinates near 2^22 push the Hadamard bound past 2^63: the 128-bit path must be taken
     rng = random.Random(seed)

@@ -152,3 +152,19 @@ def test_reduce_batch_volume_equals_oracle(idx):
     s = batch_systems(idx + 1)[idx]
     P = bd.reduce(s.A)["points"]
     assert nvol_placing([tuple(p) for p in P]) == GOLD["batch_first_256"][idx]["nvol"]
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_host_walker_all_integer_paths(seed):
+    # small coordinates: int32 coordinate minors; |x| ~ 2^10 in k = 3: int64 minors;
+    # forced: int128 minors.  All three must give the oracle's volume.
+    rng = random.Random(300 + seed)
+    k = 3
+    for span, force in [(3, False), (1 << 10, False), (3, True), (1 << 10, True)]:
+        pts = [tuple(rng.randint(-span, span) for _ in range(k)) for _ in range(rng.randint(5, 11))]
+        lf = oracle_lifts(len(pts), seed)
+        r = bd.host_volume_lifted(np.array(pts), np.array(lf), force_int128=force)
+        assert r["status"] == 0
+        assert r["nvol"] == nvol_placing(pts)
+        if force:
+            assert r["flags"] & bd.BD_FLAG_INT128
