@@ -271,6 +271,12 @@ template <class T> BD_HD T tabs(T x) { return x < 0 ? -x : x; }
 // ---------------------------------------------------------------------------------------------
 enum { ST_SINGULAR = 0, ST_REJECTED = 1, ST_ACCEPTED = 2, ST_TIE = 3 };
 
+// wider exact type for a 2x2 determinant of coordinate minors
+template <class TC> struct Wide2;
+template <> struct Wide2<int32_t> { typedef int64_t type; };
+template <> struct Wide2<int64_t> { typedef i128 type; };
+template <> struct Wide2<i128> { typedef i128 type; };  // unused: the 128-bit path tests in 2-D
+
 template <class TC, class TL, class Team>
 struct Walker {
   typedef typename DivOf<TC>::type Div;
@@ -279,16 +285,23 @@ struct Walker {
   int N, K, SLOTS;
   TC* sc;           // coordinate minors: (level j, entry e, point q) at sc[(off_j + e) * SLOTS + q]
   TL* sl;           // lift minor of level j for point q at sl[j * SLOTS + q]
-  float* fl;        // single-precision copies of the level K-1 minors: C at fl[q], L at fl[SLOTS + q]
+  float* fl;        // single-precision copies for the filters: 3 rows of SLOTS floats
   int s[KMAX + 1];  // chosen indices s_0 .. s_j
   Div dv[KMAX];     // exact divider by the pivot of each level (dv[0]: by 1)
-  int psign;        // sign of the level K-1 pivot p_{K-1}
+  TC piv[KMAX];     // the pivots p_j (piv[0] = 1)
+  int psign;        // sign of the level K-1 pivot p_{K-1} (2-D test)
 #ifdef BD_COUNT
   Acc* cnt = nullptr;
 #endif
 
   BD_HD Walker(Team& t, const int64_t* P_, int N_, int K_, int SLOTS_, TC* sc_, TL* sl_, float* fl_)
       : tm(t), P(P_), N(N_), K(K_), SLOTS(SLOTS_), sc(sc_), sl(sl_), fl(fl_) {}
+
+  // the 3-D test runs for the int32 and int64 coordinate paths; the 128-bit path and K = 1 use
+  // the 2-D test on the fully reduced state
+  static constexpr bool kUse3D = sizeof(TL) == 8;
+  // the bottom stage runs on state K-2 (both tests finish the last two levels themselves)
+  BD_HD int bottom_depth() const { return K >= 2 ? K - 1 : 1; }
 
   // state 0: lifted differences z_q = (a_q - a_{s_0}, w_q - w_{s_0})
   BD_HD void start(int s0) {
@@ -299,24 +312,15 @@ struct Walker {
       sl[q] = (TL)(P[K * N + q] - P[K * N + s0]);
     }
     dv[0] = make_div((TC)1);
+    piv[0] = 1;
     psign = 1;
     tm.sync();
   }
 
-  // the float copies of the last level (K-1) for the leaf filter
-  BD_HD void copy_floats(int j) {
-    const int o = level_offset(K, j);
-    for (int q = tm.lane(); q < N; q += tm.lanes()) {
-      fl[q] = (float)sc[o * SLOTS + q];
-      fl[SLOTS + q] = (float)sl[j * SLOTS + q];
-    }
-  }
-
-  // Bareiss step: state j from state j-1 with pivot point c (s_j = c).  Returns false when the
-  // pivot row has no nonzero coordinate minor (every extension is singular).  At the last level
-  // the coordinate minors come first; the lift minors are formed only when some candidate last
-  // point p > c has a nonzero coordinate minor (lazy: *live = 0 means nothing left to test).
-  BD_HD bool build(int j, int c, uint64_t* live = nullptr) {
+  // Bareiss step: state j (j < K-1, or j = K-1 on the 2-D path via build_last) from state j-1
+  // with pivot point c (s_j = c).  false when the pivot row has no nonzero coordinate minor
+  // (every extension is singular).
+  BD_HD bool build(int j, int c) {
     const int po = level_offset(K, j - 1), no = level_offset(K, j);
     const int ncoord = K - j + 1;  // coordinate minors of state j-1
     int pi = -1;
@@ -329,69 +333,64 @@ struct Walker {
     const TC pj = sc[(po + pi) * SLOTS + c];
     const TL rl = sl[(j - 1) * SLOTS + c];
     const Div D = dv[j - 1];
-    const bool last = (j == K - 1);
     tm.sync();  // readers of the old state j (a sibling's subtree) are done
-    uint64_t mine = 0;
     for (int q = tm.lane(); q < N; q += tm.lanes()) {
       const TC bq = sc[(po + pi) * SLOTS + q];
       for (int e = 0; e < ncoord - 1; ++e) {
         const int ep = e < pi ? e : e + 1;
-        const TC v = bareiss(sc[(po + ep) * SLOTS + q], pj, bq, sc[(po + ep) * SLOTS + c], D);
-        sc[(no + e) * SLOTS + q] = v;
-        if (last && v != 0 && q > c) mine |= 1ull << q;
+        sc[(no + e) * SLOTS + q] = bareiss(sc[(po + ep) * SLOTS + q], pj, bq, sc[(po + ep) * SLOTS + c], D);
       }
-      if (!last) sl[j * SLOTS + q] = bareiss(sl[(j - 1) * SLOTS + q], pj, bq, rl, D);
+      sl[j * SLOTS + q] = bareiss(sl[(j - 1) * SLOTS + q], pj, bq, rl, D);
     }
     s[j] = c;
-    if (!last) {
-      dv[j] = make_div(pj);
-      tm.sync();
-      return true;
-    }
-    psign = pj < 0 ? -1 : 1;  // the leaf test needs only the sign of p_{K-1}
-    const uint64_t cand = tm.or_all(mine);
-    *live = cand;
-    if (cand) {
-      for (int q = tm.lane(); q < N; q += tm.lanes()) {
-        const TC bq = sc[(po + pi) * SLOTS + q];
-        const TL v = bareiss(sl[(j - 1) * SLOTS + q], pj, bq, rl, D);
-        sl[j * SLOTS + q] = v;
-        fl[q] = (float)sc[no * SLOTS + q];
-        fl[SLOTS + q] = (float)v;
-      }
-    }
+    piv[j] = pj;
+    dv[j] = make_div(pj);
     tm.sync();
     return true;
   }
 
-  // level 0 is the last level when K = 1
-  BD_HD uint64_t finish_level0() {
+  BD_HD uint64_t member_mask(int upto) const {
+    uint64_t mask = 0;
+    for (int i = 0; i < upto; ++i) mask |= 1ull << s[i];
+    return mask;
+  }
+
+  // ---------------------------------------------------------------------------------------
+  // 2-D test on the fully reduced state K-1: each point q carries (C_q, L_q); for the last
+  // point p, s(q) = sigma (C_p L_q - C_q L_p) / p_{K-1} and D0 = sigma C_p.
+  // ---------------------------------------------------------------------------------------
+  BD_HD uint64_t build_last(int c) {  // state K-1 with pivot c; returns the candidate mask
+    if (K == 1) {
+      uint64_t mine = 0;
+      for (int q = tm.lane(); q < N; q += tm.lanes()) {
+        if (q > s[0] && sc[q] != 0) mine |= 1ull << q;
+        fl[q] = (float)sc[q];
+        fl[SLOTS + q] = (float)sl[q];
+      }
+      const uint64_t cand = tm.or_all(mine);
+      tm.sync();
+      return cand;
+    }
+    if (!build(K - 1, c)) return 0;
+    psign = piv[K - 1] < 0 ? -1 : 1;
+    const int o = level_offset(K, K - 1);
     uint64_t mine = 0;
-    for (int q = tm.lane(); q < N; q += tm.lanes())
-      if (q > s[0] && sc[q] != 0) mine |= 1ull << q;
-    copy_floats(0);
+    for (int q = tm.lane(); q < N; q += tm.lanes()) {
+      const TC v = sc[o * SLOTS + q];
+      if (v != 0 && q > c) mine |= 1ull << q;
+      fl[q] = (float)v;
+      fl[SLOTS + q] = (float)sl[(K - 1) * SLOTS + q];
+    }
     const uint64_t cand = tm.or_all(mine);
     tm.sync();
     return cand;
   }
 
-  BD_HD uint64_t member_mask() const {
-    uint64_t mask = 0;
-    for (int i = 0; i < K; ++i) mask |= 1ull << s[i];
-    return mask;
-  }
-
-  // status of the cell {s_0 .. s_{K-1}, p} (its coordinate minor C_p is nonzero); |D0| in
-  // absdet.  s(q) = sigma (C_p L_q - C_q L_p) / p_{K-1} and D0 = sigma C_p, so q lies strictly
-  // below the lifted hyperplane iff sign(C_p) sign(p_{K-1}) (C_p L_q - C_q L_p) < 0.
-  BD_HD int leaf(int p, uint64_t mask, TL& absdet) {
+  BD_HD int leaf2(int p, uint64_t mask, TL& absdet) {
     const int lo = level_offset(K, K - 1);
     const TL Cp = (TL)sc[lo * SLOTS + p];
     const TL Lp = sl[(K - 1) * SLOTS + p];
     absdet = tabs(Cp);
-#ifdef BD_COUNT
-    if (cnt) cnt->leaves++;
-#endif
     if (Cp == 0) return ST_SINGULAR;
     const float Cpf = fl[p], Lpf = fl[SLOTS + p];
     const int sig = (Cp < 0 ? -1 : 1) * psign;
@@ -399,12 +398,7 @@ struct Walker {
     for (int q = tm.lane(); q < N; q += tm.lanes()) {
       if (((mask >> q) & 1ull) || q == p) continue;
       int sg = sizeof(TL) == 8 ? cross_sign_filtered(Cpf, fl[SLOTS + q], fl[q], Lpf) : 2;
-      if (sg == 2) {
-#ifdef BD_COUNT
-        if (cnt) cnt->exact_fallbacks++;
-#endif
-        sg = cross_sign(Cp, sl[(K - 1) * SLOTS + q], (TL)sc[lo * SLOTS + q], Lp);
-      }
+      if (sg == 2) sg = cross_sign(Cp, sl[(K - 1) * SLOTS + q], (TL)sc[lo * SLOTS + q], Lp);
       if (sg == 0) on = true;
       else if (sg != sig) below = true;
     }
@@ -412,26 +406,134 @@ struct Walker {
     return tm.any(on) ? ST_TIE : ST_ACCEPTED;
   }
 
-  BD_HD void leaves(uint64_t cand, Acc& acc) {
-    const uint64_t mask = member_mask();
+  // all cells below a state-(K-2) node on the 2-D path (every child c, then every p > c)
+  BD_HD void bottom2(Acc& acc) {
+    if (K == 1) {
+      const uint64_t cand = build_last(0);
+      acc.singular += (uint64_t)(N - 1 - s[0]) - (uint64_t)popc64(cand);
+      leaves2(cand, acc);
+      return;
+    }
+    for (int c = s[K - 2] + 1; c <= N - 2; ++c) {
+      const uint64_t cand = build_last(c);
+      acc.singular += (uint64_t)(N - 1 - c) - (uint64_t)popc64(cand);
+      if (cand) leaves2(cand, acc);
+    }
+  }
+
+  BD_HD void leaves2(uint64_t cand, Acc& acc) {
+    const uint64_t mask = member_mask(K);
     while (cand) {
       const int p = ctz64(cand);
       cand &= cand - 1;
       TL ad;
-      const int stt = leaf(p, mask, ad);
+      const int stt = leaf2(p, mask, ad);
       if (stt == ST_ACCEPTED) { acc.cells += 1; acc.nvol += (u128)ad; }
       else if (stt == ST_TIE) acc.ties += 1;
     }
   }
 
-  // every (K+1)-subset extending the prefix it.idx[0 .. it.len-1]
+  // ---------------------------------------------------------------------------------------
+  // 3-D test on state K-2.  Each point is v_q = (x_q, y_q, l_q) (two coordinate minors and the
+  // lift minor).  Eliminating one more pivot row c (Sylvester) turns the 2-D test into
+  //     C_p L_q - C_q L_p = x_c det3(v_c, v_p, v_q) / p_{K-2}^2,   C_p = det2(c, p) / p_{K-2},
+  // (for pivot column x; the y-pivot case flips both signs), so q lies strictly below the
+  // lifted cell {s_0..s_{K-2}, c, p} iff  sign(det2) sign(p_{K-2}) det3 < 0, and
+  // |D0| = |det2| / |p_{K-2}|.  det3 = v_q . (v_c x v_p) is evaluated in single precision with a
+  // rigorous error bound; undecided signs use the exact 2-D formulation for that (c, p, q).
+  // ---------------------------------------------------------------------------------------
+  typedef typename Wide2<TC>::type W2;
+
+  BD_HD void exact_pair_minors(int c, int x, TL& C, TL& L) const {
+    // level K-1 minors of point x for pivot row c (the exact route of build for one point)
+    const int o = level_offset(K, K - 2);
+    const TC xc = sc[o * SLOTS + c], yc = sc[(o + 1) * SLOTS + c];
+    const int pi = xc != 0 ? 0 : 1;
+    const TC a = pi == 0 ? xc : yc, b = pi == 0 ? yc : xc;
+    const TC ex_pi = sc[(o + pi) * SLOTS + x], ex_o = sc[(o + 1 - pi) * SLOTS + x];
+    const Div& D = dv[K - 2];
+    C = (TL)bareiss(ex_o, a, ex_pi, b, D);
+    L = bareiss(sl[(K - 2) * SLOTS + x], a, ex_pi, sl[(K - 2) * SLOTS + c], D);
+  }
+
+  BD_HD void bottom3(Acc& acc) {
+    const int o = level_offset(K, K - 2);
+    const int sd = piv[K - 2] < 0 ? -1 : 1;
+    const uint64_t prefix = member_mask(K - 1);
+    // single-precision copies of this lane's points and of every point for the uniform reads
+    for (int q = tm.lane(); q < N; q += tm.lanes()) {
+      fl[q] = (float)sc[o * SLOTS + q];
+      fl[SLOTS + q] = (float)sc[(o + 1) * SLOTS + q];
+      fl[2 * SLOTS + q] = (float)sl[(K - 2) * SLOTS + q];
+    }
+    tm.sync();
+    for (int c = s[K - 2] + 1; c <= N - 2; ++c) {
+      const TC xc = sc[o * SLOTS + c], yc = sc[(o + 1) * SLOTS + c];
+      if (xc == 0 && yc == 0) {  // no pivot: every cell through c is singular
+        acc.singular += (uint64_t)(N - 1 - c);
+        continue;
+      }
+      const float xcf = fl[c], ycf = fl[SLOTS + c], lcf = fl[2 * SLOTS + c];
+      for (int p = c + 1; p < N; ++p) {
+        const TC xp = sc[o * SLOTS + p], yp = sc[(o + 1) * SLOTS + p];
+        const W2 d2 = (W2)xc * yp - (W2)yc * xp;
+        if (d2 == 0) {
+          acc.singular += 1;
+          continue;
+        }
+        const float xpf = fl[p], ypf = fl[SLOTS + p], lpf = fl[2 * SLOTS + p];
+        // n = v_c x v_p and the magnitudes of its terms
+        const float t1 = ycf * lpf, t2 = lcf * ypf, t3 = lcf * xpf, t4 = xcf * lpf;
+        const float nx = t1 - t2, ny = t3 - t4, nz = (float)d2;
+        const float ax = fabsf(t1) + fabsf(t2), ay = fabsf(t3) + fabsf(t4), az = fabsf(nz);
+        const int sig = (d2 < 0 ? -1 : 1) * sd;  // q is below iff sig * det3 < 0
+        bool below = false, on = false;
+        for (int q = tm.lane(); q < N; q += tm.lanes()) {
+          if (((prefix >> q) & 1ull) || q == c || q == p) continue;
+          const float xq = fl[q], yq = fl[SLOTS + q], lq = fl[2 * SLOTS + q];
+          const float v = fmaf(nx, xq, fmaf(ny, yq, nz * lq));
+          // 2^-18 * sum |terms|: each term carries at most ~9 roundings of 2^-24
+          const float bound = 3.82e-6f * fmaf(ax, fabsf(xq), fmaf(ay, fabsf(yq), az * fabsf(lq)));
+          int sg;
+          if (v > bound) sg = 1;
+          else if (v < -bound) sg = -1;
+          else {  // exact: C_p L_q - C_q L_p on the reduced state, with its own sign rule
+            TL Cp, Lp, Cq, Lq;
+            exact_pair_minors(c, p, Cp, Lp);
+            exact_pair_minors(c, q, Cq, Lq);
+            const int cs = cross_sign(Cp, Lq, Cq, Lp);
+            const int pc = (xc != 0 ? xc : yc) < 0 ? -1 : 1;
+            // below iff cs != 0 and cs != sign(C_p) * sign(pivot of c)
+            sg = cs == 0 ? 0 : ((cs == ((Cp < 0 ? -1 : 1) * pc)) ? sig : -sig);
+          }
+          if (sg == 0) on = true;
+          else if (sg != sig) below = true;
+        }
+        if (tm.any(below)) continue;
+        if (tm.any(on)) {
+          acc.ties += 1;
+          continue;
+        }
+        acc.cells += 1;
+        const W2 ad = d2 < 0 ? -d2 : d2;
+        const W2 dd = piv[K - 2] < 0 ? -(W2)piv[K - 2] : (W2)piv[K - 2];
+        acc.nvol += (u128)(ad / dd);  // exact: det2 = p_{K-2} * C_p
+      }
+    }
+  }
+
+  BD_HD void bottom(Acc& acc) {
+    if (kUse3D && K >= 2) bottom3(acc);
+    else bottom2(acc);
+  }
+
+  // every (K+1)-subset extending the prefix it.idx[0 .. it.len-1] (len <= bottom depth)
   BD_HD void run_item(const Item& it, Acc& acc) {
     const int L = it.len;
+    const int B = bottom_depth();
     start(it.idx[0]);
-    uint64_t live = 0;
-    if (K == 1) live = finish_level0();
     for (int j = 1; j < L; ++j) {
-      if (!build(j, it.idx[j], &live)) {
+      if (!build(j, it.idx[j])) {
         acc.singular += subtree_size(N, K, it.idx[L - 1], L);
         return;
       }
@@ -440,11 +542,8 @@ struct Walker {
     int j = L;
     cur[j] = it.idx[L - 1];
     for (;;) {
-      if (j == K) {
-        // candidates with a zero coordinate minor are singular cells
-        const int s_last = s[K - 1];
-        acc.singular += (uint64_t)(N - 1 - s_last) - (uint64_t)popc64(live);
-        leaves(live, acc);
+      if (j == B) {
+        bottom(acc);
         if (--j < L) break;
         continue;
       }
@@ -453,7 +552,7 @@ struct Walker {
         if (--j < L) break;
         continue;
       }
-      if (!build(j, c, &live)) {
+      if (!build(j, c)) {
         acc.singular += binom(N - 1 - c, K - j);
         continue;
       }
@@ -462,15 +561,15 @@ struct Walker {
     }
   }
 
-  // status of one given subset sub[0] < .. < sub[K]
+  // status of one given subset sub[0] < .. < sub[K] (2-D route)
   BD_HD int classify(const uint8_t* sub, TL& absdet) {
     start(sub[0]);
-    uint64_t live = 0;
-    if (K == 1) live = finish_level0();
-    for (int j = 1; j < K; ++j)
-      if (!build(j, sub[j], &live)) { absdet = 0; return ST_SINGULAR; }
-    if (!((live >> sub[K]) & 1ull)) { absdet = 0; return ST_SINGULAR; }
-    return leaf(sub[K], member_mask(), absdet);
+    for (int j = 1; j < K - 1; ++j)
+      if (!build(j, sub[j])) { absdet = 0; return ST_SINGULAR; }
+    if (K >= 2) s[K - 1] = sub[K - 1];
+    const uint64_t cand = build_last(K >= 2 ? sub[K - 1] : 0);
+    if (!((cand >> sub[K]) & 1ull)) { absdet = 0; return ST_SINGULAR; }
+    return leaf2(sub[K], member_mask(K), absdet);
   }
 };
 

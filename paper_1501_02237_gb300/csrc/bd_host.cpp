@@ -503,7 +503,7 @@ std::vector<Item> build_items(int N, int K, uint64_t max_subsets) {
   pre[0] = 0;
   for (;;) {
     const uint64_t T = subtree_size(N, K, pre[len - 1], len);
-    if (T > max_subsets && len < K) {  // split: descend to the first child
+    if (T > max_subsets && len < std::max(K - 1, 1)) {  // split (items stop at the bottom stage's depth)
       pre[len] = pre[len - 1] + 1;
       ++len;
       continue;
@@ -546,7 +546,7 @@ void host_run(const int64_t* P, int N, int K, const std::vector<Item>& items, in
     HostTeam tm;
     std::vector<TC> sc((size_t)N * stack_entries(K));
     std::vector<TL> sl((size_t)N * K);
-    std::vector<float> fl((size_t)2 * N);
+    std::vector<float> fl((size_t)3 * N);
     Walker<TC, TL, HostTeam> W(tm, P, N, K, N, sc.data(), sl.data(), fl.data());
     Acc a{};
     for (;;) {

@@ -34,8 +34,8 @@ double hadamard_log2(const int64_t* pts, const int64_t* lifts, int npts, int k, 
 int choose_path(double coord_bits, double full_bits);
 
 // Prefix work list: every (k+1)-subset of {0..npts-1} lies below exactly one item; items are
-// split until each holds at most `max_subsets` subsets (or reaches length k), then sorted by
-// decreasing size.
+// split until each holds at most `max_subsets` subsets (or reaches length max(k-1, 1), the
+// depth of the walker's bottom stage), then sorted by decreasing size.
 std::vector<Item> build_items(int npts, int k, uint64_t max_subsets);
 
 // Host emulation of the warp enumeration on `threads` CPU threads, for an integer path.

@@ -50,12 +50,12 @@ struct WarpTeam {
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 __host__ __device__ inline int round32(int x) { return (x + 31) & ~31; }
 
-// one warp's shared memory: its coordinate-minor stack, lift-minor stack and the two float rows
-// of the last level, each 16-byte aligned
+// one warp's shared memory: its coordinate-minor stack, lift-minor stack and three float rows
+// for the single-precision filters, each 16-byte aligned
 template <class TC, class TL>
 __host__ __device__ inline size_t warp_bytes(int slots, int K) {
   return align16((size_t)slots * stack_entries(K) * sizeof(TC)) + align16((size_t)slots * K * sizeof(TL)) +
-         align16((size_t)2 * slots * sizeof(float));
+         align16((size_t)3 * slots * sizeof(float));
 }
 
 template <class TC, class TL>
