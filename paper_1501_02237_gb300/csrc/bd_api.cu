@@ -3,8 +3,12 @@
 
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
 #include <new>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/binodeg.h"
@@ -63,19 +67,75 @@ void set_u128(uint64_t& lo, uint64_t& hi, u128 v) {
   hi = (uint64_t)(v >> 64);
 }
 
+// Work lists depend only on (N, K, split size): built once per process and device, kept on the
+// device and shared by every plan that needs them.
+struct ItemList {
+  std::vector<bd::Item> host;
+  bd::Item* dev = nullptr;
+};
+std::mutex g_cache_mu;
+std::map<std::tuple<int, int, int64_t, int>, std::shared_ptr<ItemList>> g_items;
+std::map<std::tuple<int, int, int, int, int, int>, bd::LaunchShape> g_shapes;
+
+int current_device() {
+  int d = 0;
+  cudaGetDevice(&d);
+  return d;
+}
+
+int get_items(int N, int K, int64_t thr, std::shared_ptr<ItemList>& out) {
+  const auto key = std::make_tuple(N, K, thr, current_device());
+  std::lock_guard<std::mutex> lk(g_cache_mu);
+  auto it = g_items.find(key);
+  if (it != g_items.end()) {
+    out = it->second;
+    return BD_OK;
+  }
+  auto L = std::make_shared<ItemList>();
+  L->host = bd::build_items(N, K, (uint64_t)thr);
+  const size_t bytes = sizeof(bd::Item) * std::max<size_t>(1, L->host.size());
+  cudaError_t e = cudaMalloc(&L->dev, bytes);
+  if (e == cudaSuccess && !L->host.empty())
+    e = cudaMemcpy(L->dev, L->host.data(), sizeof(bd::Item) * L->host.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "work list upload");
+  g_items[key] = L;
+  out = L;
+  return BD_OK;
+}
+
+int get_shape(int N, int K, int path, int warps_req, int bps_req, bd::LaunchShape& out) {
+  const auto key = std::make_tuple(N, K, path, warps_req, bps_req, current_device());
+  std::lock_guard<std::mutex> lk(g_cache_mu);
+  auto it = g_shapes.find(key);
+  if (it != g_shapes.end()) {
+    out = it->second;
+    return BD_OK;
+  }
+  cudaError_t e;
+  out = bd::enum_shape(N, K, path, warps_req, bps_req, sm_count(), &e);
+  if (e != cudaSuccess) return cuda_fail(e, "launch shape");
+  g_shapes[key] = out;
+  return BD_OK;
+}
+
 }  // namespace
 
+// A plan owns small fixed-size device buffers (points of up to BD_NMAX x BD_KMAX coordinates,
+// lifts, accumulators) and pinned host staging; it can be re-targeted at another point set
+// without allocating, which is what the synchronous calls do through one plan per thread.
 struct bd_plan {
   int N = 0, K = 0;
   int path = 0;  // bd::PATH_NARROW / MID / WIDE
   double bound = 0;
   int64_t max_abs = 0;
-  std::vector<bd::Item> items;
-  int64_t* d_pts = nullptr;
-  int64_t* d_lifts = nullptr;  // explicit lifts (optional)
-  bd::Item* d_items = nullptr;
+  bool explicit_lifts = false;
+  int device = -1;
+  std::shared_ptr<ItemList> items;
+  int64_t* d_pts = nullptr;          // BD_NMAX * BD_KMAX
+  int64_t* d_lifts = nullptr;        // BD_NMAX
   unsigned char* d_state = nullptr;  // [DevAcc][counter]
   bd::DevAcc* h_acc = nullptr;       // pinned
+  int64_t* h_stage = nullptr;        // pinned: points then lifts
   bd::LaunchShape shape;
   cudaStream_t stream = nullptr;
   bool launched = false;
@@ -85,35 +145,67 @@ struct bd_plan {
 namespace {
 
 size_t state_bytes() { return sizeof(bd::DevAcc) + 16; }
+constexpr size_t STAGE_WORDS = (size_t)BD_NMAX * BD_KMAX + BD_NMAX;
+
+void plan_release(bd_plan* p) {
+  cudaFree(p->d_pts);
+  cudaFree(p->d_lifts);
+  cudaFree(p->d_state);
+  cudaFreeHost(p->h_acc);
+  cudaFreeHost(p->h_stage);
+  p->d_pts = p->d_lifts = nullptr;
+  p->d_state = nullptr;
+  p->h_acc = nullptr;
+  p->h_stage = nullptr;
+  p->device = -1;
+}
 
 void plan_free(bd_plan* p) {
   if (!p) return;
-  cudaFree(p->d_pts);
-  cudaFree(p->d_lifts);
-  cudaFree(p->d_items);
-  cudaFree(p->d_state);
-  cudaFreeHost(p->h_acc);
+  plan_release(p);
   delete p;
 }
 
-int plan_make(const int64_t* points, const int64_t* lifts, int32_t npts, int32_t k, const bd_plan_opts* opts,
-              bd_plan** out) {
+int plan_alloc(bd_plan* p) {
+  const int dev = current_device();
+  if (p->device == dev) return BD_OK;
+  if (p->device >= 0) plan_release(p);
+  cudaError_t e = cudaMalloc(&p->d_pts, sizeof(int64_t) * BD_NMAX * BD_KMAX);
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_lifts, sizeof(int64_t) * BD_NMAX);
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_state, state_bytes());
+  if (e == cudaSuccess) e = cudaMallocHost(&p->h_acc, sizeof(bd::DevAcc));
+  if (e == cudaSuccess) e = cudaMallocHost(&p->h_stage, sizeof(int64_t) * STAGE_WORDS);
+  if (e != cudaSuccess) {
+    plan_release(p);
+    return e == cudaErrorMemoryAllocation ? fail(BD_ERR_NOMEM, "plan buffers") : cuda_fail(e, "plan buffers");
+  }
+  p->device = dev;
+  return BD_OK;
+}
+
+// point the plan at a point set: bound, integer path, launch shape, work list, and the
+// asynchronous upload of points (and explicit lifts) on stream st
+int plan_prepare(bd_plan* p, const int64_t* points, const int64_t* lifts, int32_t npts, int32_t k,
+                 const bd_plan_opts* opts, cudaStream_t st) {
   int rc = check_points(points, npts, k);
   if (rc) return rc;
   if (npts < k + 1) return fail(BD_ERR_ARG, "a plan needs at least k+1 points");
-  bd_plan* p = new (std::nothrow) bd_plan();
-  if (!p) return fail(BD_ERR_NOMEM, "host allocation");
+  rc = plan_alloc(p);
+  if (rc) return rc;
+  if (p->launched) {  // the staging buffer may still feed the previous launch
+    cudaError_t e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    p->launched = false;
+  }
   p->N = npts;
   p->K = k;
+  p->max_abs = 0;
   for (int64_t i = 0; i < (int64_t)npts * k; ++i) p->max_abs = std::max<int64_t>(p->max_abs, std::llabs(points[i]));
   int64_t spread = (1 << 20) - 1;
   if (lifts) {
     int64_t lo = lifts[0], hi = lifts[0];
     for (int i = 0; i < npts; ++i) {
-      if (lifts[i] >= ((int64_t)1 << 40) || lifts[i] <= -((int64_t)1 << 40)) {
-        delete p;
-        return fail(BD_ERR_ARG, "|lift| must be below 2^40");
-      }
+      if (lifts[i] >= ((int64_t)1 << 40) || lifts[i] <= -((int64_t)1 << 40)) return fail(BD_ERR_ARG, "|lift| must be below 2^40");
       lo = std::min(lo, lifts[i]);
       hi = std::max(hi, lifts[i]);
     }
@@ -122,19 +214,10 @@ int plan_make(const int64_t* points, const int64_t* lifts, int32_t npts, int32_t
   double coord_bits = 0;
   p->bound = bd::hadamard_log2(points, lifts, npts, k, spread, &coord_bits);
   p->path = bd::choose_path(coord_bits, p->bound);
-  if (p->path < 0) {
-    delete p;
-    return fail(BD_ERR_OVERFLOW, "Hadamard bound of the lifted minors exceeds 2^127");
-  }
+  if (p->path < 0) return fail(BD_ERR_OVERFLOW, "Hadamard bound of the lifted minors exceeds 2^127");
   if (opts && opts->force_int128) p->path = bd::PATH_WIDE;
-  const int sms = sm_count();
-  cudaError_t e;
-  p->shape = bd::enum_shape(npts, k, p->path, opts ? opts->warps_per_block : 0, opts ? opts->blocks_per_sm : 0,
-                            sms, &e);
-  if (e != cudaSuccess) {
-    delete p;
-    return cuda_fail(e, "launch shape");
-  }
+  rc = get_shape(npts, k, p->path, opts ? opts->warps_per_block : 0, opts ? opts->blocks_per_sm : 0, p->shape);
+  if (rc) return rc;
   const uint64_t total = bd::binom(npts, k + 1);
   int64_t thr = opts && opts->item_subsets > 0 ? opts->item_subsets : 0;
   if (!thr) {
@@ -143,40 +226,60 @@ int plan_make(const int64_t* points, const int64_t* lifts, int32_t npts, int32_t
     thr = std::max<int64_t>(thr, 256);
     thr = std::min<int64_t>(thr, (int64_t)1 << 22);
   }
-  p->items = bd::build_items(npts, k, (uint64_t)thr);
-  std::vector<int64_t> P(points, points + (size_t)npts * k);
-#define PLAN_CUDA(call)                  \
-  do {                                   \
-    cudaError_t e_ = (call);             \
-    if (e_ != cudaSuccess) {             \
-      plan_free(p);                      \
-      return cuda_fail(e_, #call);       \
-    }                                    \
-  } while (0)
-  PLAN_CUDA(cudaMalloc(&p->d_pts, sizeof(int64_t) * P.size()));
-  PLAN_CUDA(cudaMemcpy(p->d_pts, P.data(), sizeof(int64_t) * P.size(), cudaMemcpyHostToDevice));
-  if (lifts) {
-    PLAN_CUDA(cudaMalloc(&p->d_lifts, sizeof(int64_t) * npts));
-    PLAN_CUDA(cudaMemcpy(p->d_lifts, lifts, sizeof(int64_t) * npts, cudaMemcpyHostToDevice));
+  rc = get_items(npts, k, thr, p->items);
+  if (rc) return rc;
+  std::memcpy(p->h_stage, points, sizeof(int64_t) * npts * k);
+  cudaError_t e = cudaMemcpyAsync(p->d_pts, p->h_stage, sizeof(int64_t) * npts * k, cudaMemcpyHostToDevice, st);
+  p->explicit_lifts = lifts != nullptr;
+  if (e == cudaSuccess && lifts) {
+    std::memcpy(p->h_stage + (size_t)BD_NMAX * BD_KMAX, lifts, sizeof(int64_t) * npts);
+    e = cudaMemcpyAsync(p->d_lifts, p->h_stage + (size_t)BD_NMAX * BD_KMAX, sizeof(int64_t) * npts,
+                        cudaMemcpyHostToDevice, st);
   }
-  PLAN_CUDA(cudaMalloc(&p->d_items, sizeof(bd::Item) * std::max<size_t>(1, p->items.size())));
-  if (!p->items.empty())
-    PLAN_CUDA(cudaMemcpy(p->d_items, p->items.data(), sizeof(bd::Item) * p->items.size(), cudaMemcpyHostToDevice));
-  PLAN_CUDA(cudaMalloc(&p->d_state, state_bytes()));
-  PLAN_CUDA(cudaMallocHost(&p->h_acc, sizeof(bd::DevAcc)));
-#undef PLAN_CUDA
+  if (e != cudaSuccess) return cuda_fail(e, "point upload");
+  p->stream = st;
+  return BD_OK;
+}
+
+int plan_make(const int64_t* points, const int64_t* lifts, int32_t npts, int32_t k, const bd_plan_opts* opts,
+              bd_plan** out) {
+  bd_plan* p = new (std::nothrow) bd_plan();
+  if (!p) return fail(BD_ERR_NOMEM, "host allocation");
+  int rc = plan_prepare(p, points, lifts, npts, k, opts, g_stream);
+  if (rc) {
+    plan_free(p);
+    return rc;
+  }
+  cudaError_t e = cudaStreamSynchronize(g_stream);  // the plan owns its inputs from here on
+  if (e != cudaSuccess) {
+    plan_free(p);
+    return cuda_fail(e, "cudaStreamSynchronize");
+  }
   *out = p;
   return BD_OK;
+}
+
+// the calling thread's plan for the synchronous calls
+bd_plan* thread_plan() {
+  struct Holder {
+    bd_plan* p = nullptr;
+    ~Holder() {
+      if (p) plan_free(p);
+    }
+  };
+  thread_local Holder h;
+  if (!h.p) h.p = new (std::nothrow) bd_plan();
+  return h.p;
 }
 
 int plan_launch(bd_plan* p, uint64_t seed, int attempt, cudaStream_t st) {
   BD_CUDA(cudaMemsetAsync(p->d_state, 0, state_bytes(), st));
   bd::EnumParams ep{};
   ep.pts = p->d_pts;
-  ep.lifts = p->d_lifts;
+  ep.lifts = p->explicit_lifts ? p->d_lifts : nullptr;
   ep.lift_seed = bd::lift_stream_seed(seed, (uint32_t)attempt);
-  ep.items = p->d_items;
-  ep.nitems = (int)p->items.size();
+  ep.items = p->items->dev;
+  ep.nitems = (int)p->items->host.size();
   ep.N = p->N;
   ep.K = p->K;
   ep.acc = reinterpret_cast<bd::DevAcc*>(p->d_state);
@@ -204,12 +307,12 @@ int plan_read(bd_plan* p, bd_volume_out* out) {
   out->flags = (p->path == bd::PATH_WIDE ? BD_FLAG_INT128 : 0) | ((a.nvol_lo | a.nvol_hi) == 0 ? BD_FLAG_DEGENERATE : 0);
   out->max_abs_coord = (int32_t)std::min<int64_t>(p->max_abs, INT32_MAX);
   out->bound_bits = (int32_t)std::ceil(p->bound);
-  if (a.items_done != p->items.size()) return fail(BD_ERR_CUDA, "enumeration did not process every work item");
+  if (a.items_done != p->items->host.size()) return fail(BD_ERR_CUDA, "enumeration did not process every work item");
   return BD_OK;
 }
 
 int plan_volume(bd_plan* p, uint64_t seed, cudaStream_t st, bd_volume_out* out) {
-  const int tries = p->d_lifts ? 1 : MAX_LIFTINGS;
+  const int tries = p->explicit_lifts ? 1 : MAX_LIFTINGS;
   for (int attempt = 0; attempt < tries; ++attempt) {
     int rc = plan_launch(p, seed, attempt, st);
     if (rc) return rc;
@@ -217,7 +320,7 @@ int plan_volume(bd_plan* p, uint64_t seed, cudaStream_t st, bd_volume_out* out) 
     if (rc) return rc;
     if (out->ties == 0) return BD_OK;
   }
-  return fail(BD_ERR_TIES, p->d_lifts ? "the given lifting has ties" : "every allowed lifting had ties");
+  return fail(BD_ERR_TIES, p->explicit_lifts ? "the given lifting has ties" : "every allowed lifting had ties");
 }
 
 void degenerate_volume(int32_t npts, int32_t k, const int64_t* points, bd_volume_out* out) {
@@ -262,7 +365,7 @@ int bd_plan_volume(bd_plan* plan, uint64_t seed, bd_volume_out* out) {
 
 int bd_plan_info(const bd_plan* plan, int64_t* info) {
   if (!plan || !info) return fail(BD_ERR_ARG, "NULL argument");
-  info[0] = (int64_t)plan->items.size();
+  info[0] = (int64_t)plan->items->host.size();
   info[1] = plan->shape.blocks;
   info[2] = plan->shape.warps;
   info[3] = (int64_t)plan->shape.smem;
@@ -286,12 +389,11 @@ int bd_volume(const int64_t* points, int32_t npts, int32_t k, uint64_t seed, bd_
     degenerate_volume(npts, k, points, out);
     return BD_OK;
   }
-  bd_plan* p = nullptr;
-  rc = plan_make(points, nullptr, npts, k, nullptr, &p);
+  bd_plan* p = thread_plan();
+  if (!p) return fail(BD_ERR_NOMEM, "host allocation");
+  rc = plan_prepare(p, points, nullptr, npts, k, nullptr, g_stream);
   if (rc) return rc;
-  rc = plan_volume(p, seed, g_stream, out);
-  plan_free(p);
-  return rc;
+  return plan_volume(p, seed, g_stream, out);
 }
 
 int bd_volume_lifted(const int64_t* points, const int64_t* lifts, int32_t npts, int32_t k, bd_volume_out* out) {
@@ -302,12 +404,11 @@ int bd_volume_lifted(const int64_t* points, const int64_t* lifts, int32_t npts, 
     degenerate_volume(npts, k, points, out);
     return BD_OK;
   }
-  bd_plan* p = nullptr;
-  rc = plan_make(points, lifts, npts, k, nullptr, &p);
+  bd_plan* p = thread_plan();
+  if (!p) return fail(BD_ERR_NOMEM, "host allocation");
+  rc = plan_prepare(p, points, lifts, npts, k, nullptr, g_stream);
   if (rc) return rc;
-  rc = plan_volume(p, 0, g_stream, out);
-  plan_free(p);
-  return rc;
+  return plan_volume(p, 0, g_stream, out);
 }
 
 int bd_reduce(const int64_t* A, int32_t n, int32_t m, const int64_t* coef, int64_t* points, int64_t* info) {

@@ -38,8 +38,10 @@
 
 #ifdef __CUDACC__
 #define BD_HD __host__ __device__ __forceinline__
+#define BD_COLD __host__ __device__ __noinline__
 #else
 #define BD_HD inline
+#define BD_COLD __attribute__((noinline))
 #endif
 
 namespace bd {
@@ -187,6 +189,17 @@ BD_HD i128 bareiss(i128 a, i128 p, i128 b, i128 r, const Div128& D) {
   u128 q = (lo >> t) | (hi << (128 - t));
   return (i128)(q * D.inv);
 }
+
+// single-precision value of a 64-bit integer without a 64-bit conversion instruction: the
+// magnitude is split into 32-bit halves, each converted (one rounding each) and recombined by
+// one fused multiply-add, so the relative error is at most 2^-23.
+BD_HD float f32_of(int64_t x) {
+  const uint64_t a = x < 0 ? (uint64_t)0 - (uint64_t)x : (uint64_t)x;
+  const float f = fmaf((float)(uint32_t)(a >> 32), 4294967296.0f, (float)(uint32_t)a);
+  return x < 0 ? -f : f;
+}
+BD_HD float f32_of(int32_t x) { return (float)x; }
+BD_HD float f32_of(i128 x) { return (float)x; }
 
 // sign of a*b - c*d, exact (-1, 0, 1)
 BD_HD int cross_sign(int64_t a, int64_t b, int64_t c, int64_t d) {
@@ -456,17 +469,52 @@ struct Walker {
     L = bareiss(sl[(K - 2) * SLOTS + x], a, ex_pi, sl[(K - 2) * SLOTS + c], D);
   }
 
+  // the test of one lane-owned point q against the pair (c, p); 0 tie, +-1 side, computed
+  // exactly when the single-precision value is too close to zero
+  BD_HD int side3(int c, int p, int q, float nx, float ny, float nz, float ax, float ay, float az, float xq,
+                  float yq, float lq, int sig, TC xc, TC yc) const {
+    const float v = fmaf(nx, xq, fmaf(ny, yq, nz * lq));
+    // Error budget with u = 2^-24: point copies 2u (f32_of), products 5u, the components of
+    // n 6u of their magnitude sums a_*, then one more copy and three roundings: 11u in all of
+    // sum a_i |v_qi|.  The bound 2^-17 * sum (32u) leaves a factor ~3 of slack.
+    const float bound = 7.63e-6f * fmaf(ax, fabsf(xq), fmaf(ay, fabsf(yq), az * fabsf(lq)));
+    if (v > bound) return 1;
+    if (v < -bound) return -1;
+    return side3_exact(c, p, q, sig, xc, yc);
+  }
+
+  // exact: C_p L_q - C_q L_p on the reduced state, with the 2-D sign rule (rarely reached;
+  // kept out of line so that the common path keeps its registers)
+  BD_COLD int side3_exact(int c, int p, int q, int sig, TC xc, TC yc) const {
+    TL Cp, Lp, Cq, Lq;
+    exact_pair_minors(c, p, Cp, Lp);
+    exact_pair_minors(c, q, Cq, Lq);
+    const int cs = cross_sign(Cp, Lq, Cq, Lp);
+    const int pc = (xc != 0 ? xc : yc) < 0 ? -1 : 1;
+    // below iff cs != 0 and cs != sign(C_p) * sign(pivot of c); map onto sig's convention
+    return cs == 0 ? 0 : ((cs == ((Cp < 0 ? -1 : 1) * pc)) ? sig : -sig);
+  }
+
   BD_HD void bottom3(Acc& acc) {
     const int o = level_offset(K, K - 2);
     const int sd = piv[K - 2] < 0 ? -1 : 1;
     const uint64_t prefix = member_mask(K - 1);
-    // single-precision copies of this lane's points and of every point for the uniform reads
+    // single-precision copies of every point for the uniform reads, and of this lane's own
+    // points (at most two: q0 = lane, q1 = lane + 32) in registers
     for (int q = tm.lane(); q < N; q += tm.lanes()) {
-      fl[q] = (float)sc[o * SLOTS + q];
-      fl[SLOTS + q] = (float)sc[(o + 1) * SLOTS + q];
-      fl[2 * SLOTS + q] = (float)sl[(K - 2) * SLOTS + q];
+      fl[q] = f32_of(sc[o * SLOTS + q]);
+      fl[SLOTS + q] = f32_of(sc[(o + 1) * SLOTS + q]);
+      fl[2 * SLOTS + q] = f32_of(sl[(K - 2) * SLOTS + q]);
     }
     tm.sync();
+    const int q0 = tm.lane(), q1 = tm.lane() + tm.lanes();
+    const bool own0 = q0 < N && !((prefix >> q0) & 1ull);
+    const bool warp = tm.lanes() == 32;  // the host emulation runs every point in the rest loop
+    const bool own1 = warp && q1 < N && !((prefix >> q1) & 1ull);
+    const int rest = warp ? q1 + tm.lanes() : q1;
+    float x0 = 0, y0 = 0, l0 = 0, x1 = 0, y1 = 0, l1 = 0;
+    if (q0 < N) { x0 = fl[q0]; y0 = fl[SLOTS + q0]; l0 = fl[2 * SLOTS + q0]; }
+    if (warp && q1 < N) { x1 = fl[q1]; y1 = fl[SLOTS + q1]; l1 = fl[2 * SLOTS + q1]; }
     for (int c = s[K - 2] + 1; c <= N - 2; ++c) {
       const TC xc = sc[o * SLOTS + c], yc = sc[(o + 1) * SLOTS + c];
       if (xc == 0 && yc == 0) {  // no pivot: every cell through c is singular
@@ -483,31 +531,26 @@ struct Walker {
         }
         const float xpf = fl[p], ypf = fl[SLOTS + p], lpf = fl[2 * SLOTS + p];
         // n = v_c x v_p and the magnitudes of its terms
-        const float t1 = ycf * lpf, t2 = lcf * ypf, t3 = lcf * xpf, t4 = xcf * lpf;
-        const float nx = t1 - t2, ny = t3 - t4, nz = (float)d2;
-        const float ax = fabsf(t1) + fabsf(t2), ay = fabsf(t3) + fabsf(t4), az = fabsf(nz);
+        const float t1 = ycf * lpf, t2 = lcf * ypf, t3 = lcf * xpf, t4 = xcf * lpf, t5 = xcf * ypf, t6 = ycf * xpf;
+        const float nx = t1 - t2, ny = t3 - t4, nz = t5 - t6;
+        const float ax = fabsf(t1) + fabsf(t2), ay = fabsf(t3) + fabsf(t4), az = fabsf(t5) + fabsf(t6);
         const int sig = (d2 < 0 ? -1 : 1) * sd;  // q is below iff sig * det3 < 0
         bool below = false, on = false;
-        for (int q = tm.lane(); q < N; q += tm.lanes()) {
+        if (own0 && q0 != c && q0 != p) {
+          const int sg = side3(c, p, q0, nx, ny, nz, ax, ay, az, x0, y0, l0, sig, xc, yc);
+          on = sg == 0;
+          below = sg != 0 && sg != sig;
+        }
+        if (own1 && q1 != c && q1 != p) {
+          const int sg = side3(c, p, q1, nx, ny, nz, ax, ay, az, x1, y1, l1, sig, xc, yc);
+          on = on || sg == 0;
+          below = below || (sg != 0 && sg != sig);
+        }
+        for (int q = rest; q < N; q += tm.lanes()) {  // host emulation: the remaining points
           if (((prefix >> q) & 1ull) || q == c || q == p) continue;
-          const float xq = fl[q], yq = fl[SLOTS + q], lq = fl[2 * SLOTS + q];
-          const float v = fmaf(nx, xq, fmaf(ny, yq, nz * lq));
-          // 2^-18 * sum |terms|: each term carries at most ~9 roundings of 2^-24
-          const float bound = 3.82e-6f * fmaf(ax, fabsf(xq), fmaf(ay, fabsf(yq), az * fabsf(lq)));
-          int sg;
-          if (v > bound) sg = 1;
-          else if (v < -bound) sg = -1;
-          else {  // exact: C_p L_q - C_q L_p on the reduced state, with its own sign rule
-            TL Cp, Lp, Cq, Lq;
-            exact_pair_minors(c, p, Cp, Lp);
-            exact_pair_minors(c, q, Cq, Lq);
-            const int cs = cross_sign(Cp, Lq, Cq, Lp);
-            const int pc = (xc != 0 ? xc : yc) < 0 ? -1 : 1;
-            // below iff cs != 0 and cs != sign(C_p) * sign(pivot of c)
-            sg = cs == 0 ? 0 : ((cs == ((Cp < 0 ? -1 : 1) * pc)) ? sig : -sig);
-          }
-          if (sg == 0) on = true;
-          else if (sg != sig) below = true;
+          const int sg = side3(c, p, q, nx, ny, nz, ax, ay, az, fl[q], fl[SLOTS + q], fl[2 * SLOTS + q], sig, xc, yc);
+          on = on || sg == 0;
+          below = below || (sg != 0 && sg != sig);
         }
         if (tm.any(below)) continue;
         if (tm.any(on)) {
