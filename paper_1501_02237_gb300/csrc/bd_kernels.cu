@@ -155,10 +155,16 @@ cudaError_t configure(int smem) {
   return cudaFuncSetAttribute(k_classify<TC, TL>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
 }
 
-cudaError_t configure_path(int path, int smem) {
-  if (path == PATH_NARROW) return configure<int32_t, int64_t>(smem);
-  if (path == PATH_MID) return configure<int64_t, int64_t>(smem);
-  return configure<i128, i128>(smem);
+// The dynamic shared-memory ceiling of every kernel is raised once to the device's opt-in
+// maximum, so that launch shapes computed (and cached) at different times never invalidate
+// each other.
+cudaError_t configure_path(int path, int /*smem*/) {
+  int dev = 0, max_optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (path == PATH_NARROW) return configure<int32_t, int64_t>(max_optin);
+  if (path == PATH_MID) return configure<int64_t, int64_t>(max_optin);
+  return configure<i128, i128>(max_optin);
 }
 
 }  // namespace
