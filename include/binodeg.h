@@ -152,6 +152,32 @@ int bd_plan_volume(bd_plan* plan, uint64_t seed, bd_volume_out* out);
 int bd_plan_info(const bd_plan* plan, int64_t* info);
 int bd_plan_destroy(bd_plan* plan);
 
+/* ---- allocation-free variant ------------------------------------------------------------
+ *
+ * bd_volume_noalloc: the same exact volume as bd_volume (same kernel, same liftings, same
+ * result fields), for callers that cannot allocate device memory: for instance a process whose
+ * device memory is entirely reserved by another allocator, or a latency-critical loop in which
+ * cudaMalloc / cudaFree are not acceptable because they can block and synchronize the device.
+ * The paper has no counterpart: this is a deployment convenience of this library.
+ *
+ * Inputs and outputs are the caller's HOST buffers, as for bd_volume.  All device scratch (the
+ * staged points, the work list, the work counter and the accumulators) lives in one static
+ * device array of BD_NOALLOC_SCRATCH_BYTES bytes inside the library image, which every GPU that
+ * loads the library keeps until the process exits; the call itself never allocates.  The work
+ * list is capped at BD_NOALLOC_MAX_ITEMS prefixes (the split is coarsened to fit); point sets
+ * beyond BD_NMAX points or BD_KMAX dimensions are rejected with BD_ERR_ARG.
+ *
+ * The first call on each device looks up the device address of the array (a one-time set-up
+ * with that device current); make that first call before any stream capture.  Every call
+ * shares the array and the array keeps the last call's contents; the call clears what must
+ * start at zero.  Calls from this process are serialized and each one waits for its own work
+ * on the thread's stream, but two calls whose work overlapped on the GPU would race on the
+ * shared array.
+ */
+#define BD_NOALLOC_MAX_ITEMS 65536
+#define BD_NOALLOC_SCRATCH_BYTES (8192 + 16 * BD_NOALLOC_MAX_ITEMS)
+int bd_volume_noalloc(const int64_t* points, int32_t npts, int32_t k, uint64_t seed, bd_volume_out* out);
+
 /* ---- host emulation (CPU tests and the native CPU baseline; never used by the calls above) */
 
 /* Runs the same lower-facet enumeration as the GPU kernel on |threads| CPU threads, with

@@ -16,7 +16,7 @@ from ._lib import (BD_FLAG_DEGENERATE, BD_FLAG_INCONSISTENT, BD_FLAG_INT128, KMA
                    BinodegError, DegreeOut, PlanOpts, VolumeOut, check, i64, lib, ptr)
 from ._lib import I32P, U8P
 
-__all__ = ["degree", "volume", "volume_lifted", "classify", "reduce", "Plan", "set_stream",
+__all__ = ["degree", "volume", "volume_noalloc", "volume_lifted", "classify", "reduce", "Plan", "set_stream",
            "host_volume_lifted", "BinodegError", "lib"]
 
 
@@ -63,6 +63,15 @@ def volume(points, seed: int = 0) -> dict:
     npts, k = P.shape
     out = VolumeOut()
     check(lib().bd_volume(ptr(P), npts, k, C.c_uint64(seed), C.byref(out)))
+    return out.as_dict()
+
+
+def volume_noalloc(points, seed: int = 0) -> dict:
+    """bd_volume_noalloc: bd_volume without any device allocation (static scratch in the library)."""
+    P = i64(points)
+    npts, k = P.shape
+    out = VolumeOut()
+    check(lib().bd_volume_noalloc(ptr(P), npts, k, C.c_uint64(seed), C.byref(out)))
     return out.as_dict()
 
 

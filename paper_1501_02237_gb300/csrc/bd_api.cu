@@ -13,6 +13,7 @@
 
 #include "../../include/binodeg.h"
 #include "bd_host.h"
+#include "bd_internal.h"
 #include "bd_kernels.cuh"
 #include "bd_lifts.h"
 
@@ -119,6 +120,11 @@ int get_shape(int N, int K, int path, int warps_req, int bps_req, bd::LaunchShap
 }
 
 }  // namespace
+
+namespace bd {
+int set_error(int code, const char* msg) { return fail(code, msg); }
+cudaStream_t thread_stream() { return g_stream; }
+}  // namespace bd
 
 // A plan owns small fixed-size device buffers (points of up to BD_NMAX x BD_KMAX coordinates,
 // lifts, accumulators) and pinned host staging; it can be re-targeted at another point set

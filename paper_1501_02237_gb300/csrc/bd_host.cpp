@@ -495,10 +495,13 @@ int choose_path(double coord_bits, double full_bits) {
   return -1;
 }
 
-std::vector<Item> build_items(int N, int K, uint64_t max_subsets) {
-  std::vector<Item> items;
-  if (K < 1 || N < K + 1) return items;
-  std::vector<int> pre(K + 1);
+namespace {
+
+// every prefix of the split tree, depth first; emit(item) returns false to stop early
+template <class Emit>
+bool for_each_item(int N, int K, uint64_t max_subsets, Emit emit) {
+  if (K < 1 || N < K + 1) return true;
+  int pre[KMAX + 1];
   int len = 1;
   pre[0] = 0;
   for (;;) {
@@ -512,20 +515,53 @@ std::vector<Item> build_items(int N, int K, uint64_t max_subsets) {
       Item x{};
       x.len = (uint8_t)len;
       for (int i = 0; i < len; ++i) x.idx[i] = (uint8_t)pre[i];
-      items.push_back(x);
+      if (!emit(x)) return false;
     }
     // next sibling, backtracking as needed; position i admits indices up to N-1-(K-i)
     for (;;) {
       const int nxt = pre[len - 1] + 1;
       if (nxt <= N - 1 - (K - (len - 1))) { pre[len - 1] = nxt; break; }
-      if (--len == 0) break;
+      if (--len == 0) return true;
     }
-    if (len == 0) break;
   }
-  std::stable_sort(items.begin(), items.end(), [&](const Item& a, const Item& b) {
-    return subtree_size(N, K, a.idx[a.len - 1], a.len) > subtree_size(N, K, b.idx[b.len - 1], b.len);
+}
+
+// largest subtree first; ties broken by the prefix itself, so the order is a total order
+struct ItemOrder {
+  int N, K;
+  bool operator()(const Item& a, const Item& b) const {
+    const uint64_t sa = subtree_size(N, K, a.idx[a.len - 1], a.len), sb = subtree_size(N, K, b.idx[b.len - 1], b.len);
+    if (sa != sb) return sa > sb;
+    if (a.len != b.len) return a.len < b.len;
+    for (int i = 0; i < a.len; ++i)
+      if (a.idx[i] != b.idx[i]) return a.idx[i] < b.idx[i];
+    return false;
+  }
+};
+
+}  // namespace
+
+std::vector<Item> build_items(int N, int K, uint64_t max_subsets) {
+  std::vector<Item> items;
+  for_each_item(N, K, max_subsets, [&](const Item& x) {
+    items.push_back(x);
+    return true;
   });
+  std::sort(items.begin(), items.end(), ItemOrder{N, K});
   return items;
+}
+
+bool build_items_into(int N, int K, uint64_t max_subsets, Item* out, size_t cap, size_t* count) {
+  size_t n = 0;
+  const bool ok = for_each_item(N, K, max_subsets, [&](const Item& x) {
+    if (n == cap) return false;
+    out[n++] = x;
+    return true;
+  });
+  *count = n;
+  if (!ok) return false;
+  std::sort(out, out + n, ItemOrder{N, K});
+  return true;
 }
 
 namespace {

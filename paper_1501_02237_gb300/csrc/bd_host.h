@@ -38,6 +38,10 @@ int choose_path(double coord_bits, double full_bits);
 // depth of the walker's bottom stage), then sorted by decreasing size.
 std::vector<Item> build_items(int npts, int k, uint64_t max_subsets);
 
+// The same list written into a caller-owned array of `cap` items (no allocation); false when
+// it does not fit.
+bool build_items_into(int npts, int k, uint64_t max_subsets, Item* out, size_t cap, size_t* count);
+
 // Host emulation of the warp enumeration on `threads` CPU threads, for an integer path.
 void host_enumerate(int path, const int64_t* P, int N, int K, const std::vector<Item>& items, int threads, Acc& acc);
 

@@ -1,0 +1,13 @@
+// Library-internal helpers shared by the C ABI translation units (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace bd {
+
+// records the message returned by bd_last_error() on this thread and returns `code`
+int set_error(int code, const char* msg);
+// the stream chosen with bd_set_stream() on this thread
+cudaStream_t thread_stream();
+
+}  // namespace bd
