@@ -48,7 +48,12 @@ struct WarpTeam {
 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
-__host__ __device__ inline int round32(int x) { return (x + 31) & ~31; }
+// point slots of a warp stack: N rounded up to 4 (rows stay 16-byte aligned for every entry
+// type; lane l owns points l and l + 32 whatever the stride)
+__host__ __device__ inline int slots_of(int N) { return (N + 3) & ~3; }
+
+// at most 256 threads per block and at least 3 resident blocks: about 85 registers per thread
+#define BD_ENUM_BOUNDS __launch_bounds__(256, 3)
 
 // one warp's shared memory: its coordinate-minor stack, lift-minor stack and three float rows
 // for the single-precision filters, each 16-byte aligned
@@ -97,11 +102,11 @@ __device__ void flush(const Acc& a, DevAcc* g, unsigned long long items) {
 }
 
 template <class TC, class TL>
-__global__ void k_enumerate(EnumParams p) {
+__global__ void BD_ENUM_BOUNDS k_enumerate(EnumParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
   int64_t* P = reinterpret_cast<int64_t*>(smem);
   const int N = p.N, K = p.K;
-  const int slots = round32(N);
+  const int slots = slots_of(N);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   WarpMem<TC, TL> m(smem, N, K, slots, warp);
   load_points(P, p);
@@ -133,7 +138,7 @@ __global__ void k_classify(const int64_t* pts, const int64_t* lifts, int N, int 
   p.N = N;
   p.K = K;
   load_points(P, p);
-  const int slots = round32(N);
+  const int slots = slots_of(N);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, warps = blockDim.x >> 5;
   WarpMem<TC, TL> m(smem, N, K, slots, warp);
   WarpTeam tm;
@@ -171,7 +176,7 @@ cudaError_t configure_path(int path, int /*smem*/) {
 
 size_t enum_smem_bytes(int N, int K, int warps, int path) {
   const size_t pts = align16((size_t)(K + 1) * N * sizeof(int64_t));
-  const int slots = round32(N);
+  const int slots = slots_of(N);
   const size_t per_warp = path == PATH_NARROW ? warp_bytes<int32_t, int64_t>(slots, K)
                           : path == PATH_MID  ? warp_bytes<int64_t, int64_t>(slots, K)
                                               : warp_bytes<i128, i128>(slots, K);
@@ -188,7 +193,7 @@ LaunchShape enum_shape(int N, int K, int path, int warps_req, int blocks_per_sm_
   while (warps > 1 && enum_smem_bytes(N, K, warps, path) > (size_t)max_optin) warps /= 2;
   s.warps = warps;
   s.smem = enum_smem_bytes(N, K, warps, path);
-  s.slots = round32(N);
+  s.slots = slots_of(N);
   if (s.smem > (size_t)max_optin) { *err = cudaErrorInvalidConfiguration; return s; }
   cudaError_t e = configure_path(path, (int)s.smem);
   if (e != cudaSuccess) { *err = e; return s; }
