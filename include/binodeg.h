@@ -152,6 +152,66 @@ int bd_plan_volume(bd_plan* plan, uint64_t seed, bd_volume_out* out);
 int bd_plan_info(const bd_plan* plan, int64_t* info);
 int bd_plan_destroy(bd_plan* plan);
 
+/* ---- batches (many systems in one persistent launch) ----------------------------------------
+ *
+ * A batch collects systems (bd_batch_add: an exponent matrix as for bd_degree; or
+ * bd_batch_add_points: a point set as for bd_volume, dimension <= 12), reduces them on host
+ * threads (bd_batch_prepare), then bd_batch_run enumerates all of them.  In the batched mode one
+ * persistent kernel per integer path (int32/int64/int128 minors) pulls (system, prefix) work
+ * items, largest predicted cost first, from one global list; each warp reloads the points of the
+ * system it is working on.  Item sizes follow the per-system predicted cost (`cost`, e.g. from a
+ * learned model; NULL: the closed-form bound C(N,k+1) (k^3/3 + (N-k)(k+1))).  The launches can
+ * be captured in a CUDA graph and replayed; an autotuner can pick warps per block and items per
+ * warp by timing candidates on a sample of the batch.  Systems with ties are re-lifted and rerun.
+ * mode 1 instead calls bd_volume once per system (the plain form, for comparison).
+ * Results are exact and identical in every mode.  The batch owns its device buffers (freed by
+ * bd_batch_destroy).
+ */
+#define BD_FEATURES 16  /* per-system cost-model features written by bd_batch_features */
+
+typedef struct bd_batch bd_batch;
+
+typedef struct {
+  int32_t mode;            /* 0: batched persistent launches, 1: one bd_volume per system */
+  int32_t warps_per_block; /* 0: 4 (or the autotuned value) */
+  int32_t item_factor;     /* work items per resident warp; 0: 4 (or the autotuned value) */
+  int32_t use_graph;       /* 1: capture the batched launches in a CUDA graph and replay it */
+  int32_t autotune;        /* 1: choose warps_per_block and item_factor by timing candidates */
+  int32_t reserved0;
+  const float* cost;       /* NULL or one predicted cost per system (any positive unit) */
+  int32_t reserved[4];
+} bd_batch_opts;
+
+typedef struct {
+  double host_ms;          /* bd_batch_prepare wall time */
+  double gpu_ms;           /* device time of the batched launches (CUDA events) */
+  double wall_ms;          /* wall time of bd_batch_run (without autotuning) */
+  double tune_ms;          /* device time spent by the autotuner */
+  int64_t subsets;         /* (k+1)-subsets resolved per lifting, all systems */
+  int64_t items;           /* work items launched */
+  int32_t launches;        /* kernel launches (mode 1: one per system and lifting) */
+  int32_t warps_per_block, item_factor;
+  int32_t relifted;        /* systems re-lifted because of ties */
+} bd_batch_stats;
+
+int bd_batch_create(bd_batch** batch);
+int bd_batch_add(bd_batch* batch, const int64_t* A, int32_t n, int32_t m, const int64_t* coef, uint64_t seed,
+                 int32_t* index);
+int bd_batch_add_points(bd_batch* batch, const int64_t* points, int32_t npts, int32_t k, uint64_t seed,
+                        int32_t* index);
+int bd_batch_size(const bd_batch* batch, int32_t* count);
+/* Host reductions of every system on `threads` threads (0: all hardware threads). */
+int bd_batch_prepare(bd_batch* batch, int32_t threads);
+/* count x BD_FEATURES floats: N, k, log2 C(N,k+1), log2 closed-form cost, integer path, Hadamard
+ * bits (all, coordinates), log2(1 + max |coordinate|), fraction of zero and of +-1 coordinates,
+ * mean coordinate range, N - k, n, m, rank, log2 torsion.  Needs bd_batch_prepare. */
+int bd_batch_features(const bd_batch* batch, float* features);
+int bd_batch_run(bd_batch* batch, const bd_batch_opts* opts, bd_batch_stats* stats);
+/* Result of system `index` after bd_batch_run; cycles (may be NULL) receives the SM cycles its
+ * work items took in the batched mode (0 in mode 1). */
+int bd_batch_result(const bd_batch* batch, int32_t index, bd_degree_out* out, uint64_t* cycles);
+int bd_batch_destroy(bd_batch* batch);
+
 /* ---- allocation-free variant ------------------------------------------------------------
  *
  * bd_volume_noalloc: the same exact volume as bd_volume (same kernel, same liftings, same

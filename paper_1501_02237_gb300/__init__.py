@@ -12,11 +12,11 @@ from typing import Optional, Sequence
 
 import numpy as np
 
-from ._lib import (BD_FLAG_DEGENERATE, BD_FLAG_INCONSISTENT, BD_FLAG_INT128, KMAX, NMAX,  # noqa: F401
-                   BinodegError, DegreeOut, PlanOpts, VolumeOut, check, i64, lib, ptr)
-from ._lib import I32P, U8P
+from ._lib import (BD_FEATURES, BD_FLAG_DEGENERATE, BD_FLAG_INCONSISTENT, BD_FLAG_INT128, KMAX,  # noqa: F401
+                   NMAX, BatchOpts, BatchStats, BinodegError, DegreeOut, PlanOpts, VolumeOut, check, i64, lib, ptr)
+from ._lib import F32P, I32P, U8P
 
-__all__ = ["degree", "volume", "volume_noalloc", "volume_lifted", "classify", "reduce", "Plan", "set_stream",
+__all__ = ["degree", "volume", "volume_noalloc", "volume_lifted", "classify", "reduce", "Plan", "Batch", "set_stream",
            "host_volume_lifted", "BinodegError", "lib"]
 
 
@@ -151,6 +151,73 @@ class Plan:
     def close(self) -> None:
         if getattr(self, "handle", None):
             lib().bd_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """bd_batch_*: many systems reduced on host threads and enumerated in persistent launches."""
+
+    def __init__(self):
+        h = C.c_void_p()
+        check(lib().bd_batch_create(C.byref(h)))
+        self.handle = h
+        self.count = 0
+
+    def add(self, A, coef=None, seed: int = 0) -> int:
+        A = i64(A)
+        n, m = A.shape
+        c = _coef_array(coef, m)
+        idx = C.c_int32()
+        check(lib().bd_batch_add(self.handle, ptr(A), n, m, ptr(c) if c is not None else None, C.c_uint64(seed),
+                                 C.byref(idx)))
+        self.count += 1
+        return idx.value
+
+    def add_points(self, points, seed: int = 0) -> int:
+        P = i64(points)
+        npts, k = P.shape
+        idx = C.c_int32()
+        check(lib().bd_batch_add_points(self.handle, ptr(P), npts, k, C.c_uint64(seed), C.byref(idx)))
+        self.count += 1
+        return idx.value
+
+    def prepare(self, threads: int = 0) -> None:
+        check(lib().bd_batch_prepare(self.handle, threads))
+
+    def features(self) -> np.ndarray:
+        f = np.zeros((self.count, BD_FEATURES), dtype=np.float32)
+        check(lib().bd_batch_features(self.handle, f.ctypes.data_as(F32P)))
+        return f
+
+    def run(self, mode: int = 0, warps_per_block: int = 0, item_factor: int = 0, use_graph: bool = False,
+            autotune: bool = False, cost=None) -> dict:
+        self._cost = None if cost is None else np.ascontiguousarray(np.asarray(cost, dtype=np.float32))
+        o = BatchOpts(mode, warps_per_block, item_factor, int(use_graph), int(autotune), 0,
+                      self._cost.ctypes.data_as(F32P) if self._cost is not None else None)
+        st = BatchStats()
+        check(lib().bd_batch_run(self.handle, C.byref(o), C.byref(st)))
+        return st.as_dict()
+
+    def result(self, index: int) -> dict:
+        out = DegreeOut()
+        cyc = C.c_uint64()
+        check(lib().bd_batch_result(self.handle, index, C.byref(out), C.byref(cyc)))
+        d = out.as_dict()
+        d["cycles"] = int(cyc.value)
+        return d
+
+    def results(self) -> list:
+        return [self.result(i) for i in range(self.count)]
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            lib().bd_batch_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

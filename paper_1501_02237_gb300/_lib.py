@@ -59,8 +59,25 @@ class PlanOpts(C.Structure):
                 ("force_int128", C.c_int32), ("reserved", C.c_int32 * 3)]
 
 
+class BatchOpts(C.Structure):
+    _fields_ = [("mode", C.c_int32), ("warps_per_block", C.c_int32), ("item_factor", C.c_int32),
+                ("use_graph", C.c_int32), ("autotune", C.c_int32), ("reserved0", C.c_int32),
+                ("cost", C.POINTER(C.c_float)), ("reserved", C.c_int32 * 4)]
+
+
+class BatchStats(C.Structure):
+    _fields_ = [("host_ms", C.c_double), ("gpu_ms", C.c_double), ("wall_ms", C.c_double), ("tune_ms", C.c_double),
+                ("subsets", C.c_int64), ("items", C.c_int64), ("launches", C.c_int32),
+                ("warps_per_block", C.c_int32), ("item_factor", C.c_int32), ("relifted", C.c_int32)]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
+BD_FEATURES = 16
 I64P = C.POINTER(C.c_int64)
 I32P = C.POINTER(C.c_int32)
+F32P = C.POINTER(C.c_float)
 U8P = C.POINTER(C.c_uint8)
 
 # name -> (restype, argtypes); every symbol include/binodeg.h declares
@@ -80,6 +97,15 @@ SIGNATURES = {
     "bd_plan_destroy": (C.c_int, [C.c_void_p]),
     "bd_host_volume_lifted": (C.c_int, [I64P, I64P, C.c_int32, C.c_int32, C.c_int32, C.POINTER(VolumeOut)]),
     "bd_volume_noalloc": (C.c_int, [I64P, C.c_int32, C.c_int32, C.c_uint64, C.POINTER(VolumeOut)]),
+    "bd_batch_create": (C.c_int, [C.POINTER(C.c_void_p)]),
+    "bd_batch_add": (C.c_int, [C.c_void_p, I64P, C.c_int32, C.c_int32, I64P, C.c_uint64, I32P]),
+    "bd_batch_add_points": (C.c_int, [C.c_void_p, I64P, C.c_int32, C.c_int32, C.c_uint64, I32P]),
+    "bd_batch_size": (C.c_int, [C.c_void_p, I32P]),
+    "bd_batch_prepare": (C.c_int, [C.c_void_p, C.c_int32]),
+    "bd_batch_features": (C.c_int, [C.c_void_p, C.POINTER(C.c_float)]),
+    "bd_batch_run": (C.c_int, [C.c_void_p, C.POINTER(BatchOpts), C.POINTER(BatchStats)]),
+    "bd_batch_result": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(DegreeOut), C.POINTER(C.c_uint64)]),
+    "bd_batch_destroy": (C.c_int, [C.c_void_p]),
 }
 
 _lib = None

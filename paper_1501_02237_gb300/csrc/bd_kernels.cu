@@ -237,4 +237,124 @@ cudaError_t launch_classify(const int64_t* pts, const int64_t* lifts, int N, int
   return cudaGetLastError();
 }
 
+// ---- batches --------------------------------------------------------------------------------
+
+namespace {
+
+__device__ void flush_sys(const Acc& a, unsigned long long items, unsigned long long cyc, const BatchParams& p,
+                          int sys) {
+  flush(a, p.acc + sys, items);
+  if (cyc) atomicAdd(p.cycles + sys, cyc);
+  if (items) atomicAdd(p.done + sys, (unsigned int)items);
+}
+
+// Persistent: every warp takes the next (system, prefix) item; when the system changes it
+// loads that system's lifted points into its own shared-memory buffer (so warps of one block
+// may work on different systems) and flushes its accumulators for the previous one.
+template <class TC, class TL>
+__global__ void BD_ENUM_BOUNDS k_batch(BatchParams p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int slots = slots_of(p.maxN);
+  const size_t pbytes = align16((size_t)(p.maxK + 1) * p.maxN * sizeof(int64_t));
+  unsigned char* base = smem + (size_t)warp * (pbytes + warp_bytes<TC, TL>(slots, p.maxK));
+  int64_t* P = reinterpret_cast<int64_t*>(base);
+  TC* sc = reinterpret_cast<TC*>(base + pbytes);
+  TL* sl = reinterpret_cast<TL*>(base + pbytes + align16((size_t)slots * stack_entries(p.maxK) * sizeof(TC)));
+  float* fl = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(sl) + align16((size_t)slots * p.maxK * sizeof(TL)));
+  WarpTeam tm;
+  int cur = -1, N = 0, K = 0;
+  Acc acc{};
+  unsigned long long items = 0, cyc = 0;
+  for (;;) {
+    unsigned int i = 0;
+    if (lane == 0) i = atomicAdd(p.counter, 1u);
+    i = __shfl_sync(0xffffffffu, i, 0);
+    if (i >= (unsigned int)p.nitems) break;
+    const BatchItem bi = p.items[i];
+    if ((int)bi.sys != cur) {
+      if (cur >= 0 && lane == 0) flush_sys(acc, items, cyc, p, cur);
+      acc = Acc{};
+      items = cyc = 0;
+      cur = (int)bi.sys;
+      const BatchDesc d = p.desc[cur];
+      N = d.N;
+      K = d.K;
+      __syncwarp();
+      for (int t = lane; t < N * K; t += 32) {
+        const int q = t / K, c = t - q * K;
+        P[c * N + q] = p.pts[d.pts_off + t];
+      }
+      for (int q = lane; q < N; q += 32) P[K * N + q] = lift_height(d.lift_seed, q);
+      __syncwarp();
+    }
+    Item it{};
+    it.len = bi.len;
+    for (int t = 0; t < bi.len; ++t) it.idx[t] = bi.idx[t];
+    Walker<TC, TL, WarpTeam> W(tm, P, N, K, slots, sc, sl, fl);
+    const long long t0 = clock64();
+    W.run_item(it, acc);
+    cyc += (unsigned long long)(clock64() - t0);
+    ++items;
+  }
+  if (cur >= 0 && lane == 0) flush_sys(acc, items, cyc, p, cur);
+}
+
+template <class TC, class TL>
+cudaError_t configure_batch() {
+  int dev = 0, max_optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  return cudaFuncSetAttribute(k_batch<TC, TL>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_optin);
+}
+
+}  // namespace
+
+size_t batch_smem_bytes(int maxN, int maxK, int warps, int path) {
+  const int slots = slots_of(maxN);
+  const size_t pbytes = align16((size_t)(maxK + 1) * maxN * sizeof(int64_t));
+  const size_t per_warp = path == PATH_NARROW ? warp_bytes<int32_t, int64_t>(slots, maxK)
+                          : path == PATH_MID  ? warp_bytes<int64_t, int64_t>(slots, maxK)
+                                              : warp_bytes<i128, i128>(slots, maxK);
+  return (pbytes + per_warp) * warps;
+}
+
+LaunchShape batch_shape(int maxN, int maxK, int path, int warps_req, int blocks_per_sm_req, int sms, cudaError_t* err) {
+  LaunchShape s;
+  *err = cudaSuccess;
+  int dev = 0, max_optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  int warps = warps_req > 0 ? warps_req : 4;
+  while (warps > 1 && batch_smem_bytes(maxN, maxK, warps, path) > (size_t)max_optin) warps /= 2;
+  s.warps = warps;
+  s.smem = batch_smem_bytes(maxN, maxK, warps, path);
+  s.slots = slots_of(maxN);
+  if (s.smem > (size_t)max_optin) { *err = cudaErrorInvalidConfiguration; return s; }
+  cudaError_t e = path == PATH_NARROW ? configure_batch<int32_t, int64_t>()
+                  : path == PATH_MID  ? configure_batch<int64_t, int64_t>()
+                                      : configure_batch<i128, i128>();
+  if (e != cudaSuccess) { *err = e; return s; }
+  int per_sm = blocks_per_sm_req;
+  if (per_sm <= 0) {
+    if (path == PATH_NARROW)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<int32_t, int64_t>, warps * 32, s.smem);
+    else if (path == PATH_MID)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<int64_t, int64_t>, warps * 32, s.smem);
+    else
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<i128, i128>, warps * 32, s.smem);
+    if (e != cudaSuccess) { *err = e; return s; }
+    if (per_sm < 1) per_sm = 1;
+  }
+  s.blocks = per_sm * sms;
+  return s;
+}
+
+cudaError_t launch_batch(const BatchParams& p, const LaunchShape& s, int path, cudaStream_t st) {
+  if (path == PATH_NARROW) k_batch<int32_t, int64_t><<<s.blocks, s.warps * 32, s.smem, st>>>(p);
+  else if (path == PATH_MID) k_batch<int64_t, int64_t><<<s.blocks, s.warps * 32, s.smem, st>>>(p);
+  else k_batch<i128, i128><<<s.blocks, s.warps * 32, s.smem, st>>>(p);
+  return cudaGetLastError();
+}
+
 }  // namespace bd

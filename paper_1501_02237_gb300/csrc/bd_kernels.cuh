@@ -44,4 +44,37 @@ cudaError_t launch_enumerate(const EnumParams& p, const LaunchShape& s, int path
 cudaError_t launch_classify(const int64_t* pts, const int64_t* lifts, int N, int K, const uint8_t* subsets,
                             int count, int32_t* status, int64_t* absdet, int path, cudaStream_t st);
 
+// ---- batches: many systems in one persistent launch ---------------------------------------
+
+constexpr int BATCH_KMAX = 12;  // a batch item keeps 11 prefix indices
+
+struct BatchDesc {       // one system of a batch
+  int N, K;
+  int pts_off;           // offset of its N x K coordinates in the packed point array
+  int path;
+  uint64_t lift_seed;    // stream seed of its current lifting
+};
+
+struct BatchItem {       // a prefix of one system's subset tree
+  uint32_t sys;
+  uint8_t len;
+  uint8_t idx[11];
+};
+
+struct BatchParams {
+  const BatchDesc* desc;
+  const int64_t* pts;
+  const BatchItem* items;
+  int nitems;
+  int maxN, maxK;                 // shared-memory layout bounds of this launch
+  unsigned int* counter;          // next item (reset before the launch)
+  DevAcc* acc;                    // per system (reset before the launch)
+  unsigned long long* cycles;     // per system: SM cycles spent in its items
+  unsigned int* done;             // per system: items finished (for streaming completion)
+};
+
+size_t batch_smem_bytes(int maxN, int maxK, int warps, int path);
+LaunchShape batch_shape(int maxN, int maxK, int path, int warps_req, int blocks_per_sm_req, int sms, cudaError_t* err);
+cudaError_t launch_batch(const BatchParams& p, const LaunchShape& s, int path, cudaStream_t st);
+
 }  // namespace bd
