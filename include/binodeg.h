@@ -212,6 +212,33 @@ int bd_batch_run(bd_batch* batch, const bd_batch_opts* opts, bd_batch_stats* sta
 int bd_batch_result(const bd_batch* batch, int32_t index, bd_degree_out* out, uint64_t* cycles);
 int bd_batch_destroy(bd_batch* batch);
 
+/* ---- learned cost model ------------------------------------------------------------------
+ *
+ * A 16 -> 64 -> 64 -> 1 fully connected ReLU network in FP32 that predicts log2 of a system's
+ * enumeration cost (SM cycles of its work items) from the BD_FEATURES features of
+ * bd_batch_features.  Forward, backward and Adam run in this library's CUDA kernels.  The
+ * prediction only sizes and orders work (bd_batch_opts.cost); it never touches a result.
+ * Parameters: BD_MLP_PARAMS floats, W1[64][16], b1[64], W2[64][64], b2[64], W3[64], b3;
+ * normalization: mean[16] then std[16] applied to the features before the first layer.
+ */
+#define BD_MLP_PARAMS 5313
+typedef struct bd_mlp bd_mlp;
+/* He-uniform initialisation from a counter-based generator seeded by `seed`. */
+int bd_mlp_create(uint64_t seed, bd_mlp** mlp);
+int bd_mlp_destroy(bd_mlp* mlp);
+int bd_mlp_get_params(const bd_mlp* mlp, float* params, float* norm /* NULL or 32 floats */);
+int bd_mlp_set_params(bd_mlp* mlp, const float* params, const float* norm /* NULL or 32 floats */);
+/* y[i] = network(features of row i), X: count x 16 host floats. */
+int bd_mlp_predict(bd_mlp* mlp, const float* X, int32_t count, float* y);
+/* Gradient of the mean squared error (1/count) sum (f(x_i) - y_i)^2 with respect to every
+ * parameter (BD_MLP_PARAMS floats) and the loss itself, at the current parameters. */
+int bd_mlp_gradient(bd_mlp* mlp, const float* X, const float* y, int32_t count, float* grad, float* loss);
+/* Adam (lr, beta 0.9/0.999) on the mean squared error, minibatches of `batch`, `epochs` passes
+ * over a seeded permutation; sets the normalization from X first.  final_loss: the mean
+ * squared error over the last epoch. */
+int bd_mlp_train(bd_mlp* mlp, const float* X, const float* y, int32_t count, int32_t epochs, int32_t batch, float lr,
+                 uint64_t seed, float* final_loss);
+
 /* ---- allocation-free variant ------------------------------------------------------------
  *
  * bd_volume_noalloc: the same exact volume as bd_volume (same kernel, same liftings, same

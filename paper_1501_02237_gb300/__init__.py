@@ -12,11 +12,11 @@ from typing import Optional, Sequence
 
 import numpy as np
 
-from ._lib import (BD_FEATURES, BD_FLAG_DEGENERATE, BD_FLAG_INCONSISTENT, BD_FLAG_INT128, KMAX,  # noqa: F401
+from ._lib import (BD_FEATURES, BD_MLP_PARAMS, BD_FLAG_DEGENERATE, BD_FLAG_INCONSISTENT, BD_FLAG_INT128, KMAX,  # noqa: F401
                    NMAX, BatchOpts, BatchStats, BinodegError, DegreeOut, PlanOpts, VolumeOut, check, i64, lib, ptr)
 from ._lib import F32P, I32P, U8P
 
-__all__ = ["degree", "volume", "volume_noalloc", "volume_lifted", "classify", "reduce", "Plan", "Batch", "set_stream",
+__all__ = ["CostModel", "degree", "volume", "volume_noalloc", "volume_lifted", "classify", "reduce", "Plan", "Batch", "set_stream",
            "host_volume_lifted", "BinodegError", "lib"]
 
 
@@ -218,6 +218,62 @@ class Batch:
     def close(self) -> None:
         if getattr(self, "handle", None):
             lib().bd_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _f32(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+
+
+class CostModel:
+    """bd_mlp_*: the learned cost model (16 -> 64 -> 64 -> 1, FP32) trained by the library's kernels."""
+
+    def __init__(self, seed: int = 0):
+        h = C.c_void_p()
+        check(lib().bd_mlp_create(C.c_uint64(seed), C.byref(h)))
+        self.handle = h
+
+    def params(self):
+        p = np.zeros(BD_MLP_PARAMS, dtype=np.float32)
+        nrm = np.zeros(2 * BD_FEATURES, dtype=np.float32)
+        check(lib().bd_mlp_get_params(self.handle, p.ctypes.data_as(F32P), nrm.ctypes.data_as(F32P)))
+        return p, nrm
+
+    def set_params(self, params, norm=None) -> None:
+        p = _f32(params)
+        n = None if norm is None else _f32(norm)
+        check(lib().bd_mlp_set_params(self.handle, p.ctypes.data_as(F32P), None if n is None else n.ctypes.data_as(F32P)))
+
+    def predict(self, X) -> np.ndarray:
+        X = _f32(X)
+        y = np.zeros(X.shape[0], dtype=np.float32)
+        check(lib().bd_mlp_predict(self.handle, X.ctypes.data_as(F32P), X.shape[0], y.ctypes.data_as(F32P)))
+        return y
+
+    def gradient(self, X, y):
+        X, y = _f32(X), _f32(y)
+        g = np.zeros(BD_MLP_PARAMS, dtype=np.float32)
+        loss = C.c_float()
+        check(lib().bd_mlp_gradient(self.handle, X.ctypes.data_as(F32P), y.ctypes.data_as(F32P), X.shape[0],
+                                    g.ctypes.data_as(F32P), C.byref(loss)))
+        return g, float(loss.value)
+
+    def train(self, X, y, epochs: int = 60, batch: int = 256, lr: float = 2e-3, seed: int = 0) -> float:
+        X, y = _f32(X), _f32(y)
+        loss = C.c_float()
+        check(lib().bd_mlp_train(self.handle, X.ctypes.data_as(F32P), y.ctypes.data_as(F32P), X.shape[0], epochs,
+                                 batch, C.c_float(lr), C.c_uint64(seed), C.byref(loss)))
+        return float(loss.value)
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            lib().bd_mlp_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -75,6 +75,7 @@ class BatchStats(C.Structure):
 
 
 BD_FEATURES = 16
+BD_MLP_PARAMS = 5313
 I64P = C.POINTER(C.c_int64)
 I32P = C.POINTER(C.c_int32)
 F32P = C.POINTER(C.c_float)
@@ -106,6 +107,15 @@ SIGNATURES = {
     "bd_batch_run": (C.c_int, [C.c_void_p, C.POINTER(BatchOpts), C.POINTER(BatchStats)]),
     "bd_batch_result": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(DegreeOut), C.POINTER(C.c_uint64)]),
     "bd_batch_destroy": (C.c_int, [C.c_void_p]),
+    "bd_mlp_create": (C.c_int, [C.c_uint64, C.POINTER(C.c_void_p)]),
+    "bd_mlp_destroy": (C.c_int, [C.c_void_p]),
+    "bd_mlp_get_params": (C.c_int, [C.c_void_p, C.POINTER(C.c_float), C.POINTER(C.c_float)]),
+    "bd_mlp_set_params": (C.c_int, [C.c_void_p, C.POINTER(C.c_float), C.POINTER(C.c_float)]),
+    "bd_mlp_predict": (C.c_int, [C.c_void_p, C.POINTER(C.c_float), C.c_int32, C.POINTER(C.c_float)]),
+    "bd_mlp_gradient": (C.c_int, [C.c_void_p, C.POINTER(C.c_float), C.POINTER(C.c_float), C.c_int32,
+                                  C.POINTER(C.c_float), C.POINTER(C.c_float)]),
+    "bd_mlp_train": (C.c_int, [C.c_void_p, C.POINTER(C.c_float), C.POINTER(C.c_float), C.c_int32, C.c_int32,
+                               C.c_int32, C.c_float, C.c_uint64, C.POINTER(C.c_float)]),
 }
 
 _lib = None

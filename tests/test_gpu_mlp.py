@@ -1,0 +1,82 @@
+"""The cost model's CUDA forward, gradient and training kernels against the float64 reference
+network (oracle/mlp.py), and what the trained network gains over the closed-form bound.
+
+Tolerance: FP32 evaluation of dot products of at most 64 terms and gradient sums over at most a
+few hundred samples carry relative errors of order (64 + n) * 2^-24 ~ 3e-5 of the summed
+magnitudes; 1e-3 of the largest magnitude is used, far below what a wrong term would cause."""
+
+import numpy as np
+import pytest
+
+import paper_1501_02237_gb300 as bd
+from oracle import mlp
+from workloads import batch_systems
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.init()
+    yield
+
+
+def close(a, b, rel=1e-3):
+    a, b = np.asarray(a, dtype=np.float64), np.asarray(b, dtype=np.float64)
+    return np.max(np.abs(a - b)) <= rel * max(1.0, np.max(np.abs(b)))
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_forward_and_gradient_match_reference(seed):
+    rng = np.random.default_rng(seed)
+    m = bd.CostModel(seed)
+    p = rng.normal(0, 0.2, mlp.NPARAM).astype(np.float32)
+    mean = rng.normal(0, 1, mlp.F).astype(np.float32)
+    std = rng.uniform(0.5, 2.0, mlp.F).astype(np.float32)
+    m.set_params(p, np.concatenate([mean, std]))
+    X = rng.normal(0, 2, (300, mlp.F)).astype(np.float32)
+    y = rng.normal(0, 1, 300).astype(np.float32)
+    f_ref, _ = mlp.forward(p.astype(np.float64), X, mean, std)
+    assert close(m.predict(X), f_ref)
+    g, loss = m.gradient(X, y)
+    g_ref = mlp.gradient(p.astype(np.float64), X, y, mean, std)
+    assert close(g, g_ref)
+    assert abs(loss - mlp.loss(p.astype(np.float64), X, y, mean, std)) <= 1e-3 * max(1.0, loss)
+
+
+def test_training_fits_a_smooth_target():
+    rng = np.random.default_rng(1)
+    X = rng.normal(0, 1, (4000, mlp.F)).astype(np.float32)
+    y = (X @ rng.normal(0, 1, mlp.F) + 0.5 * np.abs(X[:, 0])).astype(np.float32)
+    m = bd.CostModel(3)
+    base = float(np.mean((y - y.mean()) ** 2))
+    final = m.train(X, y, epochs=40, batch=128, lr=3e-3, seed=5)
+    assert final < 0.05 * base
+    assert float(np.mean((m.predict(X) - y) ** 2)) < 0.05 * base
+
+
+def test_trained_model_beats_closed_form_bound():
+    # training data made by the method itself: per-system SM cycles of a batched run
+    systems = batch_systems(700, first_seed=20000)
+    b = bd.Batch()
+    for s in systems:
+        b.add(s.A, seed=0)
+    b.prepare()
+    b.run(mode=0)
+    cyc = np.array([r["cycles"] for r in b.results()], dtype=np.float64)
+    X = b.features()
+    keep = cyc > 0
+    X, y = X[keep], np.log2(cyc[keep]).astype(np.float32)
+    n_train = int(0.7 * len(y))
+    m = bd.CostModel(0)
+    m.train(X[:n_train], y[:n_train], epochs=300, batch=64, lr=2e-3, seed=1)
+    err_mlp = np.mean(np.abs(m.predict(X[n_train:]) - y[n_train:]))
+    # the method without the network: log2 of the closed-form bound, calibrated by least squares
+    cf = X[:, 3].astype(np.float64)
+    A = np.stack([np.ones(n_train), cf[:n_train]], 1)
+    coef, *_ = np.linalg.lstsq(A, y[:n_train], rcond=None)
+    err_cf = np.mean(np.abs(coef[0] + coef[1] * cf[n_train:] - y[n_train:]))
+    assert err_mlp < 0.8 * err_cf, (err_mlp, err_cf)
