@@ -212,6 +212,45 @@ int bd_batch_run(bd_batch* batch, const bd_batch_opts* opts, bd_batch_stats* sta
 int bd_batch_result(const bd_batch* batch, int32_t index, bd_degree_out* out, uint64_t* cycles);
 int bd_batch_destroy(bd_batch* batch);
 
+/* ---- serving (continuous batching) ---------------------------------------------------------
+ *
+ * bd_server_start launches a host pump thread; one persistent kernel (relaunched on demand when
+ * it has exited after ~40 ms without work) claims (slot, prefix) work items from a device ring
+ * while the pump keeps appending to it.  bd_server_submit reduces a system on the caller's thread
+ * and queues it; the pump admits queued systems into free slots whenever the device budget
+ * allows (a slot, ring room, and at most max_inflight_items items in flight), in arrival order
+ * (order 0) or by smallest predicted cost (order 1; predicted_cost from the cost model, or <= 0
+ * for the closed-form bound).  Admitted systems' items interleave on the device with those of
+ * systems already running.  Finished degrees are returned by bd_server_poll with their latency
+ * from submission.  Served systems need dimension <= 10 and 32/64-bit minors (BD_ERR_ARG
+ * otherwise: use bd_degree).  Results are identical to bd_degree's.
+ */
+typedef struct bd_server bd_server;
+typedef struct {
+  int32_t slots;             /* systems resident at once (0: 256) */
+  int32_t ring_items;        /* work-item ring capacity (0: 2^20) */
+  int64_t memory_budget;     /* device bytes for slots and ring (0: as sized above) */
+  int32_t warps_per_block;   /* 0: 4 */
+  int32_t blocks_per_sm;     /* 0: occupancy minus one (room for other kernels) */
+  int64_t item_subsets;      /* smallest work item in subsets (0: 256) */
+  int64_t max_inflight_items;/* admitted but unfinished items (0: the ring capacity) */
+  int32_t order;             /* 0 FIFO, 1 smallest predicted cost first */
+  int32_t reserved[3];
+} bd_server_opts;
+typedef struct {
+  int64_t submitted, completed, relifted, launches;
+  int64_t ring_items;
+  int32_t slots, blocks, warps_per_block, waiting;
+} bd_server_stats;
+int bd_server_start(const bd_server_opts* opts, bd_server** server);
+int bd_server_submit(bd_server* server, const int64_t* A, int32_t n, int32_t m, const int64_t* coef, uint64_t seed,
+                     double predicted_cost, int64_t* ticket);
+/* One finished request, waiting up to wait_ms for one; BD_ERR_STATE when none is ready. */
+int bd_server_poll(bd_server* server, int32_t wait_ms, int64_t* ticket, bd_degree_out* out, double* latency_ms);
+int bd_server_stats_get(bd_server* server, bd_server_stats* stats);
+/* Finishes every submitted request, then stops the kernel and frees the server. */
+int bd_server_stop(bd_server* server);
+
 /* ---- learned cost model ------------------------------------------------------------------
  *
  * A 16 -> 64 -> 64 -> 1 fully connected ReLU network in FP32 that predicts log2 of a system's

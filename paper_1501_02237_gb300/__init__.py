@@ -13,10 +13,11 @@ from typing import Optional, Sequence
 import numpy as np
 
 from ._lib import (BD_FEATURES, BD_MLP_PARAMS, BD_FLAG_DEGENERATE, BD_FLAG_INCONSISTENT, BD_FLAG_INT128, KMAX,  # noqa: F401
-                   NMAX, BatchOpts, BatchStats, BinodegError, DegreeOut, PlanOpts, VolumeOut, check, i64, lib, ptr)
+                   NMAX, BatchOpts, BatchStats, BinodegError, DegreeOut, PlanOpts, ServerOpts, ServerStats, VolumeOut,
+                   check, i64, lib, ptr)
 from ._lib import F32P, I32P, U8P
 
-__all__ = ["CostModel", "degree", "volume", "volume_noalloc", "volume_lifted", "classify", "reduce", "Plan", "Batch", "set_stream",
+__all__ = ["CostModel", "Server", "degree", "volume", "volume_noalloc", "volume_lifted", "classify", "reduce", "Plan", "Batch", "set_stream",
            "host_volume_lifted", "BinodegError", "lib"]
 
 
@@ -279,5 +280,53 @@ class CostModel:
     def __del__(self):
         try:
             self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """bd_server_*: continuous-batching service (persistent kernel fed while it runs)."""
+
+    def __init__(self, slots: int = 0, ring_items: int = 0, memory_budget: int = 0, warps_per_block: int = 0,
+                 blocks_per_sm: int = 0, item_subsets: int = 0, max_inflight_items: int = 0, order: int = 0):
+        o = ServerOpts(slots, ring_items, memory_budget, warps_per_block, blocks_per_sm, item_subsets,
+                       max_inflight_items, order)
+        h = C.c_void_p()
+        check(lib().bd_server_start(C.byref(o), C.byref(h)))
+        self.handle = h
+
+    def submit(self, A, coef=None, seed: int = 0, predicted_cost: float = 0.0) -> int:
+        A = i64(A)
+        n, m = A.shape
+        c = _coef_array(coef, m)
+        t = C.c_int64()
+        check(lib().bd_server_submit(self.handle, ptr(A), n, m, ptr(c) if c is not None else None,
+                                     C.c_uint64(seed), C.c_double(predicted_cost), C.byref(t)))
+        return t.value
+
+    def poll(self, wait_ms: int = 0):
+        """(ticket, result dict, latency ms) of one finished request, or None."""
+        out = DegreeOut()
+        t = C.c_int64()
+        lat = C.c_double()
+        rc = lib().bd_server_poll(self.handle, wait_ms, C.byref(t), C.byref(out), C.byref(lat))
+        if rc == 7:  # BD_ERR_STATE: nothing finished yet
+            return None
+        check(rc)
+        return t.value, out.as_dict(), lat.value
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        check(lib().bd_server_stats_get(self.handle, C.byref(s)))
+        return s.as_dict()
+
+    def stop(self) -> None:
+        if getattr(self, "handle", None):
+            check(lib().bd_server_stop(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.stop()
         except Exception:
             pass

@@ -74,6 +74,21 @@ class BatchStats(C.Structure):
         return {n: getattr(self, n) for n, _ in self._fields_}
 
 
+class ServerOpts(C.Structure):
+    _fields_ = [("slots", C.c_int32), ("ring_items", C.c_int32), ("memory_budget", C.c_int64),
+                ("warps_per_block", C.c_int32), ("blocks_per_sm", C.c_int32), ("item_subsets", C.c_int64),
+                ("max_inflight_items", C.c_int64), ("order", C.c_int32), ("reserved", C.c_int32 * 3)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("relifted", C.c_int64), ("launches", C.c_int64),
+                ("ring_items", C.c_int64), ("slots", C.c_int32), ("blocks", C.c_int32),
+                ("warps_per_block", C.c_int32), ("waiting", C.c_int32)]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
 BD_FEATURES = 16
 BD_MLP_PARAMS = 5313
 I64P = C.POINTER(C.c_int64)
@@ -107,6 +122,13 @@ SIGNATURES = {
     "bd_batch_run": (C.c_int, [C.c_void_p, C.POINTER(BatchOpts), C.POINTER(BatchStats)]),
     "bd_batch_result": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(DegreeOut), C.POINTER(C.c_uint64)]),
     "bd_batch_destroy": (C.c_int, [C.c_void_p]),
+    "bd_server_start": (C.c_int, [C.POINTER(ServerOpts), C.POINTER(C.c_void_p)]),
+    "bd_server_submit": (C.c_int, [C.c_void_p, I64P, C.c_int32, C.c_int32, I64P, C.c_uint64, C.c_double,
+                                   C.POINTER(C.c_int64)]),
+    "bd_server_poll": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int64), C.POINTER(DegreeOut),
+                                 C.POINTER(C.c_double)]),
+    "bd_server_stats_get": (C.c_int, [C.c_void_p, C.POINTER(ServerStats)]),
+    "bd_server_stop": (C.c_int, [C.c_void_p]),
     "bd_mlp_create": (C.c_int, [C.c_uint64, C.POINTER(C.c_void_p)]),
     "bd_mlp_destroy": (C.c_int, [C.c_void_p]),
     "bd_mlp_get_params": (C.c_int, [C.c_void_p, C.POINTER(C.c_float), C.POINTER(C.c_float)]),

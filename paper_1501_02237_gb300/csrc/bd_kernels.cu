@@ -357,4 +357,126 @@ cudaError_t launch_batch(const BatchParams& p, const LaunchShape& s, int path, c
   return cudaGetLastError();
 }
 
+// ---- serving ---------------------------------------------------------------------------------
+
+namespace {
+
+// One warp processes one item of a slot with the walker of that slot's integer path.  The
+// shared-memory region is laid out for the int64 path (the larger); the int32 path uses the
+// same bytes.
+template <class TC, class TL>
+__device__ void serve_item(WarpTeam& tm, const int64_t* P, int N, int K, int slots, unsigned char* stack, int maxK,
+                           const Item& it, Acc& acc) {
+  TC* sc = reinterpret_cast<TC*>(stack);
+  TL* sl = reinterpret_cast<TL*>(stack + align16((size_t)slots * stack_entries(maxK) * sizeof(int64_t)));
+  float* fl = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(sl) + align16((size_t)slots * maxK * sizeof(int64_t)));
+  Walker<TC, TL, WarpTeam> W(tm, P, N, K, slots, sc, sl, fl);
+  W.run_item(it, acc);
+}
+
+__global__ void BD_ENUM_BOUNDS k_serve(ServeParams p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int slots = slots_of(p.maxN);
+  const size_t pbytes = align16((size_t)(p.maxK + 1) * p.maxN * sizeof(int64_t));
+  unsigned char* base = smem + (size_t)warp * (pbytes + warp_bytes<int64_t, int64_t>(slots, p.maxK));
+  int64_t* P = reinterpret_cast<int64_t*>(base);
+  unsigned char* stack = base + pbytes;
+  WarpTeam tm;
+  unsigned long long idle = 0;
+  for (;;) {
+    unsigned long long got = ~0ull;
+    int quit = 0;
+    if (lane == 0) {
+      const unsigned long long h = *(volatile unsigned long long*)p.head;
+      const unsigned long long t = *p.tail;
+      if (h < t) {
+        if (atomicCAS(p.head, h, h + 1) == h) got = h;
+      } else if (*p.stop || ++idle > p.idle_spins) {
+        quit = 1;
+      } else {
+        __nanosleep(2000);
+      }
+    }
+    got = __shfl_sync(0xffffffffu, got, 0);
+    quit = __shfl_sync(0xffffffffu, quit, 0);
+    if (quit) break;
+    if (got == ~0ull) continue;
+    idle = 0;
+    __threadfence();  // the item and its slot were published before the tail
+    const volatile unsigned int* rp = reinterpret_cast<const volatile unsigned int*>(p.ring + (got % p.ring_cap));
+    BatchItem bi;
+    unsigned int* bw = reinterpret_cast<unsigned int*>(&bi);
+    for (int t = 0; t < 4; ++t) bw[t] = rp[t];
+    const int slot = (int)bi.sys;
+    // a slot is reused for other systems and liftings: its descriptor and points are read past L1
+    const unsigned long long* dw = reinterpret_cast<const unsigned long long*>(p.desc + slot);
+    BatchDesc d;
+    unsigned long long* dd = reinterpret_cast<unsigned long long*>(&d);
+    for (int t = 0; t < (int)(sizeof(BatchDesc) / 8); ++t) dd[t] = __ldcg(dw + t);
+    const int N = d.N, K = d.K, path = d.path;
+    __syncwarp();
+    for (int t = lane; t < N * K; t += 32) {
+      const int q = t / K, c = t - q * K;
+      P[c * N + q] = __ldcg(p.pts + (size_t)slot * BD_SERVE_PTS + t);
+    }
+    for (int q = lane; q < N; q += 32) P[K * N + q] = lift_height(d.lift_seed, q);
+    __syncwarp();
+    Item it{};
+    it.len = bi.len;
+    for (int t = 0; t < bi.len; ++t) it.idx[t] = bi.idx[t];
+    Acc acc{};
+    const long long t0 = clock64();
+    if (path == PATH_NARROW) serve_item<int32_t, int64_t>(tm, P, N, K, slots, stack, p.maxK, it, acc);
+    else serve_item<int64_t, int64_t>(tm, P, N, K, slots, stack, p.maxK, it, acc);
+    const unsigned long long cyc = (unsigned long long)(clock64() - t0);
+    if (lane == 0) {
+      flush(acc, p.acc + slot, 1);
+      atomicAdd(p.cycles + slot, cyc);
+      __threadfence();
+      if (atomicSub(p.remaining + slot, 1u) == 1u) {  // the slot's last item: publish its completion
+        __threadfence();
+        const unsigned long long i = atomicAdd(p.comp_count, 1ull);
+        p.comp[i % p.comp_cap] = ((i + 1) << 32) | (unsigned long long)(unsigned)slot;
+        __threadfence_system();
+      }
+    }
+  }
+}
+
+}  // namespace
+
+size_t serve_smem_bytes(int maxN, int maxK, int warps) {
+  const int slots = slots_of(maxN);
+  return (align16((size_t)(maxK + 1) * maxN * sizeof(int64_t)) + warp_bytes<int64_t, int64_t>(slots, maxK)) * warps;
+}
+
+LaunchShape serve_shape(int maxN, int maxK, int warps_req, int blocks_per_sm_req, int sms, cudaError_t* err) {
+  LaunchShape s;
+  *err = cudaSuccess;
+  int dev = 0, max_optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  int warps = warps_req > 0 ? warps_req : 4;
+  while (warps > 1 && serve_smem_bytes(maxN, maxK, warps) > (size_t)max_optin) warps /= 2;
+  s.warps = warps;
+  s.smem = serve_smem_bytes(maxN, maxK, warps);
+  s.slots = slots_of(maxN);
+  cudaError_t e = cudaFuncSetAttribute(k_serve, cudaFuncAttributeMaxDynamicSharedMemorySize, max_optin);
+  if (e != cudaSuccess) { *err = e; return s; }
+  int per_sm = blocks_per_sm_req;
+  if (per_sm <= 0) {
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_serve, warps * 32, s.smem);
+    if (e != cudaSuccess) { *err = e; return s; }
+    per_sm = per_sm > 1 ? per_sm - 1 : 1;  // leave room for other kernels (cost-model inference)
+  }
+  s.blocks = per_sm * sms;
+  return s;
+}
+
+cudaError_t launch_serve(const ServeParams& p, const LaunchShape& s, cudaStream_t st) {
+  k_serve<<<s.blocks, s.warps * 32, s.smem, st>>>(p);
+  return cudaGetLastError();
+}
+
 }  // namespace bd

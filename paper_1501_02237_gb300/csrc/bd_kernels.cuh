@@ -47,6 +47,7 @@ cudaError_t launch_classify(const int64_t* pts, const int64_t* lifts, int N, int
 // ---- batches: many systems in one persistent launch ---------------------------------------
 
 constexpr int BATCH_KMAX = 12;  // a batch item keeps 11 prefix indices
+constexpr int BD_SERVE_PTS = 64 * BATCH_KMAX;  // coordinates kept per serving slot
 
 struct BatchDesc {       // one system of a batch
   int N, K;
@@ -76,5 +77,29 @@ struct BatchParams {
 size_t batch_smem_bytes(int maxN, int maxK, int warps, int path);
 LaunchShape batch_shape(int maxN, int maxK, int path, int warps_req, int blocks_per_sm_req, int sms, cudaError_t* err);
 cudaError_t launch_batch(const BatchParams& p, const LaunchShape& s, int path, cudaStream_t st);
+
+// ---- serving: a persistent kernel fed while it runs ------------------------------------------
+
+struct ServeParams {
+  const BatchDesc* desc;            // per slot (device)
+  const int64_t* pts;               // per slot: BD_NMAX x BATCH_KMAX coordinates (device)
+  const BatchItem* ring;            // work items, index = ticket % ring_cap (device)
+  unsigned long long ring_cap;
+  unsigned long long* head;         // next ticket to claim (device, claimed by CAS)
+  const volatile unsigned long long* tail;  // tickets below tail are published (device, host-written)
+  unsigned int* remaining;          // per slot: items not yet finished (device)
+  DevAcc* acc;                      // per slot (device)
+  unsigned long long* cycles;       // per slot (device)
+  unsigned long long* comp_count;   // completions so far (device)
+  volatile unsigned long long* comp; // completion records (host-mapped): (sequence << 32) | slot
+  unsigned long long comp_cap;
+  const volatile int* stop;         // host-mapped: 1 asks the kernel to exit
+  unsigned long long idle_spins;    // idle polls before a warp exits (the host relaunches on demand)
+  int maxN, maxK;
+};
+
+size_t serve_smem_bytes(int maxN, int maxK, int warps);
+LaunchShape serve_shape(int maxN, int maxK, int warps_req, int blocks_per_sm_req, int sms, cudaError_t* err);
+cudaError_t launch_serve(const ServeParams& p, const LaunchShape& s, cudaStream_t st);
 
 }  // namespace bd

@@ -1,0 +1,504 @@
+// Serving with continuous batching.  One persistent kernel (k_serve) claims work items from a
+// device ring while the host keeps appending to it: a pump thread admits submitted systems into
+// free slots as long as the device budget (slots and ring capacity) allows, publishes their
+// items, watches completion records the kernel writes to host-mapped memory, re-lifts ties and
+// hands finished degrees to bd_server_poll.  Systems that arrive while others run are admitted
+// immediately, so their items interleave with the running ones on the device.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <new>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/binodeg.h"
+#include "bd_host.h"
+#include "bd_internal.h"
+#include "bd_kernels.cuh"
+#include "bd_lifts.h"
+
+using bd::u128;
+
+namespace {
+
+double now_ms() {
+  using namespace std::chrono;
+  return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+struct Req {
+  int64_t ticket = 0;
+  double t_submit = 0, t_admit = 0, t_done = 0;
+  int rank = 0, dim = 0, N = 0, K = 0, path = 0, attempt = 0;
+  uint64_t torsion = 1, seed = 0;
+  bool consistent = true;
+  int64_t max_abs = 0;
+  double cost = 0;
+  std::vector<int64_t> pts;
+  std::vector<bd::BatchItem> items;
+  uint64_t ring_start = 0;  // first ring ticket of the current publication
+  int slot = -1;
+  bd_degree_out out{};
+  int status = BD_OK;
+  uint64_t cycles = 0;
+};
+
+}  // namespace
+
+struct bd_server {
+  bd_server_opts opts{};
+  int slots = 0;
+  uint64_t ring_cap = 0, comp_cap = 0;
+  int maxN = BD_NMAX, maxK = 10;
+  bd::LaunchShape shape;
+  // device
+  bd::BatchDesc* d_desc = nullptr;
+  int64_t* d_pts = nullptr;
+  bd::BatchItem* d_ring = nullptr;
+  unsigned long long* d_head = nullptr;
+  unsigned long long* d_tail = nullptr;
+  unsigned int* d_remaining = nullptr;
+  bd::DevAcc* d_acc = nullptr;
+  unsigned long long* d_cycles = nullptr;
+  unsigned long long* d_comp_count = nullptr;
+  // host-mapped
+  volatile unsigned long long* h_comp = nullptr;
+  unsigned long long* d_comp = nullptr;
+  volatile int* h_stop = nullptr;
+  int* d_stop = nullptr;
+  // pinned staging
+  bd::BatchDesc* h_desc = nullptr;   // per slot
+  int64_t* h_pts = nullptr;          // per slot
+  unsigned int* h_rem = nullptr;     // per slot
+  bd::BatchItem* h_ring = nullptr;   // mirror of the ring
+  unsigned long long* h_tail = nullptr;
+  bd::DevAcc* h_acc = nullptr;       // one slot's result
+  unsigned long long* h_cyc = nullptr;
+  cudaStream_t s_kernel = nullptr, s_ctl = nullptr;
+  int device = 0;
+  // host state
+  std::mutex mu;
+  std::condition_variable cv;
+  std::deque<Req*> waiting, done;
+  std::vector<Req*> in_slot;
+  std::vector<int> free_slots;
+  uint64_t tail = 0, ring_used = 0, comp_read = 0, inflight_items = 0;
+  int64_t next_ticket = 0;
+  std::atomic<bool> running{false};
+  bool kernel_live = false;
+  std::thread pump;
+  bd_server_stats stats{};
+  std::string error;
+};
+
+namespace {
+
+int cu(cudaError_t e, const char* what) {
+  return e == cudaSuccess ? BD_OK : bd::set_error(BD_ERR_CUDA, (std::string(what) + ": " + cudaGetErrorString(e)).c_str());
+}
+
+// publish one request's items (it already owns a slot) and its slot state
+int publish(bd_server* s, Req* r) {
+  const int slot = r->slot;
+  bd::BatchDesc& d = s->h_desc[slot];
+  d.N = r->N;
+  d.K = r->K;
+  d.pts_off = 0;
+  d.path = r->path;
+  d.lift_seed = bd::lift_stream_seed(r->seed, (uint32_t)r->attempt);
+  std::memcpy(s->h_pts + (size_t)slot * bd::BD_SERVE_PTS, r->pts.data(), sizeof(int64_t) * r->pts.size());
+  s->h_rem[slot] = (unsigned)r->items.size();
+  cudaError_t e = cudaMemcpyAsync(s->d_desc + slot, &d, sizeof(d), cudaMemcpyHostToDevice, s->s_ctl);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(s->d_pts + (size_t)slot * bd::BD_SERVE_PTS, s->h_pts + (size_t)slot * bd::BD_SERVE_PTS,
+                        sizeof(int64_t) * r->pts.size(), cudaMemcpyHostToDevice, s->s_ctl);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->d_acc + slot, 0, sizeof(bd::DevAcc), s->s_ctl);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->d_cycles + slot, 0, sizeof(unsigned long long), s->s_ctl);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(s->d_remaining + slot, s->h_rem + slot, sizeof(unsigned), cudaMemcpyHostToDevice, s->s_ctl);
+  // items into the ring (possibly wrapping), then the new tail: same stream, so in this order
+  const uint64_t n = r->items.size();
+  r->ring_start = s->tail;
+  for (uint64_t i = 0; i < n; ++i) {
+    bd::BatchItem it = r->items[i];
+    it.sys = (uint32_t)slot;
+    s->h_ring[(s->tail + i) % s->ring_cap] = it;
+  }
+  uint64_t start = s->tail % s->ring_cap, first = std::min<uint64_t>(n, s->ring_cap - start);
+  if (e == cudaSuccess && first)
+    e = cudaMemcpyAsync(s->d_ring + start, s->h_ring + start, sizeof(bd::BatchItem) * first, cudaMemcpyHostToDevice, s->s_ctl);
+  if (e == cudaSuccess && n > first)
+    e = cudaMemcpyAsync(s->d_ring, s->h_ring, sizeof(bd::BatchItem) * (n - first), cudaMemcpyHostToDevice, s->s_ctl);
+  s->tail += n;
+  *s->h_tail = s->tail;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(s->d_tail, s->h_tail, sizeof(unsigned long long), cudaMemcpyHostToDevice, s->s_ctl);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->s_ctl);  // staging may be reused afterwards
+  s->ring_used += n;
+  s->inflight_items += n;
+  return cu(e, "publish");
+}
+
+void build_request_items(bd_server* s, Req* r) {
+  const uint64_t sub = bd::binom(r->N, r->K + 1);
+  const uint64_t warps = (uint64_t)s->shape.blocks * s->shape.warps;
+  const uint64_t want = std::max<uint64_t>(1, warps / 2);  // enough items to spread one system over the GPU
+  uint64_t thr = std::max<uint64_t>(s->opts.item_subsets > 0 ? (uint64_t)s->opts.item_subsets : 256, sub / want);
+  r->items.clear();
+  for (const bd::Item& it : bd::build_items(r->N, r->K, thr)) {
+    bd::BatchItem x{};
+    x.len = it.len;
+    for (int t = 0; t < it.len && t < 11; ++t) x.idx[t] = it.idx[t];
+    r->items.push_back(x);
+  }
+}
+
+void finish(bd_server* s, Req* r) {
+  r->t_done = now_ms();
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->done.push_back(r);
+    s->stats.completed += 1;
+  }
+  s->cv.notify_all();
+}
+
+// one pump iteration; returns true if it made progress
+bool pump_once(bd_server* s) {
+  bool progress = false;
+  // completions
+  for (;;) {
+    const unsigned long long rec = s->h_comp[s->comp_read % s->comp_cap];
+    if ((rec >> 32) != (unsigned long long)(s->comp_read + 1)) break;
+    const int slot = (int)(rec & 0xffffffffull);
+    s->comp_read += 1;
+    progress = true;
+    Req* r = s->in_slot[slot];
+    cudaError_t e = cudaMemcpyAsync(s->h_acc, s->d_acc + slot, sizeof(bd::DevAcc), cudaMemcpyDeviceToHost, s->s_ctl);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->h_cyc, s->d_cycles + slot, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s->s_ctl);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->s_ctl);
+    s->ring_used -= r->items.size();
+    s->inflight_items -= r->items.size();
+    if (e != cudaSuccess) {
+      r->status = BD_ERR_CUDA;
+    } else if (s->h_acc->ties && r->attempt < 7) {  // re-lift in the same slot
+      r->attempt += 1;
+      s->stats.relifted += 1;
+      if (publish(s, r) != BD_OK) r->status = BD_ERR_CUDA;
+      else continue;
+    } else if (s->h_acc->ties) {
+      r->status = BD_ERR_TIES;
+    } else if (s->h_acc->items_done != r->items.size()) {
+      r->status = BD_ERR_CUDA;
+    } else {
+      const u128 nvol = ((u128)s->h_acc->nvol_hi << 64) | s->h_acc->nvol_lo;
+      const u128 deg = nvol * (u128)r->torsion;
+      r->out.nvol_lo = (uint64_t)nvol;
+      r->out.nvol_hi = (uint64_t)(nvol >> 64);
+      r->out.degree_lo = (uint64_t)deg;
+      r->out.degree_hi = (uint64_t)(deg >> 64);
+      r->out.cells = s->h_acc->cells;
+      r->out.relifts = r->attempt;
+      r->out.flags = nvol == 0 ? BD_FLAG_DEGENERATE : 0;
+      r->cycles = *s->h_cyc;
+    }
+    s->in_slot[slot] = nullptr;
+    s->free_slots.push_back(slot);
+    finish(s, r);
+  }
+  // admissions: FIFO or shortest predicted cost first, while a slot and ring room are free and
+  // the in-flight work stays below the budget
+  for (;;) {
+    Req* r = nullptr;
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      if (s->waiting.empty() || s->free_slots.empty()) break;
+      auto it = s->waiting.begin();
+      if (s->opts.order == 1)
+        it = std::min_element(s->waiting.begin(), s->waiting.end(), [](Req* a, Req* b) { return a->cost < b->cost; });
+      r = *it;
+      if (r->items.empty()) build_request_items(s, r);
+      const uint64_t limit = s->opts.max_inflight_items > 0 ? (uint64_t)s->opts.max_inflight_items : s->ring_cap;
+      // ring room: requests finish out of order, so the oldest publication still in a slot
+      // bounds what may be overwritten
+      uint64_t oldest = s->tail;
+      for (Req* q : s->in_slot)
+        if (q) oldest = std::min(oldest, q->ring_start);
+      if (s->tail + r->items.size() - oldest > s->ring_cap ||
+          (s->inflight_items > 0 && s->inflight_items + r->items.size() > limit))
+        break;
+      s->waiting.erase(it);
+    }
+    r->slot = s->free_slots.back();
+    s->free_slots.pop_back();
+    s->in_slot[r->slot] = r;
+    r->t_admit = now_ms();
+    if (publish(s, r) != BD_OK) {
+      r->status = BD_ERR_CUDA;
+      s->in_slot[r->slot] = nullptr;
+      s->free_slots.push_back(r->slot);
+      finish(s, r);
+    }
+    progress = true;
+  }
+  // the kernel: relaunch when work is in flight and the previous launch has exited
+  if (s->inflight_items > 0) {
+    if (s->kernel_live && cudaStreamQuery(s->s_kernel) == cudaSuccess) s->kernel_live = false;
+    if (!s->kernel_live) {
+      bd::ServeParams p{};
+      p.desc = s->d_desc;
+      p.pts = s->d_pts;
+      p.ring = s->d_ring;
+      p.ring_cap = s->ring_cap;
+      p.head = s->d_head;
+      p.tail = s->d_tail;
+      p.remaining = s->d_remaining;
+      p.acc = s->d_acc;
+      p.cycles = s->d_cycles;
+      p.comp_count = s->d_comp_count;
+      p.comp = s->d_comp;
+      p.comp_cap = s->comp_cap;
+      p.stop = s->d_stop;
+      p.idle_spins = 20000;  // ~40 ms of 2 us naps without work, then the warps exit
+      p.maxN = s->maxN;
+      p.maxK = s->maxK;
+      if (bd::launch_serve(p, s->shape, s->s_kernel) == cudaSuccess) {
+        s->kernel_live = true;
+        s->stats.launches += 1;
+      }
+    }
+  }
+  return progress;
+}
+
+void pump_loop(bd_server* s) {
+  cudaSetDevice(s->device);
+  while (s->running.load()) {
+    if (!pump_once(s)) std::this_thread::sleep_for(std::chrono::microseconds(20));
+  }
+  // drain: finish what was admitted and what still waits
+  for (;;) {
+    bool busy;
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      busy = !s->waiting.empty();
+    }
+    busy = busy || s->inflight_items > 0;
+    if (!busy) break;
+    if (!pump_once(s)) std::this_thread::sleep_for(std::chrono::microseconds(20));
+  }
+}
+
+void release(bd_server* s) {
+  cudaFree(s->d_desc);
+  cudaFree(s->d_pts);
+  cudaFree(s->d_ring);
+  cudaFree(s->d_head);
+  cudaFree(s->d_tail);
+  cudaFree(s->d_remaining);
+  cudaFree(s->d_acc);
+  cudaFree(s->d_cycles);
+  cudaFree(s->d_comp_count);
+  cudaFreeHost((void*)s->h_comp);
+  cudaFreeHost((void*)s->h_stop);
+  cudaFreeHost(s->h_desc);
+  cudaFreeHost(s->h_pts);
+  cudaFreeHost(s->h_rem);
+  cudaFreeHost(s->h_ring);
+  cudaFreeHost(s->h_tail);
+  cudaFreeHost(s->h_acc);
+  cudaFreeHost(s->h_cyc);
+  if (s->s_kernel) cudaStreamDestroy(s->s_kernel);
+  if (s->s_ctl) cudaStreamDestroy(s->s_ctl);
+  for (Req* r : s->waiting) delete r;
+  for (Req* r : s->done) delete r;
+  for (Req* r : s->in_slot) delete r;
+}
+
+}  // namespace
+
+extern "C" {
+
+int bd_server_start(const bd_server_opts* opts, bd_server** out) {
+  if (!out) return bd::set_error(BD_ERR_ARG, "NULL argument");
+  bd_server* s = new (std::nothrow) bd_server();
+  if (!s) return bd::set_error(BD_ERR_NOMEM, "host allocation");
+  if (opts) s->opts = *opts;
+  s->slots = s->opts.slots > 0 ? s->opts.slots : 256;
+  s->ring_cap = s->opts.ring_items > 0 ? (uint64_t)s->opts.ring_items : (1u << 20);
+  if (s->opts.memory_budget > 0) {  // admission by device memory: the ring shrinks to the budget
+    const int64_t per_slot = sizeof(int64_t) * bd::BD_SERVE_PTS + sizeof(bd::BatchDesc) + sizeof(bd::DevAcc) + 12;
+    const int64_t left = s->opts.memory_budget - per_slot * s->slots;
+    if (left < (int64_t)sizeof(bd::BatchItem) * 1024) {
+      delete s;
+      return bd::set_error(BD_ERR_ARG, "memory budget below the slot table plus 1024 ring items");
+    }
+    s->ring_cap = std::min<uint64_t>(s->ring_cap, (uint64_t)(left / (int64_t)sizeof(bd::BatchItem)));
+  }
+  s->comp_cap = 4096;
+  cudaGetDevice(&s->device);
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
+  cudaError_t e;
+  s->shape = bd::serve_shape(s->maxN, s->maxK, s->opts.warps_per_block, s->opts.blocks_per_sm, sms, &e);
+  int rc = cu(e, "serve shape");
+  auto A = [&](cudaError_t x) {
+    if (rc == BD_OK && x != cudaSuccess) rc = cu(x, "server allocation");
+  };
+  A(cudaMalloc(&s->d_desc, sizeof(bd::BatchDesc) * s->slots));
+  A(cudaMalloc(&s->d_pts, sizeof(int64_t) * bd::BD_SERVE_PTS * s->slots));
+  A(cudaMalloc(&s->d_ring, sizeof(bd::BatchItem) * s->ring_cap));
+  A(cudaMalloc(&s->d_head, sizeof(unsigned long long)));
+  A(cudaMalloc(&s->d_tail, sizeof(unsigned long long)));
+  A(cudaMalloc(&s->d_remaining, sizeof(unsigned) * s->slots));
+  A(cudaMalloc(&s->d_acc, sizeof(bd::DevAcc) * s->slots));
+  A(cudaMalloc(&s->d_cycles, sizeof(unsigned long long) * s->slots));
+  A(cudaMalloc(&s->d_comp_count, sizeof(unsigned long long)));
+  A(cudaHostAlloc((void**)&s->h_comp, sizeof(unsigned long long) * s->comp_cap, cudaHostAllocMapped));
+  A(cudaHostAlloc((void**)&s->h_stop, sizeof(int), cudaHostAllocMapped));
+  A(cudaMallocHost(&s->h_desc, sizeof(bd::BatchDesc) * s->slots));
+  A(cudaMallocHost(&s->h_pts, sizeof(int64_t) * bd::BD_SERVE_PTS * s->slots));
+  A(cudaMallocHost(&s->h_rem, sizeof(unsigned) * s->slots));
+  A(cudaMallocHost(&s->h_ring, sizeof(bd::BatchItem) * s->ring_cap));
+  A(cudaMallocHost(&s->h_tail, sizeof(unsigned long long)));
+  A(cudaMallocHost(&s->h_acc, sizeof(bd::DevAcc)));
+  A(cudaMallocHost(&s->h_cyc, sizeof(unsigned long long)));
+  A(cudaStreamCreateWithFlags(&s->s_kernel, cudaStreamNonBlocking));
+  A(cudaStreamCreateWithFlags(&s->s_ctl, cudaStreamNonBlocking));
+  if (rc == BD_OK) {
+    std::memset((void*)s->h_comp, 0, sizeof(unsigned long long) * s->comp_cap);
+    *s->h_stop = 0;
+    A(cudaHostGetDevicePointer((void**)&s->d_comp, (void*)s->h_comp, 0));
+    A(cudaHostGetDevicePointer((void**)&s->d_stop, (void*)s->h_stop, 0));
+    A(cudaMemset(s->d_head, 0, sizeof(unsigned long long)));
+    A(cudaMemset(s->d_tail, 0, sizeof(unsigned long long)));
+    A(cudaMemset(s->d_comp_count, 0, sizeof(unsigned long long)));
+  }
+  if (rc != BD_OK) {
+    release(s);
+    delete s;
+    return rc;
+  }
+  s->in_slot.assign(s->slots, nullptr);
+  for (int i = s->slots - 1; i >= 0; --i) s->free_slots.push_back(i);
+  s->stats.ring_items = (int64_t)s->ring_cap;
+  s->stats.slots = s->slots;
+  s->stats.blocks = s->shape.blocks;
+  s->stats.warps_per_block = s->shape.warps;
+  s->running = true;
+  s->pump = std::thread(pump_loop, s);
+  *out = s;
+  return BD_OK;
+}
+
+int bd_server_submit(bd_server* s, const int64_t* A, int32_t n, int32_t m, const int64_t* coef, uint64_t seed,
+                     double predicted_cost, int64_t* ticket) {
+  if (!s || (!A && m > 0)) return bd::set_error(BD_ERR_ARG, "NULL argument");
+  if (n < 1 || n >= BD_NMAX || m < 0 || m > 256) return bd::set_error(BD_ERR_ARG, "need 1 <= n < BD_NMAX, 0 <= m <= 256");
+  Req* r = new (std::nothrow) Req();
+  if (!r) return bd::set_error(BD_ERR_NOMEM, "host allocation");
+  r->t_submit = now_ms();
+  bd::Reduction red;
+  std::string err;
+  int rc = bd::reduce_system(A, n, m, coef, red, err);
+  if (rc) {
+    delete r;
+    return bd::set_error(rc, err.c_str());
+  }
+  r->rank = red.rank;
+  r->dim = red.dim;
+  r->torsion = red.torsion;
+  r->consistent = red.consistent;
+  r->max_abs = red.max_abs_coord;
+  r->N = n + 1;
+  r->K = red.dim;
+  r->pts = std::move(red.points);
+  r->seed = seed;
+  r->out.rank = r->rank;
+  r->out.dim = r->dim;
+  r->out.torsion = r->torsion;
+  r->out.consistent = r->consistent ? 1 : 0;
+  r->out.max_abs_coord = (int32_t)std::min<int64_t>(r->max_abs, INT32_MAX);
+  r->out.subsets = r->K > 0 ? bd::binom(r->N, r->K + 1) : 0;
+  bool direct = !r->consistent || r->K == 0;
+  if (!direct) {
+    if (r->K > s->maxK) {
+      delete r;
+      return bd::set_error(BD_ERR_ARG, "served systems need dimension <= 10");
+    }
+    double coord = 0;
+    const double bound = bd::hadamard_log2(r->pts.data(), nullptr, r->N, r->K, (1 << 20) - 1, &coord);
+    r->path = bd::choose_path(coord, bound);
+    if (r->path < 0 || r->path == bd::PATH_WIDE) {
+      // the serving kernel carries the int32 and int64 walkers; wider systems go through the
+      // single-system path (bd_degree)
+      const int code = r->path < 0 ? BD_ERR_OVERFLOW : BD_ERR_ARG;
+      delete r;
+      return bd::set_error(code, "system needs 128-bit minors: use bd_degree for it");
+    }
+    const double sub = (double)bd::binom(r->N, r->K + 1);
+    r->cost = predicted_cost > 0 ? predicted_cost : sub * ((double)r->K * r->K * r->K / 3.0 + (double)(r->N - r->K) * (r->K + 1));
+  }
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    r->ticket = s->next_ticket++;
+    s->stats.submitted += 1;
+    if (direct) {
+      if (!r->consistent) r->out.flags = BD_FLAG_INCONSISTENT;
+      else {
+        r->out.nvol_lo = 1;
+        r->out.degree_lo = r->torsion;
+      }
+    } else {
+      s->waiting.push_back(r);
+    }
+  }
+  if (ticket) *ticket = r->ticket;
+  if (direct) finish(s, r);
+  return BD_OK;
+}
+
+int bd_server_poll(bd_server* s, int32_t wait_ms, int64_t* ticket, bd_degree_out* out, double* latency_ms) {
+  if (!s || !out) return bd::set_error(BD_ERR_ARG, "NULL argument");
+  Req* r = nullptr;
+  {
+    std::unique_lock<std::mutex> lk(s->mu);
+    if (s->done.empty() && wait_ms > 0) s->cv.wait_for(lk, std::chrono::milliseconds(wait_ms), [&] { return !s->done.empty(); });
+    if (s->done.empty()) return bd::set_error(BD_ERR_STATE, "no finished request");
+    r = s->done.front();
+    s->done.pop_front();
+  }
+  const int st = r->status;
+  *out = r->out;
+  if (ticket) *ticket = r->ticket;
+  if (latency_ms) *latency_ms = r->t_done - r->t_submit;
+  delete r;
+  return st == BD_OK ? BD_OK : bd::set_error(st, "request failed");
+}
+
+int bd_server_stats_get(bd_server* s, bd_server_stats* out) {
+  if (!s || !out) return bd::set_error(BD_ERR_ARG, "NULL argument");
+  std::lock_guard<std::mutex> lk(s->mu);
+  *out = s->stats;
+  out->waiting = (int32_t)s->waiting.size();
+  return BD_OK;
+}
+
+int bd_server_stop(bd_server* s) {
+  if (!s) return BD_OK;
+  s->running = false;
+  if (s->pump.joinable()) s->pump.join();  // drains admitted and waiting requests first
+  *s->h_stop = 1;
+  cudaStreamSynchronize(s->s_kernel);
+  release(s);
+  delete s;
+  return BD_OK;
+}
+
+}  // extern "C"
