@@ -39,6 +39,8 @@ def parse():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch-serve", action="store_true", help="skip the batch and serving sections")
+    ap.add_argument("--workload", default=WORKLOAD, help="single system timed (profiling runs use the others)")
     return ap.parse_args()
 
 
@@ -150,6 +152,104 @@ def cpu_baseline(system, subsets, budget_s=15.0):
                 sample=f"{n} full exact degrees of the workload ({dt:.1f} s, single thread)")
 
 
+def batch_section(bd, seed=0):
+    """The batched form against one launch per system on the uneven 4096-system workload
+    (n ~ U[12,28], k ~ U[4,9], exponents in {0,1,2}, seeds 0..4095), exact agreement checked."""
+    from workloads import batch_systems
+
+    systems = batch_systems(4096)
+    b = bd.Batch()
+    for s in systems:
+        b.add(s.A, seed=seed)
+    b.prepare()
+    out = {}
+    ref = None
+    for label, kw in [("batched", dict(mode=0, autotune=True)), ("batched", dict(mode=0, autotune=True)),
+                      ("batched_graph", dict(mode=0, autotune=True, use_graph=True)),
+                      ("per_system", dict(mode=1))]:
+        st = b.run(**kw)
+        res = [(r["degree"], r["nvol"]) for r in b.results()]
+        ref = ref or res
+        assert res == ref, "batched and per-system results differ"
+        out[label] = dict(systems_per_s=len(systems) / (st["wall_ms"] / 1e3), wall_ms=st["wall_ms"],
+                          gpu_ms=st["gpu_ms"], subsets_per_s=st["subsets"] / (st["wall_ms"] / 1e3),
+                          launches=st["launches"], warps_per_block=st["warps_per_block"],
+                          item_factor=st["item_factor"])
+    out["systems"] = len(systems)
+    out["subsets"] = int(st["subsets"])
+    out["host_reduce_ms"] = st["host_ms"]
+    out["speedup_batched_vs_per_system"] = out["batched"]["systems_per_s"] / out["per_system"]["systems_per_s"]
+    return out
+
+
+def serve_section(bd, rate=200.0, count=1000, train_count=20000):
+    """Cost model trained on method-generated runs, then a Poisson stream served with continuous
+    batching (n ~ U[12,30], k ~ U[4,10]); p50/p99 latency and degrees/s per admission policy."""
+    import numpy as np
+
+    from workloads import batch_systems, poisson_arrivals
+
+    t0 = time.perf_counter()
+    train = batch_systems(train_count, first_seed=200000, n_range=(12, 30), k_range=(4, 10))
+    b = bd.Batch()
+    for s in train:
+        b.add(s.A)
+    b.prepare()
+    b.run(mode=0)
+    cyc = np.array([r["cycles"] for r in b.results()], dtype=np.float64)
+    X = b.features()
+    keep = cyc > 0
+    X, y = X[keep], np.log2(cyc[keep]).astype(np.float32)
+    ntr = int(0.8 * len(y))
+    model = bd.CostModel(0)
+    model.train(X[:ntr], y[:ntr], epochs=150, batch=256, lr=2e-3, seed=1)
+    mae_model = float(np.mean(np.abs(model.predict(X[ntr:]) - y[ntr:])))
+    cf = X[:, 3].astype(np.float64)
+    A = np.stack([np.ones(ntr), cf[:ntr]], 1)
+    coef, *_ = np.linalg.lstsq(A, y[:ntr], rcond=None)
+    mae_cf = float(np.mean(np.abs(coef[0] + coef[1] * cf[ntr:] - y[ntr:])))
+    train_s = time.perf_counter() - t0
+
+    stream = batch_systems(count, first_seed=300000, n_range=(12, 30), k_range=(4, 10))
+    sb = bd.Batch()
+    for s in stream:
+        sb.add(s.A)
+    sb.prepare()
+    pred = np.exp2(model.predict(sb.features()))
+    arrivals = poisson_arrivals(rate, count, 7)
+    res = {}
+    for label, order, costs in [("fifo", 0, None), ("cost_model_order", 1, pred)]:
+        srv = bd.Server(order=order)
+        lat = []
+        skipped = 0
+        i = 0
+        t1 = time.perf_counter()
+        while i < count or len(lat) + skipped < count:
+            now = time.perf_counter() - t1
+            if i < count and now >= arrivals[i]:
+                try:
+                    srv.submit(stream[i].A, seed=0, predicted_cost=float(costs[i]) if costs is not None else 0.0)
+                except bd.BinodegError:
+                    skipped += 1
+                i += 1
+                continue
+            got = srv.poll()
+            if got:
+                lat.append(got[2])
+            else:
+                time.sleep(0.0001)
+        el = time.perf_counter() - t1
+        srv.stop()
+        lat = np.array(lat)
+        res[label] = dict(degrees_per_s=len(lat) / el, p50_ms=float(np.percentile(lat, 50)),
+                          p99_ms=float(np.percentile(lat, 99)), mean_ms=float(lat.mean()), served=len(lat),
+                          not_served_128bit=skipped)
+    res.update(rate_per_s=rate, requests=count, cost_model=dict(
+        train_runs=int(keep.sum()), mae_log2_runtime_model=mae_model, mae_log2_runtime_closed_form=mae_cf,
+        train_and_data_s=train_s))
+    return res
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -173,7 +273,7 @@ def main():
     stream = torch.cuda.Stream(device=dev)
     bd.set_stream(stream)
 
-    s = config_system(WORKLOAD)
+    s = config_system(args.workload)
     red = bd.reduce(s.A)
     P = red["points"]
     N, k = P.shape
@@ -254,7 +354,7 @@ def main():
     line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
                 ms_per_step=ms_per_step, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="int64",
                 data="synthetic",
-                config=dict(workload=WORKLOAD, n=s.n, m=s.m, k=k, points=N, subsets_per_step=subsets,
+                config=dict(workload=args.workload, n=s.n, m=s.m, k=k, points=N, subsets_per_step=subsets,
                             l2="flushed before each timed step (256 MB device write)", items=info["items"],
                             blocks=info["blocks"], warps_per_block=info["warps_per_block"],
                             int_path="int128" if info["int128"] else "int64", max_abs_coord=red["max_abs_coord"]),
@@ -267,6 +367,9 @@ def main():
                               ops_per_subset=ops_per_subset,
                               note="int64 ops of the plain per-subset method vs INT32 lane peak "
                                    f"({props.multi_processor_count} SMs x 128 lanes x {sm_max:.0f} MHz)"))
+    if rank == 0 and world == 1 and not args.no_batch_serve:
+        line["batch"] = batch_section(bd)
+        line["serve"] = serve_section(bd)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(s, subsets)
     if rank == 0:
