@@ -117,7 +117,7 @@ def run_reference(args, rank, world):
 
     from workloads import config_system
 
-    s = config_system(WORKLOAD)
+    s = config_system(args.workload)
     r = oracle_step(s)
     subsets = comb(s.n + 1, r.dim + 1)
     for _ in range(args.warmup):
@@ -130,7 +130,7 @@ def run_reference(args, rank, world):
     line = dict(impl="reference", metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps,
                 warmup=args.warmup, ms_per_step=1e3 * dt / args.steps, higher_is_better=True, scaling="weak",
                 vs_baseline=None, dtype="exact rationals (Python int)", data="synthetic",
-                config=dict(workload=WORKLOAD, n=s.n, m=s.m, k=r.dim, subsets_per_step=subsets,
+                config=dict(workload=args.workload, n=s.n, m=s.m, k=r.dim, subsets_per_step=subsets,
                             note="each step = one exact degree of the workload by the oracle"),
                 degrees_per_s=args.steps / dt,
                 cpu_baseline=dict(value=value, unit=UNIT, cores=1, kind="oracle",
