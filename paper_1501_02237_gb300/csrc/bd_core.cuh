@@ -252,6 +252,9 @@ struct Acc {
 #endif
 };
 
+// Accumulators are per lane: uniform counts are added by lane 0 only, per-pair results by the
+// lane that decided them; the kernels sum them over the warp before flushing.
+
 BD_HD uint64_t binom(int n, int k) {
   if (k < 0 || n < k) return 0;
   if (k > n - k) k = n - k;
@@ -421,15 +424,16 @@ struct Walker {
 
   // all cells below a state-(K-2) node on the 2-D path (every child c, then every p > c)
   BD_HD void bottom2(Acc& acc) {
+    const bool lead = tm.lane() == 0;
     if (K == 1) {
       const uint64_t cand = build_last(0);
-      acc.singular += (uint64_t)(N - 1 - s[0]) - (uint64_t)popc64(cand);
+      if (lead) acc.singular += (uint64_t)(N - 1 - s[0]) - (uint64_t)popc64(cand);
       leaves2(cand, acc);
       return;
     }
     for (int c = s[K - 2] + 1; c <= N - 2; ++c) {
       const uint64_t cand = build_last(c);
-      acc.singular += (uint64_t)(N - 1 - c) - (uint64_t)popc64(cand);
+      if (lead) acc.singular += (uint64_t)(N - 1 - c) - (uint64_t)popc64(cand);
       if (cand) leaves2(cand, acc);
     }
   }
@@ -441,6 +445,7 @@ struct Walker {
       cand &= cand - 1;
       TL ad;
       const int stt = leaf2(p, mask, ad);
+      if (tm.lane() != 0) continue;  // uniform verdict: counted once per team
       if (stt == ST_ACCEPTED) { acc.cells += 1; acc.nvol += (u128)ad; }
       else if (stt == ST_TIE) acc.ties += 1;
     }
@@ -495,72 +500,73 @@ struct Walker {
     return cs == 0 ? 0 : ((cs == ((Cp < 0 ? -1 : 1) * pc)) ? sig : -sig);
   }
 
+  // Lane l owns the pair (c, p), p = c+1+l (+32 per chunk); it walks the points q in index order
+  // and stops at the first one strictly below; the warp leaves the walk as soon as every lane
+  // has a verdict.  A rejected pair usually meets a point below within a few steps, so this
+  // costs far less than testing every point for every pair.  Per-lane results go into the
+  // lane's own accumulator (summed over the warp by the caller).
   BD_HD void bottom3(Acc& acc) {
     const int o = level_offset(K, K - 2);
-    const int sd = piv[K - 2] < 0 ? -1 : 1;
+    const TC dp = piv[K - 2];
+    const int sd = dp < 0 ? -1 : 1;
     const uint64_t prefix = member_mask(K - 1);
-    // single-precision copies of every point for the uniform reads, and of this lane's own
-    // points (at most two: q0 = lane, q1 = lane + 32) in registers
+    const bool lead = tm.lane() == 0;
     for (int q = tm.lane(); q < N; q += tm.lanes()) {
       fl[q] = f32_of(sc[o * SLOTS + q]);
       fl[SLOTS + q] = f32_of(sc[(o + 1) * SLOTS + q]);
       fl[2 * SLOTS + q] = f32_of(sl[(K - 2) * SLOTS + q]);
     }
     tm.sync();
-    const int q0 = tm.lane(), q1 = tm.lane() + tm.lanes();
-    const bool own0 = q0 < N && !((prefix >> q0) & 1ull);
-    const bool warp = tm.lanes() == 32;  // the host emulation runs every point in the rest loop
-    const bool own1 = warp && q1 < N && !((prefix >> q1) & 1ull);
-    const int rest = warp ? q1 + tm.lanes() : q1;
-    float x0 = 0, y0 = 0, l0 = 0, x1 = 0, y1 = 0, l1 = 0;
-    if (q0 < N) { x0 = fl[q0]; y0 = fl[SLOTS + q0]; l0 = fl[2 * SLOTS + q0]; }
-    if (warp && q1 < N) { x1 = fl[q1]; y1 = fl[SLOTS + q1]; l1 = fl[2 * SLOTS + q1]; }
     for (int c = s[K - 2] + 1; c <= N - 2; ++c) {
       const TC xc = sc[o * SLOTS + c], yc = sc[(o + 1) * SLOTS + c];
       if (xc == 0 && yc == 0) {  // no pivot: every cell through c is singular
-        acc.singular += (uint64_t)(N - 1 - c);
+        if (lead) acc.singular += (uint64_t)(N - 1 - c);
         continue;
       }
       const float xcf = fl[c], ycf = fl[SLOTS + c], lcf = fl[2 * SLOTS + c];
-      for (int p = c + 1; p < N; ++p) {
-        const TC xp = sc[o * SLOTS + p], yp = sc[(o + 1) * SLOTS + p];
-        const W2 d2 = (W2)xc * yp - (W2)yc * xp;
-        if (d2 == 0) {
-          acc.singular += 1;
-          continue;
+      const uint64_t excl = prefix | (1ull << c);
+      for (int pb = c + 1; pb < N; pb += tm.lanes()) {
+        const int p = pb + tm.lane();
+        bool live = p < N;
+        W2 d2 = 0;
+        if (live) {
+          d2 = (W2)xc * sc[(o + 1) * SLOTS + p] - (W2)yc * sc[o * SLOTS + p];
+          if (d2 == 0) {
+            acc.singular += 1;
+            live = false;
+          }
         }
-        const float xpf = fl[p], ypf = fl[SLOTS + p], lpf = fl[2 * SLOTS + p];
-        // n = v_c x v_p and the magnitudes of its terms
-        const float t1 = ycf * lpf, t2 = lcf * ypf, t3 = lcf * xpf, t4 = xcf * lpf, t5 = xcf * ypf, t6 = ycf * xpf;
-        const float nx = t1 - t2, ny = t3 - t4, nz = t5 - t6;
-        const float ax = fabsf(t1) + fabsf(t2), ay = fabsf(t3) + fabsf(t4), az = fabsf(t5) + fabsf(t6);
-        const int sig = (d2 < 0 ? -1 : 1) * sd;  // q is below iff sig * det3 < 0
+        float nx = 0, ny = 0, nz = 0, ax = 0, ay = 0, az = 0;
+        int sig = 1;
+        if (live) {
+          const float xpf = fl[p], ypf = fl[SLOTS + p], lpf = fl[2 * SLOTS + p];
+          const float t1 = ycf * lpf, t2 = lcf * ypf, t3 = lcf * xpf, t4 = xcf * lpf, t5 = xcf * ypf, t6 = ycf * xpf;
+          nx = t1 - t2;
+          ny = t3 - t4;
+          nz = t5 - t6;
+          ax = fabsf(t1) + fabsf(t2);
+          ay = fabsf(t3) + fabsf(t4);
+          az = fabsf(t5) + fabsf(t6);
+          sig = (d2 < 0 ? -1 : 1) * sd;  // q is below iff sig * det3 < 0
+        }
         bool below = false, on = false;
-        if (own0 && q0 != c && q0 != p) {
-          const int sg = side3(c, p, q0, nx, ny, nz, ax, ay, az, x0, y0, l0, sig, xc, yc);
-          on = sg == 0;
-          below = sg != 0 && sg != sig;
-        }
-        if (own1 && q1 != c && q1 != p) {
-          const int sg = side3(c, p, q1, nx, ny, nz, ax, ay, az, x1, y1, l1, sig, xc, yc);
-          on = on || sg == 0;
-          below = below || (sg != 0 && sg != sig);
-        }
-        for (int q = rest; q < N; q += tm.lanes()) {  // host emulation: the remaining points
-          if (((prefix >> q) & 1ull) || q == c || q == p) continue;
+        for (int q = 0; q < N; ++q) {
+          if (tm.all(!live || below)) break;
+          if (!live || below || ((excl >> q) & 1ull) || q == p) continue;
           const int sg = side3(c, p, q, nx, ny, nz, ax, ay, az, fl[q], fl[SLOTS + q], fl[2 * SLOTS + q], sig, xc, yc);
-          on = on || sg == 0;
-          below = below || (sg != 0 && sg != sig);
+          if (sg == 0) on = true;
+          else if (sg != sig) below = true;
         }
-        if (tm.any(below)) continue;
-        if (tm.any(on)) {
-          acc.ties += 1;
-          continue;
+        if (live && !below) {
+          if (on) {
+            acc.ties += 1;
+          } else {
+            acc.cells += 1;
+            const W2 ad = d2 < 0 ? -d2 : d2;
+            const W2 dd = dp < 0 ? -(W2)dp : (W2)dp;
+            acc.nvol += (u128)(ad / dd);  // exact: det2 = p_{K-2} * C_p
+          }
         }
-        acc.cells += 1;
-        const W2 ad = d2 < 0 ? -d2 : d2;
-        const W2 dd = piv[K - 2] < 0 ? -(W2)piv[K - 2] : (W2)piv[K - 2];
-        acc.nvol += (u128)(ad / dd);  // exact: det2 = p_{K-2} * C_p
       }
     }
   }
@@ -575,9 +581,10 @@ struct Walker {
     const int L = it.len;
     const int B = bottom_depth();
     start(it.idx[0]);
+    const bool lead = tm.lane() == 0;  // uniform counts are added once per team
     for (int j = 1; j < L; ++j) {
       if (!build(j, it.idx[j])) {
-        acc.singular += subtree_size(N, K, it.idx[L - 1], L);
+        if (lead) acc.singular += subtree_size(N, K, it.idx[L - 1], L);
         return;
       }
     }
@@ -596,7 +603,7 @@ struct Walker {
         continue;
       }
       if (!build(j, c)) {
-        acc.singular += binom(N - 1 - c, K - j);
+        if (lead) acc.singular += binom(N - 1 - c, K - j);
         continue;
       }
       ++j;

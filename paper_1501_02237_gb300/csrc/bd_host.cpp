@@ -569,6 +569,7 @@ struct HostTeam {
   int lane() const { return 0; }
   int lanes() const { return 1; }
   bool any(bool b) const { return b; }
+  bool all(bool b) const { return b; }
   void sync() const {}
   uint64_t or_all(uint64_t x) const { return x; }
 };

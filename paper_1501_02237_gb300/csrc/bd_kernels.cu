@@ -36,6 +36,13 @@ struct WarpTeam {
     __syncwarp();
 #endif
   }
+  BD_HD bool all(bool b) const {
+#ifdef __CUDA_ARCH__
+    return __all_sync(0xffffffffu, b);
+#else
+    return b;
+#endif
+  }
   BD_HD uint64_t or_all(uint64_t x) const {
 #ifdef __CUDA_ARCH__
     const unsigned lo = __reduce_or_sync(0xffffffffu, (unsigned)x);
@@ -89,6 +96,19 @@ __device__ void load_points(int64_t* P, const EnumParams& p) {
   __syncthreads();
 }
 
+// sum of the lanes' accumulators, valid in lane 0
+__device__ Acc warp_sum(Acc a) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long lo = __shfl_down_sync(0xffffffffu, (unsigned long long)(uint64_t)a.nvol, o);
+    const unsigned long long hi = __shfl_down_sync(0xffffffffu, (unsigned long long)(uint64_t)(a.nvol >> 64), o);
+    a.nvol += ((u128)hi << 64) | lo;
+    a.cells += __shfl_down_sync(0xffffffffu, (unsigned long long)a.cells, o);
+    a.singular += __shfl_down_sync(0xffffffffu, (unsigned long long)a.singular, o);
+    a.ties += __shfl_down_sync(0xffffffffu, (unsigned long long)a.ties, o);
+  }
+  return a;
+}
+
 __device__ void flush(const Acc& a, DevAcc* g, unsigned long long items) {
   const unsigned long long lo = (unsigned long long)(uint64_t)a.nvol;
   const unsigned long long hi = (unsigned long long)(uint64_t)(a.nvol >> 64);
@@ -124,6 +144,7 @@ __global__ void BD_ENUM_BOUNDS k_enumerate(EnumParams p) {
     W.run_item(it, acc);
     ++done;
   }
+  acc = warp_sum(acc);
   if (lane == 0) flush(acc, p.acc, done);
 }
 
@@ -273,7 +294,10 @@ __global__ void BD_ENUM_BOUNDS k_batch(BatchParams p) {
     if (i >= (unsigned int)p.nitems) break;
     const BatchItem bi = p.items[i];
     if ((int)bi.sys != cur) {
-      if (cur >= 0 && lane == 0) flush_sys(acc, items, cyc, p, cur);
+      if (cur >= 0) {
+        const Acc s = warp_sum(acc);
+        if (lane == 0) flush_sys(s, items, cyc, p, cur);
+      }
       acc = Acc{};
       items = cyc = 0;
       cur = (int)bi.sys;
@@ -297,7 +321,10 @@ __global__ void BD_ENUM_BOUNDS k_batch(BatchParams p) {
     cyc += (unsigned long long)(clock64() - t0);
     ++items;
   }
-  if (cur >= 0 && lane == 0) flush_sys(acc, items, cyc, p, cur);
+  if (cur >= 0) {
+    const Acc s = warp_sum(acc);
+    if (lane == 0) flush_sys(s, items, cyc, p, cur);
+  }
 }
 
 template <class TC, class TL>
@@ -430,6 +457,7 @@ __global__ void BD_ENUM_BOUNDS k_serve(ServeParams p) {
     if (path == PATH_NARROW) serve_item<int32_t, int64_t>(tm, P, N, K, slots, stack, p.maxK, it, acc);
     else serve_item<int64_t, int64_t>(tm, P, N, K, slots, stack, p.maxK, it, acc);
     const unsigned long long cyc = (unsigned long long)(clock64() - t0);
+    acc = warp_sum(acc);
     if (lane == 0) {
       flush(acc, p.acc + slot, 1);
       atomicAdd(p.cycles + slot, cyc);
