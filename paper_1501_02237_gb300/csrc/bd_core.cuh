@@ -235,6 +235,11 @@ BD_HD int cross_sign_filtered(float af, float bf, float cf, float df) {
 // work items and per-team accumulators
 // ---------------------------------------------------------------------------------------------
 constexpr int KMAX = 14;           // largest lattice dimension K (a work item is 16 bytes)
+
+// points tested per warp vote in the bottom stage
+#ifndef BD_QUNROLL
+#define BD_QUNROLL 1
+#endif
 constexpr int NMAX = 64;           // largest number of points (one 64-bit membership mask)
 
 struct Item {                      // a subset prefix s_0 < .. < s_{L-1}, 1 <= L <= K
@@ -249,6 +254,7 @@ struct Acc {
   uint64_t ties;     // subsets with no point below and at least one point on the hyperplane
 #ifdef BD_COUNT
   uint64_t builds[KMAX + 1], fails[KMAX + 1], leaves, leaf_singular, exact_fallbacks;
+  uint64_t bottoms, cs, pairs, qtests, qmax_sum;
 #endif
 };
 
@@ -525,6 +531,10 @@ struct Walker {
       }
       const float xcf = fl[c], ycf = fl[SLOTS + c], lcf = fl[2 * SLOTS + c];
       const uint64_t excl = prefix | (1ull << c);
+#ifdef BD_COUNT
+      uint64_t cmax = 0;
+      if (cnt) cnt->cs++;
+#endif
       for (int pb = c + 1; pb < N; pb += tm.lanes()) {
         const int p = pb + tm.lane();
         bool live = p < N;
@@ -550,13 +560,28 @@ struct Walker {
           sig = (d2 < 0 ? -1 : 1) * sd;  // q is below iff sig * det3 < 0
         }
         bool below = false, on = false;
-        for (int q = 0; q < N; ++q) {
+#ifdef BD_COUNT
+        int qt = 0;
+#endif
+        // BD_QUNROLL points per vote: independent tests overlap their latencies
+        for (int q0 = 0; q0 < N; q0 += BD_QUNROLL) {
           if (tm.all(!live || below)) break;
-          if (!live || below || ((excl >> q) & 1ull) || q == p) continue;
-          const int sg = side3(c, p, q, nx, ny, nz, ax, ay, az, fl[q], fl[SLOTS + q], fl[2 * SLOTS + q], sig, xc, yc);
-          if (sg == 0) on = true;
-          else if (sg != sig) below = true;
+#ifdef BD_COUNT
+          if (live && !below) qt += BD_QUNROLL;
+#endif
+          if (!live || below) continue;
+#pragma unroll
+          for (int u = 0; u < BD_QUNROLL; ++u) {
+            const int q = q0 + u;
+            if (q >= N || ((excl >> q) & 1ull) || q == p) continue;
+            const int sg = side3(c, p, q, nx, ny, nz, ax, ay, az, fl[q], fl[SLOTS + q], fl[2 * SLOTS + q], sig, xc, yc);
+            if (sg == 0) on = true;
+            else if (sg != sig) below = true;
+          }
         }
+#ifdef BD_COUNT
+        if (cnt && live) { cnt->pairs++; cnt->qtests += qt; if ((uint64_t)qt > cmax) cmax = qt; }
+#endif
         if (live && !below) {
           if (on) {
             acc.ties += 1;
@@ -568,6 +593,9 @@ struct Walker {
           }
         }
       }
+#ifdef BD_COUNT
+      if (cnt) cnt->qmax_sum += cmax;
+#endif
     }
   }
 

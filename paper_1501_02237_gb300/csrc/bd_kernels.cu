@@ -60,7 +60,10 @@ __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t
 __host__ __device__ inline int slots_of(int N) { return (N + 3) & ~3; }
 
 // at most 256 threads per block and at least 3 resident blocks: about 85 registers per thread
-#define BD_ENUM_BOUNDS __launch_bounds__(256, 3)
+#ifndef BD_LB_BLOCKS
+#define BD_LB_BLOCKS 3
+#endif
+#define BD_ENUM_BOUNDS __launch_bounds__(256, BD_LB_BLOCKS)
 
 // one warp's shared memory: its coordinate-minor stack, lift-minor stack and three float rows
 // for the single-precision filters, each 16-byte aligned
