@@ -254,15 +254,35 @@ struct Acc {
   uint64_t ties;     // subsets with no point below and at least one point on the hyperplane
 #ifdef BD_COUNT
   uint64_t builds[KMAX + 1], fails[KMAX + 1], leaves, leaf_singular, exact_fallbacks;
-  uint64_t bottoms, cs, pairs, qtests, qmax_sum;
+  uint64_t bottoms, pairs, qtests;
 #endif
 };
 
 // Accumulators are per lane: uniform counts are added by lane 0 only, per-pair results by the
 // lane that decided them; the kernels sum them over the warp before flushing.
 
+// Binomial coefficients C(n, k), n <= 64, k <= 15, by Pascal's rule at compile time; the device
+// reads them from constant memory (a division loop costs dozens of instructions per step there).
+struct BinomTable {
+  uint64_t v[NMAX + 1][KMAX + 2];
+};
+constexpr BinomTable make_binom_table() {
+  BinomTable t{};
+  for (int n = 0; n <= NMAX; ++n) {
+    t.v[n][0] = 1;
+    for (int k = 1; k <= KMAX + 1; ++k) t.v[n][k] = n == 0 ? 0 : t.v[n - 1][k - 1] + t.v[n - 1][k];
+  }
+  return t;
+}
+#ifdef __CUDACC__
+static __constant__ BinomTable c_binom = make_binom_table();
+#endif
+
 BD_HD uint64_t binom(int n, int k) {
   if (k < 0 || n < k) return 0;
+#ifdef __CUDA_ARCH__
+  if (n <= NMAX && k <= KMAX + 1) return c_binom.v[n][k];
+#endif
   if (k > n - k) k = n - k;
   uint64_t r = 1;
   for (int i = 1; i <= k; ++i) r = r * (uint64_t)(n - k + i) / (uint64_t)i;
@@ -506,96 +526,86 @@ struct Walker {
     return cs == 0 ? 0 : ((cs == ((Cp < 0 ? -1 : 1) * pc)) ? sig : -sig);
   }
 
-  // Lane l owns the pair (c, p), p = c+1+l (+32 per chunk); it walks the points q in index order
-  // and stops at the first one strictly below; the warp leaves the walk as soon as every lane
-  // has a verdict.  A rejected pair usually meets a point below within a few steps, so this
-  // costs far less than testing every point for every pair.  Per-lane results go into the
-  // lane's own accumulator (summed over the warp by the caller).
+  // The pairs (c, p), s_{K-2} < c < p < N, are taken in lexicographic order, one per lane and a
+  // warp-width of them per round; each lane walks the points q in index order and stops at the
+  // first one strictly below its cell, and the round ends when every lane has a verdict.  A
+  // rejected pair usually meets a point below within a few steps, so this costs far less than
+  // testing every point for every pair.  Per-lane results go into the lane's own accumulator
+  // (summed over the warp by the caller).
   BD_HD void bottom3(Acc& acc) {
     const int o = level_offset(K, K - 2);
     const TC dp = piv[K - 2];
     const int sd = dp < 0 ? -1 : 1;
     const uint64_t prefix = member_mask(K - 1);
-    const bool lead = tm.lane() == 0;
     for (int q = tm.lane(); q < N; q += tm.lanes()) {
       fl[q] = f32_of(sc[o * SLOTS + q]);
       fl[SLOTS + q] = f32_of(sc[(o + 1) * SLOTS + q]);
       fl[2 * SLOTS + q] = f32_of(sl[(K - 2) * SLOTS + q]);
     }
     tm.sync();
-    for (int c = s[K - 2] + 1; c <= N - 2; ++c) {
-      const TC xc = sc[o * SLOTS + c], yc = sc[(o + 1) * SLOTS + c];
-      if (xc == 0 && yc == 0) {  // no pivot: every cell through c is singular
-        if (lead) acc.singular += (uint64_t)(N - 1 - c);
-        continue;
+    // this lane's pair: the lane-th pair, then every lanes()-th one
+    int c = s[K - 2] + 1, p = c + 1 + tm.lane();
+    for (;;) {
+      while (p >= N && c < N - 2) {  // carry into the next c: N-1-c pairs per c
+        p -= N - c - 2;
+        ++c;
       }
-      const float xcf = fl[c], ycf = fl[SLOTS + c], lcf = fl[2 * SLOTS + c];
-      const uint64_t excl = prefix | (1ull << c);
-#ifdef BD_COUNT
-      uint64_t cmax = 0;
-      if (cnt) cnt->cs++;
-#endif
-      for (int pb = c + 1; pb < N; pb += tm.lanes()) {
-        const int p = pb + tm.lane();
-        bool live = p < N;
-        W2 d2 = 0;
-        if (live) {
-          d2 = (W2)xc * sc[(o + 1) * SLOTS + p] - (W2)yc * sc[o * SLOTS + p];
-          if (d2 == 0) {
-            acc.singular += 1;
-            live = false;
-          }
-        }
-        float nx = 0, ny = 0, nz = 0, ax = 0, ay = 0, az = 0;
-        int sig = 1;
-        if (live) {
-          const float xpf = fl[p], ypf = fl[SLOTS + p], lpf = fl[2 * SLOTS + p];
-          const float t1 = ycf * lpf, t2 = lcf * ypf, t3 = lcf * xpf, t4 = xcf * lpf, t5 = xcf * ypf, t6 = ycf * xpf;
-          nx = t1 - t2;
-          ny = t3 - t4;
-          nz = t5 - t6;
-          ax = fabsf(t1) + fabsf(t2);
-          ay = fabsf(t3) + fabsf(t4);
-          az = fabsf(t5) + fabsf(t6);
-          sig = (d2 < 0 ? -1 : 1) * sd;  // q is below iff sig * det3 < 0
-        }
-        bool below = false, on = false;
-#ifdef BD_COUNT
-        int qt = 0;
-#endif
-        // BD_QUNROLL points per vote: independent tests overlap their latencies
-        for (int q0 = 0; q0 < N; q0 += BD_QUNROLL) {
-          if (tm.all(!live || below)) break;
-#ifdef BD_COUNT
-          if (live && !below) qt += BD_QUNROLL;
-#endif
-          if (!live || below) continue;
-#pragma unroll
-          for (int u = 0; u < BD_QUNROLL; ++u) {
-            const int q = q0 + u;
-            if (q >= N || ((excl >> q) & 1ull) || q == p) continue;
-            const int sg = side3(c, p, q, nx, ny, nz, ax, ay, az, fl[q], fl[SLOTS + q], fl[2 * SLOTS + q], sig, xc, yc);
-            if (sg == 0) on = true;
-            else if (sg != sig) below = true;
-          }
-        }
-#ifdef BD_COUNT
-        if (cnt && live) { cnt->pairs++; cnt->qtests += qt; if ((uint64_t)qt > cmax) cmax = qt; }
-#endif
-        if (live && !below) {
-          if (on) {
-            acc.ties += 1;
-          } else {
-            acc.cells += 1;
-            const W2 ad = d2 < 0 ? -d2 : d2;
-            const W2 dd = dp < 0 ? -(W2)dp : (W2)dp;
-            acc.nvol += (u128)(ad / dd);  // exact: det2 = p_{K-2} * C_p
-          }
+      bool live = p < N;
+      if (!tm.any(live)) break;
+      W2 d2 = 0;
+      TC xc = 0, yc = 0;
+      float nx = 0, ny = 0, nz = 0, ax = 0, ay = 0, az = 0;
+      int sig = 1;
+      if (live) {
+        xc = sc[o * SLOTS + c];
+        yc = sc[(o + 1) * SLOTS + c];
+        d2 = (W2)xc * sc[(o + 1) * SLOTS + p] - (W2)yc * sc[o * SLOTS + p];
+        if (d2 == 0) {  // also every pair whose c has no pivot left
+          acc.singular += 1;
+          live = false;
         }
       }
+      if (live) {
+        const float xcf = fl[c], ycf = fl[SLOTS + c], lcf = fl[2 * SLOTS + c];
+        const float xpf = fl[p], ypf = fl[SLOTS + p], lpf = fl[2 * SLOTS + p];
+        const float t1 = ycf * lpf, t2 = lcf * ypf, t3 = lcf * xpf, t4 = xcf * lpf, t5 = xcf * ypf, t6 = ycf * xpf;
+        nx = t1 - t2;
+        ny = t3 - t4;
+        nz = t5 - t6;
+        ax = fabsf(t1) + fabsf(t2);
+        ay = fabsf(t3) + fabsf(t4);
+        az = fabsf(t5) + fabsf(t6);
+        sig = (d2 < 0 ? -1 : 1) * sd;  // q is below iff sig * det3 < 0
+      }
+      const uint64_t excl = prefix | (1ull << c) | (1ull << (live ? p : c));
+      bool below = false, on = false;
 #ifdef BD_COUNT
-      if (cnt) cnt->qmax_sum += cmax;
+      int qt = 0;
 #endif
+      for (int q = 0; q < N; ++q) {
+        if (tm.all(!live || below)) break;
+        if (!live || below || ((excl >> q) & 1ull)) continue;
+#ifdef BD_COUNT
+        ++qt;
+#endif
+        const int sg = side3(c, p, q, nx, ny, nz, ax, ay, az, fl[q], fl[SLOTS + q], fl[2 * SLOTS + q], sig, xc, yc);
+        if (sg == 0) on = true;
+        else if (sg != sig) below = true;
+      }
+#ifdef BD_COUNT
+      if (cnt && live) { cnt->pairs++; cnt->qtests += qt; }
+#endif
+      if (live && !below) {
+        if (on) {
+          acc.ties += 1;
+        } else {
+          acc.cells += 1;
+          const W2 ad = d2 < 0 ? -d2 : d2;
+          const W2 dd = dp < 0 ? -(W2)dp : (W2)dp;
+          acc.nvol += (u128)(ad / dd);  // exact: det2 = p_{K-2} * C_p
+        }
+      }
+      p += tm.lanes();
     }
   }
 
