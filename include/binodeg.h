@@ -307,10 +307,11 @@ int bd_volume_noalloc(const int64_t* points, int32_t npts, int32_t k, uint64_t s
 /* ---- host emulation (CPU tests and the native CPU baseline; never used by the calls above) */
 
 /* Runs the same lower-facet enumeration as the GPU kernel on |threads| CPU threads, with
- * the given lifts (no re-lift); a negative count forces the 128-bit path.  Returns
- * BD_ERR_TIES when the lifting has a tie. */
+ * the given lifts (no re-lift); a negative count forces the 128-bit path.  item_subsets is
+ * the work-item split threshold in subsets (0: 4096; 1 splits every prefix down to the
+ * deepest item level).  Returns BD_ERR_TIES when the lifting has a tie. */
 int bd_host_volume_lifted(const int64_t* points, const int64_t* lifts, int32_t npts, int32_t k,
-                          int32_t threads, bd_volume_out* out);
+                          int32_t threads, uint64_t item_subsets, bd_volume_out* out);
 
 #ifdef __cplusplus
 }

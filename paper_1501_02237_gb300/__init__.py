@@ -102,14 +102,15 @@ def classify(points, lifts, subsets) -> tuple:
     return status, absdet
 
 
-def host_volume_lifted(points, lifts, threads: int = 1, force_int128: bool = False) -> dict:
+def host_volume_lifted(points, lifts, threads: int = 1, force_int128: bool = False, item_subsets: int = 0) -> dict:
     """bd_host_volume_lifted: CPU emulation of the enumeration (CPU tests and the native baseline).
-    force_int128 runs the 128-bit walker (a negative thread count at the C ABI)."""
+    force_int128 runs the 128-bit walker (a negative thread count at the C ABI); item_subsets is
+    the work-item split threshold (0: the library's default)."""
     P, W = i64(points), i64(lifts)
     npts, k = P.shape
     out = VolumeOut()
     t = -max(1, threads) if force_int128 else threads
-    rc = lib().bd_host_volume_lifted(ptr(P), ptr(W), npts, k, t, C.byref(out))
+    rc = lib().bd_host_volume_lifted(ptr(P), ptr(W), npts, k, t, item_subsets, C.byref(out))
     res = out.as_dict()
     res["status"] = rc
     if rc not in (0, 3):

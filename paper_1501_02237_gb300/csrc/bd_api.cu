@@ -532,7 +532,7 @@ int bd_classify(const int64_t* points, const int64_t* lifts, int32_t npts, int32
 }
 
 int bd_host_volume_lifted(const int64_t* points, const int64_t* lifts, int32_t npts, int32_t k, int32_t threads,
-                          bd_volume_out* out) {
+                          uint64_t item_subsets, bd_volume_out* out) {
   if (!out || !lifts) return fail(BD_ERR_ARG, "NULL argument");
   int rc = check_points(points, npts, k);
   if (rc) return rc;
@@ -558,7 +558,7 @@ int bd_host_volume_lifted(const int64_t* points, const int64_t* lifts, int32_t n
     for (int c = 0; c < k; ++c) P[(size_t)c * npts + q] = points[(size_t)q * k + c];
     P[(size_t)k * npts + q] = lifts[q];
   }
-  const auto items = bd::build_items(npts, k, 4096);
+  const auto items = bd::build_items(npts, k, item_subsets ? item_subsets : 4096);
   bd::Acc acc{};
   bd::host_enumerate(path, P.data(), npts, k, items, std::max(1, threads), acc);
   std::memset(out, 0, sizeof(*out));

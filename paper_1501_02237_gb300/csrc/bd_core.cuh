@@ -236,13 +236,9 @@ BD_HD int cross_sign_filtered(float af, float bf, float cf, float df) {
 // ---------------------------------------------------------------------------------------------
 constexpr int KMAX = 14;           // largest lattice dimension K (a work item is 16 bytes)
 
-// points tested per warp vote in the bottom stage
-#ifndef BD_QUNROLL
-#define BD_QUNROLL 1
-#endif
 constexpr int NMAX = 64;           // largest number of points (one 64-bit membership mask)
 
-struct Item {                      // a subset prefix s_0 < .. < s_{L-1}, 1 <= L <= K
+struct Item {                      // a subset prefix s_0 < .. < s_{L-1}, 1 <= L <= max(K-2, 1)
   uint8_t len;
   uint8_t idx[15];
 };
@@ -327,7 +323,7 @@ struct Walker {
   int N, K, SLOTS;
   TC* sc;           // coordinate minors: (level j, entry e, point q) at sc[(off_j + e) * SLOTS + q]
   TL* sl;           // lift minor of level j for point q at sl[j * SLOTS + q]
-  float* fl;        // single-precision copies for the filters: 3 rows of SLOTS floats
+  float* fl;        // single-precision copies for the filters: 4 rows of SLOTS floats
   int s[KMAX + 1];  // chosen indices s_0 .. s_j
   Div dv[KMAX];     // exact divider by the pivot of each level (dv[0]: by 1)
   TC piv[KMAX];     // the pivots p_j (piv[0] = 1)
@@ -339,11 +335,13 @@ struct Walker {
   BD_HD Walker(Team& t, const int64_t* P_, int N_, int K_, int SLOTS_, TC* sc_, TL* sl_, float* fl_)
       : tm(t), P(P_), N(N_), K(K_), SLOTS(SLOTS_), sc(sc_), sl(sl_), fl(fl_) {}
 
-  // the 3-D test runs for the int32 and int64 coordinate paths; the 128-bit path and K = 1 use
-  // the 2-D test on the fully reduced state
-  static constexpr bool kUse3D = sizeof(TL) == 8;
-  // the bottom stage runs on state K-2 (both tests finish the last two levels themselves)
-  BD_HD int bottom_depth() const { return K >= 2 ? K - 1 : 1; }
+  // the single-precision filtered tests run for the int32 and int64 coordinate paths: the 4-D
+  // test on state K-3 when K >= 3, the 3-D test on state 0 when K = 2; the 128-bit path and
+  // K = 1 use the 2-D test on the fully reduced state
+  static constexpr bool kFiltered = sizeof(TL) == 8;
+  // DFS depth at which the bottom stage takes over (the chosen prefix is s_0 .. s_{depth-1}):
+  // the 4-D test finishes the last three levels, the 3-D and 2-D tests the last two
+  BD_HD int bottom_depth() const { return kFiltered && K >= 3 ? K - 2 : (K >= 2 ? K - 1 : 1); }
 
   // state 0: lifted differences z_q = (a_q - a_{s_0}, w_q - w_{s_0})
   BD_HD void start(int s0) {
@@ -609,8 +607,187 @@ struct Walker {
     }
   }
 
+  // ---------------------------------------------------------------------------------------
+  // 4-D test on state K-3.  Each point is v_q = (x_q, y_q, z_q, l_q) (three coordinate minors
+  // and the lift minor, all scaled by the pivot p_{K-3}).  For a triple c1 < c < p the simplex
+  // {s_0 .. s_{K-3}, c1, c, p} is full-dimensional iff D = det3(x, y, z of c1, c, p) != 0, and
+  // then its normalized volume is |D| / p_{K-3}^2 (Sylvester's identity).  The lifted hyperplane
+  // through its vertices has height det4(v_c1, v_c, v_p, v_q) / D above q (in the scaled
+  // coordinates), so q lies strictly below the lifted cell iff
+  //     sign(D) sign(p_{K-3}) det4(v_c1, v_c, v_p, v_q) < 0.
+  // det4 = n . v_q with n the cofactor vector of the rows c1, c, p, evaluated in single
+  // precision with a rigorous error bound; undecided signs take two exact Bareiss steps
+  // (pivot rows c1, then c) and the 2-D rule, as the 2-D path would.
+  // ---------------------------------------------------------------------------------------
+
+  // level K-2 values of point x after the Bareiss step with pivot row c1 on state K-3 (two
+  // coordinate minors X, Y and the lift minor L); a is c1's pivot, pi its column (-1: none)
+  BD_HD void level_after(int c1, int x, TC& X, TC& Y, TL& L, TC& a, int& pi) const {
+    const int o = level_offset(K, K - 3);
+    pi = -1;
+    for (int e = 0; e < 3; ++e)
+      if (sc[(o + e) * SLOTS + c1] != 0) { pi = e; break; }
+    if (pi < 0) { X = Y = 0; L = 0; a = 0; return; }
+    a = sc[(o + pi) * SLOTS + c1];
+    const TC bq = sc[(o + pi) * SLOTS + x];
+    const int r0 = pi == 0 ? 1 : 0, r1 = pi == 2 ? 1 : 2;
+    const Div& D = dv[K - 3];
+    X = bareiss(sc[(o + r0) * SLOTS + x], a, bq, sc[(o + r0) * SLOTS + c1], D);
+    Y = bareiss(sc[(o + r1) * SLOTS + x], a, bq, sc[(o + r1) * SLOTS + c1], D);
+    L = bareiss(sl[(K - 3) * SLOTS + x], a, bq, sl[(K - 3) * SLOTS + c1], D);
+  }
+
+  // exact K x K minor of {s_0 .. s_{K-3}, c1, c, p} with the sign of D (the coordinate det3 on
+  // state K-3): moving c1's pivot column pi to the front permutes the columns by (-1)^pi
+  BD_COLD W2 exact_minor(int c1, int c, int p) const {
+    TC Xc, Yc, Xp, Yp, a;
+    TL Lc, Lp;
+    int pi;
+    level_after(c1, c, Xc, Yc, Lc, a, pi);
+    if (pi < 0) return 0;
+    level_after(c1, p, Xp, Yp, Lp, a, pi);
+    const W2 m = ((W2)Xc * Yp - (W2)Yc * Xp) / (W2)a;  // exact
+    return pi == 1 ? -m : m;
+  }
+
+  // exact side of q for the nonsingular triple (c1, c, p), in the convention of sig (0 on the
+  // hyperplane, sig above, -sig below)
+  BD_COLD int side4_exact(int c1, int c, int p, int q, int sig) const {
+    TC Xc, Yc, Xp, Yp, Xq, Yq, a;
+    TL Lc, Lp, Lq;
+    int pi;
+    level_after(c1, c, Xc, Yc, Lc, a, pi);
+    level_after(c1, p, Xp, Yp, Lp, a, pi);
+    level_after(c1, q, Xq, Yq, Lq, a, pi);
+    const Div D = make_div(a);
+    const bool px = Xc != 0;  // c's pivot column on state K-2
+    const TC b = px ? Xc : Yc, ob = px ? Yc : Xc;
+    const TL Cp = (TL)bareiss(px ? Yp : Xp, b, px ? Xp : Yp, ob, D);
+    const TL Cq = (TL)bareiss(px ? Yq : Xq, b, px ? Xq : Yq, ob, D);
+    const TL Mp = bareiss(Lp, b, px ? Xp : Yp, Lc, D);
+    const TL Mq = bareiss(Lq, b, px ? Xq : Yq, Lc, D);
+    const int cs = cross_sign(Cp, Mq, Cq, Mp);
+    if (cs == 0) return 0;
+    const bool below = cs != (Cp < 0 ? -1 : 1) * (b < 0 ? -1 : 1);  // the 2-D rule
+    return below ? -sig : sig;
+  }
+
+  // The triples (c1, c, p), s_{K-3} < c1 < c < p < N, are dealt to lanes in lexicographic
+  // order, a warp-width per round; each lane walks the points q in index order and stops at
+  // the first one strictly below its cell; the round ends when every lane has a verdict.
+  BD_HD void bottom4(Acc& acc) {
+    const int o = level_offset(K, K - 3);
+    const int sd = piv[K - 3] < 0 ? -1 : 1;
+    const uint64_t prefix = member_mask(K - 2);
+    for (int q = tm.lane(); q < N; q += tm.lanes()) {
+      fl[q] = f32_of(sc[o * SLOTS + q]);
+      fl[SLOTS + q] = f32_of(sc[(o + 1) * SLOTS + q]);
+      fl[2 * SLOTS + q] = f32_of(sc[(o + 2) * SLOTS + q]);
+      fl[3 * SLOTS + q] = f32_of(sl[(K - 3) * SLOTS + q]);
+    }
+    tm.sync();
+    // Error bounds, u = 2^-24: every term of det4 is a product of four point copies (2u each,
+    // f32_of) through at most nine roundings (2x2 minor: product and difference; cofactor:
+    // product and two sums; det4: product and three sums), so |error| <= 17.001u T with T the
+    // sum of the magnitudes of all 24 terms; T evaluated in single precision (same depth, one
+    // more rounding for the scale) is at least (1 - 19u) T, so eps = 2^-19 = 32u covers it with
+    // a factor ~1.9 to spare.  The cofactor det3 (11u) uses the same eps.  Below 2^23 every
+    // operand and partial result is an integer held exactly, and the single-precision value is
+    // the exact one.
+    const float eps = 1.9073486328125e-6f;  // 2^-19
+    int c1 = s[K - 3] + 1, c = c1 + 1, p = c + 1 + tm.lane();
+    for (;;) {
+      for (;;) {  // carry: N-1-c pairs per c, then the next c1
+        if (p < N) break;
+        if (c < N - 2) {
+          p -= N - c - 2;
+          ++c;
+          continue;
+        }
+        if (c1 < N - 3) {
+          const int off = p - N;
+          ++c1;
+          c = c1 + 1;
+          p = c + 1 + off;
+          continue;
+        }
+        break;
+      }
+      bool live = p < N;
+      if (!tm.any(live)) break;
+      float n0 = 0, n1 = 0, n2 = 0, n3 = 0, e0 = 0, e1 = 0, e2 = 0, e3 = 0;
+      int sig = 1, s3 = 0;
+      if (live) {
+        const float a0 = fl[c1], a1 = fl[SLOTS + c1], a2 = fl[2 * SLOTS + c1], a3 = fl[3 * SLOTS + c1];
+        const float u0 = fl[c], u1 = fl[SLOTS + c], u2 = fl[2 * SLOTS + c], u3 = fl[3 * SLOTS + c];
+        const float w0 = fl[p], w1 = fl[SLOTS + p], w2 = fl[2 * SLOTS + p], w3 = fl[3 * SLOTS + p];
+        // 2x2 minors of rows (c, p) and their magnitude sums
+        const float m01 = u0 * w1 - u1 * w0, m02 = u0 * w2 - u2 * w0, m12 = u1 * w2 - u2 * w1;
+        const float M01 = fabsf(u0 * w1) + fabsf(u1 * w0), M02 = fabsf(u0 * w2) + fabsf(u2 * w0),
+                    M12 = fabsf(u1 * w2) + fabsf(u2 * w1);
+        const float D3 = a0 * m12 - a1 * m02 + a2 * m01;
+        const float B3 = fabsf(a0) * M12 + fabsf(a1) * M02 + fabsf(a2) * M01;
+        if (fabsf(D3) > eps * B3 || B3 < 8388608.0f) s3 = (D3 > 0) - (D3 < 0);
+        else {
+          const W2 m = exact_minor(c1, c, p);
+          s3 = (m > 0) - (m < 0);
+        }
+        if (s3 == 0) {
+          acc.singular += 1;
+          live = false;
+        } else {
+          const float m03 = u0 * w3 - u3 * w0, m13 = u1 * w3 - u3 * w1, m23 = u2 * w3 - u3 * w2;
+          const float M03 = fabsf(u0 * w3) + fabsf(u3 * w0), M13 = fabsf(u1 * w3) + fabsf(u3 * w1),
+                      M23 = fabsf(u2 * w3) + fabsf(u3 * w2);
+          // det4(c1, c, p, q) = -q0 D0 + q1 D1 - q2 D2 + q3 D3, D_i the det3 without column i
+          n0 = -(a1 * m23 - a2 * m13 + a3 * m12);
+          n1 = a0 * m23 - a2 * m03 + a3 * m02;
+          n2 = -(a0 * m13 - a1 * m03 + a3 * m01);
+          n3 = D3;
+          e0 = eps * (fabsf(a1) * M23 + fabsf(a2) * M13 + fabsf(a3) * M12);
+          e1 = eps * (fabsf(a0) * M23 + fabsf(a2) * M03 + fabsf(a3) * M02);
+          e2 = eps * (fabsf(a0) * M13 + fabsf(a1) * M03 + fabsf(a3) * M01);
+          e3 = eps * B3;
+          sig = s3 * sd;  // q is below iff sig * det4 < 0
+        }
+      }
+      const uint64_t excl = prefix | (1ull << c1) | (1ull << c) | (live ? 1ull << p : 0ull);
+      bool below = false, on = false;
+#ifdef BD_COUNT
+      int qt = 0;
+#endif
+      for (int q = 0; q < N; ++q) {
+        if (tm.all(!live || below)) break;
+        if (!live || below || ((excl >> q) & 1ull)) continue;
+#ifdef BD_COUNT
+        ++qt;
+#endif
+        const float x0 = fl[q], x1 = fl[SLOTS + q], x2 = fl[2 * SLOTS + q], x3 = fl[3 * SLOTS + q];
+        const float v = fmaf(n0, x0, fmaf(n1, x1, fmaf(n2, x2, n3 * x3)));
+        const float bound = fmaf(e0, fabsf(x0), fmaf(e1, fabsf(x1), fmaf(e2, fabsf(x2), e3 * fabsf(x3))));
+        const int sg = v > bound ? 1 : (v < -bound ? -1 : side4_exact(c1, c, p, q, sig));
+        if (sg == 0) on = true;
+        else if (sg != sig) below = true;
+      }
+#ifdef BD_COUNT
+      if (cnt && live) { cnt->pairs++; cnt->qtests += qt; }
+#endif
+      if (live && !below) {
+        if (on) {
+          acc.ties += 1;
+        } else {
+          acc.cells += 1;
+          const W2 m = exact_minor(c1, c, p);
+          acc.nvol += (u128)(m < 0 ? -m : m);
+        }
+      }
+      p += tm.lanes();
+    }
+  }
+
   BD_HD void bottom(Acc& acc) {
-    if (kUse3D && K >= 2) bottom3(acc);
+    if (kFiltered && K >= 3) bottom4(acc);
+    else if (kFiltered && K == 2) bottom3(acc);
     else bottom2(acc);
   }
 

@@ -506,7 +506,8 @@ bool for_each_item(int N, int K, uint64_t max_subsets, Emit emit) {
   pre[0] = 0;
   for (;;) {
     const uint64_t T = subtree_size(N, K, pre[len - 1], len);
-    if (T > max_subsets && len < std::max(K - 1, 1)) {  // split (items stop at the bottom stage's depth)
+    if (T > max_subsets && len < std::max(K - 2, 1)) {  // split; items stop at depth max(K-2, 1), where the
+                                                         // shallowest bottom stage (the 4-D test) starts
       pre[len] = pre[len - 1] + 1;
       ++len;
       continue;
@@ -583,7 +584,7 @@ void host_run(const int64_t* P, int N, int K, const std::vector<Item>& items, in
     HostTeam tm;
     std::vector<TC> sc((size_t)N * stack_entries(K));
     std::vector<TL> sl((size_t)N * K);
-    std::vector<float> fl((size_t)3 * N);
+    std::vector<float> fl((size_t)4 * N);
     Walker<TC, TL, HostTeam> W(tm, P, N, K, N, sc.data(), sl.data(), fl.data());
     Acc a{};
     for (;;) {

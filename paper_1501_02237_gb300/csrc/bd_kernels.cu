@@ -65,12 +65,12 @@ __host__ __device__ inline int slots_of(int N) { return (N + 3) & ~3; }
 #endif
 #define BD_ENUM_BOUNDS __launch_bounds__(256, BD_LB_BLOCKS)
 
-// one warp's shared memory: its coordinate-minor stack, lift-minor stack and three float rows
+// one warp's shared memory: its coordinate-minor stack, lift-minor stack and four float rows
 // for the single-precision filters, each 16-byte aligned
 template <class TC, class TL>
 __host__ __device__ inline size_t warp_bytes(int slots, int K) {
   return align16((size_t)slots * stack_entries(K) * sizeof(TC)) + align16((size_t)slots * K * sizeof(TL)) +
-         align16((size_t)3 * slots * sizeof(float));
+         align16((size_t)4 * slots * sizeof(float));
 }
 
 template <class TC, class TL>

@@ -168,3 +168,33 @@ def test_host_walker_all_integer_paths(seed):
         assert r["nvol"] == nvol_placing(pts)
         if force:
             assert r["flags"] & bd.BD_FLAG_INT128
+
+
+@pytest.mark.parametrize("seed", range(16))
+def test_host_walker_deepest_items_and_exact_routes(seed):
+    # item_subsets=1 splits every prefix down to the deepest item level, where the bottom stage
+    # starts right away; coordinates scaled by 2^8 push the single-precision filters of the
+    # bottom stage onto their exact routes (singular triples with large terms).  Every path
+    # and split must give the oracle's volume.
+    rng = random.Random(900 + seed)
+    k = rng.choice([3, 4, 5])
+    n = rng.randint(k + 2, 11)
+    base = [tuple(rng.randint(-2, 2) for _ in range(k)) for _ in range(n)]
+    for scale in (1, 256):
+        pts = [tuple(scale * x for x in p) for p in base]
+        ref = nvol_placing(pts)
+        lf = oracle_lifts(n, seed)
+        for items in (1, 0):
+            for force in (False, True):
+                r = bd.host_volume_lifted(np.array(pts), np.array(lf), force_int128=force, item_subsets=items)
+                assert r["status"] == 0
+                assert r["nvol"] == ref, (scale, items, force)
+
+
+def test_host_walker_zero_lifts_are_ties():
+    # constant lifts put every point on every lifted hyperplane: the filtered tests cannot
+    # decide a sign and the exact route must report the ties
+    rng = random.Random(5)
+    pts = np.array([[rng.randint(-3, 3) for _ in range(4)] for _ in range(9)] + [[0] * 4])
+    r = bd.host_volume_lifted(pts, np.zeros(len(pts), dtype=np.int64))
+    assert r["status"] == 3 and r["ties"] > 0
