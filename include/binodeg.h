@@ -306,12 +306,19 @@ int bd_volume_noalloc(const int64_t* points, int32_t npts, int32_t k, uint64_t s
 
 /* ---- host emulation (CPU tests and the native CPU baseline; never used by the calls above) */
 
-/* Runs the same lower-facet enumeration as the GPU kernel on |threads| CPU threads, with
- * the given lifts (no re-lift); a negative count forces the 128-bit path.  item_subsets is
- * the work-item split threshold in subsets (0: 4096; 1 splits every prefix down to the
- * deepest item level).  Returns BD_ERR_TIES when the lifting has a tie. */
+typedef struct bd_host_opts {
+  int32_t threads;       /* CPU threads, each emulating one single-lane team (<= 0: 1) */
+  int32_t force_int128;  /* nonzero: run the 128-bit walker whatever the bound */
+  uint64_t item_subsets; /* work-item split threshold in subsets (0: 4096; 1: deepest items) */
+  int32_t team_width;    /* > 1: one team of this many lanes, run as threads in lockstep */
+  int32_t reserved;      /* 0 */
+} bd_host_opts;
+
+/* Runs the same lower-facet enumeration as the GPU kernel on CPU threads, with the given
+ * lifts (no re-lift); opts may be NULL (one thread, default split).  Returns BD_ERR_TIES
+ * when the lifting has a tie. */
 int bd_host_volume_lifted(const int64_t* points, const int64_t* lifts, int32_t npts, int32_t k,
-                          int32_t threads, uint64_t item_subsets, bd_volume_out* out);
+                          const bd_host_opts* opts, bd_volume_out* out);
 
 #ifdef __cplusplus
 }

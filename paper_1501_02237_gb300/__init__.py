@@ -13,7 +13,7 @@ from typing import Optional, Sequence
 import numpy as np
 
 from ._lib import (BD_FEATURES, BD_MLP_PARAMS, BD_FLAG_DEGENERATE, BD_FLAG_INCONSISTENT, BD_FLAG_INT128, KMAX,  # noqa: F401
-                   NMAX, BatchOpts, BatchStats, BinodegError, DegreeOut, PlanOpts, ServerOpts, ServerStats, VolumeOut,
+                   NMAX, BatchOpts, BatchStats, BinodegError, DegreeOut, HostOpts, PlanOpts, ServerOpts, ServerStats, VolumeOut,
                    check, i64, lib, ptr)
 from ._lib import F32P, I32P, U8P
 
@@ -102,15 +102,16 @@ def classify(points, lifts, subsets) -> tuple:
     return status, absdet
 
 
-def host_volume_lifted(points, lifts, threads: int = 1, force_int128: bool = False, item_subsets: int = 0) -> dict:
+def host_volume_lifted(points, lifts, threads: int = 1, force_int128: bool = False, item_subsets: int = 0,
+                       team_width: int = 1) -> dict:
     """bd_host_volume_lifted: CPU emulation of the enumeration (CPU tests and the native baseline).
-    force_int128 runs the 128-bit walker (a negative thread count at the C ABI); item_subsets is
-    the work-item split threshold (0: the library's default)."""
+    force_int128 runs the 128-bit walker; item_subsets is the work-item split threshold (0: the
+    library's default); team_width > 1 runs one team of that many lanes as threads in lockstep."""
     P, W = i64(points), i64(lifts)
     npts, k = P.shape
     out = VolumeOut()
-    t = -max(1, threads) if force_int128 else threads
-    rc = lib().bd_host_volume_lifted(ptr(P), ptr(W), npts, k, t, item_subsets, C.byref(out))
+    opts = HostOpts(threads, int(force_int128), item_subsets, team_width, 0)
+    rc = lib().bd_host_volume_lifted(ptr(P), ptr(W), npts, k, C.byref(opts), C.byref(out))
     res = out.as_dict()
     res["status"] = rc
     if rc not in (0, 3):

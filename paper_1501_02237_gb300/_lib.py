@@ -59,6 +59,11 @@ class PlanOpts(C.Structure):
                 ("force_int128", C.c_int32), ("reserved", C.c_int32 * 3)]
 
 
+class HostOpts(C.Structure):
+    _fields_ = [("threads", C.c_int32), ("force_int128", C.c_int32), ("item_subsets", C.c_uint64),
+                ("team_width", C.c_int32), ("reserved", C.c_int32)]
+
+
 class BatchOpts(C.Structure):
     _fields_ = [("mode", C.c_int32), ("warps_per_block", C.c_int32), ("item_factor", C.c_int32),
                 ("use_graph", C.c_int32), ("autotune", C.c_int32), ("reserved0", C.c_int32),
@@ -111,7 +116,7 @@ SIGNATURES = {
     "bd_plan_volume": (C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(VolumeOut)]),
     "bd_plan_info": (C.c_int, [C.c_void_p, I64P]),
     "bd_plan_destroy": (C.c_int, [C.c_void_p]),
-    "bd_host_volume_lifted": (C.c_int, [I64P, I64P, C.c_int32, C.c_int32, C.c_int32, C.c_uint64, C.POINTER(VolumeOut)]),
+    "bd_host_volume_lifted": (C.c_int, [I64P, I64P, C.c_int32, C.c_int32, C.POINTER(HostOpts), C.POINTER(VolumeOut)]),
     "bd_volume_noalloc": (C.c_int, [I64P, C.c_int32, C.c_int32, C.c_uint64, C.POINTER(VolumeOut)]),
     "bd_batch_create": (C.c_int, [C.POINTER(C.c_void_p)]),
     "bd_batch_add": (C.c_int, [C.c_void_p, I64P, C.c_int32, C.c_int32, I64P, C.c_uint64, I32P]),

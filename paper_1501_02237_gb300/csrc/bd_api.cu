@@ -531,9 +531,11 @@ int bd_classify(const int64_t* points, const int64_t* lifts, int32_t npts, int32
   return BD_OK;
 }
 
-int bd_host_volume_lifted(const int64_t* points, const int64_t* lifts, int32_t npts, int32_t k, int32_t threads,
-                          uint64_t item_subsets, bd_volume_out* out) {
+int bd_host_volume_lifted(const int64_t* points, const int64_t* lifts, int32_t npts, int32_t k,
+                          const bd_host_opts* opts, bd_volume_out* out) {
   if (!out || !lifts) return fail(BD_ERR_ARG, "NULL argument");
+  const bd_host_opts o = opts ? *opts : bd_host_opts{};
+  if (o.team_width > 64) return fail(BD_ERR_ARG, "team_width above 64");
   int rc = check_points(points, npts, k);
   if (rc) return rc;
   if (npts < k + 1) {
@@ -549,18 +551,15 @@ int bd_host_volume_lifted(const int64_t* points, const int64_t* lifts, int32_t n
   const double bound = bd::hadamard_log2(points, lifts, npts, k, hi - lo, &coord_bits);
   int path = bd::choose_path(coord_bits, bound);
   if (path < 0) return fail(BD_ERR_OVERFLOW, "Hadamard bound exceeds 2^127");
-  if (threads < 0) {  // a negative thread count forces the 128-bit path (tests of the wide walker)
-    path = bd::PATH_WIDE;
-    threads = -threads;
-  }
+  if (o.force_int128) path = bd::PATH_WIDE;
   std::vector<int64_t> P((size_t)(k + 1) * npts);
   for (int q = 0; q < npts; ++q) {
     for (int c = 0; c < k; ++c) P[(size_t)c * npts + q] = points[(size_t)q * k + c];
     P[(size_t)k * npts + q] = lifts[q];
   }
-  const auto items = bd::build_items(npts, k, item_subsets ? item_subsets : 4096);
+  const auto items = bd::build_items(npts, k, o.item_subsets ? o.item_subsets : 4096);
   bd::Acc acc{};
-  bd::host_enumerate(path, P.data(), npts, k, items, std::max(1, threads), acc);
+  bd::host_enumerate(path, P.data(), npts, k, items, std::max(1, o.threads), acc, o.team_width);
   std::memset(out, 0, sizeof(*out));
   set_u128(out->nvol_lo, out->nvol_hi, acc.nvol);
   out->cells = acc.cells;

@@ -347,9 +347,16 @@ struct Walker {
   BD_HD void start(int s0) {
     tm.sync();  // the previous item's readers are done with the stack
     s[0] = s0;
+    const bool conv = kFiltered && K == 3;  // state 0 is the 4-D stage's input
     for (int q = tm.lane(); q < N; q += tm.lanes()) {
-      for (int c = 0; c < K; ++c) sc[c * SLOTS + q] = (TC)(P[c * N + q] - P[c * N + s0]);
-      sl[q] = (TL)(P[K * N + q] - P[K * N + s0]);
+      for (int c = 0; c < K; ++c) {
+        const TC v = (TC)(P[c * N + q] - P[c * N + s0]);
+        sc[c * SLOTS + q] = v;
+        if (conv) fl[c * SLOTS + q] = f32_of(v);
+      }
+      const TL l = (TL)(P[K * N + q] - P[K * N + s0]);
+      sl[q] = l;
+      if (conv) fl[3 * SLOTS + q] = f32_of(l);
     }
     dv[0] = make_div((TC)1);
     piv[0] = 1;
@@ -374,13 +381,19 @@ struct Walker {
     const TL rl = sl[(j - 1) * SLOTS + c];
     const Div D = dv[j - 1];
     tm.sync();  // readers of the old state j (a sibling's subtree) are done
+    // state K-3 is the 4-D stage's input: its single-precision copies are written here too
+    const bool conv = kFiltered && j == K - 3;
     for (int q = tm.lane(); q < N; q += tm.lanes()) {
       const TC bq = sc[(po + pi) * SLOTS + q];
       for (int e = 0; e < ncoord - 1; ++e) {
         const int ep = e < pi ? e : e + 1;
-        sc[(no + e) * SLOTS + q] = bareiss(sc[(po + ep) * SLOTS + q], pj, bq, sc[(po + ep) * SLOTS + c], D);
+        const TC v = bareiss(sc[(po + ep) * SLOTS + q], pj, bq, sc[(po + ep) * SLOTS + c], D);
+        sc[(no + e) * SLOTS + q] = v;
+        if (conv) fl[e * SLOTS + q] = f32_of(v);
       }
-      sl[j * SLOTS + q] = bareiss(sl[(j - 1) * SLOTS + q], pj, bq, rl, D);
+      const TL l = bareiss(sl[(j - 1) * SLOTS + q], pj, bq, rl, D);
+      sl[j * SLOTS + q] = l;
+      if (conv) fl[3 * SLOTS + q] = f32_of(l);
     }
     s[j] = c;
     piv[j] = pj;
@@ -672,20 +685,13 @@ struct Walker {
     return below ? -sig : sig;
   }
 
-  // The triples (c1, c, p), s_{K-3} < c1 < c < p < N, are dealt to lanes in lexicographic
-  // order, a warp-width per round; each lane walks the points q in index order and stops at
-  // the first one strictly below its cell; the round ends when every lane has a verdict.
+  // The triples (c1, c, p), s_{K-3} < c1 < c < p < N, are dealt to lanes in colex order, a
+  // warp-width per round; each lane walks the points q in index order and stops at the first
+  // one strictly below its cell; the round ends when every lane has a verdict.
   BD_HD void bottom4(Acc& acc) {
-    const int o = level_offset(K, K - 3);
     const int sd = piv[K - 3] < 0 ? -1 : 1;
     const uint64_t prefix = member_mask(K - 2);
-    for (int q = tm.lane(); q < N; q += tm.lanes()) {
-      fl[q] = f32_of(sc[o * SLOTS + q]);
-      fl[SLOTS + q] = f32_of(sc[(o + 1) * SLOTS + q]);
-      fl[2 * SLOTS + q] = f32_of(sc[(o + 2) * SLOTS + q]);
-      fl[3 * SLOTS + q] = f32_of(sl[(K - 3) * SLOTS + q]);
-    }
-    tm.sync();
+    // fl holds the single-precision copies of state K-3 (written by the step that built it).
     // Error bounds, u = 2^-24: every term of det4 is a product of four point copies (2u each,
     // f32_of) through at most nine roundings (2x2 minor: product and difference; cofactor:
     // product and two sums; det4: product and three sums), so |error| <= 17.001u T with T the
@@ -695,26 +701,26 @@ struct Walker {
     // operand and partial result is an integer held exactly, and the single-precision value is
     // the exact one.
     const float eps = 1.9073486328125e-6f;  // 2^-19
-    int c1 = s[K - 3] + 1, c = c1 + 1, p = c + 1 + tm.lane();
-    for (;;) {
-      for (;;) {  // carry: N-1-c pairs per c, then the next c1
-        if (p < N) break;
-        if (c < N - 2) {
-          p -= N - c - 2;
-          ++c;
-          continue;
-        }
-        if (c1 < N - 3) {
-          const int off = p - N;
-          ++c1;
-          c = c1 + 1;
-          p = c + 1 + off;
-          continue;
-        }
-        break;
+    // Triple number t in colex order (by p, then c, then c1) is decoded directly:
+    // C(k,3) <= t < C(k+1,3), then C(j,2) <= t - C(k,3) < C(j+1,2), i = t - C(k,3) - C(j,2),
+    // and (c1, c, p) = s_{K-3} + 1 + (i, j, k).  k never decreases for a lane.
+    const int base = s[K - 3] + 1, R = N - base;
+    const int total = R * (R - 1) * (R - 2) / 6;
+    int k = 2;
+    for (int t0 = 0; t0 < total; t0 += tm.lanes()) {
+      const int t = t0 + tm.lane();
+      bool live = t < total;
+      int c1 = base, c = base, p = base;
+      if (live) {
+        while ((k + 1) * k * (k - 1) / 6 <= t) ++k;
+        const int u = t - k * (k - 1) * (k - 2) / 6;
+        int jj = (int)((1.0f + sqrtf(8.0f * (float)u + 1.0f)) * 0.5f);
+        if (jj * (jj - 1) / 2 > u) --jj;
+        else if ((jj + 1) * jj / 2 <= u) ++jj;
+        c1 = base + u - jj * (jj - 1) / 2;
+        c = base + jj;
+        p = base + k;
       }
-      bool live = p < N;
-      if (!tm.any(live)) break;
       float n0 = 0, n1 = 0, n2 = 0, n3 = 0, e0 = 0, e1 = 0, e2 = 0, e3 = 0;
       int sig = 1, s3 = 0;
       if (live) {
@@ -781,7 +787,6 @@ struct Walker {
           acc.nvol += (u128)(m < 0 ? -m : m);
         }
       }
-      p += tm.lanes();
     }
   }
 

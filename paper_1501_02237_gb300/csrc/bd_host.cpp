@@ -5,7 +5,9 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <condition_variable>
 #include <cstdlib>
+#include <mutex>
 #include <thread>
 #ifdef BD_DEBUG
 #include <cstdio>
@@ -576,6 +578,74 @@ struct HostTeam {
 };
 }  // namespace
 
+// A team of `width` lanes run as CPU threads in lockstep: every collective (vote, sync) is a
+// barrier, as a warp-synchronous program requires of its lanes.  Tests use it to run the
+// multi-lane logic of the walker (lane dealing, ragged tails, votes) without a GPU.
+struct LockstepShared {
+  std::mutex mu;
+  std::condition_variable cv;
+  int width, waiting = 0;
+  uint64_t generation = 0;
+  std::vector<uint64_t> votes;
+  explicit LockstepShared(int w) : width(w), votes(w) {}
+  void barrier() {
+    std::unique_lock<std::mutex> lk(mu);
+    const uint64_t g = generation;
+    if (++waiting == width) {
+      waiting = 0;
+      ++generation;
+      cv.notify_all();
+    } else {
+      cv.wait(lk, [&] { return generation != g; });
+    }
+  }
+};
+
+struct LockstepTeam {
+  LockstepShared* sh;
+  int ln;
+  int lane() const { return ln; }
+  int lanes() const { return sh->width; }
+  uint64_t reduce_or(uint64_t x, bool all_of) const {
+    sh->votes[ln] = x;
+    sh->barrier();
+    uint64_t r = all_of ? 1 : 0;
+    for (int w = 0; w < sh->width; ++w) r = all_of ? (r & (sh->votes[w] != 0)) : (r | sh->votes[w]);
+    sh->barrier();
+    return r;
+  }
+  bool any(bool b) const { return reduce_or(b, false) != 0; }
+  bool all(bool b) const { return reduce_or(b, true) != 0; }
+  void sync() const { sh->barrier(); }
+  uint64_t or_all(uint64_t x) const { return reduce_or(x, false); }
+};
+
+template <class TC, class TL>
+void lockstep_run(const int64_t* P, int N, int K, const std::vector<Item>& items, int width, Acc& acc) {
+  LockstepShared sh(width);
+  std::vector<TC> sc((size_t)N * stack_entries(K));
+  std::vector<TL> sl((size_t)N * K);
+  std::vector<float> fl((size_t)4 * N);
+  std::vector<Acc> part(width);
+  std::vector<std::thread> th;
+  for (int l = 0; l < width; ++l)
+    th.emplace_back([&, l] {
+      LockstepTeam tm{&sh, l};
+      Walker<TC, TL, LockstepTeam> W(tm, P, N, K, N, sc.data(), sl.data(), fl.data());
+      Acc a{};
+      for (const Item& it : items) W.run_item(it, a);
+      part[l] = a;
+    });
+  for (auto& t : th) t.join();
+  acc = Acc{};
+  for (auto& a : part) {
+    acc.nvol += a.nvol;
+    acc.cells += a.cells;
+    acc.singular += a.singular;
+    acc.ties += a.ties;
+  }
+}
+
 template <class TC, class TL>
 void host_run(const int64_t* P, int N, int K, const std::vector<Item>& items, int threads, Acc& acc) {
   std::atomic<size_t> next(0);
@@ -610,7 +680,14 @@ void host_run(const int64_t* P, int N, int K, const std::vector<Item>& items, in
   }
 }
 
-void host_enumerate(int path, const int64_t* P, int N, int K, const std::vector<Item>& items, int threads, Acc& acc) {
+void host_enumerate(int path, const int64_t* P, int N, int K, const std::vector<Item>& items, int threads, Acc& acc,
+                    int team_width) {
+  if (team_width > 1) {
+    if (path == 0) lockstep_run<int32_t, int64_t>(P, N, K, items, team_width, acc);
+    else if (path == 1) lockstep_run<int64_t, int64_t>(P, N, K, items, team_width, acc);
+    else lockstep_run<i128, i128>(P, N, K, items, team_width, acc);
+    return;
+  }
   if (path == 0) host_run<int32_t, int64_t>(P, N, K, items, threads, acc);
   else if (path == 1) host_run<int64_t, int64_t>(P, N, K, items, threads, acc);
   else host_run<i128, i128>(P, N, K, items, threads, acc);

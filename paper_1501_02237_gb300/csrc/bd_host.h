@@ -42,7 +42,10 @@ std::vector<Item> build_items(int npts, int k, uint64_t max_subsets);
 // it does not fit.
 bool build_items_into(int npts, int k, uint64_t max_subsets, Item* out, size_t cap, size_t* count);
 
-// Host emulation of the warp enumeration on `threads` CPU threads, for an integer path.
-void host_enumerate(int path, const int64_t* P, int N, int K, const std::vector<Item>& items, int threads, Acc& acc);
+// Host emulation of the warp enumeration on `threads` CPU threads (one single-lane team
+// each), for an integer path; team_width > 1 instead runs one team of that many lanes as
+// threads in lockstep.
+void host_enumerate(int path, const int64_t* P, int N, int K, const std::vector<Item>& items, int threads, Acc& acc,
+                    int team_width = 1);
 
 }  // namespace bd

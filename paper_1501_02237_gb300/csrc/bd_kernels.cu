@@ -59,9 +59,9 @@ __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t
 // type; lane l owns points l and l + 32 whatever the stride)
 __host__ __device__ inline int slots_of(int N) { return (N + 3) & ~3; }
 
-// at most 256 threads per block and at least 3 resident blocks: about 85 registers per thread
+// at most 256 threads per block and at least 2 resident blocks: up to 128 registers per thread
 #ifndef BD_LB_BLOCKS
-#define BD_LB_BLOCKS 3
+#define BD_LB_BLOCKS 2
 #endif
 #define BD_ENUM_BOUNDS __launch_bounds__(256, BD_LB_BLOCKS)
 

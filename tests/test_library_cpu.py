@@ -198,3 +198,22 @@ def test_host_walker_zero_lifts_are_ties():
     pts = np.array([[rng.randint(-3, 3) for _ in range(4)] for _ in range(9)] + [[0] * 4])
     r = bd.host_volume_lifted(pts, np.zeros(len(pts), dtype=np.int64))
     assert r["status"] == 3 and r["ties"] > 0
+
+
+@pytest.mark.parametrize("seed", range(10))
+@pytest.mark.parametrize("width", [32, 7])
+def test_lockstep_team_matches_oracle(seed, width):
+    # one team of `width` lanes as CPU threads in lockstep runs the walker's multi-lane logic
+    # (rows and triples dealt to lanes, ragged tails, votes); 32 is the GPU's team width
+    rng = random.Random(1200 + seed)
+    k = rng.choice([2, 3, 4, 5])
+    n = rng.randint(k + 2, 10)
+    pts = [tuple(rng.randint(-2, 2) for _ in range(k)) for _ in range(n)]
+    pts = [tuple(16 * x for x in p) for p in pts] if seed % 3 == 2 else pts
+    lf = oracle_lifts(n, seed)
+    ref = nvol_placing(pts)
+    for force in (False, True):
+        r = bd.host_volume_lifted(np.array(pts), np.array(lf), force_int128=force, item_subsets=1 + seed % 2 * 40,
+                                  team_width=width)
+        assert r["status"] == 0
+        assert r["nvol"] == ref, (k, n, force)
