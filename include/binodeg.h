@@ -148,7 +148,7 @@ int bd_plan_read(bd_plan* plan, bd_volume_out* out);
 int bd_plan_volume(bd_plan* plan, uint64_t seed, bd_volume_out* out);
 /* Number of work items, kernel launch geometry and integer path: {items, blocks, warps_per_block,
  * shared_bytes_per_block, path (0: int32 coordinate / int64 lift minors, 1: int64, 2: int128),
- * slots_per_warp, 0, 0}. */
+ * slots_per_warp, ranges (work units: runs of consecutive items a warp takes at once), 0}. */
 int bd_plan_info(const bd_plan* plan, int64_t* info);
 int bd_plan_destroy(bd_plan* plan);
 

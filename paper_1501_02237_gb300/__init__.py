@@ -149,7 +149,7 @@ class Plan:
         a = np.zeros(8, dtype=np.int64)
         check(lib().bd_plan_info(self.handle, ptr(a)))
         return dict(items=int(a[0]), blocks=int(a[1]), warps_per_block=int(a[2]), smem=int(a[3]),
-                    path=("int32/int64", "int64", "int128")[int(a[4])], int128=int(a[4]) == 2, slots=int(a[5]))
+                    path=("int32/int64", "int64", "int128")[int(a[4])], int128=int(a[4]) == 2, slots=int(a[5]), ranges=int(a[6]))
 
     def close(self) -> None:
         if getattr(self, "handle", None):

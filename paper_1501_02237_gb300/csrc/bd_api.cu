@@ -71,11 +71,13 @@ void set_u128(uint64_t& lo, uint64_t& hi, u128 v) {
 // Work lists depend only on (N, K, split size): built once per process and device, kept on the
 // device and shared by every plan that needs them.
 struct ItemList {
-  std::vector<bd::Item> host;
+  std::vector<bd::Item> host;  // lexicographic order
+  std::vector<bd::Range> ranges;
   bd::Item* dev = nullptr;
+  bd::Range* dev_ranges = nullptr;
 };
 std::mutex g_cache_mu;
-std::map<std::tuple<int, int, int64_t, int>, std::shared_ptr<ItemList>> g_items;
+std::map<std::tuple<int, int, int64_t, int64_t, int>, std::shared_ptr<ItemList>> g_items;
 std::map<std::tuple<int, int, int, int, int, int>, bd::LaunchShape> g_shapes;
 
 int current_device() {
@@ -84,8 +86,8 @@ int current_device() {
   return d;
 }
 
-int get_items(int N, int K, int64_t thr, std::shared_ptr<ItemList>& out) {
-  const auto key = std::make_tuple(N, K, thr, current_device());
+int get_items(int N, int K, int64_t thr, int64_t teams, std::shared_ptr<ItemList>& out) {
+  const auto key = std::make_tuple(N, K, thr, teams, current_device());
   std::lock_guard<std::mutex> lk(g_cache_mu);
   auto it = g_items.find(key);
   if (it != g_items.end()) {
@@ -93,11 +95,13 @@ int get_items(int N, int K, int64_t thr, std::shared_ptr<ItemList>& out) {
     return BD_OK;
   }
   auto L = std::make_shared<ItemList>();
-  L->host = bd::build_items(N, K, (uint64_t)thr);
-  const size_t bytes = sizeof(bd::Item) * std::max<size_t>(1, L->host.size());
-  cudaError_t e = cudaMalloc(&L->dev, bytes);
+  bd::build_ranges(N, K, (uint64_t)thr, (uint64_t)teams, L->host, L->ranges);
+  cudaError_t e = cudaMalloc(&L->dev, sizeof(bd::Item) * std::max<size_t>(1, L->host.size()));
+  if (e == cudaSuccess) e = cudaMalloc(&L->dev_ranges, sizeof(bd::Range) * std::max<size_t>(1, L->ranges.size()));
   if (e == cudaSuccess && !L->host.empty())
     e = cudaMemcpy(L->dev, L->host.data(), sizeof(bd::Item) * L->host.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !L->ranges.empty())
+    e = cudaMemcpy(L->dev_ranges, L->ranges.data(), sizeof(bd::Range) * L->ranges.size(), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return cuda_fail(e, "work list upload");
   g_items[key] = L;
   out = L;
@@ -225,14 +229,14 @@ int plan_prepare(bd_plan* p, const int64_t* points, const int64_t* lifts, int32_
   rc = get_shape(npts, k, p->path, opts ? opts->warps_per_block : 0, opts ? opts->blocks_per_sm : 0, p->shape);
   if (rc) return rc;
   const uint64_t total = bd::binom(npts, k + 1);
+  const uint64_t warps = (uint64_t)p->shape.blocks * p->shape.warps;
   int64_t thr = opts && opts->item_subsets > 0 ? opts->item_subsets : 0;
-  if (!thr) {
-    const uint64_t warps = (uint64_t)p->shape.blocks * p->shape.warps;
-    thr = (int64_t)(total / (warps * 4 + 1));
-    thr = std::max<int64_t>(thr, 256);
-    thr = std::min<int64_t>(thr, (int64_t)1 << 22);
+  if (!thr) {  // items fine enough for the tail of the guided ranges
+    thr = (int64_t)(total / (warps * 32 + 1));
+    thr = std::max<int64_t>(thr, 64);
+    thr = std::min<int64_t>(thr, (int64_t)1 << 20);
   }
-  rc = get_items(npts, k, thr, p->items);
+  rc = get_items(npts, k, thr, (int64_t)warps, p->items);
   if (rc) return rc;
   std::memcpy(p->h_stage, points, sizeof(int64_t) * npts * k);
   cudaError_t e = cudaMemcpyAsync(p->d_pts, p->h_stage, sizeof(int64_t) * npts * k, cudaMemcpyHostToDevice, st);
@@ -286,6 +290,8 @@ int plan_launch(bd_plan* p, uint64_t seed, int attempt, cudaStream_t st) {
   ep.lift_seed = bd::lift_stream_seed(seed, (uint32_t)attempt);
   ep.items = p->items->dev;
   ep.nitems = (int)p->items->host.size();
+  ep.ranges = p->items->dev_ranges;
+  ep.nranges = (int)p->items->ranges.size();
   ep.N = p->N;
   ep.K = p->K;
   ep.acc = reinterpret_cast<bd::DevAcc*>(p->d_state);
@@ -377,7 +383,7 @@ int bd_plan_info(const bd_plan* plan, int64_t* info) {
   info[3] = (int64_t)plan->shape.smem;
   info[4] = plan->path;
   info[5] = plan->shape.slots;
-  info[6] = 0;
+  info[6] = (int64_t)plan->items->ranges.size();
   info[7] = 0;
   return BD_OK;
 }
@@ -557,9 +563,13 @@ int bd_host_volume_lifted(const int64_t* points, const int64_t* lifts, int32_t n
     for (int c = 0; c < k; ++c) P[(size_t)c * npts + q] = points[(size_t)q * k + c];
     P[(size_t)k * npts + q] = lifts[q];
   }
-  const auto items = bd::build_items(npts, k, o.item_subsets ? o.item_subsets : 4096);
+  // the device's work list: items in lexicographic order, taken in ranges (8 teams' worth of
+  // guided ranges, so that range boundaries and prefix reuse are exercised on one thread too)
+  std::vector<bd::Item> items;
+  std::vector<bd::Range> ranges;
+  bd::build_ranges(npts, k, o.item_subsets ? o.item_subsets : 4096, 8, items, ranges);
   bd::Acc acc{};
-  bd::host_enumerate(path, P.data(), npts, k, items, std::max(1, o.threads), acc, o.team_width);
+  bd::host_enumerate(path, P.data(), npts, k, items, std::max(1, o.threads), acc, o.team_width, &ranges);
   std::memset(out, 0, sizeof(*out));
   set_u128(out->nvol_lo, out->nvol_hi, acc.nvol);
   out->cells = acc.cells;

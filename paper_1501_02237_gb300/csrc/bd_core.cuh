@@ -243,6 +243,10 @@ struct Item {                      // a subset prefix s_0 < .. < s_{L-1}, 1 <= L
   uint8_t idx[15];
 };
 
+struct Range {                     // items first .. first+count-1 of a lexicographic work list
+  uint32_t first, count;
+};
+
 struct Acc {
   u128 nvol;         // sum of |D0| over accepted cells
   uint64_t cells;    // accepted cells
@@ -328,6 +332,7 @@ struct Walker {
   Div dv[KMAX];     // exact divider by the pivot of each level (dv[0]: by 1)
   TC piv[KMAX];     // the pivots p_j (piv[0] = 1)
   int psign;        // sign of the level K-1 pivot p_{K-1} (2-D test)
+  int valid = 0;    // states 0 .. valid-1 are those of s_0 .. s_{valid-1} (kept across items)
 #ifdef BD_COUNT
   Acc* cnt = nullptr;
 #endif
@@ -796,17 +801,26 @@ struct Walker {
     else bottom2(acc);
   }
 
-  // every (K+1)-subset extending the prefix it.idx[0 .. it.len-1] (len <= bottom depth)
+  // every (K+1)-subset extending the prefix it.idx[0 .. it.len-1] (len <= bottom depth).  The
+  // states of a prefix shared with the previous item are still in place and are not rebuilt
+  // (the depth-first walk below an item only rewrites levels >= its length).
   BD_HD void run_item(const Item& it, Acc& acc) {
     const int L = it.len;
     const int B = bottom_depth();
-    start(it.idx[0]);
     const bool lead = tm.lane() == 0;  // uniform counts are added once per team
-    for (int j = 1; j < L; ++j) {
+    int m = 0;
+    while (m < valid && m < L && s[m] == it.idx[m]) ++m;
+    if (m == 0) {
+      start(it.idx[0]);
+      m = 1;
+    }
+    valid = m;
+    for (int j = m; j < L; ++j) {
       if (!build(j, it.idx[j])) {
         if (lead) acc.singular += subtree_size(N, K, it.idx[L - 1], L);
         return;
       }
+      valid = j + 1;
     }
     int cur[KMAX + 1];
     int j = L;
@@ -833,6 +847,7 @@ struct Walker {
 
   // status of one given subset sub[0] < .. < sub[K] (2-D route)
   BD_HD int classify(const uint8_t* sub, TL& absdet) {
+    valid = 0;
     start(sub[0]);
     for (int j = 1; j < K - 1; ++j)
       if (!build(j, sub[j])) { absdet = 0; return ST_SINGULAR; }

@@ -554,6 +554,55 @@ std::vector<Item> build_items(int N, int K, uint64_t max_subsets) {
   return items;
 }
 
+// estimated work of an item, in warp rounds of the bottom stage plus one per level step
+static uint64_t item_cost(int N, int K, const Item& it) {
+  const int L = it.len, a = it.idx[L - 1];
+  if (K < 3) return subtree_size(N, K, a, L);
+  // the 4-D bottom stage: one Bareiss step and ceil(C(R,3)/32) warp rounds per level-(K-3)
+  // node with R points after its last index; nodes with last index v below this prefix:
+  // C(v-a-1, K-3-L) (none deeper than K-2 exists when L = K-2)
+  auto node = [&](int v) {
+    const uint64_t t = binom(N - 1 - v, 3);
+    return 1 + (t + 31) / 32;
+  };
+  if (L >= K - 2) return node(a);
+  uint64_t c = 0;
+  for (int v = a + (K - 2 - L); v <= N - 4; ++v) c += binom(v - a - 1, K - 3 - L) * node(v);
+  return c;
+}
+
+void build_ranges(int N, int K, uint64_t max_subsets, uint64_t teams, std::vector<Item>& items,
+                  std::vector<Range>& ranges) {
+  items.clear();
+  ranges.clear();
+  std::vector<uint64_t> cost;
+  uint64_t remaining = 0;
+  for_each_item(N, K, max_subsets, [&](const Item& x) {
+    items.push_back(x);
+    cost.push_back(std::max<uint64_t>(1, item_cost(N, K, x)));
+    remaining += cost.back();
+    return true;
+  });
+  // runs of consecutive items packed up to 1/8 of a team's share, then taken largest first
+  const uint64_t cap = std::max<uint64_t>(1, remaining / (8 * std::max<uint64_t>(1, teams)));
+  std::vector<uint64_t> rcost;
+  size_t i = 0;
+  while (i < items.size()) {
+    const size_t first = i;
+    uint64_t got = 0;
+    while (i < items.size() && (i == first || got + cost[i] <= cap)) got += cost[i++];
+    ranges.push_back(Range{(uint32_t)first, (uint32_t)(i - first)});
+    rcost.push_back(got);
+  }
+  std::vector<size_t> order(ranges.size());
+  for (size_t r = 0; r < order.size(); ++r) order[r] = r;
+  std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return rcost[a] > rcost[b]; });
+  std::vector<Range> sorted;
+  sorted.reserve(ranges.size());
+  for (size_t r : order) sorted.push_back(ranges[r]);
+  ranges.swap(sorted);
+}
+
 bool build_items_into(int N, int K, uint64_t max_subsets, Item* out, size_t cap, size_t* count) {
   size_t n = 0;
   const bool ok = for_each_item(N, K, max_subsets, [&](const Item& x) {
@@ -647,9 +696,11 @@ void lockstep_run(const int64_t* P, int N, int K, const std::vector<Item>& items
 }
 
 template <class TC, class TL>
-void host_run(const int64_t* P, int N, int K, const std::vector<Item>& items, int threads, Acc& acc) {
+void host_run(const int64_t* P, int N, int K, const std::vector<Item>& items, const std::vector<Range>* ranges,
+              int threads, Acc& acc) {
   std::atomic<size_t> next(0);
   std::vector<Acc> part(std::max(1, threads));
+  const size_t units = ranges ? ranges->size() : items.size();
   auto work = [&](int tid) {
     HostTeam tm;
     std::vector<TC> sc((size_t)N * stack_entries(K));
@@ -658,9 +709,10 @@ void host_run(const int64_t* P, int N, int K, const std::vector<Item>& items, in
     Walker<TC, TL, HostTeam> W(tm, P, N, K, N, sc.data(), sl.data(), fl.data());
     Acc a{};
     for (;;) {
-      const size_t i = next.fetch_add(1);
-      if (i >= items.size()) break;
-      W.run_item(items[i], a);
+      const size_t u = next.fetch_add(1);
+      if (u >= units) break;
+      const Range r = ranges ? (*ranges)[u] : Range{(uint32_t)u, 1};
+      for (uint32_t i = r.first; i < r.first + r.count; ++i) W.run_item(items[i], a);
     }
     part[tid] = a;
   };
@@ -681,16 +733,16 @@ void host_run(const int64_t* P, int N, int K, const std::vector<Item>& items, in
 }
 
 void host_enumerate(int path, const int64_t* P, int N, int K, const std::vector<Item>& items, int threads, Acc& acc,
-                    int team_width) {
-  if (team_width > 1) {
+                    int team_width, const std::vector<Range>* ranges) {
+  if (team_width > 1) {  // one team walks every item in order (ranges are contiguous anyway)
     if (path == 0) lockstep_run<int32_t, int64_t>(P, N, K, items, team_width, acc);
     else if (path == 1) lockstep_run<int64_t, int64_t>(P, N, K, items, team_width, acc);
     else lockstep_run<i128, i128>(P, N, K, items, team_width, acc);
     return;
   }
-  if (path == 0) host_run<int32_t, int64_t>(P, N, K, items, threads, acc);
-  else if (path == 1) host_run<int64_t, int64_t>(P, N, K, items, threads, acc);
-  else host_run<i128, i128>(P, N, K, items, threads, acc);
+  if (path == 0) host_run<int32_t, int64_t>(P, N, K, items, ranges, threads, acc);
+  else if (path == 1) host_run<int64_t, int64_t>(P, N, K, items, ranges, threads, acc);
+  else host_run<i128, i128>(P, N, K, items, ranges, threads, acc);
 }
 
 }  // namespace bd

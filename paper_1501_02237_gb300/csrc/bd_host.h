@@ -38,14 +38,21 @@ int choose_path(double coord_bits, double full_bits);
 // depth of the walker's bottom stage), then sorted by decreasing size.
 std::vector<Item> build_items(int npts, int k, uint64_t max_subsets);
 
+// The same items in lexicographic order, grouped into ranges of consecutive items for `teams`
+// teams: runs packed up to 1/8 of a team's share of the estimated work (the bottom stage's
+// warp rounds and level steps, not subsets, which misjudge regions of small nodes), taken
+// largest first.  A team builds the prefixes its range's items share once.
+void build_ranges(int npts, int k, uint64_t max_subsets, uint64_t teams, std::vector<Item>& items,
+                  std::vector<Range>& ranges);
+
 // The same list written into a caller-owned array of `cap` items (no allocation); false when
 // it does not fit.
 bool build_items_into(int npts, int k, uint64_t max_subsets, Item* out, size_t cap, size_t* count);
 
 // Host emulation of the warp enumeration on `threads` CPU threads (one single-lane team
 // each), for an integer path; team_width > 1 instead runs one team of that many lanes as
-// threads in lockstep.
+// threads in lockstep.  With ranges, teams take whole ranges of consecutive items.
 void host_enumerate(int path, const int64_t* P, int N, int K, const std::vector<Item>& items, int threads, Acc& acc,
-                    int team_width = 1);
+                    int team_width = 1, const std::vector<Range>* ranges = nullptr);
 
 }  // namespace bd

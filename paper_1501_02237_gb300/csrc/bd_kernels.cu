@@ -138,14 +138,18 @@ __global__ void BD_ENUM_BOUNDS k_enumerate(EnumParams p) {
   Walker<TC, TL, WarpTeam> W(tm, P, N, K, slots, m.sc, m.sl, m.fl);
   Acc acc{};
   unsigned long long done = 0;
+  const unsigned int units = p.ranges ? (unsigned int)p.nranges : (unsigned int)p.nitems;
   for (;;) {
-    unsigned int i = 0;
-    if (lane == 0) i = atomicAdd(p.counter, 1u);
-    i = __shfl_sync(0xffffffffu, i, 0);
-    if (i >= (unsigned int)p.nitems) break;
-    const Item it = p.items[i];
-    W.run_item(it, acc);
-    ++done;
+    unsigned int u = 0;
+    if (lane == 0) u = atomicAdd(p.counter, 1u);
+    u = __shfl_sync(0xffffffffu, u, 0);
+    if (u >= units) break;
+    const Range r = p.ranges ? p.ranges[u] : Range{u, 1u};
+    for (unsigned int i = r.first; i < r.first + r.count; ++i) {
+      const Item it = p.items[i];
+      W.run_item(it, acc);
+      ++done;
+    }
   }
   acc = warp_sum(acc);
   if (lane == 0) flush(acc, p.acc, done);

@@ -21,8 +21,10 @@ struct EnumParams {
   uint64_t lift_seed;     // stream seed (see bd_lifts.h)
   const Item* items;
   int nitems;
+  const Range* ranges;    // work units: ranges of consecutive items, or nullptr: one item each
+  int nranges;
   int N, K;
-  unsigned int* counter;  // next item (reset to 0 before the launch)
+  unsigned int* counter;  // next work unit (reset to 0 before the launch)
   DevAcc* acc;            // reset to 0 before the launch
 };
 
