@@ -27,6 +27,24 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = "single_n24_k8"
+
+# DRAM bytes (read + write) of one enumeration launch, from an ncu capture of the kernel built
+# from exactly these sources (profiles/k_enumerate_*.md); reported only while the library
+# sources still hash to the captured version, null otherwise.
+TRAFFIC = {"sources_sha256": "1de3b58818513f1cb2806c20626c41567c899b017db9c467dae700a83f281395",
+           "single_n24_k8": 1127424 + 70656, "heavy_quiver_n32_k10": 8005120 + 788224}
+
+
+def sources_sha256() -> str:
+    import hashlib
+    d = os.path.join(ROOT, "paper_1501_02237_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh", ".h", ".cpp")):
+            h.update(f.encode())
+            with open(os.path.join(d, f), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()
 METRIC = "exact (k+1)-subsets tested/sec (exact degrees/sec alongside), 1 GB300"
 UNIT = "subsets/s"
 
@@ -339,7 +357,7 @@ def main():
         assert r["nvol"] == expect_nvol
     e2e_ms = e2e_ms[1:]
     e2e_value = subsets / (statistics.mean(e2e_ms) / 1e3)
-    h2d = N * k * 8 + info["items"] * 16
+    h2d = N * k * 8  # the reduced points; the work list stays on the device after the first call
     d2h = 48
 
     # roofline: the algorithmic int64 work of the plain per-subset method (differences,
@@ -363,7 +381,10 @@ def main():
                 e2e=dict(value=e2e_value, unit=UNIT, h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h,
                          ms_per_step=statistics.mean(e2e_ms), call="bd_degree(A) from host memory"),
                 roofline=dict(bound="alu", achieved=achieved / 1e9, peak=peak_int32 / 1e9, unit="Gop/s",
-                              frac=achieved / peak_int32, traffic=None,
+                              frac=achieved / peak_int32,
+                              traffic=(TRAFFIC.get(args.workload)
+                                       if sources_sha256() == TRAFFIC["sources_sha256"] else None),
+                              traffic_unit="bytes per launch (DRAM read + write, ncu)",
                               ops_per_subset=ops_per_subset,
                               note="int64 ops of the plain per-subset method vs INT32 lane peak "
                                    f"({props.multi_processor_count} SMs x 128 lanes x {sm_max:.0f} MHz)"))
