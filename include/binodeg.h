@@ -85,8 +85,10 @@ int bd_set_stream(void* stream);
  *          is decided exactly.  Denominators and numerators must be nonzero.
  *   seed : lift seed; the result does not depend on it.
  * Host reduction (Smith form, LLL-reduced kernel basis, torsion) runs on the CPU; the
- * volume on the GPU.  dim = 0 gives degree = torsion.  Errors: BD_ERR_ARG, BD_ERR_OVERFLOW,
- * BD_ERR_TIES, BD_ERR_CUDA, BD_ERR_NOMEM.
+ * volume on the GPU.  dim = 0 gives degree = torsion; dim = 1 is a segment, whose normalized
+ * length max - min of the kernel points (and 0) is taken directly (kernel points of any size
+ * below 2^62; the enumeration takes coordinates below 2^40).  Errors: BD_ERR_ARG,
+ * BD_ERR_OVERFLOW, BD_ERR_TIES, BD_ERR_CUDA, BD_ERR_NOMEM.
  */
 int bd_degree(const int64_t* A, int32_t n, int32_t m, const int64_t* coef, uint64_t seed,
               bd_degree_out* out);

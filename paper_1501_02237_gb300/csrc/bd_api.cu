@@ -9,6 +9,7 @@
 #include <new>
 #include <string>
 #include <tuple>
+#include <algorithm>
 #include <vector>
 
 #include "../../include/binodeg.h"
@@ -465,6 +466,16 @@ int bd_degree(const int64_t* A, int32_t n, int32_t m, const int64_t* coef, uint6
     return BD_OK;
   }
   if (r.dim > BD_KMAX) return fail(BD_ERR_ARG, "solution dimension exceeds BD_KMAX");
+  if (r.dim == 1) {  // a segment: NVol_1(conv{0, p_1 .. p_n}) = max - min, cells = distinct values - 1
+    std::vector<int64_t> x(r.points.begin(), r.points.end());  // n kernel points, then the origin
+    std::sort(x.begin(), x.end());
+    const u128 nvol = (u128)((i128)x.back() - (i128)x.front());
+    set_u128(out->nvol_lo, out->nvol_hi, nvol);
+    set_u128(out->degree_lo, out->degree_hi, nvol * r.torsion);
+    out->cells = (uint64_t)(std::unique(x.begin(), x.end()) - x.begin()) - 1;
+    out->subsets = bd::binom(n + 1, 2);
+    return BD_OK;
+  }
   bd_volume_out v;
   rc = bd_volume(r.points.data(), n + 1, r.dim, seed, &v);
   if (rc) return rc;

@@ -217,9 +217,10 @@ bool add_ok(i128 a, i128 b, i128& r) { return !__builtin_add_overflow(a, b, &r);
 // Column by column: the values v = U m_j of the current basis are sent to (g, 0, .., 0) by the
 // unimodular 2x2 Bezout steps of Sec. 3 applied to the basis rows; the row carrying g leaves
 // the basis, the others span exactly the vectors of the old lattice orthogonal to m_j.  The
-// basis is LLL-reduced after every column, which keeps its entries small.  The result is
+// basis is LLL-reduced whenever its entries grow, and after the last column when reduce_last
+// (the kernel points themselves; bases used only for determinants skip it).  The result is
 // saturated: it is a basis of ker(M) intersected with Z^rows.
-bool kernel_rows(const Mat& M, Mat& U, std::string& err) {
+bool kernel_rows(const Mat& M, Mat& U, std::string& err, bool reduce_last = true) {
   const int n = M.r, m = M.c;
   std::vector<std::vector<i128>> B(n, std::vector<i128>(n, 0));
   for (int i = 0; i < n; ++i) B[i][i] = 1;
@@ -239,6 +240,8 @@ bool kernel_rows(const Mat& M, Mat& U, std::string& err) {
     for (int i = 0; i < d; ++i)
       if (v[i] != 0) all_zero = false;
     if (all_zero) continue;  // the whole current lattice is orthogonal to this column
+    int resets = 0;  // mid-way LLL passes on this column (bounded: a lattice whose kernel
+                     // rows must be long would otherwise cycle between growth and reduction)
     for (int guard = 0;; ++guard) {
       int piv = -1, nz = 0;
       for (int i = 0; i < d; ++i)
@@ -254,8 +257,9 @@ bool kernel_rows(const Mat& M, Mat& U, std::string& err) {
       i128 big = 0;
       for (int i = 0; i < d; ++i) {
         if (i == piv || v[i] == 0) continue;
-        i128 q = v[i] / v[piv];  // truncation; the remainder is smaller than |v_piv|
-        const i128 r = v[i] - q * v[piv];
+        const bool narrow = iabs(v[i]) < ((i128)1 << 62) && iabs(v[piv]) < ((i128)1 << 62);
+        i128 q = narrow ? (i128)((int64_t)v[i] / (int64_t)v[piv]) : v[i] / v[piv];  // truncation
+        const i128 r = v[i] - q * v[piv];  // smaller than |v_piv|
         if (2 * iabs(r) > iabs(v[piv])) q += ((r > 0) == (v[piv] > 0)) ? 1 : -1;  // nearest quotient
         for (int c = 0; c < n; ++c) {
           i128 t;
@@ -264,7 +268,8 @@ bool kernel_rows(const Mat& M, Mat& U, std::string& err) {
         }
         v[i] -= q * v[piv];
       }
-      if (big > ((i128)1 << 40) || guard > 4000) {
+      if (big > ((i128)1 << 40) && resets < 3) {
+        ++resets;
         std::vector<i128> flat;
         for (auto& row : B) flat.insert(flat.end(), row.begin(), row.end());
         if (!lll(flat, d, n)) { err = "kernel basis entries exceed 2^62"; return false; }
@@ -276,14 +281,14 @@ bool kernel_rows(const Mat& M, Mat& U, std::string& err) {
             if (!mul_ok(B[i][c], M.at(c, j), pr) || !add_ok(v[i], pr, v[i])) { err = "kernel values overflow"; return false; }
           }
         }
-        if (guard > 8000) { err = "kernel elimination did not converge"; return false; }
       }
+      if (guard > 8000) { err = "kernel elimination did not converge"; return false; }
     }
     B.erase(B.begin());
     i128 big = 0;
     for (auto& r : B)
       for (i128 x : r) big = std::max(big, iabs(x));
-    const bool last_col = (j == m - 1);
+    const bool last_col = reduce_last && (j == m - 1);
 #ifdef BD_DEBUG
     {
       double lb = 0;
@@ -316,8 +321,47 @@ Mat transpose(const Mat& A) {
   return T;
 }
 
-// exact determinant of a k x k i128 matrix (fraction-free elimination, overflow-checked)
+// exact determinant of a k x k i128 matrix (fraction-free elimination, overflow-checked).
+// Every intermediate value is a minor of a, bounded by the product of its row norms
+// (Hadamard); below 2^62 the elimination runs in 64 bits with the exact 2-adic division of
+// the GPU walker, otherwise in checked 128-bit arithmetic.
 bool det_exact(std::vector<i128> a, int k, i128& det) {
+  double lg = 0;
+  bool small = true;
+  for (int r = 0; r < k && small; ++r) {
+    double n2 = 0;
+    for (int j = 0; j < k; ++j) {
+      const i128 x = a[(size_t)r * k + j];
+      if (iabs(x) >= ((i128)1 << 62)) small = false;
+      n2 += (double)x * (double)x;
+    }
+    lg += 0.5 * std::log2(std::max(n2, 1.0));
+  }
+  if (small && lg < 61.9) {
+    std::vector<int64_t> b(a.begin(), a.end());
+    Div64 D = make_div((int64_t)1);
+    int sign = 1;
+    for (int c = 0; c < k; ++c) {
+      int p = -1;
+      for (int r = c; r < k; ++r)
+        if (b[(size_t)r * k + c] != 0) { p = r; break; }
+      if (p < 0) { det = 0; return true; }
+      if (p != c) {
+        for (int j = 0; j < k; ++j) std::swap(b[(size_t)c * k + j], b[(size_t)p * k + j]);
+        sign = -sign;
+      }
+      const int64_t pc = b[(size_t)c * k + c];
+      for (int r = c + 1; r < k; ++r) {
+        const int64_t rc = b[(size_t)r * k + c];
+        for (int j = c + 1; j < k; ++j)
+          b[(size_t)r * k + j] = bareiss(b[(size_t)r * k + j], pc, rc, b[(size_t)c * k + j], D);
+        b[(size_t)r * k + c] = 0;
+      }
+      D = make_div(pc);
+    }
+    det = k == 0 ? 1 : (i128)sign * b[(size_t)(k - 1) * k + (k - 1)];
+    return true;
+  }
   i128 prev = 1;
   int sign = 1;
   for (int c = 0; c < k; ++c) {
@@ -345,20 +389,24 @@ bool det_exact(std::vector<i128> a, int k, i128& det) {
   return true;
 }
 
-// rows I and columns J of an r x r submatrix of A that is nonsingular modulo a prime
+// rows I and columns J of an r x r submatrix of A that is nonsingular modulo a prime.  The
+// primes are below 2^31 (products reduce with 64-bit arithmetic); the rank drops modulo p only
+// when p divides every r x r minor, i.e. the torsion, and torsion < 2^63 is divisible by at
+// most two of them, so one of the first three always serves.
 bool pivot_sets(const Mat& A, int r, std::vector<int>& I, std::vector<int>& J) {
-  const uint64_t primes[4] = {2305843009213693951ull, 4611686018427387847ull, 1000000000000000003ull,
-                              999999999999999989ull};
+  const uint64_t primes[4] = {2147483647ull, 2147483629ull, 2147483587ull, 2147483579ull};
   for (uint64_t pr : primes) {
     const int n = A.r, m = A.c;
     std::vector<uint64_t> M((size_t)n * m);
     for (int i = 0; i < n; ++i)
       for (int j = 0; j < m; ++j) {
-        i128 x = A.at(i, j) % (i128)pr;
-        if (x < 0) x += pr;
+        const i128 a = A.at(i, j);
+        int64_t x = (a >= -((i128)1 << 62) && a < ((i128)1 << 62)) ? (int64_t)a % (int64_t)pr
+                                                                    : (int64_t)(a % (i128)pr);
+        if (x < 0) x += (int64_t)pr;
         M[(size_t)i * m + j] = (uint64_t)x;
       }
-    auto mulmod = [pr](uint64_t a, uint64_t b) { return (uint64_t)((u128)a * b % pr); };
+    auto mulmod = [pr](uint64_t a, uint64_t b) { return a * b % pr; };
     auto inv = [&](uint64_t a) {
       uint64_t r = 1, e = pr - 2;
       while (e) { if (e & 1) r = mulmod(r, a); a = mulmod(a, a); e >>= 1; }
@@ -410,15 +458,15 @@ int reduce_system(const int64_t* A, int n, int m, const int64_t* coef, Reduction
   Mat P0, R;
   if (!kernel_rows(M, P0, err)) return BD_ERR_OVERFLOW;
   const int d = P0.r, rank = n - d;
-  if (!kernel_rows(transpose(M), R, err)) return BD_ERR_OVERFLOW;
+  if (!kernel_rows(transpose(M), R, err, false)) return BD_ERR_OVERFLOW;
   if (R.r != m - rank) { err = "inconsistent kernel dimensions"; return BD_ERR_OVERFLOW; }
   out.rank = rank;
   out.dim = d;
   out.torsion = 1;
   if (rank > 0) {
     Mat X, S;
-    if (!kernel_rows(transpose(P0), X, err)) return BD_ERR_OVERFLOW;  // {y : P_0 y = 0}
-    if (!kernel_rows(transpose(R), S, err)) return BD_ERR_OVERFLOW;   // {x : R x = 0}
+    if (!kernel_rows(transpose(P0), X, err, false)) return BD_ERR_OVERFLOW;  // {y : P_0 y = 0}
+    if (!kernel_rows(transpose(R), S, err, false)) return BD_ERR_OVERFLOW;   // {x : R x = 0}
     std::vector<int> I, J;
     if (X.r != rank || S.r != rank || !pivot_sets(M, rank, I, J)) { err = "rank selection failed"; return BD_ERR_OVERFLOW; }
     std::vector<i128> a((size_t)rank * rank), x((size_t)rank * rank), sm((size_t)rank * rank);
@@ -451,7 +499,8 @@ int reduce_system(const int64_t* A, int n, int m, const int64_t* coef, Reduction
   for (int q = 0; q < n; ++q)
     for (int i = 0; i < d; ++i) {
       const i128 v = P0.at(i, q);
-      if (iabs(v) >= ((i128)1 << 40)) { err = "kernel point coordinate exceeds 2^40"; return BD_ERR_OVERFLOW; }
+      // the enumeration takes coordinates below 2^40; a segment (d = 1) has a closed form
+      if (d > 1 && iabs(v) >= ((i128)1 << 40)) { err = "kernel point coordinate exceeds 2^40"; return BD_ERR_OVERFLOW; }
       out.points[(size_t)q * d + i] = (int64_t)v;
       out.max_abs_coord = std::max<int64_t>(out.max_abs_coord, (int64_t)iabs(v));
     }

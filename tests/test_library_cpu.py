@@ -217,3 +217,29 @@ def test_lockstep_team_matches_oracle(seed, width):
                                   team_width=width)
         assert r["status"] == 0
         assert r["nvol"] == ref, (k, n, force)
+
+
+@pytest.mark.parametrize("seed,n,m", [(198, 46, 45), (234, 42, 41), (711, 39, 38), (5, 6, 5), (13, 12, 11), (44, 20, 19)])
+def test_degree_of_curves_matches_oracle(seed, n, m):
+    # one-dimensional solution sets: the degree is torsion x the length of the segment spanned
+    # by the kernel points and 0 (taken directly, no enumeration), also for kernel vectors far
+    # beyond the enumeration's coordinate range; the oracle runs its own Smith form and volume
+    from oracle.degree import degree as oracle_degree
+    from workloads import random_binomial_system
+    s = random_binomial_system(n, m, seed, max_nonzeros=3 + seed % 4)
+    o = oracle_degree(np.asarray(s.A).tolist())
+    r = bd.degree(s.A)
+    assert r["dim"] == 1 == o.dim
+    assert r["degree"] == o.degree
+
+
+@pytest.mark.parametrize("seed", [38, 39, 75, 118])
+def test_reduce_large_systems_converges(seed):
+    # n ~ 45 variables: the kernel elimination must not cycle between growth and LLL
+    from workloads import random_binomial_system
+    n = 8 + seed % 40
+    m = max(1, n - 1 - seed % 9)
+    s = random_binomial_system(n, m, seed, max_nonzeros=3 + seed % 4)
+    red = bd.reduce(s.A)
+    ref = BinomialStructure(np.asarray(s.A).tolist())
+    assert (red["rank"], red["dim"], red["torsion"]) == (ref.rank, ref.dim, ref.torsion)
