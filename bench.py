@@ -299,22 +299,36 @@ def main():
     plan = bd.Plan(P)
     info = plan.info()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    seed = args.seed + 1000 * rank
+    seed = args.seed  # every rank lifts alike: with N GPUs each enumerates 1/N of the work list
+    if world > 1:
+        from paper_1501_02237_gb300 import shard
 
     # correctness of the timed configuration before timing it
-    res = plan.volume(seed=seed)
+    if world > 1:
+        with torch.cuda.stream(stream):
+            res = shard.volume(plan, seed=seed, stream=stream)
+    else:
+        res = plan.volume(seed=seed)
     expect_nvol = res["nvol"]
 
     def step(i, timing=None):
         # one exact volume pass; a tie (none expected) re-lifts.  Device time is taken with CUDA
-        # events on the launching stream around memset + enumeration kernel + 48-byte result copy.
+        # events on the launching stream around memset + enumeration kernel + 48-byte result copy;
+        # with N GPUs the step is this rank's shard plus the all-reduce of the partial sums.
         attempt, ms = 0, 0.0
         while True:
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            plan.launch(seed=seed + i, attempt=attempt, stream=stream)
-            b.record(stream)
-            out = plan.read()
+            with torch.cuda.stream(stream):
+                a.record(stream)
+                if world > 1:
+                    plan.launch(seed=seed + i, attempt=attempt, stream=stream, shard=rank, shards=world)
+                    out = shard.combine(plan.read())
+                else:
+                    plan.launch(seed=seed + i, attempt=attempt, stream=stream)
+                b.record(stream)
+                if world == 1:
+                    out = plan.read()
+            b.synchronize()
             ms += a.elapsed_time(b)
             if out["ties"] == 0:
                 return out, attempt + 1, ms
@@ -345,17 +359,30 @@ def main():
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         total_ms = float(t.item())
     ms_per_step = total_ms / args.steps
-    value = world * subsets * args.steps / (total_ms / 1e3)
+    value = subsets * args.steps / (total_ms / 1e3)  # one volume per step across all ranks
 
-    # end to end through the public call from a host matrix (pinned copy of A each step)
+    # end to end through the public calls from a host matrix (pinned copy of A each step): with
+    # one GPU bd_degree(A); with N, the host reduction, a plan and the sharded volume
     A_host = torch.from_numpy(np.ascontiguousarray(s.A)).pin_memory()
     e2e_ms = []
     for i in range(max(3, args.steps // 5)):
+        if world > 1:
+            torch.distributed.barrier()
         t0 = time.perf_counter()
-        r = bd.degree(A_host.numpy(), seed=seed + i)
+        if world > 1:
+            p_i = bd.Plan(bd.reduce(A_host.numpy())["points"])
+            with torch.cuda.stream(stream):
+                r = shard.volume(p_i, seed=seed + i, stream=stream)
+            p_i.close()
+        else:
+            r = bd.degree(A_host.numpy(), seed=seed + i)
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
         assert r["nvol"] == expect_nvol
     e2e_ms = e2e_ms[1:]
+    if world > 1:
+        t = torch.tensor([statistics.mean(e2e_ms)], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_ms = [float(t.item())]
     e2e_value = subsets / (statistics.mean(e2e_ms) / 1e3)
     h2d = N * k * 8  # the reduced points; the work list stays on the device after the first call
     d2h = 48
@@ -368,15 +395,15 @@ def main():
     props = torch.cuda.get_device_properties(dev)
     sm_max = clk.get("sm_max_mhz") or 2070.0
     peak_int32 = props.multi_processor_count * 128 * sm_max * 1e6
-    achieved = ops_per_subset * subsets / (ms_per_step / 1e3)
+    achieved = ops_per_subset * (subsets / world) / (ms_per_step / 1e3)  # one GPU's shard
     line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
-                ms_per_step=ms_per_step, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="int64",
+                ms_per_step=ms_per_step, higher_is_better=True, scaling="strong", vs_baseline=None, dtype="int64",
                 data="synthetic",
                 config=dict(workload=args.workload, n=s.n, m=s.m, k=k, points=N, subsets_per_step=subsets,
                             l2="flushed before each timed step (256 MB device write)", items=info["items"],
                             blocks=info["blocks"], warps_per_block=info["warps_per_block"],
                             int_path="int128" if info["int128"] else "int64", max_abs_coord=red["max_abs_coord"]),
-                degrees_per_s=world * args.steps / (total_ms / 1e3), nvol=int(expect_nvol), cells=res["cells"],
+                degrees_per_s=args.steps / (total_ms / 1e3), nvol=int(expect_nvol), cells=res["cells"],
                 clocks=clk, gpu_launches=launches,
                 e2e=dict(value=e2e_value, unit=UNIT, h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h,
                          ms_per_step=statistics.mean(e2e_ms), call="bd_degree(A) from host memory"),

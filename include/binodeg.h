@@ -144,6 +144,15 @@ int bd_plan_create(const int64_t* points, int32_t npts, int32_t k, const bd_plan
 /* Enqueue one pass over all subsets with lifting (seed, attempt) on `stream` (NULL: the
  * thread's stream).  Asynchronous: nothing is copied to or from the host. */
 int bd_plan_launch(bd_plan* plan, uint64_t seed, int32_t attempt, void* stream);
+/* One shard of such a pass (multi-GPU sharding, one process per GPU): the work list's ranges
+ * u with u % shards == shard, 0 <= shard < shards.  The shards of one (seed, attempt) together
+ * cover every subset exactly once, so the exact volume is the sum of the shards' nvol, cells,
+ * singular and ties (an all-reduce of a few words); a tie in any shard means a re-lift for all.
+ * Every shard must use the same plan options on the same GPU model (the work list depends on
+ * the resident warp count; bd_plan_info reports it for a cross-check).  bd_plan_read then
+ * returns this shard's partial sums. */
+int bd_plan_launch_shard(bd_plan* plan, uint64_t seed, int32_t attempt, int32_t shard, int32_t shards,
+                         void* stream);
 /* Wait for the last launch on its stream and read its result. */
 int bd_plan_read(bd_plan* plan, bd_volume_out* out);
 /* The full volume (launch, read, re-lift on ties) with inputs already on the device. */
@@ -313,6 +322,8 @@ typedef struct bd_host_opts {
   int32_t force_int128;  /* nonzero: run the 128-bit walker whatever the bound */
   uint64_t item_subsets; /* work-item split threshold in subsets (0: 4096; 1: deepest items) */
   int32_t team_width;    /* > 1: one team of this many lanes, run as threads in lockstep */
+  int32_t shard;         /* with shards > 1: only the work ranges u with u % shards == shard */
+  int32_t shards;        /* <= 1: the whole enumeration */
   int32_t reserved;      /* 0 */
 } bd_host_opts;
 

@@ -103,14 +103,15 @@ def classify(points, lifts, subsets) -> tuple:
 
 
 def host_volume_lifted(points, lifts, threads: int = 1, force_int128: bool = False, item_subsets: int = 0,
-                       team_width: int = 1) -> dict:
+                       team_width: int = 1, shard: int = 0, shards: int = 1) -> dict:
     """bd_host_volume_lifted: CPU emulation of the enumeration (CPU tests and the native baseline).
     force_int128 runs the 128-bit walker; item_subsets is the work-item split threshold (0: the
-    library's default); team_width > 1 runs one team of that many lanes as threads in lockstep."""
+    library's default); team_width > 1 runs one team of that many lanes as threads in lockstep;
+    shards > 1 runs only shard `shard` of the work list (partial sums)."""
     P, W = i64(points), i64(lifts)
     npts, k = P.shape
     out = VolumeOut()
-    opts = HostOpts(threads, int(force_int128), item_subsets, team_width, 0)
+    opts = HostOpts(threads, int(force_int128), item_subsets, team_width, shard, shards, 0)
     rc = lib().bd_host_volume_lifted(ptr(P), ptr(W), npts, k, C.byref(opts), C.byref(out))
     res = out.as_dict()
     res["status"] = rc
@@ -131,9 +132,12 @@ class Plan:
         check(lib().bd_plan_create(ptr(P), self.npts, self.k, C.byref(opts), C.byref(h)))
         self.handle = h
 
-    def launch(self, seed: int = 0, attempt: int = 0, stream=None) -> None:
+    def launch(self, seed: int = 0, attempt: int = 0, stream=None, shard: int = 0, shards: int = 1) -> None:
         s = getattr(stream, "cuda_stream", stream)
-        check(lib().bd_plan_launch(self.handle, C.c_uint64(seed), attempt, C.c_void_p(s or 0)))
+        if shards > 1:
+            check(lib().bd_plan_launch_shard(self.handle, C.c_uint64(seed), attempt, shard, shards, C.c_void_p(s or 0)))
+        else:
+            check(lib().bd_plan_launch(self.handle, C.c_uint64(seed), attempt, C.c_void_p(s or 0)))
 
     def read(self) -> dict:
         out = VolumeOut()

@@ -61,7 +61,7 @@ class PlanOpts(C.Structure):
 
 class HostOpts(C.Structure):
     _fields_ = [("threads", C.c_int32), ("force_int128", C.c_int32), ("item_subsets", C.c_uint64),
-                ("team_width", C.c_int32), ("reserved", C.c_int32)]
+                ("team_width", C.c_int32), ("shard", C.c_int32), ("shards", C.c_int32), ("reserved", C.c_int32)]
 
 
 class BatchOpts(C.Structure):
@@ -112,6 +112,7 @@ SIGNATURES = {
     "bd_classify": (C.c_int, [I64P, I64P, C.c_int32, C.c_int32, U8P, C.c_int32, I32P, I64P]),
     "bd_plan_create": (C.c_int, [I64P, C.c_int32, C.c_int32, C.POINTER(PlanOpts), C.POINTER(C.c_void_p)]),
     "bd_plan_launch": (C.c_int, [C.c_void_p, C.c_uint64, C.c_int32, C.c_void_p]),
+    "bd_plan_launch_shard": (C.c_int, [C.c_void_p, C.c_uint64, C.c_int32, C.c_int32, C.c_int32, C.c_void_p]),
     "bd_plan_read": (C.c_int, [C.c_void_p, C.POINTER(VolumeOut)]),
     "bd_plan_volume": (C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(VolumeOut)]),
     "bd_plan_info": (C.c_int, [C.c_void_p, I64P]),

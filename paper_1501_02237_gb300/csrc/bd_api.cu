@@ -151,6 +151,8 @@ struct bd_plan {
   cudaStream_t stream = nullptr;
   bool launched = false;
   int attempt = 0;
+  int shard = 0, shards = 1;  // of the last launch
+  uint64_t items_expected = 0;
 };
 
 namespace {
@@ -283,7 +285,7 @@ bd_plan* thread_plan() {
   return h.p;
 }
 
-int plan_launch(bd_plan* p, uint64_t seed, int attempt, cudaStream_t st) {
+int plan_launch(bd_plan* p, uint64_t seed, int attempt, cudaStream_t st, int shard = 0, int shards = 1) {
   BD_CUDA(cudaMemsetAsync(p->d_state, 0, state_bytes(), st));
   bd::EnumParams ep{};
   ep.pts = p->d_pts;
@@ -293,6 +295,10 @@ int plan_launch(bd_plan* p, uint64_t seed, int attempt, cudaStream_t st) {
   ep.nitems = (int)p->items->host.size();
   ep.ranges = p->items->dev_ranges;
   ep.nranges = (int)p->items->ranges.size();
+  ep.shard = shard;
+  ep.shards = shards;
+  uint64_t expected = 0;
+  for (size_t u = (size_t)shard; u < p->items->ranges.size(); u += (size_t)shards) expected += p->items->ranges[u].count;
   ep.N = p->N;
   ep.K = p->K;
   ep.acc = reinterpret_cast<bd::DevAcc*>(p->d_state);
@@ -302,6 +308,9 @@ int plan_launch(bd_plan* p, uint64_t seed, int attempt, cudaStream_t st) {
   p->stream = st;
   p->launched = true;
   p->attempt = attempt;
+  p->shard = shard;
+  p->shards = shards;
+  p->items_expected = expected;
   return BD_OK;
 }
 
@@ -320,7 +329,7 @@ int plan_read(bd_plan* p, bd_volume_out* out) {
   out->flags = (p->path == bd::PATH_WIDE ? BD_FLAG_INT128 : 0) | ((a.nvol_lo | a.nvol_hi) == 0 ? BD_FLAG_DEGENERATE : 0);
   out->max_abs_coord = (int32_t)std::min<int64_t>(p->max_abs, INT32_MAX);
   out->bound_bits = (int32_t)std::ceil(p->bound);
-  if (a.items_done != p->items->host.size()) return fail(BD_ERR_CUDA, "enumeration did not process every work item");
+  if (a.items_done != p->items_expected) return fail(BD_ERR_CUDA, "enumeration did not process every work item");
   return BD_OK;
 }
 
@@ -364,6 +373,13 @@ int bd_plan_create(const int64_t* points, int32_t npts, int32_t k, const bd_plan
 int bd_plan_launch(bd_plan* plan, uint64_t seed, int32_t attempt, void* stream) {
   if (!plan) return fail(BD_ERR_ARG, "plan is NULL");
   return plan_launch(plan, seed, attempt, stream ? reinterpret_cast<cudaStream_t>(stream) : g_stream);
+}
+
+int bd_plan_launch_shard(bd_plan* plan, uint64_t seed, int32_t attempt, int32_t shard, int32_t shards,
+                         void* stream) {
+  if (!plan) return fail(BD_ERR_ARG, "plan is NULL");
+  if (shards < 1 || shard < 0 || shard >= shards) return fail(BD_ERR_ARG, "need 0 <= shard < shards");
+  return plan_launch(plan, seed, attempt, stream ? reinterpret_cast<cudaStream_t>(stream) : g_stream, shard, shards);
 }
 
 int bd_plan_read(bd_plan* plan, bd_volume_out* out) {
@@ -553,6 +569,8 @@ int bd_host_volume_lifted(const int64_t* points, const int64_t* lifts, int32_t n
   if (!out || !lifts) return fail(BD_ERR_ARG, "NULL argument");
   const bd_host_opts o = opts ? *opts : bd_host_opts{};
   if (o.team_width > 64) return fail(BD_ERR_ARG, "team_width above 64");
+  const int shards = o.shards > 1 ? o.shards : 1;
+  if (o.shard < 0 || o.shard >= shards) return fail(BD_ERR_ARG, "need 0 <= shard < shards");
   int rc = check_points(points, npts, k);
   if (rc) return rc;
   if (npts < k + 1) {
@@ -579,6 +597,11 @@ int bd_host_volume_lifted(const int64_t* points, const int64_t* lifts, int32_t n
   std::vector<bd::Item> items;
   std::vector<bd::Range> ranges;
   bd::build_ranges(npts, k, o.item_subsets ? o.item_subsets : 4096, 8, items, ranges);
+  if (shards > 1) {  // this shard's ranges only (u % shards == shard, as on the device)
+    std::vector<bd::Range> mine;
+    for (size_t u = (size_t)o.shard; u < ranges.size(); u += (size_t)shards) mine.push_back(ranges[u]);
+    ranges.swap(mine);
+  }
   bd::Acc acc{};
   bd::host_enumerate(path, P.data(), npts, k, items, std::max(1, o.threads), acc, o.team_width, &ranges);
   std::memset(out, 0, sizeof(*out));

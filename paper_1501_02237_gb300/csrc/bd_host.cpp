@@ -719,7 +719,8 @@ struct LockstepTeam {
 };
 
 template <class TC, class TL>
-void lockstep_run(const int64_t* P, int N, int K, const std::vector<Item>& items, int width, Acc& acc) {
+void lockstep_run(const int64_t* P, int N, int K, const std::vector<Item>& items, const std::vector<Range>* ranges,
+                  int width, Acc& acc) {
   LockstepShared sh(width);
   std::vector<TC> sc((size_t)N * stack_entries(K));
   std::vector<TL> sl((size_t)N * K);
@@ -731,7 +732,12 @@ void lockstep_run(const int64_t* P, int N, int K, const std::vector<Item>& items
       LockstepTeam tm{&sh, l};
       Walker<TC, TL, LockstepTeam> W(tm, P, N, K, N, sc.data(), sl.data(), fl.data());
       Acc a{};
-      for (const Item& it : items) W.run_item(it, a);
+      if (ranges) {
+        for (const Range& r : *ranges)
+          for (uint32_t i = r.first; i < r.first + r.count; ++i) W.run_item(items[i], a);
+      } else {
+        for (const Item& it : items) W.run_item(it, a);
+      }
       part[l] = a;
     });
   for (auto& t : th) t.join();
@@ -783,10 +789,10 @@ void host_run(const int64_t* P, int N, int K, const std::vector<Item>& items, co
 
 void host_enumerate(int path, const int64_t* P, int N, int K, const std::vector<Item>& items, int threads, Acc& acc,
                     int team_width, const std::vector<Range>* ranges) {
-  if (team_width > 1) {  // one team walks every item in order (ranges are contiguous anyway)
-    if (path == 0) lockstep_run<int32_t, int64_t>(P, N, K, items, team_width, acc);
-    else if (path == 1) lockstep_run<int64_t, int64_t>(P, N, K, items, team_width, acc);
-    else lockstep_run<i128, i128>(P, N, K, items, team_width, acc);
+  if (team_width > 1) {  // one team walks every range in order
+    if (path == 0) lockstep_run<int32_t, int64_t>(P, N, K, items, ranges, team_width, acc);
+    else if (path == 1) lockstep_run<int64_t, int64_t>(P, N, K, items, ranges, team_width, acc);
+    else lockstep_run<i128, i128>(P, N, K, items, ranges, team_width, acc);
     return;
   }
   if (path == 0) host_run<int32_t, int64_t>(P, N, K, items, ranges, threads, acc);

@@ -139,10 +139,12 @@ __global__ void BD_ENUM_BOUNDS k_enumerate(EnumParams p) {
   Acc acc{};
   unsigned long long done = 0;
   const unsigned int units = p.ranges ? (unsigned int)p.nranges : (unsigned int)p.nitems;
+  const unsigned int shards = p.shards > 1 ? (unsigned int)p.shards : 1u;
   for (;;) {
     unsigned int u = 0;
     if (lane == 0) u = atomicAdd(p.counter, 1u);
     u = __shfl_sync(0xffffffffu, u, 0);
+    u = u * shards + (unsigned int)p.shard;  // this shard's units only
     if (u >= units) break;
     const Range r = p.ranges ? p.ranges[u] : Range{u, 1u};
     for (unsigned int i = r.first; i < r.first + r.count; ++i) {

@@ -23,6 +23,7 @@ struct EnumParams {
   int nitems;
   const Range* ranges;    // work units: ranges of consecutive items, or nullptr: one item each
   int nranges;
+  int shard, shards;      // this launch takes the units u with u % shards == shard (shards >= 1)
   int N, K;
   unsigned int* counter;  // next work unit (reset to 0 before the launch)
   DevAcc* acc;            // reset to 0 before the launch

@@ -202,3 +202,30 @@ def test_inconsistent_and_zero_dimensional():
     assert (r["degree"], r["dim"]) == (6, 0)
     assert bd.degree(np.array([[-2], [1]]))["degree"] == 2
     assert bd.degree(np.array([[2], [2]]))["degree"] == oracle_degree([[2], [2]]).degree == 4
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("name", ["small_n10_k4", "single_n24_k8"])
+def test_shards_cover_every_subset_once(name):
+    # the shards of one launch (run one after another on this GPU: they never wait on each
+    # other) add up to the whole enumeration, for several shard counts
+    P = bd.reduce(config_system(name).A)["points"]
+    plan = bd.Plan(P)
+    full = plan.volume(seed=0)
+    for world in (2, 3, 8):
+        parts = []
+        for r in range(world):
+            plan.launch(seed=0, attempt=full["relifts"], shard=r, shards=world)
+            parts.append(plan.read())
+        for key in ("nvol", "cells", "singular", "ties"):
+            assert sum(p[key] for p in parts) == full[key], (world, key)
+        assert all(p["nvol"] > 0 for p in parts) or name == "small_n10_k4"
+    plan.close()
+
+
+@pytest.mark.gpu
+def test_shard_arguments_are_checked():
+    plan = bd.Plan(bd.reduce(config_system("small_n10_k4").A)["points"])
+    with pytest.raises(bd.BinodegError):
+        plan.launch(seed=0, shard=2, shards=2)
+    plan.close()
