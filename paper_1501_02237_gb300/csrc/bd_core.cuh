@@ -35,6 +35,7 @@
 
 #include <math.h>
 #include <stdint.h>
+#include <string.h>
 
 #ifdef __CUDACC__
 #define BD_HD __host__ __device__ __forceinline__
@@ -190,6 +191,15 @@ BD_HD i128 bareiss(i128 a, i128 p, i128 b, i128 r, const Div128& D) {
   return (i128)(q * D.inv);
 }
 
+// square root of v >= 1 to a few ulps (the callers correct the integer part they take from it)
+BD_HD float approx_sqrt(float v) {
+#ifdef __CUDA_ARCH__
+  return v * rsqrtf(v);
+#else
+  return sqrtf(v);
+#endif
+}
+
 // single-precision value of a 64-bit integer without a 64-bit conversion instruction: the
 // magnitude is split into 32-bit halves, each converted (one rounding each) and recombined by
 // one fused multiply-add, so the relative error is at most 2^-23.
@@ -319,6 +329,124 @@ template <> struct Wide2<int32_t> { typedef int64_t type; };
 template <> struct Wide2<int64_t> { typedef i128 type; };
 template <> struct Wide2<i128> { typedef i128 type; };  // unused: the 128-bit path tests in 2-D
 
+// Up to 15 point indices below 64, six bits each, in two registers (entries 0..9 in lo,
+// 10..14 in hi): the walk's prefix and cursor live here instead of in per-thread local arrays,
+// which the compiler would place in local memory (dynamic indices).
+struct Idx15 {
+  uint64_t lo = 0, hi = 0;
+  BD_HD int get(int j) const {
+    return j < 10 ? (int)((lo >> (6 * j)) & 63u) : (int)((hi >> (6 * (j - 10))) & 63u);
+  }
+  BD_HD void set(int j, int v) {
+    if (j < 10) lo = (lo & ~(63ull << (6 * j))) | ((uint64_t)v << (6 * j));
+    else hi = (hi & ~(63ull << (6 * (j - 10)))) | ((uint64_t)v << (6 * (j - 10)));
+  }
+};
+
+// The pivots and exact dividers of the levels: the same for every lane of a team, so one copy
+// per team (in shared memory on the GPU), written by lane 0 and read after a team sync.
+template <class TC>
+struct Uniform {
+  TC piv[KMAX];                        // the pivots p_j (piv[0] = 1)
+  typename DivOf<TC>::type dv[KMAX];   // exact divider by p_j (dv[0]: by 1)
+};
+constexpr size_t kUniformBytes = 1024;  // room for Uniform<TC> of every coordinate type
+
+static_assert(sizeof(Uniform<i128>) <= kUniformBytes, "uniform state area too small");
+static_assert(sizeof(Item) == 16, "an item is four words");
+
+// The reduced state that a walker's exact routes read.  The routes run out of line and take it
+// by value: a pointer to the walker itself would pin the whole walker in local memory.
+template <class TC, class TL>
+struct StateView {
+  const TC* sc;
+  const TL* sl;
+  const Uniform<TC>* u;
+  int SLOTS, K;
+};
+
+// level K-1 minors of point x for pivot row c on state K-2 (the exact route of a Bareiss step
+// for one point)
+template <class TC, class TL>
+BD_HD void exact_pair_minors(const StateView<TC, TL>& v, int c, int x, TL& C, TL& L) {
+  const int o = level_offset(v.K, v.K - 2), S = v.SLOTS;
+  const TC xc = v.sc[o * S + c], yc = v.sc[(o + 1) * S + c];
+  const int pi = xc != 0 ? 0 : 1;
+  const TC a = pi == 0 ? xc : yc, b = pi == 0 ? yc : xc;
+  const TC ex_pi = v.sc[(o + pi) * S + x], ex_o = v.sc[(o + 1 - pi) * S + x];
+  const typename DivOf<TC>::type D = v.u->dv[v.K - 2];
+  C = (TL)bareiss(ex_o, a, ex_pi, b, D);
+  L = bareiss(v.sl[(v.K - 2) * S + x], a, ex_pi, v.sl[(v.K - 2) * S + c], D);
+}
+
+// exact: C_p L_q - C_q L_p on the reduced state K-2, with the 2-D sign rule (rarely reached)
+template <class TC, class TL>
+BD_COLD int side3_exact(StateView<TC, TL> v, int c, int p, int q, int sig, TC xc, TC yc) {
+  TL Cp, Lp, Cq, Lq;
+  exact_pair_minors(v, c, p, Cp, Lp);
+  exact_pair_minors(v, c, q, Cq, Lq);
+  const int cs = cross_sign(Cp, Lq, Cq, Lp);
+  const int pc = (xc != 0 ? xc : yc) < 0 ? -1 : 1;
+  // below iff cs != 0 and cs != sign(C_p) * sign(pivot of c); map onto sig's convention
+  return cs == 0 ? 0 : ((cs == ((Cp < 0 ? -1 : 1) * pc)) ? sig : -sig);
+}
+
+// level K-2 values of point x after the Bareiss step with pivot row c1 on state K-3 (two
+// coordinate minors X, Y and the lift minor L); a is c1's pivot, pi its column (-1: none)
+template <class TC, class TL>
+BD_HD void level_after(const StateView<TC, TL>& v, int c1, int x, TC& X, TC& Y, TL& L, TC& a, int& pi) {
+  const int o = level_offset(v.K, v.K - 3), S = v.SLOTS;
+  pi = -1;
+  for (int e = 0; e < 3; ++e)
+    if (v.sc[(o + e) * S + c1] != 0) { pi = e; break; }
+  if (pi < 0) { X = Y = 0; L = 0; a = 0; return; }
+  a = v.sc[(o + pi) * S + c1];
+  const TC bq = v.sc[(o + pi) * S + x];
+  const int r0 = pi == 0 ? 1 : 0, r1 = pi == 2 ? 1 : 2;
+  const typename DivOf<TC>::type D = v.u->dv[v.K - 3];
+  X = bareiss(v.sc[(o + r0) * S + x], a, bq, v.sc[(o + r0) * S + c1], D);
+  Y = bareiss(v.sc[(o + r1) * S + x], a, bq, v.sc[(o + r1) * S + c1], D);
+  L = bareiss(v.sl[(v.K - 3) * S + x], a, bq, v.sl[(v.K - 3) * S + c1], D);
+}
+
+// exact K x K minor of {s_0 .. s_{K-3}, c1, c, p} with the sign of D (the coordinate det3 on
+// state K-3): moving c1's pivot column pi to the front permutes the columns by (-1)^pi
+template <class TC, class TL>
+BD_COLD typename Wide2<TC>::type exact_minor(StateView<TC, TL> v, int c1, int c, int p) {
+  typedef typename Wide2<TC>::type W2;
+  TC Xc, Yc, Xp, Yp, a;
+  TL Lc, Lp;
+  int pi;
+  level_after(v, c1, c, Xc, Yc, Lc, a, pi);
+  if (pi < 0) return 0;
+  level_after(v, c1, p, Xp, Yp, Lp, a, pi);
+  const W2 m = ((W2)Xc * Yp - (W2)Yc * Xp) / (W2)a;  // exact
+  return pi == 1 ? -m : m;
+}
+
+// exact side of q for the nonsingular triple (c1, c, p), in the convention of sig (0 on the
+// hyperplane, sig above, -sig below)
+template <class TC, class TL>
+BD_COLD int side4_exact(StateView<TC, TL> v, int c1, int c, int p, int q, int sig) {
+  TC Xc, Yc, Xp, Yp, Xq, Yq, a;
+  TL Lc, Lp, Lq;
+  int pi;
+  level_after(v, c1, c, Xc, Yc, Lc, a, pi);
+  level_after(v, c1, p, Xp, Yp, Lp, a, pi);
+  level_after(v, c1, q, Xq, Yq, Lq, a, pi);
+  const typename DivOf<TC>::type D = make_div(a);
+  const bool px = Xc != 0;  // c's pivot column on state K-2
+  const TC b = px ? Xc : Yc, ob = px ? Yc : Xc;
+  const TL Cp = (TL)bareiss(px ? Yp : Xp, b, px ? Xp : Yp, ob, D);
+  const TL Cq = (TL)bareiss(px ? Yq : Xq, b, px ? Xq : Yq, ob, D);
+  const TL Mp = bareiss(Lp, b, px ? Xp : Yp, Lc, D);
+  const TL Mq = bareiss(Lq, b, px ? Xq : Yq, Lc, D);
+  const int cs = cross_sign(Cp, Mq, Cq, Mp);
+  if (cs == 0) return 0;
+  const bool below = cs != (Cp < 0 ? -1 : 1) * (b < 0 ? -1 : 1);  // the 2-D rule
+  return below ? -sig : sig;
+}
+
 template <class TC, class TL, class Team>
 struct Walker {
   typedef typename DivOf<TC>::type Div;
@@ -328,17 +456,18 @@ struct Walker {
   TC* sc;           // coordinate minors: (level j, entry e, point q) at sc[(off_j + e) * SLOTS + q]
   TL* sl;           // lift minor of level j for point q at sl[j * SLOTS + q]
   float* fl;        // single-precision copies for the filters: 4 rows of SLOTS floats
-  int s[KMAX + 1];  // chosen indices s_0 .. s_j
-  Div dv[KMAX];     // exact divider by the pivot of each level (dv[0]: by 1)
-  TC piv[KMAX];     // the pivots p_j (piv[0] = 1)
+  Uniform<TC>* u;   // pivots and dividers (team-shared)
+  Idx15 s;          // chosen indices s_0 .. s_j
   int psign;        // sign of the level K-1 pivot p_{K-1} (2-D test)
   int valid = 0;    // states 0 .. valid-1 are those of s_0 .. s_{valid-1} (kept across items)
 #ifdef BD_COUNT
   Acc* cnt = nullptr;
 #endif
 
-  BD_HD Walker(Team& t, const int64_t* P_, int N_, int K_, int SLOTS_, TC* sc_, TL* sl_, float* fl_)
-      : tm(t), P(P_), N(N_), K(K_), SLOTS(SLOTS_), sc(sc_), sl(sl_), fl(fl_) {}
+  BD_HD Walker(Team& t, const int64_t* P_, int N_, int K_, int SLOTS_, TC* sc_, TL* sl_, float* fl_, void* uni)
+      : tm(t), P(P_), N(N_), K(K_), SLOTS(SLOTS_), sc(sc_), sl(sl_), fl(fl_), u(static_cast<Uniform<TC>*>(uni)) {}
+
+  BD_HD StateView<TC, TL> view() const { return StateView<TC, TL>{sc, sl, u, SLOTS, K}; }
 
   // the single-precision filtered tests run for the int32 and int64 coordinate paths: the 4-D
   // test on state K-3 when K >= 3, the 3-D test on state 0 when K = 2; the 128-bit path and
@@ -351,7 +480,7 @@ struct Walker {
   // state 0: lifted differences z_q = (a_q - a_{s_0}, w_q - w_{s_0})
   BD_HD void start(int s0) {
     tm.sync();  // the previous item's readers are done with the stack
-    s[0] = s0;
+    s.set(0, s0);
     const bool conv = kFiltered && K == 3;  // state 0 is the 4-D stage's input
     for (int q = tm.lane(); q < N; q += tm.lanes()) {
       for (int c = 0; c < K; ++c) {
@@ -363,8 +492,10 @@ struct Walker {
       sl[q] = l;
       if (conv) fl[3 * SLOTS + q] = f32_of(l);
     }
-    dv[0] = make_div((TC)1);
-    piv[0] = 1;
+    if (tm.lane() == 0) {
+      u->dv[0] = make_div((TC)1);
+      u->piv[0] = 1;
+    }
     psign = 1;
     tm.sync();
   }
@@ -384,7 +515,7 @@ struct Walker {
     if (pi < 0) return false;
     const TC pj = sc[(po + pi) * SLOTS + c];
     const TL rl = sl[(j - 1) * SLOTS + c];
-    const Div D = dv[j - 1];
+    const Div D = u->dv[j - 1];
     tm.sync();  // readers of the old state j (a sibling's subtree) are done
     // state K-3 is the 4-D stage's input: its single-precision copies are written here too
     const bool conv = kFiltered && j == K - 3;
@@ -400,16 +531,18 @@ struct Walker {
       sl[j * SLOTS + q] = l;
       if (conv) fl[3 * SLOTS + q] = f32_of(l);
     }
-    s[j] = c;
-    piv[j] = pj;
-    dv[j] = make_div(pj);
+    s.set(j, c);
+    if (tm.lane() == 0) {
+      u->piv[j] = pj;
+      u->dv[j] = make_div(pj);
+    }
     tm.sync();
     return true;
   }
 
   BD_HD uint64_t member_mask(int upto) const {
     uint64_t mask = 0;
-    for (int i = 0; i < upto; ++i) mask |= 1ull << s[i];
+    for (int i = 0; i < upto; ++i) mask |= 1ull << s.get(i);
     return mask;
   }
 
@@ -421,7 +554,7 @@ struct Walker {
     if (K == 1) {
       uint64_t mine = 0;
       for (int q = tm.lane(); q < N; q += tm.lanes()) {
-        if (q > s[0] && sc[q] != 0) mine |= 1ull << q;
+        if (q > s.get(0) && sc[q] != 0) mine |= 1ull << q;
         fl[q] = (float)sc[q];
         fl[SLOTS + q] = (float)sl[q];
       }
@@ -430,7 +563,7 @@ struct Walker {
       return cand;
     }
     if (!build(K - 1, c)) return 0;
-    psign = piv[K - 1] < 0 ? -1 : 1;
+    psign = u->piv[K - 1] < 0 ? -1 : 1;
     const int o = level_offset(K, K - 1);
     uint64_t mine = 0;
     for (int q = tm.lane(); q < N; q += tm.lanes()) {
@@ -469,11 +602,11 @@ struct Walker {
     const bool lead = tm.lane() == 0;
     if (K == 1) {
       const uint64_t cand = build_last(0);
-      if (lead) acc.singular += (uint64_t)(N - 1 - s[0]) - (uint64_t)popc64(cand);
+      if (lead) acc.singular += (uint64_t)(N - 1 - s.get(0)) - (uint64_t)popc64(cand);
       leaves2(cand, acc);
       return;
     }
-    for (int c = s[K - 2] + 1; c <= N - 2; ++c) {
+    for (int c = s.get(K - 2) + 1; c <= N - 2; ++c) {
       const uint64_t cand = build_last(c);
       if (lead) acc.singular += (uint64_t)(N - 1 - c) - (uint64_t)popc64(cand);
       if (cand) leaves2(cand, acc);
@@ -504,18 +637,6 @@ struct Walker {
   // ---------------------------------------------------------------------------------------
   typedef typename Wide2<TC>::type W2;
 
-  BD_HD void exact_pair_minors(int c, int x, TL& C, TL& L) const {
-    // level K-1 minors of point x for pivot row c (the exact route of build for one point)
-    const int o = level_offset(K, K - 2);
-    const TC xc = sc[o * SLOTS + c], yc = sc[(o + 1) * SLOTS + c];
-    const int pi = xc != 0 ? 0 : 1;
-    const TC a = pi == 0 ? xc : yc, b = pi == 0 ? yc : xc;
-    const TC ex_pi = sc[(o + pi) * SLOTS + x], ex_o = sc[(o + 1 - pi) * SLOTS + x];
-    const Div& D = dv[K - 2];
-    C = (TL)bareiss(ex_o, a, ex_pi, b, D);
-    L = bareiss(sl[(K - 2) * SLOTS + x], a, ex_pi, sl[(K - 2) * SLOTS + c], D);
-  }
-
   // the test of one lane-owned point q against the pair (c, p); 0 tie, +-1 side, computed
   // exactly when the single-precision value is too close to zero
   BD_HD int side3(int c, int p, int q, float nx, float ny, float nz, float ax, float ay, float az, float xq,
@@ -527,19 +648,7 @@ struct Walker {
     const float bound = 7.63e-6f * fmaf(ax, fabsf(xq), fmaf(ay, fabsf(yq), az * fabsf(lq)));
     if (v > bound) return 1;
     if (v < -bound) return -1;
-    return side3_exact(c, p, q, sig, xc, yc);
-  }
-
-  // exact: C_p L_q - C_q L_p on the reduced state, with the 2-D sign rule (rarely reached;
-  // kept out of line so that the common path keeps its registers)
-  BD_COLD int side3_exact(int c, int p, int q, int sig, TC xc, TC yc) const {
-    TL Cp, Lp, Cq, Lq;
-    exact_pair_minors(c, p, Cp, Lp);
-    exact_pair_minors(c, q, Cq, Lq);
-    const int cs = cross_sign(Cp, Lq, Cq, Lp);
-    const int pc = (xc != 0 ? xc : yc) < 0 ? -1 : 1;
-    // below iff cs != 0 and cs != sign(C_p) * sign(pivot of c); map onto sig's convention
-    return cs == 0 ? 0 : ((cs == ((Cp < 0 ? -1 : 1) * pc)) ? sig : -sig);
+    return side3_exact(view(), c, p, q, sig, xc, yc);
   }
 
   // The pairs (c, p), s_{K-2} < c < p < N, are taken in lexicographic order, one per lane and a
@@ -550,7 +659,7 @@ struct Walker {
   // (summed over the warp by the caller).
   BD_HD void bottom3(Acc& acc) {
     const int o = level_offset(K, K - 2);
-    const TC dp = piv[K - 2];
+    const TC dp = u->piv[K - 2];
     const int sd = dp < 0 ? -1 : 1;
     const uint64_t prefix = member_mask(K - 1);
     for (int q = tm.lane(); q < N; q += tm.lanes()) {
@@ -560,7 +669,7 @@ struct Walker {
     }
     tm.sync();
     // this lane's pair: the lane-th pair, then every lanes()-th one
-    int c = s[K - 2] + 1, p = c + 1 + tm.lane();
+    int c = s.get(K - 2) + 1, p = c + 1 + tm.lane();
     for (;;) {
       while (p >= N && c < N - 2) {  // carry into the next c: N-1-c pairs per c
         p -= N - c - 2;
@@ -638,63 +747,11 @@ struct Walker {
   // (pivot rows c1, then c) and the 2-D rule, as the 2-D path would.
   // ---------------------------------------------------------------------------------------
 
-  // level K-2 values of point x after the Bareiss step with pivot row c1 on state K-3 (two
-  // coordinate minors X, Y and the lift minor L); a is c1's pivot, pi its column (-1: none)
-  BD_HD void level_after(int c1, int x, TC& X, TC& Y, TL& L, TC& a, int& pi) const {
-    const int o = level_offset(K, K - 3);
-    pi = -1;
-    for (int e = 0; e < 3; ++e)
-      if (sc[(o + e) * SLOTS + c1] != 0) { pi = e; break; }
-    if (pi < 0) { X = Y = 0; L = 0; a = 0; return; }
-    a = sc[(o + pi) * SLOTS + c1];
-    const TC bq = sc[(o + pi) * SLOTS + x];
-    const int r0 = pi == 0 ? 1 : 0, r1 = pi == 2 ? 1 : 2;
-    const Div& D = dv[K - 3];
-    X = bareiss(sc[(o + r0) * SLOTS + x], a, bq, sc[(o + r0) * SLOTS + c1], D);
-    Y = bareiss(sc[(o + r1) * SLOTS + x], a, bq, sc[(o + r1) * SLOTS + c1], D);
-    L = bareiss(sl[(K - 3) * SLOTS + x], a, bq, sl[(K - 3) * SLOTS + c1], D);
-  }
-
-  // exact K x K minor of {s_0 .. s_{K-3}, c1, c, p} with the sign of D (the coordinate det3 on
-  // state K-3): moving c1's pivot column pi to the front permutes the columns by (-1)^pi
-  BD_COLD W2 exact_minor(int c1, int c, int p) const {
-    TC Xc, Yc, Xp, Yp, a;
-    TL Lc, Lp;
-    int pi;
-    level_after(c1, c, Xc, Yc, Lc, a, pi);
-    if (pi < 0) return 0;
-    level_after(c1, p, Xp, Yp, Lp, a, pi);
-    const W2 m = ((W2)Xc * Yp - (W2)Yc * Xp) / (W2)a;  // exact
-    return pi == 1 ? -m : m;
-  }
-
-  // exact side of q for the nonsingular triple (c1, c, p), in the convention of sig (0 on the
-  // hyperplane, sig above, -sig below)
-  BD_COLD int side4_exact(int c1, int c, int p, int q, int sig) const {
-    TC Xc, Yc, Xp, Yp, Xq, Yq, a;
-    TL Lc, Lp, Lq;
-    int pi;
-    level_after(c1, c, Xc, Yc, Lc, a, pi);
-    level_after(c1, p, Xp, Yp, Lp, a, pi);
-    level_after(c1, q, Xq, Yq, Lq, a, pi);
-    const Div D = make_div(a);
-    const bool px = Xc != 0;  // c's pivot column on state K-2
-    const TC b = px ? Xc : Yc, ob = px ? Yc : Xc;
-    const TL Cp = (TL)bareiss(px ? Yp : Xp, b, px ? Xp : Yp, ob, D);
-    const TL Cq = (TL)bareiss(px ? Yq : Xq, b, px ? Xq : Yq, ob, D);
-    const TL Mp = bareiss(Lp, b, px ? Xp : Yp, Lc, D);
-    const TL Mq = bareiss(Lq, b, px ? Xq : Yq, Lc, D);
-    const int cs = cross_sign(Cp, Mq, Cq, Mp);
-    if (cs == 0) return 0;
-    const bool below = cs != (Cp < 0 ? -1 : 1) * (b < 0 ? -1 : 1);  // the 2-D rule
-    return below ? -sig : sig;
-  }
-
   // The triples (c1, c, p), s_{K-3} < c1 < c < p < N, are dealt to lanes in colex order, a
   // warp-width per round; each lane walks the points q in index order and stops at the first
   // one strictly below its cell; the round ends when every lane has a verdict.
   BD_HD void bottom4(Acc& acc) {
-    const int sd = piv[K - 3] < 0 ? -1 : 1;
+    const int sd = u->piv[K - 3] < 0 ? -1 : 1;
     const uint64_t prefix = member_mask(K - 2);
     // fl holds the single-precision copies of state K-3 (written by the step that built it).
     // Error bounds, u = 2^-24: every term of det4 is a product of four point copies (2u each,
@@ -709,7 +766,7 @@ struct Walker {
     // Triple number t in colex order (by p, then c, then c1) is decoded directly:
     // C(k,3) <= t < C(k+1,3), then C(j,2) <= t - C(k,3) < C(j+1,2), i = t - C(k,3) - C(j,2),
     // and (c1, c, p) = s_{K-3} + 1 + (i, j, k).  k never decreases for a lane.
-    const int base = s[K - 3] + 1, R = N - base;
+    const int base = s.get(K - 3) + 1, R = N - base;
     const int total = R * (R - 1) * (R - 2) / 6;
     int k = 2;
     for (int t0 = 0; t0 < total; t0 += tm.lanes()) {
@@ -719,7 +776,7 @@ struct Walker {
       if (live) {
         while ((k + 1) * k * (k - 1) / 6 <= t) ++k;
         const int u = t - k * (k - 1) * (k - 2) / 6;
-        int jj = (int)((1.0f + sqrtf(8.0f * (float)u + 1.0f)) * 0.5f);
+        int jj = (int)((1.0f + approx_sqrt(8.0f * (float)u + 1.0f)) * 0.5f);
         if (jj * (jj - 1) / 2 > u) --jj;
         else if ((jj + 1) * jj / 2 <= u) ++jj;
         c1 = base + u - jj * (jj - 1) / 2;
@@ -740,7 +797,7 @@ struct Walker {
         const float B3 = fabsf(a0) * M12 + fabsf(a1) * M02 + fabsf(a2) * M01;
         if (fabsf(D3) > eps * B3 || B3 < 8388608.0f) s3 = (D3 > 0) - (D3 < 0);
         else {
-          const W2 m = exact_minor(c1, c, p);
+          const W2 m = exact_minor(view(), c1, c, p);
           s3 = (m > 0) - (m < 0);
         }
         if (s3 == 0) {
@@ -776,7 +833,7 @@ struct Walker {
         const float x0 = fl[q], x1 = fl[SLOTS + q], x2 = fl[2 * SLOTS + q], x3 = fl[3 * SLOTS + q];
         const float v = fmaf(n0, x0, fmaf(n1, x1, fmaf(n2, x2, n3 * x3)));
         const float bound = fmaf(e0, fabsf(x0), fmaf(e1, fabsf(x1), fmaf(e2, fabsf(x2), e3 * fabsf(x3))));
-        const int sg = v > bound ? 1 : (v < -bound ? -1 : side4_exact(c1, c, p, q, sig));
+        const int sg = v > bound ? 1 : (v < -bound ? -1 : side4_exact(view(), c1, c, p, q, sig));
         if (sg == 0) on = true;
         else if (sg != sig) below = true;
       }
@@ -788,7 +845,7 @@ struct Walker {
           acc.ties += 1;
         } else {
           acc.cells += 1;
-          const W2 m = exact_minor(c1, c, p);
+          const W2 m = exact_minor(view(), c1, c, p);
           acc.nvol += (u128)(m < 0 ? -m : m);
         }
       }
@@ -808,30 +865,41 @@ struct Walker {
     const int L = it.len;
     const int B = bottom_depth();
     const bool lead = tm.lane() == 0;  // uniform counts are added once per team
+    // the item's bytes as four words in registers; prefix index j is byte j+1
+    uint32_t w[4];
+    memcpy(w, &it, sizeof(w));
+    const uint32_t w0 = w[0], w1 = w[1], w2 = w[2], w3 = w[3];
+    auto pre = [&](int j) -> int {
+      const int b = j + 1, wi = b >> 2;
+      const uint32_t x = wi == 0 ? w0 : (wi == 1 ? w1 : (wi == 2 ? w2 : w3));
+      return (int)((x >> ((b & 3) * 8)) & 255u);
+    };
+    const int last = pre(L - 1);
     int m = 0;
-    while (m < valid && m < L && s[m] == it.idx[m]) ++m;
+    while (m < valid && m < L && s.get(m) == pre(m)) ++m;
     if (m == 0) {
-      start(it.idx[0]);
+      start(pre(0));
       m = 1;
     }
     valid = m;
     for (int j = m; j < L; ++j) {
-      if (!build(j, it.idx[j])) {
-        if (lead) acc.singular += subtree_size(N, K, it.idx[L - 1], L);
+      if (!build(j, pre(j))) {
+        if (lead) acc.singular += subtree_size(N, K, last, L);
         return;
       }
       valid = j + 1;
     }
-    int cur[KMAX + 1];
+    Idx15 cur;  // cur[j]: the last index tried at level j
     int j = L;
-    cur[j] = it.idx[L - 1];
+    cur.set(j, last);
     for (;;) {
       if (j == B) {
         bottom(acc);
         if (--j < L) break;
         continue;
       }
-      const int c = ++cur[j];
+      const int c = cur.get(j) + 1;
+      cur.set(j, c);
       if (c > N - 1 - (K - j)) {
         if (--j < L) break;
         continue;
@@ -841,7 +909,7 @@ struct Walker {
         continue;
       }
       ++j;
-      cur[j] = c;
+      cur.set(j, c);
     }
   }
 
@@ -851,7 +919,7 @@ struct Walker {
     start(sub[0]);
     for (int j = 1; j < K - 1; ++j)
       if (!build(j, sub[j])) { absdet = 0; return ST_SINGULAR; }
-    if (K >= 2) s[K - 1] = sub[K - 1];
+    if (K >= 2) s.set(K - 1, sub[K - 1]);
     const uint64_t cand = build_last(K >= 2 ? sub[K - 1] : 0);
     if (!((cand >> sub[K]) & 1ull)) { absdet = 0; return ST_SINGULAR; }
     return leaf2(sub[K], member_mask(K), absdet);

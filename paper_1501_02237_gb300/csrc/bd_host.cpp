@@ -725,12 +725,13 @@ void lockstep_run(const int64_t* P, int N, int K, const std::vector<Item>& items
   std::vector<TC> sc((size_t)N * stack_entries(K));
   std::vector<TL> sl((size_t)N * K);
   std::vector<float> fl((size_t)4 * N);
+  std::vector<Uniform<TC>> uni(1);  // one copy for the team, as in a warp's shared memory
   std::vector<Acc> part(width);
   std::vector<std::thread> th;
   for (int l = 0; l < width; ++l)
     th.emplace_back([&, l] {
       LockstepTeam tm{&sh, l};
-      Walker<TC, TL, LockstepTeam> W(tm, P, N, K, N, sc.data(), sl.data(), fl.data());
+      Walker<TC, TL, LockstepTeam> W(tm, P, N, K, N, sc.data(), sl.data(), fl.data(), uni.data());
       Acc a{};
       if (ranges) {
         for (const Range& r : *ranges)
@@ -761,7 +762,8 @@ void host_run(const int64_t* P, int N, int K, const std::vector<Item>& items, co
     std::vector<TC> sc((size_t)N * stack_entries(K));
     std::vector<TL> sl((size_t)N * K);
     std::vector<float> fl((size_t)4 * N);
-    Walker<TC, TL, HostTeam> W(tm, P, N, K, N, sc.data(), sl.data(), fl.data());
+    std::vector<Uniform<TC>> uni(1);
+    Walker<TC, TL, HostTeam> W(tm, P, N, K, N, sc.data(), sl.data(), fl.data(), uni.data());
     Acc a{};
     for (;;) {
       const size_t u = next.fetch_add(1);

@@ -65,12 +65,18 @@ __host__ __device__ inline int slots_of(int N) { return (N + 3) & ~3; }
 #endif
 #define BD_ENUM_BOUNDS __launch_bounds__(256, BD_LB_BLOCKS)
 
-// one warp's shared memory: its coordinate-minor stack, lift-minor stack and four float rows
-// for the single-precision filters, each 16-byte aligned
+// one warp's shared memory: its coordinate-minor stack, lift-minor stack, four float rows for
+// the single-precision filters and the walker's team-shared pivots and dividers, each 16-byte
+// aligned
 template <class TC, class TL>
 __host__ __device__ inline size_t warp_bytes(int slots, int K) {
   return align16((size_t)slots * stack_entries(K) * sizeof(TC)) + align16((size_t)slots * K * sizeof(TL)) +
-         align16((size_t)4 * slots * sizeof(float));
+         align16((size_t)4 * slots * sizeof(float)) + kUniformBytes;
+}
+
+// the uniform-state area of a warp region laid out as in warp_bytes, given its float rows
+__device__ inline void* uniform_after(float* fl, int slots) {
+  return reinterpret_cast<unsigned char*>(fl) + align16((size_t)4 * slots * sizeof(float));
 }
 
 template <class TC, class TL>
@@ -78,6 +84,7 @@ struct WarpMem {
   TC* sc;
   TL* sl;
   float* fl;
+  void* uni;
   __device__ WarpMem(unsigned char* smem, int N, int K, int slots, int warp) {
     unsigned char* b = smem + align16((size_t)(K + 1) * N * sizeof(int64_t)) + (size_t)warp * warp_bytes<TC, TL>(slots, K);
     sc = reinterpret_cast<TC*>(b);
@@ -85,6 +92,7 @@ struct WarpMem {
     sl = reinterpret_cast<TL*>(b);
     b += align16((size_t)slots * K * sizeof(TL));
     fl = reinterpret_cast<float*>(b);
+    uni = uniform_after(fl, slots);
   }
 };
 
@@ -135,7 +143,7 @@ __global__ void BD_ENUM_BOUNDS k_enumerate(EnumParams p) {
   load_points(P, p);
 
   WarpTeam tm;
-  Walker<TC, TL, WarpTeam> W(tm, P, N, K, slots, m.sc, m.sl, m.fl);
+  Walker<TC, TL, WarpTeam> W(tm, P, N, K, slots, m.sc, m.sl, m.fl, m.uni);
   Acc acc{};
   unsigned long long done = 0;
   const unsigned int units = p.ranges ? (unsigned int)p.nranges : (unsigned int)p.nitems;
@@ -172,7 +180,7 @@ __global__ void k_classify(const int64_t* pts, const int64_t* lifts, int N, int 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, warps = blockDim.x >> 5;
   WarpMem<TC, TL> m(smem, N, K, slots, warp);
   WarpTeam tm;
-  Walker<TC, TL, WarpTeam> W(tm, P, N, K, slots, m.sc, m.sl, m.fl);
+  Walker<TC, TL, WarpTeam> W(tm, P, N, K, slots, m.sc, m.sl, m.fl, m.uni);
   for (int i = blockIdx.x * warps + warp; i < count; i += gridDim.x * warps) {
     TL ad = 0;
     const int s = W.classify(subsets + (size_t)i * (K + 1), ad);
@@ -324,7 +332,7 @@ __global__ void BD_ENUM_BOUNDS k_batch(BatchParams p) {
     Item it{};
     it.len = bi.len;
     for (int t = 0; t < bi.len; ++t) it.idx[t] = bi.idx[t];
-    Walker<TC, TL, WarpTeam> W(tm, P, N, K, slots, sc, sl, fl);
+    Walker<TC, TL, WarpTeam> W(tm, P, N, K, slots, sc, sl, fl, uniform_after(fl, slots));
     const long long t0 = clock64();
     W.run_item(it, acc);
     cyc += (unsigned long long)(clock64() - t0);
@@ -406,7 +414,7 @@ __device__ void serve_item(WarpTeam& tm, const int64_t* P, int N, int K, int slo
   TC* sc = reinterpret_cast<TC*>(stack);
   TL* sl = reinterpret_cast<TL*>(stack + align16((size_t)slots * stack_entries(maxK) * sizeof(int64_t)));
   float* fl = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(sl) + align16((size_t)slots * maxK * sizeof(int64_t)));
-  Walker<TC, TL, WarpTeam> W(tm, P, N, K, slots, sc, sl, fl);
+  Walker<TC, TL, WarpTeam> W(tm, P, N, K, slots, sc, sl, fl, uniform_after(fl, slots));
   W.run_item(it, acc);
 }
 
