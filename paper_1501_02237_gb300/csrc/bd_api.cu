@@ -109,6 +109,28 @@ int get_items(int N, int K, int64_t thr, int64_t teams, std::shared_ptr<ItemList
   return BD_OK;
 }
 
+// the colex triple decode table, uploaded once per device
+std::map<int, uint32_t*> g_tri;
+
+int get_tri(const uint32_t*& out) {
+  const int dev = current_device();
+  std::lock_guard<std::mutex> lk(g_cache_mu);
+  auto it = g_tri.find(dev);
+  if (it != g_tri.end()) {
+    out = it->second;
+    return BD_OK;
+  }
+  std::vector<uint32_t> h(bd::kTriEntries);
+  bd::fill_colex_table(h.data());
+  uint32_t* d = nullptr;
+  cudaError_t e = cudaMalloc(&d, sizeof(uint32_t) * h.size());
+  if (e == cudaSuccess) e = cudaMemcpy(d, h.data(), sizeof(uint32_t) * h.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "decode table upload");
+  g_tri[dev] = d;
+  out = d;
+  return BD_OK;
+}
+
 int get_shape(int N, int K, int path, int warps_req, int bps_req, bd::LaunchShape& out) {
   const auto key = std::make_tuple(N, K, path, warps_req, bps_req, current_device());
   std::lock_guard<std::mutex> lk(g_cache_mu);
@@ -152,6 +174,7 @@ struct bd_plan {
   bool launched = false;
   int attempt = 0;
   int shard = 0, shards = 1;  // of the last launch
+  const uint32_t* tri = nullptr;  // the device's colex decode table
   uint64_t items_expected = 0;
 };
 
@@ -241,6 +264,8 @@ int plan_prepare(bd_plan* p, const int64_t* points, const int64_t* lifts, int32_
   }
   rc = get_items(npts, k, thr, (int64_t)warps, p->items);
   if (rc) return rc;
+  rc = get_tri(p->tri);
+  if (rc) return rc;
   std::memcpy(p->h_stage, points, sizeof(int64_t) * npts * k);
   cudaError_t e = cudaMemcpyAsync(p->d_pts, p->h_stage, sizeof(int64_t) * npts * k, cudaMemcpyHostToDevice, st);
   p->explicit_lifts = lifts != nullptr;
@@ -297,6 +322,7 @@ int plan_launch(bd_plan* p, uint64_t seed, int attempt, cudaStream_t st, int sha
   ep.nranges = (int)p->items->ranges.size();
   ep.shard = shard;
   ep.shards = shards;
+  ep.tri = p->tri;
   uint64_t expected = 0;
   for (size_t u = (size_t)shard; u < p->items->ranges.size(); u += (size_t)shards) expected += p->items->ranges[u].count;
   ep.N = p->N;

@@ -191,6 +191,27 @@ BD_HD i128 bareiss(i128 a, i128 p, i128 b, i128 r, const Div128& D) {
   return (i128)(q * D.inv);
 }
 
+// read-only load through the non-coherent cache on the device
+BD_HD uint32_t ldg_u32(const uint32_t* p) {
+#ifdef __CUDA_ARCH__
+  return __ldg(p);
+#else
+  return *p;
+#endif
+}
+
+// Number of triples i < j < k < 63: the colex decode table covers every node (R <= 63).
+constexpr int kTriEntries = 63 * 62 * 61 / 6;
+
+// entry t of the colex order of triples i < j < k (by k, then j, then i), packed
+// i | j << 8 | k << 16 (host side: the table the device reads)
+inline void fill_colex_table(uint32_t* out) {
+  int t = 0;
+  for (int k = 2; k < 63; ++k)
+    for (int j = 1; j < k; ++j)
+      for (int i = 0; i < j; ++i) out[t++] = (uint32_t)i | ((uint32_t)j << 8) | ((uint32_t)k << 16);
+}
+
 // square root of v >= 1 to a few ulps (the callers correct the integer part they take from it)
 BD_HD float approx_sqrt(float v) {
 #ifdef __CUDA_ARCH__
@@ -352,6 +373,119 @@ struct Uniform {
 };
 constexpr size_t kUniformBytes = 1024;  // room for Uniform<TC> of every coordinate type
 
+// ---------------------------------------------------------------------------------------------
+// Cells of the triangulation and their inner normals (Sec. 6, Eq. lower-d-face-again): the
+// witness-set construction needs, for every cell {a_0 .. a_k}, the unique alpha^ = (alpha, 1)
+// with <a^_j, alpha^> = beta on the cell (and > beta off it, which the lower-facet test has
+// established).
+// ---------------------------------------------------------------------------------------------
+
+// A cell sink: accepted cells are appended as 16-byte records (the K+1 increasing indices,
+// then zeros); records past cap are counted but not written.
+struct CellSink {
+  uint8_t* out;
+  unsigned long long* count;
+  unsigned long long cap;
+};
+
+static BD_COLD void record_cell(CellSink sink, Idx15 s, int pre, int a, int b, int c) {
+#ifdef __CUDA_ARCH__
+  const unsigned long long slot = atomicAdd(sink.count, 1ull);
+#else
+  const unsigned long long slot = __atomic_fetch_add(sink.count, 1ull, __ATOMIC_RELAXED);
+#endif
+  if (slot >= sink.cap) return;
+  uint8_t rec[16] = {};
+  int n = 0;
+  for (int i = 0; i < pre; ++i) rec[n++] = (uint8_t)s.get(i);
+  if (a >= 0) rec[n++] = (uint8_t)a;
+  if (b >= 0) rec[n++] = (uint8_t)b;
+  if (c >= 0) rec[n++] = (uint8_t)c;
+  memcpy(sink.out + 16 * slot, rec, 16);
+}
+
+// 256-bit accumulator for the exact back substitution
+struct Acc256 {
+  u128 hi = 0, lo = 0;
+  BD_HD void add(i128 a, i128 b, bool negate) {  // += (or -=) a * b, modulo 2^256
+    u128 h, l;
+    mul_wide(a, b, h, l);
+    if (negate) {  // two's complement of (h, l)
+      l = ~l + 1;
+      h = ~h + (l == 0 ? 1 : 0);
+    }
+    const u128 nl = lo + l;
+    hi += h + (nl < lo ? 1 : 0);
+    lo = nl;
+  }
+  BD_HD i128 div_exact(const Div128& D) const {  // quotient known to fit 128 bits
+    const int t = D.shift;
+    const u128 q = t == 0 ? lo : ((lo >> t) | (hi << (128 - t)));
+    return (i128)(q * D.inv);
+  }
+};
+
+// The inner normal of the cell with indices idx[0..K] over points pts (row-major N x K) lifted
+// by lifts: alpha = y / den, beta = beta_num / den with den > 0.  It solves
+// (a_j - a_0) . alpha = w_0 - w_j (j = 1..K) by fraction-free elimination (every entry a minor
+// of the lifted system) and fraction-free back substitution (y_i = den alpha_i, Cramer), then
+// beta = a_0 . alpha + w_0.  false when the cell is flat or a value leaves the output range
+// (den and y in int64, beta_num in int128).
+BD_HD bool cell_normal_exact(const int64_t* pts, const int64_t* lifts, int K, const uint8_t* idx, int64_t& den,
+                             int64_t* y_out, i128& beta_num) {
+  i128 A[KMAX][KMAX + 1];
+  const int i0 = idx[0];
+  for (int r = 0; r < K; ++r) {
+    const int q = idx[r + 1];
+    for (int c = 0; c < K; ++c) A[r][c] = (i128)pts[(size_t)q * K + c] - pts[(size_t)i0 * K + c];
+    A[r][K] = (i128)lifts[i0] - lifts[q];
+  }
+  Div128 D = make_div((i128)1);
+  for (int c = 0; c < K; ++c) {
+    int p = -1;
+    for (int r = c; r < K; ++r)
+      if (A[r][c] != 0) { p = r; break; }
+    if (p < 0) return false;
+    if (p != c)
+      for (int j = 0; j <= K; ++j) {
+        const i128 t = A[c][j];
+        A[c][j] = A[p][j];
+        A[p][j] = t;
+      }
+    for (int r = c + 1; r < K; ++r) {
+      for (int j = c + 1; j <= K; ++j) A[r][j] = bareiss(A[r][j], A[c][c], A[r][c], A[c][j], D);
+      A[r][c] = 0;
+    }
+    D = make_div(A[c][c]);
+  }
+  const i128 dd = A[K - 1][K - 1];
+  i128 y[KMAX];
+  for (int i = K - 1; i >= 0; --i) {
+    Acc256 num;
+    num.add(dd, A[i][K], false);
+    for (int j = i + 1; j < K; ++j) num.add(A[i][j], y[j], true);
+    y[i] = i == K - 1 ? A[i][K] : num.div_exact(make_div(A[i][i]));
+  }
+  const bool flip = dd < 0;
+  const i128 lim = (i128)1 << 63;
+  const i128 dpos = flip ? -dd : dd;
+  if (dpos >= lim) return false;
+  den = (int64_t)dpos;
+  Acc256 b;
+  b.add((i128)lifts[i0], dd, false);
+  for (int i = 0; i < K; ++i) {
+    const i128 yi = flip ? -y[i] : y[i];
+    if (yi >= lim || yi < -lim) return false;
+    y_out[i] = (int64_t)yi;
+    b.add((i128)pts[(size_t)i0 * K + i], y[i], false);
+  }
+  // beta_num = (a_0 . y + w_0 dd), sign-normalised; it must fit int128
+  const bool hi_ok = (b.hi == 0 && (b.lo >> 127) == 0) || (b.hi == ~(u128)0 && (b.lo >> 127) == 1);
+  if (!hi_ok) return false;
+  beta_num = flip ? -(i128)b.lo : (i128)b.lo;
+  return true;
+}
+
 static_assert(sizeof(Uniform<i128>) <= kUniformBytes, "uniform state area too small");
 static_assert(sizeof(Item) == 16, "an item is four words");
 
@@ -457,6 +591,8 @@ struct Walker {
   TL* sl;           // lift minor of level j for point q at sl[j * SLOTS + q]
   float* fl;        // single-precision copies for the filters: 4 rows of SLOTS floats
   Uniform<TC>* u;   // pivots and dividers (team-shared)
+  const uint32_t* tri = nullptr;  // optional colex decode table (device memory; see bottom4)
+  CellSink sink{nullptr, nullptr, 0};  // optional: where accepted cells are recorded
   Idx15 s;          // chosen indices s_0 .. s_j
   int psign;        // sign of the level K-1 pivot p_{K-1} (2-D test)
   int valid = 0;    // states 0 .. valid-1 are those of s_0 .. s_{valid-1} (kept across items)
@@ -519,7 +655,10 @@ struct Walker {
     tm.sync();  // readers of the old state j (a sibling's subtree) are done
     // state K-3 is the 4-D stage's input: its single-precision copies are written here too
     const bool conv = kFiltered && j == K - 3;
-    for (int q = tm.lane(); q < N; q += tm.lanes()) {
+    // whole points one per lane; when N exceeds the team width, the last N mod width points
+    // have their entries dealt across the lanes instead (one lane would carry them alone)
+    const int W = tm.lanes(), whole = N > W ? N - N % W : N;
+    for (int q = tm.lane(); q < whole; q += W) {
       const TC bq = sc[(po + pi) * SLOTS + q];
       for (int e = 0; e < ncoord - 1; ++e) {
         const int ep = e < pi ? e : e + 1;
@@ -530,6 +669,20 @@ struct Walker {
       const TL l = bareiss(sl[(j - 1) * SLOTS + q], pj, bq, rl, D);
       sl[j * SLOTS + q] = l;
       if (conv) fl[3 * SLOTS + q] = f32_of(l);
+    }
+    for (int t = tm.lane(); t < (N - whole) * ncoord; t += W) {
+      const int q = whole + t / ncoord, e = t % ncoord;  // entry e < ncoord-1: coordinate; last: lift
+      const TC bq = sc[(po + pi) * SLOTS + q];
+      if (e < ncoord - 1) {
+        const int ep = e < pi ? e : e + 1;
+        const TC v = bareiss(sc[(po + ep) * SLOTS + q], pj, bq, sc[(po + ep) * SLOTS + c], D);
+        sc[(no + e) * SLOTS + q] = v;
+        if (conv) fl[e * SLOTS + q] = f32_of(v);
+      } else {
+        const TL l = bareiss(sl[(j - 1) * SLOTS + q], pj, bq, rl, D);
+        sl[j * SLOTS + q] = l;
+        if (conv) fl[3 * SLOTS + q] = f32_of(l);
+      }
     }
     s.set(j, c);
     if (tm.lane() == 0) {
@@ -621,7 +774,11 @@ struct Walker {
       TL ad;
       const int stt = leaf2(p, mask, ad);
       if (tm.lane() != 0) continue;  // uniform verdict: counted once per team
-      if (stt == ST_ACCEPTED) { acc.cells += 1; acc.nvol += (u128)ad; }
+      if (stt == ST_ACCEPTED) {
+        acc.cells += 1;
+        acc.nvol += (u128)ad;
+        if (sink.out) record_cell(sink, s, K, p, -1, -1);
+      }
       else if (stt == ST_TIE) acc.ties += 1;
     }
   }
@@ -728,6 +885,7 @@ struct Walker {
           const W2 ad = d2 < 0 ? -d2 : d2;
           const W2 dd = dp < 0 ? -(W2)dp : (W2)dp;
           acc.nvol += (u128)(ad / dd);  // exact: det2 = p_{K-2} * C_p
+          if (sink.out) record_cell(sink, s, K - 1, c, p, -1);
         }
       }
       p += tm.lanes();
@@ -769,11 +927,23 @@ struct Walker {
     const int base = s.get(K - 3) + 1, R = N - base;
     const int total = R * (R - 1) * (R - 2) / 6;
     int k = 2;
+    // with a decode table (colex triples packed i | j << 8 | k << 16), the next round's entry
+    // is loaded while this round runs
+    uint32_t nxt = 0;
+    if (tri && (int)tm.lane() < total) nxt = ldg_u32(tri + tm.lane());
     for (int t0 = 0; t0 < total; t0 += tm.lanes()) {
       const int t = t0 + tm.lane();
       bool live = t < total;
       int c1 = base, c = base, p = base;
-      if (live) {
+      if (tri) {
+        const uint32_t w = nxt;
+        if (t + (int)tm.lanes() < total) nxt = ldg_u32(tri + t + tm.lanes());
+        if (live) {
+          c1 = base + (int)(w & 255u);
+          c = base + (int)((w >> 8) & 255u);
+          p = base + (int)(w >> 16);
+        }
+      } else if (live) {
         while ((k + 1) * k * (k - 1) / 6 <= t) ++k;
         const int u = t - k * (k - 1) * (k - 2) / 6;
         int jj = (int)((1.0f + approx_sqrt(8.0f * (float)u + 1.0f)) * 0.5f);
@@ -847,6 +1017,7 @@ struct Walker {
           acc.cells += 1;
           const W2 m = exact_minor(view(), c1, c, p);
           acc.nvol += (u128)(m < 0 ? -m : m);
+          if (sink.out) record_cell(sink, s, K - 2, c1, c, p);
         }
       }
     }

@@ -676,6 +676,16 @@ struct HostTeam {
 };
 }  // namespace
 
+// the colex decode table the enumeration kernel reads, for the host emulation
+const uint32_t* colex_table() {
+  static const std::vector<uint32_t> t = [] {
+    std::vector<uint32_t> v(kTriEntries);
+    fill_colex_table(v.data());
+    return v;
+  }();
+  return t.data();
+}
+
 // A team of `width` lanes run as CPU threads in lockstep: every collective (vote, sync) is a
 // barrier, as a warp-synchronous program requires of its lanes.  Tests use it to run the
 // multi-lane logic of the walker (lane dealing, ragged tails, votes) without a GPU.
@@ -732,6 +742,7 @@ void lockstep_run(const int64_t* P, int N, int K, const std::vector<Item>& items
     th.emplace_back([&, l] {
       LockstepTeam tm{&sh, l};
       Walker<TC, TL, LockstepTeam> W(tm, P, N, K, N, sc.data(), sl.data(), fl.data(), uni.data());
+      W.tri = colex_table();
       Acc a{};
       if (ranges) {
         for (const Range& r : *ranges)
@@ -764,6 +775,7 @@ void host_run(const int64_t* P, int N, int K, const std::vector<Item>& items, co
     std::vector<float> fl((size_t)4 * N);
     std::vector<Uniform<TC>> uni(1);
     Walker<TC, TL, HostTeam> W(tm, P, N, K, N, sc.data(), sl.data(), fl.data(), uni.data());
+    W.tri = colex_table();
     Acc a{};
     for (;;) {
       const size_t u = next.fetch_add(1);

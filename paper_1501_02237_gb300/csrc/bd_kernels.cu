@@ -144,6 +144,8 @@ __global__ void BD_ENUM_BOUNDS k_enumerate(EnumParams p) {
 
   WarpTeam tm;
   Walker<TC, TL, WarpTeam> W(tm, P, N, K, slots, m.sc, m.sl, m.fl, m.uni);
+  W.tri = p.tri;
+  W.sink = p.sink;
   Acc acc{};
   unsigned long long done = 0;
   const unsigned int units = p.ranges ? (unsigned int)p.nranges : (unsigned int)p.nitems;
@@ -521,6 +523,41 @@ LaunchShape serve_shape(int maxN, int maxK, int warps_req, int blocks_per_sm_req
 
 cudaError_t launch_serve(const ServeParams& p, const LaunchShape& s, cudaStream_t st) {
   k_serve<<<s.blocks, s.warps * 32, s.smem, st>>>(p);
+  return cudaGetLastError();
+}
+
+// ---- cell normals ----------------------------------------------------------------------------
+
+namespace {
+
+__global__ void k_cell_normals(const int64_t* pts, const int64_t* lifts, uint64_t lift_seed, int N, int K,
+                               const uint8_t* cells, unsigned long long count, int64_t* den, int64_t* alpha,
+                               int64_t* beta, int32_t* status) {
+  const unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  int64_t lf[NMAX];
+  for (int q = 0; q < N; ++q) lf[q] = lifts ? lifts[q] : lift_height(lift_seed, q);
+  uint8_t idx[16];
+  for (int t = 0; t < 16; ++t) idx[t] = cells[16 * i + t];
+  int64_t d = 0;
+  i128 b = 0;
+  const bool ok = cell_normal_exact(pts, lf, K, idx, d, alpha + i * K, b);
+  den[i] = ok ? d : 0;
+  beta[2 * i] = (int64_t)(uint64_t)(u128)b;
+  beta[2 * i + 1] = (int64_t)(b >> 64);
+  status[i] = ok ? 0 : 1;
+}
+
+}  // namespace
+
+cudaError_t launch_cell_normals(const int64_t* pts, const int64_t* lifts, uint64_t lift_seed, int N, int K,
+                                const uint8_t* cells, unsigned long long count, int64_t* den, int64_t* alpha,
+                                int64_t* beta, int32_t* status, cudaStream_t st) {
+  if (count == 0) return cudaSuccess;
+  const unsigned int threads = 64;
+  const unsigned long long blocks = (count + threads - 1) / threads;
+  k_cell_normals<<<(unsigned int)blocks, threads, 0, st>>>(pts, lifts, lift_seed, N, K, cells, count, den, alpha,
+                                                           beta, status);
   return cudaGetLastError();
 }
 

@@ -26,6 +26,8 @@ struct EnumParams {
   int shard, shards;      // this launch takes the units u with u % shards == shard (shards >= 1)
   int N, K;
   unsigned int* counter;  // next work unit (reset to 0 before the launch)
+  const uint32_t* tri;    // colex decode table of kTriEntries words (device), or nullptr
+  CellSink sink;          // accepted cells are recorded here when sink.out is non-null
   DevAcc* acc;            // reset to 0 before the launch
 };
 
@@ -104,5 +106,12 @@ struct ServeParams {
 size_t serve_smem_bytes(int maxN, int maxK, int warps);
 LaunchShape serve_shape(int maxN, int maxK, int warps_req, int blocks_per_sm_req, int sms, cudaError_t* err);
 cudaError_t launch_serve(const ServeParams& p, const LaunchShape& s, cudaStream_t st);
+
+// The inner normals of `count` recorded cells (16-byte records), one thread per cell:
+// den[i] > 0, alpha[i*K + c], beta[2i] (low 64 bits) and beta[2i+1] (high); status[i] = 0 or
+// 1 (flat cell or a value out of range).  Lifts: explicit (lifts) or from lift_seed.
+cudaError_t launch_cell_normals(const int64_t* pts, const int64_t* lifts, uint64_t lift_seed, int N, int K,
+                                const uint8_t* cells, unsigned long long count, int64_t* den, int64_t* alpha,
+                                int64_t* beta, int32_t* status, cudaStream_t st);
 
 }  // namespace bd
