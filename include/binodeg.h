@@ -333,6 +333,29 @@ typedef struct bd_host_opts {
 int bd_host_volume_lifted(const int64_t* points, const int64_t* lifts, int32_t npts, int32_t k,
                           const bd_host_opts* opts, bd_volume_out* out);
 
+/* ---- cells of the triangulation and their inner normals (Sec. 6, witness-set start systems) */
+
+/* The cells of the regular triangulation of conv(points) that the volume's lifting induces
+ * (bd_volume's lifting for this seed, re-lifted on ties), in lexicographic order, each with its
+ * inner normal (Eq. lower-d-face-again): alpha^ = (alpha, 1) with <a_j, alpha> + omega_j = beta
+ * on the cell's points and > beta on every other point; (alpha, beta) give the change of
+ * variables t_i = y_i s^alpha_i and the factor s^-beta of the cell's homotopy.
+ *   cells : capacity x (k+1) point indices, increasing within a cell
+ *   den   : capacity positive denominators: alpha = alpha_num / den, beta = beta_num / den
+ *   alpha : capacity x k numerators
+ *   beta  : capacity x 2 words, the 128-bit numerator: low 64 bits, then high 64 bits
+ *   count : the number of cells; when it exceeds capacity nothing is written and the call
+ *           returns BD_ERR_ARG (capacity 0 just counts)
+ *   out   : the volume result (the sum of the cells' normalized volumes)
+ * Errors: BD_ERR_ARG, BD_ERR_OVERFLOW (a normal outside the output range), BD_ERR_TIES,
+ * BD_ERR_CUDA, BD_ERR_NOMEM. */
+int bd_cells(const int64_t* points, int32_t npts, int32_t k, uint64_t seed, int64_t capacity, uint8_t* cells,
+             int64_t* den, int64_t* alpha, int64_t* beta, int64_t* count, bd_volume_out* out);
+/* The same with the given lifts on one host core (CPU tests); BD_ERR_TIES when the lifting has
+ * a tie. */
+int bd_host_cells(const int64_t* points, const int64_t* lifts, int32_t npts, int32_t k, int64_t capacity,
+                  uint8_t* cells, int64_t* den, int64_t* alpha, int64_t* beta, int64_t* count);
+
 #ifdef __cplusplus
 }
 #endif

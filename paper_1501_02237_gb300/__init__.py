@@ -18,7 +18,7 @@ from ._lib import (BD_FEATURES, BD_MLP_PARAMS, BD_FLAG_DEGENERATE, BD_FLAG_INCON
 from ._lib import F32P, I32P, U8P
 
 __all__ = ["CostModel", "Server", "degree", "volume", "volume_noalloc", "volume_lifted", "classify", "reduce", "Plan", "Batch", "set_stream",
-           "host_volume_lifted", "BinodegError", "lib"]
+           "host_volume_lifted", "cells", "host_cells", "BinodegError", "lib"]
 
 
 def set_stream(stream) -> None:
@@ -44,6 +44,54 @@ def degree(A, coef=None, seed: int = 0) -> dict:
     check(lib().bd_degree(ptr(A), n, m, ptr(c) if c is not None else None, C.c_uint64(seed), C.byref(out)))
     return out.as_dict()
 
+
+
+def _cells_result(n, k, cells, den, alpha, beta):
+    from fractions import Fraction
+    out = []
+    for r in range(n):
+        b = (int(beta[2 * r + 1]) << 64) | (int(beta[2 * r]) & ((1 << 64) - 1))
+        d = int(den[r])
+        out.append(dict(cell=tuple(int(x) for x in cells[r * (k + 1):(r + 1) * (k + 1)]),
+                        alpha=[Fraction(int(a), d) for a in alpha[r * k:(r + 1) * k]], beta=Fraction(b, d)))
+    return out
+
+
+def _cells_call(fn, k, capacity):
+    """Call fn(capacity, cells, den, alpha, beta, count) twice if the first capacity is too small."""
+    for _ in range(2):
+        cap = max(1, capacity)
+        cells = np.zeros(cap * (k + 1), dtype=np.uint8)
+        den = np.zeros(cap, dtype=np.int64)
+        alpha = np.zeros(cap * k, dtype=np.int64)
+        beta = np.zeros(2 * cap, dtype=np.int64)
+        count = C.c_int64(0)
+        rc = fn(capacity, cells.ctypes.data_as(U8P), ptr(den), ptr(alpha), ptr(beta), C.byref(count))
+        if rc == 1 and count.value > capacity:  # BD_ERR_ARG with the true count: retry once
+            capacity = int(count.value)
+            continue
+        check(rc)
+        return _cells_result(int(count.value), k, cells, den, alpha, beta)
+    check(rc)
+
+
+def cells(points, seed: int = 0, capacity: int = 4096):
+    """bd_cells: the cells of the lifting's triangulation with their exact inner normals
+    (alpha, beta as Fractions) and the volume result: (cells, volume dict)."""
+    P = i64(points)
+    npts, k = P.shape
+    out = VolumeOut()
+    res = _cells_call(lambda cap, c, d, a, b, n: lib().bd_cells(ptr(P), npts, k, C.c_uint64(seed), cap, c, d, a, b, n,
+                                                             C.byref(out)), k, capacity)
+    return res, out.as_dict()
+
+
+def host_cells(points, lifts, capacity: int = 4096):
+    """bd_host_cells: the same with the given lifts on the host (CPU tests)."""
+    P, W = i64(points), i64(lifts)
+    npts, k = P.shape
+    return _cells_call(lambda cap, c, d, a, b, n: lib().bd_host_cells(ptr(P), ptr(W), npts, k, cap, c, d, a, b, n),
+                       k, capacity)
 
 def reduce(A, coef=None) -> dict:
     """bd_reduce: host front end only -> kernel points (n+1 x d, origin last), rank, torsion."""

@@ -310,7 +310,8 @@ bd_plan* thread_plan() {
   return h.p;
 }
 
-int plan_launch(bd_plan* p, uint64_t seed, int attempt, cudaStream_t st, int shard = 0, int shards = 1) {
+int plan_launch(bd_plan* p, uint64_t seed, int attempt, cudaStream_t st, int shard = 0, int shards = 1,
+                const bd::CellSink* sink = nullptr) {
   BD_CUDA(cudaMemsetAsync(p->d_state, 0, state_bytes(), st));
   bd::EnumParams ep{};
   ep.pts = p->d_pts;
@@ -323,6 +324,7 @@ int plan_launch(bd_plan* p, uint64_t seed, int attempt, cudaStream_t st, int sha
   ep.shard = shard;
   ep.shards = shards;
   ep.tri = p->tri;
+  if (sink) ep.sink = *sink;
   uint64_t expected = 0;
   for (size_t u = (size_t)shard; u < p->items->ranges.size(); u += (size_t)shards) expected += p->items->ranges[u].count;
   ep.N = p->N;
@@ -642,6 +644,154 @@ int bd_host_volume_lifted(const int64_t* points, const int64_t* lifts, int32_t n
   out->max_abs_coord = (int32_t)std::min<int64_t>(mx, INT32_MAX);
   out->bound_bits = (int32_t)std::ceil(bound);
   if (acc.ties) return fail(BD_ERR_TIES, "the given lifting has ties");
+  return BD_OK;
+}
+
+int bd_cells(const int64_t* points, int32_t npts, int32_t k, uint64_t seed, int64_t capacity, uint8_t* cells,
+             int64_t* den, int64_t* alpha, int64_t* beta, int64_t* count, bd_volume_out* out) {
+  if (!out || !count) return fail(BD_ERR_ARG, "NULL argument");
+  if (capacity < 0 || (capacity > 0 && (!cells || !den || !alpha || !beta))) return fail(BD_ERR_ARG, "NULL output array");
+  *count = 0;
+  int rc = check_points(points, npts, k);
+  if (rc) return rc;
+  if (npts < k + 1) {
+    degenerate_volume(npts, k, points, out);
+    return BD_OK;
+  }
+  bd_plan* p = thread_plan();
+  if (!p) return fail(BD_ERR_NOMEM, "plan");
+  cudaStream_t st = g_stream;
+  rc = plan_prepare(p, points, nullptr, npts, k, nullptr, st);
+  if (rc) return rc;
+  const size_t cap = (size_t)std::max<int64_t>(capacity, 1);
+  uint8_t* d_cells = nullptr;
+  unsigned long long* d_count = nullptr;
+  int64_t *d_den = nullptr, *d_alpha = nullptr, *d_beta = nullptr;
+  int32_t* d_status = nullptr;
+  auto release = [&]() {
+    cudaFree(d_cells);
+    cudaFree(d_count);
+    cudaFree(d_den);
+    cudaFree(d_alpha);
+    cudaFree(d_beta);
+    cudaFree(d_status);
+  };
+#define CC(x)                                              \
+  do {                                                     \
+    cudaError_t e_ = (x);                                  \
+    if (e_ != cudaSuccess) {                               \
+      release();                                           \
+      return cuda_fail(e_, #x);                            \
+    }                                                      \
+  } while (0)
+  CC(cudaMalloc(&d_cells, 16 * cap));
+  CC(cudaMalloc(&d_count, sizeof(unsigned long long)));
+  CC(cudaMalloc(&d_den, sizeof(int64_t) * cap));
+  CC(cudaMalloc(&d_alpha, sizeof(int64_t) * cap * k));
+  CC(cudaMalloc(&d_beta, sizeof(int64_t) * 2 * cap));
+  CC(cudaMalloc(&d_status, sizeof(int32_t) * cap));
+  const bd::CellSink sink{d_cells, d_count, (unsigned long long)capacity};
+  int attempt = 0;
+  for (;; ++attempt) {
+    if (attempt == MAX_LIFTINGS) {
+      release();
+      return fail(BD_ERR_TIES, "every allowed lifting had ties");
+    }
+    CC(cudaMemsetAsync(d_count, 0, sizeof(unsigned long long), st));
+    rc = plan_launch(p, seed, attempt, st, 0, 1, &sink);
+    if (!rc) rc = plan_read(p, out);
+    if (rc) {
+      release();
+      return rc;
+    }
+    if (out->ties == 0) break;
+  }
+  out->relifts = attempt;
+  unsigned long long n = 0;
+  CC(cudaMemcpy(&n, d_count, sizeof(n), cudaMemcpyDeviceToHost));
+  *count = (int64_t)n;
+  if (n > (unsigned long long)capacity) {
+    release();
+    return fail(BD_ERR_ARG, "capacity is below the number of cells (count holds it)");
+  }
+  CC(bd::launch_cell_normals(p->d_pts, nullptr, bd::lift_stream_seed(seed, (uint32_t)attempt), npts, k, d_cells, n,
+                             d_den, d_alpha, d_beta, d_status, st));
+  std::vector<uint8_t> hc(16 * std::max<size_t>(n, 1));
+  std::vector<int64_t> hd(std::max<size_t>(n, 1)), ha(std::max<size_t>(n, 1) * k), hb(2 * std::max<size_t>(n, 1));
+  std::vector<int32_t> hs(std::max<size_t>(n, 1));
+  CC(cudaStreamSynchronize(st));
+  if (n) {
+    CC(cudaMemcpy(hc.data(), d_cells, 16 * n, cudaMemcpyDeviceToHost));
+    CC(cudaMemcpy(hd.data(), d_den, sizeof(int64_t) * n, cudaMemcpyDeviceToHost));
+    CC(cudaMemcpy(ha.data(), d_alpha, sizeof(int64_t) * n * k, cudaMemcpyDeviceToHost));
+    CC(cudaMemcpy(hb.data(), d_beta, sizeof(int64_t) * 2 * n, cudaMemcpyDeviceToHost));
+    CC(cudaMemcpy(hs.data(), d_status, sizeof(int32_t) * n, cudaMemcpyDeviceToHost));
+  }
+#undef CC
+  release();
+  for (unsigned long long i = 0; i < n; ++i)
+    if (hs[i]) return fail(BD_ERR_OVERFLOW, "a cell normal leaves the int64/int128 output range");
+  // cells in lexicographic order of their index records (the device appends them in any order)
+  std::vector<size_t> ord(n);
+  for (size_t i = 0; i < n; ++i) ord[i] = i;
+  std::sort(ord.begin(), ord.end(), [&](size_t a, size_t b) { return std::memcmp(&hc[16 * a], &hc[16 * b], 16) < 0; });
+  for (size_t r = 0; r < n; ++r) {
+    const size_t i = ord[r];
+    std::memcpy(cells + r * (k + 1), &hc[16 * i], (size_t)k + 1);
+    den[r] = hd[i];
+    for (int c = 0; c < k; ++c) alpha[r * k + c] = ha[i * k + c];
+    beta[2 * r] = hb[2 * i];
+    beta[2 * r + 1] = hb[2 * i + 1];
+  }
+  return BD_OK;
+}
+
+int bd_host_cells(const int64_t* points, const int64_t* lifts, int32_t npts, int32_t k, int64_t capacity,
+                  uint8_t* cells, int64_t* den, int64_t* alpha, int64_t* beta, int64_t* count) {
+  if (!count || !lifts) return fail(BD_ERR_ARG, "NULL argument");
+  if (capacity < 0 || (capacity > 0 && (!cells || !den || !alpha || !beta))) return fail(BD_ERR_ARG, "NULL output array");
+  *count = 0;
+  int rc = check_points(points, npts, k);
+  if (rc) return rc;
+  if (npts < k + 1) return BD_OK;
+  int64_t lo = lifts[0], hi = lifts[0];
+  for (int i = 0; i < npts; ++i) {
+    lo = std::min(lo, lifts[i]);
+    hi = std::max(hi, lifts[i]);
+  }
+  double coord_bits = 0;
+  const double bound = bd::hadamard_log2(points, lifts, npts, k, hi - lo, &coord_bits);
+  const int path = bd::choose_path(coord_bits, bound);
+  if (path < 0) return fail(BD_ERR_OVERFLOW, "Hadamard bound exceeds 2^127");
+  std::vector<int64_t> P((size_t)(k + 1) * npts);
+  for (int q = 0; q < npts; ++q) {
+    for (int c = 0; c < k; ++c) P[(size_t)c * npts + q] = points[(size_t)q * k + c];
+    P[(size_t)k * npts + q] = lifts[q];
+  }
+  std::vector<bd::Item> items;
+  std::vector<bd::Range> ranges;
+  bd::build_ranges(npts, k, 4096, 8, items, ranges);
+  const size_t cap = (size_t)std::max<int64_t>(capacity, 1);
+  std::vector<uint8_t> rec(16 * cap);
+  unsigned long long n = 0;
+  const bd::CellSink sink{rec.data(), &n, (unsigned long long)capacity};
+  bd::Acc acc{};
+  bd::host_enumerate(path, P.data(), npts, k, items, 1, acc, 1, &ranges, &sink);
+  *count = (int64_t)n;
+  if (acc.ties) return fail(BD_ERR_TIES, "the given lifting has ties");
+  if (n > (unsigned long long)capacity) return fail(BD_ERR_ARG, "capacity is below the number of cells (count holds it)");
+  std::vector<size_t> ord(n);
+  for (size_t i = 0; i < n; ++i) ord[i] = i;
+  std::sort(ord.begin(), ord.end(), [&](size_t a, size_t b) { return std::memcmp(&rec[16 * a], &rec[16 * b], 16) < 0; });
+  for (size_t r = 0; r < n; ++r) {
+    const uint8_t* c = &rec[16 * ord[r]];
+    std::memcpy(cells + r * (k + 1), c, (size_t)k + 1);
+    i128 b = 0;
+    if (!bd::cell_normal_exact(points, lifts, k, c, den[r], alpha + r * k, b))
+      return fail(BD_ERR_OVERFLOW, "a cell normal leaves the int64/int128 output range");
+    beta[2 * r] = (int64_t)(uint64_t)(u128)b;
+    beta[2 * r + 1] = (int64_t)(b >> 64);
+  }
   return BD_OK;
 }
 

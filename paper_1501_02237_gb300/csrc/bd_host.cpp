@@ -730,7 +730,7 @@ struct LockstepTeam {
 
 template <class TC, class TL>
 void lockstep_run(const int64_t* P, int N, int K, const std::vector<Item>& items, const std::vector<Range>* ranges,
-                  int width, Acc& acc) {
+                  int width, Acc& acc, const CellSink* sink) {
   LockstepShared sh(width);
   std::vector<TC> sc((size_t)N * stack_entries(K));
   std::vector<TL> sl((size_t)N * K);
@@ -743,6 +743,7 @@ void lockstep_run(const int64_t* P, int N, int K, const std::vector<Item>& items
       LockstepTeam tm{&sh, l};
       Walker<TC, TL, LockstepTeam> W(tm, P, N, K, N, sc.data(), sl.data(), fl.data(), uni.data());
       W.tri = colex_table();
+      if (sink) W.sink = *sink;
       Acc a{};
       if (ranges) {
         for (const Range& r : *ranges)
@@ -764,7 +765,7 @@ void lockstep_run(const int64_t* P, int N, int K, const std::vector<Item>& items
 
 template <class TC, class TL>
 void host_run(const int64_t* P, int N, int K, const std::vector<Item>& items, const std::vector<Range>* ranges,
-              int threads, Acc& acc) {
+              int threads, Acc& acc, const CellSink* sink) {
   std::atomic<size_t> next(0);
   std::vector<Acc> part(std::max(1, threads));
   const size_t units = ranges ? ranges->size() : items.size();
@@ -776,6 +777,7 @@ void host_run(const int64_t* P, int N, int K, const std::vector<Item>& items, co
     std::vector<Uniform<TC>> uni(1);
     Walker<TC, TL, HostTeam> W(tm, P, N, K, N, sc.data(), sl.data(), fl.data(), uni.data());
     W.tri = colex_table();
+    if (sink) W.sink = *sink;
     Acc a{};
     for (;;) {
       const size_t u = next.fetch_add(1);
@@ -802,16 +804,16 @@ void host_run(const int64_t* P, int N, int K, const std::vector<Item>& items, co
 }
 
 void host_enumerate(int path, const int64_t* P, int N, int K, const std::vector<Item>& items, int threads, Acc& acc,
-                    int team_width, const std::vector<Range>* ranges) {
+                    int team_width, const std::vector<Range>* ranges, const CellSink* sink) {
   if (team_width > 1) {  // one team walks every range in order
-    if (path == 0) lockstep_run<int32_t, int64_t>(P, N, K, items, ranges, team_width, acc);
-    else if (path == 1) lockstep_run<int64_t, int64_t>(P, N, K, items, ranges, team_width, acc);
-    else lockstep_run<i128, i128>(P, N, K, items, ranges, team_width, acc);
+    if (path == 0) lockstep_run<int32_t, int64_t>(P, N, K, items, ranges, team_width, acc, sink);
+    else if (path == 1) lockstep_run<int64_t, int64_t>(P, N, K, items, ranges, team_width, acc, sink);
+    else lockstep_run<i128, i128>(P, N, K, items, ranges, team_width, acc, sink);
     return;
   }
-  if (path == 0) host_run<int32_t, int64_t>(P, N, K, items, ranges, threads, acc);
-  else if (path == 1) host_run<int64_t, int64_t>(P, N, K, items, ranges, threads, acc);
-  else host_run<i128, i128>(P, N, K, items, ranges, threads, acc);
+  if (path == 0) host_run<int32_t, int64_t>(P, N, K, items, ranges, threads, acc, sink);
+  else if (path == 1) host_run<int64_t, int64_t>(P, N, K, items, ranges, threads, acc, sink);
+  else host_run<i128, i128>(P, N, K, items, ranges, threads, acc, sink);
 }
 
 }  // namespace bd

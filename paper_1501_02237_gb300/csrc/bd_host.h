@@ -53,6 +53,6 @@ bool build_items_into(int npts, int k, uint64_t max_subsets, Item* out, size_t c
 // each), for an integer path; team_width > 1 instead runs one team of that many lanes as
 // threads in lockstep.  With ranges, teams take whole ranges of consecutive items.
 void host_enumerate(int path, const int64_t* P, int N, int K, const std::vector<Item>& items, int threads, Acc& acc,
-                    int team_width = 1, const std::vector<Range>* ranges = nullptr);
+                    int team_width = 1, const std::vector<Range>* ranges = nullptr, const CellSink* sink = nullptr);
 
 }  // namespace bd
