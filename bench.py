@@ -35,15 +35,18 @@ TRAFFIC = {"sources_sha256": "1de3b58818513f1cb2806c20626c41567c899b017db9c467da
            "single_n24_k8": 1127424 + 70656, "heavy_quiver_n32_k10": 8005120 + 788224}
 
 
+# the sources that determine the enumeration kernel's code and its work list
+KERNEL_SOURCES = ("bd_core.cuh", "bd_kernels.cuh", "bd_kernels.cu", "bd_host.cpp", "bd_host.h", "bd_lifts.h")
+
+
 def sources_sha256() -> str:
     import hashlib
     d = os.path.join(ROOT, "paper_1501_02237_gb300", "csrc")
     h = hashlib.sha256()
-    for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh", ".h", ".cpp")):
-            h.update(f.encode())
-            with open(os.path.join(d, f), "rb") as fh:
-                h.update(fh.read())
+    for f in KERNEL_SOURCES + ("../build.py",):  # and the compiler flags
+        h.update(f.encode())
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()
 METRIC = "exact (k+1)-subsets tested/sec (exact degrees/sec alongside), 1 GB300"
 UNIT = "subsets/s"

@@ -256,12 +256,7 @@ int plan_prepare(bd_plan* p, const int64_t* points, const int64_t* lifts, int32_
   if (rc) return rc;
   const uint64_t total = bd::binom(npts, k + 1);
   const uint64_t warps = (uint64_t)p->shape.blocks * p->shape.warps;
-  int64_t thr = opts && opts->item_subsets > 0 ? opts->item_subsets : 0;
-  if (!thr) {  // items fine enough for the tail of the guided ranges
-    thr = (int64_t)(total / (warps * 32 + 1));
-    thr = std::max<int64_t>(thr, 64);
-    thr = std::min<int64_t>(thr, (int64_t)1 << 20);
-  }
+  const int64_t thr = opts && opts->item_subsets > 0 ? opts->item_subsets : (int64_t)bd::default_item_subsets(total, warps);
   rc = get_items(npts, k, thr, (int64_t)warps, p->items);
   if (rc) return rc;
   rc = get_tri(p->tri);

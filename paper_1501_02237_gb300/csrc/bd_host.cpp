@@ -620,6 +620,11 @@ static uint64_t item_cost(int N, int K, const Item& it) {
   return c;
 }
 
+uint64_t default_item_subsets(uint64_t total, uint64_t teams) {
+  const uint64_t t = total / (teams * 32 + 1);
+  return std::min<uint64_t>(std::max<uint64_t>(t, 64), (uint64_t)1 << 20);
+}
+
 void build_ranges(int N, int K, uint64_t max_subsets, uint64_t teams, std::vector<Item>& items,
                   std::vector<Range>& ranges) {
   items.clear();

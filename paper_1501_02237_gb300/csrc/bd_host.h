@@ -38,6 +38,10 @@ int choose_path(double coord_bits, double full_bits);
 // depth of the walker's bottom stage), then sorted by decreasing size.
 std::vector<Item> build_items(int npts, int k, uint64_t max_subsets);
 
+// The work-item split threshold for a launch of `teams` warps over `total` subsets: fine enough
+// for the packing of ranges (1/32 of a warp's share), between 64 and 2^20 subsets.
+uint64_t default_item_subsets(uint64_t total, uint64_t teams);
+
 // The same items in lexicographic order, grouped into ranges of consecutive items for `teams`
 // teams: runs packed up to 1/8 of a team's share of the estimated work (the bottom stage's
 // warp rounds and level steps, not subsets, which misjudge regions of small nodes), taken
