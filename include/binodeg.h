@@ -356,6 +356,24 @@ int bd_cells(const int64_t* points, int32_t npts, int32_t k, uint64_t seed, int6
 int bd_host_cells(const int64_t* points, const int64_t* lifts, int32_t npts, int32_t k, int64_t capacity,
                   uint8_t* cells, int64_t* den, int64_t* alpha, int64_t* beta, int64_t* count);
 
+/* The start solutions of the witness-set homotopy, cell by cell (Sec. 6): for every cell of
+ * bd_cells (same seed, lexicographic order) and generic coefficients c_{i,q} = exp(2 pi i u),
+ * u from SplitMix64 on the stream mix(coef_seed XOR 0xC2B2AE3D27D4EB4F) at counter
+ * i*npts + q + 1, the solutions of the cell's start system (Eq. affine-cut-starting, reduced
+ * to the binomial system of Eq. affine-cut-eliminated), |det| of them per cell and the volume
+ * in all.
+ *   sols          : capacity x k complex numbers (re, im interleaved); solution s, coordinate
+ *                   i at sols[2 (s k + i)]; a device pointer when sols_on_device is nonzero
+ *   count         : the number of solutions (when above capacity: BD_ERR_ARG, nothing written)
+ *   max_residual  : NULL, or receives the largest |y^{E_j} / b_j - 1| over all solutions and
+ *                   equations (checked on the device)
+ * Errors: BD_ERR_ARG, BD_ERR_OVERFLOW, BD_ERR_TIES, BD_ERR_CUDA, BD_ERR_NOMEM. */
+int bd_start_solutions(const int64_t* points, int32_t npts, int32_t k, uint64_t seed, uint64_t coef_seed,
+                       int64_t capacity, double* sols, int32_t sols_on_device, int64_t* count, double* max_residual);
+/* The same on one host core with the given lifts (CPU tests). */
+int bd_host_start_solutions(const int64_t* points, const int64_t* lifts, int32_t npts, int32_t k, uint64_t coef_seed,
+                            int64_t capacity, double* sols, int64_t* count, double* max_residual);
+
 #ifdef __cplusplus
 }
 #endif

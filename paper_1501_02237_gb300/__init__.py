@@ -18,7 +18,8 @@ from ._lib import (BD_FEATURES, BD_MLP_PARAMS, BD_FLAG_DEGENERATE, BD_FLAG_INCON
 from ._lib import F32P, I32P, U8P
 
 __all__ = ["CostModel", "Server", "degree", "volume", "volume_noalloc", "volume_lifted", "classify", "reduce", "Plan", "Batch", "set_stream",
-           "host_volume_lifted", "cells", "host_cells", "BinodegError", "lib"]
+           "host_volume_lifted", "cells", "host_cells", "start_solutions", "host_start_solutions", "BinodegError",
+           "lib"]
 
 
 def set_stream(stream) -> None:
@@ -92,6 +93,44 @@ def host_cells(points, lifts, capacity: int = 4096):
     npts, k = P.shape
     return _cells_call(lambda cap, c, d, a, b, n: lib().bd_host_cells(ptr(P), ptr(W), npts, k, cap, c, d, a, b, n),
                        k, capacity)
+
+
+def _start_call(fn, k):
+    count = C.c_int64(0)
+    res = C.c_double(0)
+    rc = fn(0, None, C.byref(count), C.byref(res))  # the count first
+    if rc not in (0, 1):
+        check(rc)
+    n = int(count.value)
+    out = np.zeros((max(n, 1), k), dtype=np.complex128)
+    check(fn(n, out.ctypes.data_as(C.c_void_p), C.byref(count), C.byref(res)))
+    return out[:n], float(res.value)
+
+
+def start_solutions(points, seed: int = 0, coef_seed: int = 0, device_out=None):
+    """bd_start_solutions: (solutions as an (nvol, k) complex array, cell by cell in the order
+    of cells(), and the largest equation residual checked on the device).  With device_out (a
+    contiguous complex128 CUDA tensor of at least nvol x k elements) the solutions stay in it
+    and (count, residual) is returned instead."""
+    P = i64(points)
+    npts, k = P.shape
+    if device_out is not None:
+        count, res = C.c_int64(0), C.c_double(0)
+        check(lib().bd_start_solutions(ptr(P), npts, k, C.c_uint64(seed), C.c_uint64(coef_seed),
+                                       device_out.numel() // k, C.c_void_p(device_out.data_ptr()), 1,
+                                       C.byref(count), C.byref(res)))
+        return int(count.value), float(res.value)
+    return _start_call(lambda cap, buf, cnt, res: lib().bd_start_solutions(ptr(P), npts, k, C.c_uint64(seed),
+                                                                          C.c_uint64(coef_seed), cap, buf, 0, cnt, res), k)
+
+
+def host_start_solutions(points, lifts, coef_seed: int = 0):
+    """bd_host_start_solutions: the same with the given lifts on the host (CPU tests)."""
+    P, W = i64(points), i64(lifts)
+    npts, k = P.shape
+    return _start_call(lambda cap, buf, cnt, res: lib().bd_host_start_solutions(ptr(P), ptr(W), npts, k,
+                                                                               C.c_uint64(coef_seed), cap, buf, cnt,
+                                                                               res), k)
 
 def reduce(A, coef=None) -> dict:
     """bd_reduce: host front end only -> kernel points (n+1 x d, origin last), rank, torsion."""

@@ -122,6 +122,10 @@ SIGNATURES = {
                            C.POINTER(C.c_int64), C.POINTER(VolumeOut)]),
     "bd_host_cells": (C.c_int, [I64P, I64P, C.c_int32, C.c_int32, C.c_int64, U8P, I64P, I64P, I64P,
                                 C.POINTER(C.c_int64)]),
+    "bd_start_solutions": (C.c_int, [I64P, C.c_int32, C.c_int32, C.c_uint64, C.c_uint64, C.c_int64, C.c_void_p,
+                                     C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_double)]),
+    "bd_host_start_solutions": (C.c_int, [I64P, I64P, C.c_int32, C.c_int32, C.c_uint64, C.c_int64, C.c_void_p,
+                                          C.POINTER(C.c_int64), C.POINTER(C.c_double)]),
     "bd_volume_noalloc": (C.c_int, [I64P, C.c_int32, C.c_int32, C.c_uint64, C.POINTER(VolumeOut)]),
     "bd_batch_create": (C.c_int, [C.POINTER(C.c_void_p)]),
     "bd_batch_add": (C.c_int, [C.c_void_p, I64P, C.c_int32, C.c_int32, I64P, C.c_uint64, I32P]),

@@ -1,0 +1,46 @@
+"""Start solutions of the witness-set homotopy (Sec. 6) from the host emulation against the
+oracle (oracle/start.py, which solves each cell's binomial system through its own Smith form):
+the same solution set per cell, |det| solutions per cell, residuals at rounding level."""
+
+import random
+
+import numpy as np
+import pytest
+
+import paper_1501_02237_gb300 as bd
+from oracle.cells import lower_cells
+from oracle.lifts import lifts as oracle_lifts
+from oracle.start import start_solutions
+
+
+def same_sets(mine, ref, tol=1e-9):
+    if len(mine) != len(ref):
+        return False
+    ref = np.array(ref)
+    used = np.zeros(len(ref), dtype=bool)
+    for y in mine:
+        d = np.max(np.abs(ref - y[None, :]), axis=1)
+        d[used] = np.inf
+        j = int(np.argmin(d))
+        if d[j] > tol * max(1.0, float(np.max(np.abs(y)))):
+            return False
+        used[j] = True
+    return True
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_host_start_solutions_match_oracle(seed):
+    rng = random.Random(5100 + seed)
+    k = rng.choice([1, 2, 3, 4])
+    n = rng.randint(k + 2, 8)
+    pts = [tuple(rng.randint(-2, 2) for _ in range(k)) for _ in range(n)]
+    lf = oracle_lifts(n, seed)
+    ys, res = bd.host_start_solutions(np.array(pts), np.array(lf), coef_seed=seed)
+    cells = lower_cells(pts, lf)
+    ref = start_solutions(pts, [c[0] for c in cells], seed)
+    assert len(ys) == sum(c[1] for c in cells)
+    assert res < 1e-10
+    i = 0
+    for (cell, vol, _, _), rc in zip(cells, ref):
+        assert same_sets(ys[i:i + vol], rc)
+        i += vol
