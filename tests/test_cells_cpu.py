@@ -30,3 +30,17 @@ def test_host_cells_count_only_and_ties():
     pts = np.array([(0, 0), (1, 0), (0, 1), (1, 1)])
     with pytest.raises(bd.BinodegError):
         bd.host_cells(pts, np.zeros(4, dtype=np.int64))  # constant lifts: ties
+
+
+def test_host_cells_segment_and_mid_path():
+    # k = 1: cells are consecutive distinct points; coordinates of 2^20 take the 64-bit path
+    pts = np.array([[0], [3], [-2], [5], [3]])
+    got = bd.host_cells(pts, np.array(oracle_lifts(5, 1)))
+    assert sum(1 for _ in got) == len(lower_cells(pts.tolist(), oracle_lifts(5, 1)))
+    big = [(1 << 20) * x for x in (0, 1, 2)] 
+    pts2 = [(a, b) for a in (0, 1 << 20) for b in (0, 3 << 19)] + [(1 << 19, 1 << 18)]
+    lf = oracle_lifts(len(pts2), 2)
+    got2 = bd.host_cells(np.array(pts2), np.array(lf))
+    ref2 = lower_cells(pts2, lf)
+    assert [g["cell"] for g in got2] == [tuple(c[0]) for c in ref2]
+    assert all(g["alpha"] == c[2] and g["beta"] == c[3] for g, c in zip(got2, ref2))
