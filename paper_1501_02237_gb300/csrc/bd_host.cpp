@@ -464,20 +464,34 @@ int reduce_system(const int64_t* A, int n, int m, const int64_t* coef, Reduction
   out.dim = d;
   out.torsion = 1;
   if (rank > 0) {
-    Mat X, S;
-    if (!kernel_rows(transpose(P0), X, err, false)) return BD_ERR_OVERFLOW;  // {y : P_0 y = 0}
-    if (!kernel_rows(transpose(R), S, err, false)) return BD_ERR_OVERFLOW;   // {x : R x = 0}
+    // |det X_I| and |det S_J| from the complementary minors of the orthogonal complements
+    // already at hand: for a saturated lattice and its saturated orthogonal complement the
+    // Plucker coordinates agree up to sign on complementary index sets (Jacobi's complementary
+    // minor theorem applied to a unimodular completion of a basis), so
+    // |det X_I| = |det P_0 restricted to the columns outside I| and likewise for S and R.
     std::vector<int> I, J;
-    if (X.r != rank || S.r != rank || !pivot_sets(M, rank, I, J)) { err = "rank selection failed"; return BD_ERR_OVERFLOW; }
-    std::vector<i128> a((size_t)rank * rank), x((size_t)rank * rank), sm((size_t)rank * rank);
+    if (!pivot_sets(M, rank, I, J)) { err = "rank selection failed"; return BD_ERR_OVERFLOW; }
+    std::vector<int> Ic, Jc;
+    for (int t = 0, u = 0; t < n; ++t) {
+      if (u < rank && I[u] == t) ++u;
+      else Ic.push_back(t);
+    }
+    std::vector<int> Js(J);
+    std::sort(Js.begin(), Js.end());
+    for (int t = 0, u = 0; t < m; ++t) {
+      if (u < rank && Js[u] == t) ++u;
+      else Jc.push_back(t);
+    }
+    std::vector<i128> a((size_t)rank * rank), x((size_t)d * d), sm(Jc.size() * Jc.size());
     for (int u = 0; u < rank; ++u)
-      for (int v = 0; v < rank; ++v) {
-        a[(size_t)u * rank + v] = M.at(I[u], J[v]);
-        x[(size_t)u * rank + v] = X.at(u, I[v]);
-        sm[(size_t)u * rank + v] = S.at(u, J[v]);
-      }
+      for (int v = 0; v < rank; ++v) a[(size_t)u * rank + v] = M.at(I[u], J[v]);
+    for (int u = 0; u < d; ++u)
+      for (int v = 0; v < d; ++v) x[(size_t)u * d + v] = P0.at(u, Ic[v]);
+    const int e = (int)Jc.size();
+    for (int u = 0; u < e; ++u)
+      for (int v = 0; v < e; ++v) sm[(size_t)u * e + v] = R.at(u, Jc[v]);
     i128 da, dx, ds;
-    if (!det_exact(a, rank, da) || !det_exact(x, rank, dx) || !det_exact(sm, rank, ds)) {
+    if (!det_exact(a, rank, da) || !det_exact(x, d, dx) || !det_exact(sm, e, ds)) {
       err = "torsion determinants exceed 2^127";
       return BD_ERR_OVERFLOW;
     }

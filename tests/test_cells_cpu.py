@@ -37,7 +37,6 @@ def test_host_cells_segment_and_mid_path():
     pts = np.array([[0], [3], [-2], [5], [3]])
     got = bd.host_cells(pts, np.array(oracle_lifts(5, 1)))
     assert sum(1 for _ in got) == len(lower_cells(pts.tolist(), oracle_lifts(5, 1)))
-    big = [(1 << 20) * x for x in (0, 1, 2)] 
     pts2 = [(a, b) for a in (0, 1 << 20) for b in (0, 3 << 19)] + [(1 << 19, 1 << 18)]
     lf = oracle_lifts(len(pts2), 2)
     got2 = bd.host_cells(np.array(pts2), np.array(lf))
