@@ -151,7 +151,10 @@ bool consistent(const int64_t* coef, int m, const Mat& R, std::string& err, bool
 // the doubles trustworthy with large entries, the coefficients of row k are recomputed from the
 // exact integer row before each use and size reduction is repeated until it makes only small
 // corrections (the usual floating-point LLL safeguard).
-bool lll(std::vector<i128>& B, int d, int n) {
+template <class T>
+bool lll_t(std::vector<T>& B, int d, int n) {
+  const T limit = (T)1 << 62;
+  auto tabs_ = [](T x) { return x < 0 ? -x : x; };
   if (d <= 1) return true;
   std::vector<double> bs((size_t)d * n), bn(d, 0.0), mu((size_t)d * d, 0.0);
   auto row = [&](int i) { return &B[(size_t)i * n]; };
@@ -167,17 +170,16 @@ bool lll(std::vector<i128>& B, int d, int n) {
         const double m = mu[(size_t)k * d + j];
         if (std::fabs(m) <= 0.51) continue;
         if (std::fabs(m) > 4e18) return false;
-        const i128 q = (i128)std::llround(m);
+        const T q = (T)std::llround(m);
         for (int c = 0; c < n; ++c) {
-          i128 t;
-          if (__builtin_mul_overflow(q, row(j)[c], &t)) return false;
-          const i128 v = row(k)[c] - t;
-          if (iabs(v) >= ENTRY_LIMIT) return false;
+          T t, v;
+          if (__builtin_mul_overflow(q, row(j)[c], &t) || __builtin_sub_overflow(row(k)[c], t, &v)) return false;
+          if (tabs_(v) >= limit) return false;
           row(k)[c] = v;
         }
         for (int l = 0; l < j; ++l) mu[(size_t)k * d + l] -= (double)q * mu[(size_t)j * d + l];
         mu[(size_t)k * d + j] -= (double)q;
-        if (iabs(q) > ((i128)1 << 20)) large = true;
+        if (tabs_(q) > ((T)1 << 20)) large = true;
       }
       if (!large) break;
     }
@@ -209,6 +211,8 @@ bool lll(std::vector<i128>& B, int d, int n) {
   return true;
 }
 
+bool lll(std::vector<i128>& B, int d, int n) { return lll_t<i128>(B, d, n); }
+
 // checked i128 arithmetic
 bool mul_ok(i128 a, i128 b, i128& r) { return !__builtin_mul_overflow(a, b, &r); }
 bool add_ok(i128 a, i128 b, i128& r) { return !__builtin_add_overflow(a, b, &r); }
@@ -220,17 +224,26 @@ bool add_ok(i128 a, i128 b, i128& r) { return !__builtin_add_overflow(a, b, &r);
 // basis is LLL-reduced whenever its entries grow, and after the last column when reduce_last
 // (the kernel points themselves; bases used only for determinants skip it).  The result is
 // saturated: it is a basis of ker(M) intersected with Z^rows.
-bool kernel_rows(const Mat& M, Mat& U, std::string& err, bool reduce_last = true) {
+template <class T>
+bool kernel_rows_t(const Mat& M, Mat& U, std::string& err, bool reduce_last) {
+  auto tabs_ = [](T x) { return x < 0 ? -x : x; };
+  auto mul_t = [](T a, T b, T& r) { return !__builtin_mul_overflow(a, b, &r); };
+  auto add_t = [](T a, T b, T& r) { return !__builtin_add_overflow(a, b, &r); };
+  auto entry = [&](int t, int j, T& x) {  // M's entry in T
+    const i128 v = M.at(t, j);
+    x = (T)v;
+    return (i128)x == v;
+  };
   const int n = M.r, m = M.c;
-  std::vector<std::vector<i128>> B(n, std::vector<i128>(n, 0));
+  std::vector<std::vector<T>> B(n, std::vector<T>(n, 0));
   for (int i = 0; i < n; ++i) B[i][i] = 1;
   for (int j = 0; j < m && !B.empty(); ++j) {
     const int d = (int)B.size();
-    std::vector<i128> v(d, 0);
+    std::vector<T> v(d, 0);
     for (int i = 0; i < d; ++i)
       for (int t = 0; t < n; ++t) {
-        i128 pr;
-        if (!mul_ok(B[i][t], M.at(t, j), pr) || !add_ok(v[i], pr, v[i])) { err = "kernel values overflow"; return false; }
+        T pr, mt;
+        if (!entry(t, j, mt) || !mul_t(B[i][t], mt, pr) || !add_t(v[i], pr, v[i])) { err = "kernel values overflow"; return false; }
       }
     // Euclid on the value vector: reduce every value modulo the smallest nonzero one (row
     // operations b_i -= q b_min) until a single nonzero value g = gcd remains; this keeps the
@@ -247,60 +260,62 @@ bool kernel_rows(const Mat& M, Mat& U, std::string& err, bool reduce_last = true
       for (int i = 0; i < d; ++i)
         if (v[i] != 0) {
           ++nz;
-          if (piv < 0 || iabs(v[i]) < iabs(v[piv])) piv = i;
+          if (piv < 0 || tabs_(v[i]) < tabs_(v[piv])) piv = i;
         }
       if (nz <= 1) {
         std::swap(B[0], B[piv]);
         std::swap(v[0], v[piv]);
         break;
       }
-      i128 big = 0;
+      T big = 0;
       for (int i = 0; i < d; ++i) {
         if (i == piv || v[i] == 0) continue;
-        const bool narrow = iabs(v[i]) < ((i128)1 << 62) && iabs(v[piv]) < ((i128)1 << 62);
-        i128 q = narrow ? (i128)((int64_t)v[i] / (int64_t)v[piv]) : v[i] / v[piv];  // truncation
-        const i128 r = v[i] - q * v[piv];  // smaller than |v_piv|
-        if (2 * iabs(r) > iabs(v[piv])) q += ((r > 0) == (v[piv] > 0)) ? 1 : -1;  // nearest quotient
+        const bool narrow = v[i] > -((T)1 << 62) && v[i] < ((T)1 << 62) && v[piv] > -((T)1 << 62) &&
+                            v[piv] < ((T)1 << 62);
+        if (!narrow && sizeof(T) == 8) { err = "kernel values leave 62 bits"; return false; }
+        T q = narrow ? (T)((int64_t)v[i] / (int64_t)v[piv]) : v[i] / v[piv];  // truncation
+        const T r = v[i] - q * v[piv];  // smaller than |v_piv|
+        if (tabs_(r) > tabs_(v[piv]) - tabs_(r)) q += ((r > 0) == (v[piv] > 0)) ? 1 : -1;  // nearest quotient
         for (int c = 0; c < n; ++c) {
-          i128 t;
-          if (!mul_ok(q, B[piv][c], t) || !add_ok(B[i][c], -t, B[i][c])) { err = "kernel basis overflow"; return false; }
-          big = std::max(big, iabs(B[i][c]));
+          T t;
+          if (!mul_t(q, B[piv][c], t) || __builtin_sub_overflow(B[i][c], t, &B[i][c])) { err = "kernel basis overflow"; return false; }
+          big = std::max(big, tabs_(B[i][c]));
         }
         v[i] -= q * v[piv];
       }
-      if (big > ((i128)1 << 40) && resets < 3) {
+      if (big > ((T)1 << 40) && resets < 3) {
         ++resets;
-        std::vector<i128> flat;
+        std::vector<T> flat;
         for (auto& row : B) flat.insert(flat.end(), row.begin(), row.end());
-        if (!lll(flat, d, n)) { err = "kernel basis entries exceed 2^62"; return false; }
+        if (!lll_t<T>(flat, d, n)) { err = "kernel basis entries exceed 2^62"; return false; }
         for (int i = 0; i < d; ++i) {
           v[i] = 0;
           for (int c = 0; c < n; ++c) {
             B[i][c] = flat[(size_t)i * n + c];
-            i128 pr;
-            if (!mul_ok(B[i][c], M.at(c, j), pr) || !add_ok(v[i], pr, v[i])) { err = "kernel values overflow"; return false; }
+            T pr, mt;
+            if (!entry(c, j, mt) || !mul_t(B[i][c], mt, pr) || !add_t(v[i], pr, v[i])) { err = "kernel values overflow"; return false; }
           }
         }
       }
       if (guard > 8000) { err = "kernel elimination did not converge"; return false; }
     }
     B.erase(B.begin());
-    i128 big = 0;
+    T big = 0;
     for (auto& r : B)
-      for (i128 x : r) big = std::max(big, iabs(x));
+      for (T x : r) big = std::max(big, tabs_(x));
     const bool last_col = reduce_last && (j == m - 1);
 #ifdef BD_DEBUG
     {
       double lb = 0;
-      for (auto& r : B) for (i128 x : r) lb = std::max(lb, (double)iabs(x));
+      for (auto& r : B) for (T x : r) lb = std::max(lb, (double)tabs_(x));
       double vb = 0;
       fprintf(stderr, "kernel_rows %dx%d col %d d=%zu big=%.3g\n", n, m, j, B.size(), lb);
     }
 #endif
-    if (!B.empty() && (big > ((i128)1 << 16) || last_col)) {
-      std::vector<i128> flat;
+    if (!B.empty() && (big > ((T)1 << 16) || last_col)) {
+      std::vector<T> flat;
       for (auto& row : B) flat.insert(flat.end(), row.begin(), row.end());
-      if (!lll(flat, (int)B.size(), n)) { err = "kernel basis entries exceed 2^62"; return false; }
+      if (!lll_t<T>(flat, (int)B.size(), n)) { err = "kernel basis entries exceed 2^62"; return false; }
       for (size_t i = 0; i < B.size(); ++i)
         for (int c = 0; c < n; ++c) B[i][c] = flat[i * n + c];
     }
@@ -308,10 +323,18 @@ bool kernel_rows(const Mat& M, Mat& U, std::string& err, bool reduce_last = true
   U = Mat((int)B.size(), n);
   for (size_t i = 0; i < B.size(); ++i)
     for (int c = 0; c < n; ++c) {
-      if (iabs(B[i][c]) >= ENTRY_LIMIT) { err = "kernel basis entries exceed 2^62"; return false; }
-      U.at((int)i, c) = B[i][c];
+      if (tabs_(B[i][c]) >= ((T)1 << 62)) { err = "kernel basis entries exceed 2^62"; return false; }
+      U.at((int)i, c) = (i128)B[i][c];
     }
   return true;
+}
+
+// int64 arithmetic while every value fits (the common case), else the same steps in int128
+// (identical decisions, so identical results)
+bool kernel_rows(const Mat& M, Mat& U, std::string& err, bool reduce_last = true) {
+  if (kernel_rows_t<int64_t>(M, U, err, reduce_last)) return true;
+  err.clear();
+  return kernel_rows_t<i128>(M, U, err, reduce_last);
 }
 
 Mat transpose(const Mat& A) {
