@@ -36,7 +36,7 @@ TRAFFIC = {"sources_sha256": "487789872a6c4990dd2b7a185402711f613c8bc096d5c3a8c0
 
 
 # the sources that determine the enumeration kernel's code and its work list
-KERNEL_SOURCES = ("bd_core.cuh", "bd_kernels.cuh", "bd_kernels.cu", "bd_host.cpp", "bd_host.h", "bd_lifts.h")
+KERNEL_SOURCES = ("bd_core.cuh", "bd_kernels.cuh", "bd_kernels.cu", "bd_worklist.cpp", "bd_host.h", "bd_lifts.h")
 
 
 def sources_sha256() -> str:

@@ -583,129 +583,6 @@ int choose_path(double coord_bits, double full_bits) {
   return -1;
 }
 
-namespace {
-
-// every prefix of the split tree, depth first; emit(item) returns false to stop early
-template <class Emit>
-bool for_each_item(int N, int K, uint64_t max_subsets, Emit emit) {
-  if (K < 1 || N < K + 1) return true;
-  int pre[KMAX + 1];
-  int len = 1;
-  pre[0] = 0;
-  for (;;) {
-    const uint64_t T = subtree_size(N, K, pre[len - 1], len);
-    if (T > max_subsets && len < std::max(K - 2, 1)) {  // split; items stop at depth max(K-2, 1), where the
-                                                         // shallowest bottom stage (the 4-D test) starts
-      pre[len] = pre[len - 1] + 1;
-      ++len;
-      continue;
-    }
-    if (T > 0) {
-      Item x{};
-      x.len = (uint8_t)len;
-      for (int i = 0; i < len; ++i) x.idx[i] = (uint8_t)pre[i];
-      if (!emit(x)) return false;
-    }
-    // next sibling, backtracking as needed; position i admits indices up to N-1-(K-i)
-    for (;;) {
-      const int nxt = pre[len - 1] + 1;
-      if (nxt <= N - 1 - (K - (len - 1))) { pre[len - 1] = nxt; break; }
-      if (--len == 0) return true;
-    }
-  }
-}
-
-// largest subtree first; ties broken by the prefix itself, so the order is a total order
-struct ItemOrder {
-  int N, K;
-  bool operator()(const Item& a, const Item& b) const {
-    const uint64_t sa = subtree_size(N, K, a.idx[a.len - 1], a.len), sb = subtree_size(N, K, b.idx[b.len - 1], b.len);
-    if (sa != sb) return sa > sb;
-    if (a.len != b.len) return a.len < b.len;
-    for (int i = 0; i < a.len; ++i)
-      if (a.idx[i] != b.idx[i]) return a.idx[i] < b.idx[i];
-    return false;
-  }
-};
-
-}  // namespace
-
-std::vector<Item> build_items(int N, int K, uint64_t max_subsets) {
-  std::vector<Item> items;
-  for_each_item(N, K, max_subsets, [&](const Item& x) {
-    items.push_back(x);
-    return true;
-  });
-  std::sort(items.begin(), items.end(), ItemOrder{N, K});
-  return items;
-}
-
-// estimated work of an item, in warp rounds of the bottom stage plus one per level step
-static uint64_t item_cost(int N, int K, const Item& it) {
-  const int L = it.len, a = it.idx[L - 1];
-  if (K < 3) return subtree_size(N, K, a, L);
-  // the 4-D bottom stage: one Bareiss step and ceil(C(R,3)/32) warp rounds per level-(K-3)
-  // node with R points after its last index; nodes with last index v below this prefix:
-  // C(v-a-1, K-3-L) (none deeper than K-2 exists when L = K-2)
-  auto node = [&](int v) {
-    const uint64_t t = binom(N - 1 - v, 3);
-    return 1 + (t + 31) / 32;
-  };
-  if (L >= K - 2) return node(a);
-  uint64_t c = 0;
-  for (int v = a + (K - 2 - L); v <= N - 4; ++v) c += binom(v - a - 1, K - 3 - L) * node(v);
-  return c;
-}
-
-uint64_t default_item_subsets(uint64_t total, uint64_t teams) {
-  const uint64_t t = total / (teams * 32 + 1);
-  return std::min<uint64_t>(std::max<uint64_t>(t, 64), (uint64_t)1 << 20);
-}
-
-void build_ranges(int N, int K, uint64_t max_subsets, uint64_t teams, std::vector<Item>& items,
-                  std::vector<Range>& ranges) {
-  items.clear();
-  ranges.clear();
-  std::vector<uint64_t> cost;
-  uint64_t remaining = 0;
-  for_each_item(N, K, max_subsets, [&](const Item& x) {
-    items.push_back(x);
-    cost.push_back(std::max<uint64_t>(1, item_cost(N, K, x)));
-    remaining += cost.back();
-    return true;
-  });
-  // runs of consecutive items packed up to 1/8 of a team's share, then taken largest first
-  const uint64_t cap = std::max<uint64_t>(1, remaining / (8 * std::max<uint64_t>(1, teams)));
-  std::vector<uint64_t> rcost;
-  size_t i = 0;
-  while (i < items.size()) {
-    const size_t first = i;
-    uint64_t got = 0;
-    while (i < items.size() && (i == first || got + cost[i] <= cap)) got += cost[i++];
-    ranges.push_back(Range{(uint32_t)first, (uint32_t)(i - first)});
-    rcost.push_back(got);
-  }
-  std::vector<size_t> order(ranges.size());
-  for (size_t r = 0; r < order.size(); ++r) order[r] = r;
-  std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return rcost[a] > rcost[b]; });
-  std::vector<Range> sorted;
-  sorted.reserve(ranges.size());
-  for (size_t r : order) sorted.push_back(ranges[r]);
-  ranges.swap(sorted);
-}
-
-bool build_items_into(int N, int K, uint64_t max_subsets, Item* out, size_t cap, size_t* count) {
-  size_t n = 0;
-  const bool ok = for_each_item(N, K, max_subsets, [&](const Item& x) {
-    if (n == cap) return false;
-    out[n++] = x;
-    return true;
-  });
-  *count = n;
-  if (!ok) return false;
-  std::sort(out, out + n, ItemOrder{N, K});
-  return true;
-}
 
 namespace {
 struct HostTeam {
