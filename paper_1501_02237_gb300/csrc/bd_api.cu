@@ -151,6 +151,7 @@ int get_shape(int N, int K, int path, int warps_req, int bps_req, bd::LaunchShap
 namespace bd {
 int set_error(int code, const char* msg) { return fail(code, msg); }
 cudaStream_t thread_stream() { return g_stream; }
+int device_tri_table(const uint32_t** out) { return get_tri(*out); }
 }  // namespace bd
 
 // A plan owns small fixed-size device buffers (points of up to BD_NMAX x BD_KMAX coordinates,

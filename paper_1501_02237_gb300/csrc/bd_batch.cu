@@ -295,6 +295,11 @@ int run_batched(bd_batch* b, const std::vector<int>& active, const float* cost, 
     if (e != cudaSuccess) return bd::set_error(BD_ERR_CUDA, cudaGetErrorString(e));
     shapes.push_back(s);
   }
+  const uint32_t* tri = nullptr;  // fetched before any stream capture
+  {
+    const int trc = bd::device_tri_table(&tri);
+    if (trc) return trc;
+  }
   auto enqueue = [&](cudaStream_t s) -> cudaError_t {
     cudaError_t r = cudaMemsetAsync(b->d_acc, 0, sizeof(bd::DevAcc) * nsys, s);
     if (r == cudaSuccess) r = cudaMemsetAsync(b->d_cycles, 0, sizeof(unsigned long long) * nsys, s);
@@ -313,6 +318,7 @@ int run_batched(bd_batch* b, const std::vector<int>& active, const float* cost, 
       p.acc = b->d_acc;
       p.cycles = b->d_cycles;
       p.done = b->d_done;
+      p.tri = tri;
       r = bd::launch_batch(p, shapes[gi], g.path, s);
     }
     if (r == cudaSuccess) r = cudaMemcpyAsync(b->h_acc, b->d_acc, sizeof(bd::DevAcc) * nsys, cudaMemcpyDeviceToHost, s);

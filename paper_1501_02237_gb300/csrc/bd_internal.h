@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <stdint.h>
 
 namespace bd {
 
@@ -9,5 +10,8 @@ namespace bd {
 int set_error(int code, const char* msg);
 // the stream chosen with bd_set_stream() on this thread
 cudaStream_t thread_stream();
+// the current device's colex decode table for the enumeration's 4-D stage (uploaded on first
+// use; call outside stream capture)
+int device_tri_table(const uint32_t** out);
 
 }  // namespace bd

@@ -335,6 +335,7 @@ __global__ void BD_ENUM_BOUNDS k_batch(BatchParams p) {
     it.len = bi.len;
     for (int t = 0; t < bi.len; ++t) it.idx[t] = bi.idx[t];
     Walker<TC, TL, WarpTeam> W(tm, P, N, K, slots, sc, sl, fl, uniform_after(fl, slots));
+    W.tri = p.tri;
     const long long t0 = clock64();
     W.run_item(it, acc);
     cyc += (unsigned long long)(clock64() - t0);
@@ -412,11 +413,12 @@ namespace {
 // same bytes.
 template <class TC, class TL>
 __device__ void serve_item(WarpTeam& tm, const int64_t* P, int N, int K, int slots, unsigned char* stack, int maxK,
-                           const Item& it, Acc& acc) {
+                           const Item& it, Acc& acc, const uint32_t* tri) {
   TC* sc = reinterpret_cast<TC*>(stack);
   TL* sl = reinterpret_cast<TL*>(stack + align16((size_t)slots * stack_entries(maxK) * sizeof(int64_t)));
   float* fl = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(sl) + align16((size_t)slots * maxK * sizeof(int64_t)));
   Walker<TC, TL, WarpTeam> W(tm, P, N, K, slots, sc, sl, fl, uniform_after(fl, slots));
+  W.tri = tri;
   W.run_item(it, acc);
 }
 
@@ -473,8 +475,8 @@ __global__ void BD_ENUM_BOUNDS k_serve(ServeParams p) {
     for (int t = 0; t < bi.len; ++t) it.idx[t] = bi.idx[t];
     Acc acc{};
     const long long t0 = clock64();
-    if (path == PATH_NARROW) serve_item<int32_t, int64_t>(tm, P, N, K, slots, stack, p.maxK, it, acc);
-    else serve_item<int64_t, int64_t>(tm, P, N, K, slots, stack, p.maxK, it, acc);
+    if (path == PATH_NARROW) serve_item<int32_t, int64_t>(tm, P, N, K, slots, stack, p.maxK, it, acc, p.tri);
+    else serve_item<int64_t, int64_t>(tm, P, N, K, slots, stack, p.maxK, it, acc, p.tri);
     const unsigned long long cyc = (unsigned long long)(clock64() - t0);
     acc = warp_sum(acc);
     if (lane == 0) {

@@ -77,6 +77,7 @@ struct BatchParams {
   DevAcc* acc;                    // per system (reset before the launch)
   unsigned long long* cycles;     // per system: SM cycles spent in its items
   unsigned int* done;             // per system: items finished (for streaming completion)
+  const uint32_t* tri;            // colex decode table (device) or nullptr
 };
 
 size_t batch_smem_bytes(int maxN, int maxK, int warps, int path);
@@ -101,6 +102,7 @@ struct ServeParams {
   const volatile int* stop;         // host-mapped: 1 asks the kernel to exit
   unsigned long long idle_spins;    // idle polls before a warp exits (the host relaunches on demand)
   int maxN, maxK;
+  const uint32_t* tri;              // colex decode table (device) or nullptr
 };
 
 size_t serve_smem_bytes(int maxN, int maxK, int warps);

@@ -58,6 +58,7 @@ struct bd_server {
   uint64_t ring_cap = 0, comp_cap = 0;
   int maxN = BD_NMAX, maxK = 10;
   bd::LaunchShape shape;
+  const uint32_t* tri = nullptr;  // the device's colex decode table
   // device
   bd::BatchDesc* d_desc = nullptr;
   int64_t* d_pts = nullptr;
@@ -268,6 +269,7 @@ bool pump_once(bd_server* s) {
       p.idle_spins = 20000;  // ~40 ms of 2 us naps without work, then the warps exit
       p.maxN = s->maxN;
       p.maxK = s->maxK;
+      p.tri = s->tri;
       if (bd::launch_serve(p, s->shape, s->s_kernel) == cudaSuccess) {
         s->kernel_live = true;
         s->stats.launches += 1;
@@ -348,6 +350,7 @@ int bd_server_start(const bd_server_opts* opts, bd_server** out) {
   cudaError_t e;
   s->shape = bd::serve_shape(s->maxN, s->maxK, s->opts.warps_per_block, s->opts.blocks_per_sm, sms, &e);
   int rc = cu(e, "serve shape");
+  if (!rc) rc = bd::device_tri_table(&s->tri);
   auto A = [&](cudaError_t x) {
     if (rc == BD_OK && x != cudaSuccess) rc = cu(x, "server allocation");
   };
