@@ -9,7 +9,10 @@ with kappa_j = (-1)^j det(C without column j), so y^{a_j} = lambda kappa_j and t
 binomial system y^{a_j - a_k} = kappa_j / kappa_k, j < k (Eq. affine-cut-eliminated).  It is
 solved by Sec. 3's method: with the Smith form P E Q = D of the exponent matrix E (rows
 a_j - a_k), w = Q^-1 log y satisfies d_i w_i = (P log b)_i + 2 pi i r_i, r_i = 0 .. |d_i| - 1,
-and y = exp(Q w): |det E| solutions, the cell's normalized volume.
+and y = exp(Q w): |det E| solutions, the cell's normalized volume.  Written as
+log y = E^-1 log b + 2 pi i Q (r / d), the first term uses the exact rational E^-1 and the
+second is an exact fraction of a turn per coordinate (reduced mod 1 before any rounding), so
+large transform entries cost no precision.
 
 Generic coefficients (reading: the paper only asks for generic complex coefficients): unit
 complex numbers c_{i,q} = exp(2 pi i u) with u from SplitMix64 (the generator of
@@ -24,6 +27,7 @@ from __future__ import annotations
 
 import cmath
 import math
+from fractions import Fraction
 from itertools import product
 from typing import List, Sequence
 
@@ -52,20 +56,42 @@ def cell_binomial(points: Sequence[Sequence[int]], cell: Sequence[int], coef_see
     return E, b
 
 
+def _inverse(E):
+    """Exact inverse over Q (Gauss-Jordan with Fractions)."""
+    k = len(E)
+    a = [[Fraction(x) for x in row] + [Fraction(int(i == j)) for j in range(k)] for i, row in enumerate(E)]
+    for c in range(k):
+        p = next(r for r in range(c, k) if a[r][c] != 0)
+        a[c], a[p] = a[p], a[c]
+        piv = a[c][c]
+        a[c] = [x / piv for x in a[c]]
+        for r in range(k):
+            if r != c and a[r][c] != 0:
+                f = a[r][c]
+                a[r] = [x - f * y for x, y in zip(a[r], a[c])]
+    return [row[k:] for row in a]
+
+
 def solve_binomial(E: Sequence[Sequence[int]], b: Sequence[complex]) -> List[List[complex]]:
     """All solutions y in (C*)^k of prod_i y_i^E[j][i] = b_j (Sec. 3, via the Smith form)."""
     k = len(E)
     P, D, Q, r = smith_normal_form(E)
     if r < k:
         raise ValueError("singular exponent matrix")
+    Einv = _inverse(E)
     logb = [cmath.log(x) for x in b]
-    Plogb = [sum(P[i][j] * logb[j] for j in range(k)) for i in range(k)]
+    base = [complex(math.fsum(float(Einv[i][j]) * logb[j].real for j in range(k)),
+                    math.fsum(float(Einv[i][j]) * logb[j].imag for j in range(k))) for i in range(k)]
     d = [D[i][i] for i in range(k)]
+    L = 1
+    for x in d:
+        L = L * abs(x) // math.gcd(L, abs(x))
+    # turns_i = (Q (r / d))_i mod 1 = (sum_j Q_ij r_j L / d_j mod L) / L, in integers
+    w = [[Q[i][j] * (L // d[j]) for j in range(k)] for i in range(k)]
     out = []
     for rr in product(*[range(abs(x)) for x in d]):
-        w = [(Plogb[i] + 2j * math.pi * rr[i]) / d[i] for i in range(k)]
-        x = [sum(Q[i][j] * w[j] for j in range(k)) for i in range(k)]
-        out.append([cmath.exp(v) for v in x])
+        turns = [(sum(w[i][j] * rr[j] for j in range(k)) % L) / L for i in range(k)]
+        out.append([cmath.exp(base[i] + 2j * math.pi * turns[i]) for i in range(k)])
     return out
 
 

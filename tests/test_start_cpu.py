@@ -44,3 +44,23 @@ def test_host_start_solutions_match_oracle(seed):
     for (cell, vol, _, _), rc in zip(cells, ref):
         assert same_sets(ys[i:i + vol], rc)
         i += vol
+
+
+@pytest.mark.parametrize("seed", range(2))
+def test_host_start_solutions_larger_cells(seed):
+    # k = 5 cells with volumes in the hundreds: Hermite forms whose entries would grow without
+    # the modular reduction, and Smith transforms large enough to test the oracle's exact phases
+    rng = random.Random(7800 + seed)
+    k = 5
+    n = k + 3
+    pts = [tuple(rng.randint(-3, 3) for _ in range(k)) for _ in range(n)]
+    lf = oracle_lifts(n, seed)
+    ys, res = bd.host_start_solutions(np.array(pts), np.array(lf), coef_seed=seed)
+    cells = lower_cells(pts, lf)
+    assert max(c[1] for c in cells) <= 4000, "pick a smaller case"
+    ref = start_solutions(pts, [c[0] for c in cells], seed)
+    assert len(ys) == sum(c[1] for c in cells) and res < 1e-9
+    i = 0
+    for (cell, vol, _, _), rc in zip(cells, ref):
+        assert same_sets(ys[i:i + vol], rc, tol=1e-9)
+        i += vol
