@@ -205,6 +205,25 @@ def batch_section(bd, seed=0):
     return out
 
 
+def start_section(bd, P, seed=0, coef_seed=1):
+    """The witness-set start solutions of every cell of the workload (Sec. 6), kept on the
+    device: solutions/s end to end (cells, per-cell preparation, solutions, residual check)."""
+    import torch
+    _, vol = bd.cells(P, seed=seed, capacity=1 << 16)
+    out = torch.empty((vol["nvol"], P.shape[1]), dtype=torch.complex128, device="cuda")
+    bd.start_solutions(P, seed=seed, coef_seed=coef_seed, device_out=out)  # warm-up
+    ts = []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        n, res = bd.start_solutions(P, seed=seed, coef_seed=coef_seed, device_out=out)
+        torch.cuda.synchronize()
+        ts.append(time.perf_counter() - t0)
+    dt = statistics.median(ts)
+    return dict(solutions=n, cells=vol["cells"], ms=1e3 * dt, solutions_per_s=n / dt, max_residual=res,
+                note="all start solutions of the workload's cells, on the device")
+
+
 def serve_section(bd, rate=200.0, count=1000, train_count=20000):
     """Cost model trained on method-generated runs, then a Poisson stream served with continuous
     batching (n ~ U[12,30], k ~ U[4,10]); p50/p99 latency and degrees/s per admission policy."""
@@ -423,6 +442,7 @@ def main():
     if rank == 0 and world == 1 and not args.no_batch_serve:
         line["batch"] = batch_section(bd)
         line["serve"] = serve_section(bd)
+        line["start_solutions"] = start_section(bd, P, seed=seed)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(s, subsets)
     if rank == 0:
