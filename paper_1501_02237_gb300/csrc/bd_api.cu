@@ -74,7 +74,7 @@ void set_u128(uint64_t& lo, uint64_t& hi, u128 v) {
 struct ItemList {
   std::vector<bd::Item> host;  // lexicographic order
   std::vector<bd::Range> ranges;
-  bd::Item* dev = nullptr;
+  bd::PackedItem* dev = nullptr;  // the same items, packed, on the device
   bd::Range* dev_ranges = nullptr;
 };
 std::mutex g_cache_mu;
@@ -97,10 +97,12 @@ int get_items(int N, int K, int64_t thr, int64_t teams, std::shared_ptr<ItemList
   }
   auto L = std::make_shared<ItemList>();
   bd::build_ranges(N, K, (uint64_t)thr, (uint64_t)teams, L->host, L->ranges);
-  cudaError_t e = cudaMalloc(&L->dev, sizeof(bd::Item) * std::max<size_t>(1, L->host.size()));
+  std::vector<bd::PackedItem> packed(L->host.size());
+  for (size_t i = 0; i < packed.size(); ++i) packed[i] = bd::pack_item(L->host[i]);
+  cudaError_t e = cudaMalloc(&L->dev, sizeof(bd::PackedItem) * std::max<size_t>(1, L->host.size()));
   if (e == cudaSuccess) e = cudaMalloc(&L->dev_ranges, sizeof(bd::Range) * std::max<size_t>(1, L->ranges.size()));
   if (e == cudaSuccess && !L->host.empty())
-    e = cudaMemcpy(L->dev, L->host.data(), sizeof(bd::Item) * L->host.size(), cudaMemcpyHostToDevice);
+    e = cudaMemcpy(L->dev, packed.data(), sizeof(bd::PackedItem) * packed.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess && !L->ranges.empty())
     e = cudaMemcpy(L->dev_ranges, L->ranges.data(), sizeof(bd::Range) * L->ranges.size(), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return cuda_fail(e, "work list upload");

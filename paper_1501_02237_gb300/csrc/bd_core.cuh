@@ -364,6 +364,27 @@ struct Idx15 {
   }
 };
 
+// the first field at which two packed index lists differ (15 when none of the 15 does)
+constexpr uint64_t kIdxHiMask = (1ull << 30) - 1;
+BD_HD int first_difference(const Idx15& a, const Idx15& b) {
+  const uint64_t x = a.lo ^ b.lo;
+  if (x) return ctz64(x) / 6;
+  const uint64_t y = (a.hi ^ b.hi) & kIdxHiMask;
+  return y ? 10 + ctz64(y) / 6 : 15;
+}
+
+// A work item as the device reads it: the prefix as six-bit fields (entries 0..9 in lo, 10..14
+// in the low 30 bits of hi) and its length in the top byte of hi.
+struct PackedItem {
+  uint64_t lo, hi;
+};
+BD_HD int packed_len(const PackedItem& p) { return (int)(p.hi >> 56); }
+BD_HD PackedItem pack_item(const Item& it) {
+  Idx15 x;
+  for (int i = 0; i < it.len; ++i) x.set(i, it.idx[i]);
+  return PackedItem{x.lo, x.hi | ((uint64_t)it.len << 56)};
+}
+
 // The pivots and exact dividers of the levels: the same for every lane of a team, so one copy
 // per team (in shared memory on the GPU), written by lane 0 and read after a team sync.
 template <class TC>
@@ -1032,29 +1053,25 @@ struct Walker {
   // every (K+1)-subset extending the prefix it.idx[0 .. it.len-1] (len <= bottom depth).  The
   // states of a prefix shared with the previous item are still in place and are not rebuilt
   // (the depth-first walk below an item only rewrites levels >= its length).
-  BD_HD void run_item(const Item& it, Acc& acc) {
-    const int L = it.len;
+  BD_HD void run_item(const Item& it, Acc& acc) { run_item(pack_item(it), acc); }
+
+  BD_HD void run_item(const PackedItem& it, Acc& acc) {
+    const Idx15 pre{it.lo, it.hi & kIdxHiMask};
+    const int L = packed_len(it);
     const int B = bottom_depth();
     const bool lead = tm.lane() == 0;  // uniform counts are added once per team
-    // the item's bytes as four words in registers; prefix index j is byte j+1
-    uint32_t w[4];
-    memcpy(w, &it, sizeof(w));
-    const uint32_t w0 = w[0], w1 = w[1], w2 = w[2], w3 = w[3];
-    auto pre = [&](int j) -> int {
-      const int b = j + 1, wi = b >> 2;
-      const uint32_t x = wi == 0 ? w0 : (wi == 1 ? w1 : (wi == 2 ? w2 : w3));
-      return (int)((x >> ((b & 3) * 8)) & 255u);
-    };
-    const int last = pre(L - 1);
-    int m = 0;
-    while (m < valid && m < L && s.get(m) == pre(m)) ++m;
+    const int last = pre.get(L - 1);
+    // the first level whose index differs from the built prefix (six-bit fields compared at once)
+    int m = first_difference(s, pre);
+    m = m < valid ? m : valid;
+    m = m < L ? m : L;
     if (m == 0) {
-      start(pre(0));
+      start(pre.get(0));
       m = 1;
     }
     valid = m;
     for (int j = m; j < L; ++j) {
-      if (!build(j, pre(j))) {
+      if (!build(j, pre.get(j))) {
         if (lead) acc.singular += subtree_size(N, K, last, L);
         return;
       }

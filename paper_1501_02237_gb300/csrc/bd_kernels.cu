@@ -158,7 +158,7 @@ __global__ void BD_ENUM_BOUNDS k_enumerate(EnumParams p) {
     if (u >= units) break;
     const Range r = p.ranges ? p.ranges[u] : Range{u, 1u};
     for (unsigned int i = r.first; i < r.first + r.count; ++i) {
-      const Item it = p.items[i];
+      const PackedItem it = p.items[i];
       W.run_item(it, acc);
       ++done;
     }

@@ -19,7 +19,7 @@ struct EnumParams {
   const int64_t* pts;     // N x K coordinates, row-major (device)
   const int64_t* lifts;   // N explicit lift heights (device) or nullptr: use (lift_seed, attempt)
   uint64_t lift_seed;     // stream seed (see bd_lifts.h)
-  const Item* items;
+  const PackedItem* items;  // the work list (packed prefixes)
   int nitems;
   const Range* ranges;    // work units: ranges of consecutive items, or nullptr: one item each
   int nranges;

@@ -26,7 +26,7 @@ namespace {
 constexpr size_t kPointsOffset = 256;                                  // after the accumulators and counter
 constexpr size_t kItemsOffset = 8192;                                  // after BD_NMAX x BD_KMAX points
 constexpr size_t kItemsMax = BD_NOALLOC_MAX_ITEMS;
-constexpr size_t kScratchBytes = kItemsOffset + kItemsMax * sizeof(bd::Item);
+constexpr size_t kScratchBytes = kItemsOffset + kItemsMax * sizeof(bd::PackedItem);
 static_assert(kPointsOffset >= sizeof(bd::DevAcc) + sizeof(unsigned int), "scratch header");
 static_assert(kPointsOffset + sizeof(int64_t) * BD_NMAX * BD_KMAX <= kItemsOffset, "scratch points");
 static_assert(kScratchBytes == BD_NOALLOC_SCRATCH_BYTES, "scratch size");
@@ -36,7 +36,8 @@ static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 std::mutex g_mu;                     // one call at a time in this process
 void* g_addr[256] = {};              // device address of g_scratch, per device ordinal
-bd::Item g_host_items[kItemsMax];    // host-side staging of the work list (static, no heap)
+bd::Item g_host_items[kItemsMax];          // host-side work list (static, no heap)
+bd::PackedItem g_host_packed[kItemsMax];   // the same, packed as the device reads it
 
 int scratch_address(unsigned char** out) {
   int dev = 0;
@@ -101,10 +102,11 @@ extern "C" int bd_volume_noalloc(const int64_t* points, int32_t npts, int32_t k,
   bd::DevAcc* d_acc = reinterpret_cast<bd::DevAcc*>(base);
   unsigned int* d_counter = reinterpret_cast<unsigned int*>(base + sizeof(bd::DevAcc));
   int64_t* d_pts = reinterpret_cast<int64_t*>(base + kPointsOffset);
-  bd::Item* d_items = reinterpret_cast<bd::Item*>(base + kItemsOffset);
+  bd::PackedItem* d_items = reinterpret_cast<bd::PackedItem*>(base + kItemsOffset);
+  for (size_t i = 0; i < nitems; ++i) g_host_packed[i] = bd::pack_item(g_host_items[i]);
   e = cudaMemcpyAsync(d_pts, points, sizeof(int64_t) * npts * k, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(d_items, g_host_items, sizeof(bd::Item) * nitems, cudaMemcpyHostToDevice, st);
+    e = cudaMemcpyAsync(d_items, g_host_packed, sizeof(bd::PackedItem) * nitems, cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return bd::set_error(BD_ERR_CUDA, cudaGetErrorString(e));
   for (int attempt = 0; attempt < 8; ++attempt) {
     bd::DevAcc acc{};
