@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <thread>
 #include <vector>
 
 #include "../../include/binodeg.h"
@@ -207,17 +208,27 @@ int bd_host_start_solutions(const int64_t* points, const int64_t* lifts, int32_t
   }
   *count = (int64_t)total;
   if (total > (uint64_t)capacity) return bd::set_error(BD_ERR_ARG, "capacity is below the number of solutions (count holds it)");
-  double worst = 0;
-  for (int64_t c = 0; c < nc; ++c) {
-    const uint64_t m = (uint64_t)(cells[c].det < 0 ? -cells[c].det : cells[c].det);
-    for (uint64_t t = 0; t < m; ++t) {
-      double* y = sols + 2ull * k * (first[c] + t);
-      bd::start_solution(cells[c], k, t, y);
-      const double r = bd::start_residual(cells[c], k, y);
-      worst = (r != r) ? 1e300 : (r > worst ? r : worst);
+  // cells dealt round-robin to the host threads, each with its own worst residual
+  const int nt = (int)std::max<int64_t>(1, std::min<int64_t>(nc, std::max(1u, std::thread::hardware_concurrency())));
+  std::vector<double> worst_of(nt, 0.0);
+  auto work = [&](int w) {
+    double worst = 0;
+    for (int64_t c = w; c < nc; c += nt) {
+      const uint64_t m = (uint64_t)(cells[c].det < 0 ? -cells[c].det : cells[c].det);
+      for (uint64_t t = 0; t < m; ++t) {
+        double* y = sols + 2ull * k * (first[c] + t);
+        bd::start_solution(cells[c], k, t, y);
+        const double r = bd::start_residual(cells[c], k, y);
+        worst = (r != r) ? 1e300 : (r > worst ? r : worst);
+      }
     }
-  }
-  if (max_residual) *max_residual = worst;
+    worst_of[w] = worst;
+  };
+  std::vector<std::thread> th;
+  for (int w = 1; w < nt; ++w) th.emplace_back(work, w);
+  work(0);
+  for (auto& t : th) t.join();
+  if (max_residual) *max_residual = *std::max_element(worst_of.begin(), worst_of.end());
   return BD_OK;
 }
 

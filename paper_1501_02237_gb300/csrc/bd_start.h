@@ -57,36 +57,73 @@ BD_HD void start_solution(const StartCell& sc, int k, uint64_t t, double* out) {
   }
 }
 
+// A complex number as (re + i im) * 2^ex, rescaled to max(|re|, |im|) in [0.5, 1) whenever the
+// mantissa drifts far from 1, so that the powers and products below neither overflow nor
+// underflow however far |y| is from 1.
+struct ScaledCx {
+  double re, im;
+  int64_t ex;
+};
+
+BD_HD void rescale(ScaledCx& z) {
+  const double a = fabs(z.re) > fabs(z.im) ? fabs(z.re) : fabs(z.im);
+  if (a == 0 || !(a < INFINITY)) return;
+  int s;
+  frexp(a, &s);
+  z.re = ldexp(z.re, -s);
+  z.im = ldexp(z.im, -s);
+  z.ex += s;
+}
+
+// Mantissas are kept within [2^-400, 2^400], so one product of two of them is still a normal
+// double; only a mantissa that leaves the range is rescaled.
+BD_HD void keep_in_range(ScaledCx& z) {
+  const double m = fabs(z.re) > fabs(z.im) ? fabs(z.re) : fabs(z.im);
+  if (!(m > 0x1p-400 && m < 0x1p+400)) rescale(z);
+}
+
+BD_HD ScaledCx scaled_mul(const ScaledCx& a, const ScaledCx& b) {
+  ScaledCx z{a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re, a.ex + b.ex};
+  keep_in_range(z);
+  return z;
+}
+
 // max over the cell's equations of |y^{E_j} / b_j - 1| for one solution y (k complex numbers)
 BD_HD double start_residual(const StartCell& sc, int k, const double* y) {
+  ScaledCx pos[KMAX], neg[KMAX];  // y_i and 1 / y_i, scaled
+  for (int i = 0; i < k; ++i) {
+    pos[i] = ScaledCx{y[2 * i], y[2 * i + 1], 0};
+    keep_in_range(pos[i]);
+    const double n2 = pos[i].re * pos[i].re + pos[i].im * pos[i].im;  // 1/y = conj(y) / |y|^2
+    neg[i] = ScaledCx{pos[i].re / n2, -pos[i].im / n2, -pos[i].ex};
+    keep_in_range(neg[i]);
+  }
   double worst = 0;
   for (int j = 0; j < k; ++j) {
-    double pr = 1, pi = 0;
+    ScaledCx p{1, 0, 0};
     for (int i = 0; i < k; ++i) {
-      int e = sc.E[j * k + i];
-      double br = y[2 * i], bi = y[2 * i + 1];
-      if (e < 0) {  // y^-1 = conj(y) / |y|^2
-        const double n2 = br * br + bi * bi;
-        br = br / n2;
-        bi = -bi / n2;
-        e = -e;
-      }
+      int64_t e = sc.E[j * k + i];
+      ScaledCx base = e < 0 ? neg[i] : pos[i];
+      e = e < 0 ? -e : e;
       while (e) {  // square and multiply
-        if (e & 1) {
-          const double r = pr * br - pi * bi;
-          pi = pr * bi + pi * br;
-          pr = r;
-        }
-        const double r = br * br - bi * bi;
-        bi = 2 * br * bi;
-        br = r;
+        if (e & 1) p = scaled_mul(p, base);
         e >>= 1;
+        if (e) base = scaled_mul(base, base);
       }
     }
-    // |p / b - 1| = |p - b| / |b|
-    const double dr = pr - sc.b_re[j], di = pi - sc.b_im[j];
-    const double v = sqrt((dr * dr + di * di) / (sc.b_re[j] * sc.b_re[j] + sc.b_im[j] * sc.b_im[j]));
-    worst = v > worst ? v : worst;
+    // |p / b - 1| = |p - b| / |b|, both brought to b's binary exponent
+    ScaledCx b{sc.b_re[j], sc.b_im[j], 0};
+    keep_in_range(b);
+    const int64_t d = p.ex - b.ex;
+    double v;
+    if (d > 2000) {
+      v = INFINITY;
+    } else {
+      const double scale = d == 0 ? 1.0 : (d < -2000 ? 0.0 : ldexp(1.0, (int)d));
+      const double dr = p.re * scale - b.re, di = p.im * scale - b.im;
+      v = sqrt((dr * dr + di * di) / (b.re * b.re + b.im * b.im));
+    }
+    worst = (v > worst || v != v) ? v : worst;  // a NaN stays visible
   }
   return worst;
 }

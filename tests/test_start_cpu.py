@@ -64,3 +64,28 @@ def test_host_start_solutions_larger_cells(seed):
     for (cell, vol, _, _), rc in zip(cells, ref):
         assert same_sets(ys[i:i + vol], rc, tol=1e-9)
         i += vol
+
+
+def test_host_start_residual_far_from_unit_modulus():
+    # n=24, k=8 system, coefficient stream 1: solutions range over |y| from 1e-177 to 1e153, so
+    # the plain square-and-multiply of y^E under- or overflows; the residual check must not
+    from oracle.start import cell_binomial
+    from oracle.volume import det_int
+    from workloads import config_system
+    P = bd.reduce(config_system("single_n24_k8").A)["points"]
+    W = np.array(oracle_lifts(P.shape[0], 0))
+    ys, res = bd.host_start_solutions(P, W, coef_seed=1)
+    mag = np.abs(np.log(np.abs(ys))).max(axis=1)
+    assert mag.max() > 300, "the case no longer exercises extreme magnitudes"
+    assert res < 1e-10
+    # the most extreme solutions, checked in the log domain against the oracle's systems
+    cells = bd.host_cells(P, W, capacity=1 << 14)
+    pts = P.tolist()
+    vols = [abs(det_int([[a - b for a, b in zip(pts[i], pts[c["cell"][-1]])] for i in c["cell"][:-1]]))
+            for c in cells]
+    first = np.cumsum([0] + vols)
+    for t in np.argsort(mag)[-40:]:
+        ci = int(np.searchsorted(first, t, side="right")) - 1
+        E, b = cell_binomial(pts, cells[ci]["cell"], 1)
+        lv = np.log(ys[t]) @ np.array(E).T
+        assert np.max(np.abs(np.exp(lv - np.log(np.array(b, dtype=complex))) - 1)) < 1e-9
