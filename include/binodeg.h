@@ -374,6 +374,55 @@ int bd_start_solutions(const int64_t* points, int32_t npts, int32_t k, uint64_t 
 int bd_host_start_solutions(const int64_t* points, const int64_t* lifts, int32_t npts, int32_t k, uint64_t coef_seed,
                             int64_t capacity, double* sols, int64_t* count, double* max_residual);
 
+/* ---- mixed volume: the BKK generalisation of the degree (Appendix A) ------------------- */
+
+typedef struct {
+  uint64_t mv_lo, mv_hi;  /* MV(conv A_1, .., conv A_k), exact unsigned 128-bit; MV(P, .., P) = NVol(P) */
+  uint64_t cells;         /* fine mixed cells of the final lifting */
+  uint64_t singular;      /* tuples of pairs with det M = 0 */
+  uint64_t ties;          /* tie tuples of the final lifting (0 whenever BD_OK) */
+  uint64_t tuples;        /* prod_i C(|A_i|, 2): tuples of pairs resolved per lifting */
+  int32_t relifts;        /* liftings discarded because of ties */
+  int32_t flags;          /* BD_FLAG_INT128, BD_FLAG_DEGENERATE (a component without two distinct
+                             points: MV = 0, nothing launched) */
+  int32_t bound_bits;     /* ceil(log2) of the Hadamard bound that chose the integer path */
+  int32_t reserved;
+  double device_ms;       /* the final lifting's enumeration kernel, CUDA events on the library's
+                             stream; 0 for the host emulation */
+} bd_mixed_out;
+
+/*
+ * Mixed volume of k lattice point sets in Z^k (Bernstein's count of the isolated C*-solutions
+ * of a generic system with these supports), by enumerating the fine mixed cells of a random
+ * lifting on the GPU: every tuple of one pair {p_i, q_i} per set with M = [a_{q_i} - a_{p_i}]
+ * nonsingular, whose inner normal puts every other point of every set strictly above its
+ * pair; MV = sum |det M| over them.
+ *   points : the sets back to back, sum(counts) x k integers (row = point), |x| < 2^40
+ *   counts : k set sizes, each >= 1, sum <= BD_NMAX; 1 <= k <= BD_KMAX
+ *   seed   : lift seed (heights as bd_volume's for the flat point list); ties are re-lifted
+ *            (up to 8 liftings, then BD_ERR_TIES).  The result does not depend on it.
+ * Errors: BD_ERR_ARG (sizes, limits, more than 2^62 tuples, walk state above shared memory),
+ * BD_ERR_OVERFLOW (exact minors beyond 128 bits), BD_ERR_TIES, BD_ERR_CUDA, BD_ERR_NOMEM.
+ */
+int bd_mixed_volume(const int64_t* points, const int32_t* counts, int32_t k, uint64_t seed, bd_mixed_out* out);
+
+/* As bd_mixed_volume with caller-given heights (sum(counts) values, |lift| < 2^40) and no
+ * re-lift (a tie returns BD_ERR_TIES), optionally listing the fine mixed cells:
+ *   cells    : NULL, or capacity x 2k indices: cell c, set i -> (p, q), p < q, local indices
+ *              into set i, at cells[c * 2k + 2i]; cells in lexicographic order of these rows
+ *   absdet   : NULL, or capacity values |det M| (-1 when above 63 bits)
+ *   capacity : cells the buffers hold; fewer than out->cells -> BD_ERR_ARG (out->cells counts)
+ *   force_int128 : nonzero takes the 128-bit path even when 64 bits suffice. */
+int bd_mixed_volume_lifted(const int64_t* points, const int32_t* counts, int32_t k, const int64_t* lifts,
+                           int32_t force_int128, bd_mixed_out* out, int32_t* cells, int64_t capacity,
+                           int64_t* absdet);
+/* The same walker on CPU threads (team_width 1: one lane per thread, items taken in turn) or as
+ * one lockstep team of team_width lanes run as threads (1..32), for CPU tests.  prefix_levels > 0
+ * fixes that many levels per work item (at most k-1; 0: the library's choice). */
+int bd_host_mixed_volume_lifted(const int64_t* points, const int32_t* counts, int32_t k, const int64_t* lifts,
+                                int32_t team_width, int32_t force_int128, int32_t prefix_levels, bd_mixed_out* out,
+                                int32_t* cells, int64_t capacity, int64_t* absdet);
+
 #ifdef __cplusplus
 }
 #endif

@@ -21,6 +21,12 @@ Contents (all arithmetic is exact: Python integers and `fractions.Fraction`):
 * `lifts`      -- the counter-based lift generator (splitmix64, Steele-Lea-Flood 2014)
                   implemented from its published definition.
 * `degree`     -- degree = |prod d_j| * NVol_d(conv{0, columns of P_0}) (Props. 1, 4).
+* `cells`, `start` -- the cells of the lifting's triangulation with their inner normals
+                  and the start solutions of every cell's binomial system (Sec. 6).
+* `mixed`      -- the mixed volume of k point sets (the BKK bound that Appendix A names
+                  as the general case of the degree): by the polarization formula over
+                  Minkowski sums, and by the fine mixed cells of a lifting in rationals.
+* `mlp`        -- the cost model's forward and backward passes in float64.
 
 Parity status: every function here is pinned by tests against closed forms, the
 paper's worked example and its master-space degree table; see tests/test_oracle_*.py.

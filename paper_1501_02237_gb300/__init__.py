@@ -13,13 +13,13 @@ from typing import Optional, Sequence
 import numpy as np
 
 from ._lib import (BD_FEATURES, BD_MLP_PARAMS, BD_FLAG_DEGENERATE, BD_FLAG_INCONSISTENT, BD_FLAG_INT128, KMAX,  # noqa: F401
-                   NMAX, BatchOpts, BatchStats, BinodegError, DegreeOut, HostOpts, PlanOpts, ServerOpts, ServerStats, VolumeOut,
-                   check, i64, lib, ptr)
+                   NMAX, BatchOpts, BatchStats, BinodegError, DegreeOut, HostOpts, MixedOut, PlanOpts, ServerOpts,
+                   ServerStats, VolumeOut, check, i64, lib, ptr)
 from ._lib import F32P, I32P, U8P
 
 __all__ = ["CostModel", "Server", "degree", "volume", "volume_noalloc", "volume_lifted", "classify", "reduce", "Plan", "Batch", "set_stream",
-           "host_volume_lifted", "cells", "host_cells", "start_solutions", "host_start_solutions", "BinodegError",
-           "lib"]
+           "host_volume_lifted", "cells", "host_cells", "start_solutions", "host_start_solutions", "mixed_volume",
+           "mixed_volume_lifted", "host_mixed_volume_lifted", "BinodegError", "lib"]
 
 
 def set_stream(stream) -> None:
@@ -205,6 +205,66 @@ def host_volume_lifted(points, lifts, threads: int = 1, force_int128: bool = Fal
     if rc not in (0, 3):
         check(rc)
     return res
+
+
+def _supports(supports):
+    """Point sets -> (flat points, counts, k)."""
+    sets = [i64(A).reshape(len(A), -1) for A in supports]
+    k = len(sets)
+    if any(A.shape[1] != k for A in sets):
+        raise ValueError("k point sets in Z^k")
+    return i64(np.concatenate(sets, axis=0)), np.array([len(A) for A in sets], dtype=np.int32), k
+
+
+def mixed_volume(supports, seed: int = 0) -> dict:
+    """bd_mixed_volume: MV(conv A_1, .., conv A_k) of k point sets in Z^k on the GPU (the BKK
+    bound; MV(P, .., P) = NVol(P))."""
+    P, cnt, k = _supports(supports)
+    out = MixedOut()
+    check(lib().bd_mixed_volume(ptr(P), cnt.ctypes.data_as(I32P), k, C.c_uint64(seed), C.byref(out)))
+    return out.as_dict()
+
+
+def _mixed_lifted(fn, supports, lifts, with_cells, capacity):
+    P, cnt, k = _supports(supports)
+    W = i64(lifts)
+    out = MixedOut()
+    while True:
+        cap = capacity if with_cells else 0
+        cells = np.zeros((max(cap, 1), 2 * k), dtype=np.int32)
+        dets = np.zeros(max(cap, 1), dtype=np.int64)
+        rc = fn(ptr(P), cnt.ctypes.data_as(I32P), k, ptr(W), out, cells.ctypes.data_as(I32P) if with_cells else None,
+                cap, ptr(dets) if with_cells else None)
+        if with_cells and rc == 1 and out.cells > cap:
+            capacity = int(out.cells)
+            continue
+        break
+    res = out.as_dict()
+    res["status"] = rc
+    if rc not in (0, 3):
+        check(rc)
+    if with_cells and rc == 0:
+        n = int(out.cells)
+        res["cell_list"] = [tuple((int(c[2 * i]), int(c[2 * i + 1])) for i in range(k)) for c in cells[:n]]
+        res["absdet"] = [int(d) for d in dets[:n]]
+    return res
+
+
+def mixed_volume_lifted(supports, lifts, cells: bool = False, force_int128: bool = False, capacity: int = 4096) -> dict:
+    """bd_mixed_volume_lifted: the same on the GPU with the given flat heights and no re-lift
+    (status 3 on a tie); cells=True also lists the fine mixed cells in "cell_list" (pairs of
+    local indices per set, lexicographic) with their |det M| in "absdet"."""
+    f = lambda *a: lib().bd_mixed_volume_lifted(a[0], a[1], a[2], a[3], int(force_int128), C.byref(a[4]), *a[5:])
+    return _mixed_lifted(f, supports, lifts, cells, capacity)
+
+
+def host_mixed_volume_lifted(supports, lifts, team_width: int = 1, cells: bool = False, force_int128: bool = False,
+                             capacity: int = 4096, prefix_levels: int = 0) -> dict:
+    """bd_host_mixed_volume_lifted: the mixed-cell walker on CPU threads (CPU tests);
+    prefix_levels > 0 fixes that many levels per work item."""
+    f = lambda *a: lib().bd_host_mixed_volume_lifted(a[0], a[1], a[2], a[3], team_width, int(force_int128),
+                                                     prefix_levels, C.byref(a[4]), *a[5:])
+    return _mixed_lifted(f, supports, lifts, cells, capacity)
 
 
 class Plan:

@@ -40,6 +40,18 @@ class VolumeOut(C.Structure):
                     max_abs_coord=int(self.max_abs_coord), bound_bits=int(self.bound_bits))
 
 
+class MixedOut(C.Structure):
+    _fields_ = [("mv_lo", C.c_uint64), ("mv_hi", C.c_uint64), ("cells", C.c_uint64), ("singular", C.c_uint64),
+                ("ties", C.c_uint64), ("tuples", C.c_uint64), ("relifts", C.c_int32), ("flags", C.c_int32),
+                ("bound_bits", C.c_int32), ("reserved", C.c_int32), ("device_ms", C.c_double)]
+
+    def as_dict(self):
+        return dict(mv=(int(self.mv_hi) << 64) | int(self.mv_lo), cells=int(self.cells),
+                    singular=int(self.singular), ties=int(self.ties), tuples=int(self.tuples),
+                    relifts=int(self.relifts), flags=int(self.flags), bound_bits=int(self.bound_bits),
+                    device_ms=float(self.device_ms))
+
+
 class DegreeOut(C.Structure):
     _fields_ = [("degree_lo", C.c_uint64), ("degree_hi", C.c_uint64), ("nvol_lo", C.c_uint64),
                 ("nvol_hi", C.c_uint64), ("torsion", C.c_uint64), ("rank", C.c_int32), ("dim", C.c_int32),
@@ -127,6 +139,11 @@ SIGNATURES = {
     "bd_host_start_solutions": (C.c_int, [I64P, I64P, C.c_int32, C.c_int32, C.c_uint64, C.c_int64, C.c_void_p,
                                           C.POINTER(C.c_int64), C.POINTER(C.c_double)]),
     "bd_volume_noalloc": (C.c_int, [I64P, C.c_int32, C.c_int32, C.c_uint64, C.POINTER(VolumeOut)]),
+    "bd_mixed_volume": (C.c_int, [I64P, I32P, C.c_int32, C.c_uint64, C.POINTER(MixedOut)]),
+    "bd_mixed_volume_lifted": (C.c_int, [I64P, I32P, C.c_int32, I64P, C.c_int32, C.POINTER(MixedOut), I32P,
+                                         C.c_int64, I64P]),
+    "bd_host_mixed_volume_lifted": (C.c_int, [I64P, I32P, C.c_int32, I64P, C.c_int32, C.c_int32, C.c_int32,
+                                              C.POINTER(MixedOut), I32P, C.c_int64, I64P]),
     "bd_batch_create": (C.c_int, [C.POINTER(C.c_void_p)]),
     "bd_batch_add": (C.c_int, [C.c_void_p, I64P, C.c_int32, C.c_int32, I64P, C.c_uint64, I32P]),
     "bd_batch_add_points": (C.c_int, [C.c_void_p, I64P, C.c_int32, C.c_int32, C.c_uint64, I32P]),

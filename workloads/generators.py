@@ -192,6 +192,37 @@ def random_points(npts: int, k: int, seed: int, lo: int = -3, hi: int = 3) -> np
     return rng.integers(lo, hi + 1, size=(npts, k), dtype=np.int64)
 
 
+def sparse_supports(k: int, points_per_set: int, seed: int, max_nonzeros: int = 3) -> List[np.ndarray]:
+    """k supports in Z^k for a mixed volume (the BKK bound of a sparse polynomial system):
+    each set holds the origin (a constant term) and points_per_set - 1 distinct exponent
+    vectors with 1..max_nonzeros entries in {1, 2} at random positions."""
+    rng = np.random.default_rng(seed)
+    sets = []
+    for _ in range(k):
+        pts = {tuple([0] * k)}
+        while len(pts) < points_per_set:
+            v = np.zeros(k, dtype=np.int64)
+            nz = rng.choice(k, size=int(rng.integers(1, max_nonzeros + 1)), replace=False)
+            v[nz] = rng.integers(1, 3, size=len(nz))
+            pts.add(tuple(int(x) for x in v))
+        sets.append(np.array(sorted(pts), dtype=np.int64))
+    return sets
+
+
+# mixed-volume workloads: (k, points per set, seed)
+MIXED_CONFIGS: Dict[str, Tuple[int, int, int]] = {
+    "mixed_k3_p5": (3, 5, 0),    # 1,000 tuples of pairs: the oracle's size
+    "mixed_k5_p6": (5, 6, 0),    # 759,375 tuples
+    "mixed_k6_p7": (6, 7, 0),    # 85,766,121 tuples
+    "mixed_k7_p8": (7, 8, 0),    # 13,492,928,512 tuples: the benchmark's mixed workload
+}
+
+
+def mixed_config(name: str) -> List[np.ndarray]:
+    k, p, seed = MIXED_CONFIGS[name]
+    return sparse_supports(k, p, seed)
+
+
 def poisson_arrivals(rate_per_s: float, count: int, seed: int) -> np.ndarray:
     """Arrival times (s) of a Poisson stream: cumulative exponential gaps."""
     rng = np.random.default_rng(seed)
