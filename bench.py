@@ -224,6 +224,47 @@ def start_section(bd, P, seed=0, coef_seed=1):
                 note="all start solutions of the workload's cells, on the device")
 
 
+MIXED_WORKLOAD = "mixed_k7_p8"
+
+
+def mixed_section(bd, name=MIXED_WORKLOAD, seed=0, runs=3, cpu_seconds=5.0):
+    """Mixed volume (the BKK bound, Appendix A) of the sparse supports `name` (k = 7 sets of 8
+    exponent vectors in {0,1,2}^7: 28^7 = 1.35e10 tuples of pairs): tuples of pairs resolved per
+    second by the enumeration kernel (CUDA events) and per public call, against the oracle's
+    rational test of single tuples on one host core (a bounded random sample)."""
+    import random
+
+    from oracle.lifts import lifts as oracle_lifts
+    from oracle.mixed import cell_status
+    from workloads import mixed_config
+
+    S = mixed_config(name)
+    bd.mixed_volume(S, seed=seed)  # warm-up
+    dev, wall = [], []
+    r = None
+    for _ in range(runs):
+        t0 = time.perf_counter()
+        r = bd.mixed_volume(S, seed=seed)
+        wall.append(time.perf_counter() - t0)
+        dev.append(r["device_ms"])
+    d, w = statistics.median(dev), statistics.median(wall)
+    # the oracle on a sample of random tuples
+    SL = [A.tolist() for A in S]
+    W = oracle_lifts(sum(len(A) for A in SL), seed)
+    pairs = [[(p, q) for p in range(len(A)) for q in range(p + 1, len(A))] for A in SL]
+    rng = random.Random(1)
+    done, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < cpu_seconds:
+        cell_status(SL, W, tuple(rng.choice(P) for P in pairs))
+        done += 1
+    cpu_rate = done / (time.perf_counter() - t0)
+    return dict(workload=name, k=len(S), points_per_set=len(S[0]), tuples=r["tuples"], mv=r["mv"], cells=r["cells"],
+                int_path="int128" if r["flags"] & bd.BD_FLAG_INT128 else "int64", kernel_ms=d,
+                tuples_per_s=r["tuples"] / (d / 1e3), call_ms=1e3 * w, call_tuples_per_s=r["tuples"] / w,
+                cpu_baseline=dict(value=cpu_rate, unit="tuples/s", cores=1, kind="oracle",
+                                  sample=f"{done} random tuples through oracle.mixed.cell_status ({cpu_seconds:.0f} s)"))
+
+
 def serve_section(bd, rate=200.0, count=1000, train_count=20000):
     """Cost model trained on method-generated runs, then a Poisson stream served with continuous
     batching (n ~ U[12,30], k ~ U[4,10]); p50/p99 latency and degrees/s per admission policy."""
@@ -443,6 +484,7 @@ def main():
         line["batch"] = batch_section(bd)
         line["serve"] = serve_section(bd)
         line["start_solutions"] = start_section(bd, P, seed=seed)
+        line["mixed_volume"] = mixed_section(bd, seed=seed)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(s, subsets)
     if rank == 0:

@@ -418,10 +418,12 @@ int bd_mixed_volume_lifted(const int64_t* points, const int32_t* counts, int32_t
                            int64_t* absdet);
 /* The same walker on CPU threads (team_width 1: one lane per thread, items taken in turn) or as
  * one lockstep team of team_width lanes run as threads (1..32), for CPU tests.  prefix_levels > 0
- * fixes that many levels per work item (at most k-1; 0: the library's choice). */
+ * fixes that many levels per work item (at most k-1, k-2 with the 3-D leaf stage; 0: the
+ * library's choice); leaf3 1 / 0 forces the 3-D leaf stage on / off where the 64-bit path and
+ * k >= 3 allow it (-1: the library's choice). */
 int bd_host_mixed_volume_lifted(const int64_t* points, const int32_t* counts, int32_t k, const int64_t* lifts,
-                                int32_t team_width, int32_t force_int128, int32_t prefix_levels, bd_mixed_out* out,
-                                int32_t* cells, int64_t capacity, int64_t* absdet);
+                                int32_t team_width, int32_t force_int128, int32_t prefix_levels, int32_t leaf3,
+                                bd_mixed_out* out, int32_t* cells, int64_t capacity, int64_t* absdet);
 
 #ifdef __cplusplus
 }

@@ -259,11 +259,12 @@ def mixed_volume_lifted(supports, lifts, cells: bool = False, force_int128: bool
 
 
 def host_mixed_volume_lifted(supports, lifts, team_width: int = 1, cells: bool = False, force_int128: bool = False,
-                             capacity: int = 4096, prefix_levels: int = 0) -> dict:
+                             capacity: int = 4096, prefix_levels: int = 0, leaf3: int = -1) -> dict:
     """bd_host_mixed_volume_lifted: the mixed-cell walker on CPU threads (CPU tests);
-    prefix_levels > 0 fixes that many levels per work item."""
+    prefix_levels > 0 fixes that many levels per work item; leaf3 1/0 forces the 3-D leaf
+    stage on/off (-1: the library's choice)."""
     f = lambda *a: lib().bd_host_mixed_volume_lifted(a[0], a[1], a[2], a[3], team_width, int(force_int128),
-                                                     prefix_levels, C.byref(a[4]), *a[5:])
+                                                     prefix_levels, leaf3, C.byref(a[4]), *a[5:])
     return _mixed_lifted(f, supports, lifts, cells, capacity)
 
 

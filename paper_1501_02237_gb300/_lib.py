@@ -143,7 +143,7 @@ SIGNATURES = {
     "bd_mixed_volume_lifted": (C.c_int, [I64P, I32P, C.c_int32, I64P, C.c_int32, C.POINTER(MixedOut), I32P,
                                          C.c_int64, I64P]),
     "bd_host_mixed_volume_lifted": (C.c_int, [I64P, I32P, C.c_int32, I64P, C.c_int32, C.c_int32, C.c_int32,
-                                              C.POINTER(MixedOut), I32P, C.c_int64, I64P]),
+                                              C.c_int32, C.POINTER(MixedOut), I32P, C.c_int64, I64P]),
     "bd_batch_create": (C.c_int, [C.POINTER(C.c_void_p)]),
     "bd_batch_add": (C.c_int, [C.c_void_p, I64P, C.c_int32, C.c_int32, I64P, C.c_uint64, I32P]),
     "bd_batch_add_points": (C.c_int, [C.c_void_p, I64P, C.c_int32, C.c_int32, C.c_uint64, I32P]),

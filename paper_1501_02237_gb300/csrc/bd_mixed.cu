@@ -28,6 +28,7 @@ struct MixedWarp {
   __device__ int lane() const { return threadIdx.x & 31; }
   __device__ int lanes() const { return 32; }
   __device__ void sync() const { __syncwarp(); }
+  __device__ uint32_t max_u32(uint32_t x) const { return __reduce_max_sync(0xffffffffu, x); }
 };
 
 // One problem ready for a launch: rows in level order, relative to each component's first
@@ -38,6 +39,7 @@ struct MixedPrep {
   std::vector<int> orig_first;   // caller's component c starts at orig_first[c] in the flat input
   std::vector<int> level_point;  // global point index (level order) -> flat input index
   std::vector<uint16_t> last_pairs;
+  std::vector<uint16_t> prev_pairs;  // component K-2's pairs (the 3-D leaf stage)
   int path = 0;                  // 0: int64, 1: int128
   double bound_bits = 0;
   bool zero = false;             // some component has fewer than two distinct points
@@ -46,7 +48,7 @@ struct MixedPrep {
 uint64_t choose2(uint64_t n) { return n * (n - 1) / 2; }
 
 int prepare(const int64_t* pts, const int32_t* counts, int k, bool force128, double lift_span, int prefix_levels,
-            MixedPrep& mp) {
+            int leaf3, MixedPrep& mp) {
   if (!pts || !counts) return bd::set_error(BD_ERR_ARG, "NULL argument");
   if (k < 1 || k > BD_KMAX) return bd::set_error(BD_ERR_ARG, "need 1 <= k <= BD_KMAX");
   int n = 0;
@@ -116,16 +118,25 @@ int prepare(const int64_t* pts, const int32_t* counts, int k, bool force128, dou
   mp.bound_bits = 2 + lgc + lgw;
   mp.path = (force128 || mp.bound_bits >= 62.99) ? 1 : 0;
   if (mp.bound_bits >= 126.99) return bd::set_error(BD_ERR_OVERFLOW, "the exact minors may leave 128 bits");
+  // the 3-D leaf stage (64-bit path) when the nodes above it are enough to spread the work
+  double nodes3 = 1;
+  for (int j = 0; j + 2 < k; ++j) nodes3 *= s.npairs[j];
+  s.leaf3 = (mp.path == 0 && k >= 3 && (leaf3 > 0 || (leaf3 < 0 && nodes3 >= 1024))) ? 1 : 0;
   // items: fix levels until there are enough subtrees to spread over the GPU
+  const int deepest = s.leaf3 ? k - 2 : k - 1;
   s.prefix = 0;
   s.items = 1;
-  const int want = prefix_levels > 0 ? std::min(prefix_levels, k - 1) : k - 1;
+  const int want = prefix_levels > 0 ? std::min(prefix_levels, deepest) : deepest;
   while (s.prefix < want && (prefix_levels > 0 || s.items < (1u << 17))) s.items *= s.npairs[s.prefix++];
-  const int last = k - 1, nl = s.first[last + 1] - s.first[last];
-  mp.last_pairs.clear();
-  for (int p = 0; p < nl; ++p)
-    for (int q = p + 1; q < nl; ++q)
-      mp.last_pairs.push_back((uint16_t)((s.first[last] + p) | ((s.first[last] + q) << 8)));
+  auto pairs_of = [&](int j, std::vector<uint16_t>& out) {
+    out.clear();
+    const int n = s.first[j + 1] - s.first[j];
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) out.push_back((uint16_t)((s.first[j] + p) | ((s.first[j] + q) << 8)));
+  };
+  pairs_of(k - 1, mp.last_pairs);
+  if (k >= 2) pairs_of(k - 2, mp.prev_pairs);
+  else mp.prev_pairs.clear();
   return BD_OK;
 }
 
@@ -148,8 +159,9 @@ size_t smem_bytes(const MixedPrep& mp, int elem) {
   size_t b = (size_t)(K + 1) * N * elem;                                  // rows
   b += sizeof(bd::MixedShape);
   b += (mp.last_pairs.size() * sizeof(uint16_t) + 15) / 16 * 16;          // last level's pairs
+  b += (mp.prev_pairs.size() * sizeof(uint16_t) + 15) / 16 * 16;          // level K-2's pairs
   b = (b + 15) / 16 * 16;
-  const size_t per_warp = sizeof(bd::MixedUniform<i128>) + (size_t)bd::mixed_stack_entries(K) * N * elem;
+  const size_t per_warp = sizeof(bd::MixedUniform<i128>) + 16 * (size_t)N + (size_t)bd::mixed_stack_entries(K) * N * elem;
   return b + kMixedWarps * ((per_warp + 15) / 16 * 16);
 }
 
@@ -159,7 +171,8 @@ struct MixedDevAcc {
 
 template <class T>
 __global__ void __launch_bounds__(32 * kMixedWarps) k_mixed(const T* rows, bd::MixedShape shape,
-                                                            const uint16_t* last_pairs, unsigned long long* next,
+                                                            const uint16_t* last_pairs, const uint16_t* prev_pairs,
+                                                            unsigned long long* next,
                                                             unsigned long long chunk, bd::MixedSink sink,
                                                             MixedDevAcc* out) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -169,22 +182,26 @@ __global__ void __launch_bounds__(32 * kMixedWarps) k_mixed(const T* rows, bd::M
   bd::MixedShape* sh = reinterpret_cast<bd::MixedShape*>(smem + at);
   at += sizeof(bd::MixedShape);
   uint16_t* lp = reinterpret_cast<uint16_t*>(smem + at);
-  const uint32_t npl = shape.npairs[K - 1];
+  const uint32_t npl = shape.npairs[K - 1], npp = K >= 2 ? shape.npairs[K - 2] : 0;
   at += ((size_t)npl * sizeof(uint16_t) + 15) / 16 * 16;
+  uint16_t* pp = reinterpret_cast<uint16_t*>(smem + at);
+  at += ((size_t)npp * sizeof(uint16_t) + 15) / 16 * 16;
   at = (at + 15) / 16 * 16;
-  const size_t per_warp =
-      ((sizeof(bd::MixedUniform<i128>) + (size_t)bd::mixed_stack_entries(K) * N * sizeof(T)) + 15) / 16 * 16;
+  const size_t stack_bytes = (size_t)bd::mixed_stack_entries(K) * N * sizeof(T);
+  const size_t per_warp = ((sizeof(bd::MixedUniform<i128>) + 16 * (size_t)N + stack_bytes) + 15) / 16 * 16;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   unsigned char* wbase = smem + at + warp * per_warp;
   auto* uni = reinterpret_cast<bd::MixedUniform<T>*>(wbase);
-  T* stack = reinterpret_cast<T*>(wbase + sizeof(bd::MixedUniform<i128>));
+  float* fl = reinterpret_cast<float*>(wbase + sizeof(bd::MixedUniform<i128>));  // 16-byte aligned
+  T* stack = reinterpret_cast<T*>(wbase + sizeof(bd::MixedUniform<i128>) + 16 * (size_t)N);
   for (int i = threadIdx.x; i < (K + 1) * N; i += blockDim.x) P[i] = rows[i];
   for (uint32_t i = threadIdx.x; i < npl; i += blockDim.x) lp[i] = last_pairs[i];
+  for (uint32_t i = threadIdx.x; i < npp; i += blockDim.x) pp[i] = prev_pairs[i];
   if (threadIdx.x == 0) *sh = shape;
   __syncthreads();
 
   MixedWarp tm;
-  bd::MixedWalker<T, MixedWarp> W(tm, P, sh, stack, uni, lp);
+  bd::MixedWalker<T, MixedWarp> W(tm, P, sh, stack, fl, uni, lp, pp);
   W.sink = sink;
   bd::MixedAcc acc{};
   for (;;) {
@@ -247,6 +264,7 @@ int device_run(const MixedPrep& mp, const std::vector<T>& rows, uint64_t cap, Ru
   const unsigned long long chunk = std::max<unsigned long long>(1, items / (warps * 8));
   T* d_rows = nullptr;
   uint16_t* d_lp = nullptr;
+  uint16_t* d_pp = nullptr;
   unsigned long long* d_next = nullptr;
   MixedDevAcc* d_acc = nullptr;
   bd::MixedCellRec* d_recs = nullptr;
@@ -254,6 +272,7 @@ int device_run(const MixedPrep& mp, const std::vector<T>& rows, uint64_t cap, Ru
   auto release = [&]() {
     cudaFree(d_rows);
     cudaFree(d_lp);
+    cudaFree(d_pp);
     cudaFree(d_next);
     cudaFree(d_acc);
     cudaFree(d_recs);
@@ -262,6 +281,7 @@ int device_run(const MixedPrep& mp, const std::vector<T>& rows, uint64_t cap, Ru
   };
   e = cudaMalloc(&d_rows, sizeof(T) * rows.size());
   if (e == cudaSuccess) e = cudaMalloc(&d_lp, sizeof(uint16_t) * std::max<size_t>(mp.last_pairs.size(), 1));
+  if (e == cudaSuccess) e = cudaMalloc(&d_pp, sizeof(uint16_t) * std::max<size_t>(mp.prev_pairs.size(), 1));
   if (e == cudaSuccess) e = cudaMalloc(&d_next, sizeof(unsigned long long) * 2);
   if (e == cudaSuccess) e = cudaMalloc(&d_acc, sizeof(MixedDevAcc));
   if (e == cudaSuccess && cap) e = cudaMalloc(&d_recs, sizeof(bd::MixedCellRec) * cap);
@@ -270,12 +290,15 @@ int device_run(const MixedPrep& mp, const std::vector<T>& rows, uint64_t cap, Ru
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_rows, rows.data(), sizeof(T) * rows.size(), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && !mp.last_pairs.empty())
     e = cudaMemcpyAsync(d_lp, mp.last_pairs.data(), sizeof(uint16_t) * mp.last_pairs.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && !mp.prev_pairs.empty())
+    e = cudaMemcpyAsync(d_pp, mp.prev_pairs.data(), sizeof(uint16_t) * mp.prev_pairs.size(), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(d_next, 0, sizeof(unsigned long long) * 2, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(d_acc, 0, sizeof(MixedDevAcc), st);
   if (e == cudaSuccess) e = cudaEventRecord(e0, st);
   if (e == cudaSuccess) {
     bd::MixedSink sink{d_recs, d_next + 1, cap};
-    k_mixed<T><<<(unsigned int)blocks, 32 * kMixedWarps, smem, st>>>(d_rows, mp.shape, d_lp, d_next, chunk, sink, d_acc);
+    k_mixed<T><<<(unsigned int)blocks, 32 * kMixedWarps, smem, st>>>(d_rows, mp.shape, d_lp, d_pp, d_next, chunk, sink,
+                                                                       d_acc);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaEventRecord(e1, st);
@@ -314,13 +337,15 @@ int host_run(const MixedPrep& mp, const std::vector<T>& rows, uint64_t cap, int 
   if (width > 1) {
     bd::LockstepShared shl(width);
     std::vector<T> stack(entries);
+    std::vector<float> fl(4 * (size_t)N);
     bd::MixedUniform<T> uni{};
     part.assign(width, bd::MixedAcc{});
     std::vector<std::thread> th;
     for (int l = 0; l < width; ++l)
       th.emplace_back([&, l] {
         bd::LockstepTeam tm{&shl, l};
-        bd::MixedWalker<T, bd::LockstepTeam> W(tm, rows.data(), &mp.shape, stack.data(), &uni, mp.last_pairs.data());
+        bd::MixedWalker<T, bd::LockstepTeam> W(tm, rows.data(), &mp.shape, stack.data(), fl.data(), &uni,
+                                               mp.last_pairs.data(), mp.prev_pairs.data());
         W.sink = sink;
         for (uint64_t it = 0; it < mp.shape.items; ++it) W.run_item(it, part[l]);
       });
@@ -331,9 +356,11 @@ int host_run(const MixedPrep& mp, const std::vector<T>& rows, uint64_t cap, int 
     std::atomic<uint64_t> next(0);
     auto work = [&](int w) {
       std::vector<T> stack(entries);
+      std::vector<float> fl(4 * (size_t)N);
       bd::MixedUniform<T> uni{};
       bd::HostTeam tm;
-      bd::MixedWalker<T, bd::HostTeam> W(tm, rows.data(), &mp.shape, stack.data(), &uni, mp.last_pairs.data());
+      bd::MixedWalker<T, bd::HostTeam> W(tm, rows.data(), &mp.shape, stack.data(), fl.data(), &uni,
+                                         mp.last_pairs.data(), mp.prev_pairs.data());
       W.sink = sink;
       for (;;) {
         const uint64_t it = next.fetch_add(1);
@@ -403,8 +430,8 @@ int write_cells(const MixedPrep& mp, const RunResult& rr, int k, int32_t* cells,
 }
 
 int mixed_common(const int64_t* pts, const int32_t* counts, int32_t k, const int64_t* given_lifts, uint64_t seed,
-                 int host_width, int force128, int prefix_levels, bd_mixed_out* out, int32_t* cells, int64_t capacity,
-                 int64_t* absdet) {
+                 int host_width, int force128, int prefix_levels, int leaf3, bd_mixed_out* out, int32_t* cells,
+                 int64_t capacity, int64_t* absdet) {
   if (!out) return bd::set_error(BD_ERR_ARG, "NULL argument");
   std::memset(out, 0, sizeof(*out));
   if (cells && capacity < 0) return bd::set_error(BD_ERR_ARG, "negative capacity");
@@ -421,7 +448,7 @@ int mixed_common(const int64_t* pts, const int32_t* counts, int32_t k, const int
     }
   }
   MixedPrep mp;
-  int rc = prepare(pts, counts, k, force128 != 0, span, prefix_levels, mp);
+  int rc = prepare(pts, counts, k, force128 != 0, span, prefix_levels, leaf3, mp);
   if (rc) return rc;
   if (mp.zero) {
     out->tuples = mp.shape.below[0];
@@ -460,24 +487,24 @@ int mixed_common(const int64_t* pts, const int32_t* counts, int32_t k, const int
 extern "C" {
 
 int bd_mixed_volume(const int64_t* points, const int32_t* counts, int32_t k, uint64_t seed, bd_mixed_out* out) {
-  return mixed_common(points, counts, k, nullptr, seed, 0, 0, 0, out, nullptr, 0, nullptr);
+  return mixed_common(points, counts, k, nullptr, seed, 0, 0, 0, -1, out, nullptr, 0, nullptr);
 }
 
 int bd_mixed_volume_lifted(const int64_t* points, const int32_t* counts, int32_t k, const int64_t* lifts,
                            int32_t force_int128, bd_mixed_out* out, int32_t* cells, int64_t capacity,
                            int64_t* absdet) {
   if (!lifts) return bd::set_error(BD_ERR_ARG, "NULL argument");
-  return mixed_common(points, counts, k, lifts, 0, 0, force_int128, 0, out, cells, capacity, absdet);
+  return mixed_common(points, counts, k, lifts, 0, 0, force_int128, 0, -1, out, cells, capacity, absdet);
 }
 
 int bd_host_mixed_volume_lifted(const int64_t* points, const int32_t* counts, int32_t k, const int64_t* lifts,
-                                int32_t team_width, int32_t force_int128, int32_t prefix_levels, bd_mixed_out* out,
-                                int32_t* cells, int64_t capacity, int64_t* absdet) {
+                                int32_t team_width, int32_t force_int128, int32_t prefix_levels, int32_t leaf3,
+                                bd_mixed_out* out, int32_t* cells, int64_t capacity, int64_t* absdet) {
   if (!lifts) return bd::set_error(BD_ERR_ARG, "NULL argument");
   if (team_width < 1 || team_width > 32) return bd::set_error(BD_ERR_ARG, "team width must be 1..32");
   if (prefix_levels < 0) return bd::set_error(BD_ERR_ARG, "negative prefix_levels");
-  return mixed_common(points, counts, k, lifts, 0, team_width, force_int128, prefix_levels, out, cells, capacity,
-                      absdet);
+  return mixed_common(points, counts, k, lifts, 0, team_width, force_int128, prefix_levels, leaf3 < 0 ? -1 : leaf3,
+                      out, cells, capacity, absdet);
 }
 
 }  // extern "C"

@@ -30,7 +30,8 @@
 //
 // Parallel layout: a warp owns one subtree at a time; its lanes own points round-robin for
 // the state updates, and the pairs of the last component are dealt to lanes, each lane
-// scanning the points with early exit.
+// scanning the points with early exit, in single precision with a rigorous error bound and an
+// exact fallback (see leaves()).
 #pragma once
 
 #include "bd_core.cuh"
@@ -43,7 +44,8 @@ struct MixedShape {
   int first[KMAX + 1];       // component j owns points first[j] .. first[j+1]-1
   uint32_t npairs[KMAX];     // C(|A_j|, 2)
   uint64_t below[KMAX + 1];  // tuples under one node of level j: prod_{i >= j} npairs[i]
-  int prefix;                // levels fixed by a work item (0 <= prefix <= K-1)
+  int prefix;                // levels fixed by a work item (0 <= prefix <= K-1; <= K-2 with leaf3)
+  int leaf3;                 // 1: the last two levels are tested together from level K-2
   uint64_t items;            // prod_{j < prefix} npairs[j]
 };
 
@@ -99,7 +101,27 @@ struct Pairs14 {
 // per-warp values every lane needs after a level is built (written by lane 0)
 template <class T> struct MixedUniform {
   T dv[KMAX + 1];  // dv[j]: the pivot of level j-1 (the divisor of level j's update); dv[0] = 1
+  float xmax, ymax, wmax;  // upper bounds of the magnitudes of the leaf level's columns
 };
+
+BD_HD uint32_t f2u(float f) {
+  uint32_t u;
+  memcpy(&u, &f, 4);
+  return u;
+}
+BD_HD float u2f(uint32_t u) {
+  float f;
+  memcpy(&f, &u, 4);
+  return f;
+}
+
+// nearest float (relative error below 2^-23 in every case)
+BD_HD float to_float(int64_t v) { return (float)v; }
+BD_HD float to_float(i128 v) {
+  const u128 a = v < 0 ? (u128)(-v) : (u128)v;
+  const float r = (float)((double)(uint64_t)(a >> 64) * 18446744073709551616.0 + (double)(uint64_t)a);
+  return v < 0 ? -r : r;
+}
 
 struct MixedAcc {
   u128 mv;            // sum |det M| over accepted tuples
@@ -114,15 +136,20 @@ template <class T, class Team> struct MixedWalker {
   const T* P;              // raw rows, column-major: P[c * N + g], c < K coordinates, c = K lift
   const MixedShape* sh;
   T* st;                   // this team's stack: level j >= 1 at st[(off(j) + e) * N + g]
+  float* fl;               // the leaf level in single precision: level K-1 as fl[g] = x_g,
+                           // fl[N + g] = y_g; with leaf3, level K-2 as float4 (u, v, w, 0) per point
   MixedUniform<T>* uni;
   const uint16_t* last_pairs;  // pairs of the last component as p | q << 8 (global indices)
+  const uint16_t* prev_pairs;  // pairs of component K-2 (leaf3)
   MixedSink sink{nullptr, nullptr, 0};
   Pairs14 cur;             // the pairs of the built levels
   int built = 0;           // levels 0..built-1 are reduced (state `built` is valid)
   int K, N;
+  int kill = -1, kill_c = 0;  // this lane's last point found below a candidate, and its set
 
-  BD_HD MixedWalker(Team t, const T* P_, const MixedShape* s, T* stack, MixedUniform<T>* u, const uint16_t* lp)
-      : tm(t), P(P_), sh(s), st(stack), uni(u), last_pairs(lp), K(s->K), N(s->N) {
+  BD_HD MixedWalker(Team t, const T* P_, const MixedShape* s, T* stack, float* f, MixedUniform<T>* u,
+                    const uint16_t* lp, const uint16_t* pp)
+      : tm(t), P(P_), sh(s), st(stack), fl(f), uni(u), last_pairs(lp), prev_pairs(pp), K(s->K), N(s->N) {
     if (tm.lane() == 0) uni->dv[0] = T(1);
     tm.sync();
   }
@@ -154,6 +181,43 @@ template <class T, class Team> struct MixedWalker {
       const int en = e - (e > c ? 1 : 0);
       for (int g = tm.lane(); g < N; g += tm.lanes()) put(j + 1, en, g) = bareiss(at(j, e, g), vc, at(j, c, g), ve, D);
     }
+    if (sh->leaf3 && j + 3 == K) {  // level K-2 for the 3-D leaf stage: (u, v, w) as float4
+      uint32_t mu = 0, mv = 0, mw = 0;
+      for (int g = tm.lane(); g < N; g += tm.lanes()) {
+        const float u = to_float(put(j + 1, 0, g)), v = to_float(put(j + 1, 1, g)), w = to_float(put(j + 1, 2, g));
+        fl[4 * g] = u;
+        fl[4 * g + 1] = v;
+        fl[4 * g + 2] = w;
+        fl[4 * g + 3] = 0.f;
+        mu = f2u(fabsf(u)) > mu ? f2u(fabsf(u)) : mu;
+        mv = f2u(fabsf(v)) > mv ? f2u(fabsf(v)) : mv;
+        mw = f2u(fabsf(w)) > mw ? f2u(fabsf(w)) : mw;
+      }
+      mu = tm.max_u32(mu);
+      mv = tm.max_u32(mv);
+      mw = tm.max_u32(mw);
+      if (tm.lane() == 0) {
+        uni->xmax = u2f(mu) * 1.0000005f;
+        uni->ymax = u2f(mv) * 1.0000005f;
+        uni->wmax = u2f(mw) * 1.0000005f;
+      }
+    }
+    if (!sh->leaf3 && j + 2 == K) {  // the leaf level: single-precision copies and bounds of their magnitudes
+      uint32_t mx = 0, my = 0;
+      for (int g = tm.lane(); g < N; g += tm.lanes()) {
+        const float x = to_float(put(j + 1, 0, g)), y = to_float(put(j + 1, 1, g));
+        fl[g] = x;
+        fl[N + g] = y;
+        mx = f2u(fabsf(x)) > mx ? f2u(fabsf(x)) : mx;  // non-negative floats order as their bits
+        my = f2u(fabsf(y)) > my ? f2u(fabsf(y)) : my;
+      }
+      mx = tm.max_u32(mx);
+      my = tm.max_u32(my);
+      if (tm.lane() == 0) {  // rounded up past the conversion error
+        uni->xmax = u2f(mx) * 1.0000005f;
+        uni->ymax = u2f(my) * 1.0000005f;
+      }
+    }
     if (tm.lane() == 0) uni->dv[j + 1] = vc;
     tm.sync();
     cur.set_pair(j, p, q);
@@ -161,11 +225,28 @@ template <class T, class Team> struct MixedWalker {
     return true;
   }
 
+  // exact sign of f(z(g)) - f(z(b)) times sigma / d at the leaf (X, Y)
+  BD_HD int exact_sign(T X, T Y, int g, int b) const {
+    const int j = K - 1;
+    return sgn(X * at(j, 1, g) - at(j, 0, g) * Y - (X * at(j, 1, b) - at(j, 0, b) * Y));
+  }
+
   // All pairs of the last component under the built prefix (levels 0..K-2 fixed).
+  //
+  // Filter: with w = +-1 the wanted sign, t = w (X y_g - Y x_g - (X y_b - Y x_b)) is evaluated
+  // in single precision from the rounded copies.  Every operand carries a conversion error below
+  // u = 2^-24, so each of the four products is within 3.01 u of its exact value, and the three
+  // differences add at most 3 u of the sum of the products' magnitudes: the computed t is within
+  // 6.1 u (|X| (|y_g| + |y_b|) + |Y| (|x_g| + |x_b|)) <= 12.2 u (|X| ymax + |Y| xmax) of the
+  // exact value.  eps = 2^-19 (|X| ymax + |Y| xmax) = 32 u (..) keeps a factor 2.6 over that for
+  // the rounding of eps and of the bounds.  |t| > eps decides the sign; otherwise the point is
+  // tested exactly.  Each lane first retries the point that rejected its previous candidate.
   BD_HD void leaves(MixedAcc& acc) {
     const int j = K - 1;
     const uint32_t np = sh->npairs[j];
     const int sd = sgn(uni->dv[j]);
+    const bool filt = K >= 2;  // the raw level 0 has no single-precision copy
+    const float xmax = filt ? uni->xmax : 0.f, ymax = filt ? uni->ymax : 0.f;
     for (uint32_t t = tm.lane(); t < np; t += tm.lanes()) {
       const uint16_t pq = last_pairs[t];
       const int p = pq & 255, q = pq >> 8;
@@ -176,21 +257,38 @@ template <class T, class Team> struct MixedWalker {
       }
       const T Y = at(j, 1, q) - at(j, 1, p);
       const int want = sgn(X) * sd;  // sign of f(b) - f(base) for a point strictly above
+      const float wf = want > 0 ? 1.f : -1.f;
+      const float Xw = to_float(X) * wf, Yw = to_float(Y) * wf;
+      const float eps = 0x1p-19f * (fabsf(Xw) * ymax + fabsf(Yw) * xmax);
+      // 1: strictly above, 0: on the cell's plane, -1: strictly below
+      auto verdict = [&](int g, int b, float cbw) -> int {
+        if (filt) {
+          const float tt = (Xw * fl[N + g] - Yw * fl[g]) - cbw;
+          if (tt > eps) return 1;
+          if (tt < -eps) return -1;
+        }
+        return exact_sign(X, Y, g, b) * want;
+      };
       bool below = false, on = false;
+      if (kill >= 0) {
+        const int i = kill_c;
+        const int pi = i == j ? p : cur.p(i), qi = i == j ? q : cur.q(i);
+        if (kill != pi && kill != qi)
+          below = verdict(kill, pi, filt ? Xw * fl[N + pi] - Yw * fl[pi] : 0.f) < 0;
+      }
       for (int i = 0; i < K && !below; ++i) {
         const int pi = i == j ? p : cur.p(i), qi = i == j ? q : cur.q(i);
-        const T cb = X * at(j, 1, pi) - at(j, 0, pi) * Y;
+        const float cbw = filt ? Xw * fl[N + pi] - Yw * fl[pi] : 0.f;
         for (int g = sh->first[i]; g < sh->first[i + 1]; ++g) {
           if (g == pi || g == qi) continue;
-          const int s = sgn(X * at(j, 1, g) - at(j, 0, g) * Y - cb);
-          if (s != want) {
-            if (s == 0) {
-              on = true;
-            } else {
-              below = true;
-              break;
-            }
+          const int v = verdict(g, pi, cbw);
+          if (v < 0) {
+            below = true;
+            kill = g;
+            kill_c = i;
+            break;
           }
+          on |= v == 0;
         }
       }
       if (below) continue;
@@ -201,11 +299,116 @@ template <class T, class Team> struct MixedWalker {
       const T ax = X < 0 ? -X : X;
       acc.mv += (u128)ax;
       ++acc.cells;
-      if (sink.out) record(p, q, ax);
+      if (sink.out) record(-1, -1, p, q, ax);
     }
   }
 
-  BD_HD void record(int p, int q, T ax) {
+  // Exact verdict of point g against base b for the tuple whose last two pivot rows are
+  // a = r(q1) - r(p1), c = r(q) - r(p) at level K-2 (1 above, 0 on, -1 below): level K-1 is
+  // formed for the four rows only, and the test is the one of leaves().
+  BD_HD int exact3(int p1, int q1, int p, int q, int g, int b, const Div& D) const {
+    const int j = K - 2;
+    const T a0 = at(j, 0, q1) - at(j, 0, p1), a1 = at(j, 1, q1) - at(j, 1, p1), a2 = at(j, 2, q1) - at(j, 2, p1);
+    const int c = a0 != 0 ? 0 : 1, o = 1 - c;  // a's pivot column (det M != 0: a has one)
+    const T ac = c == 0 ? a0 : a1, ao = c == 0 ? a1 : a0;
+    auto x = [&](int r) { return bareiss(at(j, o, r), ac, at(j, c, r), ao, D); };
+    auto y = [&](int r) { return bareiss(at(j, 2, r), ac, at(j, c, r), a2, D); };
+    const T xp = x(p), X = x(q) - xp, Y = y(q) - y(p);
+    const int want = sgn(X) * sgn(ac);
+    return sgn(X * (y(g) - y(b)) - (x(g) - x(b)) * Y) * want;
+  }
+
+  // The 3-D leaf stage: every pair (p1, q1) of component K-2 with every pair (p, q) of the
+  // last component, dealt to lanes, tested from level K-2 without forming level K-1.  With a, c
+  // the two pivot rows and e = r(b) - r(base) (columns u, v, w of level K-2, d its divisor),
+  // eliminating a and then c gives (Sylvester) X = det2 / d, det2 = a_u c_v - a_v c_u, and the
+  // test value of the two-level rule a_piv det[a; c; e] / d^2, so b is above iff
+  // det[a; c; e] * det2 * sign(d) > 0 and |det M| = |det2 / d|.
+  //
+  // Filter: a, c, n = a x c and n . F(b) - n . F(base) in single precision from the rounded
+  // copies F.  With U, V, W bounds of |u|, |v|, |w|: each entry of a or c is within 4 u U (V, W)
+  // of its exact value (u = 2^-24), each component of n within 48 u of its bound 8 V W (8 W U,
+  // 8 U V), each of the six products n_i F_i within 64 u U V W and the five additions within
+  // 240 u U V W: the computed value is within 624 u U V W < 2^-14.7 U V W of det[a; c; e], and
+  // eps3 = 2^-13 U V W.  det2 is within 48 u U V < 2^-18.4 U V; eps2 = 2^-16 U V.  Values
+  // inside the bounds are decided exactly (exact3, or det2 from the stored integers).
+  BD_HD void leaves3(MixedAcc& acc) {
+    const int j = K - 2;
+    const uint32_t n1 = sh->npairs[j], n2 = sh->npairs[j + 1], total = n1 * n2;
+    const T d = uni->dv[j];
+    const Div D = make_div(d);
+    const int sd = sgn(d);
+    const float U = uni->xmax, V = uni->ymax, Wm = uni->wmax;
+    const float eps2 = 0x1p-16f * U * V, eps3 = 0x1p-13f * U * V * Wm;
+    for (uint32_t t = tm.lane(); t < total; t += tm.lanes()) {
+      const uint16_t pa = prev_pairs[t / n2], pc = last_pairs[t % n2];
+      const int p1 = pa & 255, q1 = pa >> 8, p = pc & 255, q = pc >> 8;
+      const float a0 = fl[4 * q1] - fl[4 * p1], a1 = fl[4 * q1 + 1] - fl[4 * p1 + 1], a2 = fl[4 * q1 + 2] - fl[4 * p1 + 2];
+      const float c0 = fl[4 * q] - fl[4 * p], c1 = fl[4 * q + 1] - fl[4 * p + 1], c2 = fl[4 * q + 2] - fl[4 * p + 2];
+      const float det2f = a0 * c1 - a1 * c0;
+      int s2;
+      T det2 = 0;
+      bool exact2 = false;
+      if (fabsf(det2f) > eps2) {
+        s2 = det2f > 0 ? 1 : -1;
+      } else {
+        det2 = (at(j, 0, q1) - at(j, 0, p1)) * (at(j, 1, q) - at(j, 1, p)) -
+               (at(j, 1, q1) - at(j, 1, p1)) * (at(j, 0, q) - at(j, 0, p));
+        exact2 = true;
+        if (det2 == 0) {
+          ++acc.singular;
+          continue;
+        }
+        s2 = sgn(det2);
+      }
+      s2 *= sd;  // b is above iff s2 * det[a; c; e] > 0
+      const float w = s2 > 0 ? 1.f : -1.f;
+      const float n0 = (a1 * c2 - a2 * c1) * w, n1v = (a2 * c0 - a0 * c2) * w, n2v = (a0 * c1 - a1 * c0) * w;
+      auto nd = [&](int r) { return n0 * fl[4 * r] + n1v * fl[4 * r + 1] + n2v * fl[4 * r + 2]; };
+      auto verdict = [&](int g, int b, float nb) -> int {
+        const float tt = nd(g) - nb;
+        if (tt > eps3) return 1;
+        if (tt < -eps3) return -1;
+        return exact3(p1, q1, p, q, g, b, D);
+      };
+      bool below = false, on = false;
+      if (kill >= 0) {
+        const int i = kill_c;
+        const int pi = i == j + 1 ? p : (i == j ? p1 : cur.p(i)), qi = i == j + 1 ? q : (i == j ? q1 : cur.q(i));
+        if (kill != pi && kill != qi) below = verdict(kill, pi, nd(pi)) < 0;
+      }
+      for (int i = 0; i < K && !below; ++i) {
+        const int pi = i == j + 1 ? p : (i == j ? p1 : cur.p(i)), qi = i == j + 1 ? q : (i == j ? q1 : cur.q(i));
+        const float nb = nd(pi);
+        for (int g = sh->first[i]; g < sh->first[i + 1]; ++g) {
+          if (g == pi || g == qi) continue;
+          const int v = verdict(g, pi, nb);
+          if (v < 0) {
+            below = true;
+            kill = g;
+            kill_c = i;
+            break;
+          }
+          on |= v == 0;
+        }
+      }
+      if (below) continue;
+      if (on) {
+        ++acc.ties;
+        continue;
+      }
+      if (!exact2)
+        det2 = (at(j, 0, q1) - at(j, 0, p1)) * (at(j, 1, q) - at(j, 1, p)) -
+               (at(j, 1, q1) - at(j, 1, p1)) * (at(j, 0, q) - at(j, 0, p));
+      T ax = det2 / d;  // |det M| = |det2 / d|, an exact quotient
+      ax = ax < 0 ? -ax : ax;
+      acc.mv += (u128)ax;
+      ++acc.cells;
+      if (sink.out) record(p1, q1, p, q, ax);
+    }
+  }
+
+  BD_HD void record(int p1, int q1, int p, int q, T ax) {
 #ifdef __CUDA_ARCH__
     const unsigned long long slot = atomicAdd(sink.count, 1ull);
 #else
@@ -217,6 +420,10 @@ template <class T, class Team> struct MixedWalker {
     for (int i = 0; i < K - 1; ++i) {
       r.idx[2 * i] = (uint8_t)cur.p(i);
       r.idx[2 * i + 1] = (uint8_t)cur.q(i);
+    }
+    if (p1 >= 0) {  // leaf3: level K-2's pair is not in the cursor
+      r.idx[2 * (K - 2)] = (uint8_t)p1;
+      r.idx[2 * (K - 2) + 1] = (uint8_t)q1;
     }
     r.idx[2 * (K - 1)] = (uint8_t)p;
     r.idx[2 * (K - 1) + 1] = (uint8_t)q;
@@ -252,18 +459,21 @@ template <class T, class Team> struct MixedWalker {
         return;
       }
     }
-    if (L == K - 1) {
-      leaves(acc);
+    const int leaf_at = sh->leaf3 ? K - 2 : K - 1;  // the level whose state feeds the leaf stage
+    if (L == leaf_at) {
+      if (sh->leaf3) leaves3(acc);
+      else leaves(acc);
       return;
     }
-    // walk levels L..K-2; pair (p, q) of level j runs over component j in lexicographic order
+    // walk levels L..leaf_at-1; pair (p, q) of level j runs over component j in lexicographic order
     int j = L;
     int p = sh->first[j], q = p + 1;
     for (;;) {
       bool down = false;
       if (descend(j, p, q)) {
-        if (j + 1 == K - 1) {
-          leaves(acc);
+        if (j + 1 == leaf_at) {
+          if (sh->leaf3) leaves3(acc);
+          else leaves(acc);
         } else {
           ++j;
           p = sh->first[j];

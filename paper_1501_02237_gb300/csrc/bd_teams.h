@@ -16,6 +16,7 @@ struct HostTeam {
   bool all(bool b) const { return b; }
   void sync() const {}
   uint64_t or_all(uint64_t x) const { return x; }
+  uint32_t max_u32(uint32_t x) const { return x; }
 };
 
 // A team of `width` lanes run as CPU threads in lockstep: every collective (vote, sync) is a
@@ -58,6 +59,14 @@ struct LockstepTeam {
   bool all(bool b) const { return reduce_or(b, true) != 0; }
   void sync() const { sh->barrier(); }
   uint64_t or_all(uint64_t x) const { return reduce_or(x, false); }
+  uint32_t max_u32(uint32_t x) const {
+    sh->votes[ln] = x;
+    sh->barrier();
+    uint64_t r = 0;
+    for (int w = 0; w < sh->width; ++w) r = sh->votes[w] > r ? sh->votes[w] : r;
+    sh->barrier();
+    return (uint32_t)r;
+  }
 };
 
 }  // namespace bd

@@ -41,6 +41,39 @@ def test_gpu_mixed_cells_match_oracle(seed):
     assert r["mv"] == sum(v for _, v in cells) and r["singular"] == sing
 
 
+@pytest.mark.parametrize("seed,big", [(0, 1 << 20), (1, 1 << 20), (2, 1 << 30), (3, 1 << 30), (4, 1 << 33)])
+def test_gpu_mixed_near_coplanar_lifts(seed, big):
+    # every point within a few units of one plane: the exact route decides most tests
+    rng = random.Random(9400 + seed)
+    k = 3
+    S = random_supports(rng, k, lo=3, hi=5)
+    l = [rng.randint(-3, 3) for _ in range(k)]
+    W = [big * sum(x * y for x, y in zip(p, l)) + rng.randint(-2, 2) for A in S for p in A]
+    cells, sing, ties = mixed_cells(S, W)
+    r = bd.mixed_volume_lifted(S, W, cells=True)
+    if ties:
+        assert r["status"] == 3 and r["ties"] == ties
+        return
+    assert r["cell_list"] == [c for c, _ in cells] and r["singular"] == sing
+
+
+@pytest.mark.parametrize("seed,big", [(0, 1 << 24), (1, 1 << 28)])
+def test_gpu_mixed_near_coplanar_mid_size(seed, big):
+    # the 3-D leaf stage (1024+ nodes above it) with heights near one plane: its exact route
+    S = [A.tolist() for A in mixed_config("mixed_k5_p6")]
+    rng = random.Random(9500 + seed)
+    l = [rng.randint(-3, 3) for _ in range(5)]
+    W = [big * sum(x * y for x, y in zip(p, l)) + rng.randint(-1000, 1000) for A in S for p in A]
+    g = bd.mixed_volume_lifted(S, W, cells=True)
+    h = bd.host_mixed_volume_lifted(S, W, cells=True, leaf3=0)
+    assert g["status"] == h["status"]
+    if g["status"] == 0:
+        assert (g["mv"], g["cell_list"], g["singular"]) == (h["mv"], h["cell_list"], h["singular"])
+        SL = S
+        for c, v in zip(g["cell_list"], g["absdet"]):
+            assert cell_status(SL, W, c) == ("accepted", v)
+
+
 @pytest.mark.parametrize("seed", range(6))
 def test_gpu_mixed_volume_equals_polarization(seed):
     rng = random.Random(9200 + seed)
@@ -97,7 +130,7 @@ def test_gpu_mixed_mid_size_equals_host_emulation():
     S = mixed_config("mixed_k5_p6")
     W = oracle_lifts(sum(len(A) for A in S), 2)
     g = bd.mixed_volume_lifted(S, W, cells=True)
-    h = bd.host_mixed_volume_lifted(S, W, cells=True)
+    h = bd.host_mixed_volume_lifted(S, W, cells=True, leaf3=0)  # the two-level leaf stage
     assert g["status"] == 0 and g == {**h, "device_ms": g["device_ms"]}
     g128 = bd.mixed_volume_lifted(S, W, force_int128=True)
     assert g128["flags"] & bd.BD_FLAG_INT128 and (g128["mv"], g128["cells"], g128["singular"]) == \

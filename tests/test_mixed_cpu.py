@@ -29,9 +29,13 @@ def test_host_mixed_cells_match_oracle(seed):
     S = random_supports(rng, k, hi=5 if k < 4 else 4)
     W = oracle_lifts(sum(len(A) for A in S), seed)
     cells, sing, ties = oracle_result(S, W)
-    # work items fixing every possible number of levels, one-lane teams and a 7-lane team
-    for width, levels in [(1, 0), (7, 0)] + [(1, L) for L in range(1, k)]:
-        r = bd.host_mixed_volume_lifted(S, W, team_width=width, cells=True, prefix_levels=levels)
+    # work items fixing every possible number of levels, one-lane teams and a 7-lane team, the
+    # two-level leaf stage and the 3-D one (k >= 3)
+    runs = [(1, 0, 0), (7, 0, 0)] + [(1, L, 0) for L in range(1, k)]
+    if k >= 3:
+        runs += [(1, 0, 1), (7, 0, 1)] + [(1, L, 1) for L in range(1, k - 1)]
+    for width, levels, leaf3 in runs:
+        r = bd.host_mixed_volume_lifted(S, W, team_width=width, cells=True, prefix_levels=levels, leaf3=leaf3)
         if ties:
             assert r["status"] == 3 and r["ties"] == ties
             continue
@@ -53,6 +57,8 @@ def test_host_mixed_volume_equals_polarization(seed):
         assert r["mv"] == mv
     r32 = bd.host_mixed_volume_lifted(S, W, team_width=32, force_int128=True)
     assert (r32["status"], r32["mv"]) == (r["status"], r["mv"])
+    r3 = bd.host_mixed_volume_lifted(S, W, team_width=32, leaf3=1)
+    assert (r3["status"], r3["mv"], r3["singular"]) == (r["status"], r["mv"], r["singular"])
 
 
 @pytest.mark.parametrize("k,degs", [(4, (2, 1, 2, 2)), (5, (1, 2, 1, 1, 2))])
@@ -109,8 +115,8 @@ def test_host_mixed_degenerate_and_errors():
         P, cnt = np.zeros((2, 1), dtype=np.int64), np.array([2], dtype=np.int32)
         out = bd.MixedOut()
         bd.check(bd.lib().bd_host_mixed_volume_lifted(bd.ptr(P), cnt.ctypes.data_as(bd.I32P), 0,
-                                                       bd.ptr(np.ones(2, dtype=np.int64)), 1, 0, 0, out, None, 0,
-                                                       None))
+                                                       bd.ptr(np.ones(2, dtype=np.int64)), 1, 0, 0, -1, out, None,
+                                                       0, None))
     big = [[(i, 0) for i in range(40)], [(0, i) for i in range(30)]]
     with pytest.raises(bd.BinodegError):
         bd.host_mixed_volume_lifted(big, list(range(1, 71)))  # more than 64 points
@@ -125,3 +131,22 @@ def test_host_mixed_tie_reported():
     assert r["status"] == 3 and r["ties"] > 0
     _, _, ties = oracle_result(S, [0] * 8)
     assert r["ties"] == ties
+
+
+@pytest.mark.parametrize("seed,big", [(0, 1 << 20), (1, 1 << 20), (2, 1 << 30), (3, 1 << 30), (4, 1 << 24),
+                                      (5, 1 << 26)])
+def test_host_mixed_near_coplanar_lifts(seed, big):
+    # heights big * <l, a> + small noise: every point sits within a few units of one plane, so
+    # the single-precision filter cannot decide most tests and the exact route decides them
+    rng = random.Random(8400 + seed)
+    k = 3
+    S = random_supports(rng, k, lo=3, hi=5)
+    l = [rng.randint(-3, 3) for _ in range(k)]
+    W = [big * sum(x * y for x, y in zip(p, l)) + rng.randint(-2, 2) for A in S for p in A]
+    cells, sing, ties = oracle_result(S, W)
+    for width, leaf3 in [(1, 0), (7, 0), (1, 1), (7, 1)]:
+        r = bd.host_mixed_volume_lifted(S, W, team_width=width, cells=True, leaf3=leaf3)
+        if ties:
+            assert r["status"] == 3 and r["ties"] == ties
+            continue
+        assert r["cell_list"] == [c for c, _ in cells] and r["singular"] == sing
