@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch-serve", action="store_true", help="skip the batch and serving sections")
     ap.add_argument("--workload", default=WORKLOAD, help="single system timed (profiling runs use the others)")
+    ap.add_argument("--mixed-only", default=None, metavar="WORKLOAD",
+                    help="run only the mixed-volume section on this workload (profiling runs)")
     return ap.parse_args()
 
 
@@ -257,7 +259,7 @@ def mixed_section(bd, name=MIXED_WORKLOAD, seed=0, runs=3, cpu_seconds=5.0):
     while time.perf_counter() - t0 < cpu_seconds:
         cell_status(SL, W, tuple(rng.choice(P) for P in pairs))
         done += 1
-    cpu_rate = done / (time.perf_counter() - t0)
+    cpu_rate = done / max(time.perf_counter() - t0, 1e-9)
     return dict(workload=name, k=len(S), points_per_set=len(S[0]), tuples=r["tuples"], mv=r["mv"], cells=r["cells"],
                 int_path="int128" if r["flags"] & bd.BD_FLAG_INT128 else "int64", kernel_ms=d,
                 tuples_per_s=r["tuples"] / (d / 1e3), call_ms=1e3 * w, call_tuples_per_s=r["tuples"] / w,
@@ -355,6 +357,9 @@ def main():
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
     bd.set_stream(stream)
+    if args.mixed_only:
+        print(json.dumps(mixed_section(bd, name=args.mixed_only, seed=args.seed, runs=1, cpu_seconds=0.0)), flush=True)
+        return
 
     s = config_system(args.workload)
     red = bd.reduce(s.A)

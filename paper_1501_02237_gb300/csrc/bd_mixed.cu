@@ -22,7 +22,7 @@ using bd::u128;
 
 namespace {
 
-constexpr int kMixedWarps = 4;  // warps per block
+constexpr int kMixedMaxWarps = 8;  // warps per block: chosen per problem, at most this
 
 struct MixedWarp {
   __device__ int lane() const { return threadIdx.x & 31; }
@@ -154,15 +154,15 @@ template <class T> void make_rows(const int64_t* pts, const int64_t* lifts, cons
   }
 }
 
-size_t smem_bytes(const MixedPrep& mp, int elem) {
+size_t smem_bytes(const MixedPrep& mp, int elem, int warps) {
   const int K = mp.shape.K, N = mp.shape.N;
   size_t b = (size_t)(K + 1) * N * elem;                                  // rows
   b += sizeof(bd::MixedShape);
   b += (mp.last_pairs.size() * sizeof(uint16_t) + 15) / 16 * 16;          // last level's pairs
   b += (mp.prev_pairs.size() * sizeof(uint16_t) + 15) / 16 * 16;          // level K-2's pairs
   b = (b + 15) / 16 * 16;
-  const size_t per_warp = sizeof(bd::MixedUniform<i128>) + 16 * (size_t)N + (size_t)bd::mixed_stack_entries(K) * N * elem;
-  return b + kMixedWarps * ((per_warp + 15) / 16 * 16);
+  const size_t per_warp = sizeof(bd::MixedUniform<i128>) + 32 * (size_t)N + (size_t)bd::mixed_stack_entries(K) * N * elem;
+  return b + warps * ((per_warp + 15) / 16 * 16);
 }
 
 struct MixedDevAcc {
@@ -170,7 +170,7 @@ struct MixedDevAcc {
 };
 
 template <class T>
-__global__ void __launch_bounds__(32 * kMixedWarps) k_mixed(const T* rows, bd::MixedShape shape,
+__global__ void __launch_bounds__(32 * kMixedMaxWarps) k_mixed(const T* rows, bd::MixedShape shape,
                                                             const uint16_t* last_pairs, const uint16_t* prev_pairs,
                                                             unsigned long long* next,
                                                             unsigned long long chunk, bd::MixedSink sink,
@@ -188,12 +188,12 @@ __global__ void __launch_bounds__(32 * kMixedWarps) k_mixed(const T* rows, bd::M
   at += ((size_t)npp * sizeof(uint16_t) + 15) / 16 * 16;
   at = (at + 15) / 16 * 16;
   const size_t stack_bytes = (size_t)bd::mixed_stack_entries(K) * N * sizeof(T);
-  const size_t per_warp = ((sizeof(bd::MixedUniform<i128>) + 16 * (size_t)N + stack_bytes) + 15) / 16 * 16;
+  const size_t per_warp = ((sizeof(bd::MixedUniform<i128>) + 32 * (size_t)N + stack_bytes) + 15) / 16 * 16;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   unsigned char* wbase = smem + at + warp * per_warp;
   auto* uni = reinterpret_cast<bd::MixedUniform<T>*>(wbase);
   float* fl = reinterpret_cast<float*>(wbase + sizeof(bd::MixedUniform<i128>));  // 16-byte aligned
-  T* stack = reinterpret_cast<T*>(wbase + sizeof(bd::MixedUniform<i128>) + 16 * (size_t)N);
+  T* stack = reinterpret_cast<T*>(wbase + sizeof(bd::MixedUniform<i128>) + 32 * (size_t)N);
   for (int i = threadIdx.x; i < (K + 1) * N; i += blockDim.x) P[i] = rows[i];
   for (uint32_t i = threadIdx.x; i < npl; i += blockDim.x) lp[i] = last_pairs[i];
   for (uint32_t i = threadIdx.x; i < npp; i += blockDim.x) pp[i] = prev_pairs[i];
@@ -245,21 +245,34 @@ struct RunResult {
 template <class T>
 int device_run(const MixedPrep& mp, const std::vector<T>& rows, uint64_t cap, RunResult& rr) {
   cudaStream_t st = bd::thread_stream();
-  const size_t smem = smem_bytes(mp, sizeof(T));
   int dev = 0, sms = 0, optin = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  if (smem > (size_t)optin) return bd::set_error(BD_ERR_ARG, "the problem's walk state exceeds shared memory");
-  cudaError_t e = cudaFuncSetAttribute(k_mixed<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  int per_sm = 0;
-  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mixed<T>, 32 * kMixedWarps, smem);
+  if (smem_bytes(mp, sizeof(T), 1) > (size_t)optin)
+    return bd::set_error(BD_ERR_ARG, "the problem's walk state exceeds shared memory");
+  cudaError_t e = cudaFuncSetAttribute(k_mixed<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  // warps per block: the most resident warps per SM (the walk state is per warp, so the
+  // block size decides how much of the shared memory is left unused)
+  int wpb = 1, per_sm = 0, best = 0;
+  for (int w = 1; w <= kMixedMaxWarps && e == cudaSuccess; ++w) {
+    const size_t sm_w = smem_bytes(mp, sizeof(T), w);
+    if (sm_w > (size_t)optin) break;
+    int b = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_mixed<T>, 32 * w, sm_w);
+    if (b * w > best) {
+      best = b * w;
+      wpb = w;
+      per_sm = b;
+    }
+  }
   if (e != cudaSuccess) return bd::set_error(BD_ERR_CUDA, cudaGetErrorString(e));
   per_sm = std::max(per_sm, 1);
+  const size_t smem = smem_bytes(mp, sizeof(T), wpb);
   const unsigned long long items = mp.shape.items;
-  const unsigned long long warps = (unsigned long long)sms * per_sm * kMixedWarps;
+  const unsigned long long warps = (unsigned long long)sms * per_sm * wpb;
   const unsigned long long blocks = std::min<unsigned long long>((unsigned long long)sms * per_sm,
-                                                                 (items + kMixedWarps - 1) / kMixedWarps);
+                                                                 (items + wpb - 1) / wpb);
   // runs of consecutive items share their prefix levels, which a warp builds once
   const unsigned long long chunk = std::max<unsigned long long>(1, items / (warps * 8));
   T* d_rows = nullptr;
@@ -297,7 +310,7 @@ int device_run(const MixedPrep& mp, const std::vector<T>& rows, uint64_t cap, Ru
   if (e == cudaSuccess) e = cudaEventRecord(e0, st);
   if (e == cudaSuccess) {
     bd::MixedSink sink{d_recs, d_next + 1, cap};
-    k_mixed<T><<<(unsigned int)blocks, 32 * kMixedWarps, smem, st>>>(d_rows, mp.shape, d_lp, d_pp, d_next, chunk, sink,
+    k_mixed<T><<<(unsigned int)blocks, 32 * wpb, smem, st>>>(d_rows, mp.shape, d_lp, d_pp, d_next, chunk, sink,
                                                                        d_acc);
     e = cudaGetLastError();
   }
@@ -337,7 +350,7 @@ int host_run(const MixedPrep& mp, const std::vector<T>& rows, uint64_t cap, int 
   if (width > 1) {
     bd::LockstepShared shl(width);
     std::vector<T> stack(entries);
-    std::vector<float> fl(4 * (size_t)N);
+    std::vector<float> fl(8 * (size_t)N);
     bd::MixedUniform<T> uni{};
     part.assign(width, bd::MixedAcc{});
     std::vector<std::thread> th;
@@ -356,7 +369,7 @@ int host_run(const MixedPrep& mp, const std::vector<T>& rows, uint64_t cap, int 
     std::atomic<uint64_t> next(0);
     auto work = [&](int w) {
       std::vector<T> stack(entries);
-      std::vector<float> fl(4 * (size_t)N);
+      std::vector<float> fl(8 * (size_t)N);
       bd::MixedUniform<T> uni{};
       bd::HostTeam tm;
       bd::MixedWalker<T, bd::HostTeam> W(tm, rows.data(), &mp.shape, stack.data(), fl.data(), &uni,

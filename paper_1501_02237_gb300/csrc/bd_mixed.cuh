@@ -138,6 +138,7 @@ template <class T, class Team> struct MixedWalker {
   T* st;                   // this team's stack: level j >= 1 at st[(off(j) + e) * N + g]
   float* fl;               // the leaf level in single precision: level K-1 as fl[g] = x_g,
                            // fl[N + g] = y_g; with leaf3, level K-2 as float4 (u, v, w, 0) per point
+  float* rl;               // leaf3: per point of the fixed sets, F(g) - F(base) and the base index
   MixedUniform<T>* uni;
   const uint16_t* last_pairs;  // pairs of the last component as p | q << 8 (global indices)
   const uint16_t* prev_pairs;  // pairs of component K-2 (leaf3)
@@ -149,7 +150,8 @@ template <class T, class Team> struct MixedWalker {
 
   BD_HD MixedWalker(Team t, const T* P_, const MixedShape* s, T* stack, float* f, MixedUniform<T>* u,
                     const uint16_t* lp, const uint16_t* pp)
-      : tm(t), P(P_), sh(s), st(stack), fl(f), uni(u), last_pairs(lp), prev_pairs(pp), K(s->K), N(s->N) {
+      : tm(t), P(P_), sh(s), st(stack), fl(f), rl(f + 4 * s->N), uni(u), last_pairs(lp), prev_pairs(pp), K(s->K),
+        N(s->N) {
     if (tm.lane() == 0) uni->dv[0] = T(1);
     tm.sync();
   }
@@ -319,42 +321,85 @@ template <class T, class Team> struct MixedWalker {
   }
 
   // The 3-D leaf stage: every pair (p1, q1) of component K-2 with every pair (p, q) of the
-  // last component, dealt to lanes, tested from level K-2 without forming level K-1.  With a, c
-  // the two pivot rows and e = r(b) - r(base) (columns u, v, w of level K-2, d its divisor),
-  // eliminating a and then c gives (Sylvester) X = det2 / d, det2 = a_u c_v - a_v c_u, and the
-  // test value of the two-level rule a_piv det[a; c; e] / d^2, so b is above iff
-  // det[a; c; e] * det2 * sign(d) > 0 and |det M| = |det2 / d|.
+  // last component, tested from level K-2 without forming level K-1.  With a, c the two pivot
+  // rows and e = r(b) - r(base) (columns u, v, w of level K-2, d its divisor), eliminating a
+  // and then c gives (Sylvester) X = det2 / d, det2 = a_u c_v - a_v c_u, and the test value of
+  // the two-level rule a_piv det[a; c; e] / d^2, so b is above iff det[a; c; e] * det2 *
+  // sign(d) > 0, and |det M| = |det2 / d|.
   //
-  // Filter: a, c, n = a x c and n . F(b) - n . F(base) in single precision from the rounded
-  // copies F.  With U, V, W bounds of |u|, |v|, |w|: each entry of a or c is within 4 u U (V, W)
-  // of its exact value (u = 2^-24), each component of n within 48 u of its bound 8 V W (8 W U,
-  // 8 U V), each of the six products n_i F_i within 64 u U V W and the five additions within
-  // 240 u U V W: the computed value is within 624 u U V W < 2^-14.7 U V W of det[a; c; e], and
-  // eps3 = 2^-13 U V W.  det2 is within 48 u U V < 2^-18.4 U V; eps2 = 2^-16 U V.  Values
-  // inside the bounds are decided exactly (exact3, or det2 from the stored integers).
+  // Filter: a, c, n = a x c and n . e in single precision from the rounded copies F (and, for
+  // the sets fixed above this node, from e = F(b) - F(base) formed once per node).  With U, V,
+  // W bounds of |u|, |v|, |w|: each entry of a or c is within 4 u U (V, W) of its exact value
+  // (u = 2^-24), each component of n within 48 u of its bound 8 V W (8 W U, 8 U V), and n . F(b)
+  // - n . F(base) within 624 u U V W (n . e within 528 u U V W) of det[a; c; e] < 2^-14.7 U V W:
+  // eps3 = 2^-13 U V W.  When U, V <= 2^22 and U V <= 2^21 every value in det2 is an integer
+  // below 2^24 and det2 is exact in single precision; otherwise it is within 48 u U V <
+  // 2^-18.4 U V, eps2 = 2^-16 U V, and values inside are taken from the stored integers.  Values
+  // inside eps3 are decided exactly (exact3).
+  //
+  // Lane l takes the l-th contiguous block of the combinations, so consecutive candidates of a
+  // lane share the pair of set K-2 (its row a is formed once) and, mostly, the point that
+  // rejects them, which each lane retries first.
   BD_HD void leaves3(MixedAcc& acc) {
     const int j = K - 2;
     const uint32_t n1 = sh->npairs[j], n2 = sh->npairs[j + 1], total = n1 * n2;
+    const int f2 = sh->first[j], f3 = sh->first[j + 1];
     const T d = uni->dv[j];
     const Div D = make_div(d);
     const int sd = sgn(d);
     const float U = uni->xmax, V = uni->ymax, Wm = uni->wmax;
     const float eps2 = 0x1p-16f * U * V, eps3 = 0x1p-13f * U * V * Wm;
-    for (uint32_t t = tm.lane(); t < total; t += tm.lanes()) {
-      const uint16_t pa = prev_pairs[t / n2], pc = last_pairs[t % n2];
-      const int p1 = pa & 255, q1 = pa >> 8, p = pc & 255, q = pc >> 8;
-      const float a0 = fl[4 * q1] - fl[4 * p1], a1 = fl[4 * q1 + 1] - fl[4 * p1 + 1], a2 = fl[4 * q1 + 2] - fl[4 * p1 + 2];
+    const bool small2 = U <= 0x1p22f && V <= 0x1p22f && U * V <= 0x1p21f;
+    // the fixed sets: members and, per point, e = F(g) - F(base) with the base's index in .w
+    uint64_t members = 0;
+    for (int i = 0; i < j; ++i) members |= (1ull << cur.p(i)) | (1ull << cur.q(i));
+    tm.sync();  // readers of the previous node's relative rows are done
+    for (int g = tm.lane(); g < f2; g += tm.lanes()) {
+      int i = 0;
+      while (g >= sh->first[i + 1]) ++i;
+      const int b = cur.p(i);
+      rl[4 * g] = fl[4 * g] - fl[4 * b];
+      rl[4 * g + 1] = fl[4 * g + 1] - fl[4 * b + 1];
+      rl[4 * g + 2] = fl[4 * g + 2] - fl[4 * b + 2];
+      rl[4 * g + 3] = (float)b;
+    }
+    tm.sync();
+    const uint32_t lo = (uint32_t)(((uint64_t)total * tm.lane()) / tm.lanes());
+    const uint32_t hi = (uint32_t)(((uint64_t)total * (tm.lane() + 1)) / tm.lanes());
+    uint32_t t1 = lo / n2, t2 = lo % n2;
+    int p1 = -1, q1 = -1;
+    float a0 = 0, a1 = 0, a2 = 0;
+    for (uint32_t t = lo; t < hi; ++t, ++t2) {
+      if (t2 == n2) {
+        t2 = 0;
+        ++t1;
+      }
+      if ((int)(prev_pairs[t1] & 255) != p1 || (int)(prev_pairs[t1] >> 8) != q1) {
+        p1 = prev_pairs[t1] & 255;
+        q1 = prev_pairs[t1] >> 8;
+        a0 = fl[4 * q1] - fl[4 * p1];
+        a1 = fl[4 * q1 + 1] - fl[4 * p1 + 1];
+        a2 = fl[4 * q1 + 2] - fl[4 * p1 + 2];
+      }
+      const uint16_t pc = last_pairs[t2];
+      const int p = pc & 255, q = pc >> 8;
       const float c0 = fl[4 * q] - fl[4 * p], c1 = fl[4 * q + 1] - fl[4 * p + 1], c2 = fl[4 * q + 2] - fl[4 * p + 2];
       const float det2f = a0 * c1 - a1 * c0;
       int s2;
       T det2 = 0;
-      bool exact2 = false;
-      if (fabsf(det2f) > eps2) {
+      bool have2 = false;
+      if (small2) {
+        if (det2f == 0.f) {
+          ++acc.singular;
+          continue;
+        }
+        s2 = det2f > 0 ? 1 : -1;
+      } else if (fabsf(det2f) > eps2) {
         s2 = det2f > 0 ? 1 : -1;
       } else {
         det2 = (at(j, 0, q1) - at(j, 0, p1)) * (at(j, 1, q) - at(j, 1, p)) -
                (at(j, 1, q1) - at(j, 1, p1)) * (at(j, 0, q) - at(j, 0, p));
-        exact2 = true;
+        have2 = true;
         if (det2 == 0) {
           ++acc.singular;
           continue;
@@ -364,42 +409,45 @@ template <class T, class Team> struct MixedWalker {
       s2 *= sd;  // b is above iff s2 * det[a; c; e] > 0
       const float w = s2 > 0 ? 1.f : -1.f;
       const float n0 = (a1 * c2 - a2 * c1) * w, n1v = (a2 * c0 - a0 * c2) * w, n2v = (a0 * c1 - a1 * c0) * w;
-      auto nd = [&](int r) { return n0 * fl[4 * r] + n1v * fl[4 * r + 1] + n2v * fl[4 * r + 2]; };
-      auto verdict = [&](int g, int b, float nb) -> int {
-        const float tt = nd(g) - nb;
+      const float nb1 = n0 * fl[4 * p1] + n1v * fl[4 * p1 + 1] + n2v * fl[4 * p1 + 2];
+      const float nb2 = n0 * fl[4 * p] + n1v * fl[4 * p + 1] + n2v * fl[4 * p + 2];
+      // the single-precision value tested for point g, and the point's base
+      auto tval = [&](int g) -> float {
+        const bool fixed = g < f2;
+        const float* src = fixed ? rl : fl;
+        const float sub = fixed ? 0.f : (g >= f3 ? nb2 : nb1);
+        return n0 * src[4 * g] + n1v * src[4 * g + 1] + n2v * src[4 * g + 2] - sub;
+      };
+      auto member = [&](int g) -> bool {
+        if (g < f2) return (members >> g) & 1;
+        return g >= f3 ? (g == p || g == q) : (g == p1 || g == q1);
+      };
+      // 1 above, 0 on, -1 below
+      auto decide = [&](int g, float tt) -> int {
         if (tt > eps3) return 1;
         if (tt < -eps3) return -1;
-        return exact3(p1, q1, p, q, g, b, D);
+        return exact3(p1, q1, p, q, g, g < f2 ? (int)rl[4 * g + 3] : (g >= f3 ? p : p1), D);
       };
-      bool below = false, on = false;
-      if (kill >= 0) {
-        const int i = kill_c;
-        const int pi = i == j + 1 ? p : (i == j ? p1 : cur.p(i)), qi = i == j + 1 ? q : (i == j ? q1 : cur.q(i));
-        if (kill != pi && kill != qi) below = verdict(kill, pi, nd(pi)) < 0;
-      }
-      for (int i = 0; i < K && !below; ++i) {
-        const int pi = i == j + 1 ? p : (i == j ? p1 : cur.p(i)), qi = i == j + 1 ? q : (i == j ? q1 : cur.q(i));
-        const float nb = nd(pi);
-        for (int g = sh->first[i]; g < sh->first[i + 1]; ++g) {
-          if (g == pi || g == qi) continue;
-          const int v = verdict(g, pi, nb);
-          if (v < 0) {
-            below = true;
-            kill = g;
-            kill_c = i;
-            break;
-          }
-          on |= v == 0;
+      bool below = kill >= 0 && !member(kill) && decide(kill, tval(kill)) == -1;
+      bool on = false;
+      for (int g = 0; g < N && !below; ++g) {
+        if (member(g)) continue;
+        const int v = decide(g, tval(g));
+        if (v == -1) {
+          below = true;
+          kill = g;
         }
+        on |= v == 0;
       }
       if (below) continue;
       if (on) {
         ++acc.ties;
         continue;
       }
-      if (!exact2)
-        det2 = (at(j, 0, q1) - at(j, 0, p1)) * (at(j, 1, q) - at(j, 1, p)) -
-               (at(j, 1, q1) - at(j, 1, p1)) * (at(j, 0, q) - at(j, 0, p));
+      if (!have2)
+        det2 = small2 ? (T)(int64_t)det2f
+                      : (at(j, 0, q1) - at(j, 0, p1)) * (at(j, 1, q) - at(j, 1, p)) -
+                            (at(j, 1, q1) - at(j, 1, p1)) * (at(j, 0, q) - at(j, 0, p));
       T ax = det2 / d;  // |det M| = |det2 / d|, an exact quotient
       ax = ax < 0 ? -ax : ax;
       acc.mv += (u128)ax;

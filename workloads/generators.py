@@ -214,6 +214,7 @@ MIXED_CONFIGS: Dict[str, Tuple[int, int, int]] = {
     "mixed_k3_p5": (3, 5, 0),    # 1,000 tuples of pairs: the oracle's size
     "mixed_k5_p6": (5, 6, 0),    # 759,375 tuples
     "mixed_k6_p7": (6, 7, 0),    # 85,766,121 tuples
+    "mixed_k6_p8": (6, 8, 0),    # 481,890,304 tuples: the profiled case
     "mixed_k7_p8": (7, 8, 0),    # 13,492,928,512 tuples: the benchmark's mixed workload
 }
 
