@@ -31,7 +31,7 @@ WORKLOAD = "single_n24_k8"
 # DRAM bytes (read + write) of one enumeration launch, from an ncu capture of the kernel built
 # from exactly these sources (profiles/k_enumerate_*.md); reported only while the library
 # sources still hash to the captured version, null otherwise.
-TRAFFIC = {"sources_sha256": "93cade78f3d9ee7af1afa022cd8a0d80db7ba2aa02906849f2eecbe8b6338bd8",
+TRAFFIC = {"sources_sha256": "4c5e5db3658ba52d8528820bd46484af652a3b26d5f670e7ce88a46b0fb4ab8d",
            "single_n24_k8": 1138176 + 0, "heavy_quiver_n32_k10": 8020480 + 0}
 
 
@@ -47,8 +47,8 @@ def sources_sha256() -> str:
         h.update(f.encode())
         with open(os.path.join(d, f), "rb") as fh:
             h.update(fh.read())
-    from paper_1501_02237_gb300 import build as B  # and the compiler flags
-    h.update(repr((B.ARCH, B.FLAGS)).encode())
+    from paper_1501_02237_gb300 import build as B  # and the compiler flags (paths relative to the repo)
+    h.update(repr((B.ARCH, [f.replace(B.ROOT, "<repo>") for f in B.FLAGS])).encode())
     return h.hexdigest()
 METRIC = "exact (k+1)-subsets tested/sec (exact degrees/sec alongside), 1 GB300"
 UNIT = "subsets/s"
@@ -489,7 +489,16 @@ def main():
         line["batch"] = batch_section(bd)
         line["serve"] = serve_section(bd)
         line["start_solutions"] = start_section(bd, P, seed=seed)
-        line["mixed_volume"] = mixed_section(bd, seed=seed)
+        mx = mixed_section(bd, seed=seed)
+        # the same convention for a tuple of pairs: the k x (k+1) lifted system of the pair rows
+        # (differences, Bareiss, back substitution) per tuple, against the same INT32 lane peak
+        km = mx["k"]
+        Em = sum((km - p) * (km + 1 - p) for p in range(1, km))
+        ops_t = km * (km + 1) + 4 * Em + km * km
+        ach = ops_t * mx["tuples_per_s"]
+        mx["roofline"] = dict(bound="alu", achieved=ach / 1e9, peak=peak_int32 / 1e9, unit="Gop/s",
+                              frac=ach / peak_int32, ops_per_tuple=ops_t)
+        line["mixed_volume"] = mx
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(s, subsets)
     if rank == 0:
