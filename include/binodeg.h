@@ -425,6 +425,36 @@ int bd_host_mixed_volume_lifted(const int64_t* points, const int32_t* counts, in
                                 int32_t team_width, int32_t force_int128, int32_t prefix_levels, int32_t leaf3,
                                 bd_mixed_out* out, int32_t* cells, int64_t capacity, int64_t* absdet);
 
+/* ---- output-sensitive volume by simplicial pivoting (Sec. 4.3, Eq. pivot) -------------- */
+
+/*
+ * NVol_k(conv points) by walking the cells of the lifting's triangulation from one to the next
+ * across their ridges (breadth first, on the GPU) instead of testing every (k+1)-subset: the
+ * work grows with the number of cells, not with C(npts, k+1).  The start cell is found by
+ * extension from the lowest lifted point; the neighbour across a ridge is the point beyond it
+ * of least height / (-barycentric coordinate), decided exactly.
+ *   points : npts x k integers, |x| < 2^20, k+1 <= npts <= 64, 1 <= k <= 30
+ *   seed   : lift seed (the heights of bd_volume for the same seed); a tie re-lifts (8 liftings)
+ *   out    : nvol, cells, ties, relifts, flags (BD_FLAG_DEGENERATE when not full-dimensional),
+ *            bound_bits; subsets holds the ridges examined, (k+1) * cells
+ *   device_ms : NULL, or the traversal's time on the GPU (CUDA events; all levels)
+ * Errors: BD_ERR_ARG, BD_ERR_OVERFLOW (cell minors beyond 62 bits), BD_ERR_TIES, BD_ERR_CUDA,
+ * BD_ERR_NOMEM (more than 2^29 cells).
+ */
+int bd_volume_pivot(const int64_t* points, int32_t npts, int32_t k, uint64_t seed, bd_volume_out* out,
+                    double* device_ms);
+
+/* The same traversal on the host with the given heights (|lift| < 2^30, no re-lift: a tie
+ * returns BD_ERR_TIES), one team of team_width lanes (1..32; more than 1 runs them as threads in
+ * lockstep), for CPU tests.  cells: NULL, or capacity bitmasks of the cells' points (bit p for
+ * point p), increasing; fewer than out->cells -> BD_ERR_ARG. */
+int bd_host_volume_pivot(const int64_t* points, const int64_t* lifts, int32_t npts, int32_t k, int32_t team_width,
+                         bd_volume_out* out, uint64_t* cells, int64_t capacity);
+
+/* bd_degree with the volume by pivoting: solution sets of dimension up to 30 (BD_NMAX - 1
+ * variables), e.g. the master spaces of Table mspace-deg beyond the reach of bd_degree. */
+int bd_degree_pivot(const int64_t* A, int32_t n, int32_t m, const int64_t* coef, uint64_t seed, bd_degree_out* out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -19,7 +19,8 @@ from ._lib import F32P, I32P, U8P
 
 __all__ = ["CostModel", "Server", "degree", "volume", "volume_noalloc", "volume_lifted", "classify", "reduce", "Plan", "Batch", "set_stream",
            "host_volume_lifted", "cells", "host_cells", "start_solutions", "host_start_solutions", "mixed_volume",
-           "mixed_volume_lifted", "host_mixed_volume_lifted", "BinodegError", "lib"]
+           "mixed_volume_lifted", "host_mixed_volume_lifted", "volume_pivot", "host_volume_pivot", "degree_pivot",
+           "BinodegError", "lib"]
 
 
 def set_stream(stream) -> None:
@@ -205,6 +206,47 @@ def host_volume_lifted(points, lifts, threads: int = 1, force_int128: bool = Fal
     if rc not in (0, 3):
         check(rc)
     return res
+
+
+def volume_pivot(points, seed: int = 0) -> dict:
+    """bd_volume_pivot: exact NVol_k(conv points) by simplicial pivoting over the cells on the GPU
+    (output-sensitive; k <= 30, up to 64 points); adds the traversal's GPU time as device_ms."""
+    P = i64(points)
+    npts, k = P.shape
+    out, ms = VolumeOut(), C.c_double(0)
+    check(lib().bd_volume_pivot(ptr(P), npts, k, C.c_uint64(seed), C.byref(out), C.byref(ms)))
+    res = out.as_dict()
+    res["device_ms"] = float(ms.value)
+    return res
+
+
+def host_volume_pivot(points, lifts, team_width: int = 1, cells: bool = False, capacity: int = 1 << 16) -> dict:
+    """bd_host_volume_pivot: the same traversal on the host with the given heights (CPU tests);
+    cells=True adds the cells as sorted tuples of point indices."""
+    P, W = i64(points), i64(lifts)
+    npts, k = P.shape
+    out = VolumeOut()
+    buf = np.zeros(max(capacity, 1), dtype=np.uint64)
+    rc = lib().bd_host_volume_pivot(ptr(P), ptr(W), npts, k, team_width, C.byref(out),
+                                    buf.ctypes.data_as(C.POINTER(C.c_uint64)) if cells else None, capacity)
+    res = out.as_dict()
+    res["status"] = rc
+    if rc not in (0, 3):
+        check(rc)
+    if cells and rc == 0:
+        res["cell_list"] = [tuple(i for i in range(64) if (int(m) >> i) & 1) for m in buf[: int(out.cells)]]
+    return res
+
+
+def degree_pivot(A, coef=None, seed: int = 0) -> dict:
+    """bd_degree_pivot: bd_degree with the volume by simplicial pivoting (solution sets of
+    dimension up to 30)."""
+    A = i64(A)
+    n, m = A.shape
+    c = _coef_array(coef, m)
+    out = DegreeOut()
+    check(lib().bd_degree_pivot(ptr(A), n, m, ptr(c) if c is not None else None, C.c_uint64(seed), C.byref(out)))
+    return out.as_dict()
 
 
 def _supports(supports):

@@ -1,0 +1,533 @@
+// Output-sensitive volume by simplicial pivoting (Sec. 4.3): the start cell (host), the
+// breadth-first traversal of the cells on the GPU (one warp per cell, a hash set of cell
+// bitmasks, one launch per level), its host emulation, and the C ABI (bd_volume_pivot,
+// bd_volume_pivot_lifted, bd_host_volume_pivot, bd_degree_pivot).  The per-cell step is in
+// bd_pivot.cuh.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <deque>
+#include <string>
+#include <thread>
+#include <unordered_set>
+#include <vector>
+
+#include "../../include/binodeg.h"
+#include "bd_host.h"
+#include "bd_internal.h"
+#include "bd_lifts.h"
+#include "bd_pivot.cuh"
+#include "bd_teams.h"
+
+using bd::i128;
+using bd::u128;
+
+namespace {
+
+constexpr int kPivotWarps = 4;  // warps per block
+
+struct PivotWarp {
+  __device__ int lane() const { return threadIdx.x & 31; }
+  __device__ int lanes() const { return 32; }
+  __device__ void sync() const { __syncwarp(); }
+};
+
+enum { START_OK = 0, START_TIE = 1, START_FLAT = 2, START_OVERFLOW = 3 };
+
+i128 iabs(i128 x) { return x < 0 ? -x : x; }
+
+i128 gcd128(i128 a, i128 b) {
+  a = iabs(a);
+  b = iabs(b);
+  while (b) {
+    const i128 t = a % b;
+    a = b;
+    b = t;
+  }
+  return a;
+}
+
+bool mul_ok(i128 a, i128 b, i128& r) { return !__builtin_mul_overflow(a, b, &r); }
+bool add_ok(i128 a, i128 b, i128& r) { return !__builtin_add_overflow(a, b, &r); }
+
+// A lower facet to start from, by extension (the paper's extension process, Sec. 4.2, done
+// here without a linear program): from the lowest lifted point, a lower face F with an integer
+// support function H(p) = c w_p - <A, a_p> - B (>= 0 on all points, 0 exactly on F) is tilted
+// about F in a direction u orthogonal to F's affine span until a further point joins:
+// H' = w_q H - H(q) <u, a_p - a_f0> for the point q minimising H(q) / <u, a_q - a_f0> among
+// those with <u, .> > 0.  d steps give a cell.  pts is row-major (npts x d).
+int start_cell(const int64_t* pts, const int64_t* lifts, int N, int d, uint64_t& mask) {
+  int v0 = 0;
+  for (int p = 1; p < N; ++p)
+    if (lifts[p] < lifts[v0]) v0 = p;
+  for (int p = 0; p < N; ++p)
+    if (p != v0 && lifts[p] == lifts[v0]) return START_TIE;
+  std::vector<int> F{v0};
+  i128 c = 1, B = lifts[v0];
+  std::vector<i128> A(d, 0);
+  std::vector<i128> H(N);
+  auto eval = [&]() {
+    for (int p = 0; p < N; ++p) {
+      i128 h = c * (i128)lifts[p] - B;
+      for (int e = 0; e < d; ++e) h -= A[e] * (i128)pts[p * d + e];
+      H[p] = h;
+    }
+  };
+  while ((int)F.size() < d + 1) {
+    const int j = (int)F.size() - 1, f0 = F[0];
+    // the difference rows of F, reduced by fraction-free Gauss-Jordan to find free columns
+    std::vector<std::vector<i128>> R(j, std::vector<i128>(d));
+    for (int r = 0; r < j; ++r)
+      for (int e = 0; e < d; ++e) R[r][e] = (i128)pts[F[r + 1] * d + e] - pts[f0 * d + e];
+    std::vector<int> pivcol;
+    i128 prev = 1;
+    for (int col = 0; col < d && (int)pivcol.size() < j; ++col) {
+      const int rk = (int)pivcol.size();
+      int r = rk;
+      while (r < j && R[r][col] == 0) ++r;
+      if (r == j) continue;
+      std::swap(R[r], R[rk]);
+      const i128 pk = R[rk][col];
+      for (int i = 0; i < j; ++i) {
+        if (i == rk) continue;
+        for (int e = 0; e < d; ++e) {
+          if (e == col) continue;
+          i128 t1, t2, t;
+          if (!mul_ok(pk, R[i][e], t1) || !mul_ok(R[i][col], R[rk][e], t2) || __builtin_sub_overflow(t1, t2, &t))
+            return START_OVERFLOW;
+          R[i][e] = t / prev;  // exact (Bareiss)
+        }
+        R[i][col] = 0;
+      }
+      prev = pk;
+      pivcol.push_back(col);
+    }
+    if ((int)pivcol.size() < j) return START_TIE;  // F not affinely independent
+    eval();
+    bool extended = false;
+    for (int fcol = 0; fcol < d && !extended; ++fcol) {
+      if (std::find(pivcol.begin(), pivcol.end(), fcol) != pivcol.end()) continue;
+      // u: prev at the free column, -R[r][fcol] at pivot column r (R's pivots all equal prev)
+      std::vector<i128> u(d, 0);
+      u[fcol] = prev;
+      for (int r = 0; r < j; ++r) u[pivcol[r]] = -R[r][fcol];
+      i128 g = 0;
+      for (int e = 0; e < d; ++e) g = gcd128(g, u[e]);
+      for (int e = 0; e < d; ++e) u[e] /= g;
+      std::vector<i128> w(N);
+      bool pos = false, neg = false;
+      for (int p = 0; p < N; ++p) {
+        i128 s = 0;
+        for (int e = 0; e < d; ++e) s += u[e] * ((i128)pts[p * d + e] - pts[f0 * d + e]);
+        w[p] = s;
+        pos |= s > 0;
+        neg |= s < 0;
+      }
+      if (!pos && !neg) continue;
+      const int sg = pos ? 1 : -1;
+      int q = -1;
+      for (int p = 0; p < N; ++p) {
+        if (sg * w[p] <= 0) continue;
+        if (H[p] <= 0) return START_TIE;  // a point on the face's plane outside the face
+        if (q < 0) {
+          q = p;
+          continue;
+        }
+        // H[p] / (sg w[p]) against H[q] / (sg w[q])
+        if (bd::prod_equal(H[p], sg * w[q], H[q], sg * w[p])) return START_TIE;
+        if (bd::prod_greater(H[q], sg * w[p], H[p], sg * w[q])) q = p;
+      }
+      const i128 wq = sg * w[q], hq = H[q];
+      i128 nc, t, t2;
+      if (!mul_ok(wq, c, nc)) return START_OVERFLOW;
+      std::vector<i128> nA(d);
+      for (int e = 0; e < d; ++e) {
+        if (!mul_ok(wq, A[e], t) || !mul_ok(hq * sg, u[e], t2) || !add_ok(t, t2, nA[e])) return START_OVERFLOW;
+      }
+      i128 uf0 = 0;
+      for (int e = 0; e < d; ++e) uf0 += u[e] * (i128)pts[f0 * d + e];
+      i128 nB;
+      if (!mul_ok(wq, B, t) || !mul_ok(hq * sg, uf0, t2) || __builtin_sub_overflow(t, t2, &nB)) return START_OVERFLOW;
+      i128 gg = gcd128(nc, nB);
+      for (int e = 0; e < d; ++e) gg = gcd128(gg, nA[e]);
+      c = nc / gg;
+      B = nB / gg;
+      for (int e = 0; e < d; ++e) A[e] = nA[e] / gg;
+      F.push_back(q);
+      extended = true;
+    }
+    if (!extended) return START_FLAT;  // every point lies in F's affine span
+  }
+  eval();
+  mask = 0;
+  for (int f : F) mask |= 1ull << f;
+  for (int p = 0; p < N; ++p)
+    if (!((mask >> p) & 1) && H[p] <= 0) return START_TIE;
+  return START_OK;
+}
+
+// log2 of a Hadamard bound on every d x d minor of [M^T | a_p - a_s0] over all cells: each
+// column is a difference of two points
+double pivot_bound_log2(const int64_t* pts, int N, int d) {
+  double best = 0;
+  for (int a = 0; a < N; ++a)
+    for (int b = a + 1; b < N; ++b) {
+      double s = 0;
+      for (int e = 0; e < d; ++e) {
+        const double x = (double)(pts[b * d + e] - pts[a * d + e]);
+        s += x * x;
+      }
+      best = std::max(best, s);
+    }
+  return 0.5 * d * std::log2(std::max(best, 1.0));
+}
+
+__host__ __device__ size_t pivot_warp_bytes(int N, int d) {
+  size_t b = sizeof(bd::PivotScratch);
+  b = (b + 15) / 16 * 16 + 16 * (size_t)N;    // S: heights (i128)
+  b += 8 * (size_t)N;                         // G0
+  b += 8 * (size_t)d * (d + N);               // W
+  return (b + 15) / 16 * 16;
+}
+
+size_t pivot_smem(int N, int d) { return ((8 * (size_t)(d + 1) * N + 15) / 16 * 16) + kPivotWarps * pivot_warp_bytes(N, d); }
+
+struct PivotDev {
+  unsigned long long nvol_lo, nvol_hi, cells, boundary, next_count, flags;
+};
+
+enum { PF_TIE = 1, PF_INVALID = 2, PF_FULL = 4 };
+
+__device__ void table_insert(unsigned long long* table, unsigned long long cap, unsigned long long m,
+                             unsigned long long* next, PivotDev* dv) {
+  unsigned long long h = bd::pivot_hash(m) & (cap - 1);
+  for (unsigned long long probe = 0; probe < cap; ++probe) {
+    const unsigned long long old = atomicCAS(table + h, 0ull, m);
+    if (old == 0ull) {
+      const unsigned long long pos = atomicAdd(&dv->next_count, 1ull);
+      if (pos < cap) next[pos] = m;
+      else atomicOr(&dv->flags, (unsigned long long)PF_FULL);
+      return;
+    }
+    if (old == m) return;
+    h = (h + 1) & (cap - 1);
+  }
+  atomicOr(&dv->flags, (unsigned long long)PF_FULL);
+}
+
+// One breadth-first level: every cell of `cur` is processed by one warp; its new neighbours
+// enter the table and `next`.
+__global__ void __launch_bounds__(32 * kPivotWarps) k_pivot(const int64_t* pts, const int64_t* lifts, int N, int d,
+                                                            const unsigned long long* cur, unsigned long long ncur,
+                                                            unsigned long long* table, unsigned long long cap,
+                                                            unsigned long long* next, PivotDev* dv) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  int64_t* P = reinterpret_cast<int64_t*>(smem);  // coordinate-major, then the lifts
+  int64_t* L = P + (size_t)d * N;
+  for (int i = threadIdx.x; i < d * N; i += blockDim.x) P[i] = pts[(i % N) * d + i / N];
+  for (int i = threadIdx.x; i < N; i += blockDim.x) L[i] = lifts[i];
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  unsigned char* wb = smem + ((8 * (size_t)(d + 1) * N + 15) / 16 * 16) + warp * pivot_warp_bytes(N, d);
+  auto* sc = reinterpret_cast<bd::PivotScratch*>(wb);
+  size_t at = (sizeof(bd::PivotScratch) + 15) / 16 * 16;
+  i128* S = reinterpret_cast<i128*>(wb + at);
+  at += 16 * (size_t)N;
+  int64_t* G0 = reinterpret_cast<int64_t*>(wb + at);
+  at += 8 * (size_t)N;
+  int64_t* W = reinterpret_cast<int64_t*>(wb + at);
+  PivotWarp tm;
+  bd::PivotAcc acc{};
+  int flags = 0;
+  const unsigned long long gw = (unsigned long long)blockIdx.x * kPivotWarps + warp;
+  const unsigned long long nw = (unsigned long long)gridDim.x * kPivotWarps;
+  for (unsigned long long c = gw; c < ncur; c += nw) {
+    flags |= bd::pivot_cell(tm, P, L, N, d, cur[c], W, S, G0, sc, acc,
+                            [&](uint64_t m) { table_insert(table, cap, m, next, dv); });
+  }
+  if (lane == 0) {
+    const unsigned long long lo = (uint64_t)acc.nvol, hi = (uint64_t)(acc.nvol >> 64);
+    if (lo || hi) {
+      const unsigned long long old = atomicAdd(&dv->nvol_lo, lo);
+      const unsigned long long carry = (old + lo < old) ? 1ull : 0ull;
+      if (hi + carry) atomicAdd(&dv->nvol_hi, hi + carry);
+    }
+    if (acc.cells) atomicAdd(&dv->cells, (unsigned long long)acc.cells);
+    if (acc.boundary) atomicAdd(&dv->boundary, (unsigned long long)acc.boundary);
+    if (flags & bd::PV_TIE) atomicOr(&dv->flags, (unsigned long long)PF_TIE);
+    if (flags & bd::PV_INVALID) atomicOr(&dv->flags, (unsigned long long)PF_INVALID);
+  }
+}
+
+__global__ void k_pivot_seed(unsigned long long* table, unsigned long long cap, unsigned long long m,
+                             unsigned long long* frontier) {
+  table[bd::pivot_hash(m) & (cap - 1)] = m;
+  frontier[0] = m;
+}
+
+struct PivotRun {
+  u128 nvol = 0;
+  uint64_t cells = 0, boundary = 0;
+  int flags = 0;  // PF_*
+  int levels = 0;
+  double ms = 0;
+  std::vector<uint64_t> masks;  // host emulation: every cell
+};
+
+// The traversal on the GPU from `start`; the table grows (and the traversal restarts) while it
+// would be more than half full.
+int device_pivot(const int64_t* pts, const int64_t* lifts, int N, int d, uint64_t start, PivotRun& run) {
+  cudaStream_t st = bd::thread_stream();
+  int dev = 0, sms = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  const size_t smem = pivot_smem(N, d);
+  if (smem > (size_t)optin) return bd::set_error(BD_ERR_ARG, "the pivoting state exceeds shared memory");
+  cudaError_t e = cudaFuncSetAttribute(k_pivot, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int per_sm = 0;
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pivot, 32 * kPivotWarps, smem);
+  if (e != cudaSuccess) return bd::set_error(BD_ERR_CUDA, cudaGetErrorString(e));
+  per_sm = std::max(per_sm, 1);
+  for (unsigned long long cap = 1ull << 20; cap <= (1ull << 30); cap <<= 2) {
+    int64_t *d_pts = nullptr, *d_lifts = nullptr;
+    unsigned long long *d_table = nullptr, *d_a = nullptr, *d_b = nullptr;
+    PivotDev* d_dv = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    auto release = [&]() {
+      cudaFree(d_pts);
+      cudaFree(d_lifts);
+      cudaFree(d_table);
+      cudaFree(d_a);
+      cudaFree(d_b);
+      cudaFree(d_dv);
+      if (e0) cudaEventDestroy(e0);
+      if (e1) cudaEventDestroy(e1);
+    };
+    e = cudaMalloc(&d_pts, sizeof(int64_t) * N * d);
+    if (e == cudaSuccess) e = cudaMalloc(&d_lifts, sizeof(int64_t) * N);
+    if (e == cudaSuccess) e = cudaMalloc(&d_table, sizeof(unsigned long long) * cap);
+    if (e == cudaSuccess) e = cudaMalloc(&d_a, sizeof(unsigned long long) * cap);
+    if (e == cudaSuccess) e = cudaMalloc(&d_b, sizeof(unsigned long long) * cap);
+    if (e == cudaSuccess) e = cudaMalloc(&d_dv, sizeof(PivotDev));
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_pts, pts, sizeof(int64_t) * N * d, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_lifts, lifts, sizeof(int64_t) * N, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_table, 0, sizeof(unsigned long long) * cap, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_dv, 0, sizeof(PivotDev), st);
+    if (e == cudaSuccess) {
+      k_pivot_seed<<<1, 1, 0, st>>>(d_table, cap, start, d_a);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+    unsigned long long ncur = 1, total = 1;
+    PivotDev h{};
+    run.levels = 0;
+    while (e == cudaSuccess && ncur > 0) {
+      const unsigned long long zero = 0;
+      e = cudaMemcpyAsync(&d_dv->next_count, &zero, sizeof(zero), cudaMemcpyHostToDevice, st);
+      const unsigned long long blocks =
+          std::min<unsigned long long>((unsigned long long)sms * per_sm, (ncur + kPivotWarps - 1) / kPivotWarps);
+      if (e == cudaSuccess) {
+        k_pivot<<<(unsigned int)blocks, 32 * kPivotWarps, smem, st>>>(d_pts, d_lifts, N, d, d_a, ncur, d_table, cap,
+                                                                       d_b, d_dv);
+        e = cudaGetLastError();
+      }
+      if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d_dv, sizeof(h), cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      ++run.levels;
+      if (e != cudaSuccess || h.flags) break;
+      ncur = h.next_count;
+      total += ncur;
+      if (2 * total > cap) {  // too full for cheap probing: restart with a larger table
+        h.flags = PF_FULL;
+        break;
+      }
+      std::swap(d_a, d_b);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    release();
+    if (e != cudaSuccess) return bd::set_error(BD_ERR_CUDA, cudaGetErrorString(e));
+    if (h.flags & PF_FULL) continue;
+    run.nvol = ((u128)h.nvol_hi << 64) | h.nvol_lo;
+    run.cells = h.cells;
+    run.boundary = h.boundary;
+    run.flags = (int)h.flags;
+    run.ms = ms;
+    return BD_OK;
+  }
+  return bd::set_error(BD_ERR_NOMEM, "more than 2^29 cells");
+}
+
+// The same traversal on the host: one team (one lane, or `width` lanes run as threads in
+// lockstep), cells in breadth-first order.
+int host_pivot(const int64_t* pts, const int64_t* lifts, int N, int d, uint64_t start, int width, PivotRun& run) {
+  std::vector<int64_t> P((size_t)d * N);
+  for (int r = 0; r < d; ++r)
+    for (int p = 0; p < N; ++p) P[(size_t)r * N + p] = pts[p * d + r];
+  std::vector<int64_t> W((size_t)d * (d + N)), G0(N);
+  std::vector<i128> S(N);
+  bd::PivotScratch sc{};
+  std::unordered_set<uint64_t> seen{start};
+  std::vector<uint64_t> cur{start}, next;
+  bd::PivotAcc acc{};
+  int flags = 0;
+  auto step = [&](auto tm, std::vector<uint64_t>& out) {
+    for (uint64_t m : cur) {
+      const int f = bd::pivot_cell(tm, P.data(), lifts, N, d, m, W.data(), S.data(), G0.data(), &sc, acc,
+                                   [&](uint64_t nb) {
+                                     if (seen.insert(nb).second) out.push_back(nb);
+                                   });
+      if (tm.lane() == 0) flags |= f;
+    }
+  };
+  while (!cur.empty() && !flags) {
+    next.clear();
+    if (width <= 1) {
+      step(bd::HostTeam{}, next);
+    } else {
+      bd::LockstepShared shl(width);
+      std::vector<std::thread> th;
+      for (int l = 1; l < width; ++l) th.emplace_back([&, l] {
+        std::vector<uint64_t> sink;  // only lane 0 inserts
+        step(bd::LockstepTeam{&shl, l}, sink);
+      });
+      step(bd::LockstepTeam{&shl, 0}, next);
+      for (auto& t : th) t.join();
+    }
+    run.masks.insert(run.masks.end(), cur.begin(), cur.end());
+    ++run.levels;
+    cur.swap(next);
+  }
+  run.nvol = acc.nvol;
+  run.cells = acc.cells;
+  run.boundary = acc.boundary;
+  run.flags = (flags & bd::PV_TIE ? PF_TIE : 0) | (flags & bd::PV_INVALID ? PF_INVALID : 0);
+  std::sort(run.masks.begin(), run.masks.end());
+  return BD_OK;
+}
+
+int pivot_common(const int64_t* points, const int64_t* given_lifts, int32_t npts, int32_t k, uint64_t seed,
+                 int host_width, bd_volume_out* out, uint64_t* cells, int64_t capacity, double* device_ms) {
+  if (!out || !points) return bd::set_error(BD_ERR_ARG, "NULL argument");
+  std::memset(out, 0, sizeof(*out));
+  if (k < 1 || k > bd::kPivotDMax) return bd::set_error(BD_ERR_ARG, "need 1 <= k <= 30 for the pivoting path");
+  if (npts < k + 1 || npts > 64) return bd::set_error(BD_ERR_ARG, "need k+1 <= npts <= 64");
+  for (int i = 0; i < npts * k; ++i)
+    if (points[i] >= (1 << 20) || points[i] <= -(1 << 20))
+      return bd::set_error(BD_ERR_ARG, "coordinates must stay below 2^20 in magnitude on the pivoting path");
+  const double bits = pivot_bound_log2(points, npts, k);
+  out->bound_bits = (int32_t)std::ceil(bits);
+  if (bits >= 61.99) return bd::set_error(BD_ERR_OVERFLOW, "cell minors may leave 62 bits");
+  std::vector<int64_t> lifts(npts);
+  const int attempts = given_lifts ? 1 : 8;
+  for (int a = 0; a < attempts; ++a) {
+    if (given_lifts) {
+      for (int i = 0; i < npts; ++i) {
+        if (given_lifts[i] >= (1 << 30) || given_lifts[i] <= -(1 << 30))
+          return bd::set_error(BD_ERR_ARG, "lifts must stay below 2^30 in magnitude on the pivoting path");
+        lifts[i] = given_lifts[i];
+      }
+    } else {
+      const uint64_t ss = bd::lift_stream_seed(seed, (uint32_t)a);
+      for (int i = 0; i < npts; ++i) lifts[i] = bd::lift_height(ss, i);
+    }
+    out->relifts = a;
+    uint64_t start = 0;
+    const int sr = start_cell(points, lifts.data(), npts, k, start);
+    if (sr == START_FLAT) {
+      out->flags = BD_FLAG_DEGENERATE;
+      return BD_OK;
+    }
+    if (sr == START_OVERFLOW) return bd::set_error(BD_ERR_OVERFLOW, "the start cell's support function left 128 bits");
+    if (sr == START_TIE) {
+      out->ties = 1;
+      continue;
+    }
+    PivotRun run;
+    const int rc = host_width > 0 ? host_pivot(points, lifts.data(), npts, k, start, host_width, run)
+                                  : device_pivot(points, lifts.data(), npts, k, start, run);
+    if (rc) return rc;
+    if (run.flags & PF_INVALID) return bd::set_error(BD_ERR_ARG, "pivoting reached a non-cell (internal error)");
+    if (run.flags & PF_TIE) {
+      out->ties = 1;
+      continue;
+    }
+    out->ties = 0;
+    out->nvol_lo = (uint64_t)run.nvol;
+    out->nvol_hi = (uint64_t)(run.nvol >> 64);
+    out->cells = run.cells;
+    out->subsets = run.cells * (uint64_t)(k + 1);  // ridges examined
+    if (device_ms) *device_ms = run.ms;
+    if (cells) {
+      if ((int64_t)run.masks.size() > capacity)
+        return bd::set_error(BD_ERR_ARG, "capacity is below the number of cells (out->cells holds it)");
+      std::copy(run.masks.begin(), run.masks.end(), cells);
+    }
+    return BD_OK;
+  }
+  return bd::set_error(BD_ERR_TIES, given_lifts ? "the given lifting is not generic" : "every lifting had a tie");
+}
+
+}  // namespace
+
+extern "C" {
+
+int bd_volume_pivot(const int64_t* points, int32_t npts, int32_t k, uint64_t seed, bd_volume_out* out,
+                    double* device_ms) {
+  return pivot_common(points, nullptr, npts, k, seed, 0, out, nullptr, 0, device_ms);
+}
+
+int bd_host_volume_pivot(const int64_t* points, const int64_t* lifts, int32_t npts, int32_t k, int32_t team_width,
+                         bd_volume_out* out, uint64_t* cells, int64_t capacity) {
+  if (!lifts) return bd::set_error(BD_ERR_ARG, "NULL argument");
+  if (team_width < 1 || team_width > 32) return bd::set_error(BD_ERR_ARG, "team width must be 1..32");
+  if (cells && capacity < 0) return bd::set_error(BD_ERR_ARG, "negative capacity");
+  return pivot_common(points, lifts, npts, k, 0, team_width, out, cells, capacity, nullptr);
+}
+
+int bd_degree_pivot(const int64_t* A, int32_t n, int32_t m, const int64_t* coef, uint64_t seed, bd_degree_out* out) {
+  if (!out) return bd::set_error(BD_ERR_ARG, "out is NULL");
+  if (!A && m > 0) return bd::set_error(BD_ERR_ARG, "A is NULL");
+  if (n < 1 || n >= BD_NMAX || m < 0 || m > 256) return bd::set_error(BD_ERR_ARG, "need 1 <= n < BD_NMAX, 0 <= m <= 256");
+  std::memset(out, 0, sizeof(*out));
+  bd::Reduction r;
+  std::string err;
+  int rc = bd::reduce_system(A, n, m, coef, r, err);
+  if (rc) return bd::set_error(rc, err.c_str());
+  out->rank = r.rank;
+  out->dim = r.dim;
+  out->torsion = r.torsion;
+  out->consistent = r.consistent ? 1 : 0;
+  out->max_abs_coord = (int32_t)r.max_abs_coord;
+  if (!r.consistent) {
+    out->flags = BD_FLAG_INCONSISTENT;
+    return BD_OK;
+  }
+  u128 nvol = 1;
+  if (r.dim >= 1) {
+    bd_volume_out v;
+    rc = pivot_common(r.points.data(), nullptr, n + 1, r.dim, seed, 0, &v, nullptr, 0, nullptr);
+    if (rc) return rc;
+    nvol = ((u128)v.nvol_hi << 64) | v.nvol_lo;
+    out->relifts = v.relifts;
+    out->subsets = v.subsets;
+    out->cells = v.cells;
+    out->flags = v.flags;
+  }
+  const u128 deg = nvol * r.torsion;
+  if (r.torsion && deg / r.torsion != nvol) return bd::set_error(BD_ERR_OVERFLOW, "degree exceeds 2^128");
+  out->nvol_lo = (uint64_t)nvol;
+  out->nvol_hi = (uint64_t)(nvol >> 64);
+  out->degree_lo = (uint64_t)deg;
+  out->degree_hi = (uint64_t)(deg >> 64);
+  return BD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,81 @@
+"""Simplicial pivoting (bd_pivot.cuh) through its host emulation: the cells it walks are exactly
+the oracle's lower facets of the same lifting (oracle/cells.py, rational arithmetic) and its
+volume the oracle's placing-triangulation volume, for one-lane teams and a lockstep team of 7
+lanes; the master-space degrees of Table mspace-deg far beyond the subset enumeration
+(W_{2,6}, W_{3,4}, W_{4,3}, W_{2,7}: 9.4e9 and 4.2e11 subsets); degenerate inputs, ties and
+argument errors."""
+
+import json
+import os
+import random
+
+import numpy as np
+import pytest
+
+import paper_1501_02237_gb300 as bd
+from oracle.cells import lower_cells
+from oracle.lifts import lifts as oracle_lifts
+from oracle.volume import nvol_placing
+from workloads import master_space_system
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+TABLE = json.load(open(os.path.join(ROOT, "tests", "golden", "master_space_table.json")))
+
+
+@pytest.mark.parametrize("seed", range(24))
+def test_host_pivot_cells_match_oracle(seed):
+    rng = random.Random(7300 + seed)
+    k = rng.choice([1, 2, 3, 4, 5])
+    n = rng.randint(k + 2, 11)
+    pts = [tuple(rng.randint(-2, 2) for _ in range(k)) for _ in range(n)]
+    W = oracle_lifts(n, seed)
+    ref = lower_cells(pts, W)
+    for width in (1, 7):
+        r = bd.host_volume_pivot(np.array(pts), W, team_width=width, cells=True)
+        if r["flags"] & bd.BD_FLAG_DEGENERATE:
+            assert nvol_placing(pts) == 0
+            continue
+        assert r["status"] == 0
+        assert set(r["cell_list"]) == {tuple(sorted(c[0])) for c in ref}
+        assert r["nvol"] == sum(c[1] for c in ref) == nvol_placing(pts)
+        assert r["cells"] == len(ref) and r["subsets"] == (k + 1) * len(ref)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_host_pivot_larger_sets_match_placing(seed):
+    rng = random.Random(7400 + seed)
+    k = rng.choice([3, 4, 5, 6])
+    n = rng.randint(12, 20)
+    pts = [tuple(rng.randint(-3, 3) for _ in range(k)) for _ in range(n)]
+    r = bd.host_volume_pivot(np.array(pts), oracle_lifts(n, seed))
+    if r["status"] == 0:
+        assert r["nvol"] == nvol_placing(pts)
+
+
+@pytest.mark.parametrize("mk", ["3,3", "2,5", "2,6", "3,4", "4,3", "2,7"])
+def test_host_pivot_master_space_table(mk):
+    m, k = map(int, mk.split(","))
+    s = master_space_system(m, k)
+    red = bd.reduce(s.A)
+    P = red["points"]
+    r = bd.host_volume_pivot(P, oracle_lifts(P.shape[0], 0))
+    assert r["status"] == 0
+    assert r["nvol"] * red["torsion"] == TABLE["degree"][mk]
+
+
+def test_host_pivot_degenerate_ties_and_errors():
+    # points on a plane in Z^3: not full-dimensional
+    flat = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [1, 1, 0], [2, 1, 0]])
+    r = bd.host_volume_pivot(flat, [1, 5, 2, 9, 4])
+    assert r["nvol"] == 0 and r["flags"] & bd.BD_FLAG_DEGENERATE
+    # constant heights on the unit square: the two triangulations tie
+    sq = np.array([[0, 0], [1, 0], [0, 1], [1, 1]])
+    assert bd.host_volume_pivot(sq, [5, 5, 5, 5])["status"] == 3
+    # affine heights (x + y): all four lifted points on one plane
+    assert bd.host_volume_pivot(sq, [0, 1, 1, 2])["status"] == 3
+    with pytest.raises(bd.BinodegError):
+        bd.host_volume_pivot(np.zeros((3, 31), dtype=np.int64), [1, 2, 3])  # k above 30
+    with pytest.raises(bd.BinodegError):
+        bd.host_volume_pivot(np.array([[0], [1 << 21]]), [1, 2])  # coordinate range
+    with pytest.raises(bd.BinodegError):
+        bd.host_volume_pivot(sq, [1, 2, 3, 4], team_width=40)
