@@ -425,7 +425,7 @@ int bd_host_mixed_volume_lifted(const int64_t* points, const int32_t* counts, in
                                 int32_t team_width, int32_t force_int128, int32_t prefix_levels, int32_t leaf3,
                                 bd_mixed_out* out, int32_t* cells, int64_t capacity, int64_t* absdet);
 
-/* ---- output-sensitive volume by simplicial pivoting (Sec. 4.3, Eq. pivot) -------------- */
+/* ---- output-sensitive volume by simplicial pivoting (Sec. 4.2, Eq. pivot) -------------- */
 
 /*
  * NVol_k(conv points) by walking the cells of the lifting's triangulation from one to the next

@@ -1,4 +1,4 @@
-// Output-sensitive volume by simplicial pivoting (Sec. 4.3): the start cell (host), the
+// Output-sensitive volume by simplicial pivoting (Sec. 4.2): the start cell (host), the
 // breadth-first traversal of the cells on the GPU (one warp per cell, a hash set of cell
 // bitmasks, one launch per level), its host emulation, and the C ABI (bd_volume_pivot,
 // bd_volume_pivot_lifted, bd_host_volume_pivot, bd_degree_pivot).  The per-cell step is in
@@ -52,7 +52,7 @@ i128 gcd128(i128 a, i128 b) {
 bool mul_ok(i128 a, i128 b, i128& r) { return !__builtin_mul_overflow(a, b, &r); }
 bool add_ok(i128 a, i128 b, i128& r) { return !__builtin_add_overflow(a, b, &r); }
 
-// A lower facet to start from, by extension (the paper's extension process, Sec. 4.2, done
+// A lower facet to start from, by extension (the paper's extension process, Sec. 4.1, done
 // here without a linear program): from the lowest lifted point, a lower face F with an integer
 // support function H(p) = c w_p - <A, a_p> - B (>= 0 on all points, 0 exactly on F) is tilted
 // about F in a direction u orthogonal to F's affine span until a further point joins:
@@ -168,20 +168,27 @@ int start_cell(const int64_t* pts, const int64_t* lifts, int N, int d, uint64_t&
   return START_OK;
 }
 
-// log2 of a Hadamard bound on every d x d minor of [M^T | a_p - a_s0] over all cells: each
-// column is a difference of two points
+// log2 of a Hadamard bound on every minor (of order <= d) of [M^T | a_p - a_s0] over all cells:
+// every column is a_x - a_s0 for one base s0 and distinct points x, so a minor is at most the
+// product of the d largest norms ||a_x - a_s0|| (each taken >= 1), maximised over s0
 double pivot_bound_log2(const int64_t* pts, int N, int d) {
   double best = 0;
-  for (int a = 0; a < N; ++a)
-    for (int b = a + 1; b < N; ++b) {
+  std::vector<double> lg(N);
+  for (int s0 = 0; s0 < N; ++s0) {
+    for (int x = 0; x < N; ++x) {
       double s = 0;
       for (int e = 0; e < d; ++e) {
-        const double x = (double)(pts[b * d + e] - pts[a * d + e]);
-        s += x * x;
+        const double v = (double)(pts[x * d + e] - pts[s0 * d + e]);
+        s += v * v;
       }
-      best = std::max(best, s);
+      lg[x] = 0.5 * std::log2(std::max(s, 1.0));
     }
-  return 0.5 * d * std::log2(std::max(best, 1.0));
+    std::sort(lg.begin(), lg.end(), [](double u, double v) { return u > v; });
+    double t = 0;
+    for (int i = 0; i < d && i < N; ++i) t += lg[i];
+    best = std::max(best, t);
+  }
+  return best;
 }
 
 __host__ __device__ size_t pivot_warp_bytes(int N, int d) {

@@ -1,4 +1,4 @@
-// Output-sensitive enumeration of the lifting's cells by simplicial pivoting (Sec. 4.3,
+// Output-sensitive enumeration of the lifting's cells by simplicial pivoting (Sec. 4.2,
 // Eq. pivot), shared by the CUDA warp kernel and its host emulation.
 //
 // A cell is a lower facet {s_0 < .. < s_d} of the lifted points (Eq. lower-d-face).  Dropping
