@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD, help="single system timed (profiling runs use the others)")
     ap.add_argument("--mixed-only", default=None, metavar="WORKLOAD",
                     help="run only the mixed-volume section on this workload (profiling runs)")
+    ap.add_argument("--pivot-only", default=None, metavar="M,K",
+                    help="run only the pivoting section on the master space W_{M,K} (profiling runs)")
     return ap.parse_args()
 
 
@@ -267,6 +269,35 @@ def mixed_section(bd, name=MIXED_WORKLOAD, seed=0, runs=3, cpu_seconds=5.0):
                                   sample=f"{done} random tuples through oracle.mixed.cell_status ({cpu_seconds:.0f} s)"))
 
 
+PIVOT_WORKLOADS = ("4,4", "3,6", "4,5")
+
+
+def pivot_section(bd, systems=PIVOT_WORKLOADS, seed=0):
+    """Output-sensitive degrees by simplicial pivoting (Sec. 4.2) of master spaces of Table
+    mspace-deg that the subset enumeration cannot reach (W_{4,4}: 1.9e13 subsets, W_{3,6}: 8.4e14,
+    W_{4,5}: 3.7e16): per system the exact degree against the table, cells walked per second on
+    the GPU and the time of the public call bd_degree_pivot(A)."""
+    from workloads import master_space_system
+
+    table = json.load(open(os.path.join(ROOT, "tests", "golden", "master_space_table.json")))["degree"]
+    out = {}
+    for mk in systems:
+        m, k = map(int, mk.split(","))
+        s = master_space_system(m, k)
+        red = bd.reduce(s.A)
+        P = red["points"]
+        v = bd.volume_pivot(P, seed=seed)  # warm-up and device time
+        t0 = time.perf_counter()
+        r = bd.degree_pivot(s.A, s.coef, seed=seed)
+        call = time.perf_counter() - t0
+        out[f"W{m},{k}"] = dict(points=int(P.shape[0]), dim=int(P.shape[1]),
+                               subsets=float(math.comb(P.shape[0], P.shape[1] + 1)), degree=r["degree"],
+                               table=table.get(mk), exact_match=r["degree"] == table.get(mk), cells=v["cells"],
+                               relifts=v["relifts"], device_ms=v["device_ms"],
+                               cells_per_s=v["cells"] / (v["device_ms"] / 1e3), call_s=call)
+    return out
+
+
 def serve_section(bd, rate=200.0, count=1000, train_count=20000):
     """Cost model trained on method-generated runs, then a Poisson stream served with continuous
     batching (n ~ U[12,30], k ~ U[4,10]); p50/p99 latency and degrees/s per admission policy."""
@@ -357,6 +388,9 @@ def main():
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
     bd.set_stream(stream)
+    if args.pivot_only:
+        print(json.dumps(pivot_section(bd, systems=(args.pivot_only,), seed=args.seed)), flush=True)
+        return
     if args.mixed_only:
         print(json.dumps(mixed_section(bd, name=args.mixed_only, seed=args.seed, runs=1, cpu_seconds=0.0)), flush=True)
         return
@@ -499,6 +533,7 @@ def main():
         mx["roofline"] = dict(bound="alu", achieved=ach / 1e9, peak=peak_int32 / 1e9, unit="Gop/s",
                               frac=ach / peak_int32, ops_per_tuple=ops_t)
         line["mixed_volume"] = mx
+        line["pivoting"] = pivot_section(bd, seed=seed)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(s, subsets)
     if rank == 0:

@@ -439,7 +439,7 @@ int bd_host_mixed_volume_lifted(const int64_t* points, const int32_t* counts, in
  *            bound_bits; subsets holds the ridges examined, (k+1) * cells
  *   device_ms : NULL, or the traversal's time on the GPU (CUDA events; all levels)
  * Errors: BD_ERR_ARG, BD_ERR_OVERFLOW (cell minors beyond 62 bits), BD_ERR_TIES, BD_ERR_CUDA,
- * BD_ERR_NOMEM (more than 2^29 cells).
+ * BD_ERR_NOMEM (more than 2^30 cells).
  */
 int bd_volume_pivot(const int64_t* points, int32_t npts, int32_t k, uint64_t seed, bd_volume_out* out,
                     double* device_ms);

@@ -207,18 +207,28 @@ struct PivotDev {
 
 enum { PF_TIE = 1, PF_INVALID = 2, PF_FULL = 4 };
 
-__device__ void table_insert(unsigned long long* table, unsigned long long cap, unsigned long long m,
-                             unsigned long long* next, PivotDev* dv) {
+constexpr unsigned long long kMaxProbes = 4096;  // linear probing below half load: ~2.5 on average
+
+// Insert m unless present.  The table stays at most half full (`filled` cells entered before
+// this level); past that, or after kMaxProbes, the level reports PF_FULL and the traversal is
+// restarted with a larger table.
+__device__ void table_insert(unsigned long long* table, unsigned long long cap, unsigned long long filled,
+                             unsigned long long m, unsigned long long* next, PivotDev* dv) {
   unsigned long long h = bd::pivot_hash(m) & (cap - 1);
-  for (unsigned long long probe = 0; probe < cap; ++probe) {
-    const unsigned long long old = atomicCAS(table + h, 0ull, m);
-    if (old == 0ull) {
-      const unsigned long long pos = atomicAdd(&dv->next_count, 1ull);
-      if (pos < cap) next[pos] = m;
-      else atomicOr(&dv->flags, (unsigned long long)PF_FULL);
-      return;
+  for (unsigned long long probe = 0; probe < kMaxProbes; ++probe) {
+    const unsigned long long cur = table[h];
+    if (cur == m) return;
+    if (cur == 0ull) {
+      if (2 * (filled + *(volatile unsigned long long*)&dv->next_count) >= cap) break;  // too full
+      const unsigned long long old = atomicCAS(table + h, 0ull, m);
+      if (old == 0ull) {
+        const unsigned long long pos = atomicAdd(&dv->next_count, 1ull);
+        if (pos < cap) next[pos] = m;
+        else atomicOr(&dv->flags, (unsigned long long)PF_FULL);
+        return;
+      }
+      if (old == m) return;
     }
-    if (old == m) return;
     h = (h + 1) & (cap - 1);
   }
   atomicOr(&dv->flags, (unsigned long long)PF_FULL);
@@ -229,7 +239,8 @@ __device__ void table_insert(unsigned long long* table, unsigned long long cap, 
 __global__ void __launch_bounds__(32 * kPivotWarps) k_pivot(const int64_t* pts, const int64_t* lifts, int N, int d,
                                                             const unsigned long long* cur, unsigned long long ncur,
                                                             unsigned long long* table, unsigned long long cap,
-                                                            unsigned long long* next, PivotDev* dv) {
+                                                            unsigned long long filled, unsigned long long* next,
+                                                            PivotDev* dv) {
   extern __shared__ __align__(16) unsigned char smem[];
   int64_t* P = reinterpret_cast<int64_t*>(smem);  // coordinate-major, then the lifts
   int64_t* L = P + (size_t)d * N;
@@ -252,7 +263,7 @@ __global__ void __launch_bounds__(32 * kPivotWarps) k_pivot(const int64_t* pts, 
   const unsigned long long nw = (unsigned long long)gridDim.x * kPivotWarps;
   for (unsigned long long c = gw; c < ncur; c += nw) {
     flags |= bd::pivot_cell(tm, P, L, N, d, cur[c], W, S, G0, sc, acc,
-                            [&](uint64_t m) { table_insert(table, cap, m, next, dv); });
+                            [&](uint64_t m) { table_insert(table, cap, filled, m, next, dv); });
   }
   if (lane == 0) {
     const unsigned long long lo = (uint64_t)acc.nvol, hi = (uint64_t)(acc.nvol >> 64);
@@ -298,7 +309,7 @@ int device_pivot(const int64_t* pts, const int64_t* lifts, int N, int d, uint64_
   if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pivot, 32 * kPivotWarps, smem);
   if (e != cudaSuccess) return bd::set_error(BD_ERR_CUDA, cudaGetErrorString(e));
   per_sm = std::max(per_sm, 1);
-  for (unsigned long long cap = 1ull << 20; cap <= (1ull << 30); cap <<= 2) {
+  for (unsigned long long cap = 1ull << 22; cap <= (1ull << 31); cap <<= 3) {
     int64_t *d_pts = nullptr, *d_lifts = nullptr;
     unsigned long long *d_table = nullptr, *d_a = nullptr, *d_b = nullptr;
     PivotDev* d_dv = nullptr;
@@ -340,7 +351,7 @@ int device_pivot(const int64_t* pts, const int64_t* lifts, int N, int d, uint64_
           std::min<unsigned long long>((unsigned long long)sms * per_sm, (ncur + kPivotWarps - 1) / kPivotWarps);
       if (e == cudaSuccess) {
         k_pivot<<<(unsigned int)blocks, 32 * kPivotWarps, smem, st>>>(d_pts, d_lifts, N, d, d_a, ncur, d_table, cap,
-                                                                       d_b, d_dv);
+                                                                       total, d_b, d_dv);
         e = cudaGetLastError();
       }
       if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d_dv, sizeof(h), cudaMemcpyDeviceToHost, st);
@@ -369,7 +380,7 @@ int device_pivot(const int64_t* pts, const int64_t* lifts, int N, int d, uint64_
     run.ms = ms;
     return BD_OK;
   }
-  return bd::set_error(BD_ERR_NOMEM, "more than 2^29 cells");
+  return bd::set_error(BD_ERR_NOMEM, "more than 2^30 cells");
 }
 
 // The same traversal on the host: one team (one lane, or `width` lanes run as threads in
