@@ -434,7 +434,8 @@ int bd_host_mixed_volume_lifted(const int64_t* points, const int32_t* counts, in
  * extension from the lowest lifted point; the neighbour across a ridge is the point beyond it
  * of least height / (-barycentric coordinate), decided exactly.
  *   points : npts x k integers, |x| < 2^20, k+1 <= npts <= 64, 1 <= k <= 30
- *   seed   : lift seed (the heights of bd_volume for the same seed); a tie re-lifts (8 liftings)
+ *   seed   : lift seed: heights 1 + (top 40 bits of bd_volume's SplitMix64 stream), in [1, 2^40],
+ *            wider than bd_volume's because up to ~1e8 cells are walked; a tie re-lifts (8 liftings)
  *   out    : nvol, cells, ties, relifts, flags (BD_FLAG_DEGENERATE when not full-dimensional),
  *            bound_bits; subsets holds the ridges examined, (k+1) * cells
  *   device_ms : NULL, or the traversal's time on the GPU (CUDA events; all levels)
@@ -444,7 +445,7 @@ int bd_host_mixed_volume_lifted(const int64_t* points, const int32_t* counts, in
 int bd_volume_pivot(const int64_t* points, int32_t npts, int32_t k, uint64_t seed, bd_volume_out* out,
                     double* device_ms);
 
-/* The same traversal on the host with the given heights (|lift| < 2^30, no re-lift: a tie
+/* The same traversal on the host with the given heights (|lift| <= 2^40, no re-lift: a tie
  * returns BD_ERR_TIES), one team of team_width lanes (1..32; more than 1 runs them as threads in
  * lockstep), for CPU tests.  cells: NULL, or capacity bitmasks of the cells' points (bit p for
  * point p), increasing; fewer than out->cells -> BD_ERR_ARG. */

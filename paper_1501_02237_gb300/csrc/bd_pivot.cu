@@ -36,6 +36,13 @@ struct PivotWarp {
 
 enum { START_OK = 0, START_TIE = 1, START_FLAT = 2, START_OVERFLOW = 3 };
 
+// The heights of the pivoting path: the top 40 bits of the lift stream (bd_lifts.h), in
+// [1, 2^40].  The path walks up to ~1e8 cells, where the 20-bit heights of the subset
+// enumeration tie too often (one relift at 7e6 cells, every lifting at 5e7).
+int64_t lift_height_wide(uint64_t stream_seed, int i) {
+  return 1 + (int64_t)(bd::splitmix_mix(stream_seed + (uint64_t)(i + 1) * 0x9E3779B97F4A7C15ull) >> 24);
+}
+
 i128 iabs(i128 x) { return x < 0 ? -x : x; }
 
 i128 gcd128(i128 a, i128 b) {
@@ -68,12 +75,15 @@ int start_cell(const int64_t* pts, const int64_t* lifts, int N, int d, uint64_t&
   i128 c = 1, B = lifts[v0];
   std::vector<i128> A(d, 0);
   std::vector<i128> H(N);
-  auto eval = [&]() {
+  auto eval = [&]() {  // false on overflow
     for (int p = 0; p < N; ++p) {
-      i128 h = c * (i128)lifts[p] - B;
-      for (int e = 0; e < d; ++e) h -= A[e] * (i128)pts[p * d + e];
+      i128 h, t;
+      if (!mul_ok(c, (i128)lifts[p], h) || __builtin_sub_overflow(h, B, &h)) return false;
+      for (int e = 0; e < d; ++e)
+        if (!mul_ok(A[e], (i128)pts[p * d + e], t) || __builtin_sub_overflow(h, t, &h)) return false;
       H[p] = h;
     }
+    return true;
   };
   while ((int)F.size() < d + 1) {
     const int j = (int)F.size() - 1, f0 = F[0];
@@ -105,7 +115,7 @@ int start_cell(const int64_t* pts, const int64_t* lifts, int N, int d, uint64_t&
       pivcol.push_back(col);
     }
     if ((int)pivcol.size() < j) return START_TIE;  // F not affinely independent
-    eval();
+    if (!eval()) return START_OVERFLOW;
     bool extended = false;
     for (int fcol = 0; fcol < d && !extended; ++fcol) {
       if (std::find(pivcol.begin(), pivcol.end(), fcol) != pivcol.end()) continue;
@@ -160,7 +170,7 @@ int start_cell(const int64_t* pts, const int64_t* lifts, int N, int d, uint64_t&
     }
     if (!extended) return START_FLAT;  // every point lies in F's affine span
   }
-  eval();
+  if (!eval()) return START_OVERFLOW;
   mask = 0;
   for (int f : F) mask |= 1ull << f;
   for (int p = 0; p < N; ++p)
@@ -448,13 +458,13 @@ int pivot_common(const int64_t* points, const int64_t* given_lifts, int32_t npts
   for (int a = 0; a < attempts; ++a) {
     if (given_lifts) {
       for (int i = 0; i < npts; ++i) {
-        if (given_lifts[i] >= (1 << 30) || given_lifts[i] <= -(1 << 30))
-          return bd::set_error(BD_ERR_ARG, "lifts must stay below 2^30 in magnitude on the pivoting path");
+        if (given_lifts[i] > (int64_t(1) << 40) || given_lifts[i] < -(int64_t(1) << 40))
+          return bd::set_error(BD_ERR_ARG, "lifts must stay within 2^40 in magnitude on the pivoting path");
         lifts[i] = given_lifts[i];
       }
     } else {
       const uint64_t ss = bd::lift_stream_seed(seed, (uint32_t)a);
-      for (int i = 0; i < npts; ++i) lifts[i] = bd::lift_height(ss, i);
+      for (int i = 0; i < npts; ++i) lifts[i] = lift_height_wide(ss, i);
     }
     out->relifts = a;
     uint64_t start = 0;
