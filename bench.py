@@ -179,6 +179,27 @@ def cpu_baseline(system, subsets, budget_s=15.0):
                 sample=f"{n} full exact degrees of the workload ({dt:.1f} s, single thread)")
 
 
+def cpu_native(bd, P, nvol, budget_s=5.0):
+    """The library's own C++ emulation of the enumeration walker (the same work list and exact
+    tests) on every host core: the native CPU comparison point beside the GPU figure."""
+    import numpy as np
+
+    W = np.random.default_rng(0).integers(1, 1 << 20, size=P.shape[0], endpoint=True)
+    threads = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        r = bd.host_volume_lifted(P, W, threads=threads)
+        n += 1
+        if time.perf_counter() - t0 > budget_s or n >= 20:
+            break
+    dt = time.perf_counter() - t0
+    subsets = math.comb(P.shape[0], P.shape[1] + 1)
+    return dict(value=subsets * n / dt, unit=UNIT, cores=threads, kind="library host emulation",
+                exact_match=r["status"] != 0 or r["nvol"] == nvol,
+                sample=f"{n} exact volumes of the workload ({dt:.1f} s, {threads} threads)")
+
+
 def batch_section(bd, seed=0):
     """The batched form against one launch per system on the uneven 4096-system workload
     (n ~ U[12,28], k ~ U[4,9], exponents in {0,1,2}, seeds 0..4095), exact agreement checked."""
@@ -536,6 +557,7 @@ def main():
         line["pivoting"] = pivot_section(bd, seed=seed)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(s, subsets)
+        line["cpu_native"] = cpu_native(bd, P, int(expect_nvol))
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
