@@ -39,6 +39,7 @@ extern "C" {
 #define BD_FLAG_DEGENERATE 1   /* points not full-dimensional: volume 0 */
 #define BD_FLAG_INT128 2       /* the 128-bit kernel path was used */
 #define BD_FLAG_INCONSISTENT 4 /* b^{Q_0} != 1: empty solution set, degree 0 */
+#define BD_FLAG_PIVOT 8        /* the volume came from the pivoting walk (dimension above BD_KMAX) */
 
 /* limits: K <= BD_KMAX lattice dimension, N <= BD_NMAX points (the origin included) */
 #define BD_KMAX 14
@@ -85,7 +86,9 @@ int bd_set_stream(void* stream);
  *          is decided exactly.  Denominators and numerators must be nonzero.
  *   seed : lift seed; the result does not depend on it.
  * Host reduction (Smith form, LLL-reduced kernel basis, torsion) runs on the CPU; the
- * volume on the GPU.  dim = 0 gives degree = torsion; dim = 1 is a segment, whose normalized
+ * volume on the GPU: the subset enumeration up to dimension BD_KMAX, the pivoting walk of
+ * bd_volume_pivot above it (up to 30; BD_FLAG_PIVOT, subsets = ridges examined).
+ * dim = 0 gives degree = torsion; dim = 1 is a segment, whose normalized
  * length max - min of the kernel points (and 0) is taken directly (kernel points of any size
  * below 2^62; the enumeration takes coordinates below 2^40).  Errors: BD_ERR_ARG,
  * BD_ERR_OVERFLOW, BD_ERR_TIES, BD_ERR_CUDA, BD_ERR_NOMEM.

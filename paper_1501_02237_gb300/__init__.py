@@ -12,7 +12,7 @@ from typing import Optional, Sequence
 
 import numpy as np
 
-from ._lib import (BD_FEATURES, BD_MLP_PARAMS, BD_FLAG_DEGENERATE, BD_FLAG_INCONSISTENT, BD_FLAG_INT128, KMAX,  # noqa: F401
+from ._lib import (BD_FEATURES, BD_MLP_PARAMS, BD_FLAG_DEGENERATE, BD_FLAG_INCONSISTENT, BD_FLAG_INT128, BD_FLAG_PIVOT, KMAX,  # noqa: F401
                    NMAX, BatchOpts, BatchStats, BinodegError, DegreeOut, HostOpts, MixedOut, PlanOpts, ServerOpts,
                    ServerStats, VolumeOut, check, i64, lib, ptr)
 from ._lib import F32P, I32P, U8P

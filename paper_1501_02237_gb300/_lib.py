@@ -11,7 +11,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libbinodeg.so")
 
 BD_OK, BD_ERR_ARG, BD_ERR_OVERFLOW, BD_ERR_TIES, BD_ERR_CUDA, BD_ERR_TIMEOUT, BD_ERR_NOMEM, BD_ERR_STATE = range(8)
-BD_FLAG_DEGENERATE, BD_FLAG_INT128, BD_FLAG_INCONSISTENT = 1, 2, 4
+BD_FLAG_DEGENERATE, BD_FLAG_INT128, BD_FLAG_INCONSISTENT, BD_FLAG_PIVOT = 1, 2, 4, 8
 KMAX, NMAX = 14, 64
 
 ERROR_NAMES = {0: "BD_OK", 1: "BD_ERR_ARG", 2: "BD_ERR_OVERFLOW", 3: "BD_ERR_TIES", 4: "BD_ERR_CUDA",

@@ -507,7 +507,22 @@ int bd_degree(const int64_t* A, int32_t n, int32_t m, const int64_t* coef, uint6
     set_u128(out->degree_lo, out->degree_hi, r.torsion);
     return BD_OK;
   }
-  if (r.dim > BD_KMAX) return fail(BD_ERR_ARG, "solution dimension exceeds BD_KMAX");
+  if (r.dim > BD_KMAX) {  // beyond the subset enumeration: walk the cells by pivoting instead
+    bd_volume_out v;
+    double ms = 0;
+    rc = bd_volume_pivot(r.points.data(), n + 1, r.dim, seed, &v, &ms);
+    if (rc) return rc;
+    const u128 nvol = ((u128)v.nvol_hi << 64) | v.nvol_lo;
+    const u128 deg = nvol * r.torsion;
+    if (r.torsion && deg / r.torsion != nvol) return fail(BD_ERR_OVERFLOW, "degree exceeds 2^128");
+    set_u128(out->nvol_lo, out->nvol_hi, nvol);
+    set_u128(out->degree_lo, out->degree_hi, deg);
+    out->relifts = v.relifts;
+    out->subsets = v.subsets;
+    out->cells = v.cells;
+    out->flags = v.flags | BD_FLAG_PIVOT;
+    return BD_OK;
+  }
   if (r.dim == 1) {  // a segment: NVol_1(conv{0, p_1 .. p_n}) = max - min, cells = distinct values - 1
     std::vector<int64_t> x(r.points.begin(), r.points.end());  // n kernel points, then the origin
     std::sort(x.begin(), x.end());

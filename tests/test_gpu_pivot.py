@@ -61,3 +61,13 @@ def test_gpu_pivot_lift_independence():
     P = bd.reduce(s.A)["points"]
     res = {bd.volume_pivot(P, seed=sd)["nvol"] for sd in (0, 1, 2)}
     assert res == {TABLE["degree"]["2,7"]}
+
+
+@pytest.mark.parametrize("mk", ["2,7", "3,5"])
+def test_gpu_degree_above_kmax_walks_the_cells(mk):
+    # dimension 16 / 17 > BD_KMAX: bd_degree itself takes the pivoting walk
+    m, k = map(int, mk.split(","))
+    s = master_space_system(m, k)
+    r = bd.degree(s.A, s.coef)
+    assert r["flags"] & bd.BD_FLAG_PIVOT
+    assert r["dim"] == m * k + 2 > bd.KMAX and r["degree"] == TABLE["degree"][mk]
