@@ -450,10 +450,12 @@ int bd_volume_pivot(const int64_t* points, int32_t npts, int32_t k, uint64_t see
 
 /* The same traversal on the host with the given heights (|lift| <= 2^40, no re-lift: a tie
  * returns BD_ERR_TIES), one team of team_width lanes (1..32; more than 1 runs them as threads in
- * lockstep), for CPU tests.  cells: NULL, or capacity bitmasks of the cells' points (bit p for
- * point p), increasing; fewer than out->cells -> BD_ERR_ARG. */
+ * lockstep), for CPU tests.  walk_budget: cells entered in place (by one tableau pivot each)
+ * below every eliminated cell (the GPU path uses 64; 0 eliminates every cell).  cells: NULL, or
+ * capacity bitmasks of the cells' points (bit p for point p), increasing; fewer than out->cells
+ * -> BD_ERR_ARG. */
 int bd_host_volume_pivot(const int64_t* points, const int64_t* lifts, int32_t npts, int32_t k, int32_t team_width,
-                         bd_volume_out* out, uint64_t* cells, int64_t capacity);
+                         int32_t walk_budget, bd_volume_out* out, uint64_t* cells, int64_t capacity);
 
 /* bd_degree with the volume by pivoting: solution sets of dimension up to 30 (BD_NMAX - 1
  * variables), e.g. the master spaces of Table mspace-deg beyond the reach of bd_degree. */

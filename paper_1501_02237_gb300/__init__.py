@@ -220,14 +220,16 @@ def volume_pivot(points, seed: int = 0) -> dict:
     return res
 
 
-def host_volume_pivot(points, lifts, team_width: int = 1, cells: bool = False, capacity: int = 1 << 16) -> dict:
+def host_volume_pivot(points, lifts, team_width: int = 1, cells: bool = False, capacity: int = 1 << 16,
+                      walk_budget: int = 64) -> dict:
     """bd_host_volume_pivot: the same traversal on the host with the given heights (CPU tests);
+    walk_budget cells entered in place below each eliminated cell (0: eliminate every cell);
     cells=True adds the cells as sorted tuples of point indices."""
     P, W = i64(points), i64(lifts)
     npts, k = P.shape
     out = VolumeOut()
     buf = np.zeros(max(capacity, 1), dtype=np.uint64)
-    rc = lib().bd_host_volume_pivot(ptr(P), ptr(W), npts, k, team_width, C.byref(out),
+    rc = lib().bd_host_volume_pivot(ptr(P), ptr(W), npts, k, team_width, walk_budget, C.byref(out),
                                     buf.ctypes.data_as(C.POINTER(C.c_uint64)) if cells else None, capacity)
     res = out.as_dict()
     res["status"] = rc

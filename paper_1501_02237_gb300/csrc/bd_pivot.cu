@@ -212,36 +212,43 @@ __host__ __device__ size_t pivot_warp_bytes(int N, int d) {
 size_t pivot_smem(int N, int d) { return ((8 * (size_t)(d + 1) * N + 15) / 16 * 16) + kPivotWarps * pivot_warp_bytes(N, d); }
 
 struct PivotDev {
-  unsigned long long nvol_lo, nvol_hi, cells, boundary, next_count, flags;
+  unsigned long long nvol_lo, nvol_hi, cells, boundary, next_count, flags, claimed;
 };
+
+constexpr int kWalkBudget = 64;  // cells a warp enters in place below each cell it eliminates
 
 enum { PF_TIE = 1, PF_INVALID = 2, PF_FULL = 4 };
 
 constexpr unsigned long long kMaxProbes = 4096;  // linear probing below half load: ~2.5 on average
 
-// Insert m unless present.  The table stays at most half full (`filled` cells entered before
-// this level); past that, or after kMaxProbes, the level reports PF_FULL and the traversal is
-// restarted with a larger table.
-__device__ void table_insert(unsigned long long* table, unsigned long long cap, unsigned long long filled,
-                             unsigned long long m, unsigned long long* next, PivotDev* dv) {
+// Claim m: true if it was not in the table and now is.  The table stays at most half full
+// (counting every claimed cell); past that, or after kMaxProbes, the level reports PF_FULL and
+// the traversal restarts with a larger table.
+__device__ bool table_claim(unsigned long long* table, unsigned long long cap, unsigned long long m, PivotDev* dv) {
   unsigned long long h = bd::pivot_hash(m) & (cap - 1);
   for (unsigned long long probe = 0; probe < kMaxProbes; ++probe) {
     const unsigned long long cur = table[h];
-    if (cur == m) return;
+    if (cur == m) return false;
     if (cur == 0ull) {
-      if (2 * (filled + *(volatile unsigned long long*)&dv->next_count) >= cap) break;  // too full
+      if (2 * *(volatile unsigned long long*)&dv->claimed >= cap) break;  // too full
       const unsigned long long old = atomicCAS(table + h, 0ull, m);
       if (old == 0ull) {
-        const unsigned long long pos = atomicAdd(&dv->next_count, 1ull);
-        if (pos < cap) next[pos] = m;
-        else atomicOr(&dv->flags, (unsigned long long)PF_FULL);
-        return;
+        atomicAdd(&dv->claimed, 1ull);
+        return true;
       }
-      if (old == m) return;
+      if (old == m) return false;
     }
     h = (h + 1) & (cap - 1);
   }
   atomicOr(&dv->flags, (unsigned long long)PF_FULL);
+  return false;
+}
+
+// append a claimed cell to the next level's list
+__device__ void frontier_push(unsigned long long* next, unsigned long long cap, unsigned long long m, PivotDev* dv) {
+  const unsigned long long pos = atomicAdd(&dv->next_count, 1ull);
+  if (pos < cap) next[pos] = m;
+  else atomicOr(&dv->flags, (unsigned long long)PF_FULL);
 }
 
 // One breadth-first level: every cell of `cur` is processed by one warp; its new neighbours
@@ -249,8 +256,7 @@ __device__ void table_insert(unsigned long long* table, unsigned long long cap, 
 __global__ void __launch_bounds__(32 * kPivotWarps) k_pivot(const int64_t* pts, const int64_t* lifts, int N, int d,
                                                             const unsigned long long* cur, unsigned long long ncur,
                                                             unsigned long long* table, unsigned long long cap,
-                                                            unsigned long long filled, unsigned long long* next,
-                                                            PivotDev* dv) {
+                                                            int budget, unsigned long long* next, PivotDev* dv) {
   extern __shared__ __align__(16) unsigned char smem[];
   int64_t* P = reinterpret_cast<int64_t*>(smem);  // coordinate-major, then the lifts
   int64_t* L = P + (size_t)d * N;
@@ -272,8 +278,9 @@ __global__ void __launch_bounds__(32 * kPivotWarps) k_pivot(const int64_t* pts, 
   const unsigned long long gw = (unsigned long long)blockIdx.x * kPivotWarps + warp;
   const unsigned long long nw = (unsigned long long)gridDim.x * kPivotWarps;
   for (unsigned long long c = gw; c < ncur; c += nw) {
-    flags |= bd::pivot_cell(tm, P, L, N, d, cur[c], W, S, G0, sc, acc,
-                            [&](uint64_t m) { table_insert(table, cap, filled, m, next, dv); });
+    flags |= bd::pivot_cell(
+        tm, P, L, N, d, cur[c], W, S, G0, sc, acc, [&](uint64_t m) { return table_claim(table, cap, m, dv); },
+        [&](uint64_t m) { frontier_push(next, cap, m, dv); }, budget);
   }
   if (lane == 0) {
     const unsigned long long lo = (uint64_t)acc.nvol, hi = (uint64_t)(acc.nvol >> 64);
@@ -290,9 +297,10 @@ __global__ void __launch_bounds__(32 * kPivotWarps) k_pivot(const int64_t* pts, 
 }
 
 __global__ void k_pivot_seed(unsigned long long* table, unsigned long long cap, unsigned long long m,
-                             unsigned long long* frontier) {
+                             unsigned long long* frontier, PivotDev* dv) {
   table[bd::pivot_hash(m) & (cap - 1)] = m;
   frontier[0] = m;
+  dv->claimed = 1;
 }
 
 struct PivotRun {
@@ -347,7 +355,7 @@ int device_pivot(const int64_t* pts, const int64_t* lifts, int N, int d, uint64_
     if (e == cudaSuccess) e = cudaMemsetAsync(d_table, 0, sizeof(unsigned long long) * cap, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_dv, 0, sizeof(PivotDev), st);
     if (e == cudaSuccess) {
-      k_pivot_seed<<<1, 1, 0, st>>>(d_table, cap, start, d_a);
+      k_pivot_seed<<<1, 1, 0, st>>>(d_table, cap, start, d_a, d_dv);
       e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaEventRecord(e0, st);
@@ -361,7 +369,7 @@ int device_pivot(const int64_t* pts, const int64_t* lifts, int N, int d, uint64_
           std::min<unsigned long long>((unsigned long long)sms * per_sm, (ncur + kPivotWarps - 1) / kPivotWarps);
       if (e == cudaSuccess) {
         k_pivot<<<(unsigned int)blocks, 32 * kPivotWarps, smem, st>>>(d_pts, d_lifts, N, d, d_a, ncur, d_table, cap,
-                                                                       total, d_b, d_dv);
+                                                                       kWalkBudget, d_b, d_dv);
         e = cudaGetLastError();
       }
       if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d_dv, sizeof(h), cudaMemcpyDeviceToHost, st);
@@ -369,7 +377,7 @@ int device_pivot(const int64_t* pts, const int64_t* lifts, int N, int d, uint64_
       ++run.levels;
       if (e != cudaSuccess || h.flags) break;
       ncur = h.next_count;
-      total += ncur;
+      total = h.claimed;
       if (2 * total > cap) {  // too full for cheap probing: restart with a larger table
         h.flags = PF_FULL;
         break;
@@ -395,7 +403,8 @@ int device_pivot(const int64_t* pts, const int64_t* lifts, int N, int d, uint64_
 
 // The same traversal on the host: one team (one lane, or `width` lanes run as threads in
 // lockstep), cells in breadth-first order.
-int host_pivot(const int64_t* pts, const int64_t* lifts, int N, int d, uint64_t start, int width, PivotRun& run) {
+int host_pivot(const int64_t* pts, const int64_t* lifts, int N, int d, uint64_t start, int width, int budget,
+               PivotRun& run) {
   std::vector<int64_t> P((size_t)d * N);
   for (int r = 0; r < d; ++r)
     for (int p = 0; p < N; ++p) P[(size_t)r * N + p] = pts[p * d + r];
@@ -408,10 +417,9 @@ int host_pivot(const int64_t* pts, const int64_t* lifts, int N, int d, uint64_t 
   int flags = 0;
   auto step = [&](auto tm, std::vector<uint64_t>& out) {
     for (uint64_t m : cur) {
-      const int f = bd::pivot_cell(tm, P.data(), lifts, N, d, m, W.data(), S.data(), G0.data(), &sc, acc,
-                                   [&](uint64_t nb) {
-                                     if (seen.insert(nb).second) out.push_back(nb);
-                                   });
+      const int f = bd::pivot_cell(
+          tm, P.data(), lifts, N, d, m, W.data(), S.data(), G0.data(), &sc, acc,
+          [&](uint64_t nb) { return seen.insert(nb).second; }, [&](uint64_t nb) { out.push_back(nb); }, budget);
       if (tm.lane() == 0) flags |= f;
     }
   };
@@ -429,7 +437,7 @@ int host_pivot(const int64_t* pts, const int64_t* lifts, int N, int d, uint64_t 
       step(bd::LockstepTeam{&shl, 0}, next);
       for (auto& t : th) t.join();
     }
-    run.masks.insert(run.masks.end(), cur.begin(), cur.end());
+
     ++run.levels;
     cur.swap(next);
   }
@@ -437,12 +445,14 @@ int host_pivot(const int64_t* pts, const int64_t* lifts, int N, int d, uint64_t 
   run.cells = acc.cells;
   run.boundary = acc.boundary;
   run.flags = (flags & bd::PV_TIE ? PF_TIE : 0) | (flags & bd::PV_INVALID ? PF_INVALID : 0);
+  run.masks.assign(seen.begin(), seen.end());  // every claimed cell was processed once
   std::sort(run.masks.begin(), run.masks.end());
   return BD_OK;
 }
 
 int pivot_common(const int64_t* points, const int64_t* given_lifts, int32_t npts, int32_t k, uint64_t seed,
-                 int host_width, bd_volume_out* out, uint64_t* cells, int64_t capacity, double* device_ms) {
+                 int host_width, int host_budget, bd_volume_out* out, uint64_t* cells, int64_t capacity,
+                 double* device_ms) {
   if (!out || !points) return bd::set_error(BD_ERR_ARG, "NULL argument");
   std::memset(out, 0, sizeof(*out));
   if (k < 1 || k > bd::kPivotDMax) return bd::set_error(BD_ERR_ARG, "need 1 <= k <= 30 for the pivoting path");
@@ -479,7 +489,7 @@ int pivot_common(const int64_t* points, const int64_t* given_lifts, int32_t npts
       continue;
     }
     PivotRun run;
-    const int rc = host_width > 0 ? host_pivot(points, lifts.data(), npts, k, start, host_width, run)
+    const int rc = host_width > 0 ? host_pivot(points, lifts.data(), npts, k, start, host_width, host_budget, run)
                                   : device_pivot(points, lifts.data(), npts, k, start, run);
     if (rc) return rc;
     if (run.flags & PF_INVALID) return bd::set_error(BD_ERR_ARG, "pivoting reached a non-cell (internal error)");
@@ -509,15 +519,16 @@ extern "C" {
 
 int bd_volume_pivot(const int64_t* points, int32_t npts, int32_t k, uint64_t seed, bd_volume_out* out,
                     double* device_ms) {
-  return pivot_common(points, nullptr, npts, k, seed, 0, out, nullptr, 0, device_ms);
+  return pivot_common(points, nullptr, npts, k, seed, 0, 0, out, nullptr, 0, device_ms);
 }
 
 int bd_host_volume_pivot(const int64_t* points, const int64_t* lifts, int32_t npts, int32_t k, int32_t team_width,
-                         bd_volume_out* out, uint64_t* cells, int64_t capacity) {
+                         int32_t walk_budget, bd_volume_out* out, uint64_t* cells, int64_t capacity) {
   if (!lifts) return bd::set_error(BD_ERR_ARG, "NULL argument");
   if (team_width < 1 || team_width > 32) return bd::set_error(BD_ERR_ARG, "team width must be 1..32");
+  if (walk_budget < 0) return bd::set_error(BD_ERR_ARG, "negative walk budget");
   if (cells && capacity < 0) return bd::set_error(BD_ERR_ARG, "negative capacity");
-  return pivot_common(points, lifts, npts, k, 0, team_width, out, cells, capacity, nullptr);
+  return pivot_common(points, lifts, npts, k, 0, team_width, walk_budget, out, cells, capacity, nullptr);
 }
 
 int bd_degree_pivot(const int64_t* A, int32_t n, int32_t m, const int64_t* coef, uint64_t seed, bd_degree_out* out) {
@@ -541,7 +552,7 @@ int bd_degree_pivot(const int64_t* A, int32_t n, int32_t m, const int64_t* coef,
   u128 nvol = 1;
   if (r.dim >= 1) {
     bd_volume_out v;
-    rc = pivot_common(r.points.data(), nullptr, n + 1, r.dim, seed, 0, &v, nullptr, 0, nullptr);
+    rc = pivot_common(r.points.data(), nullptr, n + 1, r.dim, seed, 0, 0, &v, nullptr, 0, nullptr);
     if (rc) return rc;
     nvol = ((u128)v.nvol_hi << 64) | v.nvol_lo;
     out->relifts = v.relifts;

@@ -43,11 +43,18 @@ struct PivotCand {
 };
 
 // per-warp scratch of the pivoting stage
+constexpr int kWalkDepth = 64;  // deepest in-place walk below an eliminated cell
+
 struct PivotScratch {
   PivotCand cand[32];
-  uint8_t cidx[kPivotDMax + 2];  // the cell's points in increasing order
+  i128 sq;                       // the entering point's height numerator during a pivot
+  int64_t colq[kPivotDMax + 1];  // the entering point's tableau column during a pivot
+  int64_t D;                     // the current cell's +-det M
+  uint8_t cidx[kPivotDMax + 2];  // the current cell's vertices; tableau row r belongs to cidx[r]
+  uint8_t st_slot[kWalkDepth], st_old[kWalkDepth];  // the walk's stack: replaced row and point
   int32_t piv;                   // pivot row of the current elimination step
   int32_t flags;                 // PV_TIE | PV_INVALID found by any lane
+  int32_t claimed;               // lane 0's claim of a neighbour, read by every lane
 };
 
 // signed 256-bit comparison of two products: a * b > c * d
@@ -92,16 +99,20 @@ struct PivotAcc {
   uint64_t boundary;  // ridges on the boundary of conv(points)
 };
 
-// Process one cell (bitmask of its d+1 points): eliminate, check it, add |D|, and hand every
-// neighbour across a ridge to insert(mask) (called by lane 0).  P holds the points
-// coordinate-major (P[r * N + p]), L the lifts.  Per team: W, d x (d+N) int64; S, N heights;
-// G0, N values of g_0; sc, the scratch.  Returns PV_OK, or PV_TIE / PV_INVALID bits.
+// Process one cell (bitmask of its d+1 points) and up to `budget` of its descendants: eliminate
+// it, check it, add |D|; then walk its ridges.  A neighbour that claim(mask) reports as new is
+// either entered in place (one rank-one pivot of the tableau, Sec. 4.2's pivot taken literally;
+// one more pivot leads back) or, past the budget or the stack depth, handed to push(mask) for a
+// later launch.  claim and push are called by lane 0.  P holds the points coordinate-major
+// (P[r * N + p]), L the lifts.  Per team: W, d x (d+N) int64; S, N heights; G0, N values of g_0;
+// sc, the scratch.  Rows 1..d of the tableau are W's right block, row 0 is G0.  Returns PV_OK,
+// or PV_TIE / PV_INVALID bits.
 #ifdef __CUDACC__
 #pragma nv_exec_check_disable  // instantiated with host-only teams by the host emulation
 #endif
-template <class Team, class Insert>
+template <class Team, class Claim, class Push>
 BD_HD int pivot_cell(Team tm, const int64_t* P, const int64_t* L, int N, int d, uint64_t mask, int64_t* W, i128* S,
-                     int64_t* G0, PivotScratch* sc, PivotAcc& acc, Insert insert) {
+                     int64_t* G0, PivotScratch* sc, PivotAcc& acc, Claim claim, Push push, int budget) {
   const int lane = tm.lane(), nl = tm.lanes(), width = d + N;
   tm.sync();  // the previous cell's readers are done with the scratch
   if (lane == 0) sc->flags = 0;
@@ -149,7 +160,6 @@ BD_HD int pivot_cell(Team tm, const int64_t* P, const int64_t* L, int N, int d, 
     prev = pk;
   }
   const int64_t Dv = prev;  // +-det M: the cell's normalized volume up to sign
-  const int sd = Dv > 0 ? 1 : -1;
   // heights and g_0 of every point
   int fl = 0;
   for (int p = lane; p < N; p += nl) {
@@ -164,28 +174,67 @@ BD_HD int pivot_cell(Team tm, const int64_t* P, const int64_t* L, int N, int d, 
     if (!((mask >> p) & 1)) {
       const int sg = (s > 0) - (s < 0);
       if (sg == 0) fl |= PV_TIE;
-      else if (sg != sd) fl |= PV_INVALID;
+      else if (sg != (Dv > 0 ? 1 : -1)) fl |= PV_INVALID;
     }
   }
-  if (fl) {
+  auto raise = [&](int f) {
+    if (!f) return;
 #ifdef __CUDA_ARCH__
-    atomicOr(&sc->flags, fl);
+    atomicOr(&sc->flags, f);
 #else
-    __atomic_fetch_or(&sc->flags, fl, __ATOMIC_RELAXED);
+    __atomic_fetch_or(&sc->flags, f, __ATOMIC_RELAXED);
 #endif
-  }
+  };
+  raise(fl);
+  if (lane == 0) sc->D = Dv;
   tm.sync();
   if (sc->flags) return sc->flags;  // uniform: read after the sync
   if (lane == 0) {
     acc.nvol += (u128)(Dv < 0 ? -Dv : Dv);
     ++acc.cells;
   }
-  // every ridge: the far-side point of least h / (-lambda_i)
-  for (int i = 0; i <= d; ++i) {
+  auto T = [&](int r, int p) -> int64_t& { return r == 0 ? G0[p] : W[(r - 1) * width + d + p]; };
+  // Pivot row i onto point q: T'[r][p] = (T[r][p] T[i][q] - T[r][q] T[i][p]) / D for r != i,
+  // T'[i][p] = T[i][p], S'[p] = (S[p] T[i][q] - S[q] T[i][p]) / D, D' = T[i][q] (every entry
+  // again a minor, or D' times a height, of the new cell).
+  auto pivot_to = [&](int i, int q) {
+    for (int r = lane; r <= d; r += nl) sc->colq[r] = T(r, q);
+    if (lane == 0) sc->sq = S[q];
+    tm.sync();
+    const int64_t Dold = sc->D, piv = sc->colq[i];
+    const Div64 Dd = make_div(Dold);
+    const Div128 Dw = make_div((i128)Dold);
+    const i128 sq = sc->sq;
+    for (int p = lane; p < N; p += nl) {
+      const int64_t ti = T(i, p);
+      for (int r = 0; r <= d; ++r)
+        if (r != i) T(r, p) = bareiss(T(r, p), piv, sc->colq[r], ti, Dd);
+      S[p] = bareiss(S[p], (i128)piv, sq, (i128)ti, Dw);
+    }
+    tm.sync();
+    if (lane == 0) {
+      sc->D = piv;
+      sc->cidx[i] = (uint8_t)q;
+    }
+    tm.sync();
+  };
+  int depth = 0, entered = 0, r = 0;
+  for (;;) {
+    if (r > d) {  // every ridge of this cell is done
+      if (depth == 0) break;
+      --depth;
+      const int i = sc->st_slot[depth], o = sc->st_old[depth], q = sc->cidx[i];
+      pivot_to(i, o);  // back to the parent cell
+      mask = (mask & ~(1ull << q)) | (1ull << o);
+      r = i + 1;
+      continue;
+    }
+    const int sd = sc->D > 0 ? 1 : -1;
+    // the far-side point of least h / (-lambda_r)
     PivotCand best{0, 0, -1, 0};
     for (int p = lane; p < N; p += nl) {
       if ((mask >> p) & 1) continue;
-      const int64_t gi = i == 0 ? G0[p] : W[(i - 1) * width + d + p];
+      const int64_t gi = T(r, p);
       if (gi == 0 || (gi > 0 ? 1 : -1) == sd) continue;  // not beyond the ridge
       PivotCand c{S[p], gi, p, 0};
       pivot_merge(best, c, &sc->flags);
@@ -196,13 +245,54 @@ BD_HD int pivot_cell(Team tm, const int64_t* P, const int64_t* L, int N, int d, 
       if (lane % (2 * h) == 0 && lane + h < nl) pivot_merge(sc->cand[lane], sc->cand[lane + h], &sc->flags);
       tm.sync();
     }
-    if (lane == 0) {
-      const PivotCand b = sc->cand[0];
-      if (b.p < 0) ++acc.boundary;
-      else insert((mask & ~(1ull << sc->cidx[i])) | (1ull << b.p));
+    const PivotCand bst = sc->cand[0];
+    if (bst.p < 0) {
+      if (lane == 0) ++acc.boundary;
+      tm.sync();  // cand[0] is read before the next ridge overwrites the candidates
+      ++r;
+      continue;
     }
-    tm.sync();  // cand[0] is read before the next ridge overwrites the candidates
+    const uint64_t nm = (mask & ~(1ull << sc->cidx[r])) | (1ull << bst.p);
+    if (lane == 0) sc->claimed = claim(nm) ? 1 : 0;
+    tm.sync();
+    const bool fresh = sc->claimed != 0;
+    tm.sync();  // everyone has read the claim
+    if (!fresh) {
+      ++r;
+      continue;
+    }
+    if (depth < kWalkDepth && entered < budget) {  // enter the neighbour in place
+      if (lane == 0) {
+        sc->st_slot[depth] = (uint8_t)r;
+        sc->st_old[depth] = sc->cidx[r];
+      }
+      pivot_to(r, bst.p);
+      mask = nm;
+      ++depth;
+      ++entered;
+      const int sdn = sc->D > 0 ? 1 : -1;
+      int f2 = 0;
+      for (int p = lane; p < N; p += nl) {
+        if ((mask >> p) & 1) continue;
+        const int sg = (S[p] > 0) - (S[p] < 0);
+        if (sg == 0) f2 |= PV_TIE;
+        else if (sg != sdn) f2 |= PV_INVALID;
+      }
+      raise(f2);
+      tm.sync();
+      if (sc->flags) return sc->flags;
+      if (lane == 0) {
+        const int64_t Dn = sc->D;
+        acc.nvol += (u128)(Dn < 0 ? -Dn : Dn);
+        ++acc.cells;
+      }
+      r = 0;
+      continue;
+    }
+    if (lane == 0) push(nm);
+    ++r;
   }
+  tm.sync();
   return sc->flags;
 }
 
