@@ -9,6 +9,7 @@
 #include <cmath>
 #include <cstring>
 #include <deque>
+#include <mutex>
 #include <string>
 #include <thread>
 #include <unordered_set>
@@ -32,6 +33,9 @@ struct PivotWarp {
   __device__ int lane() const { return threadIdx.x & 31; }
   __device__ int lanes() const { return 32; }
   __device__ void sync() const { __syncwarp(); }
+  __device__ uint64_t or_all(uint64_t x) const {  // ridge bits: below 2^31
+    return __reduce_or_sync(0xffffffffu, (uint32_t)x);
+  }
 };
 
 enum { START_OK = 0, START_TIE = 1, START_FLAT = 2, START_OVERFLOW = 3 };
@@ -415,11 +419,21 @@ int host_pivot(const int64_t* pts, const int64_t* lifts, int N, int d, uint64_t 
   std::vector<uint64_t> cur{start}, next;
   bd::PivotAcc acc{};
   int flags = 0;
+  std::mutex mu;
   auto step = [&](auto tm, std::vector<uint64_t>& out) {
+    (void)out;
     for (uint64_t m : cur) {
       const int f = bd::pivot_cell(
           tm, P.data(), lifts, N, d, m, W.data(), S.data(), G0.data(), &sc, acc,
-          [&](uint64_t nb) { return seen.insert(nb).second; }, [&](uint64_t nb) { out.push_back(nb); }, budget);
+          [&](uint64_t nb) {
+            std::lock_guard<std::mutex> g(mu);  // lanes of a lockstep team claim concurrently
+            return seen.insert(nb).second;
+          },
+          [&](uint64_t nb) {
+            std::lock_guard<std::mutex> g(mu);
+            next.push_back(nb);
+          },
+          budget);
       if (tm.lane() == 0) flags |= f;
     }
   };

@@ -52,6 +52,8 @@ struct PivotScratch {
   int64_t D;                     // the current cell's +-det M
   uint8_t cidx[kPivotDMax + 2];  // the current cell's vertices; tableau row r belongs to cidx[r]
   uint8_t st_slot[kWalkDepth], st_old[kWalkDepth];  // the walk's stack: replaced row and point
+  uint32_t st_todo[kWalkDepth];  // the parent's new neighbours still to handle
+  uint8_t nbr[kWalkDepth][32];   // per stack level: the point beyond each ridge (255: boundary)
   int32_t piv;                   // pivot row of the current elimination step
   int32_t flags;                 // PV_TIE | PV_INVALID found by any lane
   int32_t claimed;               // lane 0's claim of a neighbour, read by every lane
@@ -103,7 +105,7 @@ struct PivotAcc {
 // it, check it, add |D|; then walk its ridges.  A neighbour that claim(mask) reports as new is
 // either entered in place (one rank-one pivot of the tableau, Sec. 4.2's pivot taken literally;
 // one more pivot leads back) or, past the budget or the stack depth, handed to push(mask) for a
-// later launch.  claim and push are called by lane 0.  P holds the points coordinate-major
+// later launch.  claim and push are called by any lane, concurrently.  P holds the points coordinate-major
 // (P[r * N + p]), L the lifts.  Per team: W, d x (d+N) int64; S, N heights; G0, N values of g_0;
 // sc, the scratch.  Rows 1..d of the tableau are W's right block, row 0 is G0.  Returns PV_OK,
 // or PV_TIE / PV_INVALID bits.
@@ -218,55 +220,51 @@ BD_HD int pivot_cell(Team tm, const int64_t* P, const int64_t* L, int N, int d, 
     }
     tm.sync();
   };
-  int depth = 0, entered = 0, r = 0;
+  // The ridges of the current cell: lane l takes ridges l, l + lanes, .. and scans every point
+  // for the least h / (-lambda_r); all lanes then claim their neighbours at once, and one vote
+  // gives the ridges whose neighbour is new (bit r).
+  auto scan = [&](int lvl) -> uint32_t {
+    const int sd = sc->D > 0 ? 1 : -1;
+    uint64_t fresh = 0;
+    for (int r = lane; r <= d; r += nl) {
+      PivotCand best{0, 0, -1, 0};
+      for (int p = 0; p < N; ++p) {
+        if ((mask >> p) & 1) continue;
+        const int64_t gi = T(r, p);
+        if (gi == 0 || (gi > 0 ? 1 : -1) == sd) continue;  // not beyond the ridge
+        PivotCand c{S[p], gi, p, 0};
+        pivot_merge(best, c, &sc->flags);
+      }
+      sc->nbr[lvl][r] = best.p < 0 ? (uint8_t)255 : (uint8_t)best.p;
+      if (best.p >= 0 && claim((mask & ~(1ull << sc->cidx[r])) | (1ull << best.p))) fresh |= 1ull << r;
+    }
+    fresh = tm.or_all(fresh);
+    tm.sync();  // the neighbours are visible to every lane
+    return (uint32_t)fresh;
+  };
+  int depth = 0, entered = 0;
+  uint32_t todo = scan(0);  // new neighbours of the current cell not yet handled
   for (;;) {
-    if (r > d) {  // every ridge of this cell is done
+    if (!todo) {  // this cell is done
       if (depth == 0) break;
       --depth;
       const int i = sc->st_slot[depth], o = sc->st_old[depth], q = sc->cidx[i];
+      todo = sc->st_todo[depth];
       pivot_to(i, o);  // back to the parent cell
       mask = (mask & ~(1ull << q)) | (1ull << o);
-      r = i + 1;
       continue;
     }
-    const int sd = sc->D > 0 ? 1 : -1;
-    // the far-side point of least h / (-lambda_r)
-    PivotCand best{0, 0, -1, 0};
-    for (int p = lane; p < N; p += nl) {
-      if ((mask >> p) & 1) continue;
-      const int64_t gi = T(r, p);
-      if (gi == 0 || (gi > 0 ? 1 : -1) == sd) continue;  // not beyond the ridge
-      PivotCand c{S[p], gi, p, 0};
-      pivot_merge(best, c, &sc->flags);
-    }
-    sc->cand[lane] = best;
-    tm.sync();
-    for (int h = 1; h < nl; h *= 2) {
-      if (lane % (2 * h) == 0 && lane + h < nl) pivot_merge(sc->cand[lane], sc->cand[lane + h], &sc->flags);
-      tm.sync();
-    }
-    const PivotCand bst = sc->cand[0];
-    if (bst.p < 0) {
-      if (lane == 0) ++acc.boundary;
-      tm.sync();  // cand[0] is read before the next ridge overwrites the candidates
-      ++r;
-      continue;
-    }
-    const uint64_t nm = (mask & ~(1ull << sc->cidx[r])) | (1ull << bst.p);
-    if (lane == 0) sc->claimed = claim(nm) ? 1 : 0;
-    tm.sync();
-    const bool fresh = sc->claimed != 0;
-    tm.sync();  // everyone has read the claim
-    if (!fresh) {
-      ++r;
-      continue;
-    }
-    if (depth < kWalkDepth && entered < budget) {  // enter the neighbour in place
+    const int r = ctz64((uint64_t)todo);
+    if (depth + 1 < kWalkDepth && entered < budget) {  // enter the neighbour in place
+      todo &= todo - 1;
+      const int q = sc->nbr[depth][r];
+      const uint64_t nm = (mask & ~(1ull << sc->cidx[r])) | (1ull << q);
       if (lane == 0) {
         sc->st_slot[depth] = (uint8_t)r;
         sc->st_old[depth] = sc->cidx[r];
+        sc->st_todo[depth] = todo;
       }
-      pivot_to(r, bst.p);
+      pivot_to(r, q);
       mask = nm;
       ++depth;
       ++entered;
@@ -286,11 +284,14 @@ BD_HD int pivot_cell(Team tm, const int64_t* P, const int64_t* L, int N, int d, 
         acc.nvol += (u128)(Dn < 0 ? -Dn : Dn);
         ++acc.cells;
       }
-      r = 0;
+      todo = scan(depth);
       continue;
     }
-    if (lane == 0) push(nm);
-    ++r;
+    // past the budget or the depth: this cell's remaining new neighbours go to the next level
+    for (int rr = lane; rr <= d; rr += nl)
+      if ((todo >> rr) & 1) push((mask & ~(1ull << sc->cidx[rr])) | (1ull << sc->nbr[depth][rr]));
+    todo = 0;
+    tm.sync();
   }
   tm.sync();
   return sc->flags;
