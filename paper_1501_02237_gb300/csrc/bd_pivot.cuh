@@ -75,6 +75,24 @@ BD_HD bool prod_equal(i128 a, i128 b, i128 c, i128 d) {
   return h1 == h2 && l1 == l2;
 }
 
+// a float near x (relative error below 2^-23.9): the top 62 bits through an int64 conversion
+BD_HD float approx_f(i128 x) {
+  const bool neg = x < 0;
+  const u128 a = neg ? (u128)(-x) : (u128)x;
+  int sh = 0;
+  if (a >> 62) {
+    const uint64_t hi = (uint64_t)(a >> 64);
+#ifdef __CUDA_ARCH__
+    const int lz = hi ? __clzll((long long)hi) : 64;
+#else
+    const int lz = hi ? __builtin_clzll(hi) : 64;
+#endif
+    sh = 66 - lz;  // leaves the value below 2^62
+  }
+  const float f = ldexpf((float)(int64_t)(a >> sh), sh);
+  return neg ? -f : f;
+}
+
 // merge candidate B into A (both for the same ridge); sets *tie on equal ratios
 BD_HD void pivot_merge(PivotCand& A, const PivotCand& B, int32_t* flags) {
   if (B.p < 0) return;
@@ -228,12 +246,24 @@ BD_HD int pivot_cell(Team tm, const int64_t* P, const int64_t* L, int N, int d, 
     uint64_t fresh = 0;
     for (int r = lane; r <= d; r += nl) {
       PivotCand best{0, 0, -1, 0};
+      float bf = 0.f;  // best's ratio in single precision
       for (int p = 0; p < N; ++p) {
         if ((mask >> p) & 1) continue;
         const int64_t gi = T(r, p);
         if (gi == 0 || (gi > 0 ? 1 : -1) == sd) continue;  // not beyond the ridge
         PivotCand c{S[p], gi, p, 0};
+        // Ratios in single precision first: each operand within 2^-23.9 of its value, the
+        // quotient rounded once, so a ratio is within 2^-22.3 of the exact one and ratios apart
+        // by more than 2^-16 of their size are ordered correctly.  Closer ones: exact test.
+        const float cf = approx_f(c.s) / (float)(-gi);
+        if (best.p < 0 || cf < bf * (1.f - 0x1p-16f)) {
+          best = c;
+          bf = cf;
+          continue;
+        }
+        if (cf > bf * (1.f + 0x1p-16f)) continue;
         pivot_merge(best, c, &sc->flags);
+        bf = approx_f(best.s) / (float)(-best.g);
       }
       sc->nbr[lvl][r] = best.p < 0 ? (uint8_t)255 : (uint8_t)best.p;
       if (best.p >= 0 && claim((mask & ~(1ull << sc->cidx[r])) | (1ull << best.p))) fresh |= 1ull << r;
