@@ -27,7 +27,7 @@ using bd::u128;
 
 namespace {
 
-constexpr int kPivotWarps = 4;  // warps per block
+constexpr int kPivotMaxWarps = 8;  // warps per block: chosen per problem, at most this
 
 struct PivotWarp {
   __device__ int lane() const { return threadIdx.x & 31; }
@@ -213,7 +213,9 @@ __host__ __device__ size_t pivot_warp_bytes(int N, int d) {
   return (b + 15) / 16 * 16;
 }
 
-size_t pivot_smem(int N, int d) { return ((8 * (size_t)(d + 1) * N + 15) / 16 * 16) + kPivotWarps * pivot_warp_bytes(N, d); }
+size_t pivot_smem(int N, int d, int warps) {
+  return ((8 * (size_t)(d + 1) * N + 15) / 16 * 16) + warps * pivot_warp_bytes(N, d);
+}
 
 struct PivotDev {
   unsigned long long nvol_lo, nvol_hi, cells, boundary, next_count, flags, claimed;
@@ -257,7 +259,7 @@ __device__ void frontier_push(unsigned long long* next, unsigned long long cap, 
 
 // One breadth-first level: every cell of `cur` is processed by one warp; its new neighbours
 // enter the table and `next`.
-__global__ void __launch_bounds__(32 * kPivotWarps) k_pivot(const int64_t* pts, const int64_t* lifts, int N, int d,
+__global__ void __launch_bounds__(32 * kPivotMaxWarps) k_pivot(const int64_t* pts, const int64_t* lifts, int N, int d,
                                                             const unsigned long long* cur, unsigned long long ncur,
                                                             unsigned long long* table, unsigned long long cap,
                                                             int budget, unsigned long long* next, PivotDev* dv) {
@@ -279,8 +281,9 @@ __global__ void __launch_bounds__(32 * kPivotWarps) k_pivot(const int64_t* pts, 
   PivotWarp tm;
   bd::PivotAcc acc{};
   int flags = 0;
-  const unsigned long long gw = (unsigned long long)blockIdx.x * kPivotWarps + warp;
-  const unsigned long long nw = (unsigned long long)gridDim.x * kPivotWarps;
+  const int wpb = blockDim.x >> 5;
+  const unsigned long long gw = (unsigned long long)blockIdx.x * wpb + warp;
+  const unsigned long long nw = (unsigned long long)gridDim.x * wpb;
   for (unsigned long long c = gw; c < ncur; c += nw) {
     flags |= bd::pivot_cell(
         tm, P, L, N, d, cur[c], W, S, G0, sc, acc, [&](uint64_t m) { return table_claim(table, cap, m, dv); },
@@ -324,13 +327,24 @@ int device_pivot(const int64_t* pts, const int64_t* lifts, int N, int d, uint64_
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  const size_t smem = pivot_smem(N, d);
-  if (smem > (size_t)optin) return bd::set_error(BD_ERR_ARG, "the pivoting state exceeds shared memory");
-  cudaError_t e = cudaFuncSetAttribute(k_pivot, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  int per_sm = 0;
-  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pivot, 32 * kPivotWarps, smem);
+  if (pivot_smem(N, d, 1) > (size_t)optin) return bd::set_error(BD_ERR_ARG, "the pivoting state exceeds shared memory");
+  cudaError_t e = cudaFuncSetAttribute(k_pivot, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  // warps per block: the most resident warps per SM (the state is per warp)
+  int wpb = 1, per_sm = 0, best = 0;
+  for (int w = 1; w <= kPivotMaxWarps && e == cudaSuccess; ++w) {
+    const size_t sm_w = pivot_smem(N, d, w);
+    if (sm_w > (size_t)optin) break;
+    int b = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_pivot, 32 * w, sm_w);
+    if (b * w > best) {
+      best = b * w;
+      wpb = w;
+      per_sm = b;
+    }
+  }
   if (e != cudaSuccess) return bd::set_error(BD_ERR_CUDA, cudaGetErrorString(e));
   per_sm = std::max(per_sm, 1);
+  const size_t smem = pivot_smem(N, d, wpb);
   for (unsigned long long cap = 1ull << 22; cap <= (1ull << 31); cap <<= 3) {
     int64_t *d_pts = nullptr, *d_lifts = nullptr;
     unsigned long long *d_table = nullptr, *d_a = nullptr, *d_b = nullptr;
@@ -370,9 +384,9 @@ int device_pivot(const int64_t* pts, const int64_t* lifts, int N, int d, uint64_
       const unsigned long long zero = 0;
       e = cudaMemcpyAsync(&d_dv->next_count, &zero, sizeof(zero), cudaMemcpyHostToDevice, st);
       const unsigned long long blocks =
-          std::min<unsigned long long>((unsigned long long)sms * per_sm, (ncur + kPivotWarps - 1) / kPivotWarps);
+          std::min<unsigned long long>((unsigned long long)sms * per_sm, (ncur + wpb - 1) / wpb);
       if (e == cudaSuccess) {
-        k_pivot<<<(unsigned int)blocks, 32 * kPivotWarps, smem, st>>>(d_pts, d_lifts, N, d, d_a, ncur, d_table, cap,
+        k_pivot<<<(unsigned int)blocks, 32 * wpb, smem, st>>>(d_pts, d_lifts, N, d, d_a, ncur, d_table, cap,
                                                                        kWalkBudget, d_b, d_dv);
         e = cudaGetLastError();
       }
