@@ -385,9 +385,13 @@ int device_pivot(const int64_t* pts, const int64_t* lifts, int N, int d, uint64_
       e = cudaMemcpyAsync(&d_dv->next_count, &zero, sizeof(zero), cudaMemcpyHostToDevice, st);
       const unsigned long long blocks =
           std::min<unsigned long long>((unsigned long long)sms * per_sm, (ncur + wpb - 1) / wpb);
+      // while a level has fewer cells than resident warps, push every new neighbour to the next
+      // level (the list grows about d-fold per level) instead of walking from a few cells alone
+      const unsigned long long warps = (unsigned long long)sms * per_sm * wpb;
+      const int budget = ncur * 4 < warps ? 0 : kWalkBudget;
       if (e == cudaSuccess) {
         k_pivot<<<(unsigned int)blocks, 32 * wpb, smem, st>>>(d_pts, d_lifts, N, d, d_a, ncur, d_table, cap,
-                                                                       kWalkBudget, d_b, d_dv);
+                                                                       budget, d_b, d_dv);
         e = cudaGetLastError();
       }
       if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d_dv, sizeof(h), cudaMemcpyDeviceToHost, st);
