@@ -477,7 +477,7 @@ int host_pivot(const int64_t* pts, const int64_t* lifts, int N, int d, CellMask 
   std::mutex mu;
   auto step = [&](auto tm, std::vector<CellMask>& out) {
     (void)out;
-    for (uint64_t m : cur) {
+    for (CellMask m : cur) {
       const int f = bd::pivot_cell(
           tm, P.data(), lifts, N, d, m, W.data(), S.data(), G0.data(), &sc, acc,
           [&](CellMask nb) {

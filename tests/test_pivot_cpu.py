@@ -94,3 +94,15 @@ def test_host_pivot_large_coordinates_checked():
     with pytest.raises(bd.BinodegError) as e:
         bd.host_volume_pivot(big, oracle_lifts(10, 0))
     assert e.value.code == 2  # BD_ERR_OVERFLOW
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_host_pivot_more_than_64_points(seed):
+    # cells as 128-bit masks: points with indices beyond 63 take part
+    rng = random.Random(7700 + seed)
+    k = rng.choice([2, 3])
+    n = rng.randint(70, 120)
+    pts = [tuple(rng.randint(-6, 6) for _ in range(k)) for _ in range(n)]
+    r = bd.host_volume_pivot(np.array(pts), oracle_lifts(n, seed), walk_budget=8)
+    if r["status"] == 0:
+        assert r["nvol"] == nvol_placing(pts)
