@@ -24,7 +24,6 @@
 
 using bd::i128;
 using bd::u128;
-using bd::CellMask;
 
 namespace {
 
@@ -70,7 +69,7 @@ bool add_ok(i128 a, i128 b, i128& r) { return !__builtin_add_overflow(a, b, &r);
 // about F in a direction u orthogonal to F's affine span until a further point joins:
 // H' = w_q H - H(q) <u, a_p - a_f0> for the point q minimising H(q) / <u, a_q - a_f0> among
 // those with <u, .> > 0.  d steps give a cell.  pts is row-major (npts x d).
-int start_cell(const int64_t* pts, const int64_t* lifts, int N, int d, CellMask& mask) {
+int start_cell(const int64_t* pts, const int64_t* lifts, int N, int d, uint64_t& mask) {
   int v0 = 0;
   for (int p = 1; p < N; ++p)
     if (lifts[p] < lifts[v0]) v0 = p;
@@ -177,13 +176,13 @@ int start_cell(const int64_t* pts, const int64_t* lifts, int N, int d, CellMask&
   }
   if (!eval()) return START_OVERFLOW;
   mask = 0;
-  for (int f : F) mask |= bd::mbit(f);
+  for (int f : F) mask |= 1ull << f;
   for (int p = 0; p < N; ++p)
-    if (!bd::mhas(mask, p) && H[p] <= 0) return START_TIE;
+    if (!((mask >> p) & 1) && H[p] <= 0) return START_TIE;
   return START_OK;
 }
 
-// log2 of a Hadamard bound (reported, not enforced) on every minor of [M^T | a_p - a_s0]:
+// log2 of a Hadamard bound on every minor (of order <= d) of [M^T | a_p - a_s0] over all cells:
 // every column is a_x - a_s0 for one base s0 and distinct points x, so a minor is at most the
 // product of the d largest norms ||a_x - a_s0|| (each taken >= 1), maximised over s0
 double pivot_bound_log2(const int64_t* pts, int N, int d) {
@@ -224,49 +223,26 @@ struct PivotDev {
 
 constexpr int kWalkBudget = 64;  // cells a warp enters in place below each cell it eliminates
 
-enum { PF_TIE = 1, PF_INVALID = 2, PF_FULL = 4, PF_OVERFLOW = 8 };
+enum { PF_TIE = 1, PF_INVALID = 2, PF_FULL = 4 };
 
 constexpr unsigned long long kMaxProbes = 4096;  // linear probing below half load: ~2.5 on average
 
-// The hash set of cells: per slot a fingerprint (0: empty), then the full mask, whose high word
-// carries kReady once both words are written.  A claim takes a slot by compare-and-swap on the
-// fingerprint; a reader meeting an equal fingerprint waits (bounded) for the mask and compares
-// it in full.
-constexpr unsigned long long kReady = 1ull << 63;  // bit 127 of a mask: never a point
-struct CellTable {
-  unsigned long long* fp;
-  unsigned long long* lo;
-  unsigned long long* hi;
-};
-
 // Claim m: true if it was not in the table and now is.  The table stays at most half full
-// (counting every claimed cell); past that, after kMaxProbes, or after a bounded wait for a
-// slot being written, the level reports PF_FULL and the traversal restarts with a larger table.
-__device__ bool table_claim(CellTable t, unsigned long long cap, CellMask m, PivotDev* dv) {
-  const unsigned long long f = bd::pivot_hash(m), mlo = (uint64_t)m, mhi = (uint64_t)(m >> 64);
-  unsigned long long h = f & (cap - 1);
+// (counting every claimed cell); past that, or after kMaxProbes, the level reports PF_FULL and
+// the traversal restarts with a larger table.
+__device__ bool table_claim(unsigned long long* table, unsigned long long cap, unsigned long long m, PivotDev* dv) {
+  unsigned long long h = bd::pivot_hash(m) & (cap - 1);
   for (unsigned long long probe = 0; probe < kMaxProbes; ++probe) {
-    unsigned long long cur = *(volatile unsigned long long*)(t.fp + h);
+    const unsigned long long cur = table[h];
+    if (cur == m) return false;
     if (cur == 0ull) {
       if (2 * *(volatile unsigned long long*)&dv->claimed >= cap) break;  // too full
-      cur = atomicCAS(t.fp + h, 0ull, f);
-      if (cur == 0ull) {
-        t.lo[h] = mlo;
-        __threadfence();
-        *(volatile unsigned long long*)(t.hi + h) = mhi | kReady;
+      const unsigned long long old = atomicCAS(table + h, 0ull, m);
+      if (old == 0ull) {
         atomicAdd(&dv->claimed, 1ull);
         return true;
       }
-    }
-    if (cur == f) {  // maybe m: wait for the slot's mask
-      unsigned long long hv = 0;
-      for (int spin = 0; spin < (1 << 22); ++spin) {
-        hv = *(volatile unsigned long long*)(t.hi + h);
-        if (hv & kReady) break;
-      }
-      if (!(hv & kReady)) break;  // gave up waiting: report and restart
-      __threadfence();
-      if ((hv & ~kReady) == mhi && *(volatile unsigned long long*)(t.lo + h) == mlo) return false;
+      if (old == m) return false;
     }
     h = (h + 1) & (cap - 1);
   }
@@ -275,7 +251,7 @@ __device__ bool table_claim(CellTable t, unsigned long long cap, CellMask m, Piv
 }
 
 // append a claimed cell to the next level's list
-__device__ void frontier_push(CellMask* next, unsigned long long cap, CellMask m, PivotDev* dv) {
+__device__ void frontier_push(unsigned long long* next, unsigned long long cap, unsigned long long m, PivotDev* dv) {
   const unsigned long long pos = atomicAdd(&dv->next_count, 1ull);
   if (pos < cap) next[pos] = m;
   else atomicOr(&dv->flags, (unsigned long long)PF_FULL);
@@ -284,9 +260,9 @@ __device__ void frontier_push(CellMask* next, unsigned long long cap, CellMask m
 // One breadth-first level: every cell of `cur` is processed by one warp; its new neighbours
 // enter the table and `next`.
 __global__ void __launch_bounds__(32 * kPivotMaxWarps) k_pivot(const int64_t* pts, const int64_t* lifts, int N, int d,
-                                                            const CellMask* cur, unsigned long long ncur,
-                                                            CellTable table, unsigned long long cap,
-                                                            int budget, CellMask* next, PivotDev* dv) {
+                                                            const unsigned long long* cur, unsigned long long ncur,
+                                                            unsigned long long* table, unsigned long long cap,
+                                                            int budget, unsigned long long* next, PivotDev* dv) {
   extern __shared__ __align__(16) unsigned char smem[];
   int64_t* P = reinterpret_cast<int64_t*>(smem);  // coordinate-major, then the lifts
   int64_t* L = P + (size_t)d * N;
@@ -310,8 +286,8 @@ __global__ void __launch_bounds__(32 * kPivotMaxWarps) k_pivot(const int64_t* pt
   const unsigned long long nw = (unsigned long long)gridDim.x * wpb;
   for (unsigned long long c = gw; c < ncur; c += nw) {
     flags |= bd::pivot_cell(
-        tm, P, L, N, d, cur[c], W, S, G0, sc, acc, [&](CellMask m) { return table_claim(table, cap, m, dv); },
-        [&](CellMask m) { frontier_push(next, cap, m, dv); }, budget);
+        tm, P, L, N, d, cur[c], W, S, G0, sc, acc, [&](uint64_t m) { return table_claim(table, cap, m, dv); },
+        [&](uint64_t m) { frontier_push(next, cap, m, dv); }, budget);
   }
   if (lane == 0) {
     const unsigned long long lo = (uint64_t)acc.nvol, hi = (uint64_t)(acc.nvol >> 64);
@@ -324,15 +300,12 @@ __global__ void __launch_bounds__(32 * kPivotMaxWarps) k_pivot(const int64_t* pt
     if (acc.boundary) atomicAdd(&dv->boundary, (unsigned long long)acc.boundary);
     if (flags & bd::PV_TIE) atomicOr(&dv->flags, (unsigned long long)PF_TIE);
     if (flags & bd::PV_INVALID) atomicOr(&dv->flags, (unsigned long long)PF_INVALID);
-    if (flags & bd::PV_OVERFLOW) atomicOr(&dv->flags, (unsigned long long)PF_OVERFLOW);
   }
 }
 
-__global__ void k_pivot_seed(CellTable t, unsigned long long cap, CellMask m, CellMask* frontier, PivotDev* dv) {
-  const unsigned long long h = bd::pivot_hash(m) & (cap - 1);
-  t.fp[h] = bd::pivot_hash(m);
-  t.lo[h] = (uint64_t)m;
-  t.hi[h] = (uint64_t)(m >> 64) | kReady;
+__global__ void k_pivot_seed(unsigned long long* table, unsigned long long cap, unsigned long long m,
+                             unsigned long long* frontier, PivotDev* dv) {
+  table[bd::pivot_hash(m) & (cap - 1)] = m;
   frontier[0] = m;
   dv->claimed = 1;
 }
@@ -343,12 +316,12 @@ struct PivotRun {
   int flags = 0;  // PF_*
   int levels = 0;
   double ms = 0;
-  std::vector<CellMask> masks;  // host emulation: every cell
+  std::vector<uint64_t> masks;  // host emulation: every cell
 };
 
 // The traversal on the GPU from `start`; the table grows (and the traversal restarts) while it
 // would be more than half full.
-int device_pivot(const int64_t* pts, const int64_t* lifts, int N, int d, CellMask start, PivotRun& run) {
+int device_pivot(const int64_t* pts, const int64_t* lifts, int N, int d, uint64_t start, PivotRun& run) {
   cudaStream_t st = bd::thread_stream();
   int dev = 0, sms = 0, optin = 0;
   cudaGetDevice(&dev);
@@ -372,18 +345,15 @@ int device_pivot(const int64_t* pts, const int64_t* lifts, int N, int d, CellMas
   if (e != cudaSuccess) return bd::set_error(BD_ERR_CUDA, cudaGetErrorString(e));
   per_sm = std::max(per_sm, 1);
   const size_t smem = pivot_smem(N, d, wpb);
-  for (unsigned long long cap = 1ull << 22; cap <= (1ull << 31); cap <<= 3) {  // 56 bytes a slot
+  for (unsigned long long cap = 1ull << 22; cap <= (1ull << 31); cap <<= 3) {
     int64_t *d_pts = nullptr, *d_lifts = nullptr;
-    CellTable tab{nullptr, nullptr, nullptr};
-    CellMask *d_a = nullptr, *d_b = nullptr;
+    unsigned long long *d_table = nullptr, *d_a = nullptr, *d_b = nullptr;
     PivotDev* d_dv = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     auto release = [&]() {
       cudaFree(d_pts);
       cudaFree(d_lifts);
-      cudaFree(tab.fp);
-      cudaFree(tab.lo);
-      cudaFree(tab.hi);
+      cudaFree(d_table);
       cudaFree(d_a);
       cudaFree(d_b);
       cudaFree(d_dv);
@@ -392,21 +362,18 @@ int device_pivot(const int64_t* pts, const int64_t* lifts, int N, int d, CellMas
     };
     e = cudaMalloc(&d_pts, sizeof(int64_t) * N * d);
     if (e == cudaSuccess) e = cudaMalloc(&d_lifts, sizeof(int64_t) * N);
-    if (e == cudaSuccess) e = cudaMalloc(&tab.fp, sizeof(unsigned long long) * cap);
-    if (e == cudaSuccess) e = cudaMalloc(&tab.lo, sizeof(unsigned long long) * cap);
-    if (e == cudaSuccess) e = cudaMalloc(&tab.hi, sizeof(unsigned long long) * cap);
-    if (e == cudaSuccess) e = cudaMalloc(&d_a, sizeof(CellMask) * cap);
-    if (e == cudaSuccess) e = cudaMalloc(&d_b, sizeof(CellMask) * cap);
+    if (e == cudaSuccess) e = cudaMalloc(&d_table, sizeof(unsigned long long) * cap);
+    if (e == cudaSuccess) e = cudaMalloc(&d_a, sizeof(unsigned long long) * cap);
+    if (e == cudaSuccess) e = cudaMalloc(&d_b, sizeof(unsigned long long) * cap);
     if (e == cudaSuccess) e = cudaMalloc(&d_dv, sizeof(PivotDev));
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_pts, pts, sizeof(int64_t) * N * d, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_lifts, lifts, sizeof(int64_t) * N, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(tab.fp, 0, sizeof(unsigned long long) * cap, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(tab.hi, 0, sizeof(unsigned long long) * cap, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_table, 0, sizeof(unsigned long long) * cap, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_dv, 0, sizeof(PivotDev), st);
     if (e == cudaSuccess) {
-      k_pivot_seed<<<1, 1, 0, st>>>(tab, cap, start, d_a, d_dv);
+      k_pivot_seed<<<1, 1, 0, st>>>(d_table, cap, start, d_a, d_dv);
       e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaEventRecord(e0, st);
@@ -423,7 +390,7 @@ int device_pivot(const int64_t* pts, const int64_t* lifts, int N, int d, CellMas
       const unsigned long long warps = (unsigned long long)sms * per_sm * wpb;
       const int budget = ncur * 4 < warps ? 0 : kWalkBudget;
       if (e == cudaSuccess) {
-        k_pivot<<<(unsigned int)blocks, 32 * wpb, smem, st>>>(d_pts, d_lifts, N, d, d_a, ncur, tab, cap,
+        k_pivot<<<(unsigned int)blocks, 32 * wpb, smem, st>>>(d_pts, d_lifts, N, d, d_a, ncur, d_table, cap,
                                                                        budget, d_b, d_dv);
         e = cudaGetLastError();
       }
@@ -458,11 +425,7 @@ int device_pivot(const int64_t* pts, const int64_t* lifts, int N, int d, CellMas
 
 // The same traversal on the host: one team (one lane, or `width` lanes run as threads in
 // lockstep), cells in breadth-first order.
-struct MaskHash {
-  size_t operator()(CellMask m) const { return (size_t)bd::pivot_hash(m); }
-};
-
-int host_pivot(const int64_t* pts, const int64_t* lifts, int N, int d, CellMask start, int width, int budget,
+int host_pivot(const int64_t* pts, const int64_t* lifts, int N, int d, uint64_t start, int width, int budget,
                PivotRun& run) {
   std::vector<int64_t> P((size_t)d * N);
   for (int r = 0; r < d; ++r)
@@ -470,21 +433,21 @@ int host_pivot(const int64_t* pts, const int64_t* lifts, int N, int d, CellMask 
   std::vector<int64_t> W((size_t)d * (d + N)), G0(N);
   std::vector<i128> S(N);
   bd::PivotScratch sc{};
-  std::unordered_set<CellMask, MaskHash> seen{start};
-  std::vector<CellMask> cur{start}, next;
+  std::unordered_set<uint64_t> seen{start};
+  std::vector<uint64_t> cur{start}, next;
   bd::PivotAcc acc{};
   int flags = 0;
   std::mutex mu;
-  auto step = [&](auto tm, std::vector<CellMask>& out) {
+  auto step = [&](auto tm, std::vector<uint64_t>& out) {
     (void)out;
-    for (CellMask m : cur) {
+    for (uint64_t m : cur) {
       const int f = bd::pivot_cell(
           tm, P.data(), lifts, N, d, m, W.data(), S.data(), G0.data(), &sc, acc,
-          [&](CellMask nb) {
+          [&](uint64_t nb) {
             std::lock_guard<std::mutex> g(mu);  // lanes of a lockstep team claim concurrently
             return seen.insert(nb).second;
           },
-          [&](CellMask nb) {
+          [&](uint64_t nb) {
             std::lock_guard<std::mutex> g(mu);
             next.push_back(nb);
           },
@@ -500,7 +463,7 @@ int host_pivot(const int64_t* pts, const int64_t* lifts, int N, int d, CellMask 
       bd::LockstepShared shl(width);
       std::vector<std::thread> th;
       for (int l = 1; l < width; ++l) th.emplace_back([&, l] {
-        std::vector<CellMask> sink;  // unused: pushes go to `next`
+        std::vector<uint64_t> sink;  // only lane 0 inserts
         step(bd::LockstepTeam{&shl, l}, sink);
       });
       step(bd::LockstepTeam{&shl, 0}, next);
@@ -513,8 +476,7 @@ int host_pivot(const int64_t* pts, const int64_t* lifts, int N, int d, CellMask 
   run.nvol = acc.nvol;
   run.cells = acc.cells;
   run.boundary = acc.boundary;
-  run.flags = (flags & bd::PV_TIE ? PF_TIE : 0) | (flags & bd::PV_INVALID ? PF_INVALID : 0) |
-              (flags & bd::PV_OVERFLOW ? PF_OVERFLOW : 0);
+  run.flags = (flags & bd::PV_TIE ? PF_TIE : 0) | (flags & bd::PV_INVALID ? PF_INVALID : 0);
   run.masks.assign(seen.begin(), seen.end());  // every claimed cell was processed once
   std::sort(run.masks.begin(), run.masks.end());
   return BD_OK;
@@ -526,13 +488,13 @@ int pivot_common(const int64_t* points, const int64_t* given_lifts, int32_t npts
   if (!out || !points) return bd::set_error(BD_ERR_ARG, "NULL argument");
   std::memset(out, 0, sizeof(*out));
   if (k < 1 || k > bd::kPivotDMax) return bd::set_error(BD_ERR_ARG, "need 1 <= k <= 30 for the pivoting path");
-  if (npts < k + 1 || npts > bd::kPivotNMax) return bd::set_error(BD_ERR_ARG, "need k+1 <= npts <= 127");
-  if (cells && npts > 64) return bd::set_error(BD_ERR_ARG, "cell lists take at most 64 points");
+  if (npts < k + 1 || npts > 64) return bd::set_error(BD_ERR_ARG, "need k+1 <= npts <= 64");
   for (int i = 0; i < npts * k; ++i)
     if (points[i] >= (1 << 20) || points[i] <= -(1 << 20))
       return bd::set_error(BD_ERR_ARG, "coordinates must stay below 2^20 in magnitude on the pivoting path");
-  // informational: every 64-bit quotient of the walk is verified instead (PV_OVERFLOW)
-  out->bound_bits = (int32_t)std::ceil(pivot_bound_log2(points, npts, k));
+  const double bits = pivot_bound_log2(points, npts, k);
+  out->bound_bits = (int32_t)std::ceil(bits);
+  if (bits >= 61.99) return bd::set_error(BD_ERR_OVERFLOW, "cell minors may leave 62 bits");
   std::vector<int64_t> lifts(npts);
   const int attempts = given_lifts ? 1 : 8;
   for (int a = 0; a < attempts; ++a) {
@@ -547,7 +509,7 @@ int pivot_common(const int64_t* points, const int64_t* given_lifts, int32_t npts
       for (int i = 0; i < npts; ++i) lifts[i] = lift_height_wide(ss, i);
     }
     out->relifts = a;
-    CellMask start = 0;
+    uint64_t start = 0;
     const int sr = start_cell(points, lifts.data(), npts, k, start);
     if (sr == START_FLAT) {
       out->flags = BD_FLAG_DEGENERATE;
@@ -562,7 +524,6 @@ int pivot_common(const int64_t* points, const int64_t* given_lifts, int32_t npts
     const int rc = host_width > 0 ? host_pivot(points, lifts.data(), npts, k, start, host_width, host_budget, run)
                                   : device_pivot(points, lifts.data(), npts, k, start, run);
     if (rc) return rc;
-    if (run.flags & PF_OVERFLOW) return bd::set_error(BD_ERR_OVERFLOW, "a cell minor left 64 bits");
     if (run.flags & PF_INVALID) return bd::set_error(BD_ERR_ARG, "pivoting reached a non-cell (internal error)");
     if (run.flags & PF_TIE) {
       out->ties = 1;
@@ -577,7 +538,7 @@ int pivot_common(const int64_t* points, const int64_t* given_lifts, int32_t npts
     if (cells) {
       if ((int64_t)run.masks.size() > capacity)
         return bd::set_error(BD_ERR_ARG, "capacity is below the number of cells (out->cells holds it)");
-      for (size_t i = 0; i < run.masks.size(); ++i) cells[i] = (uint64_t)run.masks[i];
+      std::copy(run.masks.begin(), run.masks.end(), cells);
     }
     return BD_OK;
   }
@@ -605,8 +566,7 @@ int bd_host_volume_pivot(const int64_t* points, const int64_t* lifts, int32_t np
 int bd_degree_pivot(const int64_t* A, int32_t n, int32_t m, const int64_t* coef, uint64_t seed, bd_degree_out* out) {
   if (!out) return bd::set_error(BD_ERR_ARG, "out is NULL");
   if (!A && m > 0) return bd::set_error(BD_ERR_ARG, "A is NULL");
-  if (n < 1 || n >= bd::kPivotNMax || m < 0 || m > 256)
-    return bd::set_error(BD_ERR_ARG, "need 1 <= n <= 126, 0 <= m <= 256 on the pivoting path");
+  if (n < 1 || n >= BD_NMAX || m < 0 || m > 256) return bd::set_error(BD_ERR_ARG, "need 1 <= n < BD_NMAX, 0 <= m <= 256");
   std::memset(out, 0, sizeof(*out));
   bd::Reduction r;
   std::string err;

@@ -30,29 +30,9 @@
 
 namespace bd {
 
-constexpr int kPivotDMax = 30;   // dimension limit of the pivoting path
-constexpr int kPivotNMax = 127;  // point limit: a cell is a 128-bit mask (bit 127 stays free)
+constexpr int kPivotDMax = 30;  // dimension limit of the pivoting path (N <= 64 points)
 
-typedef u128 CellMask;  // bit p set: point p is a vertex of the cell
-
-BD_HD CellMask mbit(int p) { return (CellMask)1 << p; }
-BD_HD bool mhas(CellMask m, int p) { return (uint64_t)(m >> p) & 1u; }
-BD_HD int mpopc_below(CellMask m, int b) {  // set bits below bit b
-  const CellMask low = m & (mbit(b) - 1);
-  return popc64((uint64_t)low) + popc64((uint64_t)(low >> 64));
-}
-
-enum { PV_OK = 0, PV_TIE = 1, PV_INVALID = 2, PV_OVERFLOW = 4 };
-
-// (a p - b r) / d in 64 bits, verified: the quotient of the 64-bit route (exact modulo 2^64) is
-// multiplied back in 128 bits; a mismatch means the exact minor needs more than 64 bits and sets
-// *ovf.  The entries of the pivoting tableau are minors that the inputs of interest keep far
-// below 2^63, while Hadamard's inequality cannot promise it for them.
-BD_HD int64_t bareiss_checked(int64_t a, int64_t p, int64_t b, int64_t r, const Div64& D, int64_t d, int& ovf) {
-  const int64_t q = bareiss(a, p, b, r, D);
-  if ((i128)q * d != (i128)a * p - (i128)b * r) ovf |= PV_OVERFLOW;
-  return q;
-}
+enum { PV_OK = 0, PV_TIE = 1, PV_INVALID = 2 };
 
 // one lane's best candidate for a ridge
 struct PivotCand {
@@ -139,7 +119,7 @@ struct PivotAcc {
   uint64_t boundary;  // ridges on the boundary of conv(points)
 };
 
-// Process one cell (the mask of its d+1 points) and up to `budget` of its descendants: eliminate
+// Process one cell (bitmask of its d+1 points) and up to `budget` of its descendants: eliminate
 // it, check it, add |D|; then walk its ridges.  A neighbour that claim(mask) reports as new is
 // either entered in place (one rank-one pivot of the tableau, Sec. 4.2's pivot taken literally;
 // one more pivot leads back) or, past the budget or the stack depth, handed to push(mask) for a
@@ -151,13 +131,13 @@ struct PivotAcc {
 #pragma nv_exec_check_disable  // instantiated with host-only teams by the host emulation
 #endif
 template <class Team, class Claim, class Push>
-BD_HD int pivot_cell(Team tm, const int64_t* P, const int64_t* L, int N, int d, CellMask mask, int64_t* W, i128* S,
+BD_HD int pivot_cell(Team tm, const int64_t* P, const int64_t* L, int N, int d, uint64_t mask, int64_t* W, i128* S,
                      int64_t* G0, PivotScratch* sc, PivotAcc& acc, Claim claim, Push push, int budget) {
   const int lane = tm.lane(), nl = tm.lanes(), width = d + N;
   tm.sync();  // the previous cell's readers are done with the scratch
   if (lane == 0) sc->flags = 0;
-  for (int b = lane; b < N; b += nl)
-    if (mhas(mask, b)) sc->cidx[mpopc_below(mask, b)] = (uint8_t)b;
+  for (int b = lane; b < 64; b += nl)
+    if ((mask >> b) & 1) sc->cidx[popc64(mask & ((1ull << b) - 1))] = (uint8_t)b;
   tm.sync();
   const int s0 = sc->cidx[0];
   // W = [M^T | a_p - a_{s_0}]: row r holds coordinate r
@@ -191,21 +171,12 @@ BD_HD int pivot_cell(Team tm, const int64_t* P, const int64_t* L, int N, int d, 
     }
     const int64_t pk = W[k * width + k];
     const Div64 D = make_div(prev);
-    int ovf = 0;
     for (int c = k + 1 + lane; c < width; c += nl) {
       const int64_t top = W[k * width + c];
       for (int i = 0; i < d; ++i)
-        if (i != k) W[i * width + c] = bareiss_checked(W[i * width + c], pk, W[i * width + k], top, D, prev, ovf);
-    }
-    if (ovf) {
-#ifdef __CUDA_ARCH__
-      atomicOr(&sc->flags, ovf);
-#else
-      __atomic_fetch_or(&sc->flags, ovf, __ATOMIC_RELAXED);
-#endif
+        if (i != k) W[i * width + c] = bareiss(W[i * width + c], pk, W[i * width + k], top, D);
     }
     tm.sync();
-    if (sc->flags) return sc->flags;  // uniform: read after the sync
     prev = pk;
   }
   const int64_t Dv = prev;  // +-det M: the cell's normalized volume up to sign
@@ -219,10 +190,8 @@ BD_HD int pivot_cell(Team tm, const int64_t* P, const int64_t* L, int N, int d, 
       s -= (i128)g * (L[sc->cidx[j + 1]] - L[s0]);
     }
     S[p] = s;
-    const i128 g0 = (i128)Dv - gs;  // itself a minor
-    if (g0 != (i128)(int64_t)g0) fl |= PV_OVERFLOW;
-    G0[p] = (int64_t)g0;
-    if (!mhas(mask, p)) {
+    G0[p] = (int64_t)((i128)Dv - gs);  // itself a minor: fits
+    if (!((mask >> p) & 1)) {
       const int sg = (s > 0) - (s < 0);
       if (sg == 0) fl |= PV_TIE;
       else if (sg != (Dv > 0 ? 1 : -1)) fl |= PV_INVALID;
@@ -256,14 +225,12 @@ BD_HD int pivot_cell(Team tm, const int64_t* P, const int64_t* L, int N, int d, 
     const Div64 Dd = make_div(Dold);
     const Div128 Dw = make_div((i128)Dold);
     const i128 sq = sc->sq;
-    int ovf = 0;
     for (int p = lane; p < N; p += nl) {
       const int64_t ti = T(i, p);
       for (int r = 0; r <= d; ++r)
-        if (r != i) T(r, p) = bareiss_checked(T(r, p), piv, sc->colq[r], ti, Dd, Dold, ovf);
-      S[p] = bareiss(S[p], (i128)piv, sq, (i128)ti, Dw);  // D' times a height: far inside 2^127
+        if (r != i) T(r, p) = bareiss(T(r, p), piv, sc->colq[r], ti, Dd);
+      S[p] = bareiss(S[p], (i128)piv, sq, (i128)ti, Dw);
     }
-    raise(ovf);
     tm.sync();
     if (lane == 0) {
       sc->D = piv;
@@ -281,7 +248,7 @@ BD_HD int pivot_cell(Team tm, const int64_t* P, const int64_t* L, int N, int d, 
       PivotCand best{0, 0, -1, 0};
       float bf = 0.f;  // best's ratio in single precision
       for (int p = 0; p < N; ++p) {
-        if (mhas(mask, p)) continue;
+        if ((mask >> p) & 1) continue;
         const int64_t gi = T(r, p);
         if (gi == 0 || (gi > 0 ? 1 : -1) == sd) continue;  // not beyond the ridge
         PivotCand c{S[p], gi, p, 0};
@@ -299,7 +266,7 @@ BD_HD int pivot_cell(Team tm, const int64_t* P, const int64_t* L, int N, int d, 
         bf = approx_f(best.s) / (float)(-best.g);
       }
       sc->nbr[lvl][r] = best.p < 0 ? (uint8_t)255 : (uint8_t)best.p;
-      if (best.p >= 0 && claim((mask & ~mbit(sc->cidx[r])) | mbit(best.p))) fresh |= 1ull << r;
+      if (best.p >= 0 && claim((mask & ~(1ull << sc->cidx[r])) | (1ull << best.p))) fresh |= 1ull << r;
     }
     fresh = tm.or_all(fresh);
     tm.sync();  // the neighbours are visible to every lane
@@ -314,15 +281,14 @@ BD_HD int pivot_cell(Team tm, const int64_t* P, const int64_t* L, int N, int d, 
       const int i = sc->st_slot[depth], o = sc->st_old[depth], q = sc->cidx[i];
       todo = sc->st_todo[depth];
       pivot_to(i, o);  // back to the parent cell
-      if (sc->flags) return sc->flags;
-      mask = (mask & ~mbit(q)) | mbit(o);
+      mask = (mask & ~(1ull << q)) | (1ull << o);
       continue;
     }
     const int r = ctz64((uint64_t)todo);
     if (depth + 1 < kWalkDepth && entered < budget) {  // enter the neighbour in place
       todo &= todo - 1;
       const int q = sc->nbr[depth][r];
-      const CellMask nm = (mask & ~mbit(sc->cidx[r])) | mbit(q);
+      const uint64_t nm = (mask & ~(1ull << sc->cidx[r])) | (1ull << q);
       if (lane == 0) {
         sc->st_slot[depth] = (uint8_t)r;
         sc->st_old[depth] = sc->cidx[r];
@@ -335,7 +301,7 @@ BD_HD int pivot_cell(Team tm, const int64_t* P, const int64_t* L, int N, int d, 
       const int sdn = sc->D > 0 ? 1 : -1;
       int f2 = 0;
       for (int p = lane; p < N; p += nl) {
-        if (mhas(mask, p)) continue;
+        if ((mask >> p) & 1) continue;
         const int sg = (S[p] > 0) - (S[p] < 0);
         if (sg == 0) f2 |= PV_TIE;
         else if (sg != sdn) f2 |= PV_INVALID;
@@ -353,7 +319,7 @@ BD_HD int pivot_cell(Team tm, const int64_t* P, const int64_t* L, int N, int d, 
     }
     // past the budget or the depth: this cell's remaining new neighbours go to the next level
     for (int rr = lane; rr <= d; rr += nl)
-      if ((todo >> rr) & 1) push((mask & ~mbit(sc->cidx[rr])) | mbit(sc->nbr[depth][rr]));
+      if ((todo >> rr) & 1) push((mask & ~(1ull << sc->cidx[rr])) | (1ull << sc->nbr[depth][rr]));
     todo = 0;
     tm.sync();
   }
@@ -361,9 +327,6 @@ BD_HD int pivot_cell(Team tm, const int64_t* P, const int64_t* L, int N, int d, 
   return sc->flags;
 }
 
-// a cell mask's fingerprint, never 0 (0 marks an empty slot of the hash set)
-BD_HD uint64_t pivot_hash(CellMask m) {
-  return splitmix_mix((uint64_t)m ^ splitmix_mix((uint64_t)(m >> 64) + 0x632BE59BD9B4E019ull)) | 1ull;
-}
+BD_HD uint64_t pivot_hash(uint64_t m) { return splitmix_mix(m); }  // a cell mask spread over the table
 
 }  // namespace bd

@@ -81,28 +81,3 @@ def test_host_pivot_degenerate_ties_and_errors():
         bd.host_volume_pivot(np.array([[0], [1 << 21]]), [1, 2])  # coordinate range
     with pytest.raises(bd.BinodegError):
         bd.host_volume_pivot(sq, [1, 2, 3, 4], team_width=40)
-
-
-def test_host_pivot_large_coordinates_checked():
-    rng = random.Random(7500)
-    # k = 3 with coordinates near 2^19: minors near 2^57, exact in 64 bits
-    pts = [tuple(rng.randint(-(1 << 19), 1 << 19) for _ in range(3)) for _ in range(9)]
-    r = bd.host_volume_pivot(np.array(pts), oracle_lifts(9, 0))
-    assert r["status"] == 0 and r["nvol"] == nvol_placing(pts)
-    # k = 6: minors near 2^114 cannot be held; the verified quotients report it
-    big = np.array([[rng.randint(-(1 << 19), 1 << 19) for _ in range(6)] for _ in range(10)])
-    with pytest.raises(bd.BinodegError) as e:
-        bd.host_volume_pivot(big, oracle_lifts(10, 0))
-    assert e.value.code == 2  # BD_ERR_OVERFLOW
-
-
-@pytest.mark.parametrize("seed", range(3))
-def test_host_pivot_more_than_64_points(seed):
-    # cells as 128-bit masks: points with indices beyond 63 take part
-    rng = random.Random(7700 + seed)
-    k = rng.choice([2, 3])
-    n = rng.randint(70, 120)
-    pts = [tuple(rng.randint(-6, 6) for _ in range(k)) for _ in range(n)]
-    r = bd.host_volume_pivot(np.array(pts), oracle_lifts(n, seed), walk_budget=8)
-    if r["status"] == 0:
-        assert r["nvol"] == nvol_placing(pts)
