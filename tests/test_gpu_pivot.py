@@ -71,3 +71,20 @@ def test_gpu_degree_above_kmax_walks_the_cells(mk):
     r = bd.degree(s.A, s.coef)
     assert r["flags"] & bd.BD_FLAG_PIVOT
     assert r["dim"] == m * k + 2 > bd.KMAX and r["degree"] == TABLE["degree"][mk]
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_gpu_subset_cells_equal_pivot_walk(seed):
+    # the GPU subset enumeration's cells (bd_cells) and the pivoting walk under the same heights
+    rng = random.Random(7900 + seed)
+    k = rng.choice([4, 5, 6, 8])
+    n = rng.randint(k + 6, 22)
+    P = np.array([[rng.randint(-3, 3) for _ in range(k)] for _ in range(n)])
+    cells, vol = bd.cells(P, seed=seed, capacity=1 << 15)
+    if vol["relifts"] or vol["flags"] & bd.BD_FLAG_DEGENERATE:
+        return
+    from oracle.lifts import lifts as oracle_lifts
+    piv = bd.host_volume_pivot(P, oracle_lifts(n, seed), cells=True)
+    assert piv["status"] == 0
+    assert set(piv["cell_list"]) == {tuple(sorted(c["cell"])) for c in cells}
+    assert piv["nvol"] == vol["nvol"]

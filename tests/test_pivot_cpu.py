@@ -81,3 +81,18 @@ def test_host_pivot_degenerate_ties_and_errors():
         bd.host_volume_pivot(np.array([[0], [1 << 21]]), [1, 2])  # coordinate range
     with pytest.raises(bd.BinodegError):
         bd.host_volume_pivot(sq, [1, 2, 3, 4], team_width=40)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_host_pivot_cells_equal_subset_enumeration(seed):
+    # the two walkers of the library, under the same heights, list the same triangulation
+    rng = random.Random(7800 + seed)
+    k = rng.choice([4, 5, 6, 7])
+    n = rng.randint(k + 6, 18)
+    P = np.array([[rng.randint(-3, 3) for _ in range(k)] for _ in range(n)])
+    W = oracle_lifts(n, seed)
+    piv = bd.host_volume_pivot(P, W, cells=True)
+    if piv["status"] != 0 or piv["flags"] & bd.BD_FLAG_DEGENERATE:
+        return
+    enum = bd.host_cells(P, W, capacity=1 << 14)
+    assert set(piv["cell_list"]) == {tuple(sorted(c["cell"])) for c in enum}
