@@ -78,7 +78,7 @@ int bd_set_stream(void* stream);
 
 /*
  * Degree of V(x^A - b) (Props. 1, 2, 4).
- *   A    : n x m integers, column i = alpha_i - beta_i (Eq. standard-form); 1 <= n < BD_NMAX,
+ *   A    : n x m integers, column i = alpha_i - beta_i (Eq. standard-form); 1 <= n <= 126,
  *          0 <= m <= 256.
  *   coef : NULL (generic coefficients: the system is taken as consistent) or 4*m integers,
  *          binomial i -> (num1, den1, num2, den2) = c_{i,1}, c_{i,2} as fractions,
@@ -86,8 +86,9 @@ int bd_set_stream(void* stream);
  *          is decided exactly.  Denominators and numerators must be nonzero.
  *   seed : lift seed; the result does not depend on it.
  * Host reduction (Smith form, LLL-reduced kernel basis, torsion) runs on the CPU; the
- * volume on the GPU: the subset enumeration up to dimension BD_KMAX, the pivoting walk of
- * bd_volume_pivot above it (up to 30; BD_FLAG_PIVOT, subsets = ridges examined).
+ * volume on the GPU: the subset enumeration up to dimension BD_KMAX and BD_NMAX points (n + 1,
+ * the origin included), the pivoting walk of bd_volume_pivot beyond either (dimension up to 30;
+ * BD_FLAG_PIVOT, subsets = ridges examined).
  * dim = 0 gives degree = torsion; dim = 1 is a segment, whose normalized
  * length max - min of the kernel points (and 0) is taken directly (kernel points of any size
  * below 2^62; the enumeration takes coordinates below 2^40).  Errors: BD_ERR_ARG,
@@ -436,7 +437,8 @@ int bd_host_mixed_volume_lifted(const int64_t* points, const int32_t* counts, in
  * work grows with the number of cells, not with C(npts, k+1).  The start cell is found by
  * extension from the lowest lifted point; the neighbour across a ridge is the point beyond it
  * of least height / (-barycentric coordinate), decided exactly.
- *   points : npts x k integers, |x| < 2^20, k+1 <= npts <= 64, 1 <= k <= 30
+ *   points : npts x k integers, |x| < 2^20, k+1 <= npts <= 127, 1 <= k <= 30 (a cell is a mask
+ *            of its points: one 64-bit word up to 64 points, two words above)
  *   seed   : lift seed: heights 1 + (top 40 bits of bd_volume's SplitMix64 stream), in [1, 2^40],
  *            wider than bd_volume's because up to ~1e8 cells are walked; a tie re-lifts (8 liftings)
  *   out    : nvol, cells, ties, relifts, flags (BD_FLAG_DEGENERATE when not full-dimensional),
@@ -452,13 +454,13 @@ int bd_volume_pivot(const int64_t* points, int32_t npts, int32_t k, uint64_t see
  * returns BD_ERR_TIES), one team of team_width lanes (1..32; more than 1 runs them as threads in
  * lockstep), for CPU tests.  walk_budget: cells entered in place (by one tableau pivot each)
  * below every eliminated cell (the GPU path uses 64; 0 eliminates every cell).  cells: NULL, or
- * capacity bitmasks of the cells' points (bit p for point p), increasing; fewer than out->cells
- * -> BD_ERR_ARG. */
+ * capacity bitmasks of the cells' points (bit p for point p; npts <= 64), increasing; fewer than
+ * out->cells -> BD_ERR_ARG. */
 int bd_host_volume_pivot(const int64_t* points, const int64_t* lifts, int32_t npts, int32_t k, int32_t team_width,
                          int32_t walk_budget, bd_volume_out* out, uint64_t* cells, int64_t capacity);
 
-/* bd_degree with the volume by pivoting: solution sets of dimension up to 30 (BD_NMAX - 1
- * variables), e.g. the master spaces of Table mspace-deg beyond the reach of bd_degree. */
+/* bd_degree with the volume always by pivoting: up to 126 variables and solution sets of
+ * dimension up to 30, e.g. the master spaces of Table mspace-deg. */
 int bd_degree_pivot(const int64_t* A, int32_t n, int32_t m, const int64_t* coef, uint64_t seed, bd_degree_out* out);
 
 #ifdef __cplusplus

@@ -210,7 +210,7 @@ def host_volume_lifted(points, lifts, threads: int = 1, force_int128: bool = Fal
 
 def volume_pivot(points, seed: int = 0) -> dict:
     """bd_volume_pivot: exact NVol_k(conv points) by simplicial pivoting over the cells on the GPU
-    (output-sensitive; k <= 30, up to 64 points); adds the traversal's GPU time as device_ms."""
+    (output-sensitive; k <= 30, up to 127 points); adds the traversal's GPU time as device_ms."""
     P = i64(points)
     npts, k = P.shape
     out, ms = VolumeOut(), C.c_double(0)

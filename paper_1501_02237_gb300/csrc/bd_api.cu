@@ -469,7 +469,7 @@ int bd_volume_lifted(const int64_t* points, const int64_t* lifts, int32_t npts, 
 int bd_reduce(const int64_t* A, int32_t n, int32_t m, const int64_t* coef, int64_t* points, int64_t* info) {
   if (!A && m > 0) return fail(BD_ERR_ARG, "A is NULL");
   if (!points || !info) return fail(BD_ERR_ARG, "NULL output");
-  if (n < 1 || n >= BD_NMAX || m < 0 || m > 256) return fail(BD_ERR_ARG, "need 1 <= n < BD_NMAX, 0 <= m <= 256");
+  if (n < 1 || n > 126 || m < 0 || m > 256) return fail(BD_ERR_ARG, "need 1 <= n <= 126, 0 <= m <= 256");
   bd::Reduction r;
   std::string err;
   int rc = bd::reduce_system(A, n, m, coef, r, err);
@@ -487,7 +487,7 @@ int bd_reduce(const int64_t* A, int32_t n, int32_t m, const int64_t* coef, int64
 int bd_degree(const int64_t* A, int32_t n, int32_t m, const int64_t* coef, uint64_t seed, bd_degree_out* out) {
   if (!out) return fail(BD_ERR_ARG, "out is NULL");
   if (!A && m > 0) return fail(BD_ERR_ARG, "A is NULL");
-  if (n < 1 || n >= BD_NMAX || m < 0 || m > 256) return fail(BD_ERR_ARG, "need 1 <= n < BD_NMAX, 0 <= m <= 256");
+  if (n < 1 || n > 126 || m < 0 || m > 256) return fail(BD_ERR_ARG, "need 1 <= n <= 126, 0 <= m <= 256");
   std::memset(out, 0, sizeof(*out));
   bd::Reduction r;
   std::string err;
@@ -507,7 +507,9 @@ int bd_degree(const int64_t* A, int32_t n, int32_t m, const int64_t* coef, uint6
     set_u128(out->degree_lo, out->degree_hi, r.torsion);
     return BD_OK;
   }
-  if (r.dim > BD_KMAX) {  // beyond the subset enumeration: walk the cells by pivoting instead
+  // beyond the subset enumeration (dimension above BD_KMAX, or more than BD_NMAX points in two
+  // or more dimensions): walk the cells by pivoting instead
+  if (r.dim > BD_KMAX || (r.dim > 1 && n + 1 > BD_NMAX)) {
     bd_volume_out v;
     double ms = 0;
     rc = bd_volume_pivot(r.points.data(), n + 1, r.dim, seed, &v, &ms);

@@ -12,6 +12,7 @@
 #include <mutex>
 #include <string>
 #include <thread>
+#include <type_traits>
 #include <unordered_set>
 #include <vector>
 
@@ -69,7 +70,8 @@ bool add_ok(i128 a, i128 b, i128& r) { return !__builtin_add_overflow(a, b, &r);
 // about F in a direction u orthogonal to F's affine span until a further point joins:
 // H' = w_q H - H(q) <u, a_p - a_f0> for the point q minimising H(q) / <u, a_q - a_f0> among
 // those with <u, .> > 0.  d steps give a cell.  pts is row-major (npts x d).
-int start_cell(const int64_t* pts, const int64_t* lifts, int N, int d, uint64_t& mask) {
+template <class Mask>
+int start_cell(const int64_t* pts, const int64_t* lifts, int N, int d, Mask& mask) {
   int v0 = 0;
   for (int p = 1; p < N; ++p)
     if (lifts[p] < lifts[v0]) v0 = p;
@@ -175,10 +177,10 @@ int start_cell(const int64_t* pts, const int64_t* lifts, int N, int d, uint64_t&
     if (!extended) return START_FLAT;  // every point lies in F's affine span
   }
   if (!eval()) return START_OVERFLOW;
-  mask = 0;
-  for (int f : F) mask |= 1ull << f;
+  mask = Mask{};
+  for (int f : F) bd::madd(mask, f);
   for (int p = 0; p < N; ++p)
-    if (!((mask >> p) & 1) && H[p] <= 0) return START_TIE;
+    if (!bd::mhas(mask, p) && H[p] <= 0) return START_TIE;
   return START_OK;
 }
 
@@ -227,31 +229,114 @@ enum { PF_TIE = 1, PF_INVALID = 2, PF_FULL = 4 };
 
 constexpr unsigned long long kMaxProbes = 4096;  // linear probing below half load: ~2.5 on average
 
-// Claim m: true if it was not in the table and now is.  The table stays at most half full
-// (counting every claimed cell); past that, or after kMaxProbes, the level reports PF_FULL and
-// the traversal restarts with a larger table.
-__device__ bool table_claim(unsigned long long* table, unsigned long long cap, unsigned long long m, PivotDev* dv) {
-  unsigned long long h = bd::pivot_hash(m) & (cap - 1);
-  for (unsigned long long probe = 0; probe < kMaxProbes; ++probe) {
-    const unsigned long long cur = table[h];
-    if (cur == m) return false;
-    if (cur == 0ull) {
-      if (2 * *(volatile unsigned long long*)&dv->claimed >= cap) break;  // too full
-      const unsigned long long old = atomicCAS(table + h, 0ull, m);
-      if (old == 0ull) {
-        atomicAdd(&dv->claimed, 1ull);
-        return true;
-      }
-      if (old == m) return false;
-    }
-    h = (h + 1) & (cap - 1);
+// The hash set of claimed cells, one slot per cell.  Claims stay at most half the capacity
+// (counting every claimed cell); past that, after kMaxProbes, or after a bounded wait for a
+// slot being written, the level reports PF_FULL and the traversal restarts with a larger table.
+template <class Mask>
+struct CellTable;
+
+// one-word masks (at most 64 points): a slot holds the mask itself, 0 when empty
+template <>
+struct CellTable<uint64_t> {
+  unsigned long long* slot = nullptr;
+
+  cudaError_t alloc(unsigned long long cap) { return cudaMalloc(&slot, sizeof(unsigned long long) * cap); }
+  cudaError_t clear(unsigned long long cap, cudaStream_t st) {
+    return cudaMemsetAsync(slot, 0, sizeof(unsigned long long) * cap, st);
   }
-  atomicOr(&dv->flags, (unsigned long long)PF_FULL);
-  return false;
-}
+  void release() { cudaFree(slot); }
+  __device__ void seed(unsigned long long cap, uint64_t m) const { slot[bd::pivot_hash(m) & (cap - 1)] = m; }
+  // true if m was not in the table and now is
+  __device__ bool claim(unsigned long long cap, uint64_t m, unsigned long long* claimed, unsigned long long* flags) const {
+    unsigned long long h = bd::pivot_hash(m) & (cap - 1);
+    for (unsigned long long probe = 0; probe < kMaxProbes; ++probe) {
+      const unsigned long long cur = slot[h];
+      if (cur == m) return false;
+      if (cur == 0ull) {
+        if (2 * *(volatile unsigned long long*)claimed >= cap) break;  // too full
+        const unsigned long long old = atomicCAS(slot + h, 0ull, m);
+        if (old == 0ull) {
+          atomicAdd(claimed, 1ull);
+          return true;
+        }
+        if (old == m) return false;
+      }
+      h = (h + 1) & (cap - 1);
+    }
+    atomicOr(flags, (unsigned long long)PF_FULL);
+    return false;
+  }
+};
+
+// two-word masks (up to 127 points): per slot a fingerprint (0: empty) and the two words; the
+// high word carries kReady once both are written.  A claim takes a slot by compare-and-swap on
+// the fingerprint; a reader meeting an equal fingerprint waits (bounded) for the words and
+// compares them in full.
+constexpr unsigned long long kReady = 1ull << 63;  // bit 127 of a mask: never a point
+
+template <>
+struct CellTable<bd::WideMask> {
+  unsigned long long *fp = nullptr, *lo = nullptr, *hi = nullptr;
+
+  cudaError_t alloc(unsigned long long cap) {
+    cudaError_t e = cudaMalloc(&fp, sizeof(unsigned long long) * cap);
+    if (e == cudaSuccess) e = cudaMalloc(&lo, sizeof(unsigned long long) * cap);
+    if (e == cudaSuccess) e = cudaMalloc(&hi, sizeof(unsigned long long) * cap);
+    return e;
+  }
+  cudaError_t clear(unsigned long long cap, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(fp, 0, sizeof(unsigned long long) * cap, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(hi, 0, sizeof(unsigned long long) * cap, st);
+    return e;
+  }
+  void release() {
+    cudaFree(fp);
+    cudaFree(lo);
+    cudaFree(hi);
+  }
+  __device__ void seed(unsigned long long cap, bd::WideMask m) const {
+    const unsigned long long h = bd::pivot_hash(m) & (cap - 1);
+    fp[h] = bd::pivot_hash(m);
+    lo[h] = m.lo;
+    hi[h] = m.hi | kReady;
+  }
+  __device__ bool claim(unsigned long long cap, bd::WideMask m, unsigned long long* claimed,
+                        unsigned long long* flags) const {
+    const unsigned long long f = bd::pivot_hash(m);
+    unsigned long long h = f & (cap - 1);
+    for (unsigned long long probe = 0; probe < kMaxProbes; ++probe) {
+      unsigned long long cur = *(volatile unsigned long long*)(fp + h);
+      if (cur == 0ull) {
+        if (2 * *(volatile unsigned long long*)claimed >= cap) break;  // too full
+        cur = atomicCAS(fp + h, 0ull, f);
+        if (cur == 0ull) {
+          lo[h] = m.lo;
+          __threadfence();
+          *(volatile unsigned long long*)(hi + h) = m.hi | kReady;
+          atomicAdd(claimed, 1ull);
+          return true;
+        }
+      }
+      if (cur == f) {  // maybe m: wait for the slot's words
+        unsigned long long hv = 0;
+        for (int spin = 0; spin < (1 << 22); ++spin) {
+          hv = *(volatile unsigned long long*)(hi + h);
+          if (hv & kReady) break;
+        }
+        if (!(hv & kReady)) break;  // gave up waiting: report and restart
+        __threadfence();
+        if ((hv & ~kReady) == m.hi && *(volatile unsigned long long*)(lo + h) == m.lo) return false;
+      }
+      h = (h + 1) & (cap - 1);
+    }
+    atomicOr(flags, (unsigned long long)PF_FULL);
+    return false;
+  }
+};
 
 // append a claimed cell to the next level's list
-__device__ void frontier_push(unsigned long long* next, unsigned long long cap, unsigned long long m, PivotDev* dv) {
+template <class Mask>
+__device__ void frontier_push(Mask* next, unsigned long long cap, Mask m, PivotDev* dv) {
   const unsigned long long pos = atomicAdd(&dv->next_count, 1ull);
   if (pos < cap) next[pos] = m;
   else atomicOr(&dv->flags, (unsigned long long)PF_FULL);
@@ -259,10 +344,11 @@ __device__ void frontier_push(unsigned long long* next, unsigned long long cap, 
 
 // One breadth-first level: every cell of `cur` is processed by one warp; its new neighbours
 // enter the table and `next`.
+template <class Mask>
 __global__ void __launch_bounds__(32 * kPivotMaxWarps) k_pivot(const int64_t* pts, const int64_t* lifts, int N, int d,
-                                                            const unsigned long long* cur, unsigned long long ncur,
-                                                            unsigned long long* table, unsigned long long cap,
-                                                            int budget, unsigned long long* next, PivotDev* dv) {
+                                                            const Mask* cur, unsigned long long ncur,
+                                                            CellTable<Mask> table, unsigned long long cap,
+                                                            int budget, Mask* next, PivotDev* dv) {
   extern __shared__ __align__(16) unsigned char smem[];
   int64_t* P = reinterpret_cast<int64_t*>(smem);  // coordinate-major, then the lifts
   int64_t* L = P + (size_t)d * N;
@@ -286,8 +372,9 @@ __global__ void __launch_bounds__(32 * kPivotMaxWarps) k_pivot(const int64_t* pt
   const unsigned long long nw = (unsigned long long)gridDim.x * wpb;
   for (unsigned long long c = gw; c < ncur; c += nw) {
     flags |= bd::pivot_cell(
-        tm, P, L, N, d, cur[c], W, S, G0, sc, acc, [&](uint64_t m) { return table_claim(table, cap, m, dv); },
-        [&](uint64_t m) { frontier_push(next, cap, m, dv); }, budget);
+        tm, P, L, N, d, cur[c], W, S, G0, sc, acc,
+        [&](Mask m) { return table.claim(cap, m, &dv->claimed, &dv->flags); },
+        [&](Mask m) { frontier_push(next, cap, m, dv); }, budget);
   }
   if (lane == 0) {
     const unsigned long long lo = (uint64_t)acc.nvol, hi = (uint64_t)(acc.nvol >> 64);
@@ -303,9 +390,9 @@ __global__ void __launch_bounds__(32 * kPivotMaxWarps) k_pivot(const int64_t* pt
   }
 }
 
-__global__ void k_pivot_seed(unsigned long long* table, unsigned long long cap, unsigned long long m,
-                             unsigned long long* frontier, PivotDev* dv) {
-  table[bd::pivot_hash(m) & (cap - 1)] = m;
+template <class Mask>
+__global__ void k_pivot_seed(CellTable<Mask> t, unsigned long long cap, Mask m, Mask* frontier, PivotDev* dv) {
+  t.seed(cap, m);
   frontier[0] = m;
   dv->claimed = 1;
 }
@@ -321,21 +408,22 @@ struct PivotRun {
 
 // The traversal on the GPU from `start`; the table grows (and the traversal restarts) while it
 // would be more than half full.
-int device_pivot(const int64_t* pts, const int64_t* lifts, int N, int d, uint64_t start, PivotRun& run) {
+template <class Mask>
+int device_pivot(const int64_t* pts, const int64_t* lifts, int N, int d, Mask start, PivotRun& run) {
   cudaStream_t st = bd::thread_stream();
   int dev = 0, sms = 0, optin = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (pivot_smem(N, d, 1) > (size_t)optin) return bd::set_error(BD_ERR_ARG, "the pivoting state exceeds shared memory");
-  cudaError_t e = cudaFuncSetAttribute(k_pivot, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  cudaError_t e = cudaFuncSetAttribute(k_pivot<Mask>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
   // warps per block: the most resident warps per SM (the state is per warp)
   int wpb = 1, per_sm = 0, best = 0;
   for (int w = 1; w <= kPivotMaxWarps && e == cudaSuccess; ++w) {
     const size_t sm_w = pivot_smem(N, d, w);
     if (sm_w > (size_t)optin) break;
     int b = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_pivot, 32 * w, sm_w);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_pivot<Mask>, 32 * w, sm_w);
     if (b * w > best) {
       best = b * w;
       wpb = w;
@@ -347,13 +435,14 @@ int device_pivot(const int64_t* pts, const int64_t* lifts, int N, int d, uint64_
   const size_t smem = pivot_smem(N, d, wpb);
   for (unsigned long long cap = 1ull << 22; cap <= (1ull << 31); cap <<= 3) {
     int64_t *d_pts = nullptr, *d_lifts = nullptr;
-    unsigned long long *d_table = nullptr, *d_a = nullptr, *d_b = nullptr;
+    CellTable<Mask> table;
+    Mask *d_a = nullptr, *d_b = nullptr;
     PivotDev* d_dv = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     auto release = [&]() {
       cudaFree(d_pts);
       cudaFree(d_lifts);
-      cudaFree(d_table);
+      table.release();
       cudaFree(d_a);
       cudaFree(d_b);
       cudaFree(d_dv);
@@ -362,18 +451,18 @@ int device_pivot(const int64_t* pts, const int64_t* lifts, int N, int d, uint64_
     };
     e = cudaMalloc(&d_pts, sizeof(int64_t) * N * d);
     if (e == cudaSuccess) e = cudaMalloc(&d_lifts, sizeof(int64_t) * N);
-    if (e == cudaSuccess) e = cudaMalloc(&d_table, sizeof(unsigned long long) * cap);
-    if (e == cudaSuccess) e = cudaMalloc(&d_a, sizeof(unsigned long long) * cap);
-    if (e == cudaSuccess) e = cudaMalloc(&d_b, sizeof(unsigned long long) * cap);
+    if (e == cudaSuccess) e = table.alloc(cap);
+    if (e == cudaSuccess) e = cudaMalloc(&d_a, sizeof(Mask) * cap);
+    if (e == cudaSuccess) e = cudaMalloc(&d_b, sizeof(Mask) * cap);
     if (e == cudaSuccess) e = cudaMalloc(&d_dv, sizeof(PivotDev));
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_pts, pts, sizeof(int64_t) * N * d, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_lifts, lifts, sizeof(int64_t) * N, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(d_table, 0, sizeof(unsigned long long) * cap, st);
+    if (e == cudaSuccess) e = table.clear(cap, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_dv, 0, sizeof(PivotDev), st);
     if (e == cudaSuccess) {
-      k_pivot_seed<<<1, 1, 0, st>>>(d_table, cap, start, d_a, d_dv);
+      k_pivot_seed<Mask><<<1, 1, 0, st>>>(table, cap, start, d_a, d_dv);
       e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaEventRecord(e0, st);
@@ -390,7 +479,7 @@ int device_pivot(const int64_t* pts, const int64_t* lifts, int N, int d, uint64_
       const unsigned long long warps = (unsigned long long)sms * per_sm * wpb;
       const int budget = ncur * 4 < warps ? 0 : kWalkBudget;
       if (e == cudaSuccess) {
-        k_pivot<<<(unsigned int)blocks, 32 * wpb, smem, st>>>(d_pts, d_lifts, N, d, d_a, ncur, d_table, cap,
+        k_pivot<Mask><<<(unsigned int)blocks, 32 * wpb, smem, st>>>(d_pts, d_lifts, N, d, d_a, ncur, table, cap,
                                                                        budget, d_b, d_dv);
         e = cudaGetLastError();
       }
@@ -425,7 +514,13 @@ int device_pivot(const int64_t* pts, const int64_t* lifts, int N, int d, uint64_
 
 // The same traversal on the host: one team (one lane, or `width` lanes run as threads in
 // lockstep), cells in breadth-first order.
-int host_pivot(const int64_t* pts, const int64_t* lifts, int N, int d, uint64_t start, int width, int budget,
+struct MaskHash {
+  size_t operator()(uint64_t m) const { return (size_t)bd::pivot_hash(m); }
+  size_t operator()(bd::WideMask m) const { return (size_t)bd::pivot_hash(m); }
+};
+
+template <class Mask>
+int host_pivot(const int64_t* pts, const int64_t* lifts, int N, int d, Mask start, int width, int budget,
                PivotRun& run) {
   std::vector<int64_t> P((size_t)d * N);
   for (int r = 0; r < d; ++r)
@@ -433,21 +528,20 @@ int host_pivot(const int64_t* pts, const int64_t* lifts, int N, int d, uint64_t 
   std::vector<int64_t> W((size_t)d * (d + N)), G0(N);
   std::vector<i128> S(N);
   bd::PivotScratch sc{};
-  std::unordered_set<uint64_t> seen{start};
-  std::vector<uint64_t> cur{start}, next;
+  std::unordered_set<Mask, MaskHash> seen{start};
+  std::vector<Mask> cur{start}, next;
   bd::PivotAcc acc{};
   int flags = 0;
   std::mutex mu;
-  auto step = [&](auto tm, std::vector<uint64_t>& out) {
-    (void)out;
-    for (uint64_t m : cur) {
+  auto step = [&](auto tm) {  // neighbours go to `next` under the mutex
+    for (const Mask m : cur) {
       const int f = bd::pivot_cell(
           tm, P.data(), lifts, N, d, m, W.data(), S.data(), G0.data(), &sc, acc,
-          [&](uint64_t nb) {
+          [&](Mask nb) {
             std::lock_guard<std::mutex> g(mu);  // lanes of a lockstep team claim concurrently
             return seen.insert(nb).second;
           },
-          [&](uint64_t nb) {
+          [&](Mask nb) {
             std::lock_guard<std::mutex> g(mu);
             next.push_back(nb);
           },
@@ -458,15 +552,12 @@ int host_pivot(const int64_t* pts, const int64_t* lifts, int N, int d, uint64_t 
   while (!cur.empty() && !flags) {
     next.clear();
     if (width <= 1) {
-      step(bd::HostTeam{}, next);
+      step(bd::HostTeam{});
     } else {
       bd::LockstepShared shl(width);
       std::vector<std::thread> th;
-      for (int l = 1; l < width; ++l) th.emplace_back([&, l] {
-        std::vector<uint64_t> sink;  // only lane 0 inserts
-        step(bd::LockstepTeam{&shl, l}, sink);
-      });
-      step(bd::LockstepTeam{&shl, 0}, next);
+      for (int l = 1; l < width; ++l) th.emplace_back([&, l] { step(bd::LockstepTeam{&shl, l}); });
+      step(bd::LockstepTeam{&shl, 0});
       for (auto& t : th) t.join();
     }
 
@@ -477,8 +568,10 @@ int host_pivot(const int64_t* pts, const int64_t* lifts, int N, int d, uint64_t 
   run.cells = acc.cells;
   run.boundary = acc.boundary;
   run.flags = (flags & bd::PV_TIE ? PF_TIE : 0) | (flags & bd::PV_INVALID ? PF_INVALID : 0);
-  run.masks.assign(seen.begin(), seen.end());  // every claimed cell was processed once
-  std::sort(run.masks.begin(), run.masks.end());
+  if constexpr (std::is_same<Mask, uint64_t>::value) {  // cell lists: at most 64 points
+    run.masks.assign(seen.begin(), seen.end());             // every claimed cell was processed once
+    std::sort(run.masks.begin(), run.masks.end());
+  }
   return BD_OK;
 }
 
@@ -488,7 +581,8 @@ int pivot_common(const int64_t* points, const int64_t* given_lifts, int32_t npts
   if (!out || !points) return bd::set_error(BD_ERR_ARG, "NULL argument");
   std::memset(out, 0, sizeof(*out));
   if (k < 1 || k > bd::kPivotDMax) return bd::set_error(BD_ERR_ARG, "need 1 <= k <= 30 for the pivoting path");
-  if (npts < k + 1 || npts > 64) return bd::set_error(BD_ERR_ARG, "need k+1 <= npts <= 64");
+  if (npts < k + 1 || npts > bd::kPivotNMax) return bd::set_error(BD_ERR_ARG, "need k+1 <= npts <= 127");
+  if (cells && npts > 64) return bd::set_error(BD_ERR_ARG, "cell lists take at most 64 points");
   for (int i = 0; i < npts * k; ++i)
     if (points[i] >= (1 << 20) || points[i] <= -(1 << 20))
       return bd::set_error(BD_ERR_ARG, "coordinates must stay below 2^20 in magnitude on the pivoting path");
@@ -509,8 +603,10 @@ int pivot_common(const int64_t* points, const int64_t* given_lifts, int32_t npts
       for (int i = 0; i < npts; ++i) lifts[i] = lift_height_wide(ss, i);
     }
     out->relifts = a;
-    uint64_t start = 0;
-    const int sr = start_cell(points, lifts.data(), npts, k, start);
+    uint64_t start = 0;      // at most 64 points: one-word masks
+    bd::WideMask wide{0, 0};  // more: two words
+    const int sr = npts <= 64 ? start_cell(points, lifts.data(), npts, k, start)
+                              : start_cell(points, lifts.data(), npts, k, wide);
     if (sr == START_FLAT) {
       out->flags = BD_FLAG_DEGENERATE;
       return BD_OK;
@@ -521,8 +617,13 @@ int pivot_common(const int64_t* points, const int64_t* given_lifts, int32_t npts
       continue;
     }
     PivotRun run;
-    const int rc = host_width > 0 ? host_pivot(points, lifts.data(), npts, k, start, host_width, host_budget, run)
-                                  : device_pivot(points, lifts.data(), npts, k, start, run);
+    int rc;
+    if (npts <= 64)
+      rc = host_width > 0 ? host_pivot(points, lifts.data(), npts, k, start, host_width, host_budget, run)
+                          : device_pivot(points, lifts.data(), npts, k, start, run);
+    else
+      rc = host_width > 0 ? host_pivot(points, lifts.data(), npts, k, wide, host_width, host_budget, run)
+                          : device_pivot(points, lifts.data(), npts, k, wide, run);
     if (rc) return rc;
     if (run.flags & PF_INVALID) return bd::set_error(BD_ERR_ARG, "pivoting reached a non-cell (internal error)");
     if (run.flags & PF_TIE) {
@@ -566,7 +667,8 @@ int bd_host_volume_pivot(const int64_t* points, const int64_t* lifts, int32_t np
 int bd_degree_pivot(const int64_t* A, int32_t n, int32_t m, const int64_t* coef, uint64_t seed, bd_degree_out* out) {
   if (!out) return bd::set_error(BD_ERR_ARG, "out is NULL");
   if (!A && m > 0) return bd::set_error(BD_ERR_ARG, "A is NULL");
-  if (n < 1 || n >= BD_NMAX || m < 0 || m > 256) return bd::set_error(BD_ERR_ARG, "need 1 <= n < BD_NMAX, 0 <= m <= 256");
+  if (n < 1 || n >= bd::kPivotNMax || m < 0 || m > 256)
+    return bd::set_error(BD_ERR_ARG, "need 1 <= n <= 126, 0 <= m <= 256 on the pivoting path");
   std::memset(out, 0, sizeof(*out));
   bd::Reduction r;
   std::string err;

@@ -30,7 +30,37 @@
 
 namespace bd {
 
-constexpr int kPivotDMax = 30;  // dimension limit of the pivoting path (N <= 64 points)
+constexpr int kPivotDMax = 30;   // dimension limit of the pivoting path
+constexpr int kPivotNMax = 127;  // point limit: a cell is a mask of up to 127 point bits
+
+// A cell is the set of its d+1 points, kept as a bit mask: one 64-bit word while there are at
+// most 64 points, two words (every shift below 64) up to 127.  The walk is generic in the mask.
+struct WideMask {
+  uint64_t lo, hi;  // bits 0..63 and 64..126
+};
+BD_HD bool operator==(WideMask a, WideMask b) { return a.lo == b.lo && a.hi == b.hi; }
+
+BD_HD bool mhas(uint64_t m, int p) { return (m >> p) & 1ull; }
+BD_HD bool mhas(WideMask m, int p) { return ((p < 64 ? m.lo >> p : m.hi >> (p - 64)) & 1ull) != 0; }
+// number of the mask's points below point b
+BD_HD int mrank(uint64_t m, int b) { return popc64(m & ((1ull << b) - 1)); }
+BD_HD int mrank(WideMask m, int b) {
+  return b < 64 ? popc64(m.lo & ((1ull << b) - 1)) : popc64(m.lo) + popc64(m.hi & ((1ull << (b - 64)) - 1));
+}
+// the mask without point `out`, with point `in`
+BD_HD uint64_t mswap(uint64_t m, int out, int in) { return (m & ~(1ull << out)) | (1ull << in); }
+BD_HD WideMask mswap(WideMask m, int out, int in) {
+  if (out < 64) m.lo &= ~(1ull << out);
+  else m.hi &= ~(1ull << (out - 64));
+  if (in < 64) m.lo |= 1ull << in;
+  else m.hi |= 1ull << (in - 64);
+  return m;
+}
+BD_HD void madd(uint64_t& m, int p) { m |= 1ull << p; }
+BD_HD void madd(WideMask& m, int p) {
+  if (p < 64) m.lo |= 1ull << p;
+  else m.hi |= 1ull << (p - 64);
+}
 
 enum { PV_OK = 0, PV_TIE = 1, PV_INVALID = 2 };
 
@@ -130,14 +160,14 @@ struct PivotAcc {
 #ifdef __CUDACC__
 #pragma nv_exec_check_disable  // instantiated with host-only teams by the host emulation
 #endif
-template <class Team, class Claim, class Push>
-BD_HD int pivot_cell(Team tm, const int64_t* P, const int64_t* L, int N, int d, uint64_t mask, int64_t* W, i128* S,
+template <class Team, class Mask, class Claim, class Push>
+BD_HD int pivot_cell(Team tm, const int64_t* P, const int64_t* L, int N, int d, Mask mask, int64_t* W, i128* S,
                      int64_t* G0, PivotScratch* sc, PivotAcc& acc, Claim claim, Push push, int budget) {
   const int lane = tm.lane(), nl = tm.lanes(), width = d + N;
   tm.sync();  // the previous cell's readers are done with the scratch
   if (lane == 0) sc->flags = 0;
-  for (int b = lane; b < 64; b += nl)
-    if ((mask >> b) & 1) sc->cidx[popc64(mask & ((1ull << b) - 1))] = (uint8_t)b;
+  for (int b = lane; b < N; b += nl)
+    if (mhas(mask, b)) sc->cidx[mrank(mask, b)] = (uint8_t)b;
   tm.sync();
   const int s0 = sc->cidx[0];
   // W = [M^T | a_p - a_{s_0}]: row r holds coordinate r
@@ -191,7 +221,7 @@ BD_HD int pivot_cell(Team tm, const int64_t* P, const int64_t* L, int N, int d, 
     }
     S[p] = s;
     G0[p] = (int64_t)((i128)Dv - gs);  // itself a minor: fits
-    if (!((mask >> p) & 1)) {
+    if (!mhas(mask, p)) {
       const int sg = (s > 0) - (s < 0);
       if (sg == 0) fl |= PV_TIE;
       else if (sg != (Dv > 0 ? 1 : -1)) fl |= PV_INVALID;
@@ -248,7 +278,7 @@ BD_HD int pivot_cell(Team tm, const int64_t* P, const int64_t* L, int N, int d, 
       PivotCand best{0, 0, -1, 0};
       float bf = 0.f;  // best's ratio in single precision
       for (int p = 0; p < N; ++p) {
-        if ((mask >> p) & 1) continue;
+        if (mhas(mask, p)) continue;
         const int64_t gi = T(r, p);
         if (gi == 0 || (gi > 0 ? 1 : -1) == sd) continue;  // not beyond the ridge
         PivotCand c{S[p], gi, p, 0};
@@ -266,7 +296,7 @@ BD_HD int pivot_cell(Team tm, const int64_t* P, const int64_t* L, int N, int d, 
         bf = approx_f(best.s) / (float)(-best.g);
       }
       sc->nbr[lvl][r] = best.p < 0 ? (uint8_t)255 : (uint8_t)best.p;
-      if (best.p >= 0 && claim((mask & ~(1ull << sc->cidx[r])) | (1ull << best.p))) fresh |= 1ull << r;
+      if (best.p >= 0 && claim(mswap(mask, sc->cidx[r], best.p))) fresh |= 1ull << r;
     }
     fresh = tm.or_all(fresh);
     tm.sync();  // the neighbours are visible to every lane
@@ -281,14 +311,14 @@ BD_HD int pivot_cell(Team tm, const int64_t* P, const int64_t* L, int N, int d, 
       const int i = sc->st_slot[depth], o = sc->st_old[depth], q = sc->cidx[i];
       todo = sc->st_todo[depth];
       pivot_to(i, o);  // back to the parent cell
-      mask = (mask & ~(1ull << q)) | (1ull << o);
+      mask = mswap(mask, q, o);
       continue;
     }
     const int r = ctz64((uint64_t)todo);
     if (depth + 1 < kWalkDepth && entered < budget) {  // enter the neighbour in place
       todo &= todo - 1;
       const int q = sc->nbr[depth][r];
-      const uint64_t nm = (mask & ~(1ull << sc->cidx[r])) | (1ull << q);
+      const Mask nm = mswap(mask, sc->cidx[r], q);
       if (lane == 0) {
         sc->st_slot[depth] = (uint8_t)r;
         sc->st_old[depth] = sc->cidx[r];
@@ -301,7 +331,7 @@ BD_HD int pivot_cell(Team tm, const int64_t* P, const int64_t* L, int N, int d, 
       const int sdn = sc->D > 0 ? 1 : -1;
       int f2 = 0;
       for (int p = lane; p < N; p += nl) {
-        if ((mask >> p) & 1) continue;
+        if (mhas(mask, p)) continue;
         const int sg = (S[p] > 0) - (S[p] < 0);
         if (sg == 0) f2 |= PV_TIE;
         else if (sg != sdn) f2 |= PV_INVALID;
@@ -319,7 +349,7 @@ BD_HD int pivot_cell(Team tm, const int64_t* P, const int64_t* L, int N, int d, 
     }
     // past the budget or the depth: this cell's remaining new neighbours go to the next level
     for (int rr = lane; rr <= d; rr += nl)
-      if ((todo >> rr) & 1) push((mask & ~(1ull << sc->cidx[rr])) | (1ull << sc->nbr[depth][rr]));
+      if ((todo >> rr) & 1) push(mswap(mask, sc->cidx[rr], sc->nbr[depth][rr]));
     todo = 0;
     tm.sync();
   }
@@ -328,5 +358,7 @@ BD_HD int pivot_cell(Team tm, const int64_t* P, const int64_t* L, int N, int d, 
 }
 
 BD_HD uint64_t pivot_hash(uint64_t m) { return splitmix_mix(m); }  // a cell mask spread over the table
+// a two-word mask's fingerprint, never 0 (0 marks an empty slot of the two-word table)
+BD_HD uint64_t pivot_hash(WideMask m) { return splitmix_mix(m.lo ^ splitmix_mix(m.hi + 0x632BE59BD9B4E019ull)) | 1ull; }
 
 }  // namespace bd

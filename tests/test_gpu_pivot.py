@@ -1,7 +1,8 @@
 """Simplicial pivoting on the GPU (bd_volume_pivot, bd_degree_pivot): the same volume as the
 subset enumeration and the same cells as the host emulation on random point sets; the
 master-space degrees of Table mspace-deg, which the subset enumeration cannot reach
-(W_{2,7} .. W_{4,4}: 4.2e11 to 1.9e13 subsets, dimensions 16 to 18)."""
+(W_{2,7} .. W_{4,4}: 4.2e11 to 1.9e13 subsets, dimensions 16 to 18); 65 to 127 points (two-word
+cell masks) against the oracle's placing volume, and bd_degree's route to the walk there."""
 
 import json
 import os
@@ -12,6 +13,7 @@ import pytest
 
 import paper_1501_02237_gb300 as bd
 from oracle.lifts import ATTEMPT_MULT, GOLDEN, MASK, mix
+from oracle.volume import nvol_placing
 from workloads import config_system, master_space_system
 
 pytestmark = pytest.mark.gpu
@@ -88,3 +90,30 @@ def test_gpu_subset_cells_equal_pivot_walk(seed):
     assert piv["status"] == 0
     assert set(piv["cell_list"]) == {tuple(sorted(c["cell"])) for c in cells}
     assert piv["nvol"] == vol["nvol"]
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_gpu_pivot_two_word_masks_match_oracle(seed):
+    # more than 64 points: cells are two-word masks; exact against the oracle's placing volume
+    rng = random.Random(8400 + seed)
+    k = [3, 4, 5, 6, 4, 5, 3, 4][seed]
+    n = [65, 127, rng.randint(66, 126), rng.randint(66, 80), 100, 120, 127, 64][seed]
+    pts = [tuple(rng.randint(-3, 3) for _ in range(k)) for _ in range(n)]
+    r = bd.volume_pivot(np.array(pts), seed=seed)
+    assert r["nvol"] == nvol_placing(pts)
+    if r["relifts"] == 0 and not (r["flags"] & bd.BD_FLAG_DEGENERATE):
+        h = bd.host_volume_pivot(np.array(pts), wide_lifts(n, seed))
+        assert (h["nvol"], h["cells"]) == (r["nvol"], r["cells"])
+
+
+def test_gpu_degree_beyond_64_points_walks_the_cells():
+    # 89 variables, solution set of dimension 5: 90 points, past the subset enumeration
+    rng = random.Random(8500)
+    d, n = 5, 89
+    R = np.array([[rng.randint(-2, 2) for _ in range(d)] for _ in range(n - d)], dtype=np.int64)
+    A = np.vstack([-R.T, np.eye(n - d, dtype=np.int64)])  # kernel lattice spanned by [I; R]
+    pts = [tuple(int(v) for v in row) for row in np.vstack([np.eye(d, dtype=np.int64), R])] + [(0,) * d]
+    g = bd.degree(A)
+    assert g["flags"] & bd.BD_FLAG_PIVOT
+    assert g["nvol"] == nvol_placing(pts) and g["degree"] == g["nvol"] * g["torsion"]
+    assert bd.degree_pivot(A)["degree"] == g["degree"]

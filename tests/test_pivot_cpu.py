@@ -96,3 +96,59 @@ def test_host_pivot_cells_equal_subset_enumeration(seed):
         return
     enum = bd.host_cells(P, W, capacity=1 << 14)
     assert set(piv["cell_list"]) == {tuple(sorted(c["cell"])) for c in enum}
+
+
+def wide_system(n, d, rng):
+    """A system in n variables whose solution set has dimension d and whose kernel lattice is
+    spanned by the columns of [I_d; R]: A = [-R^T; I_{n-d}], so the points of Eq. 6 are e_1..e_d,
+    the rows of R and the origin (up to a unimodular change of basis)."""
+    R = np.array([[rng.randint(-2, 2) for _ in range(d)] for _ in range(n - d)], dtype=np.int64)
+    A = np.vstack([-R.T, np.eye(n - d, dtype=np.int64)])
+    pts = [tuple(int(v) for v in row) for row in np.vstack([np.eye(d, dtype=np.int64), R])] + [(0,) * d]
+    return A, pts
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_host_pivot_two_word_masks_match_placing(seed):
+    # 65..127 points: cells are two-word masks; cells and volume as for one-word masks
+    rng = random.Random(8100 + seed)
+    k = rng.choice([3, 4, 5])
+    n = [65, 90, 127, rng.randint(66, 126), rng.randint(66, 126)][seed]
+    pts = [tuple(rng.randint(-3, 3) for _ in range(k)) for _ in range(n)]
+    W = oracle_lifts(n, seed)
+    for width, budget in [(1, 0), (7, 64)]:
+        r = bd.host_volume_pivot(np.array(pts), W, team_width=width, walk_budget=budget)
+        assert r["status"] == 0
+        assert r["nvol"] == nvol_placing(pts)
+        assert r["subsets"] == (k + 1) * r["cells"]
+
+
+def test_reduce_beyond_64_variables():
+    rng = random.Random(8200)
+    A, pts = wide_system(90, 4, rng)
+    red = bd.reduce(A)
+    assert red["dim"] == 4 and red["torsion"] == 1 and red["points"].shape == (91, 4)
+    # the reduced points are the kernel basis up to a unimodular map: same normalized volume
+    W = oracle_lifts(91, 1)
+    r = bd.host_volume_pivot(red["points"], W)
+    assert r["status"] == 0 and r["nvol"] == nvol_placing(pts)
+    with pytest.raises(bd.BinodegError):
+        bd.reduce(np.zeros((127, 3), dtype=np.int64))  # above 126 variables
+
+
+def test_two_word_mask_errors():
+    rng = random.Random(8300)
+    pts = np.array([[rng.randint(-3, 3) for _ in range(3)] for _ in range(80)])
+    with pytest.raises(bd.BinodegError):
+        bd.host_volume_pivot(pts, oracle_lifts(80, 0), cells=True)  # cell lists: 64 points at most
+    big = np.array([[rng.randint(-3, 3) for _ in range(3)] for _ in range(128)])
+    with pytest.raises(bd.BinodegError):
+        bd.host_volume_pivot(big, oracle_lifts(128, 0))  # above 127 points
+
+
+def test_pivot_refuses_minors_past_the_bound():
+    # W_{3,8}: 73 points in dimension 26, Hadamard bound of the cell minors 65 bits > 62; the
+    # refusal comes from the host before any device work
+    A = master_space_system(3, 8).A
+    with pytest.raises(bd.BinodegError, match="62 bits"):
+        bd.degree_pivot(A)
