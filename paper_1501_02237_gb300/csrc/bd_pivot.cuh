@@ -20,9 +20,9 @@
 // both g of the far side having the sign opposite to D).  A point other than the cell's with
 // s(p) of the wrong sign, a zero height or two equal ratios mean the lifting is not generic.
 //
-// Parallel layout: a warp owns one cell; its lanes own the matrix columns in the elimination
-// and the points in the height and ridge stages; each ridge's minimum is a tree reduction over
-// the lanes' candidates in shared memory.
+// Parallel layout: a warp owns one cell; its lanes own the matrix columns in the elimination and
+// the points in the height stage; in the ridge stage lane r takes ridge r and scans every point
+// for its minimum, and the lanes claim their neighbours concurrently.
 #pragma once
 
 #include "bd_core.cuh"
