@@ -99,7 +99,7 @@ int bd_degree(const int64_t* A, int32_t n, int32_t m, const int64_t* coef, uint6
 
 /*
  * Host front end of bd_degree only (no GPU): Smith form, torsion, consistency and the
- * LLL-reduced kernel points.  points receives (n + 1) x d integers (row i = point i, the
+ * LLL-reduced kernel points; A as for bd_degree (1 <= n <= 126).  points receives (n + 1) x d integers (row i = point i, the
  * last row the origin) and must hold (n + 1) * n entries.  info receives 8 int64:
  * {rank, dim, torsion, consistent, max_abs_coord, 0, 0, 0}.
  */
