@@ -412,11 +412,12 @@ template <class Mask>
 int device_pivot(const int64_t* pts, const int64_t* lifts, int N, int d, Mask start, PivotRun& run) {
   cudaStream_t st = bd::thread_stream();
   int dev = 0, sms = 0, optin = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaError_t e = cudaGetDevice(&dev);  // no device: a CUDA error, never a host fallback
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return bd::set_error(BD_ERR_CUDA, cudaGetErrorString(e));
   if (pivot_smem(N, d, 1) > (size_t)optin) return bd::set_error(BD_ERR_ARG, "the pivoting state exceeds shared memory");
-  cudaError_t e = cudaFuncSetAttribute(k_pivot<Mask>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  e = cudaFuncSetAttribute(k_pivot<Mask>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
   // warps per block: the most resident warps per SM (the state is per warp)
   int wpb = 1, per_sm = 0, best = 0;
   for (int w = 1; w <= kPivotMaxWarps && e == cudaSuccess; ++w) {

@@ -13,6 +13,7 @@ import numpy as np
 import pytest
 
 import paper_1501_02237_gb300 as bd
+from paper_1501_02237_gb300._lib import BD_ERR_CUDA
 from oracle.cells import lower_cells
 from oracle.lifts import lifts as oracle_lifts
 from oracle.volume import nvol_placing
@@ -152,3 +153,18 @@ def test_pivot_refuses_minors_past_the_bound():
     A = master_space_system(3, 8).A
     with pytest.raises(bd.BinodegError, match="62 bits"):
         bd.degree_pivot(A)
+
+
+def test_device_paths_fail_loudly_without_a_gpu():
+    # no host fallback: without a CUDA device the GPU entry points return BD_ERR_CUDA
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    rng = random.Random(8600)
+    small = np.array([[0, 0], [1, 0], [0, 1], [1, 1], [2, 1]])
+    A, _ = wide_system(80, 3, rng)  # 81 points: bd_degree routes it to the walk
+    for call in (lambda: bd.volume(small), lambda: bd.volume_pivot(small), lambda: bd.degree(A),
+                 lambda: bd.degree_pivot(A)):
+        with pytest.raises(bd.BinodegError) as err:
+            call()
+        assert err.value.code == BD_ERR_CUDA
