@@ -246,12 +246,13 @@ template <class T>
 int device_run(const MixedPrep& mp, const std::vector<T>& rows, uint64_t cap, RunResult& rr) {
   cudaStream_t st = bd::thread_stream();
   int dev = 0, sms = 0, optin = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaError_t e = cudaGetDevice(&dev);  // no device: a CUDA error, never a host fallback
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return bd::set_error(BD_ERR_CUDA, cudaGetErrorString(e));
   if (smem_bytes(mp, sizeof(T), 1) > (size_t)optin)
     return bd::set_error(BD_ERR_ARG, "the problem's walk state exceeds shared memory");
-  cudaError_t e = cudaFuncSetAttribute(k_mixed<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  e = cudaFuncSetAttribute(k_mixed<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
   // warps per block: the most resident warps per SM (the walk state is per warp, so the
   // block size decides how much of the shared memory is left unused)
   int wpb = 1, per_sm = 0, best = 0;

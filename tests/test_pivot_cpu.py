@@ -163,8 +163,10 @@ def test_device_paths_fail_loudly_without_a_gpu():
     rng = random.Random(8600)
     small = np.array([[0, 0], [1, 0], [0, 1], [1, 1], [2, 1]])
     A, _ = wide_system(80, 3, rng)  # 81 points: bd_degree routes it to the walk
+    supports = [np.array([[0, 0], [1, 0], [0, 1]]), np.array([[0, 0], [2, 0], [0, 1], [1, 1]])]
     for call in (lambda: bd.volume(small), lambda: bd.volume_pivot(small), lambda: bd.degree(A),
-                 lambda: bd.degree_pivot(A)):
+                 lambda: bd.degree_pivot(A), lambda: bd.mixed_volume(supports),
+                 lambda: bd.start_solutions(small), lambda: bd.cells(small)):
         with pytest.raises(bd.BinodegError) as err:
             call()
         assert err.value.code == BD_ERR_CUDA
