@@ -69,6 +69,14 @@ typedef struct {
   int32_t max_abs_coord;         /* largest |coordinate| of the reduced kernel points */
 } bd_degree_out;
 
+/* Fault injection for tests of the out-of-memory paths (host side: nothing fails on the GPU).
+ * Arms the library's device-allocation wrapper so that the after-th device allocation from now
+ * (0: the next one) fails as cudaMalloc does when the device is out of memory, once; the call
+ * that makes it returns BD_ERR_NOMEM, as every call does on a real out-of-memory error, and
+ * frees what it had allocated.  after < 0 disarms.  The environment variable
+ * BD_INJECT_ALLOC_FAILURE, read when the library loads, arms it the same way.  Always BD_OK. */
+int bd_inject_alloc_failure(int32_t after);
+
 /* Message of the last failed call on this thread ("" if none). Owned by the library. */
 const char* bd_last_error(void);
 
@@ -237,8 +245,10 @@ int bd_batch_destroy(bd_batch* batch);
  * (order 0) or by smallest predicted cost (order 1; predicted_cost from the cost model, or <= 0
  * for the closed-form bound).  Admitted systems' items interleave on the device with those of
  * systems already running.  Finished degrees are returned by bd_server_poll with their latency
- * from submission.  Served systems need dimension <= 10 and 32/64-bit minors (BD_ERR_ARG
- * otherwise: use bd_degree).  Results are identical to bd_degree's.
+ * from submission.  Results are identical to bd_degree's.  Systems that the persistent kernel does
+ * not carry (128-bit minors, dimension above 10, more than 64 points: up to 126 variables are
+ * accepted, as by bd_degree) are served by a side worker thread that runs bd_degree's volume
+ * path, in arrival order, on a stream of its own beside the persistent kernel.
  */
 typedef struct bd_server bd_server;
 typedef struct {
@@ -256,6 +266,9 @@ typedef struct {
   int64_t submitted, completed, relifted, launches;
   int64_t ring_items;
   int32_t slots, blocks, warps_per_block, waiting;
+  int64_t routed;            /* requests served by the side route */
+  int32_t peak_resident;     /* most requests holding a slot (items on the device) at once */
+  int32_t reserved;
 } bd_server_stats;
 int bd_server_start(const bd_server_opts* opts, bd_server** server);
 int bd_server_submit(bd_server* server, const int64_t* A, int32_t n, int32_t m, const int64_t* coef, uint64_t seed,
@@ -309,15 +322,44 @@ int bd_mlp_train(bd_mlp* mlp, const float* X, const float* y, int32_t count, int
  * beyond BD_NMAX points or BD_KMAX dimensions are rejected with BD_ERR_ARG.
  *
  * The first call on each device looks up the device address of the array (a one-time set-up
- * with that device current); make that first call before any stream capture.  Every call
- * shares the array and the array keeps the last call's contents; the call clears what must
- * start at zero.  Calls from this process are serialized and each one waits for its own work
- * on the thread's stream, but two calls whose work overlapped on the GPU would race on the
- * shared array.
+ * with that device current) and keeps it for the life of the process; make that first call
+ * before any stream capture.  A device reset (cudaDeviceReset) unloads the array with the
+ * library image and makes later calls on that device invalid.  Every call shares the array and
+ * the array keeps the last call's contents; the call clears what must start at zero.  Calls
+ * from this process are serialized, and every call synchronizes the thread's stream before it
+ * returns (on success and on every error after its first copy), so the array is idle between
+ * calls; two calls whose work overlapped on the GPU (for instance from two processes sharing
+ * the library image through another loader) would race on the shared array.
  */
 #define BD_NOALLOC_MAX_ITEMS 65536
 #define BD_NOALLOC_SCRATCH_BYTES (8192 + 16 * BD_NOALLOC_MAX_ITEMS)
 int bd_volume_noalloc(const int64_t* points, int32_t npts, int32_t k, uint64_t seed, bd_volume_out* out);
+
+/* ---- integer issue peak (the denominator of the roofline; measurement only) ---------------
+ *
+ * The lower-facet test is bound by instruction issue on the integer and single-precision pipes
+ * (Sec. 4's test runs on exact integer minors, no memory stream and no dense contraction), so
+ * its roofline is the rate at which this GPU issues 32-bit lane operations.  bd_issue_peak
+ * measures it: every thread of a full-occupancy grid (blocks_per_sm x SMs blocks of 256
+ * threads; 0 = the resident maximum) runs iters x 16 rounds of eight coupled recurrences of one
+ * instruction kind, each step one instruction (see the kinds below), on the stream of
+ * bd_set_stream.  out receives the lane operations, the CUDA-event time, lane operations per
+ * second, the largest block's SM cycle count (clock64) and the SM clock it implies, and the
+ * lane operations per SM per cycle.  Allocates and frees two small device buffers.
+ *   kind 0: LOP3 (logic, ALU pipe)    1: IMAD (32-bit multiply-add)   2: LOP3 and IMAD alternating
+ *   kind 3: FFMA (single precision)   4: LOP3 and FFMA alternating
+ * Errors: BD_ERR_ARG (kind, iters outside [1, 2^20], blocks_per_sm above the resident limit),
+ * BD_ERR_CUDA. */
+typedef struct {
+  double lane_ops;            /* lane operations executed */
+  double ms;                  /* kernel time (CUDA events) */
+  double lane_ops_per_s;
+  double sm_cycles;           /* cycles of the slowest block's timed loop */
+  double sm_mhz;              /* sm_cycles / ms: the SM clock during the run */
+  double lane_ops_per_sm_clk; /* per SM per cycle over the run (the slowest block's cycles) */
+  int32_t sms, blocks, threads_per_block, kind;
+} bd_peak_out;
+int bd_issue_peak(int32_t kind, int32_t blocks_per_sm, int32_t iters, bd_peak_out* out);
 
 /* ---- host emulation (CPU tests and the native CPU baseline; never used by the calls above) */
 

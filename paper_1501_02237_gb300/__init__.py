@@ -13,20 +13,37 @@ from typing import Optional, Sequence
 import numpy as np
 
 from ._lib import (BD_FEATURES, BD_MLP_PARAMS, BD_FLAG_DEGENERATE, BD_FLAG_INCONSISTENT, BD_FLAG_INT128, BD_FLAG_PIVOT, KMAX,  # noqa: F401
-                   NMAX, BatchOpts, BatchStats, BinodegError, DegreeOut, HostOpts, MixedOut, PlanOpts, ServerOpts,
+                   NMAX, BatchOpts, BatchStats, BinodegError, DegreeOut, HostOpts, MixedOut, PeakOut, PlanOpts, ServerOpts,
                    ServerStats, VolumeOut, check, i64, lib, ptr)
 from ._lib import F32P, I32P, U8P
 
 __all__ = ["CostModel", "Server", "degree", "volume", "volume_noalloc", "volume_lifted", "classify", "reduce", "Plan", "Batch", "set_stream",
            "host_volume_lifted", "cells", "host_cells", "start_solutions", "host_start_solutions", "mixed_volume",
            "mixed_volume_lifted", "host_mixed_volume_lifted", "volume_pivot", "host_volume_pivot", "degree_pivot",
-           "BinodegError", "lib"]
+           "issue_peak", "inject_alloc_failure", "BinodegError", "lib"]
 
 
 def set_stream(stream) -> None:
     """Stream for the synchronous calls on this thread: a torch.cuda.Stream, a raw handle or None."""
     handle = getattr(stream, "cuda_stream", stream)
     check(lib().bd_set_stream(C.c_void_p(handle or 0)))
+
+
+def inject_alloc_failure(after: int = 0) -> None:
+    """bd_inject_alloc_failure: the after-th device allocation from now fails as out of memory
+    (once; after < 0 disarms).  For tests of the error paths."""
+    check(lib().bd_inject_alloc_failure(after))
+
+
+ISSUE_KINDS = {"lop3": 0, "imad": 1, "lop3_imad": 2, "ffma": 3, "lop3_ffma": 4}
+
+
+def issue_peak(kind: str = "lop3_imad", blocks_per_sm: int = 0, iters: int = 4096) -> dict:
+    """bd_issue_peak: lane operations per second of one 32-bit instruction stream at full occupancy
+    (kinds: lop3, imad, lop3_imad, ffma, lop3_ffma)."""
+    out = PeakOut()
+    check(lib().bd_issue_peak(ISSUE_KINDS[kind], blocks_per_sm, iters, C.byref(out)))
+    return out.as_dict()
 
 
 def _coef_array(coef, m: int) -> Optional[np.ndarray]:

@@ -100,7 +100,17 @@ class ServerOpts(C.Structure):
 class ServerStats(C.Structure):
     _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("relifted", C.c_int64), ("launches", C.c_int64),
                 ("ring_items", C.c_int64), ("slots", C.c_int32), ("blocks", C.c_int32),
-                ("warps_per_block", C.c_int32), ("waiting", C.c_int32)]
+                ("warps_per_block", C.c_int32), ("waiting", C.c_int32), ("routed", C.c_int64),
+                ("peak_resident", C.c_int32), ("reserved", C.c_int32)]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
+class PeakOut(C.Structure):
+    _fields_ = [("lane_ops", C.c_double), ("ms", C.c_double), ("lane_ops_per_s", C.c_double),
+                ("sm_cycles", C.c_double), ("sm_mhz", C.c_double), ("lane_ops_per_sm_clk", C.c_double),
+                ("sms", C.c_int32), ("blocks", C.c_int32), ("threads_per_block", C.c_int32), ("kind", C.c_int32)]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}
@@ -117,6 +127,7 @@ U8P = C.POINTER(C.c_uint8)
 SIGNATURES = {
     "bd_last_error": (C.c_char_p, []),
     "bd_set_stream": (C.c_int, [C.c_void_p]),
+    "bd_inject_alloc_failure": (C.c_int, [C.c_int32]),
     "bd_degree": (C.c_int, [I64P, C.c_int32, C.c_int32, I64P, C.c_uint64, C.POINTER(DegreeOut)]),
     "bd_reduce": (C.c_int, [I64P, C.c_int32, C.c_int32, I64P, I64P, I64P]),
     "bd_volume": (C.c_int, [I64P, C.c_int32, C.c_int32, C.c_uint64, C.POINTER(VolumeOut)]),
@@ -149,6 +160,7 @@ SIGNATURES = {
                                          C.c_int64, I64P]),
     "bd_host_mixed_volume_lifted": (C.c_int, [I64P, I32P, C.c_int32, I64P, C.c_int32, C.c_int32, C.c_int32,
                                               C.c_int32, C.POINTER(MixedOut), I32P, C.c_int64, I64P]),
+    "bd_issue_peak": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.POINTER(PeakOut)]),
     "bd_batch_create": (C.c_int, [C.POINTER(C.c_void_p)]),
     "bd_batch_add": (C.c_int, [C.c_void_p, I64P, C.c_int32, C.c_int32, I64P, C.c_uint64, I32P]),
     "bd_batch_add_points": (C.c_int, [C.c_void_p, I64P, C.c_int32, C.c_int32, C.c_uint64, I32P]),

@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libbinodeg.so")
 
-SOURCES = ["bd_host.cpp", "bd_worklist.cpp", "bd_kernels.cu", "bd_api.cu", "bd_noalloc.cu", "bd_batch.cu", "bd_mlp.cu", "bd_serve.cu", "bd_start.cu", "bd_mixed.cu", "bd_pivot.cu"]
+SOURCES = ["bd_host.cpp", "bd_worklist.cpp", "bd_kernels.cu", "bd_api.cu", "bd_noalloc.cu", "bd_batch.cu", "bd_mlp.cu", "bd_serve.cu", "bd_start.cu", "bd_mixed.cu", "bd_pivot.cu", "bd_peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O3",
          "-I", os.path.join(ROOT, "include")]

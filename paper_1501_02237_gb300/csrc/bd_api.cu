@@ -1,7 +1,9 @@
 // C ABI of libbinodeg.so (declarations and contracts in include/binodeg.h).
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -32,8 +34,16 @@ int fail(int code, const std::string& msg) {
 }
 
 int cuda_fail(cudaError_t e, const char* where) {
-  return fail(BD_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+  return fail(e == cudaErrorMemoryAllocation ? BD_ERR_NOMEM : BD_ERR_CUDA,
+              std::string(where) + ": " + cudaGetErrorString(e));
 }
+
+// device allocations still to succeed before the injected failure (-1: none armed); armed by
+// bd_inject_alloc_failure or, at load, by the environment variable BD_INJECT_ALLOC_FAILURE
+std::atomic<long long> g_alloc_fail_after{[] {
+  const char* v = std::getenv("BD_INJECT_ALLOC_FAILURE");
+  return v && *v ? std::atoll(v) : -1ll;
+}()};
 
 #define BD_CUDA(call)                                   \
   do {                                                  \
@@ -99,13 +109,17 @@ int get_items(int N, int K, int64_t thr, int64_t teams, std::shared_ptr<ItemList
   bd::build_ranges(N, K, (uint64_t)thr, (uint64_t)teams, L->host, L->ranges);
   std::vector<bd::PackedItem> packed(L->host.size());
   for (size_t i = 0; i < packed.size(); ++i) packed[i] = bd::pack_item(L->host[i]);
-  cudaError_t e = cudaMalloc(&L->dev, sizeof(bd::PackedItem) * std::max<size_t>(1, L->host.size()));
-  if (e == cudaSuccess) e = cudaMalloc(&L->dev_ranges, sizeof(bd::Range) * std::max<size_t>(1, L->ranges.size()));
+  cudaError_t e = bd::dev_malloc(&L->dev, sizeof(bd::PackedItem) * std::max<size_t>(1, L->host.size()));
+  if (e == cudaSuccess) e = bd::dev_malloc(&L->dev_ranges, sizeof(bd::Range) * std::max<size_t>(1, L->ranges.size()));
   if (e == cudaSuccess && !L->host.empty())
     e = cudaMemcpy(L->dev, packed.data(), sizeof(bd::PackedItem) * packed.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess && !L->ranges.empty())
     e = cudaMemcpy(L->dev_ranges, L->ranges.data(), sizeof(bd::Range) * L->ranges.size(), cudaMemcpyHostToDevice);
-  if (e != cudaSuccess) return cuda_fail(e, "work list upload");
+  if (e != cudaSuccess) {  // not cached: free what was allocated
+    cudaFree(L->dev);
+    cudaFree(L->dev_ranges);
+    return cuda_fail(e, "work list upload");
+  }
   g_items[key] = L;
   out = L;
   return BD_OK;
@@ -125,7 +139,7 @@ int get_tri(const uint32_t*& out) {
   std::vector<uint32_t> h(bd::kTriEntries);
   bd::fill_colex_table(h.data());
   uint32_t* d = nullptr;
-  cudaError_t e = cudaMalloc(&d, sizeof(uint32_t) * h.size());
+  cudaError_t e = bd::dev_malloc(&d, sizeof(uint32_t) * h.size());
   if (e == cudaSuccess) e = cudaMemcpy(d, h.data(), sizeof(uint32_t) * h.size(), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return cuda_fail(e, "decode table upload");
   g_tri[dev] = d;
@@ -154,6 +168,24 @@ namespace bd {
 int set_error(int code, const char* msg) { return fail(code, msg); }
 cudaStream_t thread_stream() { return g_stream; }
 int device_tri_table(const uint32_t** out) { return get_tri(*out); }
+
+cudaError_t dev_malloc_raw(void** p, size_t bytes) {
+  long long n = g_alloc_fail_after.load();
+  while (n >= 0 && !g_alloc_fail_after.compare_exchange_weak(n, n - 1)) {
+  }
+  if (n == 0) {  // the armed allocation: fail as the device would when out of memory
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  const cudaError_t e = cudaMalloc(p, bytes);
+  if (e == cudaErrorMemoryAllocation) cudaGetLastError();
+  return e;
+}
+
+int cuda_error(cudaError_t e, const char* where) {
+  const std::string msg = where ? std::string(where) + ": " + cudaGetErrorString(e) : std::string(cudaGetErrorString(e));
+  return fail(e == cudaErrorMemoryAllocation ? BD_ERR_NOMEM : BD_ERR_CUDA, msg);
+}
 }  // namespace bd
 
 // A plan owns small fixed-size device buffers (points of up to BD_NMAX x BD_KMAX coordinates,
@@ -209,14 +241,14 @@ int plan_alloc(bd_plan* p) {
   const int dev = current_device();
   if (p->device == dev) return BD_OK;
   if (p->device >= 0) plan_release(p);
-  cudaError_t e = cudaMalloc(&p->d_pts, sizeof(int64_t) * BD_NMAX * BD_KMAX);
-  if (e == cudaSuccess) e = cudaMalloc(&p->d_lifts, sizeof(int64_t) * BD_NMAX);
-  if (e == cudaSuccess) e = cudaMalloc(&p->d_state, state_bytes());
+  cudaError_t e = bd::dev_malloc(&p->d_pts, sizeof(int64_t) * BD_NMAX * BD_KMAX);
+  if (e == cudaSuccess) e = bd::dev_malloc(&p->d_lifts, sizeof(int64_t) * BD_NMAX);
+  if (e == cudaSuccess) e = bd::dev_malloc(&p->d_state, state_bytes());
   if (e == cudaSuccess) e = cudaMallocHost(&p->h_acc, sizeof(bd::DevAcc));
   if (e == cudaSuccess) e = cudaMallocHost(&p->h_stage, sizeof(int64_t) * STAGE_WORDS);
   if (e != cudaSuccess) {
     plan_release(p);
-    return e == cudaErrorMemoryAllocation ? fail(BD_ERR_NOMEM, "plan buffers") : cuda_fail(e, "plan buffers");
+    return cuda_fail(e, "plan buffers");
   }
   p->device = dev;
   return BD_OK;
@@ -386,6 +418,11 @@ extern "C" {
 
 const char* bd_last_error(void) { return g_err.c_str(); }
 
+int bd_inject_alloc_failure(int32_t after) {
+  g_alloc_fail_after.store(after < 0 ? -1 : after);
+  return BD_OK;
+}
+
 int bd_set_stream(void* stream) {
   g_stream = reinterpret_cast<cudaStream_t>(stream);
   return BD_OK;
@@ -493,6 +530,16 @@ int bd_degree(const int64_t* A, int32_t n, int32_t m, const int64_t* coef, uint6
   std::string err;
   int rc = bd::reduce_system(A, n, m, coef, r, err);
   if (rc) return fail(rc, err);
+  return bd::degree_from_reduction(r, n, seed, out);
+}
+
+}  // extern "C"
+
+namespace bd {
+
+int degree_from_reduction(const Reduction& r, int n, uint64_t seed, bd_degree_out* out) {
+  int rc = BD_OK;
+  std::memset(out, 0, sizeof(*out));
   out->rank = r.rank;
   out->dim = r.dim;
   out->torsion = r.torsion;
@@ -550,6 +597,10 @@ int bd_degree(const int64_t* A, int32_t n, int32_t m, const int64_t* coef, uint6
   return BD_OK;
 }
 
+}  // namespace bd
+
+extern "C" {
+
 int bd_classify(const int64_t* points, const int64_t* lifts, int32_t npts, int32_t k, const uint8_t* subsets,
                 int32_t count, int32_t* status, int64_t* absdet) {
   int rc = check_points(points, npts, k);
@@ -589,11 +640,11 @@ int bd_classify(const int64_t* points, const int64_t* lifts, int32_t npts, int32
     e = (call);                  \
     if (e != cudaSuccess) where = #call; \
   }
-  CL(cudaMalloc(&d_pts, sizeof(int64_t) * npts * k));
-  CL(cudaMalloc(&d_lifts, sizeof(int64_t) * npts));
-  CL(cudaMalloc(&d_abs, sizeof(int64_t) * count));
-  CL(cudaMalloc(&d_sub, (size_t)count * (k + 1)));
-  CL(cudaMalloc(&d_status, sizeof(int32_t) * count));
+  CL(bd::dev_malloc(&d_pts, sizeof(int64_t) * npts * k));
+  CL(bd::dev_malloc(&d_lifts, sizeof(int64_t) * npts));
+  CL(bd::dev_malloc(&d_abs, sizeof(int64_t) * count));
+  CL(bd::dev_malloc(&d_sub, (size_t)count * (k + 1)));
+  CL(bd::dev_malloc(&d_status, sizeof(int32_t) * count));
   CL(cudaMemcpyAsync(d_pts, points, sizeof(int64_t) * npts * k, cudaMemcpyHostToDevice, st));
   CL(cudaMemcpyAsync(d_lifts, lifts, sizeof(int64_t) * npts, cudaMemcpyHostToDevice, st));
   CL(cudaMemcpyAsync(d_sub, subsets, (size_t)count * (k + 1), cudaMemcpyHostToDevice, st));
@@ -699,12 +750,12 @@ int bd_cells(const int64_t* points, int32_t npts, int32_t k, uint64_t seed, int6
       return cuda_fail(e_, #x);                            \
     }                                                      \
   } while (0)
-  CC(cudaMalloc(&d_cells, 16 * cap));
-  CC(cudaMalloc(&d_count, sizeof(unsigned long long)));
-  CC(cudaMalloc(&d_den, sizeof(int64_t) * cap));
-  CC(cudaMalloc(&d_alpha, sizeof(int64_t) * cap * k));
-  CC(cudaMalloc(&d_beta, sizeof(int64_t) * 2 * cap));
-  CC(cudaMalloc(&d_status, sizeof(int32_t) * cap));
+  CC(bd::dev_malloc(&d_cells, 16 * cap));
+  CC(bd::dev_malloc(&d_count, sizeof(unsigned long long)));
+  CC(bd::dev_malloc(&d_den, sizeof(int64_t) * cap));
+  CC(bd::dev_malloc(&d_alpha, sizeof(int64_t) * cap * k));
+  CC(bd::dev_malloc(&d_beta, sizeof(int64_t) * 2 * cap));
+  CC(bd::dev_malloc(&d_status, sizeof(int32_t) * cap));
   const bd::CellSink sink{d_cells, d_count, (unsigned long long)capacity};
   int attempt = 0;
   for (;; ++attempt) {

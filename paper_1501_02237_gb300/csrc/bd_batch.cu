@@ -124,10 +124,10 @@ int ensure(bd_batch* b, size_t nsys, size_t npts, size_t nitems) {
     cudaFreeHost(b->h_cycles);
     b->d_desc = nullptr; b->d_acc = nullptr; b->d_cycles = nullptr; b->d_done = nullptr;
     b->h_acc = nullptr; b->h_cycles = nullptr;
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_desc, sizeof(bd::BatchDesc) * c);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_acc, sizeof(bd::DevAcc) * c);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_cycles, sizeof(unsigned long long) * c);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_done, sizeof(unsigned int) * c);
+    if (e == cudaSuccess) e = bd::dev_malloc(&b->d_desc, sizeof(bd::BatchDesc) * c);
+    if (e == cudaSuccess) e = bd::dev_malloc(&b->d_acc, sizeof(bd::DevAcc) * c);
+    if (e == cudaSuccess) e = bd::dev_malloc(&b->d_cycles, sizeof(unsigned long long) * c);
+    if (e == cudaSuccess) e = bd::dev_malloc(&b->d_done, sizeof(unsigned int) * c);
     if (e == cudaSuccess) e = cudaMallocHost(&b->h_acc, sizeof(bd::DevAcc) * c);
     if (e == cudaSuccess) e = cudaMallocHost(&b->h_cycles, sizeof(unsigned long long) * c);
     b->cap_sys = c;
@@ -136,17 +136,17 @@ int ensure(bd_batch* b, size_t nsys, size_t npts, size_t nitems) {
     size_t c = std::max(npts, b->cap_pts * 2);
     cudaFree(b->d_pts);
     b->d_pts = nullptr;
-    e = cudaMalloc(&b->d_pts, sizeof(int64_t) * c);
+    e = bd::dev_malloc(&b->d_pts, sizeof(int64_t) * c);
     b->cap_pts = c;
   }
   if (e == cudaSuccess && nitems > b->cap_items) {
     size_t c = std::max(nitems, b->cap_items * 2);
     cudaFree(b->d_items);
     b->d_items = nullptr;
-    e = cudaMalloc(&b->d_items, sizeof(bd::BatchItem) * c);
+    e = bd::dev_malloc(&b->d_items, sizeof(bd::BatchItem) * c);
     b->cap_items = c;
   }
-  if (e == cudaSuccess && !b->d_counter) e = cudaMalloc(&b->d_counter, sizeof(unsigned int) * 4);
+  if (e == cudaSuccess && !b->d_counter) e = bd::dev_malloc(&b->d_counter, sizeof(unsigned int) * 4);
   if (e != cudaSuccess) {
     free_dev(b);
     return bd::set_error(e == cudaErrorMemoryAllocation ? BD_ERR_NOMEM : BD_ERR_CUDA, cudaGetErrorString(e));
@@ -262,7 +262,7 @@ int run_batched(bd_batch* b, const std::vector<int>& active, const float* cost, 
     }
     cudaError_t e;
     bd::LaunchShape s0 = bd::batch_shape(std::max(maxN, 2), std::max(maxK, 1), bd::PATH_NARROW, warps_req, 0, sms, &e);
-    if (e != cudaSuccess) return bd::set_error(BD_ERR_CUDA, cudaGetErrorString(e));
+    if (e != cudaSuccess) return bd::cuda_error(e);
     build_batch_items(b, active, cost, items_per_warp, s0.blocks * s0.warps, items, groups);
   }
   // packed descriptors and points (all systems, so that indices stay global)
@@ -286,13 +286,13 @@ int run_batched(bd_batch* b, const std::vector<int>& active, const float* cost, 
   if (e == cudaSuccess && !items.empty())
     e = cudaMemcpyAsync(b->d_items, items.data(), sizeof(bd::BatchItem) * items.size(), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // host vectors go out of scope
-  if (e != cudaSuccess) return bd::set_error(BD_ERR_CUDA, cudaGetErrorString(e));
+  if (e != cudaSuccess) return bd::cuda_error(e);
 
   // the timed part: clear, one persistent launch per path group, copy the results back
   std::vector<bd::LaunchShape> shapes;
   for (const Group& g : groups) {
     bd::LaunchShape s = bd::batch_shape(g.maxN, g.maxK, g.path, warps_req, 0, sms, &e);
-    if (e != cudaSuccess) return bd::set_error(BD_ERR_CUDA, cudaGetErrorString(e));
+    if (e != cudaSuccess) return bd::cuda_error(e);
     shapes.push_back(s);
   }
   const uint32_t* tri = nullptr;  // fetched before any stream capture
@@ -354,7 +354,7 @@ int run_batched(bd_batch* b, const std::vector<int>& active, const float* cost, 
       if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, g, 0);
       if (g) cudaGraphDestroy(g);
       cudaStreamDestroy(cs);
-      if (e != cudaSuccess) return bd::set_error(BD_ERR_CUDA, cudaGetErrorString(e));
+      if (e != cudaSuccess) return bd::cuda_error(e);
       b->graph_key = key;
     }
     e = cudaGraphLaunch(b->graph, st);
@@ -367,7 +367,7 @@ int run_batched(bd_batch* b, const std::vector<int>& active, const float* cost, 
   cudaEventElapsedTime(&ms, e0, e1);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (e != cudaSuccess) return bd::set_error(BD_ERR_CUDA, cudaGetErrorString(e));
+  if (e != cudaSuccess) return bd::cuda_error(e);
   *gpu_ms += ms;
   *launches += (int)groups.size();
   *nitems_out += items.size();

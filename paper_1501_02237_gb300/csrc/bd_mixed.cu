@@ -249,7 +249,7 @@ int device_run(const MixedPrep& mp, const std::vector<T>& rows, uint64_t cap, Ru
   cudaError_t e = cudaGetDevice(&dev);  // no device: a CUDA error, never a host fallback
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  if (e != cudaSuccess) return bd::set_error(BD_ERR_CUDA, cudaGetErrorString(e));
+  if (e != cudaSuccess) return bd::cuda_error(e);
   if (smem_bytes(mp, sizeof(T), 1) > (size_t)optin)
     return bd::set_error(BD_ERR_ARG, "the problem's walk state exceeds shared memory");
   e = cudaFuncSetAttribute(k_mixed<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
@@ -267,7 +267,7 @@ int device_run(const MixedPrep& mp, const std::vector<T>& rows, uint64_t cap, Ru
       per_sm = b;
     }
   }
-  if (e != cudaSuccess) return bd::set_error(BD_ERR_CUDA, cudaGetErrorString(e));
+  if (e != cudaSuccess) return bd::cuda_error(e);
   per_sm = std::max(per_sm, 1);
   const size_t smem = smem_bytes(mp, sizeof(T), wpb);
   const unsigned long long items = mp.shape.items;
@@ -293,12 +293,12 @@ int device_run(const MixedPrep& mp, const std::vector<T>& rows, uint64_t cap, Ru
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
   };
-  e = cudaMalloc(&d_rows, sizeof(T) * rows.size());
-  if (e == cudaSuccess) e = cudaMalloc(&d_lp, sizeof(uint16_t) * std::max<size_t>(mp.last_pairs.size(), 1));
-  if (e == cudaSuccess) e = cudaMalloc(&d_pp, sizeof(uint16_t) * std::max<size_t>(mp.prev_pairs.size(), 1));
-  if (e == cudaSuccess) e = cudaMalloc(&d_next, sizeof(unsigned long long) * 2);
-  if (e == cudaSuccess) e = cudaMalloc(&d_acc, sizeof(MixedDevAcc));
-  if (e == cudaSuccess && cap) e = cudaMalloc(&d_recs, sizeof(bd::MixedCellRec) * cap);
+  e = bd::dev_malloc(&d_rows, sizeof(T) * rows.size());
+  if (e == cudaSuccess) e = bd::dev_malloc(&d_lp, sizeof(uint16_t) * std::max<size_t>(mp.last_pairs.size(), 1));
+  if (e == cudaSuccess) e = bd::dev_malloc(&d_pp, sizeof(uint16_t) * std::max<size_t>(mp.prev_pairs.size(), 1));
+  if (e == cudaSuccess) e = bd::dev_malloc(&d_next, sizeof(unsigned long long) * 2);
+  if (e == cudaSuccess) e = bd::dev_malloc(&d_acc, sizeof(MixedDevAcc));
+  if (e == cudaSuccess && cap) e = bd::dev_malloc(&d_recs, sizeof(bd::MixedCellRec) * cap);
   if (e == cudaSuccess) e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_rows, rows.data(), sizeof(T) * rows.size(), cudaMemcpyHostToDevice, st);
@@ -329,7 +329,7 @@ int device_run(const MixedPrep& mp, const std::vector<T>& rows, uint64_t cap, Ru
   float ms = 0;
   if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
   release();
-  if (e != cudaSuccess) return bd::set_error(BD_ERR_CUDA, cudaGetErrorString(e));
+  if (e != cudaSuccess) return bd::cuda_error(e);
   rr.mv = ((u128)h.mv_hi << 64) | h.mv_lo;
   rr.cells = h.cells;
   rr.singular = h.singular;

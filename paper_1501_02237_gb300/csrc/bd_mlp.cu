@@ -149,11 +149,11 @@ struct bd_mlp {
 
 namespace {
 
-int cuda_err(cudaError_t e) { return bd::set_error(BD_ERR_CUDA, cudaGetErrorString(e)); }
+int cuda_err(cudaError_t e) { return bd::cuda_error(e); }
 
 int upload_xy(const float* X, const float* y, int count, float** dX, float** dY, cudaStream_t st) {
-  cudaError_t e = cudaMalloc(dX, sizeof(float) * (size_t)count * F);
-  if (e == cudaSuccess && y) e = cudaMalloc(dY, sizeof(float) * (size_t)count);
+  cudaError_t e = bd::dev_malloc(dX, sizeof(float) * (size_t)count * F);
+  if (e == cudaSuccess && y) e = bd::dev_malloc(dY, sizeof(float) * (size_t)count);
   if (e == cudaSuccess) e = cudaMemcpyAsync(*dX, X, sizeof(float) * (size_t)count * F, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && y) e = cudaMemcpyAsync(*dY, y, sizeof(float) * (size_t)count, cudaMemcpyHostToDevice, st);
   return e == cudaSuccess ? BD_OK : cuda_err(e);
@@ -167,7 +167,7 @@ int bd_mlp_create(uint64_t seed, bd_mlp** out) {
   if (!out) return bd::set_error(BD_ERR_ARG, "NULL argument");
   bd_mlp* m = new (std::nothrow) bd_mlp();
   if (!m) return bd::set_error(BD_ERR_NOMEM, "host allocation");
-  cudaError_t e = cudaMalloc(&m->d_w, sizeof(float) * NPARAM * 4 + sizeof(float) * (2 * F + 1));
+  cudaError_t e = bd::dev_malloc(&m->d_w, sizeof(float) * NPARAM * 4 + sizeof(float) * (2 * F + 1));
   if (e != cudaSuccess) {
     delete m;
     return cuda_err(e);
@@ -226,7 +226,7 @@ int bd_mlp_predict(bd_mlp* m, const float* X, int32_t count, float* y) {
   float *dX = nullptr, *dY = nullptr;
   int rc = upload_xy(X, nullptr, count, &dX, &dY, st);
   cudaError_t e = cudaSuccess;
-  if (!rc) e = cudaMalloc(&dY, sizeof(float) * count);
+  if (!rc) e = bd::dev_malloc(&dY, sizeof(float) * count);
   if (!rc && e == cudaSuccess) {
     const int blocks = std::min(1024, (count + SPB - 1) / SPB);
     k_mlp_forward<<<blocks, SPB * H, 0, st>>>(m->d_w, dX, m->d_norm, m->d_norm + F, count, dY);
@@ -290,8 +290,8 @@ int bd_mlp_train(bd_mlp* m, const float* X, const float* y, int32_t count, int32
   std::vector<int> perm(count);
   for (int i = 0; i < count; ++i) perm[i] = i;
   float *dX = nullptr, *dY = nullptr;
-  if (e == cudaSuccess) e = cudaMalloc(&dX, sizeof(float) * Xp.size());
-  if (e == cudaSuccess) e = cudaMalloc(&dY, sizeof(float) * count);
+  if (e == cudaSuccess) e = bd::dev_malloc(&dX, sizeof(float) * Xp.size());
+  if (e == cudaSuccess) e = bd::dev_malloc(&dY, sizeof(float) * count);
   if (e == cudaSuccess) e = cudaMemsetAsync(m->d_g, 0, sizeof(float) * NPARAM, st);
   float lsum = 0;
   for (int ep = 0; ep < epochs && e == cudaSuccess; ++ep) {

@@ -4,9 +4,11 @@
 // The array is part of the library image: every GPU that loads the library holds it until the
 // process exits.  Host code cannot use the array's name as a device address (it names a host
 // shadow), so the address is obtained once per device with cudaGetSymbolAddress while that
-// device is current, and cached.  The call never calls cudaMalloc, cudaFree or any other
-// allocating routine: inputs are staged into the array with plain copies, the work counter
-// and accumulators are cleared with a memset, and the result is copied back.
+// device is current, and cached for the life of the process (a device reset unloads the library
+// image from that device and invalidates it: the call is not valid after one).  The call never
+// calls cudaMalloc, cudaFree or any other allocating routine: inputs are staged into the array
+// with plain copies, the work counter and accumulators are cleared with a memset, and the result
+// is copied back.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -104,10 +106,16 @@ extern "C" int bd_volume_noalloc(const int64_t* points, int32_t npts, int32_t k,
   int64_t* d_pts = reinterpret_cast<int64_t*>(base + kPointsOffset);
   bd::PackedItem* d_items = reinterpret_cast<bd::PackedItem*>(base + kItemsOffset);
   for (size_t i = 0; i < nitems; ++i) g_host_packed[i] = bd::pack_item(g_host_items[i]);
+  // once work is queued, every return first waits for it, so that the array is idle whenever
+  // the lock is free (a later call may use another stream)
+  auto fail_idle = [&](int code, const char* msg) {
+    cudaStreamSynchronize(st);
+    return bd::set_error(code, msg);
+  };
   e = cudaMemcpyAsync(d_pts, points, sizeof(int64_t) * npts * k, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(d_items, g_host_packed, sizeof(bd::PackedItem) * nitems, cudaMemcpyHostToDevice, st);
-  if (e != cudaSuccess) return bd::set_error(BD_ERR_CUDA, cudaGetErrorString(e));
+  if (e != cudaSuccess) return fail_idle(BD_ERR_CUDA, cudaGetErrorString(e));
   for (int attempt = 0; attempt < 8; ++attempt) {
     bd::DevAcc acc{};
     e = cudaMemsetAsync(base, 0, kPointsOffset, st);  // accumulators and work counter start at zero
@@ -124,7 +132,7 @@ extern "C" int bd_volume_noalloc(const int64_t* points, int32_t npts, int32_t k,
     if (e == cudaSuccess) e = bd::launch_enumerate(ep, shape, path, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&acc, d_acc, sizeof(acc), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return bd::set_error(BD_ERR_CUDA, cudaGetErrorString(e));
+    if (e != cudaSuccess) return fail_idle(BD_ERR_CUDA, cudaGetErrorString(e));
     if (acc.items_done != nitems) return bd::set_error(BD_ERR_CUDA, "enumeration did not process every work item");
     out->nvol_lo = acc.nvol_lo;
     out->nvol_hi = acc.nvol_hi;

@@ -240,7 +240,7 @@ template <>
 struct CellTable<uint64_t> {
   unsigned long long* slot = nullptr;
 
-  cudaError_t alloc(unsigned long long cap) { return cudaMalloc(&slot, sizeof(unsigned long long) * cap); }
+  cudaError_t alloc(unsigned long long cap) { return bd::dev_malloc(&slot, sizeof(unsigned long long) * cap); }
   cudaError_t clear(unsigned long long cap, cudaStream_t st) {
     return cudaMemsetAsync(slot, 0, sizeof(unsigned long long) * cap, st);
   }
@@ -279,9 +279,9 @@ struct CellTable<bd::WideMask> {
   unsigned long long *fp = nullptr, *lo = nullptr, *hi = nullptr;
 
   cudaError_t alloc(unsigned long long cap) {
-    cudaError_t e = cudaMalloc(&fp, sizeof(unsigned long long) * cap);
-    if (e == cudaSuccess) e = cudaMalloc(&lo, sizeof(unsigned long long) * cap);
-    if (e == cudaSuccess) e = cudaMalloc(&hi, sizeof(unsigned long long) * cap);
+    cudaError_t e = bd::dev_malloc(&fp, sizeof(unsigned long long) * cap);
+    if (e == cudaSuccess) e = bd::dev_malloc(&lo, sizeof(unsigned long long) * cap);
+    if (e == cudaSuccess) e = bd::dev_malloc(&hi, sizeof(unsigned long long) * cap);
     return e;
   }
   cudaError_t clear(unsigned long long cap, cudaStream_t st) {
@@ -415,7 +415,7 @@ int device_pivot(const int64_t* pts, const int64_t* lifts, int N, int d, Mask st
   cudaError_t e = cudaGetDevice(&dev);  // no device: a CUDA error, never a host fallback
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  if (e != cudaSuccess) return bd::set_error(BD_ERR_CUDA, cudaGetErrorString(e));
+  if (e != cudaSuccess) return bd::cuda_error(e);
   if (pivot_smem(N, d, 1) > (size_t)optin) return bd::set_error(BD_ERR_ARG, "the pivoting state exceeds shared memory");
   e = cudaFuncSetAttribute(k_pivot<Mask>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
   // warps per block: the most resident warps per SM (the state is per warp)
@@ -431,7 +431,7 @@ int device_pivot(const int64_t* pts, const int64_t* lifts, int N, int d, Mask st
       per_sm = b;
     }
   }
-  if (e != cudaSuccess) return bd::set_error(BD_ERR_CUDA, cudaGetErrorString(e));
+  if (e != cudaSuccess) return bd::cuda_error(e);
   per_sm = std::max(per_sm, 1);
   const size_t smem = pivot_smem(N, d, wpb);
   for (unsigned long long cap = 1ull << 22; cap <= (1ull << 31); cap <<= 3) {
@@ -450,12 +450,12 @@ int device_pivot(const int64_t* pts, const int64_t* lifts, int N, int d, Mask st
       if (e0) cudaEventDestroy(e0);
       if (e1) cudaEventDestroy(e1);
     };
-    e = cudaMalloc(&d_pts, sizeof(int64_t) * N * d);
-    if (e == cudaSuccess) e = cudaMalloc(&d_lifts, sizeof(int64_t) * N);
+    e = bd::dev_malloc(&d_pts, sizeof(int64_t) * N * d);
+    if (e == cudaSuccess) e = bd::dev_malloc(&d_lifts, sizeof(int64_t) * N);
     if (e == cudaSuccess) e = table.alloc(cap);
-    if (e == cudaSuccess) e = cudaMalloc(&d_a, sizeof(Mask) * cap);
-    if (e == cudaSuccess) e = cudaMalloc(&d_b, sizeof(Mask) * cap);
-    if (e == cudaSuccess) e = cudaMalloc(&d_dv, sizeof(PivotDev));
+    if (e == cudaSuccess) e = bd::dev_malloc(&d_a, sizeof(Mask) * cap);
+    if (e == cudaSuccess) e = bd::dev_malloc(&d_b, sizeof(Mask) * cap);
+    if (e == cudaSuccess) e = bd::dev_malloc(&d_dv, sizeof(PivotDev));
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_pts, pts, sizeof(int64_t) * N * d, cudaMemcpyHostToDevice, st);
@@ -501,7 +501,7 @@ int device_pivot(const int64_t* pts, const int64_t* lifts, int N, int d, Mask st
     float ms = 0;
     if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
     release();
-    if (e != cudaSuccess) return bd::set_error(BD_ERR_CUDA, cudaGetErrorString(e));
+    if (e != cudaSuccess) return bd::cuda_error(e);
     if (h.flags & PF_FULL) continue;
     run.nvol = ((u128)h.nvol_hi << 64) | h.nvol_lo;
     run.cells = h.cells;

@@ -3,7 +3,10 @@
 // free slots as long as the device budget (slots and ring capacity) allows, publishes their
 // items, watches completion records the kernel writes to host-mapped memory, re-lifts ties and
 // hands finished degrees to bd_server_poll.  Systems that arrive while others run are admitted
-// immediately, so their items interleave with the running ones on the device.
+// immediately, so their items interleave with the running ones on the device.  Systems the
+// persistent kernel does not carry (128-bit minors, dimension above its stack, more than 64
+// points) go to a side worker thread that runs bd_degree's volume path on a stream of its own,
+// beside the persistent kernel.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -47,7 +50,9 @@ struct Req {
   int slot = -1;
   bd_degree_out out{};
   int status = BD_OK;
+  std::string err;          // message of a failed request
   uint64_t cycles = 0;
+  bd::Reduction red;        // side route only: the host reduction, for bd_degree's volume path
 };
 
 }  // namespace
@@ -82,7 +87,7 @@ struct bd_server {
   unsigned long long* h_tail = nullptr;
   bd::DevAcc* h_acc = nullptr;       // one slot's result
   unsigned long long* h_cyc = nullptr;
-  cudaStream_t s_kernel = nullptr, s_ctl = nullptr;
+  cudaStream_t s_kernel = nullptr, s_ctl = nullptr, s_side = nullptr;
   int device = 0;
   // host state
   std::mutex mu;
@@ -95,6 +100,12 @@ struct bd_server {
   std::atomic<bool> running{false};
   bool kernel_live = false;
   std::thread pump;
+  // side route: a queue served by its own thread and stream
+  std::deque<Req*> side_q;
+  std::condition_variable side_cv;
+  bool side_running = true;
+  std::thread side_worker;
+  int resident = 0;  // requests holding a slot (their items on the device)
   bd_server_stats stats{};
   std::string error;
 };
@@ -102,7 +113,7 @@ struct bd_server {
 namespace {
 
 int cu(cudaError_t e, const char* what) {
-  return e == cudaSuccess ? BD_OK : bd::set_error(BD_ERR_CUDA, (std::string(what) + ": " + cudaGetErrorString(e)).c_str());
+  return e == cudaSuccess ? BD_OK : bd::cuda_error(e, what);
 }
 
 // publish one request's items (it already owns a slot) and its slot state
@@ -211,6 +222,10 @@ bool pump_once(bd_server* s) {
     }
     s->in_slot[slot] = nullptr;
     s->free_slots.push_back(slot);
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      s->resident -= 1;
+    }
     finish(s, r);
   }
   // admissions: FIFO or shortest predicted cost first, while a slot and ring room are free and
@@ -240,10 +255,20 @@ bool pump_once(bd_server* s) {
     s->free_slots.pop_back();
     s->in_slot[r->slot] = r;
     r->t_admit = now_ms();
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      s->resident += 1;
+      s->stats.peak_resident = std::max(s->stats.peak_resident, (int32_t)s->resident);
+    }
     if (publish(s, r) != BD_OK) {
       r->status = BD_ERR_CUDA;
+      r->err = "publish failed";
       s->in_slot[r->slot] = nullptr;
       s->free_slots.push_back(r->slot);
+      {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->resident -= 1;
+      }
       finish(s, r);
     }
     progress = true;
@@ -297,6 +322,34 @@ void pump_loop(bd_server* s) {
   }
 }
 
+// the side route: requests the persistent kernel does not carry, one at a time through
+// bd_degree's volume path on the server's side stream (concurrent with the persistent kernel,
+// which leaves room on every SM); drains the queue before it exits
+void side_loop(bd_server* s) {
+  cudaSetDevice(s->device);
+  bd_set_stream(s->s_side);
+  for (;;) {
+    Req* r = nullptr;
+    {
+      std::unique_lock<std::mutex> lk(s->mu);
+      s->side_cv.wait(lk, [&] { return !s->side_q.empty() || !s->side_running; });
+      if (s->side_q.empty()) break;
+      r = s->side_q.front();
+      s->side_q.pop_front();
+    }
+    r->t_admit = now_ms();
+    bd_degree_out o;
+    const int rc = bd::degree_from_reduction(r->red, r->N - 1, r->seed, &o);
+    if (rc) {
+      r->status = rc;
+      r->err = bd_last_error();
+    } else {
+      r->out = o;
+    }
+    finish(s, r);
+  }
+}
+
 void release(bd_server* s) {
   cudaFree(s->d_desc);
   cudaFree(s->d_pts);
@@ -318,7 +371,9 @@ void release(bd_server* s) {
   cudaFreeHost(s->h_cyc);
   if (s->s_kernel) cudaStreamDestroy(s->s_kernel);
   if (s->s_ctl) cudaStreamDestroy(s->s_ctl);
+  if (s->s_side) cudaStreamDestroy(s->s_side);
   for (Req* r : s->waiting) delete r;
+  for (Req* r : s->side_q) delete r;
   for (Req* r : s->done) delete r;
   for (Req* r : s->in_slot) delete r;
 }
@@ -354,15 +409,15 @@ int bd_server_start(const bd_server_opts* opts, bd_server** out) {
   auto A = [&](cudaError_t x) {
     if (rc == BD_OK && x != cudaSuccess) rc = cu(x, "server allocation");
   };
-  A(cudaMalloc(&s->d_desc, sizeof(bd::BatchDesc) * s->slots));
-  A(cudaMalloc(&s->d_pts, sizeof(int64_t) * bd::BD_SERVE_PTS * s->slots));
-  A(cudaMalloc(&s->d_ring, sizeof(bd::BatchItem) * s->ring_cap));
-  A(cudaMalloc(&s->d_head, sizeof(unsigned long long)));
-  A(cudaMalloc(&s->d_tail, sizeof(unsigned long long)));
-  A(cudaMalloc(&s->d_remaining, sizeof(unsigned) * s->slots));
-  A(cudaMalloc(&s->d_acc, sizeof(bd::DevAcc) * s->slots));
-  A(cudaMalloc(&s->d_cycles, sizeof(unsigned long long) * s->slots));
-  A(cudaMalloc(&s->d_comp_count, sizeof(unsigned long long)));
+  A(bd::dev_malloc(&s->d_desc, sizeof(bd::BatchDesc) * s->slots));
+  A(bd::dev_malloc(&s->d_pts, sizeof(int64_t) * bd::BD_SERVE_PTS * s->slots));
+  A(bd::dev_malloc(&s->d_ring, sizeof(bd::BatchItem) * s->ring_cap));
+  A(bd::dev_malloc(&s->d_head, sizeof(unsigned long long)));
+  A(bd::dev_malloc(&s->d_tail, sizeof(unsigned long long)));
+  A(bd::dev_malloc(&s->d_remaining, sizeof(unsigned) * s->slots));
+  A(bd::dev_malloc(&s->d_acc, sizeof(bd::DevAcc) * s->slots));
+  A(bd::dev_malloc(&s->d_cycles, sizeof(unsigned long long) * s->slots));
+  A(bd::dev_malloc(&s->d_comp_count, sizeof(unsigned long long)));
   A(cudaHostAlloc((void**)&s->h_comp, sizeof(unsigned long long) * s->comp_cap, cudaHostAllocMapped));
   A(cudaHostAlloc((void**)&s->h_stop, sizeof(int), cudaHostAllocMapped));
   A(cudaMallocHost(&s->h_desc, sizeof(bd::BatchDesc) * s->slots));
@@ -374,6 +429,7 @@ int bd_server_start(const bd_server_opts* opts, bd_server** out) {
   A(cudaMallocHost(&s->h_cyc, sizeof(unsigned long long)));
   A(cudaStreamCreateWithFlags(&s->s_kernel, cudaStreamNonBlocking));
   A(cudaStreamCreateWithFlags(&s->s_ctl, cudaStreamNonBlocking));
+  A(cudaStreamCreateWithFlags(&s->s_side, cudaStreamNonBlocking));
   if (rc == BD_OK) {
     std::memset((void*)s->h_comp, 0, sizeof(unsigned long long) * s->comp_cap);
     *s->h_stop = 0;
@@ -396,6 +452,7 @@ int bd_server_start(const bd_server_opts* opts, bd_server** out) {
   s->stats.warps_per_block = s->shape.warps;
   s->running = true;
   s->pump = std::thread(pump_loop, s);
+  s->side_worker = std::thread(side_loop, s);
   *out = s;
   return BD_OK;
 }
@@ -403,7 +460,7 @@ int bd_server_start(const bd_server_opts* opts, bd_server** out) {
 int bd_server_submit(bd_server* s, const int64_t* A, int32_t n, int32_t m, const int64_t* coef, uint64_t seed,
                      double predicted_cost, int64_t* ticket) {
   if (!s || (!A && m > 0)) return bd::set_error(BD_ERR_ARG, "NULL argument");
-  if (n < 1 || n >= BD_NMAX || m < 0 || m > 256) return bd::set_error(BD_ERR_ARG, "need 1 <= n < BD_NMAX, 0 <= m <= 256");
+  if (n < 1 || n > 126 || m < 0 || m > 256) return bd::set_error(BD_ERR_ARG, "need 1 <= n <= 126, 0 <= m <= 256");
   Req* r = new (std::nothrow) Req();
   if (!r) return bd::set_error(BD_ERR_NOMEM, "host allocation");
   r->t_submit = now_ms();
@@ -421,33 +478,33 @@ int bd_server_submit(bd_server* s, const int64_t* A, int32_t n, int32_t m, const
   r->max_abs = red.max_abs_coord;
   r->N = n + 1;
   r->K = red.dim;
-  r->pts = std::move(red.points);
   r->seed = seed;
   r->out.rank = r->rank;
   r->out.dim = r->dim;
   r->out.torsion = r->torsion;
   r->out.consistent = r->consistent ? 1 : 0;
   r->out.max_abs_coord = (int32_t)std::min<int64_t>(r->max_abs, INT32_MAX);
-  r->out.subsets = r->K > 0 ? bd::binom(r->N, r->K + 1) : 0;
-  bool direct = !r->consistent || r->K == 0;
+  r->out.subsets = r->K > 0 && r->K <= BD_KMAX && r->N <= BD_NMAX ? bd::binom(r->N, r->K + 1) : 0;
+  const bool direct = !r->consistent || r->K == 0;
+  bool side = false;
   if (!direct) {
-    if (r->K > s->maxK) {
-      delete r;
-      return bd::set_error(BD_ERR_ARG, "served systems need dimension <= 10");
+    if (r->K > s->maxK || r->N > s->maxN) {
+      side = true;
+    } else {
+      double coord = 0;
+      const double bound = bd::hadamard_log2(red.points.data(), nullptr, r->N, r->K, (1 << 20) - 1, &coord);
+      r->path = bd::choose_path(coord, bound);
+      // the persistent kernel carries the int32 and int64 walkers; 128-bit systems take the side route
+      side = r->path < 0 || r->path == bd::PATH_WIDE;
     }
-    double coord = 0;
-    const double bound = bd::hadamard_log2(r->pts.data(), nullptr, r->N, r->K, (1 << 20) - 1, &coord);
-    r->path = bd::choose_path(coord, bound);
-    if (r->path < 0 || r->path == bd::PATH_WIDE) {
-      // the serving kernel carries the int32 and int64 walkers; wider systems go through the
-      // single-system path (bd_degree)
-      const int code = r->path < 0 ? BD_ERR_OVERFLOW : BD_ERR_ARG;
-      delete r;
-      return bd::set_error(code, "system needs 128-bit minors: use bd_degree for it");
+    if (!side) {
+      const double sub = (double)bd::binom(r->N, r->K + 1);
+      r->cost = predicted_cost > 0 ? predicted_cost
+                                   : sub * ((double)r->K * r->K * r->K / 3.0 + (double)(r->N - r->K) * (r->K + 1));
     }
-    const double sub = (double)bd::binom(r->N, r->K + 1);
-    r->cost = predicted_cost > 0 ? predicted_cost : sub * ((double)r->K * r->K * r->K / 3.0 + (double)(r->N - r->K) * (r->K + 1));
   }
+  if (side) r->red = std::move(red);
+  else r->pts = std::move(red.points);
   {
     std::lock_guard<std::mutex> lk(s->mu);
     r->ticket = s->next_ticket++;
@@ -458,12 +515,16 @@ int bd_server_submit(bd_server* s, const int64_t* A, int32_t n, int32_t m, const
         r->out.nvol_lo = 1;
         r->out.degree_lo = r->torsion;
       }
+    } else if (side) {
+      s->side_q.push_back(r);
+      s->stats.routed += 1;
     } else {
       s->waiting.push_back(r);
     }
   }
   if (ticket) *ticket = r->ticket;
   if (direct) finish(s, r);
+  if (side) s->side_cv.notify_all();
   return BD_OK;
 }
 
@@ -481,8 +542,9 @@ int bd_server_poll(bd_server* s, int32_t wait_ms, int64_t* ticket, bd_degree_out
   *out = r->out;
   if (ticket) *ticket = r->ticket;
   if (latency_ms) *latency_ms = r->t_done - r->t_submit;
+  const std::string msg = "request " + std::to_string(r->ticket) + " failed: " + r->err;
   delete r;
-  return st == BD_OK ? BD_OK : bd::set_error(st, "request failed");
+  return st == BD_OK ? BD_OK : bd::set_error(st, msg.c_str());
 }
 
 int bd_server_stats_get(bd_server* s, bd_server_stats* out) {
@@ -497,6 +559,12 @@ int bd_server_stop(bd_server* s) {
   if (!s) return BD_OK;
   s->running = false;
   if (s->pump.joinable()) s->pump.join();  // drains admitted and waiting requests first
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->side_running = false;
+  }
+  s->side_cv.notify_all();
+  if (s->side_worker.joinable()) s->side_worker.join();  // and the side route's queue
   *s->h_stop = 1;
   cudaStreamSynchronize(s->s_kernel);
   release(s);

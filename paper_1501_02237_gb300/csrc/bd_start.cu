@@ -111,14 +111,14 @@ int bd_start_solutions(const int64_t* points, int32_t npts, int32_t k, uint64_t 
   };
   auto fail_cuda = [&](cudaError_t e) {
     release();
-    return bd::set_error(BD_ERR_CUDA, cudaGetErrorString(e));
+    return bd::cuda_error(e);
   };
-  cudaError_t e = cudaMalloc(&d_pts, sizeof(int64_t) * npts * k);
-  if (e == cudaSuccess) e = cudaMalloc(&d_recs, 16 * n);
-  if (e == cudaSuccess) e = cudaMalloc(&d_cells, sizeof(StartCell) * n);
-  if (e == cudaSuccess) e = cudaMalloc(&d_status, sizeof(int32_t) * n);
-  if (e == cudaSuccess) e = cudaMalloc(&d_first, sizeof(unsigned long long) * n);
-  if (e == cudaSuccess) e = cudaMalloc(&d_worst, sizeof(unsigned long long));
+  cudaError_t e = bd::dev_malloc(&d_pts, sizeof(int64_t) * npts * k);
+  if (e == cudaSuccess) e = bd::dev_malloc(&d_recs, 16 * n);
+  if (e == cudaSuccess) e = bd::dev_malloc(&d_cells, sizeof(StartCell) * n);
+  if (e == cudaSuccess) e = bd::dev_malloc(&d_status, sizeof(int32_t) * n);
+  if (e == cudaSuccess) e = bd::dev_malloc(&d_first, sizeof(unsigned long long) * n);
+  if (e == cudaSuccess) e = bd::dev_malloc(&d_worst, sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_pts, points, sizeof(int64_t) * npts * k, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_recs, recs.data(), 16 * n, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) {
@@ -150,7 +150,7 @@ int bd_start_solutions(const int64_t* points, int32_t npts, int32_t k, uint64_t 
     release();
     return bd::set_error(BD_ERR_ARG, "capacity is below the number of solutions (count holds it)");
   }
-  if (!sols_on_device) e = cudaMalloc(&d_sols, sizeof(double) * 2 * k * total);
+  if (!sols_on_device) e = bd::dev_malloc(&d_sols, sizeof(double) * 2 * k * total);
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_first, first.data(), sizeof(unsigned long long) * n, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(d_worst, 0, sizeof(unsigned long long), st);
   const unsigned int threads = 128;

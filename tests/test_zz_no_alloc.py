@@ -11,11 +11,16 @@ This file sorts last so that a run stopping at the first failure has run every o
 passes both alone in a fresh process and after the rest of the suite.
 """
 
+import json
+import os
+
 import numpy as np
 import pytest
 
 import paper_1501_02237_gb300 as bd
 from workloads import config_system, random_points
+
+GOLDEN = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "oracle_volumes.json")))["configs"]
 
 pytestmark = pytest.mark.gpu
 
@@ -46,6 +51,29 @@ def test_noalloc_matches_volume_twice_in_a_row():
         second = bd.volume_noalloc(pts, seed=seed)
         assert _same(first, want), (first, want)
         assert _same(second, want), (second, want)
+    # and the oracle's exact volume of the n = 24 system
+    assert bd.volume_noalloc(P, seed=0)["nvol"] == GOLDEN["single_n24_k8"]["nvol"]
+
+
+def test_noalloc_coarsens_a_work_list_above_the_cap():
+    # 33 points in Z^10 (193,536,720 subsets): the first split makes 71,251 prefixes, more than
+    # BD_NOALLOC_MAX_ITEMS, so the call coarsens it; the result must not change
+    P = bd.reduce(config_system("heavy_quiver_n32_k10").A)["points"]
+    want = bd.volume(P, seed=0)
+    got = bd.volume_noalloc(P, seed=0)
+    assert _same(got, want), (got, want)
+    assert got["nvol"] == GOLDEN["heavy_quiver_n32_k10"]["nvol"]
+
+
+def test_noalloc_128_bit_path():
+    # kernel points of a system with exponent differences up to 1000: minors beyond 64 bits
+    A = np.random.default_rng(0).integers(-1000, 1001, size=(10, 4)).astype(np.int64)
+    P = bd.reduce(A)["points"]
+    want = bd.volume(P, seed=4)
+    assert want["flags"] & bd.BD_FLAG_INT128
+    for _ in range(2):
+        got = bd.volume_noalloc(P, seed=4)
+        assert _same(got, want), (got, want)
 
 
 def test_noalloc_rejects_sizes_beyond_the_limits():
