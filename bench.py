@@ -483,7 +483,8 @@ def serve_stream(bd, stream, arrivals, order, costs):
 def serve_section(bd, model, cm, rates=(200.0, 2000.0, 5000.0), count=2000):
     """A Poisson stream served with continuous batching (n ~ U[12,30], k ~ U[4,10]) at several
     arrival rates, up to ones that keep the GPU busy: p50/p99 latency and degrees/s for FIFO
-    admission and for smallest-predicted-cost-first admission by the learned model."""
+    admission and for smallest-predicted-cost-first admission by the closed-form bound and by
+    the learned model."""
     import numpy as np
 
     from workloads import batch_systems, poisson_arrivals
@@ -501,7 +502,8 @@ def serve_section(bd, model, cm, rates=(200.0, 2000.0, 5000.0), count=2000):
     for rate in rates:
         arrivals = poisson_arrivals(rate, count, 7)
         per = {}
-        for label, order, costs in [("fifo", 0, None), ("cost_model_order", 1, pred)]:
+        # shortest first by the closed-form bound (predicted_cost 0) isolates what the network adds
+        for label, order, costs in [("fifo", 0, None), ("closed_form_order", 1, None), ("cost_model_order", 1, pred)]:
             lat, el, st, degs = serve_stream(bd, stream, arrivals, order, costs)
             lat = np.array(lat)
             per[label] = dict(degrees_per_s=len(lat) / el, p50_ms=float(np.percentile(lat, 50)),

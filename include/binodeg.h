@@ -249,6 +249,14 @@ int bd_batch_destroy(bd_batch* batch);
  * not carry (128-bit minors, dimension above 10, more than 64 points: up to 126 variables are
  * accepted, as by bd_degree) are served by a side worker thread that runs bd_degree's volume
  * path, in arrival order, on a stream of its own beside the persistent kernel.
+ *
+ * Every work item is published with a stamp (its ticket) written after it; a warp that claims
+ * a ticket waits for the stamp, at most publish_wait_ms.  When that bound runs out the kernel
+ * records the ticket and every warp exits (no GPU fault); the pump then fails the request that
+ * owns the ticket with BD_ERR_TIMEOUT (bd_server_poll returns it with the ticket), puts the
+ * other admitted requests back at the front of the queue (they run again from the start, so
+ * their results stay exact), resets the ring and relaunches the kernel.  bd_server_stats counts
+ * these faults.
  */
 typedef struct bd_server bd_server;
 typedef struct {
@@ -260,7 +268,10 @@ typedef struct {
   int64_t item_subsets;      /* smallest work item in subsets (0: 256) */
   int64_t max_inflight_items;/* admitted but unfinished items (0: the ring capacity) */
   int32_t order;             /* 0 FIFO, 1 smallest predicted cost first */
-  int32_t reserved[3];
+  int32_t publish_wait_ms;   /* bound of the kernel's wait for a work item's publication (0: 1000) */
+  int32_t test_withhold;     /* test hook, 0 in normal use: the n-th admission's publication stamps
+                                are never written, so the bounded wait for them runs out */
+  int32_t reserved;
 } bd_server_opts;
 typedef struct {
   int64_t submitted, completed, relifted, launches;
@@ -268,7 +279,7 @@ typedef struct {
   int32_t slots, blocks, warps_per_block, waiting;
   int64_t routed;            /* requests served by the side route */
   int32_t peak_resident;     /* most requests holding a slot (items on the device) at once */
-  int32_t reserved;
+  int32_t faults;            /* publication waits that ran out (each reset the ring) */
 } bd_server_stats;
 int bd_server_start(const bd_server_opts* opts, bd_server** server);
 int bd_server_submit(bd_server* server, const int64_t* A, int32_t n, int32_t m, const int64_t* coef, uint64_t seed,

@@ -15,7 +15,7 @@ import numpy as np
 from ._lib import (BD_FEATURES, BD_MLP_PARAMS, BD_FLAG_DEGENERATE, BD_FLAG_INCONSISTENT, BD_FLAG_INT128, BD_FLAG_PIVOT, KMAX,  # noqa: F401
                    NMAX, BatchOpts, BatchStats, BinodegError, DegreeOut, HostOpts, MixedOut, PeakOut, PlanOpts, ServerOpts,
                    ServerStats, VolumeOut, check, i64, lib, ptr)
-from ._lib import F32P, I32P, U8P
+from ._lib import BD_OK, F32P, I32P, U8P
 
 __all__ = ["CostModel", "Server", "degree", "volume", "volume_noalloc", "volume_lifted", "classify", "reduce", "Plan", "Batch", "set_stream",
            "host_volume_lifted", "cells", "host_cells", "start_solutions", "host_start_solutions", "mixed_volume",
@@ -503,9 +503,10 @@ class Server:
     """bd_server_*: continuous-batching service (persistent kernel fed while it runs)."""
 
     def __init__(self, slots: int = 0, ring_items: int = 0, memory_budget: int = 0, warps_per_block: int = 0,
-                 blocks_per_sm: int = 0, item_subsets: int = 0, max_inflight_items: int = 0, order: int = 0):
+                 blocks_per_sm: int = 0, item_subsets: int = 0, max_inflight_items: int = 0, order: int = 0,
+                 publish_wait_ms: int = 0, test_withhold: int = 0):
         o = ServerOpts(slots, ring_items, memory_budget, warps_per_block, blocks_per_sm, item_subsets,
-                       max_inflight_items, order)
+                       max_inflight_items, order, publish_wait_ms, test_withhold)
         h = C.c_void_p()
         check(lib().bd_server_start(C.byref(o), C.byref(h)))
         self.handle = h
@@ -527,7 +528,10 @@ class Server:
         rc = lib().bd_server_poll(self.handle, wait_ms, C.byref(t), C.byref(out), C.byref(lat))
         if rc == 7:  # BD_ERR_STATE: nothing finished yet
             return None
-        check(rc)
+        if rc != BD_OK:  # a failed request: the error carries its ticket
+            err = BinodegError(rc, lib().bd_last_error().decode())
+            err.ticket = t.value
+            raise err
         return t.value, out.as_dict(), lat.value
 
     def stats(self) -> dict:

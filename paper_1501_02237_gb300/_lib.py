@@ -94,14 +94,15 @@ class BatchStats(C.Structure):
 class ServerOpts(C.Structure):
     _fields_ = [("slots", C.c_int32), ("ring_items", C.c_int32), ("memory_budget", C.c_int64),
                 ("warps_per_block", C.c_int32), ("blocks_per_sm", C.c_int32), ("item_subsets", C.c_int64),
-                ("max_inflight_items", C.c_int64), ("order", C.c_int32), ("reserved", C.c_int32 * 3)]
+                ("max_inflight_items", C.c_int64), ("order", C.c_int32), ("publish_wait_ms", C.c_int32),
+                ("test_withhold", C.c_int32), ("reserved", C.c_int32)]
 
 
 class ServerStats(C.Structure):
     _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("relifted", C.c_int64), ("launches", C.c_int64),
                 ("ring_items", C.c_int64), ("slots", C.c_int32), ("blocks", C.c_int32),
                 ("warps_per_block", C.c_int32), ("waiting", C.c_int32), ("routed", C.c_int64),
-                ("peak_resident", C.c_int32), ("reserved", C.c_int32)]
+                ("peak_resident", C.c_int32), ("faults", C.c_int32)]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}

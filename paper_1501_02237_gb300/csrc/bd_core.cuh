@@ -66,6 +66,39 @@ BD_HD int popc64(uint64_t x) {
 #endif
 }
 
+BD_HD int popc32(uint32_t x) {
+#ifdef __CUDA_ARCH__
+  return __popc(x);
+#else
+  return __builtin_popcount(x);
+#endif
+}
+
+// position of the r-th set bit (from 0) of m, which has more than r set bits: a binary search
+// over popcounts of the word's halves
+BD_HD int nth_set(uint64_t m, int r) {
+  int pos = 0;
+  uint32_t w = (uint32_t)m;
+  const int lo = popc32(w);
+  if (r >= lo) {
+    r -= lo;
+    w = (uint32_t)(m >> 32);
+    pos = 32;
+  }
+  for (int sh = 16; sh >= 1; sh >>= 1) {
+    const uint32_t low = w & ((1u << sh) - 1u);
+    const int c = popc32(low);
+    if (r >= c) {
+      r -= c;
+      w >>= sh;
+      pos += sh;
+    } else {
+      w = low;
+    }
+  }
+  return pos;
+}
+
 BD_HD int ctz128(u128 x) {
   uint64_t lo = (uint64_t)x;
   return lo ? ctz64(lo) : 64 + ctz64((uint64_t)(x >> 64));
@@ -211,6 +244,16 @@ inline void fill_colex_table(uint32_t* out) {
     for (int j = 1; j < k; ++j)
       for (int i = 0; i < j; ++i) out[t++] = (uint32_t)i | ((uint32_t)j << 8) | ((uint32_t)k << 16);
 }
+
+// four single-precision values loaded as one 16-byte word (16-byte aligned address)
+#ifdef __CUDACC__
+typedef float4 F4;
+#else
+struct alignas(16) F4 {
+  float x, y, z, w;
+};
+#endif
+BD_HD F4 ld4(const float* p) { return *reinterpret_cast<const F4*>(p); }
 
 // square root of v >= 1 to a few ulps (the callers correct the integer part they take from it)
 BD_HD float approx_sqrt(float v) {
@@ -391,6 +434,7 @@ template <class TC>
 struct Uniform {
   TC piv[KMAX];                        // the pivots p_j (piv[0] = 1)
   typename DivOf<TC>::type dv[KMAX];   // exact divider by p_j (dv[0]: by 1)
+  uint64_t taken[KMAX];                // taken[j]: the points s_0 .. s_j (bit q for point q)
 };
 constexpr size_t kUniformBytes = 1024;  // room for Uniform<TC> of every coordinate type
 
@@ -546,60 +590,158 @@ BD_COLD int side3_exact(StateView<TC, TL> v, int c, int p, int q, int sig, TC xc
   return cs == 0 ? 0 : ((cs == ((Cp < 0 ? -1 : 1) * pc)) ? sig : -sig);
 }
 
-// level K-2 values of point x after the Bareiss step with pivot row c1 on state K-3 (two
-// coordinate minors X, Y and the lift minor L); a is c1's pivot, pi its column (-1: none)
+// A point's values on the reduced state K-3 (three coordinate minors and the lift minor) and on
+// state K-4 (four coordinate minors and the lift minor), read from the stack or produced by an
+// exact Bareiss step.
 template <class TC, class TL>
-BD_HD void level_after(const StateView<TC, TL>& v, int c1, int x, TC& X, TC& Y, TL& L, TC& a, int& pi) {
+struct Row3 {
+  TC x[3];
+  TL l;
+};
+template <class TC, class TL>
+struct Row4 {
+  TC x[4];
+  TL l;
+};
+
+template <class TC, class TL>
+BD_HD Row3<TC, TL> row3(const StateView<TC, TL>& v, int x) {
   const int o = level_offset(v.K, v.K - 3), S = v.SLOTS;
-  pi = -1;
-  for (int e = 0; e < 3; ++e)
-    if (v.sc[(o + e) * S + c1] != 0) { pi = e; break; }
-  if (pi < 0) { X = Y = 0; L = 0; a = 0; return; }
-  a = v.sc[(o + pi) * S + c1];
-  const TC bq = v.sc[(o + pi) * S + x];
-  const int r0 = pi == 0 ? 1 : 0, r1 = pi == 2 ? 1 : 2;
-  const typename DivOf<TC>::type D = v.u->dv[v.K - 3];
-  X = bareiss(v.sc[(o + r0) * S + x], a, bq, v.sc[(o + r0) * S + c1], D);
-  Y = bareiss(v.sc[(o + r1) * S + x], a, bq, v.sc[(o + r1) * S + c1], D);
-  L = bareiss(v.sl[(v.K - 3) * S + x], a, bq, v.sl[(v.K - 3) * S + c1], D);
+  return Row3<TC, TL>{{v.sc[o * S + x], v.sc[(o + 1) * S + x], v.sc[(o + 2) * S + x]}, v.sl[(v.K - 3) * S + x]};
+}
+template <class TC, class TL>
+BD_HD Row4<TC, TL> row4(const StateView<TC, TL>& v, int x) {
+  const int o = level_offset(v.K, v.K - 4), S = v.SLOTS;
+  return Row4<TC, TL>{{v.sc[o * S + x], v.sc[(o + 1) * S + x], v.sc[(o + 2) * S + x], v.sc[(o + 3) * S + x]},
+                      v.sl[(v.K - 4) * S + x]};
 }
 
-// exact K x K minor of {s_0 .. s_{K-3}, c1, c, p} with the sign of D (the coordinate det3 on
-// state K-3): moving c1's pivot column pi to the front permutes the columns by (-1)^pi
-template <class TC, class TL>
-BD_COLD typename Wide2<TC>::type exact_minor(StateView<TC, TL> v, int c1, int c, int p) {
+// level K-2 values of row x (two coordinate minors X, Y and the lift minor L) after the Bareiss
+// step with pivot row c1, both rows on state K-3, whose pivot D divides; a is c1's pivot and pi
+// its column (-1: none)
+template <class TC, class TL, class Div>
+BD_HD void after3(const Row3<TC, TL>& c1, const Row3<TC, TL>& x, const Div& D, TC& X, TC& Y, TL& L, TC& a,
+                  int& pi) {
+  pi = c1.x[0] != 0 ? 0 : (c1.x[1] != 0 ? 1 : (c1.x[2] != 0 ? 2 : -1));
+  if (pi < 0) {
+    X = Y = 0;
+    L = 0;
+    a = 0;
+    return;
+  }
+  a = c1.x[pi];
+  const TC bq = x.x[pi];
+  const int r0 = pi == 0 ? 1 : 0, r1 = pi == 2 ? 1 : 2;
+  X = bareiss(x.x[r0], a, bq, c1.x[r0], D);
+  Y = bareiss(x.x[r1], a, bq, c1.x[r1], D);
+  L = bareiss(x.l, a, bq, c1.l, D);
+}
+
+// exact K x K minor of the prefix with rows c1, c, p (on state K-3, pivot divider D), carrying
+// the sign of the coordinate det3 of the three rows: moving c1's pivot column pi to the front
+// permutes the columns by (-1)^pi
+template <class TC, class TL, class Div>
+BD_HD typename Wide2<TC>::type minor3(const Row3<TC, TL>& c1, const Row3<TC, TL>& c, const Row3<TC, TL>& p,
+                                      const Div& D) {
   typedef typename Wide2<TC>::type W2;
   TC Xc, Yc, Xp, Yp, a;
   TL Lc, Lp;
   int pi;
-  level_after(v, c1, c, Xc, Yc, Lc, a, pi);
+  after3(c1, c, D, Xc, Yc, Lc, a, pi);
   if (pi < 0) return 0;
-  level_after(v, c1, p, Xp, Yp, Lp, a, pi);
+  after3(c1, p, D, Xp, Yp, Lp, a, pi);
   const W2 m = ((W2)Xc * Yp - (W2)Yc * Xp) / (W2)a;  // exact
   return pi == 1 ? -m : m;
 }
 
-// exact side of q for the nonsingular triple (c1, c, p), in the convention of sig (0 on the
-// hyperplane, sig above, -sig below)
-template <class TC, class TL>
-BD_COLD int side4_exact(StateView<TC, TL> v, int c1, int c, int p, int q, int sig) {
+// exact side of q for the nonsingular rows (c1, c, p) on state K-3 (pivot divider D), in the
+// convention of sig (0 on the hyperplane, sig above, -sig below): two more Bareiss steps (pivot
+// rows c1, then c) and the 2-D rule
+template <class TC, class TL, class Div>
+BD_HD int side_rows(const Row3<TC, TL>& c1, const Row3<TC, TL>& c, const Row3<TC, TL>& p, const Row3<TC, TL>& q,
+                    const Div& D, int sig) {
   TC Xc, Yc, Xp, Yp, Xq, Yq, a;
   TL Lc, Lp, Lq;
   int pi;
-  level_after(v, c1, c, Xc, Yc, Lc, a, pi);
-  level_after(v, c1, p, Xp, Yp, Lp, a, pi);
-  level_after(v, c1, q, Xq, Yq, Lq, a, pi);
-  const typename DivOf<TC>::type D = make_div(a);
+  after3(c1, c, D, Xc, Yc, Lc, a, pi);
+  after3(c1, p, D, Xp, Yp, Lp, a, pi);
+  after3(c1, q, D, Xq, Yq, Lq, a, pi);
+  const typename DivOf<TC>::type Da = make_div(a);
   const bool px = Xc != 0;  // c's pivot column on state K-2
   const TC b = px ? Xc : Yc, ob = px ? Yc : Xc;
-  const TL Cp = (TL)bareiss(px ? Yp : Xp, b, px ? Xp : Yp, ob, D);
-  const TL Cq = (TL)bareiss(px ? Yq : Xq, b, px ? Xq : Yq, ob, D);
-  const TL Mp = bareiss(Lp, b, px ? Xp : Yp, Lc, D);
-  const TL Mq = bareiss(Lq, b, px ? Xq : Yq, Lc, D);
+  const TL Cp = (TL)bareiss(px ? Yp : Xp, b, px ? Xp : Yp, ob, Da);
+  const TL Cq = (TL)bareiss(px ? Yq : Xq, b, px ? Xq : Yq, ob, Da);
+  const TL Mp = bareiss(Lp, b, px ? Xp : Yp, Lc, Da);
+  const TL Mq = bareiss(Lq, b, px ? Xq : Yq, Lc, Da);
   const int cs = cross_sign(Cp, Mq, Cq, Mp);
   if (cs == 0) return 0;
   const bool below = cs != (Cp < 0 ? -1 : 1) * (b < 0 ? -1 : 1);  // the 2-D rule
   return below ? -sig : sig;
+}
+
+// exact K x K minor of {s_0 .. s_{K-3}, c1, c, p} with the sign of the coordinate det3 on state K-3
+template <class TC, class TL>
+BD_COLD typename Wide2<TC>::type exact_minor(StateView<TC, TL> v, int c1, int c, int p) {
+  return minor3(row3(v, c1), row3(v, c), row3(v, p), v.u->dv[v.K - 3]);
+}
+
+// exact side of q for the nonsingular triple (c1, c, p) on state K-3
+template <class TC, class TL>
+BD_COLD int side4_exact(StateView<TC, TL> v, int c1, int c, int p, int q, int sig) {
+  return side_rows(row3(v, c1), row3(v, c), row3(v, p), row3(v, q), v.u->dv[v.K - 3], sig);
+}
+
+// state K-3 row of x from state K-4 after the Bareiss step with pivot row c0 (column pi0, its
+// first nonzero coordinate), divided by the pivot of state K-4; the other three columns keep
+// their order, as in the walker's own step
+template <class TC, class TL, class Div>
+BD_HD Row3<TC, TL> step43(const Row4<TC, TL>& c0, int pi0, const Row4<TC, TL>& x, const Div& D) {
+  const TC a0 = c0.x[pi0], bq = x.x[pi0];
+  const int e0 = pi0 == 0 ? 1 : 0, e1 = pi0 <= 1 ? 2 : 1, e2 = pi0 <= 2 ? 3 : 2;
+  Row3<TC, TL> r;
+  r.x[0] = bareiss(x.x[e0], a0, bq, c0.x[e0], D);
+  r.x[1] = bareiss(x.x[e1], a0, bq, c0.x[e1], D);
+  r.x[2] = bareiss(x.x[e2], a0, bq, c0.x[e2], D);
+  r.l = bareiss(x.l, a0, bq, c0.l, D);
+  return r;
+}
+
+template <class TC, class TL>
+BD_HD int first_nonzero4(const Row4<TC, TL>& r) {
+  return r.x[0] != 0 ? 0 : (r.x[1] != 0 ? 1 : (r.x[2] != 0 ? 2 : (r.x[3] != 0 ? 3 : -1)));
+}
+
+// The exact 5-D routes of a quadruple c0 < c1 < c < p on state K-4: one Bareiss step with pivot
+// row c0 reduces them to the 4-D routes on state K-3 (whose pivot is c0's, a0).  The coordinate
+// det4 D4 of the four rows satisfies D4 a0^2 = det3 p^3 (-1)^pi0 (det3 of the reduced rows, p
+// the pivot of state K-4), so sign(D4) = sign(det3) sign(p) (-1)^pi0, and the normalized volume
+// |D0| = |D4| / |p|^3 = |det3| / a0^2 is the reduced routes' minor.
+template <class TC, class TL>
+BD_COLD typename Wide2<TC>::type quad_minor(StateView<TC, TL> v, int c0, int c1, int c, int p, int& s4) {
+  const Row4<TC, TL> r0 = row4(v, c0);
+  const int pi0 = first_nonzero4(r0);
+  if (pi0 < 0) {
+    s4 = 0;
+    return 0;
+  }
+  const auto& D = v.u->dv[v.K - 4];
+  const typename DivOf<TC>::type D3 = make_div(r0.x[pi0]);
+  const typename Wide2<TC>::type m =
+      minor3(step43(r0, pi0, row4(v, c1), D), step43(r0, pi0, row4(v, c), D), step43(r0, pi0, row4(v, p), D), D3);
+  const int sd = v.u->piv[v.K - 4] < 0 ? -1 : 1;
+  s4 = m == 0 ? 0 : (m > 0 ? 1 : -1) * sd * ((pi0 & 1) ? -1 : 1);
+  return m < 0 ? -m : m;
+}
+
+// exact side of q for the nonsingular quadruple (c0, c1, c, p) on state K-4
+template <class TC, class TL>
+BD_COLD int side5_exact(StateView<TC, TL> v, int c0, int c1, int c, int p, int q, int sig) {
+  const Row4<TC, TL> r0 = row4(v, c0);
+  const int pi0 = first_nonzero4(r0);
+  const auto& D = v.u->dv[v.K - 4];
+  const typename DivOf<TC>::type D3 = make_div(r0.x[pi0]);
+  return side_rows(step43(r0, pi0, row4(v, c1), D), step43(r0, pi0, row4(v, c), D), step43(r0, pi0, row4(v, p), D),
+                   step43(r0, pi0, row4(v, q), D), D3, sig);
 }
 
 template <class TC, class TL, class Team>
@@ -643,15 +785,16 @@ struct Walker {
       for (int c = 0; c < K; ++c) {
         const TC v = (TC)(P[c * N + q] - P[c * N + s0]);
         sc[c * SLOTS + q] = v;
-        if (conv) fl[c * SLOTS + q] = f32_of(v);
+        if (conv) fl[4 * q + c] = f32_of(v);
       }
       const TL l = (TL)(P[K * N + q] - P[K * N + s0]);
       sl[q] = l;
-      if (conv) fl[3 * SLOTS + q] = f32_of(l);
+      if (conv) fl[4 * q + 3] = f32_of(l);
     }
     if (tm.lane() == 0) {
       u->dv[0] = make_div((TC)1);
       u->piv[0] = 1;
+      u->taken[0] = 1ull << s0;
     }
     psign = 1;
     tm.sync();
@@ -676,39 +819,50 @@ struct Walker {
     tm.sync();  // readers of the old state j (a sibling's subtree) are done
     // state K-3 is the 4-D stage's input: its single-precision copies are written here too
     const bool conv = kFiltered && j == K - 3;
-    // whole points one per lane; when N exceeds the team width, the last N mod width points
-    // have their entries dealt across the lanes instead (one lane would carry them alone)
-    const int W = tm.lanes(), whole = N > W ? N - N % W : N;
-    for (int q = tm.lane(); q < whole; q += W) {
+    auto whole_point = [&](int q) {
       const TC bq = sc[(po + pi) * SLOTS + q];
       for (int e = 0; e < ncoord - 1; ++e) {
         const int ep = e < pi ? e : e + 1;
         const TC v = bareiss(sc[(po + ep) * SLOTS + q], pj, bq, sc[(po + ep) * SLOTS + c], D);
         sc[(no + e) * SLOTS + q] = v;
-        if (conv) fl[e * SLOTS + q] = f32_of(v);
+        if (conv) fl[4 * q + e] = f32_of(v);
       }
       const TL l = bareiss(sl[(j - 1) * SLOTS + q], pj, bq, rl, D);
       sl[j * SLOTS + q] = l;
-      if (conv) fl[3 * SLOTS + q] = f32_of(l);
-    }
-    for (int t = tm.lane(); t < (N - whole) * ncoord; t += W) {
+      if (conv) fl[4 * q + 3] = f32_of(l);
+    };
+    // Only the points outside s_0 .. s_{j-1}, c are built: the rows of those vanish from state j
+    // on, and no reader of state j or later touches them.  When the rest fit one pass of the
+    // team (the team is narrower than N), lane l builds the l-th of them.
+    const int W = tm.lanes();
+    const uint64_t taken = u->taken[j - 1] | (1ull << c);
+    const uint64_t rest = (N >= 64 ? ~0ull : ((1ull << N) - 1)) & ~taken;
+    const int nrest = popc64(rest);
+    const bool compact = N > W && nrest <= W;
+    // otherwise whole points one per lane; when N exceeds the team width, the last N mod width
+    // points have their entries dealt across the lanes instead (one lane would carry them alone)
+    const int whole = compact ? 0 : (N > W ? N - N % W : N);
+    if (compact && (int)tm.lane() < nrest) whole_point(nth_set(rest, tm.lane()));
+    for (int q = tm.lane(); q < whole; q += W) whole_point(q);
+    for (int t = tm.lane(); !compact && t < (N - whole) * ncoord; t += W) {
       const int q = whole + t / ncoord, e = t % ncoord;  // entry e < ncoord-1: coordinate; last: lift
       const TC bq = sc[(po + pi) * SLOTS + q];
       if (e < ncoord - 1) {
         const int ep = e < pi ? e : e + 1;
         const TC v = bareiss(sc[(po + ep) * SLOTS + q], pj, bq, sc[(po + ep) * SLOTS + c], D);
         sc[(no + e) * SLOTS + q] = v;
-        if (conv) fl[e * SLOTS + q] = f32_of(v);
+        if (conv) fl[4 * q + e] = f32_of(v);
       } else {
         const TL l = bareiss(sl[(j - 1) * SLOTS + q], pj, bq, rl, D);
         sl[j * SLOTS + q] = l;
-        if (conv) fl[3 * SLOTS + q] = f32_of(l);
+        if (conv) fl[4 * q + 3] = f32_of(l);
       }
     }
     s.set(j, c);
     if (tm.lane() == 0) {
       u->piv[j] = pj;
       u->dv[j] = make_div(pj);
+      u->taken[j] = taken;
     }
     tm.sync();
     return true;
@@ -932,7 +1086,8 @@ struct Walker {
   BD_HD void bottom4(Acc& acc) {
     const int sd = u->piv[K - 3] < 0 ? -1 : 1;
     const uint64_t prefix = member_mask(K - 2);
-    // fl holds the single-precision copies of state K-3 (written by the step that built it).
+    // fl holds the single-precision copies of state K-3 (written by the step that built it),
+    // point-major: the four values of point q at fl[4q .. 4q+3], one 16-byte load per point.
     // Error bounds, u = 2^-24: every term of det4 is a product of four point copies (2u each,
     // f32_of) through at most nine roundings (2x2 minor: product and difference; cofactor:
     // product and two sums; det4: product and three sums), so |error| <= 17.001u T with T the
@@ -977,9 +1132,10 @@ struct Walker {
       float n0 = 0, n1 = 0, n2 = 0, n3 = 0, e0 = 0, e1 = 0, e2 = 0, e3 = 0;
       int sig = 1, s3 = 0;
       if (live) {
-        const float a0 = fl[c1], a1 = fl[SLOTS + c1], a2 = fl[2 * SLOTS + c1], a3 = fl[3 * SLOTS + c1];
-        const float u0 = fl[c], u1 = fl[SLOTS + c], u2 = fl[2 * SLOTS + c], u3 = fl[3 * SLOTS + c];
-        const float w0 = fl[p], w1 = fl[SLOTS + p], w2 = fl[2 * SLOTS + p], w3 = fl[3 * SLOTS + p];
+        const F4 A = ld4(fl + 4 * c1), U = ld4(fl + 4 * c), Wp = ld4(fl + 4 * p);
+        const float a0 = A.x, a1 = A.y, a2 = A.z, a3 = A.w;
+        const float u0 = U.x, u1 = U.y, u2 = U.z, u3 = U.w;
+        const float w0 = Wp.x, w1 = Wp.y, w2 = Wp.z, w3 = Wp.w;
         // 2x2 minors of rows (c, p) and their magnitude sums
         const float m01 = u0 * w1 - u1 * w0, m02 = u0 * w2 - u2 * w0, m12 = u1 * w2 - u2 * w1;
         const float M01 = fabsf(u0 * w1) + fabsf(u1 * w0), M02 = fabsf(u0 * w2) + fabsf(u2 * w0),
@@ -1021,7 +1177,8 @@ struct Walker {
 #ifdef BD_COUNT
         ++qt;
 #endif
-        const float x0 = fl[q], x1 = fl[SLOTS + q], x2 = fl[2 * SLOTS + q], x3 = fl[3 * SLOTS + q];
+        const F4 X = ld4(fl + 4 * q);
+        const float x0 = X.x, x1 = X.y, x2 = X.z, x3 = X.w;
         const float v = fmaf(n0, x0, fmaf(n1, x1, fmaf(n2, x2, n3 * x3)));
         const float bound = fmaf(e0, fabsf(x0), fmaf(e1, fabsf(x1), fmaf(e2, fabsf(x2), e3 * fabsf(x3))));
         const int sg = v > bound ? 1 : (v < -bound ? -1 : side4_exact(view(), c1, c, p, q, sig));

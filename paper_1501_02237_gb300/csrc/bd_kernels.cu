@@ -422,6 +422,12 @@ __device__ void serve_item(WarpTeam& tm, const int64_t* P, int N, int K, int slo
   W.run_item(it, acc);
 }
 
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
 __global__ void BD_ENUM_BOUNDS k_serve(ServeParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -438,7 +444,9 @@ __global__ void BD_ENUM_BOUNDS k_serve(ServeParams p) {
     if (lane == 0) {
       const unsigned long long h = *(volatile unsigned long long*)p.head;
       const unsigned long long t = *p.tail;
-      if (h < t) {
+      if (*(volatile unsigned long long*)p.fault_dev) {
+        quit = 1;  // a publication wait ran out: every warp leaves and the host resets the ring
+      } else if (h < t) {
         if (atomicCAS(p.head, h, h + 1) == h) got = h;
       } else if (*p.stop || ++idle > p.idle_spins) {
         quit = 1;
@@ -452,6 +460,32 @@ __global__ void BD_ENUM_BOUNDS k_serve(ServeParams p) {
     if (got == ~0ull) continue;
     idle = 0;
     __threadfence();  // the item and its slot were published before the tail
+    // The item's publication stamp (written after the item, before the tail) confirms that the
+    // ring position holds this ticket's item.  It is normally there already; the wait for it is
+    // bounded, and when the bound runs out the warp records the ticket and leaves without
+    // touching the item (the host fails its request and resets the ring).
+    int lost = 0;
+    if (lane == 0) {
+      const unsigned long long want = got + 1;
+      const volatile unsigned long long* sp = p.seq + (got % p.ring_cap);
+      if (*sp != want) {
+        const unsigned long long t0 = globaltimer_ns();
+        while (*sp != want) {
+          if (globaltimer_ns() - t0 > p.wait_ns) {
+            lost = 1;
+            break;
+          }
+          __nanosleep(1000);
+        }
+      }
+      if (lost && atomicCAS(p.fault_dev, 0ull, want) == 0ull) {
+        *p.fault_host = want;
+        __threadfence_system();
+      }
+    }
+    lost = __shfl_sync(0xffffffffu, lost, 0);
+    if (lost) break;
+    __threadfence();
     const volatile unsigned int* rp = reinterpret_cast<const volatile unsigned int*>(p.ring + (got % p.ring_cap));
     BatchItem bi;
     unsigned int* bw = reinterpret_cast<unsigned int*>(&bi);

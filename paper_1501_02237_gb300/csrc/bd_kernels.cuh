@@ -101,6 +101,10 @@ struct ServeParams {
   unsigned long long comp_cap;
   const volatile int* stop;         // host-mapped: 1 asks the kernel to exit
   unsigned long long idle_spins;    // idle polls before a warp exits (the host relaunches on demand)
+  const volatile unsigned long long* seq;  // per ring position: ticket + 1 once its item is published (device)
+  unsigned long long* fault_dev;    // device: ticket + 1 of the first item whose publication wait ran out
+  volatile unsigned long long* fault_host;  // host-mapped copy of fault_dev for the host's pump
+  unsigned long long wait_ns;       // bound of the publication wait (globaltimer nanoseconds)
   int maxN, maxK;
   const uint32_t* tri;              // colex decode table (device) or nullptr
 };

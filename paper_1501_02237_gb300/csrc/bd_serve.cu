@@ -48,6 +48,7 @@ struct Req {
   std::vector<bd::BatchItem> items;
   uint64_t ring_start = 0;  // first ring ticket of the current publication
   int slot = -1;
+  int64_t admission = 0;    // 1-based admission number (the test hook withholds one of them)
   bd_degree_out out{};
   int status = BD_OK;
   std::string err;          // message of a failed request
@@ -79,6 +80,12 @@ struct bd_server {
   unsigned long long* d_comp = nullptr;
   volatile int* h_stop = nullptr;
   int* d_stop = nullptr;
+  unsigned long long* d_seq = nullptr;           // per ring position: ticket + 1 once published
+  unsigned long long* h_seq = nullptr;           // pinned mirror of the stamps
+  unsigned long long* d_fault = nullptr;         // device fault word (see ServeParams)
+  volatile unsigned long long* h_fault = nullptr;  // host-mapped copy
+  unsigned long long* d_fault_map = nullptr;
+  int64_t admissions = 0;
   // pinned staging
   bd::BatchDesc* h_desc = nullptr;   // per slot
   int64_t* h_pts = nullptr;          // per slot
@@ -148,6 +155,16 @@ int publish(bd_server* s, Req* r) {
     e = cudaMemcpyAsync(s->d_ring + start, s->h_ring + start, sizeof(bd::BatchItem) * first, cudaMemcpyHostToDevice, s->s_ctl);
   if (e == cudaSuccess && n > first)
     e = cudaMemcpyAsync(s->d_ring, s->h_ring, sizeof(bd::BatchItem) * (n - first), cudaMemcpyHostToDevice, s->s_ctl);
+  // the publication stamps, after the items (same stream) and before the tail; the test hook
+  // withholds those of one admission so that the kernel's bounded wait for them runs out
+  if (r->admission != s->opts.test_withhold) {
+    for (uint64_t i = 0; i < n; ++i) s->h_seq[(s->tail + i) % s->ring_cap] = s->tail + i + 1;
+    if (e == cudaSuccess && first)
+      e = cudaMemcpyAsync(s->d_seq + start, s->h_seq + start, sizeof(unsigned long long) * first,
+                          cudaMemcpyHostToDevice, s->s_ctl);
+    if (e == cudaSuccess && n > first)
+      e = cudaMemcpyAsync(s->d_seq, s->h_seq, sizeof(unsigned long long) * (n - first), cudaMemcpyHostToDevice, s->s_ctl);
+  }
   s->tail += n;
   *s->h_tail = s->tail;
   if (e == cudaSuccess) e = cudaMemcpyAsync(s->d_tail, s->h_tail, sizeof(unsigned long long), cudaMemcpyHostToDevice, s->s_ctl);
@@ -181,10 +198,9 @@ void finish(bd_server* s, Req* r) {
   s->cv.notify_all();
 }
 
-// one pump iteration; returns true if it made progress
-bool pump_once(bd_server* s) {
+// completion records the kernel has published: results, re-lifts, freed slots
+bool take_completions(bd_server* s) {
   bool progress = false;
-  // completions
   for (;;) {
     const unsigned long long rec = s->h_comp[s->comp_read % s->comp_cap];
     if ((rec >> 32) != (unsigned long long)(s->comp_read + 1)) break;
@@ -228,6 +244,68 @@ bool pump_once(bd_server* s) {
     }
     finish(s, r);
   }
+  return progress;
+}
+
+// A publication wait in the kernel ran out: every warp has left or is leaving.  Once the kernel
+// has exited, finished requests are taken, the request that owns the lost ticket fails with
+// BD_ERR_TIMEOUT, the other admitted requests go back to the front of the queue (their partial
+// sums are discarded and they run again from the start), and the ring, its stamps and the
+// completion records start over.
+void recover_from_fault(bd_server* s) {
+  const unsigned long long ticket = *s->h_fault - 1;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stats.faults += 1;  // counted before any request of this fault is handed back
+  }
+  cudaStreamSynchronize(s->s_kernel);
+  s->kernel_live = false;
+  take_completions(s);
+  std::vector<Req*> requeue;
+  for (int slot = 0; slot < s->slots; ++slot) {
+    Req* r = s->in_slot[slot];
+    if (!r) continue;
+    s->in_slot[slot] = nullptr;
+    s->free_slots.push_back(slot);
+    if (ticket >= r->ring_start && ticket < r->ring_start + r->items.size()) {
+      r->status = BD_ERR_TIMEOUT;
+      r->err = "the device-side wait for the publication of work item " + std::to_string(ticket) +
+               " ran out";
+      {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->resident -= 1;
+      }
+      finish(s, r);
+    } else {
+      requeue.push_back(r);
+    }
+  }
+  cudaError_t e = cudaMemsetAsync(s->d_head, 0, sizeof(unsigned long long), s->s_ctl);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->d_tail, 0, sizeof(unsigned long long), s->s_ctl);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->d_comp_count, 0, sizeof(unsigned long long), s->s_ctl);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->d_seq, 0, sizeof(unsigned long long) * s->ring_cap, s->s_ctl);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->d_fault, 0, sizeof(unsigned long long), s->s_ctl);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->s_ctl);
+  std::memset((void*)s->h_comp, 0, sizeof(unsigned long long) * s->comp_cap);
+  std::memset(s->h_seq, 0, sizeof(unsigned long long) * s->ring_cap);
+  s->comp_read = 0;
+  s->tail = 0;
+  s->ring_used = 0;
+  s->inflight_items = 0;
+  *s->h_fault = 0;
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->resident -= (int)requeue.size();
+  for (auto it = requeue.rbegin(); it != requeue.rend(); ++it) s->waiting.push_front(*it);
+  if (e != cudaSuccess) s->error = cudaGetErrorString(e);
+}
+
+// one pump iteration; returns true if it made progress
+bool pump_once(bd_server* s) {
+  if (*s->h_fault) {
+    recover_from_fault(s);
+    return true;
+  }
+  bool progress = take_completions(s);
   // admissions: FIFO or shortest predicted cost first, while a slot and ring room are free and
   // the in-flight work stays below the budget
   for (;;) {
@@ -255,6 +333,7 @@ bool pump_once(bd_server* s) {
     s->free_slots.pop_back();
     s->in_slot[r->slot] = r;
     r->t_admit = now_ms();
+    r->admission = ++s->admissions;
     {
       std::lock_guard<std::mutex> lk(s->mu);
       s->resident += 1;
@@ -292,6 +371,10 @@ bool pump_once(bd_server* s) {
       p.comp_cap = s->comp_cap;
       p.stop = s->d_stop;
       p.idle_spins = 20000;  // ~40 ms of 2 us naps without work, then the warps exit
+      p.seq = s->d_seq;
+      p.fault_dev = s->d_fault;
+      p.fault_host = s->d_fault_map;
+      p.wait_ns = (unsigned long long)(s->opts.publish_wait_ms > 0 ? s->opts.publish_wait_ms : 1000) * 1000000ull;
       p.maxN = s->maxN;
       p.maxK = s->maxK;
       p.tri = s->tri;
@@ -360,6 +443,10 @@ void release(bd_server* s) {
   cudaFree(s->d_acc);
   cudaFree(s->d_cycles);
   cudaFree(s->d_comp_count);
+  cudaFree(s->d_seq);
+  cudaFree(s->d_fault);
+  cudaFreeHost((void*)s->h_fault);
+  cudaFreeHost(s->h_seq);
   cudaFreeHost((void*)s->h_comp);
   cudaFreeHost((void*)s->h_stop);
   cudaFreeHost(s->h_desc);
@@ -392,11 +479,12 @@ int bd_server_start(const bd_server_opts* opts, bd_server** out) {
   if (s->opts.memory_budget > 0) {  // admission by device memory: the ring shrinks to the budget
     const int64_t per_slot = sizeof(int64_t) * bd::BD_SERVE_PTS + sizeof(bd::BatchDesc) + sizeof(bd::DevAcc) + 12;
     const int64_t left = s->opts.memory_budget - per_slot * s->slots;
-    if (left < (int64_t)sizeof(bd::BatchItem) * 1024) {
+    const int64_t per_item = sizeof(bd::BatchItem) + sizeof(unsigned long long);  // the item and its stamp
+    if (left < per_item * 1024) {
       delete s;
       return bd::set_error(BD_ERR_ARG, "memory budget below the slot table plus 1024 ring items");
     }
-    s->ring_cap = std::min<uint64_t>(s->ring_cap, (uint64_t)(left / (int64_t)sizeof(bd::BatchItem)));
+    s->ring_cap = std::min<uint64_t>(s->ring_cap, (uint64_t)(left / per_item));
   }
   s->comp_cap = 4096;
   cudaGetDevice(&s->device);
@@ -418,6 +506,10 @@ int bd_server_start(const bd_server_opts* opts, bd_server** out) {
   A(bd::dev_malloc(&s->d_acc, sizeof(bd::DevAcc) * s->slots));
   A(bd::dev_malloc(&s->d_cycles, sizeof(unsigned long long) * s->slots));
   A(bd::dev_malloc(&s->d_comp_count, sizeof(unsigned long long)));
+  A(bd::dev_malloc(&s->d_seq, sizeof(unsigned long long) * s->ring_cap));
+  A(bd::dev_malloc(&s->d_fault, sizeof(unsigned long long)));
+  A(cudaHostAlloc((void**)&s->h_fault, sizeof(unsigned long long), cudaHostAllocMapped));
+  A(cudaMallocHost(&s->h_seq, sizeof(unsigned long long) * s->ring_cap));
   A(cudaHostAlloc((void**)&s->h_comp, sizeof(unsigned long long) * s->comp_cap, cudaHostAllocMapped));
   A(cudaHostAlloc((void**)&s->h_stop, sizeof(int), cudaHostAllocMapped));
   A(cudaMallocHost(&s->h_desc, sizeof(bd::BatchDesc) * s->slots));
@@ -435,6 +527,11 @@ int bd_server_start(const bd_server_opts* opts, bd_server** out) {
     *s->h_stop = 0;
     A(cudaHostGetDevicePointer((void**)&s->d_comp, (void*)s->h_comp, 0));
     A(cudaHostGetDevicePointer((void**)&s->d_stop, (void*)s->h_stop, 0));
+    *s->h_fault = 0;
+    A(cudaHostGetDevicePointer((void**)&s->d_fault_map, (void*)s->h_fault, 0));
+    A(cudaMemset(s->d_seq, 0, sizeof(unsigned long long) * s->ring_cap));
+    A(cudaMemset(s->d_fault, 0, sizeof(unsigned long long)));
+    std::memset(s->h_seq, 0, sizeof(unsigned long long) * s->ring_cap);
     A(cudaMemset(s->d_head, 0, sizeof(unsigned long long)));
     A(cudaMemset(s->d_tail, 0, sizeof(unsigned long long)));
     A(cudaMemset(s->d_comp_count, 0, sizeof(unsigned long long)));

@@ -243,3 +243,19 @@ def test_reduce_large_systems_converges(seed):
     red = bd.reduce(s.A)
     ref = BinomialStructure(np.asarray(s.A).tolist())
     assert (red["rank"], red["dim"], red["torsion"]) == (ref.rank, ref.dim, ref.torsion)
+
+
+@pytest.mark.parametrize("seed,width", [(0, 8), (1, 8), (2, 16), (3, 16)])
+def test_lockstep_team_narrower_than_the_point_set(seed, width):
+    # more points than lanes (the GPU runs 33 points on 32 lanes): the levels whose remaining
+    # points fit one pass build them compacted (lane l takes the l-th point outside the prefix),
+    # the others deal the ragged tail across lanes; both integer paths against the oracle
+    rng = random.Random(5100 + seed)
+    n, k = width + 1 + seed % 2 * 2, 4
+    pts = [tuple(rng.randint(-3, 3) for _ in range(k)) for _ in range(n)]
+    lf = oracle_lifts(n, seed)
+    ref = nvol_placing(pts)
+    for force in (False, True):
+        r = bd.host_volume_lifted(np.array(pts), np.array(lf), force_int128=force, team_width=width)
+        assert r["status"] == 0
+        assert r["nvol"] == ref, (n, force)
