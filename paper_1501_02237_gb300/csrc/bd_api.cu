@@ -88,7 +88,7 @@ struct ItemList {
   bd::Range* dev_ranges = nullptr;
 };
 std::mutex g_cache_mu;
-std::map<std::tuple<int, int, int64_t, int64_t, int>, std::shared_ptr<ItemList>> g_items;
+std::map<std::tuple<int, int, int64_t, int64_t, int, int>, std::shared_ptr<ItemList>> g_items;
 std::map<std::tuple<int, int, int, int, int, int>, bd::LaunchShape> g_shapes;
 
 int current_device() {
@@ -97,8 +97,8 @@ int current_device() {
   return d;
 }
 
-int get_items(int N, int K, int64_t thr, int64_t teams, std::shared_ptr<ItemList>& out) {
-  const auto key = std::make_tuple(N, K, thr, teams, current_device());
+int get_items(int N, int K, int64_t thr, int64_t teams, int depth, std::shared_ptr<ItemList>& out) {
+  const auto key = std::make_tuple(N, K, thr, teams, current_device(), depth);
   std::lock_guard<std::mutex> lk(g_cache_mu);
   auto it = g_items.find(key);
   if (it != g_items.end()) {
@@ -106,7 +106,7 @@ int get_items(int N, int K, int64_t thr, int64_t teams, std::shared_ptr<ItemList
     return BD_OK;
   }
   auto L = std::make_shared<ItemList>();
-  bd::build_ranges(N, K, (uint64_t)thr, (uint64_t)teams, L->host, L->ranges);
+  bd::build_ranges(N, K, (uint64_t)thr, (uint64_t)teams, depth, L->host, L->ranges);
   std::vector<bd::PackedItem> packed(L->host.size());
   for (size_t i = 0; i < packed.size(); ++i) packed[i] = bd::pack_item(L->host[i]);
   cudaError_t e = bd::dev_malloc(&L->dev, sizeof(bd::PackedItem) * std::max<size_t>(1, L->host.size()));
@@ -292,7 +292,7 @@ int plan_prepare(bd_plan* p, const int64_t* points, const int64_t* lifts, int32_
   const uint64_t total = bd::binom(npts, k + 1);
   const uint64_t warps = (uint64_t)p->shape.blocks * p->shape.warps;
   const int64_t thr = opts && opts->item_subsets > 0 ? opts->item_subsets : (int64_t)bd::default_item_subsets(total, warps);
-  rc = get_items(npts, k, thr, (int64_t)warps, p->items);
+  rc = get_items(npts, k, thr, (int64_t)warps, bd::item_depth(k, p->path), p->items);
   if (rc) return rc;
   rc = get_tri(p->tri);
   if (rc) return rc;
@@ -690,7 +690,7 @@ int bd_host_volume_lifted(const int64_t* points, const int64_t* lifts, int32_t n
   // guided ranges, so that range boundaries and prefix reuse are exercised on one thread too)
   std::vector<bd::Item> items;
   std::vector<bd::Range> ranges;
-  bd::build_ranges(npts, k, o.item_subsets ? o.item_subsets : 4096, 8, items, ranges);
+  bd::build_ranges(npts, k, o.item_subsets ? o.item_subsets : 4096, 8, bd::item_depth(k, path), items, ranges);
   if (shards > 1) {  // this shard's ranges only (u % shards == shard, as on the device)
     std::vector<bd::Range> mine;
     for (size_t u = (size_t)o.shard; u < ranges.size(); u += (size_t)shards) mine.push_back(ranges[u]);
@@ -836,7 +836,7 @@ int bd_host_cells(const int64_t* points, const int64_t* lifts, int32_t npts, int
   }
   std::vector<bd::Item> items;
   std::vector<bd::Range> ranges;
-  bd::build_ranges(npts, k, 4096, 8, items, ranges);
+  bd::build_ranges(npts, k, 4096, 8, bd::item_depth(k, path), items, ranges);
   const size_t cap = (size_t)std::max<int64_t>(capacity, 1);
   std::vector<uint8_t> rec(16 * cap);
   unsigned long long n = 0;

@@ -435,8 +435,9 @@ struct Uniform {
   TC piv[KMAX];                        // the pivots p_j (piv[0] = 1)
   typename DivOf<TC>::type dv[KMAX];   // exact divider by p_j (dv[0]: by 1)
   uint64_t taken[KMAX];                // taken[j]: the points s_0 .. s_j (bit q for point q)
+  uint32_t queue[64];                  // the 5-D stage's nonsingular quadruples awaiting their test
 };
-constexpr size_t kUniformBytes = 1024;  // room for Uniform<TC> of every coordinate type
+constexpr size_t kUniformBytes = 1088;  // room for Uniform<TC> of every coordinate type
 
 // ---------------------------------------------------------------------------------------------
 // Cells of the triangulation and their inner normals (Sec. 6, Eq. lower-d-face-again): the
@@ -453,7 +454,7 @@ struct CellSink {
   unsigned long long cap;
 };
 
-static BD_COLD void record_cell(CellSink sink, Idx15 s, int pre, int a, int b, int c) {
+static BD_COLD void record_cell(CellSink sink, Idx15 s, int pre, int a, int b, int c, int d = -1) {
 #ifdef __CUDA_ARCH__
   const unsigned long long slot = atomicAdd(sink.count, 1ull);
 #else
@@ -466,6 +467,7 @@ static BD_COLD void record_cell(CellSink sink, Idx15 s, int pre, int a, int b, i
   if (a >= 0) rec[n++] = (uint8_t)a;
   if (b >= 0) rec[n++] = (uint8_t)b;
   if (c >= 0) rec[n++] = (uint8_t)c;
+  if (d >= 0) rec[n++] = (uint8_t)d;
   memcpy(sink.out + 16 * slot, rec, 16);
 }
 
@@ -733,6 +735,27 @@ BD_COLD typename Wide2<TC>::type quad_minor(StateView<TC, TL> v, int c0, int c1,
   return m < 0 ? -m : m;
 }
 
+// the exact sign of D4 alone (no division): sign(det3) = sign(Xc Yp - Yc Xp) sign(a) (-1)^pi
+// with the second step's values, as minor3 computes them before its exact division
+template <class TC, class TL>
+BD_COLD int quad_sign(StateView<TC, TL> v, int c0, int c1, int c, int p) {
+  const Row4<TC, TL> r0 = row4(v, c0);
+  const int pi0 = first_nonzero4(r0);
+  if (pi0 < 0) return 0;
+  const auto& D = v.u->dv[v.K - 4];
+  const typename DivOf<TC>::type D3 = make_div(r0.x[pi0]);
+  const Row3<TC, TL> a1 = step43(r0, pi0, row4(v, c1), D);
+  TC Xc, Yc, Xp, Yp, a;
+  TL Lc, Lp;
+  int pi;
+  after3(a1, step43(r0, pi0, row4(v, c), D), D3, Xc, Yc, Lc, a, pi);
+  if (pi < 0) return 0;
+  after3(a1, step43(r0, pi0, row4(v, p), D), D3, Xp, Yp, Lp, a, pi);
+  const int cs = cross_sign((TL)Xc, (TL)Yp, (TL)Yc, (TL)Xp);
+  const int sd = v.u->piv[v.K - 4] < 0 ? -1 : 1;
+  return cs * (a < 0 ? -1 : 1) * (pi == 1 ? -1 : 1) * sd * ((pi0 & 1) ? -1 : 1);
+}
+
 // exact side of q for the nonsingular quadruple (c0, c1, c, p) on state K-4
 template <class TC, class TL>
 BD_COLD int side5_exact(StateView<TC, TL> v, int c0, int c1, int c, int p, int q, int sig) {
@@ -768,28 +791,43 @@ struct Walker {
 
   BD_HD StateView<TC, TL> view() const { return StateView<TC, TL>{sc, sl, u, SLOTS, K}; }
 
-  // the single-precision filtered tests run for the int32 and int64 coordinate paths: the 4-D
-  // test on state K-3 when K >= 3, the 3-D test on state 0 when K = 2; the 128-bit path and
-  // K = 1 use the 2-D test on the fully reduced state
+  // the single-precision filtered tests run for the int32 and int64 coordinate paths: the 5-D
+  // test on state K-4 (int32 coordinate minors, K >= 4), the 4-D test on state K-3 (int64
+  // coordinate minors, or K = 3), the 3-D test on state 0 when K = 2; the 128-bit path and K = 1
+  // use the 2-D test on the fully reduced state.  The 5-D test saves the Bareiss step of state
+  // K-3 at every node and rejects a singular quadruple for a det4, but its single-precision
+  // bound is looser (one exact elimination fewer removes cancellation); where the minors are
+  // 64-bit numbers its exact routes, in 128-bit arithmetic, cost more than the step it saves.
   static constexpr bool kFiltered = sizeof(TL) == 8;
+  static constexpr bool kFive = kFiltered && sizeof(TC) == 4;
+  BD_HD bool five() const { return kFive && K >= 4; }
   // DFS depth at which the bottom stage takes over (the chosen prefix is s_0 .. s_{depth-1}):
-  // the 4-D test finishes the last three levels, the 3-D and 2-D tests the last two
-  BD_HD int bottom_depth() const { return kFiltered && K >= 3 ? K - 2 : (K >= 2 ? K - 1 : 1); }
+  // the 5-D test finishes the last four levels, the 4-D test three, the 3-D and 2-D tests two
+  BD_HD int bottom_depth() const {
+    return five() ? K - 3 : (kFiltered && K >= 3 ? K - 2 : (K >= 2 ? K - 1 : 1));
+  }
+  // The filtered tests read single-precision copies of their input state, point-major: the
+  // coordinate minors of point q at fl[FS q + e], its lift minor at fl[FS q + LI] (FS = 8,
+  // LI = 4 for the 5-D test's five values; FS = 4, LI = 3 for the 4-D test's four).  The Bareiss
+  // step that builds that state writes them.
+  BD_HD int copy_level() const { return five() ? K - 4 : K - 3; }
+  BD_HD int copy_stride() const { return five() ? 8 : 4; }
 
   // state 0: lifted differences z_q = (a_q - a_{s_0}, w_q - w_{s_0})
   BD_HD void start(int s0) {
     tm.sync();  // the previous item's readers are done with the stack
     s.set(0, s0);
-    const bool conv = kFiltered && K == 3;  // state 0 is the 4-D stage's input
+    const bool conv = kFiltered && K >= 3 && copy_level() == 0;  // state 0 is the filter's input
+    const int FS = copy_stride();
     for (int q = tm.lane(); q < N; q += tm.lanes()) {
       for (int c = 0; c < K; ++c) {
         const TC v = (TC)(P[c * N + q] - P[c * N + s0]);
         sc[c * SLOTS + q] = v;
-        if (conv) fl[4 * q + c] = f32_of(v);
+        if (conv) fl[FS * q + c] = f32_of(v);
       }
       const TL l = (TL)(P[K * N + q] - P[K * N + s0]);
       sl[q] = l;
-      if (conv) fl[4 * q + 3] = f32_of(l);
+      if (conv) fl[FS * q + K] = f32_of(l);  // K coordinates at state 0: the lift minor at index K
     }
     if (tm.lane() == 0) {
       u->dv[0] = make_div((TC)1);
@@ -817,19 +855,21 @@ struct Walker {
     const TL rl = sl[(j - 1) * SLOTS + c];
     const Div D = u->dv[j - 1];
     tm.sync();  // readers of the old state j (a sibling's subtree) are done
-    // state K-3 is the 4-D stage's input: its single-precision copies are written here too
-    const bool conv = kFiltered && j == K - 3;
+    // the filtered test's input state: its single-precision copies are written here too (K - j
+    // coordinate minors at fl[FS q + e], the lift minor at fl[FS q + K - j])
+    const bool conv = kFiltered && K >= 3 && j == copy_level();
+    const int FS = copy_stride(), LI = K - j;
     auto whole_point = [&](int q) {
       const TC bq = sc[(po + pi) * SLOTS + q];
       for (int e = 0; e < ncoord - 1; ++e) {
         const int ep = e < pi ? e : e + 1;
         const TC v = bareiss(sc[(po + ep) * SLOTS + q], pj, bq, sc[(po + ep) * SLOTS + c], D);
         sc[(no + e) * SLOTS + q] = v;
-        if (conv) fl[4 * q + e] = f32_of(v);
+        if (conv) fl[FS * q + e] = f32_of(v);
       }
       const TL l = bareiss(sl[(j - 1) * SLOTS + q], pj, bq, rl, D);
       sl[j * SLOTS + q] = l;
-      if (conv) fl[4 * q + 3] = f32_of(l);
+      if (conv) fl[FS * q + LI] = f32_of(l);
     };
     // Only the points outside s_0 .. s_{j-1}, c are built: the rows of those vanish from state j
     // on, and no reader of state j or later touches them.  When the rest fit one pass of the
@@ -851,11 +891,11 @@ struct Walker {
         const int ep = e < pi ? e : e + 1;
         const TC v = bareiss(sc[(po + ep) * SLOTS + q], pj, bq, sc[(po + ep) * SLOTS + c], D);
         sc[(no + e) * SLOTS + q] = v;
-        if (conv) fl[4 * q + e] = f32_of(v);
+        if (conv) fl[FS * q + e] = f32_of(v);
       } else {
         const TL l = bareiss(sl[(j - 1) * SLOTS + q], pj, bq, rl, D);
         sl[j * SLOTS + q] = l;
-        if (conv) fl[4 * q + 3] = f32_of(l);
+        if (conv) fl[FS * q + LI] = f32_of(l);
       }
     }
     s.set(j, c);
@@ -1201,8 +1241,196 @@ struct Walker {
     }
   }
 
+  // ---------------------------------------------------------------------------------------
+  // 5-D test on state K-4.  Each point is v_q = (x0, x1, x2, x3, l) (four coordinate minors and
+  // the lift minor, all scaled by the pivot p of state K-4).  For a quadruple c0 < c1 < c < p
+  // the simplex {s_0 .. s_{K-4}, c0, c1, c, p} is full-dimensional iff the coordinate det4
+  // D4 of the four rows is nonzero, and then its normalized volume is |D4| / |p|^3
+  // (Sylvester's identity: a k x k determinant of state-j rows is the full minor times the
+  // state's pivot to the power k-1).  The lifted hyperplane through its vertices puts q
+  // strictly below the cell iff
+  //     sign(D4) sign(p) det5(v_c0, v_c1, v_c, v_p, v_q) < 0,
+  // det5 = n . v_q with n the five signed cofactors of the rows c0, c1, c, p.
+  // Phase A deals the quadruples to lanes in colex order, a warp-width per round, and decides
+  // sign(D4) (single precision with a rigorous error bound, exactly when undecided); the
+  // nonsingular ones go to the team's queue.  Phase B takes a warp-width of queued quadruples,
+  // one per lane, forms n and its error bounds and walks the points as the 4-D test does.  Most
+  // quadruples are singular, and a singular one costs its lane only the det4 of Phase A.
+  // ---------------------------------------------------------------------------------------
+
+  static BD_HD uint32_t c4(int n) { return n < 4 ? 0u : (uint32_t)(n * (n - 1) * (n - 2) * (n - 3) / 24); }
+
+  // colex triple of rank t (i < j < k) packed i | j << 8 | k << 16, from the decode table when
+  // present
+  BD_HD uint32_t colex3(uint32_t t) const {
+    if (tri) return ldg_u32(tri + t);
+    int k = 2;
+    while ((uint32_t)((k + 1) * k * (k - 1) / 6) <= t) ++k;
+    const uint32_t u = t - (uint32_t)(k * (k - 1) * (k - 2) / 6);
+    int j = 1;
+    while ((uint32_t)((j + 1) * j / 2) <= u) ++j;
+    const uint32_t i = u - (uint32_t)(j * (j - 1) / 2);
+    return i | (uint32_t)j << 8 | (uint32_t)k << 16;
+  }
+
+  // sign of the coordinate det4 of rows c0, c1, c, p, from the single-precision copies.
+  // Error bound, u = 2^-24: every term is a product of four copies (2u each, f32_of) through at
+  // most nine roundings (2x2 minor: product and difference; 3x3: product and two sums; det4:
+  // product and three sums), so |error| <= 17.001u T with T the sum of the magnitudes of the 24
+  // terms; T evaluated in single precision (same depth) is at least (1 - 19u) T, and
+  // eps = 2^-19 = 32u covers it with a factor ~1.9.  Below 2^23 every operand and partial result
+  // is an integer held exactly.  Undecided (or overflowed) values take the exact route.
+  BD_HD int d4_sign(int c0, int c1, int c, int p) const {
+    const float eps = 1.9073486328125e-6f;  // 2^-19
+    const F4 A = ld4(fl + 8 * c0), B = ld4(fl + 8 * c1), U = ld4(fl + 8 * c), V = ld4(fl + 8 * p);
+    const float m01 = U.x * V.y - U.y * V.x, m02 = U.x * V.z - U.z * V.x, m03 = U.x * V.w - U.w * V.x;
+    const float m12 = U.y * V.z - U.z * V.y, m13 = U.y * V.w - U.w * V.y, m23 = U.z * V.w - U.w * V.z;
+    const float M01 = fabsf(U.x * V.y) + fabsf(U.y * V.x), M02 = fabsf(U.x * V.z) + fabsf(U.z * V.x);
+    const float M03 = fabsf(U.x * V.w) + fabsf(U.w * V.x), M12 = fabsf(U.y * V.z) + fabsf(U.z * V.y);
+    const float M13 = fabsf(U.y * V.w) + fabsf(U.w * V.y), M23 = fabsf(U.z * V.w) + fabsf(U.w * V.z);
+    const float t123 = B.y * m23 - B.z * m13 + B.w * m12, t023 = B.x * m23 - B.z * m03 + B.w * m02;
+    const float t013 = B.x * m13 - B.y * m03 + B.w * m01, t012 = B.x * m12 - B.y * m02 + B.z * m01;
+    const float T123 = fabsf(B.y) * M23 + fabsf(B.z) * M13 + fabsf(B.w) * M12;
+    const float T023 = fabsf(B.x) * M23 + fabsf(B.z) * M03 + fabsf(B.w) * M02;
+    const float T013 = fabsf(B.x) * M13 + fabsf(B.y) * M03 + fabsf(B.w) * M01;
+    const float T012 = fabsf(B.x) * M12 + fabsf(B.y) * M02 + fabsf(B.z) * M01;
+    const float D4 = A.x * t123 - A.y * t023 + A.z * t013 - A.w * t012;
+    const float B4 = fabsf(A.x) * T123 + fabsf(A.y) * T023 + fabsf(A.z) * T013 + fabsf(A.w) * T012;
+    if (fabsf(D4) > eps * B4 || B4 < 8388608.0f) return (D4 > 0) - (D4 < 0);
+    return quad_sign(view(), c0, c1, c, p);
+  }
+
+  // Phase B on the first `take` of the qlen queued quadruples (one per lane); the rest move to
+  // the front of the queue.
+  // Error bound of det5, u = 2^-24: every term is a product of five copies (10u) through at most
+  // fourteen roundings (2x2: 2, 3x3: 3, cofactor: 4, det5: 5), so |error| <= 24.001u T with T
+  // the magnitude sum; the bound evaluated in single precision (cofactor magnitudes, then the
+  // sum against |q|) is at least (1 - 19u) eps T, and eps = 2^-19 = 32u covers the error with a
+  // factor ~1.3.  Undecided (or overflowed) values take the exact route.
+  BD_HD void quads(Acc& acc, int take, int qlen, int sd, uint64_t rest) {
+    const int lane = tm.lane();
+    const bool busy = lane < take;
+    const uint32_t rec = busy ? u->queue[lane] : 0u;
+    tm.sync();  // every lane has its entry
+    if (lane + take < qlen) u->queue[lane] = u->queue[lane + take];
+    tm.sync();
+    const int c0 = rec & 63u, c1 = (rec >> 6) & 63u, c = (rec >> 12) & 63u, p = (rec >> 18) & 63u;
+    const int sig = ((rec >> 31) ? -1 : 1) * sd;  // q is below iff sig * det5 < 0
+    float n0 = 0, n1 = 0, n2 = 0, n3 = 0, n4 = 0, e0 = 0, e1 = 0, e2 = 0, e3 = 0, e4 = 0;
+    if (busy) {
+      const float eps = 1.9073486328125e-6f;  // 2^-19
+      const F4 A = ld4(fl + 8 * c0), B = ld4(fl + 8 * c1), U = ld4(fl + 8 * c), V = ld4(fl + 8 * p);
+      const float A4 = fl[8 * c0 + 4], B4 = fl[8 * c1 + 4], U4 = fl[8 * c + 4], V4 = fl[8 * p + 4];
+      // 2x2 minors of rows (c, p) on columns a < b (column 4: the lift), and their magnitudes
+      const float m01 = U.x * V.y - U.y * V.x, m02 = U.x * V.z - U.z * V.x, m03 = U.x * V.w - U.w * V.x;
+      const float m04 = U.x * V4 - U4 * V.x, m12 = U.y * V.z - U.z * V.y, m13 = U.y * V.w - U.w * V.y;
+      const float m14 = U.y * V4 - U4 * V.y, m23 = U.z * V.w - U.w * V.z, m24 = U.z * V4 - U4 * V.z;
+      const float m34 = U.w * V4 - U4 * V.w;
+      const float M01 = fabsf(U.x * V.y) + fabsf(U.y * V.x), M02 = fabsf(U.x * V.z) + fabsf(U.z * V.x);
+      const float M03 = fabsf(U.x * V.w) + fabsf(U.w * V.x), M04 = fabsf(U.x * V4) + fabsf(U4 * V.x);
+      const float M12 = fabsf(U.y * V.z) + fabsf(U.z * V.y), M13 = fabsf(U.y * V.w) + fabsf(U.w * V.y);
+      const float M14 = fabsf(U.y * V4) + fabsf(U4 * V.y), M23 = fabsf(U.z * V.w) + fabsf(U.w * V.z);
+      const float M24 = fabsf(U.z * V4) + fabsf(U4 * V.z), M34 = fabsf(U.w * V4) + fabsf(U4 * V.w);
+      // 3x3 minors of rows (c1, c, p) on columns a < b < c
+      const float b0 = B.x, b1 = B.y, b2 = B.z, b3 = B.w;
+      const float ab0 = fabsf(b0), ab1 = fabsf(b1), ab2 = fabsf(b2), ab3 = fabsf(b3), ab4 = fabsf(B4);
+      const float t012 = b0 * m12 - b1 * m02 + b2 * m01, T012 = ab0 * M12 + ab1 * M02 + ab2 * M01;
+      const float t013 = b0 * m13 - b1 * m03 + b3 * m01, T013 = ab0 * M13 + ab1 * M03 + ab3 * M01;
+      const float t014 = b0 * m14 - b1 * m04 + B4 * m01, T014 = ab0 * M14 + ab1 * M04 + ab4 * M01;
+      const float t023 = b0 * m23 - b2 * m03 + b3 * m02, T023 = ab0 * M23 + ab2 * M03 + ab3 * M02;
+      const float t024 = b0 * m24 - b2 * m04 + B4 * m02, T024 = ab0 * M24 + ab2 * M04 + ab4 * M02;
+      const float t034 = b0 * m34 - b3 * m04 + B4 * m03, T034 = ab0 * M34 + ab3 * M04 + ab4 * M03;
+      const float t123 = b1 * m23 - b2 * m13 + b3 * m12, T123 = ab1 * M23 + ab2 * M13 + ab3 * M12;
+      const float t124 = b1 * m24 - b2 * m14 + B4 * m12, T124 = ab1 * M24 + ab2 * M14 + ab4 * M12;
+      const float t134 = b1 * m34 - b3 * m14 + B4 * m13, T134 = ab1 * M34 + ab3 * M14 + ab4 * M13;
+      const float t234 = b2 * m34 - b3 * m24 + B4 * m23, T234 = ab2 * M34 + ab3 * M24 + ab4 * M23;
+      // cofactors along q's row: n_e = (-1)^e det4(rows c0, c1, c, p without column e)
+      const float a0 = A.x, a1 = A.y, a2 = A.z, a3 = A.w;
+      const float aa0 = fabsf(a0), aa1 = fabsf(a1), aa2 = fabsf(a2), aa3 = fabsf(a3), aa4 = fabsf(A4);
+      n0 = a1 * t234 - a2 * t134 + a3 * t124 - A4 * t123;
+      n1 = -(a0 * t234 - a2 * t034 + a3 * t024 - A4 * t023);
+      n2 = a0 * t134 - a1 * t034 + a3 * t014 - A4 * t013;
+      n3 = -(a0 * t124 - a1 * t024 + a2 * t014 - A4 * t012);
+      n4 = a0 * t123 - a1 * t023 + a2 * t013 - a3 * t012;
+      e0 = eps * (aa1 * T234 + aa2 * T134 + aa3 * T124 + aa4 * T123);
+      e1 = eps * (aa0 * T234 + aa2 * T034 + aa3 * T024 + aa4 * T023);
+      e2 = eps * (aa0 * T134 + aa1 * T034 + aa3 * T014 + aa4 * T013);
+      e3 = eps * (aa0 * T124 + aa1 * T024 + aa2 * T014 + aa4 * T012);
+      e4 = eps * (aa0 * T123 + aa1 * T023 + aa2 * T013 + aa3 * T012);
+    }
+    const uint64_t own = busy ? (1ull << c0) | (1ull << c1) | (1ull << c) | (1ull << p) : 0ull;
+    bool below = false, on = false;
+    for (uint64_t f = rest; f; f &= f - 1) {
+      if (tm.all(!busy || below)) break;
+      const int q = ctz64(f);  // the same point for every lane
+      if (!busy || below || ((own >> q) & 1ull)) continue;
+      const F4 X = ld4(fl + 8 * q);
+      const float x4 = fl[8 * q + 4];
+      const float v = fmaf(n0, X.x, fmaf(n1, X.y, fmaf(n2, X.z, fmaf(n3, X.w, n4 * x4))));
+      const float bound = fmaf(e0, fabsf(X.x), fmaf(e1, fabsf(X.y), fmaf(e2, fabsf(X.z), fmaf(e3, fabsf(X.w), e4 * fabsf(x4)))));
+      const int sg = v > bound ? 1 : (v < -bound ? -1 : side5_exact(view(), c0, c1, c, p, q, sig));
+      if (sg == 0) on = true;
+      else if (sg != sig) below = true;
+    }
+#ifdef BD_COUNT
+    if (cnt && busy) cnt->pairs++;
+#endif
+    if (busy && !below) {
+      if (on) {
+        acc.ties += 1;
+      } else {
+        acc.cells += 1;
+        int s4;
+        const W2 m = quad_minor(view(), c0, c1, c, p, s4);
+        acc.nvol += (u128)m;
+        if (sink.out) record_cell(sink, s, K - 3, c0, c1, c, p);
+      }
+    }
+  }
+
+  BD_HD void bottom5(Acc& acc) {
+    const int sd = u->piv[K - 4] < 0 ? -1 : 1;
+    const uint64_t rest = (N >= 64 ? ~0ull : ((1ull << N) - 1)) & ~u->taken[K - 4];  // the points q to test
+    const int base = s.get(K - 4) + 1, R = N - base;
+    const uint32_t total = c4(R);
+    const int W = tm.lanes(), lane = tm.lane();
+    int qlen = 0;
+    int l = 3;  // the largest index of this lane's quadruple (colex order: never decreases)
+    for (uint32_t t0 = 0; t0 < total; t0 += (uint32_t)W) {
+      const uint32_t t = t0 + (uint32_t)lane;
+      bool live = t < total;
+      uint32_t rec = 0;
+      if (live) {
+        while (c4(l + 1) <= t) ++l;
+        const uint32_t w = colex3(t - c4(l));  // the quadruple a0 < a1 < a2 < a3
+        const int a0 = base + (int)(w & 255u), a1 = base + (int)((w >> 8) & 255u), a2 = base + (int)(w >> 16);
+        const int a3 = base + l;
+        const int s4 = d4_sign(a0, a1, a2, a3);
+        if (s4 == 0) {
+          acc.singular += 1;
+          live = false;
+        } else {
+          rec = (uint32_t)a0 | (uint32_t)a1 << 6 | (uint32_t)a2 << 12 | (uint32_t)a3 << 18 | (s4 < 0 ? 1u << 31 : 0u);
+        }
+      }
+      const uint64_t bal = tm.or_all(live ? 1ull << lane : 0ull);
+      if (live) u->queue[qlen + popc64(bal & ((1ull << lane) - 1ull))] = rec;
+      qlen += popc64(bal);
+      if (qlen >= W) {
+        tm.sync();
+        quads(acc, W, qlen, sd, rest);
+        qlen -= W;
+      }
+    }
+    if (qlen > 0) {
+      tm.sync();
+      quads(acc, qlen, qlen, sd, rest);
+    }
+  }
+
   BD_HD void bottom(Acc& acc) {
-    if (kFiltered && K >= 3) bottom4(acc);
+    if (kFive && K >= 4) bottom5(acc);
+    else if (kFiltered && K >= 3) bottom4(acc);
     else if (kFiltered && K == 2) bottom3(acc);
     else bottom2(acc);
   }

@@ -602,7 +602,7 @@ void lockstep_run(const int64_t* P, int N, int K, const std::vector<Item>& items
   LockstepShared sh(width);
   std::vector<TC> sc((size_t)N * stack_entries(K));
   std::vector<TL> sl((size_t)N * K);
-  std::vector<float> fl((size_t)4 * N);
+  std::vector<float> fl((size_t)8 * N);
   std::vector<Uniform<TC>> uni(1);  // one copy for the team, as in a warp's shared memory
   std::vector<Acc> part(width);
   std::vector<std::thread> th;
@@ -641,7 +641,7 @@ void host_run(const int64_t* P, int N, int K, const std::vector<Item>& items, co
     HostTeam tm;
     std::vector<TC> sc((size_t)N * stack_entries(K));
     std::vector<TL> sl((size_t)N * K);
-    std::vector<float> fl((size_t)4 * N);
+    std::vector<float> fl((size_t)8 * N);
     std::vector<Uniform<TC>> uni(1);
     Walker<TC, TL, HostTeam> W(tm, P, N, K, N, sc.data(), sl.data(), fl.data(), uni.data());
     W.tri = colex_table();

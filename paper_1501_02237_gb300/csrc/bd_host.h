@@ -33,10 +33,15 @@ double hadamard_log2(const int64_t* pts, const int64_t* lifts, int npts, int k, 
 // 2 (int128), -1 (too large).
 int choose_path(double coord_bits, double full_bits);
 
+// Depth of the deepest work item of the walk on integer path `path` (0: int32 coordinate
+// minors, 1: int64, 2: int128): the depth at which its bottom stage starts.  The 5-D stage
+// (int32 coordinate minors, k >= 4) starts at k-3, the 4-D stage (int64, or k = 3) at k-2.
+int item_depth(int k, int path);
+
 // Prefix work list: every (k+1)-subset of {0..npts-1} lies below exactly one item; items are
-// split until each holds at most `max_subsets` subsets (or reaches length max(k-1, 1), the
-// depth of the walker's bottom stage), then sorted by decreasing size.
-std::vector<Item> build_items(int npts, int k, uint64_t max_subsets);
+// split until each holds at most `max_subsets` subsets (or reaches length `depth`), then
+// sorted by decreasing size.
+std::vector<Item> build_items(int npts, int k, uint64_t max_subsets, int depth);
 
 // The work-item split threshold for a launch of `teams` warps over `total` subsets: fine enough
 // for the packing of ranges (1/32 of a warp's share), between 64 and 2^20 subsets.
@@ -46,12 +51,12 @@ uint64_t default_item_subsets(uint64_t total, uint64_t teams);
 // teams: runs packed up to 1/8 of a team's share of the estimated work (the bottom stage's
 // warp rounds and level steps, not subsets, which misjudge regions of small nodes), taken
 // largest first.  A team builds the prefixes its range's items share once.
-void build_ranges(int npts, int k, uint64_t max_subsets, uint64_t teams, std::vector<Item>& items,
+void build_ranges(int npts, int k, uint64_t max_subsets, uint64_t teams, int depth, std::vector<Item>& items,
                   std::vector<Range>& ranges);
 
 // The same list written into a caller-owned array of `cap` items (no allocation); false when
 // it does not fit.
-bool build_items_into(int npts, int k, uint64_t max_subsets, Item* out, size_t cap, size_t* count);
+bool build_items_into(int npts, int k, uint64_t max_subsets, int depth, Item* out, size_t cap, size_t* count);
 
 // Host emulation of the warp enumeration on `threads` CPU threads (one single-lane team
 // each), for an integer path; team_width > 1 instead runs one team of that many lanes as

@@ -65,18 +65,18 @@ __host__ __device__ inline int slots_of(int N) { return (N + 3) & ~3; }
 #endif
 #define BD_ENUM_BOUNDS __launch_bounds__(256, BD_LB_BLOCKS)
 
-// one warp's shared memory: its coordinate-minor stack, lift-minor stack, four float rows for
-// the single-precision filters and the walker's team-shared pivots and dividers, each 16-byte
-// aligned
+// one warp's shared memory: its coordinate-minor stack, lift-minor stack, eight floats per
+// point for the single-precision filters and the walker's team-shared state (pivots, dividers,
+// prefix sets, the 5-D queue), each 16-byte aligned
 template <class TC, class TL>
 __host__ __device__ inline size_t warp_bytes(int slots, int K) {
   return align16((size_t)slots * stack_entries(K) * sizeof(TC)) + align16((size_t)slots * K * sizeof(TL)) +
-         align16((size_t)4 * slots * sizeof(float)) + kUniformBytes;
+         align16((size_t)8 * slots * sizeof(float)) + kUniformBytes;
 }
 
 // the uniform-state area of a warp region laid out as in warp_bytes, given its float rows
 __device__ inline void* uniform_after(float* fl, int slots) {
-  return reinterpret_cast<unsigned char*>(fl) + align16((size_t)4 * slots * sizeof(float));
+  return reinterpret_cast<unsigned char*>(fl) + align16((size_t)8 * slots * sizeof(float));
 }
 
 template <class TC, class TL>

@@ -98,7 +98,7 @@ extern "C" int bd_volume_noalloc(const int64_t* points, int32_t npts, int32_t k,
   const uint64_t total = bd::binom(npts, k + 1);
   uint64_t thr = std::max<uint64_t>(256, total / ((uint64_t)shape.blocks * shape.warps * 4 + 1));
   size_t nitems = 0;
-  while (!bd::build_items_into(npts, k, thr, g_host_items, kItemsMax, &nitems)) thr *= 4;
+  while (!bd::build_items_into(npts, k, thr, bd::item_depth(k, path), g_host_items, kItemsMax, &nitems)) thr *= 4;
 
   cudaStream_t st = bd::thread_stream();
   bd::DevAcc* d_acc = reinterpret_cast<bd::DevAcc*>(base);

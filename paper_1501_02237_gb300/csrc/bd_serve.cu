@@ -180,7 +180,7 @@ void build_request_items(bd_server* s, Req* r) {
   const uint64_t want = std::max<uint64_t>(1, warps / 2);  // enough items to spread one system over the GPU
   uint64_t thr = std::max<uint64_t>(s->opts.item_subsets > 0 ? (uint64_t)s->opts.item_subsets : 256, sub / want);
   r->items.clear();
-  for (const bd::Item& it : bd::build_items(r->N, r->K, thr)) {
+  for (const bd::Item& it : bd::build_items(r->N, r->K, thr, bd::item_depth(r->K, r->path))) {
     bd::BatchItem x{};
     x.len = it.len;
     for (int t = 0; t < it.len && t < 11; ++t) x.idx[t] = it.idx[t];

@@ -11,15 +11,14 @@ namespace {
 
 // every prefix of the split tree, depth first; emit(item) returns false to stop early
 template <class Emit>
-bool for_each_item(int N, int K, uint64_t max_subsets, Emit emit) {
+bool for_each_item(int N, int K, uint64_t max_subsets, int depth, Emit emit) {
   if (K < 1 || N < K + 1) return true;
   int pre[KMAX + 1];
   int len = 1;
   pre[0] = 0;
   for (;;) {
     const uint64_t T = subtree_size(N, K, pre[len - 1], len);
-    if (T > max_subsets && len < std::max(K - 2, 1)) {  // split; items stop at depth max(K-2, 1), where the
-                                                         // shallowest bottom stage (the 4-D test) starts
+    if (T > max_subsets && len < depth) {  // split; items stop where the bottom stage starts
       pre[len] = pre[len - 1] + 1;
       ++len;
       continue;
@@ -54,9 +53,11 @@ struct ItemOrder {
 
 }  // namespace
 
-std::vector<Item> build_items(int N, int K, uint64_t max_subsets) {
+int item_depth(int K, int path) { return K >= 4 && path == 0 ? K - 3 : std::max(K - 2, 1); }
+
+std::vector<Item> build_items(int N, int K, uint64_t max_subsets, int depth) {
   std::vector<Item> items;
-  for_each_item(N, K, max_subsets, [&](const Item& x) {
+  for_each_item(N, K, max_subsets, depth, [&](const Item& x) {
     items.push_back(x);
     return true;
   });
@@ -65,19 +66,22 @@ std::vector<Item> build_items(int N, int K, uint64_t max_subsets) {
 }
 
 // estimated work of an item, in warp rounds of the bottom stage plus one per level step
-static uint64_t item_cost(int N, int K, const Item& it) {
+static uint64_t item_cost(int N, int K, int D, const Item& it) {
   const int L = it.len, a = it.idx[L - 1];
   if (K < 3) return subtree_size(N, K, a, L);
-  // the 4-D bottom stage: one Bareiss step and ceil(C(R,3)/32) warp rounds per level-(K-3)
-  // node with R points after its last index; nodes with last index v below this prefix:
-  // C(v-a-1, K-3-L) (none deeper than K-2 exists when L = K-2)
+  // the bottom stage runs on nodes of depth D with R points after their last index: the 5-D
+  // test (D = K-3) takes one Bareiss step, ceil(C(R,4)/32) warp rounds and about one round of
+  // queued quadruples, the 4-D test (D = K-2) one step and ceil(C(R,3)/32) rounds; nodes with
+  // last index v below this prefix: C(v-a-1, D-1-L) (none deeper when L = D)
+  const bool five = D == K - 3;
+  const int m = five ? 4 : 3;
   auto node = [&](int v) {
-    const uint64_t t = binom(N - 1 - v, 3);
-    return 1 + (t + 31) / 32;
+    const uint64_t t = binom(N - 1 - v, m);
+    return (uint64_t)(five ? 2 : 1) + (t + 31) / 32;
   };
-  if (L >= K - 2) return node(a);
+  if (L >= D) return node(a);
   uint64_t c = 0;
-  for (int v = a + (K - 2 - L); v <= N - 4; ++v) c += binom(v - a - 1, K - 3 - L) * node(v);
+  for (int v = a + (D - L); v <= N - 1 - m; ++v) c += binom(v - a - 1, D - 1 - L) * node(v);
   return c;
 }
 
@@ -86,15 +90,15 @@ uint64_t default_item_subsets(uint64_t total, uint64_t teams) {
   return std::min<uint64_t>(std::max<uint64_t>(t, 64), (uint64_t)1 << 20);
 }
 
-void build_ranges(int N, int K, uint64_t max_subsets, uint64_t teams, std::vector<Item>& items,
+void build_ranges(int N, int K, uint64_t max_subsets, uint64_t teams, int depth, std::vector<Item>& items,
                   std::vector<Range>& ranges) {
   items.clear();
   ranges.clear();
   std::vector<uint64_t> cost;
   uint64_t remaining = 0;
-  for_each_item(N, K, max_subsets, [&](const Item& x) {
+  for_each_item(N, K, max_subsets, depth, [&](const Item& x) {
     items.push_back(x);
-    cost.push_back(std::max<uint64_t>(1, item_cost(N, K, x)));
+    cost.push_back(std::max<uint64_t>(1, item_cost(N, K, depth, x)));
     remaining += cost.back();
     return true;
   });
@@ -118,9 +122,9 @@ void build_ranges(int N, int K, uint64_t max_subsets, uint64_t teams, std::vecto
   ranges.swap(sorted);
 }
 
-bool build_items_into(int N, int K, uint64_t max_subsets, Item* out, size_t cap, size_t* count) {
+bool build_items_into(int N, int K, uint64_t max_subsets, int depth, Item* out, size_t cap, size_t* count) {
   size_t n = 0;
-  const bool ok = for_each_item(N, K, max_subsets, [&](const Item& x) {
+  const bool ok = for_each_item(N, K, max_subsets, depth, [&](const Item& x) {
     if (n == cap) return false;
     out[n++] = x;
     return true;

@@ -259,3 +259,65 @@ def test_lockstep_team_narrower_than_the_point_set(seed, width):
         r = bd.host_volume_lifted(np.array(pts), np.array(lf), force_int128=force, team_width=width)
         assert r["status"] == 0
         assert r["nvol"] == ref, (n, force)
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_host_walker_5d_exact_routes(seed):
+    # degenerate point sets (coordinates 0 and +-63 in dimensions 4 and 5): the 5-D stage's
+    # coordinate det4 has terms near 2^24 and sums that round, so singular quadruples land inside
+    # the error bound and take the exact route; deepest items and default items, both against
+    # the oracle's volume
+    rng = random.Random(7700 + seed)
+    k = 4 + seed % 2
+    n = rng.randint(k + 4, 12)
+    pts = [tuple(63 * rng.choice([-1, 0, 0, 1]) for _ in range(k)) for _ in range(n)]
+    pts = list(dict.fromkeys(pts))  # distinct points
+    if len(pts) < k + 1:
+        pytest.skip("degenerate draw")
+    ref = nvol_placing(pts)
+    lf = oracle_lifts(len(pts), seed)
+    for items in (1, 0):
+        r = bd.host_volume_lifted(np.array(pts), np.array(lf), item_subsets=items)
+        assert r["status"] == 0
+        assert r["nvol"] == ref, (k, len(pts), items)
+        assert not r["flags"] & bd.BD_FLAG_INT128
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_host_walker_5d_exact_sides(seed):
+    # lifts nearly affine in the coordinates (10^6 times their sum plus a small perturbation) put
+    # every point close to every cell's hyperplane at a large scale: the 5-D stage's single-
+    # precision side test cannot decide and takes the exact route; an affine part does not change
+    # the triangulation, so the volume is the oracle's whatever the perturbation (redrawn when it
+    # happens to give a tie)
+    rng = random.Random(8800 + seed)
+    k = 4 + seed % 2
+    n = rng.randint(k + 4, 11)
+    pts = list(dict.fromkeys(tuple(31 * rng.choice([-1, 0, 1]) for _ in range(k)) for _ in range(n)))
+    if len(pts) < k + 1:
+        pytest.skip("degenerate draw")
+    ref = nvol_placing(pts)
+    for _ in range(8):
+        lf = [10**6 * sum(p) + rng.randint(-20, 20) for p in pts]
+        r = bd.host_volume_lifted(np.array(pts), np.array(lf))
+        if r["status"] == 0:
+            break
+    assert r["status"] == 0
+    assert r["nvol"] == ref
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_host_walker_64_bit_coordinates_high_dimension(seed):
+    # coordinates up to 64 (k = 4) and 40 (k = 5): coordinate minors past 31 bits and lifted
+    # minors below 63, so the walk takes the int64 path and its 4-D stage (the 5-D stage runs on
+    # 32-bit coordinate minors)
+    rng = random.Random(9100 + seed)
+    k = 4 + seed % 2
+    span = 64 if k == 4 else 40
+    pts = [tuple(rng.randint(-span, span) for _ in range(k)) for _ in range(rng.randint(k + 3, 10))]
+    lf = oracle_lifts(len(pts), seed)
+    for items in (1, 0):
+        r = bd.host_volume_lifted(np.array(pts), np.array(lf), item_subsets=items)
+        assert r["status"] == 0
+        assert r["nvol"] == nvol_placing(pts), (k, items)
+        assert r["bound_bits"] > 31 and not r["flags"] & bd.BD_FLAG_INT128
