@@ -147,7 +147,12 @@ typedef struct {
   int32_t blocks_per_sm;    /* 0: occupancy calculator */
   int64_t item_subsets;     /* split prefixes until each holds at most this many subsets; 0: auto */
   int32_t force_int128;     /* 1: use the 128-bit path even when 64 bits suffice */
-  int32_t reserved[3];
+  int32_t bottom_stage;     /* the walk's last levels on the 32-bit coordinate path (k >= 4):
+                               5 = the 5-D test (a det4 per quadruple after the Bareiss level
+                               k-4), 4 = the 4-D test (a det3 per triple after level k-3),
+                               0 = chosen from the point set (see bd_prefer_five); other paths
+                               and k < 4 ignore it; any other value: BD_ERR_ARG */
+  int32_t reserved[2];
 } bd_plan_opts;
 
 /* Copies the points to device memory and builds the work list.  opts may be NULL. */
@@ -171,7 +176,8 @@ int bd_plan_read(bd_plan* plan, bd_volume_out* out);
 int bd_plan_volume(bd_plan* plan, uint64_t seed, bd_volume_out* out);
 /* Number of work items, kernel launch geometry and integer path: {items, blocks, warps_per_block,
  * shared_bytes_per_block, path (0: int32 coordinate / int64 lift minors, 1: int64, 2: int128),
- * slots_per_warp, ranges (work units: runs of consecutive items a warp takes at once), 0}. */
+ * slots_per_warp, ranges (work units: runs of consecutive items a warp takes at once), bottom
+ * stage (the dimension of the walk's last test: 5, 4, 3 or 2)}. */
 int bd_plan_info(const bd_plan* plan, int64_t* info);
 int bd_plan_destroy(bd_plan* plan);
 
@@ -200,7 +206,7 @@ typedef struct {
   int32_t item_factor;     /* work items per resident warp; 0: 4 (or the autotuned value) */
   int32_t use_graph;       /* 1: capture the batched launches in a CUDA graph and replay it */
   int32_t autotune;        /* 1: choose warps_per_block and item_factor by timing candidates */
-  int32_t reserved0;
+  int32_t bottom_stage;    /* as in bd_plan_opts, per system (0: chosen from its points); mode 0 */
   const float* cost;       /* NULL or one predicted cost per system (any positive unit) */
   int32_t reserved[4];
 } bd_batch_opts;
@@ -381,7 +387,7 @@ typedef struct bd_host_opts {
   int32_t team_width;    /* > 1: one team of this many lanes, run as threads in lockstep */
   int32_t shard;         /* with shards > 1: only the work ranges u with u % shards == shard */
   int32_t shards;        /* <= 1: the whole enumeration */
-  int32_t reserved;      /* 0 */
+  int32_t bottom_stage;  /* as in bd_plan_opts (0: chosen from the point set) */
 } bd_host_opts;
 
 /* Runs the same lower-facet enumeration as the GPU kernel on CPU threads, with the given

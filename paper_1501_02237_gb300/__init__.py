@@ -208,15 +208,16 @@ def classify(points, lifts, subsets) -> tuple:
 
 
 def host_volume_lifted(points, lifts, threads: int = 1, force_int128: bool = False, item_subsets: int = 0,
-                       team_width: int = 1, shard: int = 0, shards: int = 1) -> dict:
+                       team_width: int = 1, shard: int = 0, shards: int = 1, bottom_stage: int = 0) -> dict:
     """bd_host_volume_lifted: CPU emulation of the enumeration (CPU tests and the native baseline).
     force_int128 runs the 128-bit walker; item_subsets is the work-item split threshold (0: the
     library's default); team_width > 1 runs one team of that many lanes as threads in lockstep;
-    shards > 1 runs only shard `shard` of the work list (partial sums)."""
+    shards > 1 runs only shard `shard` of the work list (partial sums); bottom_stage 4 or 5 fixes
+    the walk's last stage on the 32-bit coordinate path (0: chosen from the point set)."""
     P, W = i64(points), i64(lifts)
     npts, k = P.shape
     out = VolumeOut()
-    opts = HostOpts(threads, int(force_int128), item_subsets, team_width, shard, shards, 0)
+    opts = HostOpts(threads, int(force_int128), item_subsets, team_width, shard, shards, bottom_stage)
     rc = lib().bd_host_volume_lifted(ptr(P), ptr(W), npts, k, C.byref(opts), C.byref(out))
     res = out.as_dict()
     res["status"] = rc
@@ -333,10 +334,10 @@ class Plan:
     """bd_plan_*: device-resident enumeration of one point set."""
 
     def __init__(self, points, warps_per_block: int = 0, blocks_per_sm: int = 0, item_subsets: int = 0,
-                 force_int128: bool = False):
+                 force_int128: bool = False, bottom_stage: int = 0):
         P = i64(points)
         self.npts, self.k = P.shape
-        opts = PlanOpts(warps_per_block, blocks_per_sm, item_subsets, int(force_int128))
+        opts = PlanOpts(warps_per_block, blocks_per_sm, item_subsets, int(force_int128), bottom_stage)
         h = C.c_void_p()
         check(lib().bd_plan_create(ptr(P), self.npts, self.k, C.byref(opts), C.byref(h)))
         self.handle = h
@@ -362,7 +363,8 @@ class Plan:
         a = np.zeros(8, dtype=np.int64)
         check(lib().bd_plan_info(self.handle, ptr(a)))
         return dict(items=int(a[0]), blocks=int(a[1]), warps_per_block=int(a[2]), smem=int(a[3]),
-                    path=("int32/int64", "int64", "int128")[int(a[4])], int128=int(a[4]) == 2, slots=int(a[5]), ranges=int(a[6]))
+                    path=("int32/int64", "int64", "int128")[int(a[4])], int128=int(a[4]) == 2, slots=int(a[5]), ranges=int(a[6]),
+                    bottom_stage=int(a[7]))
 
     def close(self) -> None:
         if getattr(self, "handle", None):
@@ -412,9 +414,9 @@ class Batch:
         return f
 
     def run(self, mode: int = 0, warps_per_block: int = 0, item_factor: int = 0, use_graph: bool = False,
-            autotune: bool = False, cost=None) -> dict:
+            autotune: bool = False, cost=None, bottom_stage: int = 0) -> dict:
         self._cost = None if cost is None else np.ascontiguousarray(np.asarray(cost, dtype=np.float32))
-        o = BatchOpts(mode, warps_per_block, item_factor, int(use_graph), int(autotune), 0,
+        o = BatchOpts(mode, warps_per_block, item_factor, int(use_graph), int(autotune), bottom_stage,
                       self._cost.ctypes.data_as(F32P) if self._cost is not None else None)
         st = BatchStats()
         check(lib().bd_batch_run(self.handle, C.byref(o), C.byref(st)))

@@ -68,17 +68,17 @@ class DegreeOut(C.Structure):
 
 class PlanOpts(C.Structure):
     _fields_ = [("warps_per_block", C.c_int32), ("blocks_per_sm", C.c_int32), ("item_subsets", C.c_int64),
-                ("force_int128", C.c_int32), ("reserved", C.c_int32 * 3)]
+                ("force_int128", C.c_int32), ("bottom_stage", C.c_int32), ("reserved", C.c_int32 * 2)]
 
 
 class HostOpts(C.Structure):
     _fields_ = [("threads", C.c_int32), ("force_int128", C.c_int32), ("item_subsets", C.c_uint64),
-                ("team_width", C.c_int32), ("shard", C.c_int32), ("shards", C.c_int32), ("reserved", C.c_int32)]
+                ("team_width", C.c_int32), ("shard", C.c_int32), ("shards", C.c_int32), ("bottom_stage", C.c_int32)]
 
 
 class BatchOpts(C.Structure):
     _fields_ = [("mode", C.c_int32), ("warps_per_block", C.c_int32), ("item_factor", C.c_int32),
-                ("use_graph", C.c_int32), ("autotune", C.c_int32), ("reserved0", C.c_int32),
+                ("use_graph", C.c_int32), ("autotune", C.c_int32), ("bottom_stage", C.c_int32),
                 ("cost", C.POINTER(C.c_float)), ("reserved", C.c_int32 * 4)]
 
 

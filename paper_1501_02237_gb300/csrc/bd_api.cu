@@ -194,6 +194,7 @@ int cuda_error(cudaError_t e, const char* where) {
 struct bd_plan {
   int N = 0, K = 0;
   int path = 0;  // bd::PATH_NARROW / MID / WIDE
+  bool five = false;  // the walk's bottom stage is the 5-D test (32-bit coordinate path, k >= 4)
   double bound = 0;
   int64_t max_abs = 0;
   bool explicit_lifts = false;
@@ -292,7 +293,10 @@ int plan_prepare(bd_plan* p, const int64_t* points, const int64_t* lifts, int32_
   const uint64_t total = bd::binom(npts, k + 1);
   const uint64_t warps = (uint64_t)p->shape.blocks * p->shape.warps;
   const int64_t thr = opts && opts->item_subsets > 0 ? opts->item_subsets : (int64_t)bd::default_item_subsets(total, warps);
-  rc = get_items(npts, k, thr, (int64_t)warps, bd::item_depth(k, p->path), p->items);
+  const int stage = opts ? opts->bottom_stage : 0;
+  if (stage != 0 && stage != 4 && stage != 5) return fail(BD_ERR_ARG, "bottom_stage must be 0, 4 or 5");
+  p->five = p->path == bd::PATH_NARROW && k >= 4 && (stage == 5 || (stage == 0 && bd::prefer_five(points, npts, k, warps)));
+  rc = get_items(npts, k, thr, (int64_t)warps, bd::item_depth(k, p->path, p->five), p->items);
   if (rc) return rc;
   rc = get_tri(p->tri);
   if (rc) return rc;
@@ -359,6 +363,7 @@ int plan_launch(bd_plan* p, uint64_t seed, int attempt, cudaStream_t st, int sha
   for (size_t u = (size_t)shard; u < p->items->ranges.size(); u += (size_t)shards) expected += p->items->ranges[u].count;
   ep.N = p->N;
   ep.K = p->K;
+  ep.five = p->five ? 1 : 0;
   ep.acc = reinterpret_cast<bd::DevAcc*>(p->d_state);
   ep.counter = reinterpret_cast<unsigned int*>(p->d_state + sizeof(bd::DevAcc));
   BD_CUDA(bd::launch_enumerate(ep, p->shape, p->path, st));
@@ -464,7 +469,8 @@ int bd_plan_info(const bd_plan* plan, int64_t* info) {
   info[4] = plan->path;
   info[5] = plan->shape.slots;
   info[6] = (int64_t)plan->items->ranges.size();
-  info[7] = 0;
+  // the walker's bottom test: 5-D, 4-D (filtered paths, k >= 3), 3-D (k = 2), else 2-D
+  info[7] = plan->five ? 5 : plan->path != bd::PATH_WIDE && plan->K >= 3 ? 4 : plan->path != bd::PATH_WIDE && plan->K == 2 ? 3 : 2;
   return BD_OK;
 }
 
@@ -681,6 +687,10 @@ int bd_host_volume_lifted(const int64_t* points, const int64_t* lifts, int32_t n
   int path = bd::choose_path(coord_bits, bound);
   if (path < 0) return fail(BD_ERR_OVERFLOW, "Hadamard bound exceeds 2^127");
   if (o.force_int128) path = bd::PATH_WIDE;
+  if (o.bottom_stage != 0 && o.bottom_stage != 4 && o.bottom_stage != 5)
+    return fail(BD_ERR_ARG, "bottom_stage must be 0, 4 or 5");
+  const bool five = path == bd::PATH_NARROW && k >= 4 &&
+                    (o.bottom_stage == 5 || (o.bottom_stage == 0 && bd::prefer_five(points, npts, k, 0)));
   std::vector<int64_t> P((size_t)(k + 1) * npts);
   for (int q = 0; q < npts; ++q) {
     for (int c = 0; c < k; ++c) P[(size_t)c * npts + q] = points[(size_t)q * k + c];
@@ -690,14 +700,14 @@ int bd_host_volume_lifted(const int64_t* points, const int64_t* lifts, int32_t n
   // guided ranges, so that range boundaries and prefix reuse are exercised on one thread too)
   std::vector<bd::Item> items;
   std::vector<bd::Range> ranges;
-  bd::build_ranges(npts, k, o.item_subsets ? o.item_subsets : 4096, 8, bd::item_depth(k, path), items, ranges);
+  bd::build_ranges(npts, k, o.item_subsets ? o.item_subsets : 4096, 8, bd::item_depth(k, path, five), items, ranges);
   if (shards > 1) {  // this shard's ranges only (u % shards == shard, as on the device)
     std::vector<bd::Range> mine;
     for (size_t u = (size_t)o.shard; u < ranges.size(); u += (size_t)shards) mine.push_back(ranges[u]);
     ranges.swap(mine);
   }
   bd::Acc acc{};
-  bd::host_enumerate(path, P.data(), npts, k, items, std::max(1, o.threads), acc, o.team_width, &ranges);
+  bd::host_enumerate(path, five, P.data(), npts, k, items, std::max(1, o.threads), acc, o.team_width, &ranges);
   std::memset(out, 0, sizeof(*out));
   set_u128(out->nvol_lo, out->nvol_hi, acc.nvol);
   out->cells = acc.cells;
@@ -836,13 +846,14 @@ int bd_host_cells(const int64_t* points, const int64_t* lifts, int32_t npts, int
   }
   std::vector<bd::Item> items;
   std::vector<bd::Range> ranges;
-  bd::build_ranges(npts, k, 4096, 8, bd::item_depth(k, path), items, ranges);
+  const bool five = path == bd::PATH_NARROW && k >= 4 && bd::prefer_five(points, npts, k, 0);
+  bd::build_ranges(npts, k, 4096, 8, bd::item_depth(k, path, five), items, ranges);
   const size_t cap = (size_t)std::max<int64_t>(capacity, 1);
   std::vector<uint8_t> rec(16 * cap);
   unsigned long long n = 0;
   const bd::CellSink sink{rec.data(), &n, (unsigned long long)capacity};
   bd::Acc acc{};
-  bd::host_enumerate(path, P.data(), npts, k, items, 1, acc, 1, &ranges, &sink);
+  bd::host_enumerate(path, five, P.data(), npts, k, items, 1, acc, 1, &ranges, &sink);
   *count = (int64_t)n;
   if (acc.ties) return fail(BD_ERR_TIES, "the given lifting has ties");
   if (n > (unsigned long long)capacity) return fail(BD_ERR_ARG, "capacity is below the number of cells (count holds it)");

@@ -38,6 +38,8 @@ struct BatchSys {
   int status = BD_OK;
   std::string err;
   int rank = 0, dim = 0, N = 0, K = 0, path = 0;
+  bool prefer5 = false;  // the 5-D bottom stage is expected to be faster (prefer_five)
+  bool five = false;     // this run's bottom stage is the 5-D test
   uint64_t torsion = 1;
   bool consistent = true;
   double bound = 0, coord_bits = 0;
@@ -186,6 +188,7 @@ void reduce_one(BatchSys& s) {
   }
   s.bound = bd::hadamard_log2(s.pts.data(), nullptr, s.N, s.K, (1 << 20) - 1, &s.coord_bits);
   s.path = bd::choose_path(s.coord_bits, s.bound);
+  s.prefer5 = s.path == bd::PATH_NARROW && s.K >= 4 && bd::prefer_five(s.pts.data(), s.N, s.K, 0);
   if (s.path < 0) {
     s.status = BD_ERR_OVERFLOW;
     s.err = "Hadamard bound of the lifted minors exceeds 2^127";
@@ -232,7 +235,7 @@ void build_batch_items(bd_batch* b, const std::vector<int>& active, const float*
       const double c = cost ? std::max(1e-9, (double)cost[i]) : closed_form_cost(s);
       const double per_subset = c / std::max(1.0, sub);
       uint64_t thr = (uint64_t)std::max(64.0, std::min(4e9, target / per_subset));
-      for (const bd::Item& it : bd::build_items(s.N, s.K, thr, bd::item_depth(s.K, s.path))) {
+      for (const bd::Item& it : bd::build_items(s.N, s.K, thr, bd::item_depth(s.K, s.path, s.five))) {
         bd::BatchItem x{};
         x.sys = (uint32_t)i;
         x.len = it.len;
@@ -275,6 +278,7 @@ int run_batched(bd_batch* b, const std::vector<int>& active, const float* cost, 
     desc[i].K = s.K;
     desc[i].pts_off = (int)pts.size();
     desc[i].path = s.path;
+    desc[i].five = s.five ? 1 : 0;
     desc[i].lift_seed = bd::lift_stream_seed(s.seed, (uint32_t)s.attempt);
     pts.insert(pts.end(), s.pts.begin(), s.pts.begin() + (size_t)s.N * s.K);
   }
@@ -555,6 +559,10 @@ int bd_batch_run(bd_batch* b, const bd_batch_opts* opts, bd_batch_stats* stats) 
     s.done = !s.consistent || s.K == 0;
     if (!s.done) active.push_back((int)i);
   }
+  if (o.bottom_stage != 0 && o.bottom_stage != 4 && o.bottom_stage != 5)
+    return bd::set_error(BD_ERR_ARG, "bottom_stage must be 0, 4 or 5");
+  for (BatchSys& s : b->sys)
+    s.five = s.path == bd::PATH_NARROW && s.K >= 4 && (o.bottom_stage == 5 || (o.bottom_stage == 0 && s.prefer5));
   const double w0 = now_ms();
   if (o.mode == 1) {  // the plain form: one synchronous bd_volume per system
     for (int i : active) {

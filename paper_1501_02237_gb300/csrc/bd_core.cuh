@@ -800,7 +800,8 @@ struct Walker {
   // 64-bit numbers its exact routes, in 128-bit arithmetic, cost more than the step it saves.
   static constexpr bool kFiltered = sizeof(TL) == 8;
   static constexpr bool kFive = kFiltered && sizeof(TC) == 4;
-  BD_HD bool five() const { return kFive && K >= 4; }
+  bool use5 = true;  // the 5-D stage where it applies (else the 4-D test); the work list must agree
+  BD_HD bool five() const { return kFive && use5 && K >= 4; }
   // DFS depth at which the bottom stage takes over (the chosen prefix is s_0 .. s_{depth-1}):
   // the 5-D test finishes the last four levels, the 4-D test three, the 3-D and 2-D tests two
   BD_HD int bottom_depth() const {
@@ -1259,6 +1260,7 @@ struct Walker {
   // ---------------------------------------------------------------------------------------
 
   static BD_HD uint32_t c4(int n) { return n < 4 ? 0u : (uint32_t)(n * (n - 1) * (n - 2) * (n - 3) / 24); }
+  static BD_HD uint32_t c3(int n) { return n < 3 ? 0u : (uint32_t)(n * (n - 1) * (n - 2) / 6); }
 
   // colex triple of rank t (i < j < k) packed i | j << 8 | k << 16, from the decode table when
   // present
@@ -1428,39 +1430,85 @@ struct Walker {
     }
   }
 
+  // The quadruples of the node on state K-4 whose first point is `first` (a work item one level
+  // below the node: a large node's quadruples are split this way over several warps).  The
+  // triples (a1, a2, a3) after `first` are dealt in colex order, as in bottom4.
+  BD_HD void bottom5_first(Acc& acc, int first) {
+    const int sd = u->piv[K - 4] < 0 ? -1 : 1;
+    const uint64_t rest = (N >= 64 ? ~0ull : ((1ull << N) - 1)) & ~u->taken[K - 4];
+    const int base = first + 1, R = N - base;
+    const uint32_t total = c3(R);
+    const int W = tm.lanes(), lane = tm.lane();
+    int qlen = 0;
+    for (uint32_t t0 = 0; t0 < total; t0 += (uint32_t)W) {
+      const uint32_t t = t0 + (uint32_t)lane;
+      bool live = t < total;
+      uint32_t rec = 0;
+      if (live) {
+        const uint32_t w = colex3(t);
+        const int a1 = base + (int)(w & 255u), a2 = base + (int)((w >> 8) & 255u), a3 = base + (int)(w >> 16);
+        const int s4 = d4_sign(first, a1, a2, a3);
+        if (s4 == 0) {
+          acc.singular += 1;
+          live = false;
+        } else {
+          rec = (uint32_t)first | (uint32_t)a1 << 6 | (uint32_t)a2 << 12 | (uint32_t)a3 << 18 | (s4 < 0 ? 1u << 31 : 0u);
+        }
+      }
+      const uint64_t bal = tm.or_all(live ? 1ull << lane : 0ull);
+      if (live) u->queue[qlen + popc64(bal & ((1ull << lane) - 1ull))] = rec;
+      qlen += popc64(bal);
+      if (qlen >= W) {
+        tm.sync();
+        quads(acc, W, qlen, sd, rest);
+        qlen -= W;
+      }
+    }
+    if (qlen > 0) {
+      tm.sync();
+      quads(acc, qlen, qlen, sd, rest);
+    }
+  }
+
   BD_HD void bottom(Acc& acc) {
-    if (kFive && K >= 4) bottom5(acc);
+    if (five()) bottom5(acc);
     else if (kFiltered && K >= 3) bottom4(acc);
     else if (kFiltered && K == 2) bottom3(acc);
     else bottom2(acc);
   }
 
-  // every (K+1)-subset extending the prefix it.idx[0 .. it.len-1] (len <= bottom depth).  The
-  // states of a prefix shared with the previous item are still in place and are not rebuilt
-  // (the depth-first walk below an item only rewrites levels >= its length).
+  // every (K+1)-subset extending the prefix it.idx[0 .. it.len-1] (len <= bottom depth, or
+  // bottom depth + 1 for the 5-D stage: then the last index is the first point of the
+  // quadruples taken).  The states of a prefix shared with the previous item are still in place
+  // and are not rebuilt (the depth-first walk below an item only rewrites levels >= its length).
   BD_HD void run_item(const Item& it, Acc& acc) { run_item(pack_item(it), acc); }
 
   BD_HD void run_item(const PackedItem& it, Acc& acc) {
     const Idx15 pre{it.lo, it.hi & kIdxHiMask};
     const int L = packed_len(it);
     const int B = bottom_depth();
+    const int LB = L < B ? L : B;  // the levels built from the prefix
     const bool lead = tm.lane() == 0;  // uniform counts are added once per team
     const int last = pre.get(L - 1);
     // the first level whose index differs from the built prefix (six-bit fields compared at once)
     int m = first_difference(s, pre);
     m = m < valid ? m : valid;
-    m = m < L ? m : L;
+    m = m < LB ? m : LB;
     if (m == 0) {
       start(pre.get(0));
       m = 1;
     }
     valid = m;
-    for (int j = m; j < L; ++j) {
+    for (int j = m; j < LB; ++j) {
       if (!build(j, pre.get(j))) {
         if (lead) acc.singular += subtree_size(N, K, last, L);
         return;
       }
       valid = j + 1;
+    }
+    if (kFive && L > B) {  // a 5-D item below its node (the work list goes that deep only there)
+      bottom5_first(acc, last);
+      return;
     }
     Idx15 cur;  // cur[j]: the last index tried at level j
     int j = L;

@@ -597,8 +597,8 @@ const uint32_t* colex_table() {
 }
 
 template <class TC, class TL>
-void lockstep_run(const int64_t* P, int N, int K, const std::vector<Item>& items, const std::vector<Range>* ranges,
-                  int width, Acc& acc, const CellSink* sink) {
+void lockstep_run(bool five, const int64_t* P, int N, int K, const std::vector<Item>& items,
+                  const std::vector<Range>* ranges, int width, Acc& acc, const CellSink* sink) {
   LockstepShared sh(width);
   std::vector<TC> sc((size_t)N * stack_entries(K));
   std::vector<TL> sl((size_t)N * K);
@@ -611,6 +611,7 @@ void lockstep_run(const int64_t* P, int N, int K, const std::vector<Item>& items
       LockstepTeam tm{&sh, l};
       Walker<TC, TL, LockstepTeam> W(tm, P, N, K, N, sc.data(), sl.data(), fl.data(), uni.data());
       W.tri = colex_table();
+      W.use5 = five;
       if (sink) W.sink = *sink;
       Acc a{};
       if (ranges) {
@@ -632,8 +633,8 @@ void lockstep_run(const int64_t* P, int N, int K, const std::vector<Item>& items
 }
 
 template <class TC, class TL>
-void host_run(const int64_t* P, int N, int K, const std::vector<Item>& items, const std::vector<Range>* ranges,
-              int threads, Acc& acc, const CellSink* sink) {
+void host_run(bool five, const int64_t* P, int N, int K, const std::vector<Item>& items,
+              const std::vector<Range>* ranges, int threads, Acc& acc, const CellSink* sink) {
   std::atomic<size_t> next(0);
   std::vector<Acc> part(std::max(1, threads));
   const size_t units = ranges ? ranges->size() : items.size();
@@ -645,6 +646,7 @@ void host_run(const int64_t* P, int N, int K, const std::vector<Item>& items, co
     std::vector<Uniform<TC>> uni(1);
     Walker<TC, TL, HostTeam> W(tm, P, N, K, N, sc.data(), sl.data(), fl.data(), uni.data());
     W.tri = colex_table();
+    W.use5 = five;
     if (sink) W.sink = *sink;
     Acc a{};
     for (;;) {
@@ -671,17 +673,17 @@ void host_run(const int64_t* P, int N, int K, const std::vector<Item>& items, co
   }
 }
 
-void host_enumerate(int path, const int64_t* P, int N, int K, const std::vector<Item>& items, int threads, Acc& acc,
+void host_enumerate(int path, bool five, const int64_t* P, int N, int K, const std::vector<Item>& items, int threads, Acc& acc,
                     int team_width, const std::vector<Range>* ranges, const CellSink* sink) {
   if (team_width > 1) {  // one team walks every range in order
-    if (path == 0) lockstep_run<int32_t, int64_t>(P, N, K, items, ranges, team_width, acc, sink);
-    else if (path == 1) lockstep_run<int64_t, int64_t>(P, N, K, items, ranges, team_width, acc, sink);
-    else lockstep_run<i128, i128>(P, N, K, items, ranges, team_width, acc, sink);
+    if (path == 0) lockstep_run<int32_t, int64_t>(five, P, N, K, items, ranges, team_width, acc, sink);
+    else if (path == 1) lockstep_run<int64_t, int64_t>(five, P, N, K, items, ranges, team_width, acc, sink);
+    else lockstep_run<i128, i128>(five, P, N, K, items, ranges, team_width, acc, sink);
     return;
   }
-  if (path == 0) host_run<int32_t, int64_t>(P, N, K, items, ranges, threads, acc, sink);
-  else if (path == 1) host_run<int64_t, int64_t>(P, N, K, items, ranges, threads, acc, sink);
-  else host_run<i128, i128>(P, N, K, items, ranges, threads, acc, sink);
+  if (path == 0) host_run<int32_t, int64_t>(five, P, N, K, items, ranges, threads, acc, sink);
+  else if (path == 1) host_run<int64_t, int64_t>(five, P, N, K, items, ranges, threads, acc, sink);
+  else host_run<i128, i128>(five, P, N, K, items, ranges, threads, acc, sink);
 }
 
 }  // namespace bd

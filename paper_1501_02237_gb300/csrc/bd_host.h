@@ -35,12 +35,26 @@ int choose_path(double coord_bits, double full_bits);
 
 // Depth of the deepest work item of the walk on integer path `path` (0: int32 coordinate
 // minors, 1: int64, 2: int128): the depth at which its bottom stage starts.  The 5-D stage
-// (int32 coordinate minors, k >= 4) starts at k-3, the 4-D stage (int64, or k = 3) at k-2.
-int item_depth(int k, int path);
+// (int32 coordinate minors, k >= 4, when `five`) starts at k-3, the 4-D stage at k-2.
+int item_depth(int k, int path, bool five);
+
+// Whether the walk on the 32-bit coordinate path should end in the 5-D stage for these npts x k
+// points (row-major) rather than the 4-D stage.  The 5-D stage skips one Bareiss level per node
+// but tests every quadruple with a det4 and every nonsingular one with five 4x4 cofactors.  Rule,
+// from timings of both stages on random, quiver-style, master-space and batch systems on a
+// GB300: where the system's items share launches with other systems (teams = 0) the 5-D stage
+// for k >= 4 (it took fewer SM cycles on every class of the uneven batch); where the system
+// fills a launch alone (teams = its resident warps), k >= 6 and at most half of 256 sampled
+// (k+1)-subsets full-dimensional (exact rank by fraction-free elimination; a fixed seed, so the
+// choice is a function of the points): mostly nonsingular systems run faster on the 4-D stage's
+// finer work list.  Allocation-free.
+bool prefer_five(const int64_t* points, int npts, int k, uint64_t teams);
 
 // Prefix work list: every (k+1)-subset of {0..npts-1} lies below exactly one item; items are
 // split until each holds at most `max_subsets` subsets (or reaches length `depth`), then
-// sorted by decreasing size.
+// sorted by decreasing size.  With depth = k-3 (the 5-D stage), an item of that length holding
+// more than 16 times `max_subsets` is split once more (length k-2: its last index is then the
+// first point of the quadruples it takes).
 std::vector<Item> build_items(int npts, int k, uint64_t max_subsets, int depth);
 
 // The work-item split threshold for a launch of `teams` warps over `total` subsets: fine enough
@@ -60,8 +74,9 @@ bool build_items_into(int npts, int k, uint64_t max_subsets, int depth, Item* ou
 
 // Host emulation of the warp enumeration on `threads` CPU threads (one single-lane team
 // each), for an integer path; team_width > 1 instead runs one team of that many lanes as
-// threads in lockstep.  With ranges, teams take whole ranges of consecutive items.
-void host_enumerate(int path, const int64_t* P, int N, int K, const std::vector<Item>& items, int threads, Acc& acc,
+// threads in lockstep.  With ranges, teams take whole ranges of consecutive items.  `five`
+// selects the 5-D bottom stage where it applies; the items must come from item_depth(K, path, five).
+void host_enumerate(int path, bool five, const int64_t* P, int N, int K, const std::vector<Item>& items, int threads, Acc& acc,
                     int team_width = 1, const std::vector<Range>* ranges = nullptr, const CellSink* sink = nullptr);
 
 }  // namespace bd

@@ -146,6 +146,7 @@ __global__ void BD_ENUM_BOUNDS k_enumerate(EnumParams p) {
   Walker<TC, TL, WarpTeam> W(tm, P, N, K, slots, m.sc, m.sl, m.fl, m.uni);
   W.tri = p.tri;
   W.sink = p.sink;
+  W.use5 = p.five != 0;
   Acc acc{};
   unsigned long long done = 0;
   const unsigned int units = p.ranges ? (unsigned int)p.nranges : (unsigned int)p.nitems;
@@ -304,6 +305,7 @@ __global__ void BD_ENUM_BOUNDS k_batch(BatchParams p) {
   float* fl = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(sl) + align16((size_t)slots * p.maxK * sizeof(TL)));
   WarpTeam tm;
   int cur = -1, N = 0, K = 0;
+  bool five = false;
   Acc acc{};
   unsigned long long items = 0, cyc = 0;
   for (;;) {
@@ -323,6 +325,7 @@ __global__ void BD_ENUM_BOUNDS k_batch(BatchParams p) {
       const BatchDesc d = p.desc[cur];
       N = d.N;
       K = d.K;
+      five = d.five != 0;
       __syncwarp();
       for (int t = lane; t < N * K; t += 32) {
         const int q = t / K, c = t - q * K;
@@ -336,6 +339,7 @@ __global__ void BD_ENUM_BOUNDS k_batch(BatchParams p) {
     for (int t = 0; t < bi.len; ++t) it.idx[t] = bi.idx[t];
     Walker<TC, TL, WarpTeam> W(tm, P, N, K, slots, sc, sl, fl, uniform_after(fl, slots));
     W.tri = p.tri;
+    W.use5 = five;
     const long long t0 = clock64();
     W.run_item(it, acc);
     cyc += (unsigned long long)(clock64() - t0);
@@ -413,12 +417,13 @@ namespace {
 // same bytes.
 template <class TC, class TL>
 __device__ void serve_item(WarpTeam& tm, const int64_t* P, int N, int K, int slots, unsigned char* stack, int maxK,
-                           const Item& it, Acc& acc, const uint32_t* tri) {
+                           const Item& it, Acc& acc, const uint32_t* tri, bool five) {
   TC* sc = reinterpret_cast<TC*>(stack);
   TL* sl = reinterpret_cast<TL*>(stack + align16((size_t)slots * stack_entries(maxK) * sizeof(int64_t)));
   float* fl = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(sl) + align16((size_t)slots * maxK * sizeof(int64_t)));
   Walker<TC, TL, WarpTeam> W(tm, P, N, K, slots, sc, sl, fl, uniform_after(fl, slots));
   W.tri = tri;
+  W.use5 = five;
   W.run_item(it, acc);
 }
 
@@ -509,8 +514,8 @@ __global__ void BD_ENUM_BOUNDS k_serve(ServeParams p) {
     for (int t = 0; t < bi.len; ++t) it.idx[t] = bi.idx[t];
     Acc acc{};
     const long long t0 = clock64();
-    if (path == PATH_NARROW) serve_item<int32_t, int64_t>(tm, P, N, K, slots, stack, p.maxK, it, acc, p.tri);
-    else serve_item<int64_t, int64_t>(tm, P, N, K, slots, stack, p.maxK, it, acc, p.tri);
+    if (path == PATH_NARROW) serve_item<int32_t, int64_t>(tm, P, N, K, slots, stack, p.maxK, it, acc, p.tri, d.five != 0);
+    else serve_item<int64_t, int64_t>(tm, P, N, K, slots, stack, p.maxK, it, acc, p.tri, false);
     const unsigned long long cyc = (unsigned long long)(clock64() - t0);
     acc = warp_sum(acc);
     if (lane == 0) {

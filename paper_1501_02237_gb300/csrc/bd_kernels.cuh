@@ -25,6 +25,8 @@ struct EnumParams {
   int nranges;
   int shard, shards;      // this launch takes the units u with u % shards == shard (shards >= 1)
   int N, K;
+  int five;               // 1: the 5-D bottom stage (32-bit coordinate path, K >= 4); the work
+                          // list's depth must agree (item_depth)
   unsigned int* counter;  // next work unit (reset to 0 before the launch)
   const uint32_t* tri;    // colex decode table of kTriEntries words (device), or nullptr
   CellSink sink;          // accepted cells are recorded here when sink.out is non-null
@@ -58,6 +60,7 @@ struct BatchDesc {       // one system of a batch
   int N, K;
   int pts_off;           // offset of its N x K coordinates in the packed point array
   int path;
+  int five;              // 1: the 5-D bottom stage on the 32-bit coordinate path (K >= 4)
   uint64_t lift_seed;    // stream seed of its current lifting
 };
 

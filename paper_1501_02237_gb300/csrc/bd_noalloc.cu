@@ -98,7 +98,8 @@ extern "C" int bd_volume_noalloc(const int64_t* points, int32_t npts, int32_t k,
   const uint64_t total = bd::binom(npts, k + 1);
   uint64_t thr = std::max<uint64_t>(256, total / ((uint64_t)shape.blocks * shape.warps * 4 + 1));
   size_t nitems = 0;
-  while (!bd::build_items_into(npts, k, thr, bd::item_depth(k, path), g_host_items, kItemsMax, &nitems)) thr *= 4;
+  const bool five = path == bd::PATH_NARROW && k >= 4 && bd::prefer_five(points, npts, k, (uint64_t)shape.blocks * shape.warps);
+  while (!bd::build_items_into(npts, k, thr, bd::item_depth(k, path, five), g_host_items, kItemsMax, &nitems)) thr *= 4;
 
   cudaStream_t st = bd::thread_stream();
   bd::DevAcc* d_acc = reinterpret_cast<bd::DevAcc*>(base);
@@ -127,6 +128,7 @@ extern "C" int bd_volume_noalloc(const int64_t* points, int32_t npts, int32_t k,
     ep.nitems = (int)nitems;
     ep.N = npts;
     ep.K = k;
+    ep.five = five ? 1 : 0;
     ep.counter = d_counter;
     ep.acc = d_acc;
     if (e == cudaSuccess) e = bd::launch_enumerate(ep, shape, path, st);

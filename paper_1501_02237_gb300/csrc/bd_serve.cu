@@ -40,6 +40,7 @@ struct Req {
   int64_t ticket = 0;
   double t_submit = 0, t_admit = 0, t_done = 0;
   int rank = 0, dim = 0, N = 0, K = 0, path = 0, attempt = 0;
+  bool five = false;  // the walk's bottom stage is the 5-D test
   uint64_t torsion = 1, seed = 0;
   bool consistent = true;
   int64_t max_abs = 0;
@@ -131,6 +132,7 @@ int publish(bd_server* s, Req* r) {
   d.K = r->K;
   d.pts_off = 0;
   d.path = r->path;
+  d.five = r->five ? 1 : 0;
   d.lift_seed = bd::lift_stream_seed(r->seed, (uint32_t)r->attempt);
   std::memcpy(s->h_pts + (size_t)slot * bd::BD_SERVE_PTS, r->pts.data(), sizeof(int64_t) * r->pts.size());
   s->h_rem[slot] = (unsigned)r->items.size();
@@ -180,7 +182,7 @@ void build_request_items(bd_server* s, Req* r) {
   const uint64_t want = std::max<uint64_t>(1, warps / 2);  // enough items to spread one system over the GPU
   uint64_t thr = std::max<uint64_t>(s->opts.item_subsets > 0 ? (uint64_t)s->opts.item_subsets : 256, sub / want);
   r->items.clear();
-  for (const bd::Item& it : bd::build_items(r->N, r->K, thr, bd::item_depth(r->K, r->path))) {
+  for (const bd::Item& it : bd::build_items(r->N, r->K, thr, bd::item_depth(r->K, r->path, r->five))) {
     bd::BatchItem x{};
     x.len = it.len;
     for (int t = 0; t < it.len && t < 11; ++t) x.idx[t] = it.idx[t];
@@ -591,6 +593,7 @@ int bd_server_submit(bd_server* s, const int64_t* A, int32_t n, int32_t m, const
       double coord = 0;
       const double bound = bd::hadamard_log2(red.points.data(), nullptr, r->N, r->K, (1 << 20) - 1, &coord);
       r->path = bd::choose_path(coord, bound);
+      r->five = r->path == bd::PATH_NARROW && r->K >= 4 && bd::prefer_five(red.points.data(), r->N, r->K, 0);
       // the persistent kernel carries the int32 and int64 walkers; 128-bit systems take the side route
       side = r->path < 0 || r->path == bd::PATH_WIDE;
     }

@@ -9,6 +9,10 @@ namespace bd {
 
 namespace {
 
+// a 5-D node (depth K-3) is split by its quadruples' first point when it holds more than this
+// many times the split threshold
+constexpr uint64_t kNodeSplit = 16;
+
 // every prefix of the split tree, depth first; emit(item) returns false to stop early
 template <class Emit>
 bool for_each_item(int N, int K, uint64_t max_subsets, int depth, Emit emit) {
@@ -18,7 +22,12 @@ bool for_each_item(int N, int K, uint64_t max_subsets, int depth, Emit emit) {
   pre[0] = 0;
   for (;;) {
     const uint64_t T = subtree_size(N, K, pre[len - 1], len);
-    if (T > max_subsets && len < depth) {  // split; items stop where the bottom stage starts
+    // split; items stop where the bottom stage starts, except that a node of the 5-D stage much
+    // larger than the threshold splits once more, by the first point of its quadruples, so
+    // that no single node holds a large share of a launch
+    const bool split = len < depth ? T > max_subsets
+                                   : depth == K - 3 && K >= 4 && len == depth && T / kNodeSplit > max_subsets;
+    if (split) {
       pre[len] = pre[len - 1] + 1;
       ++len;
       continue;
@@ -53,7 +62,56 @@ struct ItemOrder {
 
 }  // namespace
 
-int item_depth(int K, int path) { return K >= 4 && path == 0 ? K - 3 : std::max(K - 2, 1); }
+bool prefer_five(const int64_t* points, int npts, int k, uint64_t teams) {
+  if (k < 4 || k > KMAX || npts < k + 1 || npts > NMAX) return false;
+  if (teams == 0) return true;
+  if (k < 6) return false;
+  constexpr int kSamples = 256;
+  uint64_t z = 0x243F6A8885A308D3ull ^ ((uint64_t)npts << 32 | (uint64_t)k);
+  auto next = [&z]() {  // SplitMix64 step
+    z += 0x9E3779B97F4A7C15ull;
+    uint64_t x = z;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    return x ^ (x >> 31);
+  };
+  int idx[NMAX];
+  int64_t M[KMAX][KMAX];
+  int full = 0;
+  for (int t = 0; t < kSamples; ++t) {
+    for (int i = 0; i < npts; ++i) idx[i] = i;
+    for (int i = 0; i <= k; ++i) {  // a uniform (k+1)-subset: partial Fisher-Yates
+      const int j = i + (int)(next() % (uint64_t)(npts - i));
+      std::swap(idx[i], idx[j]);
+    }
+    for (int r = 0; r < k; ++r)
+      for (int c = 0; c < k; ++c) M[r][c] = points[(size_t)idx[r + 1] * k + c] - points[(size_t)idx[0] * k + c];
+    // fraction-free elimination: every entry stays a minor of the differences (below 2^31 on the
+    // 32-bit coordinate path), products in 128 bits, divisions exact
+    int64_t prev = 1;
+    bool nonsingular = true;
+    for (int p = 0; p < k && nonsingular; ++p) {
+      int r = p;
+      while (r < k && M[r][p] == 0) ++r;
+      if (r == k) {
+        nonsingular = false;
+        break;
+      }
+      if (r != p)
+        for (int c = 0; c < k; ++c) std::swap(M[r][c], M[p][c]);
+      for (int i = p + 1; i < k; ++i) {
+        for (int c = p + 1; c < k; ++c)
+          M[i][c] = (int64_t)(((__int128)M[i][c] * M[p][p] - (__int128)M[i][p] * M[p][c]) / prev);
+        M[i][p] = 0;
+      }
+      prev = M[p][p];
+    }
+    full += nonsingular ? 1 : 0;
+  }
+  return full * 2 <= kSamples;
+}
+
+int item_depth(int K, int path, bool five) { return five && K >= 4 && path == 0 ? K - 3 : std::max(K - 2, 1); }
 
 std::vector<Item> build_items(int N, int K, uint64_t max_subsets, int depth) {
   std::vector<Item> items;
@@ -79,7 +137,8 @@ static uint64_t item_cost(int N, int K, int D, const Item& it) {
     const uint64_t t = binom(N - 1 - v, m);
     return (uint64_t)(five ? 2 : 1) + (t + 31) / 32;
   };
-  if (L >= D) return node(a);
+  if (L > D) return 1 + (binom(N - 1 - a, 3) + 31) / 32;  // a 5-D item below its node
+  if (L == D) return node(a);
   uint64_t c = 0;
   for (int v = a + (D - L); v <= N - 1 - m; ++v) c += binom(v - a - 1, D - 1 - L) * node(v);
   return c;

@@ -321,3 +321,31 @@ def test_host_walker_64_bit_coordinates_high_dimension(seed):
         assert r["status"] == 0
         assert r["nvol"] == nvol_placing(pts), (k, items)
         assert r["bound_bits"] > 31 and not r["flags"] & bd.BD_FLAG_INT128
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_host_walker_both_bottom_stages(seed):
+    # the 32-bit coordinate path ends in the 5-D test or the 4-D test (chosen per point set, or
+    # fixed by the caller): both give the oracle's volume, with the deepest items, the default
+    # items and a lockstep team of four lanes; k = 3 and the int64 path ignore the choice
+    rng = random.Random(9900 + seed)
+    k = 3 + seed % 4
+    n = rng.randint(k + 3, 13)
+    span = 3 if seed % 3 else 1
+    pts = [tuple(rng.randint(-span, span) for _ in range(k)) for _ in range(n)]
+    ref = nvol_placing(pts)
+    lf = oracle_lifts(n, seed)
+    for stage in (4, 5, 0):
+        for items, width in ((1, 1), (0, 1), (0, 4)):
+            r = bd.host_volume_lifted(np.array(pts), np.array(lf), item_subsets=items, team_width=width,
+                                      bottom_stage=stage)
+            if r["status"] == 3:
+                continue  # a tie under this lifting: the same for every stage and work list
+            assert r["status"] == 0
+            assert r["nvol"] == ref, (k, stage, items, width)
+
+
+def test_bottom_stage_argument_is_checked():
+    pts = np.array([(0, 0, 0, 0), (1, 0, 0, 0), (0, 1, 0, 0), (0, 0, 1, 0), (0, 0, 0, 1), (1, 1, 1, 1)])
+    with pytest.raises(bd.BinodegError):
+        bd.host_volume_lifted(pts, np.arange(1, 7), bottom_stage=3)
