@@ -277,7 +277,9 @@ typedef struct {
   int32_t publish_wait_ms;   /* bound of the kernel's wait for a work item's publication (0: 1000) */
   int32_t test_withhold;     /* test hook, 0 in normal use: the n-th admission's publication stamps
                                 are never written, so the bounded wait for them runs out */
-  int32_t reserved;
+  int32_t bottom_stage;      /* as in bd_plan_opts, per request; 0: chosen from its points when it
+                                is admitted, for a request alone on the GPU (latency) or for one
+                                sharing it with requests in flight or waiting (throughput) */
 } bd_server_opts;
 typedef struct {
   int64_t submitted, completed, relifted, launches;

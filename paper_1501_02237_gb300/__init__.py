@@ -506,9 +506,9 @@ class Server:
 
     def __init__(self, slots: int = 0, ring_items: int = 0, memory_budget: int = 0, warps_per_block: int = 0,
                  blocks_per_sm: int = 0, item_subsets: int = 0, max_inflight_items: int = 0, order: int = 0,
-                 publish_wait_ms: int = 0, test_withhold: int = 0):
+                 publish_wait_ms: int = 0, test_withhold: int = 0, bottom_stage: int = 0):
         o = ServerOpts(slots, ring_items, memory_budget, warps_per_block, blocks_per_sm, item_subsets,
-                       max_inflight_items, order, publish_wait_ms, test_withhold)
+                       max_inflight_items, order, publish_wait_ms, test_withhold, bottom_stage)
         h = C.c_void_p()
         check(lib().bd_server_start(C.byref(o), C.byref(h)))
         self.handle = h

@@ -95,7 +95,7 @@ class ServerOpts(C.Structure):
     _fields_ = [("slots", C.c_int32), ("ring_items", C.c_int32), ("memory_budget", C.c_int64),
                 ("warps_per_block", C.c_int32), ("blocks_per_sm", C.c_int32), ("item_subsets", C.c_int64),
                 ("max_inflight_items", C.c_int64), ("order", C.c_int32), ("publish_wait_ms", C.c_int32),
-                ("test_withhold", C.c_int32), ("reserved", C.c_int32)]
+                ("test_withhold", C.c_int32), ("bottom_stage", C.c_int32)]
 
 
 class ServerStats(C.Structure):

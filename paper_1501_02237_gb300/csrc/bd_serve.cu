@@ -40,7 +40,9 @@ struct Req {
   int64_t ticket = 0;
   double t_submit = 0, t_admit = 0, t_done = 0;
   int rank = 0, dim = 0, N = 0, K = 0, path = 0, attempt = 0;
-  bool five = false;  // the walk's bottom stage is the 5-D test
+  bool five = false;    // the walk's bottom stage is the 5-D test (set when its items are built)
+  bool alone5 = false;  // the 5-D stage is preferred when the request has the GPU to itself
+  bool pooled5 = false; // ... and when it shares the persistent kernel with other requests
   uint64_t torsion = 1, seed = 0;
   bool consistent = true;
   int64_t max_abs = 0;
@@ -319,7 +321,12 @@ bool pump_once(bd_server* s) {
       if (s->opts.order == 1)
         it = std::min_element(s->waiting.begin(), s->waiting.end(), [](Req* a, Req* b) { return a->cost < b->cost; });
       r = *it;
-      if (r->items.empty()) build_request_items(s, r);
+      if (r->items.empty()) {
+        // the bottom stage by the load at admission: alone on the GPU (latency: the standalone
+        // choice) or sharing it with requests in flight or waiting (throughput: the pooled one)
+        r->five = s->resident > 0 || s->waiting.size() > 1 ? r->pooled5 : r->alone5;
+        build_request_items(s, r);
+      }
       const uint64_t limit = s->opts.max_inflight_items > 0 ? (uint64_t)s->opts.max_inflight_items : s->ring_cap;
       // ring room: requests finish out of order, so the oldest publication still in a slot
       // bounds what may be overwritten
@@ -473,6 +480,8 @@ extern "C" {
 
 int bd_server_start(const bd_server_opts* opts, bd_server** out) {
   if (!out) return bd::set_error(BD_ERR_ARG, "NULL argument");
+  if (opts && opts->bottom_stage != 0 && opts->bottom_stage != 4 && opts->bottom_stage != 5)
+    return bd::set_error(BD_ERR_ARG, "bottom_stage must be 0, 4 or 5");
   bd_server* s = new (std::nothrow) bd_server();
   if (!s) return bd::set_error(BD_ERR_NOMEM, "host allocation");
   if (opts) s->opts = *opts;
@@ -593,7 +602,11 @@ int bd_server_submit(bd_server* s, const int64_t* A, int32_t n, int32_t m, const
       double coord = 0;
       const double bound = bd::hadamard_log2(red.points.data(), nullptr, r->N, r->K, (1 << 20) - 1, &coord);
       r->path = bd::choose_path(coord, bound);
-      r->five = r->path == bd::PATH_NARROW && r->K >= 4 && bd::prefer_five(red.points.data(), r->N, r->K, 0);
+      const int stage = s->opts.bottom_stage;
+      const bool narrow = r->path == bd::PATH_NARROW && r->K >= 4;
+      r->alone5 = narrow && (stage == 5 || (stage == 0 && bd::prefer_five(red.points.data(), r->N, r->K,
+                                                                         (uint64_t)s->shape.blocks * s->shape.warps)));
+      r->pooled5 = narrow && (stage == 5 || (stage == 0 && bd::prefer_five(red.points.data(), r->N, r->K, 0)));
       // the persistent kernel carries the int32 and int64 walkers; 128-bit systems take the side route
       side = r->path < 0 || r->path == bd::PATH_WIDE;
     }
