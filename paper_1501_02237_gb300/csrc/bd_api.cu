@@ -89,7 +89,7 @@ struct ItemList {
 };
 std::mutex g_cache_mu;
 std::map<std::tuple<int, int, int64_t, int64_t, int, int>, std::shared_ptr<ItemList>> g_items;
-std::map<std::tuple<int, int, int, int, int, int>, bd::LaunchShape> g_shapes;
+std::map<std::tuple<int, int, int, int, int, int, bool>, bd::LaunchShape> g_shapes;
 
 int current_device() {
   int d = 0;
@@ -147,8 +147,8 @@ int get_tri(const uint32_t*& out) {
   return BD_OK;
 }
 
-int get_shape(int N, int K, int path, int warps_req, int bps_req, bd::LaunchShape& out) {
-  const auto key = std::make_tuple(N, K, path, warps_req, bps_req, current_device());
+int get_shape(int N, int K, int path, bool five, int warps_req, int bps_req, bd::LaunchShape& out) {
+  const auto key = std::make_tuple(N, K, path, warps_req, bps_req, current_device(), five);
   std::lock_guard<std::mutex> lk(g_cache_mu);
   auto it = g_shapes.find(key);
   if (it != g_shapes.end()) {
@@ -156,7 +156,7 @@ int get_shape(int N, int K, int path, int warps_req, int bps_req, bd::LaunchShap
     return BD_OK;
   }
   cudaError_t e;
-  out = bd::enum_shape(N, K, path, warps_req, bps_req, sm_count(), &e);
+  out = bd::enum_shape(N, K, path, five, warps_req, bps_req, sm_count(), &e);
   if (e != cudaSuccess) return cuda_fail(e, "launch shape");
   g_shapes[key] = out;
   return BD_OK;
@@ -288,14 +288,20 @@ int plan_prepare(bd_plan* p, const int64_t* points, const int64_t* lifts, int32_
   p->path = bd::choose_path(coord_bits, p->bound);
   if (p->path < 0) return fail(BD_ERR_OVERFLOW, "Hadamard bound of the lifted minors exceeds 2^127");
   if (opts && opts->force_int128) p->path = bd::PATH_WIDE;
-  rc = get_shape(npts, k, p->path, opts ? opts->warps_per_block : 0, opts ? opts->blocks_per_sm : 0, p->shape);
+  const int wreq = opts ? opts->warps_per_block : 0, breq = opts ? opts->blocks_per_sm : 0;
+  const int stage = opts ? opts->bottom_stage : 0;
+  if (stage != 0 && stage != 4 && stage != 5) return fail(BD_ERR_ARG, "bottom_stage must be 0, 4 or 5");
+  rc = get_shape(npts, k, p->path, false, wreq, breq, p->shape);
   if (rc) return rc;
+  p->five = p->path == bd::PATH_NARROW && k >= 4 &&
+            (stage == 5 || (stage == 0 && bd::prefer_five(points, npts, k, (uint64_t)p->shape.blocks * p->shape.warps)));
+  if (p->five) {  // the 5-D kernel's own occupancy
+    rc = get_shape(npts, k, p->path, true, wreq, breq, p->shape);
+    if (rc) return rc;
+  }
   const uint64_t total = bd::binom(npts, k + 1);
   const uint64_t warps = (uint64_t)p->shape.blocks * p->shape.warps;
   const int64_t thr = opts && opts->item_subsets > 0 ? opts->item_subsets : (int64_t)bd::default_item_subsets(total, warps);
-  const int stage = opts ? opts->bottom_stage : 0;
-  if (stage != 0 && stage != 4 && stage != 5) return fail(BD_ERR_ARG, "bottom_stage must be 0, 4 or 5");
-  p->five = p->path == bd::PATH_NARROW && k >= 4 && (stage == 5 || (stage == 0 && bd::prefer_five(points, npts, k, warps)));
   rc = get_items(npts, k, thr, (int64_t)warps, bd::item_depth(k, p->path, p->five), p->items);
   if (rc) return rc;
   rc = get_tri(p->tri);

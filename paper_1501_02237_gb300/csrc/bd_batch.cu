@@ -80,7 +80,7 @@ struct bd_batch {
   bd::DevAcc* d_acc = nullptr;
   unsigned long long* d_cycles = nullptr;
   unsigned int* d_done = nullptr;
-  unsigned int* d_counter = nullptr;  // one per path group
+  unsigned int* d_counter = nullptr;  // one per launch group (integer path and bottom stage)
   bd::DevAcc* h_acc = nullptr;        // pinned, cap_sys
   unsigned long long* h_cycles = nullptr;
   cudaGraphExec_t graph = nullptr;
@@ -204,6 +204,7 @@ double closed_form_cost(const BatchSys& s) {
 
 struct Group {
   int path = 0, maxN = 0, maxK = 0;
+  bool five = false;            // the group's launch runs the 5-D bottom stage
   size_t first = 0, count = 0;  // range in the item array
 };
 
@@ -213,17 +214,22 @@ void build_batch_items(bd_batch* b, const std::vector<int>& active, const float*
                        int warps_total, std::vector<bd::BatchItem>& items, std::vector<Group>& groups) {
   items.clear();
   groups.clear();
-  for (int path = 0; path < 3; ++path) {
+  // one launch per (integer path, bottom stage): the 32-bit path with the 5-D stage, the 32-bit
+  // path with the 4-D stage, the 64-bit and the 128-bit paths
+  for (int kind = 0; kind < 4; ++kind) {
+    const int path = kind == 0 ? 0 : kind - 1;
+    const bool five = kind == 0;
     std::vector<int> in;
     double total = 0;
     for (int i : active)
-      if (b->sys[i].path == path) {
+      if (b->sys[i].path == path && b->sys[i].five == five) {
         in.push_back(i);
         total += cost ? std::max(1e-9, (double)cost[i]) : closed_form_cost(b->sys[i]);
       }
     if (in.empty()) continue;
     Group g;
     g.path = path;
+    g.five = five;
     g.first = items.size();
     const double target = total / ((double)warps_total * items_per_warp + 1.0);
     std::vector<std::pair<double, bd::BatchItem>> tmp;
@@ -264,7 +270,7 @@ int run_batched(bd_batch* b, const std::vector<int>& active, const float* cost, 
       maxK = std::max(maxK, b->sys[i].K);
     }
     cudaError_t e;
-    bd::LaunchShape s0 = bd::batch_shape(std::max(maxN, 2), std::max(maxK, 1), bd::PATH_NARROW, warps_req, 0, sms, &e);
+    bd::LaunchShape s0 = bd::batch_shape(std::max(maxN, 2), std::max(maxK, 1), bd::PATH_NARROW, false, warps_req, 0, sms, &e);
     if (e != cudaSuccess) return bd::cuda_error(e);
     build_batch_items(b, active, cost, items_per_warp, s0.blocks * s0.warps, items, groups);
   }
@@ -295,7 +301,7 @@ int run_batched(bd_batch* b, const std::vector<int>& active, const float* cost, 
   // the timed part: clear, one persistent launch per path group, copy the results back
   std::vector<bd::LaunchShape> shapes;
   for (const Group& g : groups) {
-    bd::LaunchShape s = bd::batch_shape(g.maxN, g.maxK, g.path, warps_req, 0, sms, &e);
+    bd::LaunchShape s = bd::batch_shape(g.maxN, g.maxK, g.path, g.five, warps_req, 0, sms, &e);
     if (e != cudaSuccess) return bd::cuda_error(e);
     shapes.push_back(s);
   }
@@ -323,7 +329,7 @@ int run_batched(bd_batch* b, const std::vector<int>& active, const float* cost, 
       p.cycles = b->d_cycles;
       p.done = b->d_done;
       p.tri = tri;
-      r = bd::launch_batch(p, shapes[gi], g.path, s);
+      r = bd::launch_batch(p, shapes[gi], g.path, g.five, s);
     }
     if (r == cudaSuccess) r = cudaMemcpyAsync(b->h_acc, b->d_acc, sizeof(bd::DevAcc) * nsys, cudaMemcpyDeviceToHost, s);
     if (r == cudaSuccess)
@@ -339,7 +345,8 @@ int run_batched(bd_batch* b, const std::vector<int>& active, const float* cost, 
     std::string key = std::to_string(nsys) + ":" + std::to_string((uintptr_t)b->d_acc) + ":" +
                       std::to_string((uintptr_t)b->d_items);
     for (size_t gi = 0; gi < groups.size(); ++gi)
-      key += ":" + std::to_string(groups[gi].path) + "," + std::to_string(groups[gi].first) + "," +
+      key += ":" + std::to_string(groups[gi].path) + "," + std::to_string(groups[gi].five) + "," +
+             std::to_string(groups[gi].first) + "," +
              std::to_string(groups[gi].count) + "," + std::to_string(groups[gi].maxN) + "," +
              std::to_string(groups[gi].maxK) + "," + std::to_string(shapes[gi].blocks) + "," +
              std::to_string(shapes[gi].warps);

@@ -767,7 +767,10 @@ BD_COLD int side5_exact(StateView<TC, TL> v, int c0, int c1, int c, int p, int q
                    step43(r0, pi0, row4(v, q), D), D3, sig);
 }
 
-template <class TC, class TL, class Team>
+// Stage: the bottom stage, fixed at compile time (4: the 4-D test only; 5: the 5-D test only,
+// for callers that guarantee the 32-bit coordinate path and K >= 4) or chosen at run time by
+// use5 (0).  A fixed stage keeps the other stage's code out of the kernel.
+template <class TC, class TL, class Team, int Stage = 0>
 struct Walker {
   typedef typename DivOf<TC>::type Div;
   Team& tm;
@@ -799,9 +802,9 @@ struct Walker {
   // bound is looser (one exact elimination fewer removes cancellation); where the minors are
   // 64-bit numbers its exact routes, in 128-bit arithmetic, cost more than the step it saves.
   static constexpr bool kFiltered = sizeof(TL) == 8;
-  static constexpr bool kFive = kFiltered && sizeof(TC) == 4;
-  bool use5 = true;  // the 5-D stage where it applies (else the 4-D test); the work list must agree
-  BD_HD bool five() const { return kFive && use5 && K >= 4; }
+  static constexpr bool kFive = kFiltered && sizeof(TC) == 4 && Stage != 4;
+  bool use5 = true;  // Stage 0: the 5-D stage where it applies (else the 4-D test); the work list must agree
+  BD_HD bool five() const { return Stage == 5 ? kFive : (kFive && use5 && K >= 4); }
   // DFS depth at which the bottom stage takes over (the chosen prefix is s_0 .. s_{depth-1}):
   // the 5-D test finishes the last four levels, the 4-D test three, the 3-D and 2-D tests two
   BD_HD int bottom_depth() const {

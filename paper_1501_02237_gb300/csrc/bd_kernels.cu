@@ -132,7 +132,9 @@ __device__ void flush(const Acc& a, DevAcc* g, unsigned long long items) {
   if (items) atomicAdd(&g->items_done, items);
 }
 
-template <class TC, class TL>
+// Stage: the walker's bottom stage (4 or 5; see Walker), one kernel each, so that neither carries
+// the other's code
+template <class TC, class TL, int Stage>
 __global__ void BD_ENUM_BOUNDS k_enumerate(EnumParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
   int64_t* P = reinterpret_cast<int64_t*>(smem);
@@ -143,10 +145,9 @@ __global__ void BD_ENUM_BOUNDS k_enumerate(EnumParams p) {
   load_points(P, p);
 
   WarpTeam tm;
-  Walker<TC, TL, WarpTeam> W(tm, P, N, K, slots, m.sc, m.sl, m.fl, m.uni);
+  Walker<TC, TL, WarpTeam, Stage> W(tm, P, N, K, slots, m.sc, m.sl, m.fl, m.uni);
   W.tri = p.tri;
   W.sink = p.sink;
-  W.use5 = p.five != 0;
   Acc acc{};
   unsigned long long done = 0;
   const unsigned int units = p.ranges ? (unsigned int)p.nranges : (unsigned int)p.nitems;
@@ -183,7 +184,7 @@ __global__ void k_classify(const int64_t* pts, const int64_t* lifts, int N, int 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, warps = blockDim.x >> 5;
   WarpMem<TC, TL> m(smem, N, K, slots, warp);
   WarpTeam tm;
-  Walker<TC, TL, WarpTeam> W(tm, P, N, K, slots, m.sc, m.sl, m.fl, m.uni);
+  Walker<TC, TL, WarpTeam, 4> W(tm, P, N, K, slots, m.sc, m.sl, m.fl, m.uni);
   for (int i = blockIdx.x * warps + warp; i < count; i += gridDim.x * warps) {
     TL ad = 0;
     const int s = W.classify(subsets + (size_t)i * (K + 1), ad);
@@ -196,7 +197,10 @@ __global__ void k_classify(const int64_t* pts, const int64_t* lifts, int N, int 
 
 template <class TC, class TL>
 cudaError_t configure(int smem) {
-  cudaError_t e = cudaFuncSetAttribute(k_enumerate<TC, TL>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaError_t e = cudaFuncSetAttribute(k_enumerate<TC, TL, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if constexpr (sizeof(TC) == 4) {  // the 5-D stage exists on the 32-bit coordinate path only
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_enumerate<TC, TL, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  }
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_classify<TC, TL>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
 }
@@ -224,7 +228,8 @@ size_t enum_smem_bytes(int N, int K, int warps, int path) {
   return pts + per_warp * warps;
 }
 
-LaunchShape enum_shape(int N, int K, int path, int warps_req, int blocks_per_sm_req, int sms, cudaError_t* err) {
+LaunchShape enum_shape(int N, int K, int path, bool five, int warps_req, int blocks_per_sm_req, int sms,
+                       cudaError_t* err) {
   LaunchShape s;
   *err = cudaSuccess;
   int dev = 0, max_optin = 0;
@@ -240,12 +245,14 @@ LaunchShape enum_shape(int N, int K, int path, int warps_req, int blocks_per_sm_
   if (e != cudaSuccess) { *err = e; return s; }
   int per_sm = blocks_per_sm_req;
   if (per_sm <= 0) {
-    if (path == PATH_NARROW)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_enumerate<int32_t, int64_t>, warps * 32, s.smem);
+    if (path == PATH_NARROW && five)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_enumerate<int32_t, int64_t, 5>, warps * 32, s.smem);
+    else if (path == PATH_NARROW)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_enumerate<int32_t, int64_t, 4>, warps * 32, s.smem);
     else if (path == PATH_MID)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_enumerate<int64_t, int64_t>, warps * 32, s.smem);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_enumerate<int64_t, int64_t, 4>, warps * 32, s.smem);
     else
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_enumerate<i128, i128>, warps * 32, s.smem);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_enumerate<i128, i128, 4>, warps * 32, s.smem);
     if (e != cudaSuccess) { *err = e; return s; }
     if (per_sm < 1) per_sm = 1;
   }
@@ -254,9 +261,10 @@ LaunchShape enum_shape(int N, int K, int path, int warps_req, int blocks_per_sm_
 }
 
 cudaError_t launch_enumerate(const EnumParams& p, const LaunchShape& s, int path, cudaStream_t st) {
-  if (path == PATH_NARROW) k_enumerate<int32_t, int64_t><<<s.blocks, s.warps * 32, s.smem, st>>>(p);
-  else if (path == PATH_MID) k_enumerate<int64_t, int64_t><<<s.blocks, s.warps * 32, s.smem, st>>>(p);
-  else k_enumerate<i128, i128><<<s.blocks, s.warps * 32, s.smem, st>>>(p);
+  if (path == PATH_NARROW && p.five && p.K >= 4) k_enumerate<int32_t, int64_t, 5><<<s.blocks, s.warps * 32, s.smem, st>>>(p);
+  else if (path == PATH_NARROW) k_enumerate<int32_t, int64_t, 4><<<s.blocks, s.warps * 32, s.smem, st>>>(p);
+  else if (path == PATH_MID) k_enumerate<int64_t, int64_t, 4><<<s.blocks, s.warps * 32, s.smem, st>>>(p);
+  else k_enumerate<i128, i128, 4><<<s.blocks, s.warps * 32, s.smem, st>>>(p);
   return cudaGetLastError();
 }
 
@@ -292,7 +300,7 @@ __device__ void flush_sys(const Acc& a, unsigned long long items, unsigned long 
 // Persistent: every warp takes the next (system, prefix) item; when the system changes it
 // loads that system's lifted points into its own shared-memory buffer (so warps of one block
 // may work on different systems) and flushes its accumulators for the previous one.
-template <class TC, class TL>
+template <class TC, class TL, int Stage>
 __global__ void BD_ENUM_BOUNDS k_batch(BatchParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -305,7 +313,6 @@ __global__ void BD_ENUM_BOUNDS k_batch(BatchParams p) {
   float* fl = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(sl) + align16((size_t)slots * p.maxK * sizeof(TL)));
   WarpTeam tm;
   int cur = -1, N = 0, K = 0;
-  bool five = false;
   Acc acc{};
   unsigned long long items = 0, cyc = 0;
   for (;;) {
@@ -325,7 +332,6 @@ __global__ void BD_ENUM_BOUNDS k_batch(BatchParams p) {
       const BatchDesc d = p.desc[cur];
       N = d.N;
       K = d.K;
-      five = d.five != 0;
       __syncwarp();
       for (int t = lane; t < N * K; t += 32) {
         const int q = t / K, c = t - q * K;
@@ -337,9 +343,8 @@ __global__ void BD_ENUM_BOUNDS k_batch(BatchParams p) {
     Item it{};
     it.len = bi.len;
     for (int t = 0; t < bi.len; ++t) it.idx[t] = bi.idx[t];
-    Walker<TC, TL, WarpTeam> W(tm, P, N, K, slots, sc, sl, fl, uniform_after(fl, slots));
+    Walker<TC, TL, WarpTeam, Stage> W(tm, P, N, K, slots, sc, sl, fl, uniform_after(fl, slots));
     W.tri = p.tri;
-    W.use5 = five;
     const long long t0 = clock64();
     W.run_item(it, acc);
     cyc += (unsigned long long)(clock64() - t0);
@@ -351,12 +356,12 @@ __global__ void BD_ENUM_BOUNDS k_batch(BatchParams p) {
   }
 }
 
-template <class TC, class TL>
+template <class TC, class TL, int Stage>
 cudaError_t configure_batch() {
   int dev = 0, max_optin = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  return cudaFuncSetAttribute(k_batch<TC, TL>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_optin);
+  return cudaFuncSetAttribute(k_batch<TC, TL, Stage>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_optin);
 }
 
 }  // namespace
@@ -370,7 +375,8 @@ size_t batch_smem_bytes(int maxN, int maxK, int warps, int path) {
   return (pbytes + per_warp) * warps;
 }
 
-LaunchShape batch_shape(int maxN, int maxK, int path, int warps_req, int blocks_per_sm_req, int sms, cudaError_t* err) {
+LaunchShape batch_shape(int maxN, int maxK, int path, bool five, int warps_req, int blocks_per_sm_req, int sms,
+                        cudaError_t* err) {
   LaunchShape s;
   *err = cudaSuccess;
   int dev = 0, max_optin = 0;
@@ -382,18 +388,21 @@ LaunchShape batch_shape(int maxN, int maxK, int path, int warps_req, int blocks_
   s.smem = batch_smem_bytes(maxN, maxK, warps, path);
   s.slots = slots_of(maxN);
   if (s.smem > (size_t)max_optin) { *err = cudaErrorInvalidConfiguration; return s; }
-  cudaError_t e = path == PATH_NARROW ? configure_batch<int32_t, int64_t>()
-                  : path == PATH_MID  ? configure_batch<int64_t, int64_t>()
-                                      : configure_batch<i128, i128>();
+  cudaError_t e = path == PATH_NARROW && five ? configure_batch<int32_t, int64_t, 5>()
+                  : path == PATH_NARROW       ? configure_batch<int32_t, int64_t, 4>()
+                  : path == PATH_MID          ? configure_batch<int64_t, int64_t, 4>()
+                                              : configure_batch<i128, i128, 4>();
   if (e != cudaSuccess) { *err = e; return s; }
   int per_sm = blocks_per_sm_req;
   if (per_sm <= 0) {
-    if (path == PATH_NARROW)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<int32_t, int64_t>, warps * 32, s.smem);
+    if (path == PATH_NARROW && five)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<int32_t, int64_t, 5>, warps * 32, s.smem);
+    else if (path == PATH_NARROW)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<int32_t, int64_t, 4>, warps * 32, s.smem);
     else if (path == PATH_MID)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<int64_t, int64_t>, warps * 32, s.smem);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<int64_t, int64_t, 4>, warps * 32, s.smem);
     else
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<i128, i128>, warps * 32, s.smem);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<i128, i128, 4>, warps * 32, s.smem);
     if (e != cudaSuccess) { *err = e; return s; }
     if (per_sm < 1) per_sm = 1;
   }
@@ -401,10 +410,11 @@ LaunchShape batch_shape(int maxN, int maxK, int path, int warps_req, int blocks_
   return s;
 }
 
-cudaError_t launch_batch(const BatchParams& p, const LaunchShape& s, int path, cudaStream_t st) {
-  if (path == PATH_NARROW) k_batch<int32_t, int64_t><<<s.blocks, s.warps * 32, s.smem, st>>>(p);
-  else if (path == PATH_MID) k_batch<int64_t, int64_t><<<s.blocks, s.warps * 32, s.smem, st>>>(p);
-  else k_batch<i128, i128><<<s.blocks, s.warps * 32, s.smem, st>>>(p);
+cudaError_t launch_batch(const BatchParams& p, const LaunchShape& s, int path, bool five, cudaStream_t st) {
+  if (path == PATH_NARROW && five) k_batch<int32_t, int64_t, 5><<<s.blocks, s.warps * 32, s.smem, st>>>(p);
+  else if (path == PATH_NARROW) k_batch<int32_t, int64_t, 4><<<s.blocks, s.warps * 32, s.smem, st>>>(p);
+  else if (path == PATH_MID) k_batch<int64_t, int64_t, 4><<<s.blocks, s.warps * 32, s.smem, st>>>(p);
+  else k_batch<i128, i128, 4><<<s.blocks, s.warps * 32, s.smem, st>>>(p);
   return cudaGetLastError();
 }
 

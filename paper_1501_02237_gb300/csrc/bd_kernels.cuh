@@ -25,8 +25,8 @@ struct EnumParams {
   int nranges;
   int shard, shards;      // this launch takes the units u with u % shards == shard (shards >= 1)
   int N, K;
-  int five;               // 1: the 5-D bottom stage (32-bit coordinate path, K >= 4); the work
-                          // list's depth must agree (item_depth)
+  int five;               // 1: the 5-D bottom stage (32-bit coordinate path, K >= 4): the launch
+                          // runs that stage's kernel; the work list's depth must agree (item_depth)
   unsigned int* counter;  // next work unit (reset to 0 before the launch)
   const uint32_t* tri;    // colex decode table of kTriEntries words (device), or nullptr
   CellSink sink;          // accepted cells are recorded here when sink.out is non-null
@@ -44,7 +44,8 @@ enum { PATH_NARROW = 0, PATH_MID = 1, PATH_WIDE = 2 };
 
 // Shared memory of one block: lifted points + one stack per warp.
 size_t enum_smem_bytes(int N, int K, int warps, int path);
-LaunchShape enum_shape(int N, int K, int path, int warps_req, int blocks_per_sm_req, int sms, cudaError_t* err);
+// five: the launch runs the 5-D bottom stage (path PATH_NARROW, K >= 4; EnumParams.five)
+LaunchShape enum_shape(int N, int K, int path, bool five, int warps_req, int blocks_per_sm_req, int sms, cudaError_t* err);
 cudaError_t launch_enumerate(const EnumParams& p, const LaunchShape& s, int path, cudaStream_t st);
 
 // One warp per given subset: status (0 singular, 1 rejected, 2 accepted, 3 tie) and |D0|.
@@ -84,8 +85,11 @@ struct BatchParams {
 };
 
 size_t batch_smem_bytes(int maxN, int maxK, int warps, int path);
-LaunchShape batch_shape(int maxN, int maxK, int path, int warps_req, int blocks_per_sm_req, int sms, cudaError_t* err);
-cudaError_t launch_batch(const BatchParams& p, const LaunchShape& s, int path, cudaStream_t st);
+// five: every system of the launch runs the 5-D bottom stage (path PATH_NARROW, K >= 4); a
+// launch carries one stage, so a batch groups its systems by path and stage
+LaunchShape batch_shape(int maxN, int maxK, int path, bool five, int warps_req, int blocks_per_sm_req, int sms,
+                        cudaError_t* err);
+cudaError_t launch_batch(const BatchParams& p, const LaunchShape& s, int path, bool five, cudaStream_t st);
 
 // ---- serving: a persistent kernel fed while it runs ------------------------------------------
 

@@ -91,14 +91,18 @@ extern "C" int bd_volume_noalloc(const int64_t* points, int32_t npts, int32_t k,
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaError_t e;
-  const bd::LaunchShape shape = bd::enum_shape(npts, k, path, 0, 0, sms > 0 ? sms : 1, &e);
+  bd::LaunchShape shape = bd::enum_shape(npts, k, path, false, 0, 0, sms > 0 ? sms : 1, &e);
   if (e != cudaSuccess) return bd::set_error(BD_ERR_CUDA, cudaGetErrorString(e));
+  const bool five = path == bd::PATH_NARROW && k >= 4 && bd::prefer_five(points, npts, k, (uint64_t)shape.blocks * shape.warps);
+  if (five) {  // the 5-D kernel's own occupancy
+    shape = bd::enum_shape(npts, k, path, true, 0, 0, sms > 0 ? sms : 1, &e);
+    if (e != cudaSuccess) return bd::set_error(BD_ERR_CUDA, cudaGetErrorString(e));
+  }
   // the work list must fit the array: coarsen the split until it does (the coarsest list,
   // one prefix per first index, always fits)
   const uint64_t total = bd::binom(npts, k + 1);
   uint64_t thr = std::max<uint64_t>(256, total / ((uint64_t)shape.blocks * shape.warps * 4 + 1));
   size_t nitems = 0;
-  const bool five = path == bd::PATH_NARROW && k >= 4 && bd::prefer_five(points, npts, k, (uint64_t)shape.blocks * shape.warps);
   while (!bd::build_items_into(npts, k, thr, bd::item_depth(k, path, five), g_host_items, kItemsMax, &nitems)) thr *= 4;
 
   cudaStream_t st = bd::thread_stream();
