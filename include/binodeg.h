@@ -243,18 +243,20 @@ int bd_batch_destroy(bd_batch* batch);
 
 /* ---- serving (continuous batching) ---------------------------------------------------------
  *
- * bd_server_start launches a host pump thread; one persistent kernel (relaunched on demand when
- * it has exited after ~40 ms without work) claims (slot, prefix) work items from a device ring
- * while the pump keeps appending to it.  bd_server_submit reduces a system on the caller's thread
+ * bd_server_start launches a host pump thread; one persistent kernel (launched on demand, gone
+ * after ~40 ms without work) claims (slot, prefix) work items from a device ring, one ticket per
+ * warp by fetch-and-add, while the pump keeps appending to it.  bd_server_submit reduces a system on the caller's thread
  * and queues it; the pump admits queued systems into free slots whenever the device budget
  * allows (a slot, ring room, and at most max_inflight_items items in flight), in arrival order
  * (order 0) or by smallest predicted cost (order 1; predicted_cost from the cost model, or <= 0
  * for the closed-form bound).  Admitted systems' items interleave on the device with those of
  * systems already running.  Finished degrees are returned by bd_server_poll with their latency
- * from submission.  Results are identical to bd_degree's.  Systems that the persistent kernel does
- * not carry (128-bit minors, dimension above 10, more than 64 points: up to 126 variables are
- * accepted, as by bd_degree) are served by a side worker thread that runs bd_degree's volume
- * path, in arrival order, on a stream of its own beside the persistent kernel.
+ * from submission.  Results are identical to bd_degree's.  The persistent kernel carries systems
+ * of at most 32 points (31 variables) and dimension 10 whose minors fit 64 bits (its per-warp
+ * shared memory is sized for them: 8 warps per SM, leaving room for other kernels); the others
+ * (128-bit minors, dimension above 10, more points: up to 126 variables are accepted, as by
+ * bd_degree) are served by a side worker thread that runs bd_degree's volume path, in arrival
+ * order, on a stream of its own beside the persistent kernel.
  *
  * Every work item is published with a stamp (its ticket) written after it; a warp that claims
  * a ticket waits for the stamp, at most publish_wait_ms.  When that bound runs out the kernel

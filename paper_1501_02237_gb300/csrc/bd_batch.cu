@@ -241,7 +241,8 @@ void build_batch_items(bd_batch* b, const std::vector<int>& active, const float*
       const double c = cost ? std::max(1e-9, (double)cost[i]) : closed_form_cost(s);
       const double per_subset = c / std::max(1.0, sub);
       uint64_t thr = (uint64_t)std::max(64.0, std::min(4e9, target / per_subset));
-      for (const bd::Item& it : bd::build_items(s.N, s.K, thr, bd::item_depth(s.K, s.path, s.five))) {
+      // generation order: the items of every system are ordered by predicted cost below
+      for (const bd::Item& it : bd::build_items(s.N, s.K, thr, bd::item_depth(s.K, s.path, s.five), false)) {
         bd::BatchItem x{};
         x.sys = (uint32_t)i;
         x.len = it.len;

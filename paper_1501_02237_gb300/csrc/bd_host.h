@@ -55,7 +55,8 @@ bool prefer_five(const int64_t* points, int npts, int k, uint64_t teams);
 // sorted by decreasing size.  With depth = k-3 (the 5-D stage), an item of that length holding
 // more than 16 times `max_subsets` is split once more (length k-2: its last index is then the
 // first point of the quadruples it takes).
-std::vector<Item> build_items(int npts, int k, uint64_t max_subsets, int depth);
+// sorted = false: in generation (lexicographic) order, for callers that order items themselves.
+std::vector<Item> build_items(int npts, int k, uint64_t max_subsets, int depth, bool sorted = true);
 
 // The work-item split threshold for a launch of `teams` warps over `total` subsets: fine enough
 // for the packing of ranges (1/32 of a warp's share), between 64 and 2^20 subsets.

@@ -422,19 +422,22 @@ cudaError_t launch_batch(const BatchParams& p, const LaunchShape& s, int path, b
 
 namespace {
 
-// One warp processes one item of a slot with the walker of that slot's integer path.  The
-// shared-memory region is laid out for the int64 path (the larger); the int32 path uses the
-// same bytes.
-template <class TC, class TL>
-__device__ void serve_item(WarpTeam& tm, const int64_t* P, int N, int K, int slots, unsigned char* stack, int maxK,
-                           const Item& it, Acc& acc, const uint32_t* tri, bool five) {
-  TC* sc = reinterpret_cast<TC*>(stack);
-  TL* sl = reinterpret_cast<TL*>(stack + align16((size_t)slots * stack_entries(maxK) * sizeof(int64_t)));
-  float* fl = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(sl) + align16((size_t)slots * maxK * sizeof(int64_t)));
-  Walker<TC, TL, WarpTeam> W(tm, P, N, K, slots, sc, sl, fl, uniform_after(fl, slots));
+// One item of a request with the walker of its integer path (32- or 64-bit coordinate minors),
+// starting from the prefix levels the warp built for the same system (valid, lo, hi), which are
+// updated for the next item.
+template <class TC>
+__device__ void serve_item(WarpTeam& tm, const int64_t* P, int N, int K, int slots, unsigned char* sc, int64_t* sl,
+                           float* fl, const Item& it, Acc& acc, const uint32_t* tri, bool five, int& valid,
+                           uint64_t& lo, uint64_t& hi) {
+  Walker<TC, int64_t, WarpTeam> W(tm, P, N, K, slots, reinterpret_cast<TC*>(sc), sl, fl, uniform_after(fl, slots));
   W.tri = tri;
   W.use5 = five;
+  W.valid = valid;
+  W.s = Idx15{lo, hi};
   W.run_item(it, acc);
+  valid = W.valid;
+  lo = W.s.lo;
+  hi = W.s.hi;
 }
 
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
@@ -443,100 +446,150 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
   return t;
 }
 
+// Persistent: every warp takes the next ticket by fetch-and-add (no retries, so claims do not
+// contend however many warps wait) and waits, napping, until the host has published it.  The
+// unpublished tickets are always the top ones, [tail, head); once nothing has been published for
+// idle_ns, a waiting warp gives its ticket back when every later ticket has been given back
+// (head == ticket + 1, by compare-and-swap) and exits, so an idle kernel leaves the GPU with
+// head == tail and the next launch claims from there.  A given-back ticket published in the meantime
+// is claimed again (head moved below it), never processed twice.  Consecutive items of one
+// request (same slot, admission and lifting) keep the warp's points in shared memory and the
+// walker's built prefix levels.
 __global__ void BD_ENUM_BOUNDS k_serve(ServeParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int slots = slots_of(p.maxN);
   const size_t pbytes = align16((size_t)(p.maxK + 1) * p.maxN * sizeof(int64_t));
+  // each warp's region is laid out for the 64-bit coordinate path (the larger stack); the 32-bit
+  // path uses the front of the same bytes
   unsigned char* base = smem + (size_t)warp * (pbytes + warp_bytes<int64_t, int64_t>(slots, p.maxK));
   int64_t* P = reinterpret_cast<int64_t*>(base);
-  unsigned char* stack = base + pbytes;
+  unsigned char* sc = base + pbytes;
+  int64_t* sl = reinterpret_cast<int64_t*>(sc + align16((size_t)slots * stack_entries(p.maxK) * sizeof(int64_t)));
+  float* fl = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(sl) + align16((size_t)slots * p.maxK * sizeof(int64_t)));
   WarpTeam tm;
-  unsigned long long idle = 0;
+  // the system whose points and prefix states this warp holds
+  int cur_slot = -1, cur_gen = 0;
+  uint64_t cur_seed = 0;
+  int pv_valid = 0;
+  uint64_t pv_lo = 0, pv_hi = 0;
   for (;;) {
-    unsigned long long got = ~0ull;
+    unsigned long long got = 0;
     int quit = 0;
     if (lane == 0) {
-      const unsigned long long h = *(volatile unsigned long long*)p.head;
-      const unsigned long long t = *p.tail;
-      if (*(volatile unsigned long long*)p.fault_dev) {
-        quit = 1;  // a publication wait ran out: every warp leaves and the host resets the ring
-      } else if (h < t) {
-        if (atomicCAS(p.head, h, h + 1) == h) got = h;
-      } else if (*p.stop || ++idle > p.idle_spins) {
-        quit = 1;
-      } else {
-        __nanosleep(2000);
+      got = atomicAdd(p.head, 1ull);
+      unsigned nap = 128;
+      unsigned long long seen = *p.tail, t_seen = globaltimer_ns();
+      for (;;) {
+        if (*(volatile unsigned long long*)p.fault_dev) {
+          quit = 1;  // a publication wait ran out: every warp leaves and the host resets the ring
+          break;
+        }
+        const unsigned long long tail = *p.tail;
+        if (got < tail) break;
+        if (*p.stop) {
+          quit = 1;
+          break;
+        }
+        // idle means no publication at all for idle_ns (not just this ticket's wait), so that
+        // warps do not leave one by one while work still flows
+        const unsigned long long now = globaltimer_ns();
+        if (tail != seen) {
+          seen = tail;
+          t_seen = now;
+        } else if (now - t_seen > p.idle_ns && atomicCAS(p.head, got + 1, got) == got + 1) {
+          quit = 1;  // the ticket is given back
+          break;
+        }
+        __nanosleep(nap);
+        nap = nap < 8192 ? 2 * nap : nap;
       }
     }
     got = __shfl_sync(0xffffffffu, got, 0);
     quit = __shfl_sync(0xffffffffu, quit, 0);
     if (quit) break;
-    if (got == ~0ull) continue;
-    idle = 0;
     __threadfence();  // the item and its slot were published before the tail
-    // The item's publication stamp (written after the item, before the tail) confirms that the
-    // ring position holds this ticket's item.  It is normally there already; the wait for it is
-    // bounded, and when the bound runs out the warp records the ticket and leaves without
-    // touching the item (the host fails its request and resets the ring).
-    int lost = 0;
-    if (lane == 0) {
-      const unsigned long long want = got + 1;
-      const volatile unsigned long long* sp = p.seq + (got % p.ring_cap);
-      if (*sp != want) {
-        const unsigned long long t0 = globaltimer_ns();
-        while (*sp != want) {
-          if (globaltimer_ns() - t0 > p.wait_ns) {
-            lost = 1;
-            break;
+    {
+      const unsigned long long tk = got;
+      int lost = 0;
+      // The item's publication stamp (written after the item, before the tail) confirms that the
+      // ring position holds this ticket's item.  It is normally there already; the wait for it is
+      // bounded, and when the bound runs out the warp records the ticket and leaves without
+      // touching the item (the host fails its request and resets the ring).
+      if (lane == 0) {
+        const unsigned long long want = tk + 1;
+        const volatile unsigned long long* sp = p.seq + (tk % p.ring_cap);
+        if (*sp != want) {
+          const unsigned long long t0 = globaltimer_ns();
+          while (*sp != want) {
+            if (globaltimer_ns() - t0 > p.wait_ns) {
+              lost = 1;
+              break;
+            }
+            __nanosleep(1000);
           }
-          __nanosleep(1000);
+        }
+        if (lost && atomicCAS(p.fault_dev, 0ull, want) == 0ull) {
+          *p.fault_host = want;
+          __threadfence_system();
         }
       }
-      if (lost && atomicCAS(p.fault_dev, 0ull, want) == 0ull) {
-        *p.fault_host = want;
-        __threadfence_system();
-      }
-    }
-    lost = __shfl_sync(0xffffffffu, lost, 0);
-    if (lost) break;
-    __threadfence();
-    const volatile unsigned int* rp = reinterpret_cast<const volatile unsigned int*>(p.ring + (got % p.ring_cap));
-    BatchItem bi;
-    unsigned int* bw = reinterpret_cast<unsigned int*>(&bi);
-    for (int t = 0; t < 4; ++t) bw[t] = rp[t];
-    const int slot = (int)bi.sys;
-    // a slot is reused for other systems and liftings: its descriptor and points are read past L1
-    const unsigned long long* dw = reinterpret_cast<const unsigned long long*>(p.desc + slot);
-    BatchDesc d;
-    unsigned long long* dd = reinterpret_cast<unsigned long long*>(&d);
-    for (int t = 0; t < (int)(sizeof(BatchDesc) / 8); ++t) dd[t] = __ldcg(dw + t);
-    const int N = d.N, K = d.K, path = d.path;
-    __syncwarp();
-    for (int t = lane; t < N * K; t += 32) {
-      const int q = t / K, c = t - q * K;
-      P[c * N + q] = __ldcg(p.pts + (size_t)slot * BD_SERVE_PTS + t);
-    }
-    for (int q = lane; q < N; q += 32) P[K * N + q] = lift_height(d.lift_seed, q);
-    __syncwarp();
-    Item it{};
-    it.len = bi.len;
-    for (int t = 0; t < bi.len; ++t) it.idx[t] = bi.idx[t];
-    Acc acc{};
-    const long long t0 = clock64();
-    if (path == PATH_NARROW) serve_item<int32_t, int64_t>(tm, P, N, K, slots, stack, p.maxK, it, acc, p.tri, d.five != 0);
-    else serve_item<int64_t, int64_t>(tm, P, N, K, slots, stack, p.maxK, it, acc, p.tri, false);
-    const unsigned long long cyc = (unsigned long long)(clock64() - t0);
-    acc = warp_sum(acc);
-    if (lane == 0) {
-      flush(acc, p.acc + slot, 1);
-      atomicAdd(p.cycles + slot, cyc);
+      lost = __shfl_sync(0xffffffffu, lost, 0);
+      if (lost) break;
       __threadfence();
-      if (atomicSub(p.remaining + slot, 1u) == 1u) {  // the slot's last item: publish its completion
+      const volatile unsigned int* rp = reinterpret_cast<const volatile unsigned int*>(p.ring + (tk % p.ring_cap));
+      BatchItem bi;
+      unsigned int* bw = reinterpret_cast<unsigned int*>(&bi);
+      for (int t = 0; t < 4; ++t) bw[t] = rp[t];
+      const int slot = (int)bi.sys;
+      // a slot is reused for other systems and liftings: its descriptor and points are read past L1
+      const unsigned long long* dw = reinterpret_cast<const unsigned long long*>(p.desc + slot);
+      BatchDesc d;
+      unsigned long long* dd = reinterpret_cast<unsigned long long*>(&d);
+      for (int t = 0; t < (int)(sizeof(BatchDesc) / 8); ++t) dd[t] = __ldcg(dw + t);
+      const int N = d.N, K = d.K;
+      const bool same = slot == cur_slot && d.gen == cur_gen && d.lift_seed == cur_seed;
+      if (!same) {
+        __syncwarp();  // the previous system's readers are done
+        for (int t = lane; t < N * K; t += 32) {
+          const int q = t / K, c = t - q * K;
+          P[c * N + q] = __ldcg(p.pts + (size_t)slot * BD_SERVE_PTS + t);
+        }
+        for (int q = lane; q < N; q += 32) P[K * N + q] = lift_height(d.lift_seed, q);
+        __syncwarp();
+        cur_slot = slot;
+        cur_gen = d.gen;
+        cur_seed = d.lift_seed;
+        pv_valid = 0;
+      }
+      Item it{};
+      it.len = bi.len;
+      for (int t = 0; t < bi.len; ++t) it.idx[t] = bi.idx[t];
+      Acc acc{};
+      const long long t0 = clock64();
+      if (d.path == PATH_NARROW)
+        serve_item<int32_t>(tm, P, N, K, slots, sc, sl, fl, it, acc, p.tri, d.five != 0, pv_valid, pv_lo, pv_hi);
+      else
+        serve_item<int64_t>(tm, P, N, K, slots, sc, sl, fl, it, acc, p.tri, false, pv_valid, pv_lo, pv_hi);
+      const unsigned long long cyc = (unsigned long long)(clock64() - t0);
+      acc = warp_sum(acc);
+      if (lane == 0) {
+        flush(acc, p.acc + slot, 1);
+        atomicAdd(p.cycles + slot, cyc);
         __threadfence();
-        const unsigned long long i = atomicAdd(p.comp_count, 1ull);
-        p.comp[i % p.comp_cap] = ((i + 1) << 32) | (unsigned long long)(unsigned)slot;
-        __threadfence_system();
+        if (atomicSub(p.remaining + slot, 1u) == 1u) {  // the slot's last item: publish its completion
+          __threadfence();
+          // the slot's sums (every other item's atomics are done) into host-mapped memory, so
+          // that the host reads the result without a copy
+          const unsigned long long* a = reinterpret_cast<const unsigned long long*>(p.acc + slot);
+          volatile unsigned long long* out = p.res + (size_t)slot * kServeResWords;
+          for (int w = 0; w < (int)(sizeof(DevAcc) / 8); ++w) out[w] = __ldcg(a + w);
+          out[sizeof(DevAcc) / 8] = __ldcg(p.cycles + slot);
+          __threadfence_system();
+          const unsigned long long i = atomicAdd(p.comp_count, 1ull);
+          p.comp[i % p.comp_cap] = ((i + 1) << 32) | (unsigned long long)(unsigned)slot;
+          __threadfence_system();
+        }
       }
     }
   }
@@ -566,7 +619,7 @@ LaunchShape serve_shape(int maxN, int maxK, int warps_req, int blocks_per_sm_req
   if (per_sm <= 0) {
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_serve, warps * 32, s.smem);
     if (e != cudaSuccess) { *err = e; return s; }
-    per_sm = per_sm > 1 ? per_sm - 1 : 1;  // leave room for other kernels (cost-model inference)
+    per_sm = per_sm > 2 ? per_sm - 1 : per_sm;  // leave room for other kernels (the side route, the cost model)
   }
   s.blocks = per_sm * sms;
   return s;

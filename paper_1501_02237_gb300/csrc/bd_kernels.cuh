@@ -62,8 +62,10 @@ struct BatchDesc {       // one system of a batch
   int pts_off;           // offset of its N x K coordinates in the packed point array
   int path;
   int five;              // 1: the 5-D bottom stage on the 32-bit coordinate path (K >= 4)
+  int gen;               // serving: the admission that holds the slot (a slot is reused)
   uint64_t lift_seed;    // stream seed of its current lifting
 };
+static_assert(sizeof(BatchDesc) % 8 == 0, "descriptors are read as 64-bit words");
 
 struct BatchItem {       // a prefix of one system's subset tree
   uint32_t sys;
@@ -98,16 +100,20 @@ struct ServeParams {
   const int64_t* pts;               // per slot: BD_NMAX x BATCH_KMAX coordinates (device)
   const BatchItem* ring;            // work items, index = ticket % ring_cap (device)
   unsigned long long ring_cap;
-  unsigned long long* head;         // next ticket to claim (device, claimed by CAS)
+  unsigned long long* head;         // next ticket to claim (device, fetch-and-add)
   const volatile unsigned long long* tail;  // tickets below tail are published (device, host-written)
   unsigned int* remaining;          // per slot: items not yet finished (device)
   DevAcc* acc;                      // per slot (device)
   unsigned long long* cycles;       // per slot (device)
   unsigned long long* comp_count;   // completions so far (device)
   volatile unsigned long long* comp; // completion records (host-mapped): (sequence << 32) | slot
+  volatile unsigned long long* res;  // per slot (host-mapped): its final DevAcc words and SM cycles,
+                                     // written before the slot's completion record
   unsigned long long comp_cap;
-  const volatile int* stop;         // host-mapped: 1 asks the kernel to exit
-  unsigned long long idle_spins;    // idle polls before a warp exits (the host relaunches on demand)
+  const volatile int* stop;         // device: 1 asks every warp waiting for an unpublished
+                                    // ticket to exit (server stop)
+  unsigned long long idle_ns;       // after this long without a publication, waiting warps give
+                                    // their tickets back and exit (the host relaunches on demand)
   const volatile unsigned long long* seq;  // per ring position: ticket + 1 once its item is published (device)
   unsigned long long* fault_dev;    // device: ticket + 1 of the first item whose publication wait ran out
   volatile unsigned long long* fault_host;  // host-mapped copy of fault_dev for the host's pump
@@ -116,6 +122,7 @@ struct ServeParams {
   const uint32_t* tri;              // colex decode table (device) or nullptr
 };
 
+constexpr int kServeResWords = sizeof(DevAcc) / 8 + 1;  // ServeParams.res words per slot
 size_t serve_smem_bytes(int maxN, int maxK, int warps);
 LaunchShape serve_shape(int maxN, int maxK, int warps_req, int blocks_per_sm_req, int sms, cudaError_t* err);
 cudaError_t launch_serve(const ServeParams& p, const LaunchShape& s, cudaStream_t st);

@@ -15,10 +15,12 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <map>
 #include <mutex>
 #include <new>
 #include <string>
 #include <thread>
+#include <tuple>
 #include <vector>
 
 #include "../../include/binodeg.h"
@@ -65,7 +67,7 @@ struct bd_server {
   bd_server_opts opts{};
   int slots = 0;
   uint64_t ring_cap = 0, comp_cap = 0;
-  int maxN = BD_NMAX, maxK = 10;
+  int maxN = 32, maxK = 10;  // the systems the persistent kernel carries (its shared-memory layout)
   bd::LaunchShape shape;
   const uint32_t* tri = nullptr;  // the device's colex decode table
   // device
@@ -81,8 +83,7 @@ struct bd_server {
   // host-mapped
   volatile unsigned long long* h_comp = nullptr;
   unsigned long long* d_comp = nullptr;
-  volatile int* h_stop = nullptr;
-  int* d_stop = nullptr;
+  int* d_stop = nullptr;  // device word: 1 asks the kernel's waiting warps to exit (server stop)
   unsigned long long* d_seq = nullptr;           // per ring position: ticket + 1 once published
   unsigned long long* h_seq = nullptr;           // pinned mirror of the stamps
   unsigned long long* d_fault = nullptr;         // device fault word (see ServeParams)
@@ -94,9 +95,10 @@ struct bd_server {
   int64_t* h_pts = nullptr;          // per slot
   unsigned int* h_rem = nullptr;     // per slot
   bd::BatchItem* h_ring = nullptr;   // mirror of the ring
-  unsigned long long* h_tail = nullptr;
-  bd::DevAcc* h_acc = nullptr;       // one slot's result
-  unsigned long long* h_cyc = nullptr;
+  unsigned long long* h_tails = nullptr;   // tail values, one per publication (kTailStage entries)
+  uint64_t publications = 0;
+  volatile unsigned long long* h_res = nullptr;  // host-mapped: per slot, the kernel's final sums
+  unsigned long long* d_res = nullptr;
   cudaStream_t s_kernel = nullptr, s_ctl = nullptr, s_side = nullptr;
   int device = 0;
   // host state
@@ -109,6 +111,8 @@ struct bd_server {
   int64_t next_ticket = 0;
   std::atomic<bool> running{false};
   bool kernel_live = false;
+  // work lists by (N, K, integer path, 5-D stage), built once (pump thread, under mu)
+  std::map<std::tuple<int, int, int, bool>, std::vector<bd::BatchItem>> item_cache;
   std::thread pump;
   // side route: a queue served by its own thread and stream
   std::deque<Req*> side_q;
@@ -126,6 +130,8 @@ int cu(cudaError_t e, const char* what) {
   return e == cudaSuccess ? BD_OK : bd::cuda_error(e, what);
 }
 
+constexpr uint64_t kTailStage = 1024;  // staged tail values (see publish)
+
 // publish one request's items (it already owns a slot) and its slot state
 int publish(bd_server* s, Req* r) {
   const int slot = r->slot;
@@ -135,6 +141,7 @@ int publish(bd_server* s, Req* r) {
   d.pts_off = 0;
   d.path = r->path;
   d.five = r->five ? 1 : 0;
+  d.gen = (int)r->admission;
   d.lift_seed = bd::lift_stream_seed(r->seed, (uint32_t)r->attempt);
   std::memcpy(s->h_pts + (size_t)slot * bd::BD_SERVE_PTS, r->pts.data(), sizeof(int64_t) * r->pts.size());
   s->h_rem[slot] = (unsigned)r->items.size();
@@ -169,27 +176,53 @@ int publish(bd_server* s, Req* r) {
     if (e == cudaSuccess && n > first)
       e = cudaMemcpyAsync(s->d_seq, s->h_seq, sizeof(unsigned long long) * (n - first), cudaMemcpyHostToDevice, s->s_ctl);
   }
+  // Every staging buffer is pinned and owned by the slot or the ring position until the request
+  // completes, except the tail value: each publication copies its own entry of a small ring of
+  // them, and every half turn of that ring waits for the copies in flight, so that no entry is
+  // rewritten before its copy has run.  The pump thus never waits for a publication.
   s->tail += n;
-  *s->h_tail = s->tail;
-  if (e == cudaSuccess) e = cudaMemcpyAsync(s->d_tail, s->h_tail, sizeof(unsigned long long), cudaMemcpyHostToDevice, s->s_ctl);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s->s_ctl);  // staging may be reused afterwards
+  const uint64_t ti = s->publications++ % kTailStage;
+  if (ti % (kTailStage / 2) == 0 && e == cudaSuccess) e = cudaStreamSynchronize(s->s_ctl);
+  s->h_tails[ti] = s->tail;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(s->d_tail, s->h_tails + ti, sizeof(unsigned long long), cudaMemcpyHostToDevice, s->s_ctl);
   s->ring_used += n;
   s->inflight_items += n;
   return cu(e, "publish");
 }
 
 void build_request_items(bd_server* s, Req* r) {
+  // the list depends only on (N, K, integer path, stage) for a given server: built once
+  const auto key = std::make_tuple(r->N, r->K, r->path, r->five);
+  auto hit = s->item_cache.find(key);
+  if (hit != s->item_cache.end()) {
+    r->items = hit->second;
+    return;
+  }
   const uint64_t sub = bd::binom(r->N, r->K + 1);
   const uint64_t warps = (uint64_t)s->shape.blocks * s->shape.warps;
-  const uint64_t want = std::max<uint64_t>(1, warps / 2);  // enough items to spread one system over the GPU
+  // eight items per resident warp: enough to spread one system over the GPU with balance
+  const uint64_t want = std::max<uint64_t>(1, 8 * warps);
   uint64_t thr = std::max<uint64_t>(s->opts.item_subsets > 0 ? (uint64_t)s->opts.item_subsets : 256, sub / want);
+  // a request must fit the ring and the in-flight limit on an idle device, or it would wait
+  // forever: the split is coarsened until it does (the coarsest list, one item per first index,
+  // has at most 64 items; the ring holds at least 1024)
+  const uint64_t limit = s->opts.max_inflight_items > 0 ? std::min<uint64_t>(s->ring_cap, (uint64_t)s->opts.max_inflight_items)
+                                                        : s->ring_cap;
+  std::vector<bd::Item> list;
+  for (;;) {
+    list = bd::build_items(r->N, r->K, thr, bd::item_depth(r->K, r->path, r->five));
+    if (list.size() <= limit || thr >= sub) break;
+    thr *= 2;
+  }
   r->items.clear();
-  for (const bd::Item& it : bd::build_items(r->N, r->K, thr, bd::item_depth(r->K, r->path, r->five))) {
+  for (const bd::Item& it : list) {
     bd::BatchItem x{};
     x.len = it.len;
     for (int t = 0; t < it.len && t < 11; ++t) x.idx[t] = it.idx[t];
     r->items.push_back(x);
   }
+  if (s->item_cache.size() >= 4096) s->item_cache.clear();
+  s->item_cache[key] = r->items;
 }
 
 void finish(bd_server* s, Req* r) {
@@ -212,33 +245,39 @@ bool take_completions(bd_server* s) {
     s->comp_read += 1;
     progress = true;
     Req* r = s->in_slot[slot];
-    cudaError_t e = cudaMemcpyAsync(s->h_acc, s->d_acc + slot, sizeof(bd::DevAcc), cudaMemcpyDeviceToHost, s->s_ctl);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(s->h_cyc, s->d_cycles + slot, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s->s_ctl);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s->s_ctl);
+    // the slot's sums, written by the kernel to host-mapped memory before the record
+    std::atomic_thread_fence(std::memory_order_acquire);
+    bd::DevAcc acc;
+    unsigned long long* aw = reinterpret_cast<unsigned long long*>(&acc);
+    const volatile unsigned long long* src = s->h_res + (size_t)slot * bd::kServeResWords;
+    for (size_t w = 0; w < sizeof(bd::DevAcc) / 8; ++w) aw[w] = src[w];
+    const unsigned long long cyc = src[sizeof(bd::DevAcc) / 8];
+    const bd::DevAcc* a = &acc;
+    cudaError_t e = cudaSuccess;
     s->ring_used -= r->items.size();
     s->inflight_items -= r->items.size();
     if (e != cudaSuccess) {
       r->status = BD_ERR_CUDA;
-    } else if (s->h_acc->ties && r->attempt < 7) {  // re-lift in the same slot
+    } else if (a->ties && r->attempt < 7) {  // re-lift in the same slot
       r->attempt += 1;
       s->stats.relifted += 1;
       if (publish(s, r) != BD_OK) r->status = BD_ERR_CUDA;
       else continue;
-    } else if (s->h_acc->ties) {
+    } else if (a->ties) {
       r->status = BD_ERR_TIES;
-    } else if (s->h_acc->items_done != r->items.size()) {
+    } else if (a->items_done != r->items.size()) {
       r->status = BD_ERR_CUDA;
     } else {
-      const u128 nvol = ((u128)s->h_acc->nvol_hi << 64) | s->h_acc->nvol_lo;
+      const u128 nvol = ((u128)a->nvol_hi << 64) | a->nvol_lo;
       const u128 deg = nvol * (u128)r->torsion;
       r->out.nvol_lo = (uint64_t)nvol;
       r->out.nvol_hi = (uint64_t)(nvol >> 64);
       r->out.degree_lo = (uint64_t)deg;
       r->out.degree_hi = (uint64_t)(deg >> 64);
-      r->out.cells = s->h_acc->cells;
+      r->out.cells = a->cells;
       r->out.relifts = r->attempt;
       r->out.flags = nvol == 0 ? BD_FLAG_DEGENERATE : 0;
-      r->cycles = *s->h_cyc;
+      r->cycles = cyc;
     }
     s->in_slot[slot] = nullptr;
     s->free_slots.push_back(slot);
@@ -378,8 +417,9 @@ bool pump_once(bd_server* s) {
       p.comp_count = s->d_comp_count;
       p.comp = s->d_comp;
       p.comp_cap = s->comp_cap;
+      p.res = s->d_res;
       p.stop = s->d_stop;
-      p.idle_spins = 20000;  // ~40 ms of 2 us naps without work, then the warps exit
+      p.idle_ns = 40000000ull;  // ~40 ms without a publication: waiting warps give their tickets back
       p.seq = s->d_seq;
       p.fault_dev = s->d_fault;
       p.fault_host = s->d_fault_map;
@@ -457,14 +497,13 @@ void release(bd_server* s) {
   cudaFreeHost((void*)s->h_fault);
   cudaFreeHost(s->h_seq);
   cudaFreeHost((void*)s->h_comp);
-  cudaFreeHost((void*)s->h_stop);
+  cudaFree(s->d_stop);
   cudaFreeHost(s->h_desc);
   cudaFreeHost(s->h_pts);
   cudaFreeHost(s->h_rem);
   cudaFreeHost(s->h_ring);
-  cudaFreeHost(s->h_tail);
-  cudaFreeHost(s->h_acc);
-  cudaFreeHost(s->h_cyc);
+  cudaFreeHost(s->h_tails);
+  cudaFreeHost((void*)s->h_res);
   if (s->s_kernel) cudaStreamDestroy(s->s_kernel);
   if (s->s_ctl) cudaStreamDestroy(s->s_ctl);
   if (s->s_side) cudaStreamDestroy(s->s_side);
@@ -522,22 +561,22 @@ int bd_server_start(const bd_server_opts* opts, bd_server** out) {
   A(cudaHostAlloc((void**)&s->h_fault, sizeof(unsigned long long), cudaHostAllocMapped));
   A(cudaMallocHost(&s->h_seq, sizeof(unsigned long long) * s->ring_cap));
   A(cudaHostAlloc((void**)&s->h_comp, sizeof(unsigned long long) * s->comp_cap, cudaHostAllocMapped));
-  A(cudaHostAlloc((void**)&s->h_stop, sizeof(int), cudaHostAllocMapped));
+  A(bd::dev_malloc(&s->d_stop, sizeof(int)));
   A(cudaMallocHost(&s->h_desc, sizeof(bd::BatchDesc) * s->slots));
   A(cudaMallocHost(&s->h_pts, sizeof(int64_t) * bd::BD_SERVE_PTS * s->slots));
   A(cudaMallocHost(&s->h_rem, sizeof(unsigned) * s->slots));
   A(cudaMallocHost(&s->h_ring, sizeof(bd::BatchItem) * s->ring_cap));
-  A(cudaMallocHost(&s->h_tail, sizeof(unsigned long long)));
-  A(cudaMallocHost(&s->h_acc, sizeof(bd::DevAcc)));
-  A(cudaMallocHost(&s->h_cyc, sizeof(unsigned long long)));
+  A(cudaMallocHost(&s->h_tails, sizeof(unsigned long long) * kTailStage));
+  A(cudaHostAlloc((void**)&s->h_res, sizeof(unsigned long long) * bd::kServeResWords * s->slots, cudaHostAllocMapped));
   A(cudaStreamCreateWithFlags(&s->s_kernel, cudaStreamNonBlocking));
   A(cudaStreamCreateWithFlags(&s->s_ctl, cudaStreamNonBlocking));
   A(cudaStreamCreateWithFlags(&s->s_side, cudaStreamNonBlocking));
   if (rc == BD_OK) {
     std::memset((void*)s->h_comp, 0, sizeof(unsigned long long) * s->comp_cap);
-    *s->h_stop = 0;
+    A(cudaMemset(s->d_stop, 0, sizeof(int)));
     A(cudaHostGetDevicePointer((void**)&s->d_comp, (void*)s->h_comp, 0));
-    A(cudaHostGetDevicePointer((void**)&s->d_stop, (void*)s->h_stop, 0));
+    A(cudaHostGetDevicePointer((void**)&s->d_res, (void*)s->h_res, 0));
+
     *s->h_fault = 0;
     A(cudaHostGetDevicePointer((void**)&s->d_fault_map, (void*)s->h_fault, 0));
     A(cudaMemset(s->d_seq, 0, sizeof(unsigned long long) * s->ring_cap));
@@ -607,7 +646,8 @@ int bd_server_submit(bd_server* s, const int64_t* A, int32_t n, int32_t m, const
       r->alone5 = narrow && (stage == 5 || (stage == 0 && bd::prefer_five(red.points.data(), r->N, r->K,
                                                                          (uint64_t)s->shape.blocks * s->shape.warps)));
       r->pooled5 = narrow && (stage == 5 || (stage == 0 && bd::prefer_five(red.points.data(), r->N, r->K, 0)));
-      // the persistent kernel carries the int32 and int64 walkers; 128-bit systems take the side route
+      // the persistent kernel carries the 32- and 64-bit coordinate walkers; 128-bit systems take
+      // the side route
       side = r->path < 0 || r->path == bd::PATH_WIDE;
     }
     if (!side) {
@@ -678,7 +718,9 @@ int bd_server_stop(bd_server* s) {
   }
   s->side_cv.notify_all();
   if (s->side_worker.joinable()) s->side_worker.join();  // and the side route's queue
-  *s->h_stop = 1;
+  const int one = 1;  // the copy engine delivers the flag while the kernel runs
+  cudaMemcpyAsync(s->d_stop, &one, sizeof(one), cudaMemcpyHostToDevice, s->s_ctl);
+  cudaStreamSynchronize(s->s_ctl);
   cudaStreamSynchronize(s->s_kernel);
   release(s);
   delete s;

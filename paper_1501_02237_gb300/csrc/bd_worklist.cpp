@@ -47,7 +47,8 @@ bool for_each_item(int N, int K, uint64_t max_subsets, int depth, Emit emit) {
   }
 }
 
-// largest subtree first; ties broken by the prefix itself, so the order is a total order
+// largest subtree first; ties broken by the prefix itself, so the order is a total order (the
+// same order build_items produces; used where no allocation is allowed)
 struct ItemOrder {
   int N, K;
   bool operator()(const Item& a, const Item& b) const {
@@ -113,14 +114,26 @@ bool prefer_five(const int64_t* points, int npts, int k, uint64_t teams) {
 
 int item_depth(int K, int path, bool five) { return five && K >= 4 && path == 0 ? K - 3 : std::max(K - 2, 1); }
 
-std::vector<Item> build_items(int N, int K, uint64_t max_subsets, int depth) {
+std::vector<Item> build_items(int N, int K, uint64_t max_subsets, int depth, bool sorted) {
   std::vector<Item> items;
+  std::vector<uint64_t> size;
   for_each_item(N, K, max_subsets, depth, [&](const Item& x) {
     items.push_back(x);
+    size.push_back(subtree_size(N, K, x.idx[x.len - 1], x.len));
     return true;
   });
-  std::sort(items.begin(), items.end(), ItemOrder{N, K});
-  return items;
+  if (!sorted) return items;
+  // largest subtree first, then shorter prefixes; items of equal size and length keep their
+  // lexicographic generation order (a stable sort), so the order is a total order
+  std::vector<uint32_t> ord(items.size());
+  for (uint32_t i = 0; i < ord.size(); ++i) ord[i] = i;
+  std::stable_sort(ord.begin(), ord.end(), [&](uint32_t a, uint32_t b) {
+    if (size[a] != size[b]) return size[a] > size[b];
+    return items[a].len < items[b].len;
+  });
+  std::vector<Item> out(items.size());
+  for (size_t i = 0; i < ord.size(); ++i) out[i] = items[ord[i]];
+  return out;
 }
 
 // estimated work of an item, in warp rounds of the bottom stage plus one per level step
