@@ -38,7 +38,15 @@ SECONDARY = "single_n24_k8"
 # Counters of one enumeration launch from an ncu capture of the kernel built from exactly these
 # sources: DRAM bytes (read + write), warp instructions issued and the issue-active fraction.
 # Reported only while the library sources still hash to the captured version, null otherwise.
-PROFILE = {"sources_sha256": "", "heavy_quiver_n32_k10": None, "single_n24_k8": None}
+PROFILE = {
+    "sources_sha256": "ef9c3ef8274ff30c973ba542125316f542347521edafc604975762d86e06bc72",
+    # k_enumerate<int32, int64, 5> (the 5-D stage), 388,070 items
+    "heavy_quiver_n32_k10": dict(warp_inst=2810668190, lanes_per_inst=26.12, issue_active=0.5668,
+                                 traffic=7151616 + 131584),
+    # k_enumerate<int32, int64, 4> (the 4-D stage), 53,196 items
+    "single_n24_k8": dict(warp_inst=130635601, lanes_per_inst=23.37, issue_active=0.5484,
+                          traffic=1177344 + 28672),
+}
 
 
 # the sources that determine the enumeration kernel's code and its work list
@@ -600,7 +608,10 @@ def roofline(k, subsets_per_launch, launch_ms, peak, workload, clocks_note):
              peak_kind=peak["kind"], peak_sm_mhz=peak["sm_mhz"],
              note="algorithmic int64 ops of the plain per-subset method (no scan) per second, against the "
                   f"measured {peak['kind']} issue peak (bd_issue_peak, {peak['per_sm_per_clk']:.1f} lane ops per SM "
-                  f"per cycle at {peak['sm_mhz']:.0f} MHz, of measured); {clocks_note}")
+                  f"per cycle at {peak['sm_mhz']:.0f} MHz, of measured); the walk does less than the plain method "
+                  "per subset (prefix eliminations shared by a subtree, singular subsets rejected by one "
+                  "single-precision determinant), so frac can exceed 1; the issue view (ncu lane instructions "
+                  f"per second against the same peak) is `ncu.lane_inst_frac_of_peak`; {clocks_note}")
     if prof:
         # the issue view: instructions the kernel issued (ncu) per subset and against the peak
         lane_inst = prof["warp_inst"] * prof["lanes_per_inst"]

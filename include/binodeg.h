@@ -343,8 +343,8 @@ int bd_mlp_train(bd_mlp* mlp, const float* X, const float* y, int32_t count, int
  * beyond BD_NMAX points or BD_KMAX dimensions are rejected with BD_ERR_ARG.
  *
  * The first call on each device looks up the device address of the array (a one-time set-up
- * with that device current) and keeps it for the life of the process; make that first call
- * before any stream capture.  A device reset (cudaDeviceReset) unloads the array with the
+ * with that device current) and keeps it for the life of the process.  Every call synchronizes
+ * the thread's stream, so none may be made while that stream is being captured.  A device reset (cudaDeviceReset) unloads the array with the
  * library image and makes later calls on that device invalid.  Every call shares the array and
  * the array keeps the last call's contents; the call clears what must start at zero.  Calls
  * from this process are serialized, and every call synchronizes the thread's stream before it
