@@ -1436,7 +1436,7 @@ struct Walker {
   // The quadruples of the node on state K-4 whose first point is `first` (a work item one level
   // below the node: a large node's quadruples are split this way over several warps).  The
   // triples (a1, a2, a3) after `first` are dealt in colex order, as in bottom4.
-  BD_HD void bottom5_first(Acc& acc, int first) {
+  BD_COLD void bottom5_first(Acc& acc, int first) {
     const int sd = u->piv[K - 4] < 0 ? -1 : 1;
     const uint64_t rest = (N >= 64 ? ~0ull : ((1ull << N) - 1)) & ~u->taken[K - 4];
     const int base = first + 1, R = N - base;
