@@ -39,13 +39,13 @@ SECONDARY = "single_n24_k8"
 # sources: DRAM bytes (read + write), warp instructions issued and the issue-active fraction.
 # Reported only while the library sources still hash to the captured version, null otherwise.
 PROFILE = {
-    "sources_sha256": "ef9c3ef8274ff30c973ba542125316f542347521edafc604975762d86e06bc72",
+    "sources_sha256": "c5cb0d87706b8ab08f12fb21ecdc82ec7d147a276eda50998fc568908da9dec6",
     # k_enumerate<int32, int64, 5> (the 5-D stage), 388,070 items
-    "heavy_quiver_n32_k10": dict(warp_inst=2810668190, lanes_per_inst=26.12, issue_active=0.5668,
-                                 traffic=7151616 + 131584),
+    "heavy_quiver_n32_k10": dict(warp_inst=2823111988, lanes_per_inst=26.23, issue_active=0.5736,
+                                 traffic=7769856 + 185088),
     # k_enumerate<int32, int64, 4> (the 4-D stage), 53,196 items
-    "single_n24_k8": dict(warp_inst=130635601, lanes_per_inst=23.37, issue_active=0.5484,
-                          traffic=1177344 + 28672),
+    "single_n24_k8": dict(warp_inst=130643718, lanes_per_inst=23.37, issue_active=0.5463,
+                          traffic=1175296 + 27392),
 }
 
 
