@@ -45,9 +45,10 @@ int item_depth(int k, int path, bool five);
 // GB300: where the system's items share launches with other systems (teams = 0) the 5-D stage
 // for k >= 4 (it took fewer SM cycles on every class of the uneven batch); where the system
 // fills a launch alone (teams = its resident warps), k >= 6 and at most half of 256 sampled
-// (k+1)-subsets full-dimensional (exact rank by fraction-free elimination; a fixed seed, so the
-// choice is a function of the points): mostly nonsingular systems run faster on the 4-D stage's
-// finer work list.  Allocation-free.
+// (k+1)-subsets full-dimensional (64 or 128 when at most 35 % or at least 65 % of them are; exact
+// rank by fraction-free elimination in 64 bits, so the points must be on the 32-bit coordinate
+// path; a fixed seed, so the choice is a function of the points): mostly nonsingular systems run
+// faster on the 4-D stage's finer work list.  Allocation-free.
 bool prefer_five(const int64_t* points, int npts, int k, uint64_t teams);
 
 // Prefix work list: every (k+1)-subset of {0..npts-1} lies below exactly one item; items are

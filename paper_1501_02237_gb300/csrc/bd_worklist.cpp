@@ -87,8 +87,8 @@ bool prefer_five(const int64_t* points, int npts, int k, uint64_t teams) {
     }
     for (int r = 0; r < k; ++r)
       for (int c = 0; c < k; ++c) M[r][c] = points[(size_t)idx[r + 1] * k + c] - points[(size_t)idx[0] * k + c];
-    // fraction-free elimination: every entry stays a minor of the differences (below 2^31 on the
-    // 32-bit coordinate path), products in 128 bits, divisions exact
+    // fraction-free elimination: every entry stays a minor of the differences, below 2^31 on the
+    // 32-bit coordinate path (the only one that asks), so products fit 64 bits; divisions exact
     int64_t prev = 1;
     bool nonsingular = true;
     for (int p = 0; p < k && nonsingular; ++p) {
@@ -102,12 +102,14 @@ bool prefer_five(const int64_t* points, int npts, int k, uint64_t teams) {
         for (int c = 0; c < k; ++c) std::swap(M[r][c], M[p][c]);
       for (int i = p + 1; i < k; ++i) {
         for (int c = p + 1; c < k; ++c)
-          M[i][c] = (int64_t)(((__int128)M[i][c] * M[p][p] - (__int128)M[i][p] * M[p][c]) / prev);
+          M[i][c] = (M[i][c] * M[p][p] - M[i][p] * M[p][c]) / prev;
         M[i][p] = 0;
       }
       prev = M[p][p];
     }
     full += nonsingular ? 1 : 0;
+    // a clear majority after 64 or 128 samples decides (the rule only steers speed)
+    if ((t + 1 == 64 || t + 1 == 128) && (full * 20 <= (t + 1) * 7 || full * 20 >= (t + 1) * 13)) return full * 2 <= t + 1;
   }
   return full * 2 <= kSamples;
 }
