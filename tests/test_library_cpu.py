@@ -349,3 +349,21 @@ def test_bottom_stage_argument_is_checked():
     pts = np.array([(0, 0, 0, 0), (1, 0, 0, 0), (0, 1, 0, 0), (0, 0, 1, 0), (0, 0, 0, 1), (1, 1, 1, 1)])
     with pytest.raises(bd.BinodegError):
         bd.host_volume_lifted(pts, np.arange(1, 7), bottom_stage=3)
+
+
+@pytest.mark.parametrize("k", [4, 6])
+def test_host_walker_both_stages_at_the_point_limit(k):
+    # 64 distinct points (every mask word full) and the deepest work items (5-D nodes split by the
+    # first point of their quadruples): both bottom stages give the oracle's volume
+    rng = random.Random(64 + k)
+    pts = []
+    while len(pts) < 64:
+        p = tuple(rng.randint(-3, 3) for _ in range(k))
+        if p not in pts:
+            pts.append(p)
+    ref = nvol_placing(pts)
+    lf = oracle_lifts(64, k)
+    for stage in (4, 5):
+        r = bd.host_volume_lifted(np.array(pts), np.array(lf), threads=4, item_subsets=1, bottom_stage=stage)
+        assert r["status"] == 0
+        assert r["nvol"] == ref, stage
