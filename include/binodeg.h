@@ -150,8 +150,11 @@ typedef struct {
   int32_t bottom_stage;     /* the walk's last levels on the 32-bit coordinate path (k >= 4):
                                5 = the 5-D test (a det4 per quadruple after the Bareiss level
                                k-4), 4 = the 4-D test (a det3 per triple after level k-3),
-                               0 = chosen from the point set (see bd_prefer_five); other paths
-                               and k < 4 ignore it; any other value: BD_ERR_ARG */
+                               0 = chosen from the point set: the 5-D test when k >= 6 and at
+                               most half of a fixed sample of (k+1)-subsets is full-dimensional
+                               (mostly singular systems; the 4-D test's finer work list wins
+                               otherwise); other paths and k < 4 ignore it; any other value:
+                               BD_ERR_ARG */
   int32_t reserved[2];
 } bd_plan_opts;
 
@@ -206,7 +209,9 @@ typedef struct {
   int32_t item_factor;     /* work items per resident warp; 0: 4 (or the autotuned value) */
   int32_t use_graph;       /* 1: capture the batched launches in a CUDA graph and replay it */
   int32_t autotune;        /* 1: choose warps_per_block and item_factor by timing candidates */
-  int32_t bottom_stage;    /* as in bd_plan_opts, per system (0: chosen from its points); mode 0 */
+  int32_t bottom_stage;    /* as in bd_plan_opts, per system; 0: the 5-D test for every system with
+                              k >= 4 on the 32-bit path (in a shared launch it took fewer SM
+                              cycles on every class of system); mode 0 */
   const float* cost;       /* NULL or one predicted cost per system (any positive unit) */
   int32_t reserved[4];
 } bd_batch_opts;
