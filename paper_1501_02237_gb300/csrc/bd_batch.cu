@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <atomic>
 #include <chrono>
 #include <cmath>
@@ -250,8 +251,23 @@ void build_batch_items(bd_batch* b, const std::vector<int>& active, const float*
         tmp.push_back({(double)bd::subtree_size(s.N, s.K, it.idx[it.len - 1], it.len) * per_subset, x});
       }
     }
-    std::stable_sort(tmp.begin(), tmp.end(), [](const auto& a, const auto& c) { return a.first > c.first; });
-    for (auto& t : tmp) items.push_back(t.second);
+    // largest predicted cost first, by a counting sort on quarter octaves of the cost (items
+    // within 19 % of each other keep their generation order; a comparison sort of the ~200,000
+    // items of a 4096-system batch cost more host time than the order is worth)
+    std::vector<int> key(tmp.size());
+    int kmin = INT32_MAX, kmax = INT32_MIN;
+    for (size_t t = 0; t < tmp.size(); ++t) {
+      int e = 0;
+      const double m = std::frexp(std::max(tmp[t].first, 1e-300), &e);  // m in [0.5, 1)
+      key[t] = 4 * e + (m >= 0.8408964152537145 ? 3 : m >= 0.7071067811865476 ? 2 : m >= 0.5946035575013605 ? 1 : 0);
+      kmin = std::min(kmin, key[t]);
+      kmax = std::max(kmax, key[t]);
+    }
+    std::vector<size_t> start((size_t)(kmax - kmin) + 2, 0);
+    for (size_t t = 0; t < tmp.size(); ++t) ++start[(size_t)(kmax - key[t]) + 1];
+    for (size_t b2 = 1; b2 < start.size(); ++b2) start[b2] += start[b2 - 1];
+    items.resize(g.first + tmp.size());
+    for (size_t t = 0; t < tmp.size(); ++t) items[g.first + start[(size_t)(kmax - key[t])]++] = tmp[t].second;
     g.count = items.size() - g.first;
     groups.push_back(g);
   }
