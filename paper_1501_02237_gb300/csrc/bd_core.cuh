@@ -351,11 +351,14 @@ constexpr BinomTable make_binom_table() {
 #ifdef __CUDACC__
 static __constant__ BinomTable c_binom = make_binom_table();
 #endif
+static constexpr BinomTable h_binom = make_binom_table();  // the host's copy (work-list builders)
 
 BD_HD uint64_t binom(int n, int k) {
   if (k < 0 || n < k) return 0;
 #ifdef __CUDA_ARCH__
   if (n <= NMAX && k <= KMAX + 1) return c_binom.v[n][k];
+#else
+  if (n <= NMAX && k <= KMAX + 1) return h_binom.v[n][k];
 #endif
   if (k > n - k) k = n - k;
   uint64_t r = 1;
