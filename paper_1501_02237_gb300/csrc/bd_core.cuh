@@ -333,7 +333,9 @@ struct Acc {
 };
 
 // Accumulators are per lane: uniform counts are added by lane 0 only, per-pair results by the
-// lane that decided them; the kernels sum them over the warp before flushing.
+// lane that decided them; the kernels sum them over the warp before flushing.  The kernels of
+// the 5-D stage keep the rare results of that stage (accepted cells, their |D0| and ties) in the
+// team's shared state instead (Uniform::rare), so that no register holds them during the walk.
 
 // Binomial coefficients C(n, k), n <= 64, k <= 15, by Pascal's rule at compile time; the device
 // reads them from constant memory (a division loop costs dozens of instructions per step there).
@@ -439,6 +441,7 @@ struct Uniform {
   typename DivOf<TC>::type dv[KMAX];   // exact divider by p_j (dv[0]: by 1)
   uint64_t taken[KMAX];                // taken[j]: the points s_0 .. s_j (bit q for point q)
   uint32_t queue[64];                  // the 5-D stage's nonsingular quadruples awaiting their test
+  unsigned long long rare[4];          // 5-D stage, Stage 5 kernels: sum |D0| (low, high word), cells, ties
 };
 constexpr size_t kUniformBytes = 1088;  // room for Uniform<TC> of every coordinate type
 
@@ -1258,14 +1261,17 @@ struct Walker {
   // strictly below the cell iff
   //     sign(D4) sign(p) det5(v_c0, v_c1, v_c, v_p, v_q) < 0,
   // det5 = n . v_q with n the five signed cofactors of the rows c0, c1, c, p.
-  // Phase A deals the quadruples to lanes in colex order, a warp-width per round, and decides
-  // sign(D4) (single precision with a rigorous error bound, exactly when undecided); the
-  // nonsingular ones go to the team's queue.  Phase B takes a warp-width of queued quadruples,
-  // one per lane, forms n and its error bounds and walks the points as the 4-D test does.  Most
-  // quadruples are singular, and a singular one costs its lane only the det4 of Phase A.
+  // Phase A deals the triples c1 < c < p (the three largest points of a quadruple) to lanes, a
+  // warp-width per round; each lane forms the four 3x3 minors of its triple's coordinate rows
+  // once and then, for every c0 < c1 in turn, decides sign(D4) = sign(v_c0 . minors) (single
+  // precision with a rigorous error bound, exactly when undecided); the nonsingular
+  // quadruples go to the team's queue.  The triples are taken with their smallest point c1 in
+  // descending order, so that the lanes of a round loop over similar counts of c0.  Phase B
+  // takes a warp-width of queued quadruples, one per lane, forms n and its error bounds and
+  // walks the points as the 4-D test does.  Most quadruples are singular, and a singular one
+  // costs its lane a four-term dot product of Phase A.
   // ---------------------------------------------------------------------------------------
 
-  static BD_HD uint32_t c4(int n) { return n < 4 ? 0u : (uint32_t)(n * (n - 1) * (n - 2) * (n - 3) / 24); }
   static BD_HD uint32_t c3(int n) { return n < 3 ? 0u : (uint32_t)(n * (n - 1) * (n - 2) / 6); }
 
   // colex triple of rank t (i < j < k) packed i | j << 8 | k << 16, from the decode table when
@@ -1384,50 +1390,104 @@ struct Walker {
     if (cnt && busy) cnt->pairs++;
 #endif
     if (busy && !below) {
+      int s4;
+      const W2 m = on ? (W2)0 : quad_minor(view(), c0, c1, c, p, s4);
+      if (!on && sink.out) record_cell(sink, s, K - 3, c0, c1, c, p);
+#ifdef __CUDA_ARCH__
+      if (Stage == 5) {  // into the team's shared accumulators (several lanes may decide at once)
+        if (on) {
+          atomicAdd(&u->rare[3], 1ull);
+        } else {
+          const unsigned long long lo = (unsigned long long)(uint64_t)(u128)m;
+          const unsigned long long hi = (unsigned long long)(uint64_t)((u128)m >> 64);
+          const unsigned long long old = atomicAdd(&u->rare[0], lo);
+          const unsigned long long carry = old + lo < old ? 1ull : 0ull;
+          if (hi + carry) atomicAdd(&u->rare[1], hi + carry);
+          atomicAdd(&u->rare[2], 1ull);
+        }
+      } else
+#endif
       if (on) {
         acc.ties += 1;
       } else {
         acc.cells += 1;
-        int s4;
-        const W2 m = quad_minor(view(), c0, c1, c, p, s4);
         acc.nvol += (u128)m;
-        if (sink.out) record_cell(sink, s, K - 3, c0, c1, c, p);
       }
     }
+  }
+
+
+  // the four 3x3 minors of the coordinate rows c1, c, p on state K-4 (t_abc: columns a < b < c)
+  // and their magnitude sums, the factors of D4 along the row of c0 (the same single-precision
+  // expression as d4_sign)
+  BD_HD void minors3(int c1, int c, int p, float& t123, float& t023, float& t013, float& t012, float& T123,
+                     float& T023, float& T013, float& T012) const {
+    const F4 B = ld4(fl + 8 * c1), U = ld4(fl + 8 * c), V = ld4(fl + 8 * p);
+    const float m01 = U.x * V.y - U.y * V.x, m02 = U.x * V.z - U.z * V.x, m03 = U.x * V.w - U.w * V.x;
+    const float m12 = U.y * V.z - U.z * V.y, m13 = U.y * V.w - U.w * V.y, m23 = U.z * V.w - U.w * V.z;
+    const float M01 = fabsf(U.x * V.y) + fabsf(U.y * V.x), M02 = fabsf(U.x * V.z) + fabsf(U.z * V.x);
+    const float M03 = fabsf(U.x * V.w) + fabsf(U.w * V.x), M12 = fabsf(U.y * V.z) + fabsf(U.z * V.y);
+    const float M13 = fabsf(U.y * V.w) + fabsf(U.w * V.y), M23 = fabsf(U.z * V.w) + fabsf(U.w * V.z);
+    t123 = B.y * m23 - B.z * m13 + B.w * m12;
+    t023 = B.x * m23 - B.z * m03 + B.w * m02;
+    t013 = B.x * m13 - B.y * m03 + B.w * m01;
+    t012 = B.x * m12 - B.y * m02 + B.z * m01;
+    T123 = fabsf(B.y) * M23 + fabsf(B.z) * M13 + fabsf(B.w) * M12;
+    T023 = fabsf(B.x) * M23 + fabsf(B.z) * M03 + fabsf(B.w) * M02;
+    T013 = fabsf(B.x) * M13 + fabsf(B.y) * M03 + fabsf(B.w) * M01;
+    T012 = fabsf(B.x) * M12 + fabsf(B.y) * M02 + fabsf(B.z) * M01;
   }
 
   BD_HD void bottom5(Acc& acc) {
     const int sd = u->piv[K - 4] < 0 ? -1 : 1;
     const uint64_t rest = (N >= 64 ? ~0ull : ((1ull << N) - 1)) & ~u->taken[K - 4];  // the points q to test
     const int base = s.get(K - 4) + 1, R = N - base;
-    const uint32_t total = c4(R);
+    // triples whose smallest point is not the node's first (each has c0 candidates below it):
+    // colex rank t over R-1 positions counted from the node's last point down, so that (i, j, k)
+    // is the triple c1 = base + R-1-k < c = base + R-1-j < p = base + R-1-i; the ranks ascend
+    // with k, i.e. c1 descends
+    const uint32_t total = c3(R - 1);
     const int W = tm.lanes(), lane = tm.lane();
+    const float eps = 1.9073486328125e-6f;  // 2^-19: the error bound of d4_sign
     int qlen = 0;
-    int l = 3;  // the largest index of this lane's quadruple (colex order: never decreases)
     for (uint32_t t0 = 0; t0 < total; t0 += (uint32_t)W) {
       const uint32_t t = t0 + (uint32_t)lane;
-      bool live = t < total;
-      uint32_t rec = 0;
+      const bool live = t < total;
+      int r1 = 0, c1 = base, c = base, p = base;  // r1: the number of c0 candidates (c0 < c1)
       if (live) {
-        while (c4(l + 1) <= t) ++l;
-        const uint32_t w = colex3(t - c4(l));  // the quadruple a0 < a1 < a2 < a3
-        const int a0 = base + (int)(w & 255u), a1 = base + (int)((w >> 8) & 255u), a2 = base + (int)(w >> 16);
-        const int a3 = base + l;
-        const int s4 = d4_sign(a0, a1, a2, a3);
-        if (s4 == 0) {
-          acc.singular += 1;
-          live = false;
-        } else {
-          rec = (uint32_t)a0 | (uint32_t)a1 << 6 | (uint32_t)a2 << 12 | (uint32_t)a3 << 18 | (s4 < 0 ? 1u << 31 : 0u);
-        }
+        const uint32_t w = colex3(t);
+        r1 = R - 1 - (int)(w >> 16);
+        c1 = base + r1;
+        c = base + R - 1 - (int)((w >> 8) & 255u);
+        p = base + R - 1 - (int)(w & 255u);
       }
-      const uint64_t bal = tm.or_all(live ? 1ull << lane : 0ull);
-      if (live) u->queue[qlen + popc64(bal & ((1ull << lane) - 1ull))] = rec;
-      qlen += popc64(bal);
-      if (qlen >= W) {
-        tm.sync();
-        quads(acc, W, qlen, sd, rest);
-        qlen -= W;
+      float t123, t023, t013, t012, T123, T023, T013, T012;
+      minors3(c1, c, p, t123, t023, t013, t012, T123, T023, T013, T012);
+      const int rounds = (int)tm.max_u32(live ? (uint32_t)r1 : 0u);  // lane 0's: the round's largest c1
+      for (int i0 = 0; i0 < rounds; ++i0) {
+        const int c0 = base + i0;  // the same point for every lane: a broadcast read
+        bool act = live && i0 < r1;
+        uint32_t rec = 0;
+        if (act) {
+          const F4 A = ld4(fl + 8 * c0);
+          const float D4 = A.x * t123 - A.y * t023 + A.z * t013 - A.w * t012;
+          const float B4 = fabsf(A.x) * T123 + fabsf(A.y) * T023 + fabsf(A.z) * T013 + fabsf(A.w) * T012;
+          const int s4 = (fabsf(D4) > eps * B4 || B4 < 8388608.0f) ? (D4 > 0) - (D4 < 0) : quad_sign(view(), c0, c1, c, p);
+          if (s4 == 0) {
+            acc.singular += 1;
+            act = false;
+          } else {
+            rec = (uint32_t)c0 | (uint32_t)c1 << 6 | (uint32_t)c << 12 | (uint32_t)p << 18 | (s4 < 0 ? 1u << 31 : 0u);
+          }
+        }
+        const uint64_t bal = tm.ballot(act);
+        if (act) u->queue[qlen + popc64(bal & ((1ull << lane) - 1ull))] = rec;
+        qlen += popc64(bal);
+        if (qlen >= W) {
+          tm.sync();
+          quads(acc, W, qlen, sd, rest);
+          qlen -= W;
+        }
       }
     }
     if (qlen > 0) {
@@ -1461,7 +1521,7 @@ struct Walker {
           rec = (uint32_t)first | (uint32_t)a1 << 6 | (uint32_t)a2 << 12 | (uint32_t)a3 << 18 | (s4 < 0 ? 1u << 31 : 0u);
         }
       }
-      const uint64_t bal = tm.or_all(live ? 1ull << lane : 0ull);
+      const uint64_t bal = tm.ballot(live);
       if (live) u->queue[qlen + popc64(bal & ((1ull << lane) - 1ull))] = rec;
       qlen += popc64(bal);
       if (qlen >= W) {

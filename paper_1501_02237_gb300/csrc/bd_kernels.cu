@@ -43,6 +43,20 @@ struct WarpTeam {
     return b;
 #endif
   }
+  BD_HD uint64_t ballot(bool b) const {  // bit l: lane l's vote
+#ifdef __CUDA_ARCH__
+    return (uint64_t)__ballot_sync(0xffffffffu, b);
+#else
+    return b ? 1ull : 0ull;
+#endif
+  }
+  BD_HD uint32_t max_u32(uint32_t x) const {
+#ifdef __CUDA_ARCH__
+    return __reduce_max_sync(0xffffffffu, x);
+#else
+    return x;
+#endif
+  }
   BD_HD uint64_t or_all(uint64_t x) const {
 #ifdef __CUDA_ARCH__
     const unsigned lo = __reduce_or_sync(0xffffffffu, (unsigned)x);
@@ -77,6 +91,30 @@ __host__ __device__ inline size_t warp_bytes(int slots, int K) {
 // the uniform-state area of a warp region laid out as in warp_bytes, given its float rows
 __device__ inline void* uniform_after(float* fl, int slots) {
   return reinterpret_cast<unsigned char*>(fl) + align16((size_t)8 * slots * sizeof(float));
+}
+
+// The shared accumulators of the 5-D stage in a warp's uniform area (the walker of a Stage 5
+// kernel adds accepted cells, their |D0| and ties there): cleared before the warp's first
+// item, added into lane 0's accumulator and cleared again where the kernel flushes.
+template <class TC>
+__device__ void rare_clear(void* uni) {
+  __syncwarp();
+  if ((threadIdx.x & 31) == 0) {
+    unsigned long long* r = static_cast<Uniform<TC>*>(uni)->rare;
+    r[0] = r[1] = r[2] = r[3] = 0;
+  }
+  __syncwarp();
+}
+template <class TC>
+__device__ void rare_fold(void* uni, Acc& acc) {
+  __syncwarp();
+  if ((threadIdx.x & 31) == 0) {
+    const unsigned long long* r = static_cast<Uniform<TC>*>(uni)->rare;
+    acc.nvol += ((u128)r[1] << 64) | (u128)r[0];
+    acc.cells += r[2];
+    acc.ties += r[3];
+  }
+  rare_clear<TC>(uni);
 }
 
 template <class TC, class TL>
@@ -149,6 +187,7 @@ __global__ void BD_ENUM_BOUNDS k_enumerate(EnumParams p) {
   W.tri = p.tri;
   W.sink = p.sink;
   Acc acc{};
+  if (Stage == 5) rare_clear<TC>(m.uni);
   unsigned long long done = 0;
   const unsigned int units = p.ranges ? (unsigned int)p.nranges : (unsigned int)p.nitems;
   const unsigned int shards = p.shards > 1 ? (unsigned int)p.shards : 1u;
@@ -165,6 +204,7 @@ __global__ void BD_ENUM_BOUNDS k_enumerate(EnumParams p) {
       ++done;
     }
   }
+  if (Stage == 5) rare_fold<TC>(m.uni, acc);
   acc = warp_sum(acc);
   if (lane == 0) flush(acc, p.acc, done);
 }
@@ -314,6 +354,7 @@ __global__ void BD_ENUM_BOUNDS k_batch(BatchParams p) {
   WarpTeam tm;
   int cur = -1, N = 0, K = 0;
   Acc acc{};
+  if (Stage == 5) rare_clear<TC>(uniform_after(fl, slots));
   unsigned long long items = 0, cyc = 0;
   for (;;) {
     unsigned int i = 0;
@@ -323,6 +364,7 @@ __global__ void BD_ENUM_BOUNDS k_batch(BatchParams p) {
     const BatchItem bi = p.items[i];
     if ((int)bi.sys != cur) {
       if (cur >= 0) {
+        if (Stage == 5) rare_fold<TC>(uniform_after(fl, slots), acc);
         const Acc s = warp_sum(acc);
         if (lane == 0) flush_sys(s, items, cyc, p, cur);
       }
@@ -351,6 +393,7 @@ __global__ void BD_ENUM_BOUNDS k_batch(BatchParams p) {
     ++items;
   }
   if (cur >= 0) {
+    if (Stage == 5) rare_fold<TC>(uniform_after(fl, slots), acc);
     const Acc s = warp_sum(acc);
     if (lane == 0) flush_sys(s, items, cyc, p, cur);
   }

@@ -17,6 +17,7 @@ struct HostTeam {
   void sync() const {}
   uint64_t or_all(uint64_t x) const { return x; }
   uint32_t max_u32(uint32_t x) const { return x; }
+  uint64_t ballot(bool b) const { return b ? 1ull : 0ull; }
 };
 
 // A team of `width` lanes run as CPU threads in lockstep: every collective (vote, sync) is a
@@ -56,6 +57,7 @@ struct LockstepTeam {
     return r;
   }
   bool any(bool b) const { return reduce_or(b, false) != 0; }
+  uint64_t ballot(bool b) const { return reduce_or(b ? 1ull << ln : 0ull, false); }  // bit l: lane l's vote
   bool all(bool b) const { return reduce_or(b, true) != 0; }
   void sync() const { sh->barrier(); }
   uint64_t or_all(uint64_t x) const { return reduce_or(x, false); }
