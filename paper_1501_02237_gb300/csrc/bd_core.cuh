@@ -1221,6 +1221,9 @@ struct Walker {
 #ifdef BD_COUNT
       int qt = 0;
 #endif
+      // single-precision scan; undecided points are noted and decided exactly afterwards,
+      // unless a point strictly below was found (as in the 5-D test's scan)
+      uint64_t und = 0;
       for (int q = 0; q < N; ++q) {
         if (tm.all(!live || below)) break;
         if (!live || below || ((excl >> q) & 1ull)) continue;
@@ -1231,9 +1234,24 @@ struct Walker {
         const float x0 = X.x, x1 = X.y, x2 = X.z, x3 = X.w;
         const float v = fmaf(n0, x0, fmaf(n1, x1, fmaf(n2, x2, n3 * x3)));
         const float bound = fmaf(e0, fabsf(x0), fmaf(e1, fabsf(x1), fmaf(e2, fabsf(x2), e3 * fabsf(x3))));
-        const int sg = v > bound ? 1 : (v < -bound ? -1 : side4_exact(view(), c1, c, p, q, sig));
-        if (sg == 0) on = true;
-        else if (sg != sig) below = true;
+        if (v > bound) {
+          if (sig < 0) below = true;
+        } else if (v < -bound) {
+          if (sig > 0) below = true;
+        } else {
+          und |= 1ull << q;
+        }
+      }
+      if (live && !below) {
+        for (; und; und &= und - 1) {
+          const int sg = side4_exact(view(), c1, c, p, ctz64(und), sig);
+          if (sg == 0) {
+            on = true;
+          } else if (sg != sig) {
+            below = true;
+            break;
+          }
+        }
       }
 #ifdef BD_COUNT
       if (cnt && live) { cnt->pairs++; cnt->qtests += qt; }
@@ -1374,6 +1392,11 @@ struct Walker {
     }
     const uint64_t own = busy ? (1ull << c0) | (1ull << c1) | (1ull << c) | (1ull << p) : 0ull;
     bool below = false, on = false;
+    // The scan decides each point in single precision; a point whose value lies inside the
+    // error bound is noted in `und` and decided exactly after the scan, and only if no point
+    // was found strictly below (the exact routes are calls: out of the loop, they do not
+    // constrain its registers).
+    uint64_t und = 0;
     for (uint64_t f = rest; f; f &= f - 1) {
       if (tm.all(!busy || below)) break;
       const int q = ctz64(f);  // the same point for every lane
@@ -1382,9 +1405,24 @@ struct Walker {
       const float x4 = fl[8 * q + 4];
       const float v = fmaf(n0, X.x, fmaf(n1, X.y, fmaf(n2, X.z, fmaf(n3, X.w, n4 * x4))));
       const float bound = fmaf(e0, fabsf(X.x), fmaf(e1, fabsf(X.y), fmaf(e2, fabsf(X.z), fmaf(e3, fabsf(X.w), e4 * fabsf(x4)))));
-      const int sg = v > bound ? 1 : (v < -bound ? -1 : side5_exact(view(), c0, c1, c, p, q, sig));
-      if (sg == 0) on = true;
-      else if (sg != sig) below = true;
+      if (v > bound) {
+        if (sig < 0) below = true;  // side +1 against sig -1
+      } else if (v < -bound) {
+        if (sig > 0) below = true;
+      } else {
+        und |= 1ull << q;
+      }
+    }
+    if (busy && !below) {
+      for (; und; und &= und - 1) {
+        const int sg = side5_exact(view(), c0, c1, c, p, ctz64(und), sig);
+        if (sg == 0) {
+          on = true;
+        } else if (sg != sig) {
+          below = true;
+          break;
+        }
+      }
     }
 #ifdef BD_COUNT
     if (cnt && busy) cnt->pairs++;
