@@ -869,6 +869,17 @@ struct Walker {
     // coordinate minors at fl[FS q + e], the lift minor at fl[FS q + K - j])
     const bool conv = kFiltered && K >= 3 && j == copy_level();
     const int FS = copy_stride(), LI = K - j;
+    // state j's pivot, exact divider and point set, for the levels below; every lane forms the
+    // divider (a chain of dependent multiplies) before the point loop, so that its latency
+    // overlaps the loop's independent work, and lane 0 stores it (read after the closing sync)
+    {
+      const Div Dj = make_div(pj);
+      if (tm.lane() == 0) {
+        u->piv[j] = pj;
+        u->dv[j] = Dj;
+        u->taken[j] = u->taken[j - 1] | (1ull << c);
+      }
+    }
     auto whole_point = [&](int q) {
       const TC bq = sc[(po + pi) * SLOTS + q];
       for (int e = 0; e < ncoord - 1; ++e) {
@@ -909,11 +920,6 @@ struct Walker {
       }
     }
     s.set(j, c);
-    if (tm.lane() == 0) {
-      u->piv[j] = pj;
-      u->dv[j] = make_div(pj);
-      u->taken[j] = taken;
-    }
     tm.sync();
     return true;
   }
