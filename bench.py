@@ -39,13 +39,13 @@ SECONDARY = "single_n24_k8"
 # sources: DRAM bytes (read + write), warp instructions issued and the issue-active fraction.
 # Reported only while the library sources still hash to the captured version, null otherwise.
 PROFILE = {
-    "sources_sha256": "d0228aa4b605bb814da170b36e6d68403f2953dd078215995894df36dae953e7",
+    "sources_sha256": "f00fef02a6bec655b118e443c8c9ad5950602bd5732f022fc950597c448fbe55",
     # k_enumerate<int32, int64, 5> (the 5-D stage), 388,070 items
-    "heavy_quiver_n32_k10": dict(warp_inst=2823095674, lanes_per_inst=26.23, issue_active=0.5737,
-                                 traffic=7772928 + 168960),
+    "heavy_quiver_n32_k10": dict(warp_inst=2408981505, lanes_per_inst=25.77, issue_active=0.5944,
+                                 traffic=6700032 + 43008),
     # k_enumerate<int32, int64, 4> (the 4-D stage), 53,196 items
-    "single_n24_k8": dict(warp_inst=130669566, lanes_per_inst=23.36, issue_active=0.5474,
-                          traffic=1172736 + 27648),
+    "single_n24_k8": dict(warp_inst=130585027, lanes_per_inst=23.47, issue_active=0.5623,
+                          traffic=1161728 + 16384),
 }
 
 
