@@ -509,11 +509,16 @@ int bd_host_mixed_volume_lifted(const int64_t* points, const int32_t* counts, in
  *            of its points: one 64-bit word up to 64 points, two words above)
  *   seed   : lift seed: heights 1 + (top 40 bits of bd_volume's SplitMix64 stream), in [1, 2^40],
  *            wider than bd_volume's because up to ~1e8 cells are walked; a tie re-lifts (8 liftings)
- *   out    : nvol, cells, ties, relifts, flags (BD_FLAG_DEGENERATE when not full-dimensional),
- *            bound_bits; subsets holds the ridges examined, (k+1) * cells
+ *   out    : nvol, cells, ties, relifts, flags (BD_FLAG_DEGENERATE when not full-dimensional;
+ *            BD_FLAG_INT128 when the tableau took 128-bit entries), bound_bits; subsets holds the
+ *            ridges examined, (k+1) * cells
  *   device_ms : NULL, or the traversal's time on the GPU (CUDA events; all levels)
- * Errors: BD_ERR_ARG, BD_ERR_OVERFLOW (cell minors beyond 62 bits), BD_ERR_TIES, BD_ERR_CUDA,
- * BD_ERR_NOMEM (more than 2^30 cells).
+ * The tableau's entries are minors of the cells' difference matrices: 64-bit while Hadamard's
+ * bound on them (bound_bits) stays below 2^62, 128-bit above (fewer warps per SM, slower pivots).
+ * Errors: BD_ERR_ARG, BD_ERR_OVERFLOW (heights D h(p), a minor times a 41-bit lift difference
+ * summed over k+1 terms, may leave 127 bits: bound_bits above about 84; or the start cell's
+ * support function left 128 bits), BD_ERR_TIES, BD_ERR_CUDA, BD_ERR_NOMEM (more than 2^30
+ * cells).
  */
 int bd_volume_pivot(const int64_t* points, int32_t npts, int32_t k, uint64_t seed, bd_volume_out* out,
                     double* device_ms);
@@ -526,6 +531,12 @@ int bd_volume_pivot(const int64_t* points, int32_t npts, int32_t k, uint64_t see
  * out->cells -> BD_ERR_ARG. */
 int bd_host_volume_pivot(const int64_t* points, const int64_t* lifts, int32_t npts, int32_t k, int32_t team_width,
                          int32_t walk_budget, bd_volume_out* out, uint64_t* cells, int64_t capacity);
+
+/* Test hook of the pivoting walk (process-wide; the paper has no counterpart): while on != 0,
+ * bd_volume_pivot, bd_host_volume_pivot and bd_degree_pivot take 128-bit tableau entries
+ * whatever the bound, so that the wide path runs on small inputs too.  Returns the previous
+ * setting. */
+int bd_pivot_force_wide(int32_t on);
 
 /* bd_degree with the volume always by pivoting: up to 126 variables and solution sets of
  * dimension up to 30, e.g. the master spaces of Table mspace-deg. */

@@ -20,7 +20,7 @@ from ._lib import BD_OK, F32P, I32P, U8P
 __all__ = ["CostModel", "Server", "degree", "volume", "volume_noalloc", "volume_lifted", "classify", "reduce", "Plan", "Batch", "set_stream",
            "host_volume_lifted", "cells", "host_cells", "start_solutions", "host_start_solutions", "mixed_volume",
            "mixed_volume_lifted", "host_mixed_volume_lifted", "volume_pivot", "host_volume_pivot", "degree_pivot",
-           "issue_peak", "inject_alloc_failure", "BinodegError", "lib"]
+           "issue_peak", "inject_alloc_failure", "pivot_force_wide", "BinodegError", "lib"]
 
 
 def set_stream(stream) -> None:
@@ -256,6 +256,12 @@ def host_volume_pivot(points, lifts, team_width: int = 1, cells: bool = False, c
     if cells and rc == 0:
         res["cell_list"] = [tuple(i for i in range(64) if (int(m) >> i) & 1) for m in buf[: int(out.cells)]]
     return res
+
+
+def pivot_force_wide(on: bool = True) -> bool:
+    """bd_pivot_force_wide (test hook): the pivoting walk takes 128-bit tableau entries whatever
+    the bound while on; returns the previous setting."""
+    return bool(lib().bd_pivot_force_wide(1 if on else 0))
 
 
 def degree_pivot(A, coef=None, seed: int = 0) -> dict:

@@ -154,6 +154,7 @@ SIGNATURES = {
     "bd_mixed_volume": (C.c_int, [I64P, I32P, C.c_int32, C.c_uint64, C.POINTER(MixedOut)]),
     "bd_volume_pivot": (C.c_int, [I64P, C.c_int32, C.c_int32, C.c_uint64, C.POINTER(VolumeOut),
                                   C.POINTER(C.c_double)]),
+    "bd_pivot_force_wide": (C.c_int, [C.c_int32]),
     "bd_host_volume_pivot": (C.c_int, [I64P, I64P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.POINTER(VolumeOut),
                                        C.POINTER(C.c_uint64), C.c_int64]),
     "bd_degree_pivot": (C.c_int, [I64P, C.c_int32, C.c_int32, I64P, C.c_uint64, C.POINTER(DegreeOut)]),

@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <deque>
@@ -29,6 +30,8 @@ using bd::u128;
 namespace {
 
 constexpr int kPivotMaxWarps = 8;  // warps per block: chosen per problem, at most this
+
+std::atomic<int> g_force_wide{0};  // bd_pivot_force_wide: 128-bit tableau entries whatever the bound
 
 struct PivotWarp {
   __device__ int lane() const { return threadIdx.x & 31; }
@@ -207,16 +210,20 @@ double pivot_bound_log2(const int64_t* pts, int N, int d) {
   return best;
 }
 
+// per-warp shared memory of the walk with tableau entries of type TE: the scratch, the heights
+// S (i128), then G0 and W (TE)
+template <class TE>
 __host__ __device__ size_t pivot_warp_bytes(int N, int d) {
-  size_t b = sizeof(bd::PivotScratch);
-  b = (b + 15) / 16 * 16 + 16 * (size_t)N;    // S: heights (i128)
-  b += 8 * (size_t)N;                         // G0
-  b += 8 * (size_t)d * (d + N);               // W
+  size_t b = sizeof(bd::PivotScratch<TE>);
+  b = (b + 15) / 16 * 16 + 16 * (size_t)N;     // S: heights (i128)
+  b += sizeof(TE) * (size_t)N;                 // G0
+  b += sizeof(TE) * (size_t)d * (d + N);       // W
   return (b + 15) / 16 * 16;
 }
 
+template <class TE>
 size_t pivot_smem(int N, int d, int warps) {
-  return ((8 * (size_t)(d + 1) * N + 15) / 16 * 16) + warps * pivot_warp_bytes(N, d);
+  return ((8 * (size_t)(d + 1) * N + 15) / 16 * 16) + warps * pivot_warp_bytes<TE>(N, d);
 }
 
 struct PivotDev {
@@ -344,7 +351,7 @@ __device__ void frontier_push(Mask* next, unsigned long long cap, Mask m, PivotD
 
 // One breadth-first level: every cell of `cur` is processed by one warp; its new neighbours
 // enter the table and `next`.
-template <class Mask>
+template <class Mask, class TE>
 __global__ void __launch_bounds__(32 * kPivotMaxWarps) k_pivot(const int64_t* pts, const int64_t* lifts, int N, int d,
                                                             const Mask* cur, unsigned long long ncur,
                                                             CellTable<Mask> table, unsigned long long cap,
@@ -356,14 +363,14 @@ __global__ void __launch_bounds__(32 * kPivotMaxWarps) k_pivot(const int64_t* pt
   for (int i = threadIdx.x; i < N; i += blockDim.x) L[i] = lifts[i];
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  unsigned char* wb = smem + ((8 * (size_t)(d + 1) * N + 15) / 16 * 16) + warp * pivot_warp_bytes(N, d);
-  auto* sc = reinterpret_cast<bd::PivotScratch*>(wb);
-  size_t at = (sizeof(bd::PivotScratch) + 15) / 16 * 16;
+  unsigned char* wb = smem + ((8 * (size_t)(d + 1) * N + 15) / 16 * 16) + warp * pivot_warp_bytes<TE>(N, d);
+  auto* sc = reinterpret_cast<bd::PivotScratch<TE>*>(wb);
+  size_t at = (sizeof(bd::PivotScratch<TE>) + 15) / 16 * 16;
   i128* S = reinterpret_cast<i128*>(wb + at);
   at += 16 * (size_t)N;
-  int64_t* G0 = reinterpret_cast<int64_t*>(wb + at);
-  at += 8 * (size_t)N;
-  int64_t* W = reinterpret_cast<int64_t*>(wb + at);
+  TE* G0 = reinterpret_cast<TE*>(wb + at);
+  at += sizeof(TE) * (size_t)N;
+  TE* W = reinterpret_cast<TE*>(wb + at);
   PivotWarp tm;
   bd::PivotAcc acc{};
   int flags = 0;
@@ -371,7 +378,7 @@ __global__ void __launch_bounds__(32 * kPivotMaxWarps) k_pivot(const int64_t* pt
   const unsigned long long gw = (unsigned long long)blockIdx.x * wpb + warp;
   const unsigned long long nw = (unsigned long long)gridDim.x * wpb;
   for (unsigned long long c = gw; c < ncur; c += nw) {
-    flags |= bd::pivot_cell(
+    flags |= bd::pivot_cell<TE>(
         tm, P, L, N, d, cur[c], W, S, G0, sc, acc,
         [&](Mask m) { return table.claim(cap, m, &dv->claimed, &dv->flags); },
         [&](Mask m) { frontier_push(next, cap, m, dv); }, budget);
@@ -408,7 +415,7 @@ struct PivotRun {
 
 // The traversal on the GPU from `start`; the table grows (and the traversal restarts) while it
 // would be more than half full.
-template <class Mask>
+template <class Mask, class TE>
 int device_pivot(const int64_t* pts, const int64_t* lifts, int N, int d, Mask start, PivotRun& run) {
   cudaStream_t st = bd::thread_stream();
   int dev = 0, sms = 0, optin = 0;
@@ -416,15 +423,15 @@ int device_pivot(const int64_t* pts, const int64_t* lifts, int N, int d, Mask st
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (e != cudaSuccess) return bd::cuda_error(e);
-  if (pivot_smem(N, d, 1) > (size_t)optin) return bd::set_error(BD_ERR_ARG, "the pivoting state exceeds shared memory");
-  e = cudaFuncSetAttribute(k_pivot<Mask>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  if (pivot_smem<TE>(N, d, 1) > (size_t)optin) return bd::set_error(BD_ERR_ARG, "the pivoting state exceeds shared memory");
+  e = cudaFuncSetAttribute(k_pivot<Mask, TE>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
   // warps per block: the most resident warps per SM (the state is per warp)
   int wpb = 1, per_sm = 0, best = 0;
   for (int w = 1; w <= kPivotMaxWarps && e == cudaSuccess; ++w) {
-    const size_t sm_w = pivot_smem(N, d, w);
+    const size_t sm_w = pivot_smem<TE>(N, d, w);
     if (sm_w > (size_t)optin) break;
     int b = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_pivot<Mask>, 32 * w, sm_w);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_pivot<Mask, TE>, 32 * w, sm_w);
     if (b * w > best) {
       best = b * w;
       wpb = w;
@@ -433,8 +440,11 @@ int device_pivot(const int64_t* pts, const int64_t* lifts, int N, int d, Mask st
   }
   if (e != cudaSuccess) return bd::cuda_error(e);
   per_sm = std::max(per_sm, 1);
-  const size_t smem = pivot_smem(N, d, wpb);
-  for (unsigned long long cap = 1ull << 22; cap <= (1ull << 31); cap <<= 3) {
+  const size_t smem = pivot_smem<TE>(N, d, wpb);
+  // the table starts at 2^22 slots (2^26 for two-word masks: point sets past 64 points are the
+  // large walks) and grows 8-fold (4-fold) per restart
+  const bool two_words = std::is_same<Mask, bd::WideMask>::value;
+  for (unsigned long long cap = two_words ? 1ull << 26 : 1ull << 22; cap <= (1ull << 31); cap <<= (two_words ? 2 : 3)) {
     int64_t *d_pts = nullptr, *d_lifts = nullptr;
     CellTable<Mask> table;
     Mask *d_a = nullptr, *d_b = nullptr;
@@ -480,8 +490,8 @@ int device_pivot(const int64_t* pts, const int64_t* lifts, int N, int d, Mask st
       const unsigned long long warps = (unsigned long long)sms * per_sm * wpb;
       const int budget = ncur * 4 < warps ? 0 : kWalkBudget;
       if (e == cudaSuccess) {
-        k_pivot<Mask><<<(unsigned int)blocks, 32 * wpb, smem, st>>>(d_pts, d_lifts, N, d, d_a, ncur, table, cap,
-                                                                       budget, d_b, d_dv);
+        k_pivot<Mask, TE><<<(unsigned int)blocks, 32 * wpb, smem, st>>>(d_pts, d_lifts, N, d, d_a, ncur, table, cap,
+                                                                           budget, d_b, d_dv);
         e = cudaGetLastError();
       }
       if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d_dv, sizeof(h), cudaMemcpyDeviceToHost, st);
@@ -520,15 +530,15 @@ struct MaskHash {
   size_t operator()(bd::WideMask m) const { return (size_t)bd::pivot_hash(m); }
 };
 
-template <class Mask>
+template <class Mask, class TE>
 int host_pivot(const int64_t* pts, const int64_t* lifts, int N, int d, Mask start, int width, int budget,
                PivotRun& run) {
   std::vector<int64_t> P((size_t)d * N);
   for (int r = 0; r < d; ++r)
     for (int p = 0; p < N; ++p) P[(size_t)r * N + p] = pts[p * d + r];
-  std::vector<int64_t> W((size_t)d * (d + N)), G0(N);
+  std::vector<TE> W((size_t)d * (d + N)), G0(N);
   std::vector<i128> S(N);
-  bd::PivotScratch sc{};
+  bd::PivotScratch<TE> sc{};
   std::unordered_set<Mask, MaskHash> seen{start};
   std::vector<Mask> cur{start}, next;
   bd::PivotAcc acc{};
@@ -536,7 +546,7 @@ int host_pivot(const int64_t* pts, const int64_t* lifts, int N, int d, Mask star
   std::mutex mu;
   auto step = [&](auto tm) {  // neighbours go to `next` under the mutex
     for (const Mask m : cur) {
-      const int f = bd::pivot_cell(
+      const int f = bd::pivot_cell<TE>(
           tm, P.data(), lifts, N, d, m, W.data(), S.data(), G0.data(), &sc, acc,
           [&](Mask nb) {
             std::lock_guard<std::mutex> g(mu);  // lanes of a lockstep team claim concurrently
@@ -589,7 +599,11 @@ int pivot_common(const int64_t* points, const int64_t* given_lifts, int32_t npts
       return bd::set_error(BD_ERR_ARG, "coordinates must stay below 2^20 in magnitude on the pivoting path");
   const double bits = pivot_bound_log2(points, npts, k);
   out->bound_bits = (int32_t)std::ceil(bits);
-  if (bits >= 61.99) return bd::set_error(BD_ERR_OVERFLOW, "cell minors may leave 62 bits");
+  // the tableau's entries are cell minors: 64-bit while the bound stays below 2^62, else 128-bit;
+  // the heights D h(p) (d+1 terms of a minor times a lift difference below 2^41) are 128-bit
+  const bool wide = bits >= 61.99 || g_force_wide.load() != 0;
+  if (bits + 41.0 + std::log2((double)(k + 1)) >= 125.99)
+    return bd::set_error(BD_ERR_OVERFLOW, "cell heights may leave 127 bits (cell minors past 2^84)");
   std::vector<int64_t> lifts(npts);
   const int attempts = given_lifts ? 1 : 8;
   for (int a = 0; a < attempts; ++a) {
@@ -604,10 +618,10 @@ int pivot_common(const int64_t* points, const int64_t* given_lifts, int32_t npts
       for (int i = 0; i < npts; ++i) lifts[i] = lift_height_wide(ss, i);
     }
     out->relifts = a;
-    uint64_t start = 0;      // at most 64 points: one-word masks
-    bd::WideMask wide{0, 0};  // more: two words
+    uint64_t start = 0;        // at most 64 points: one-word masks
+    bd::WideMask wmask{0, 0};  // more: two words
     const int sr = npts <= 64 ? start_cell(points, lifts.data(), npts, k, start)
-                              : start_cell(points, lifts.data(), npts, k, wide);
+                              : start_cell(points, lifts.data(), npts, k, wmask);
     if (sr == START_FLAT) {
       out->flags = BD_FLAG_DEGENERATE;
       return BD_OK;
@@ -619,12 +633,18 @@ int pivot_common(const int64_t* points, const int64_t* given_lifts, int32_t npts
     }
     PivotRun run;
     int rc;
-    if (npts <= 64)
-      rc = host_width > 0 ? host_pivot(points, lifts.data(), npts, k, start, host_width, host_budget, run)
-                          : device_pivot(points, lifts.data(), npts, k, start, run);
+    if (npts <= 64 && !wide)
+      rc = host_width > 0 ? host_pivot<uint64_t, int64_t>(points, lifts.data(), npts, k, start, host_width, host_budget, run)
+                          : device_pivot<uint64_t, int64_t>(points, lifts.data(), npts, k, start, run);
+    else if (npts <= 64)
+      rc = host_width > 0 ? host_pivot<uint64_t, i128>(points, lifts.data(), npts, k, start, host_width, host_budget, run)
+                          : device_pivot<uint64_t, i128>(points, lifts.data(), npts, k, start, run);
+    else if (!wide)
+      rc = host_width > 0 ? host_pivot<bd::WideMask, int64_t>(points, lifts.data(), npts, k, wmask, host_width, host_budget, run)
+                          : device_pivot<bd::WideMask, int64_t>(points, lifts.data(), npts, k, wmask, run);
     else
-      rc = host_width > 0 ? host_pivot(points, lifts.data(), npts, k, wide, host_width, host_budget, run)
-                          : device_pivot(points, lifts.data(), npts, k, wide, run);
+      rc = host_width > 0 ? host_pivot<bd::WideMask, i128>(points, lifts.data(), npts, k, wmask, host_width, host_budget, run)
+                          : device_pivot<bd::WideMask, i128>(points, lifts.data(), npts, k, wmask, run);
     if (rc) return rc;
     if (run.flags & PF_INVALID) return bd::set_error(BD_ERR_ARG, "pivoting reached a non-cell (internal error)");
     if (run.flags & PF_TIE) {
@@ -632,6 +652,7 @@ int pivot_common(const int64_t* points, const int64_t* given_lifts, int32_t npts
       continue;
     }
     out->ties = 0;
+    if (wide) out->flags |= BD_FLAG_INT128;
     out->nvol_lo = (uint64_t)run.nvol;
     out->nvol_hi = (uint64_t)(run.nvol >> 64);
     out->cells = run.cells;
@@ -664,6 +685,8 @@ int bd_host_volume_pivot(const int64_t* points, const int64_t* lifts, int32_t np
   if (cells && capacity < 0) return bd::set_error(BD_ERR_ARG, "negative capacity");
   return pivot_common(points, lifts, npts, k, 0, team_width, walk_budget, out, cells, capacity, nullptr);
 }
+
+int bd_pivot_force_wide(int32_t on) { return g_force_wide.exchange(on != 0 ? 1 : 0); }
 
 int bd_degree_pivot(const int64_t* A, int32_t n, int32_t m, const int64_t* coef, uint64_t seed, bd_degree_out* out) {
   if (!out) return bd::set_error(BD_ERR_ARG, "out is NULL");

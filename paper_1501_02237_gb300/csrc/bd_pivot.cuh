@@ -15,9 +15,11 @@
 // once by fraction-free Gauss-Jordan elimination of [M^T | a_p - a_{s_0}], whose entries stay
 // minors of that matrix (bounded on the host by Hadamard's inequality): at the end the left
 // block is D I with D = +-det M and the right block holds g(p) = D lambda(p) (g_0 = D - sum g_j).
-// The height is s(p) = D h(p) = D (w_p - w_{s_0}) - sum_j g_j(p) (w_{s_j} - w_{s_0}) in 128 bits,
-// and ratios are compared by 256-bit cross products (s_A g_B > s_B g_A means A comes first,
-// both g of the far side having the sign opposite to D).  A point other than the cell's with
+// The tableau holds 64-bit entries while that bound stays below 2^62 and 128-bit entries above
+// it (TE, the entry type).  The height is s(p) = D h(p) = D (w_p - w_{s_0}) - sum_j g_j(p)
+// (w_{s_j} - w_{s_0}) in 128 bits (the host also bounds it: minors times 2^41 heights, d+1
+// terms), and ratios are compared by 256-bit cross products (s_A g_B > s_B g_A means A comes
+// first, both g of the far side having the sign opposite to D).  A point other than the cell's with
 // s(p) of the wrong sign, a zero height or two equal ratios mean the lifting is not generic.
 //
 // Parallel layout: a warp owns one cell; its lanes own the matrix columns in the elimination and
@@ -64,10 +66,11 @@ BD_HD void madd(WideMask& m, int p) {
 
 enum { PV_OK = 0, PV_TIE = 1, PV_INVALID = 2 };
 
-// one lane's best candidate for a ridge
+// one lane's best candidate for a ridge (TE: the tableau's entry type, int64_t or i128)
+template <class TE>
 struct PivotCand {
   i128 s;      // height numerator s(p)
-  int64_t g;   // barycentric numerator of the dropped vertex, g_i(p)
+  TE g;        // barycentric numerator of the dropped vertex, g_i(p)
   int32_t p;   // point index, -1 for none
   int32_t pad;
 };
@@ -75,11 +78,11 @@ struct PivotCand {
 // per-warp scratch of the pivoting stage
 constexpr int kWalkDepth = 64;  // deepest in-place walk below an eliminated cell
 
+template <class TE>
 struct PivotScratch {
-  PivotCand cand[32];
   i128 sq;                       // the entering point's height numerator during a pivot
-  int64_t colq[kPivotDMax + 1];  // the entering point's tableau column during a pivot
-  int64_t D;                     // the current cell's +-det M
+  TE colq[kPivotDMax + 1];       // the entering point's tableau column during a pivot
+  TE D;                          // the current cell's +-det M
   uint8_t cidx[kPivotDMax + 2];  // the current cell's vertices; tableau row r belongs to cidx[r]
   uint8_t st_slot[kWalkDepth], st_old[kWalkDepth];  // the walk's stack: replaced row and point
   uint32_t st_todo[kWalkDepth];  // the parent's new neighbours still to handle
@@ -106,6 +109,8 @@ BD_HD bool prod_equal(i128 a, i128 b, i128 c, i128 d) {
 }
 
 // a float near x (relative error below 2^-23.9): the top 62 bits through an int64 conversion
+BD_HD float approx_f(i128 x);
+BD_HD float approx_f(int64_t x) { return (float)x; }  // rounded once
 BD_HD float approx_f(i128 x) {
   const bool neg = x < 0;
   const u128 a = neg ? (u128)(-x) : (u128)x;
@@ -124,7 +129,8 @@ BD_HD float approx_f(i128 x) {
 }
 
 // merge candidate B into A (both for the same ridge); sets *tie on equal ratios
-BD_HD void pivot_merge(PivotCand& A, const PivotCand& B, int32_t* flags) {
+template <class TE>
+BD_HD void pivot_merge(PivotCand<TE>& A, const PivotCand<TE>& B, int32_t* flags) {
   if (B.p < 0) return;
   if (A.p < 0) {
     A = B;
@@ -154,15 +160,17 @@ struct PivotAcc {
 // either entered in place (one rank-one pivot of the tableau, Sec. 4.2's pivot taken literally;
 // one more pivot leads back) or, past the budget or the stack depth, handed to push(mask) for a
 // later launch.  claim and push are called by any lane, concurrently.  P holds the points coordinate-major
-// (P[r * N + p]), L the lifts.  Per team: W, d x (d+N) int64; S, N heights; G0, N values of g_0;
-// sc, the scratch.  Rows 1..d of the tableau are W's right block, row 0 is G0.  Returns PV_OK,
+// (P[r * N + p]), L the lifts.  Per team: W, d x (d+N) entries; S, N heights; G0, N values of g_0;
+// sc, the scratch.  Rows 1..d of the tableau are W's right block, row 0 is G0.  TE is int64_t
+// (cell minors below 2^62) or i128 (below 2^126; the host checks the bounds).  Returns PV_OK,
 // or PV_TIE / PV_INVALID bits.
 #ifdef __CUDACC__
 #pragma nv_exec_check_disable  // instantiated with host-only teams by the host emulation
 #endif
-template <class Team, class Mask, class Claim, class Push>
-BD_HD int pivot_cell(Team tm, const int64_t* P, const int64_t* L, int N, int d, Mask mask, int64_t* W, i128* S,
-                     int64_t* G0, PivotScratch* sc, PivotAcc& acc, Claim claim, Push push, int budget) {
+template <class TE, class Team, class Mask, class Claim, class Push>
+BD_HD int pivot_cell(Team tm, const int64_t* P, const int64_t* L, int N, int d, Mask mask, TE* W, i128* S,
+                     TE* G0, PivotScratch<TE>* sc, PivotAcc& acc, Claim claim, Push push, int budget) {
+  typedef typename DivOf<TE>::type Div;
   const int lane = tm.lane(), nl = tm.lanes(), width = d + N;
   tm.sync();  // the previous cell's readers are done with the scratch
   if (lane == 0) sc->flags = 0;
@@ -177,7 +185,7 @@ BD_HD int pivot_cell(Team tm, const int64_t* P, const int64_t* L, int N, int d, 
   }
   tm.sync();
   // fraction-free Gauss-Jordan: after step k, rows i != k have no entry in column k
-  int64_t prev = 1;
+  TE prev = 1;
   for (int k = 0; k < d; ++k) {
     if (lane == 0) {
       int r = k;
@@ -193,34 +201,34 @@ BD_HD int pivot_cell(Team tm, const int64_t* P, const int64_t* L, int N, int d, 
     }
     if (pr != k) {
       for (int c = lane; c < width; c += nl) {
-        const int64_t t = W[k * width + c];
+        const TE t = W[k * width + c];
         W[k * width + c] = W[pr * width + c];
         W[pr * width + c] = t;
       }
       tm.sync();
     }
-    const int64_t pk = W[k * width + k];
-    const Div64 D = make_div(prev);
+    const TE pk = W[k * width + k];
+    const Div D = make_div(prev);
     for (int c = k + 1 + lane; c < width; c += nl) {
-      const int64_t top = W[k * width + c];
+      const TE top = W[k * width + c];
       for (int i = 0; i < d; ++i)
         if (i != k) W[i * width + c] = bareiss(W[i * width + c], pk, W[i * width + k], top, D);
     }
     tm.sync();
     prev = pk;
   }
-  const int64_t Dv = prev;  // +-det M: the cell's normalized volume up to sign
+  const TE Dv = prev;  // +-det M: the cell's normalized volume up to sign
   // heights and g_0 of every point
   int fl = 0;
   for (int p = lane; p < N; p += nl) {
     i128 s = (i128)Dv * (L[p] - L[s0]), gs = 0;
     for (int j = 0; j < d; ++j) {
-      const int64_t g = W[j * width + d + p];
+      const TE g = W[j * width + d + p];
       gs += g;
       s -= (i128)g * (L[sc->cidx[j + 1]] - L[s0]);
     }
     S[p] = s;
-    G0[p] = (int64_t)((i128)Dv - gs);  // itself a minor: fits
+    G0[p] = (TE)((i128)Dv - gs);  // itself a minor: fits
     if (!mhas(mask, p)) {
       const int sg = (s > 0) - (s < 0);
       if (sg == 0) fl |= PV_TIE;
@@ -243,7 +251,7 @@ BD_HD int pivot_cell(Team tm, const int64_t* P, const int64_t* L, int N, int d, 
     acc.nvol += (u128)(Dv < 0 ? -Dv : Dv);
     ++acc.cells;
   }
-  auto T = [&](int r, int p) -> int64_t& { return r == 0 ? G0[p] : W[(r - 1) * width + d + p]; };
+  auto T = [&](int r, int p) -> TE& { return r == 0 ? G0[p] : W[(r - 1) * width + d + p]; };
   // Pivot row i onto point q: T'[r][p] = (T[r][p] T[i][q] - T[r][q] T[i][p]) / D for r != i,
   // T'[i][p] = T[i][p], S'[p] = (S[p] T[i][q] - S[q] T[i][p]) / D, D' = T[i][q] (every entry
   // again a minor, or D' times a height, of the new cell).
@@ -251,12 +259,12 @@ BD_HD int pivot_cell(Team tm, const int64_t* P, const int64_t* L, int N, int d, 
     for (int r = lane; r <= d; r += nl) sc->colq[r] = T(r, q);
     if (lane == 0) sc->sq = S[q];
     tm.sync();
-    const int64_t Dold = sc->D, piv = sc->colq[i];
-    const Div64 Dd = make_div(Dold);
+    const TE Dold = sc->D, piv = sc->colq[i];
+    const Div Dd = make_div(Dold);
     const Div128 Dw = make_div((i128)Dold);
     const i128 sq = sc->sq;
     for (int p = lane; p < N; p += nl) {
-      const int64_t ti = T(i, p);
+      const TE ti = T(i, p);
       for (int r = 0; r <= d; ++r)
         if (r != i) T(r, p) = bareiss(T(r, p), piv, sc->colq[r], ti, Dd);
       S[p] = bareiss(S[p], (i128)piv, sq, (i128)ti, Dw);
@@ -275,17 +283,17 @@ BD_HD int pivot_cell(Team tm, const int64_t* P, const int64_t* L, int N, int d, 
     const int sd = sc->D > 0 ? 1 : -1;
     uint64_t fresh = 0;
     for (int r = lane; r <= d; r += nl) {
-      PivotCand best{0, 0, -1, 0};
+      PivotCand<TE> best{0, 0, -1, 0};
       float bf = 0.f;  // best's ratio in single precision
       for (int p = 0; p < N; ++p) {
         if (mhas(mask, p)) continue;
-        const int64_t gi = T(r, p);
+        const TE gi = T(r, p);
         if (gi == 0 || (gi > 0 ? 1 : -1) == sd) continue;  // not beyond the ridge
-        PivotCand c{S[p], gi, p, 0};
+        PivotCand<TE> c{S[p], gi, p, 0};
         // Ratios in single precision first: each operand within 2^-23.9 of its value, the
         // quotient rounded once, so a ratio is within 2^-22.3 of the exact one and ratios apart
         // by more than 2^-16 of their size are ordered correctly.  Closer ones: exact test.
-        const float cf = approx_f(c.s) / (float)(-gi);
+        const float cf = approx_f(c.s) / approx_f((TE)-gi);
         if (best.p < 0 || cf < bf * (1.f - 0x1p-16f)) {
           best = c;
           bf = cf;
@@ -293,7 +301,7 @@ BD_HD int pivot_cell(Team tm, const int64_t* P, const int64_t* L, int N, int d, 
         }
         if (cf > bf * (1.f + 0x1p-16f)) continue;
         pivot_merge(best, c, &sc->flags);
-        bf = approx_f(best.s) / (float)(-best.g);
+        bf = approx_f(best.s) / approx_f((TE)-best.g);
       }
       sc->nbr[lvl][r] = best.p < 0 ? (uint8_t)255 : (uint8_t)best.p;
       if (best.p >= 0 && claim(mswap(mask, sc->cidx[r], best.p))) fresh |= 1ull << r;
@@ -340,7 +348,7 @@ BD_HD int pivot_cell(Team tm, const int64_t* P, const int64_t* L, int N, int d, 
       tm.sync();
       if (sc->flags) return sc->flags;
       if (lane == 0) {
-        const int64_t Dn = sc->D;
+        const TE Dn = sc->D;
         acc.nvol += (u128)(Dn < 0 ? -Dn : Dn);
         ++acc.cells;
       }

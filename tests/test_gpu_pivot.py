@@ -117,3 +117,41 @@ def test_gpu_degree_beyond_64_points_walks_the_cells():
     assert g["flags"] & bd.BD_FLAG_PIVOT
     assert g["nvol"] == nvol_placing(pts) and g["degree"] == g["nvol"] * g["torsion"]
     assert bd.degree_pivot(A)["degree"] == g["degree"]
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_gpu_pivot_wide_tableau_matches_oracle(seed):
+    # cell-minor bounds past 2^62 (random coordinates in [-6, 6] times 2^12..2^16): the GPU walk
+    # takes 128-bit tableau entries (BD_FLAG_INT128); exact against the oracle's placing volume,
+    # and the same volume and cell count as the host emulation with the same heights
+    rng = random.Random(8900 + seed)
+    k = [4, 4, 5, 4, 5, 4][seed]
+    n = [12, 24, 14, 40, 30, 80][seed]
+    sh = [14, 12, 10, 16, 11, 14][seed]
+    pts = sorted({tuple(rng.randint(-6, 6) << sh for _ in range(k)) for _ in range(n)})
+    n = len(pts)
+    r = bd.volume_pivot(np.array(pts), seed=seed)
+    assert r["flags"] & bd.BD_FLAG_INT128 and r["bound_bits"] > 62
+    assert r["nvol"] == nvol_placing(pts)
+    if r["relifts"] == 0:
+        h = bd.host_volume_pivot(np.array(pts), wide_lifts(n, seed))
+        assert (h["nvol"], h["cells"]) == (r["nvol"], r["cells"])
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_gpu_pivot_forced_wide_tableau_two_word_masks(seed):
+    # the 128-bit tableau forced (test hook) with one- and two-word masks: the same volume and cell
+    # count as the 64-bit tableau on the GPU, exact against the oracle's placing volume
+    rng = random.Random(8950 + seed)
+    k = [3, 4, 5, 4][seed]
+    n = [40, 70, 100, 127][seed]
+    pts = [tuple(rng.randint(-3, 3) for _ in range(k)) for _ in range(n)]
+    narrow = bd.volume_pivot(np.array(pts), seed=seed)
+    prev = bd.pivot_force_wide(True)
+    try:
+        wide = bd.volume_pivot(np.array(pts), seed=seed)
+    finally:
+        bd.pivot_force_wide(prev)
+    assert wide["flags"] & bd.BD_FLAG_INT128 and not narrow["flags"] & bd.BD_FLAG_INT128
+    assert (wide["nvol"], wide["cells"], wide["relifts"]) == (narrow["nvol"], narrow["cells"], narrow["relifts"])
+    assert wide["nvol"] == nvol_placing(pts)

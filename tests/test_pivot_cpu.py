@@ -147,12 +147,126 @@ def test_two_word_mask_errors():
         bd.host_volume_pivot(big, oracle_lifts(128, 0))  # above 127 points
 
 
-def test_pivot_refuses_minors_past_the_bound():
-    # W_{3,8}: 73 points in dimension 26, Hadamard bound of the cell minors 65 bits > 62; the
-    # refusal comes from the host before any device work
-    A = master_space_system(3, 8).A
-    with pytest.raises(bd.BinodegError, match="62 bits"):
+def big_coordinate_set(rng, n, k, bits):
+    """n random points in Z^k with coordinates below 2^bits in magnitude (distinct points)."""
+    pts = set()
+    while len(pts) < n:
+        pts.add(tuple(rng.randint(-(1 << bits) + 1, (1 << bits) - 1) for _ in range(k)))
+    return sorted(pts)
+
+
+def hadamard_bits(pts):
+    """log2 of the pivoting path's bound on the cell minors: the product of the k largest norms
+    ||a_x - a_s|| over one base point s, maximised over s (as the library computes it)."""
+    import math
+    k, best = len(pts[0]), 0.0
+    for s in pts:
+        lg = sorted((0.5 * math.log2(max(sum((a - b) ** 2 for a, b in zip(x, s)), 1))) for x in pts)[::-1]
+        best = max(best, sum(lg[:k]))
+    return best
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_host_pivot_wide_tableau_matches_placing(seed):
+    # cell-minor bounds past 2^62: random points with coordinates in [-6, 6] multiplied by 2^12..2^16
+    # (the start cell's support function stays within 128 bits for such sets; random coordinates
+    # near 2^16 overflow it and are refused).  The tableau takes 128-bit entries (BD_FLAG_INT128);
+    # the volume equals the oracle's placing volume of the given points and, for the smallest
+    # sets, the cells equal the oracle's lower facets of the same lifting; one lane and a 7-lane
+    # lockstep team, every cell eliminated or walked into in place
+    rng = random.Random(8600 + seed)
+    k = [4, 4, 5, 4, 5][seed]
+    n = [12, 24, 14, 40, 30][seed]
+    sh = [14, 12, 10, 16, 11][seed]
+    pts = sorted({tuple(rng.randint(-6, 6) << sh for _ in range(k)) for _ in range(n)})
+    n = len(pts)
+    assert hadamard_bits(pts) > 62
+    W = oracle_lifts(n, seed)
+    ref_vol = nvol_placing(pts)
+    ref = lower_cells(pts, W) if n <= 14 else None
+    for width, budget in [(1, 0), (7, 64)]:
+        r = bd.host_volume_pivot(np.array(pts), W, team_width=width, walk_budget=budget, cells=ref is not None)
+        assert r["status"] == 0
+        assert r["flags"] & bd.BD_FLAG_INT128 and r["bound_bits"] > 62
+        assert r["nvol"] == ref_vol
+        assert r["subsets"] == (k + 1) * r["cells"]
+        if ref is not None:
+            assert set(r["cell_list"]) == {tuple(sorted(c[0])) for c in ref}
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_host_pivot_forced_wide_tableau_matches_oracle(seed):
+    # the 128-bit tableau forced (test hook) on small sets: the cells equal the oracle's lower
+    # facets, the volume its placing volume
+    rng = random.Random(8620 + seed)
+    k = [2, 3, 4, 5][seed]
+    n = [9, 11, 12, 12][seed]
+    pts = [tuple(rng.randint(-3, 3) for _ in range(k)) for _ in range(n)]
+    W = oracle_lifts(n, seed)
+    ref = lower_cells(pts, W)
+    prev = bd.pivot_force_wide(True)
+    try:
+        for width, budget in [(1, 0), (1, 64), (7, 64)]:
+            r = bd.host_volume_pivot(np.array(pts), W, team_width=width, walk_budget=budget, cells=True)
+            if r["flags"] & bd.BD_FLAG_DEGENERATE:
+                assert nvol_placing(pts) == 0
+                continue
+            assert r["status"] == 0 and r["flags"] & bd.BD_FLAG_INT128
+            assert set(r["cell_list"]) == {tuple(sorted(c[0])) for c in ref}
+            assert r["nvol"] == sum(c[1] for c in ref) == nvol_placing(pts)
+    finally:
+        bd.pivot_force_wide(prev)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_host_pivot_wide_tableau_two_word_masks(seed):
+    # 128-bit tableau entries (forced by the test hook) with two-word masks (65..127 points):
+    # the same volume as the oracle's placing volume and as the 64-bit tableau
+    rng = random.Random(8650 + seed)
+    k = [3, 4, 5][seed]
+    n = [70, 100, 127][seed]
+    pts = [tuple(rng.randint(-3, 3) for _ in range(k)) for _ in range(n)]
+    W = oracle_lifts(n, seed)
+    narrow = bd.host_volume_pivot(np.array(pts), W)
+    prev = bd.pivot_force_wide(True)
+    try:
+        for width, budget in [(1, 0), (7, 64)]:
+            r = bd.host_volume_pivot(np.array(pts), W, team_width=width, walk_budget=budget)
+            assert r["status"] == 0 and r["flags"] & bd.BD_FLAG_INT128
+            assert (r["nvol"], r["cells"]) == (narrow["nvol"], narrow["cells"])
+    finally:
+        bd.pivot_force_wide(prev)
+    assert not narrow["flags"] & bd.BD_FLAG_INT128
+    assert narrow["nvol"] == nvol_placing(pts)
+
+
+def test_host_pivot_wide_tableau_agrees_with_narrow():
+    # the same points below the 62-bit bound, run with 64-bit entries, and scaled by 2^14 (bound
+    # past 62 bits, 128-bit entries): NVol scales by 2^(14k) and the cells stay the same
+    rng = random.Random(8700)
+    k, n = 4, 30
+    pts = [tuple(rng.randint(-6, 6) for _ in range(k)) for _ in range(n)]
+    W = oracle_lifts(n, 5)
+    a = bd.host_volume_pivot(np.array(pts), W, cells=True)
+    big = np.array(pts, dtype=np.int64) << 14
+    b = bd.host_volume_pivot(big, W, cells=True)
+    assert a["status"] == b["status"] == 0
+    assert not (a["flags"] & bd.BD_FLAG_INT128) and b["flags"] & bd.BD_FLAG_INT128
+    assert b["nvol"] == a["nvol"] << (14 * k)
+    assert b["cell_list"] == a["cell_list"] and b["cells"] == a["cells"]
+
+
+def test_pivot_refuses_heights_past_the_bound():
+    # W_{4,6}: 73 points in dimension 26, Hadamard bound of the cell minors 84 bits: the heights
+    # (a minor times a 41-bit lift difference, 27 terms) may leave 127 bits; the refusal comes from
+    # the host before any device work.  W_{3,8} (65 bits) takes the 128-bit tableau instead.
+    A = master_space_system(4, 6).A
+    with pytest.raises(bd.BinodegError, match="127 bits"):
         bd.degree_pivot(A)
+    rng = random.Random(8800)
+    pts = big_coordinate_set(rng, 12, 6, 19)  # 6 x ~20 bits + 41 > 126
+    with pytest.raises(bd.BinodegError, match="127 bits"):
+        bd.host_volume_pivot(np.array(pts), oracle_lifts(12, 0))
 
 
 def test_device_paths_fail_loudly_without_a_gpu():
