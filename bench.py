@@ -722,6 +722,7 @@ def main():
                 launch=dict(items=info["items"], blocks=info["blocks"], warps_per_block=info["warps_per_block"],
                             int_path="int128" if info["int128"] else "int64", max_abs_coord=red["max_abs_coord"]),
                 degrees_per_s=args.steps / (t["total_ms"] / 1e3), nvol=int(expect_nvol), cells=res["cells"],
+                singular=res["singular"], full_dimensional=subsets - res["singular"],
                 clocks=clk, gpu_launches=t["launches"],
                 e2e=dict(value=e2e_value, unit=UNIT, h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h,
                          ms_per_step=statistics.mean(e2e_ms), call="bd_degree(A) from host memory"),
@@ -736,7 +737,8 @@ def main():
         assert t2["nvols"] == {res2["nvol"]}
         line[SECONDARY] = dict(config=workload_config(SECONDARY, s2, N2, k2), value=t2["value"], unit=UNIT,
                                ms_per_step=t2["ms_per_step"], degrees_per_s=args.steps / (t2["total_ms"] / 1e3),
-                               nvol=int(res2["nvol"]), roofline=roofline(k2, sub2, t2["ms_per_step"], peak, SECONDARY, ""))
+                               nvol=int(res2["nvol"]), singular=res2["singular"], full_dimensional=sub2 - res2["singular"],
+                               roofline=roofline(k2, sub2, t2["ms_per_step"], peak, SECONDARY, ""))
         plan2.close()
         model, cm = train_cost_model(bd)
         line["batch"] = batch_section(bd, model, pool_cpu)
