@@ -39,13 +39,13 @@ SECONDARY = "single_n24_k8"
 # sources: DRAM bytes (read + write), warp instructions issued and the issue-active fraction.
 # Reported only while the library sources still hash to the captured version, null otherwise.
 PROFILE = {
-    "sources_sha256": "f00fef02a6bec655b118e443c8c9ad5950602bd5732f022fc950597c448fbe55",
+    "sources_sha256": "7b024fb2ac13dff5495cc8ff5b59430c6ac43f6afd6fd438fe6d49c72eb72965",
     # k_enumerate<int32, int64, 5> (the 5-D stage), 388,070 items
-    "heavy_quiver_n32_k10": dict(warp_inst=2408981505, lanes_per_inst=25.77, issue_active=0.5944,
-                                 traffic=6700032 + 43008),
+    "heavy_quiver_n32_k10": dict(warp_inst=2408999333, lanes_per_inst=25.77, issue_active=0.5944,
+                                 traffic=6700544 + 42496),
     # k_enumerate<int32, int64, 4> (the 4-D stage), 53,196 items
-    "single_n24_k8": dict(warp_inst=130585027, lanes_per_inst=23.47, issue_active=0.5623,
-                          traffic=1161728 + 16384),
+    "single_n24_k8": dict(warp_inst=130995030, lanes_per_inst=23.46, issue_active=0.5992,
+                          traffic=1161472 + 19200),
 }
 
 
