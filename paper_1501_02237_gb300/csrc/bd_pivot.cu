@@ -218,6 +218,7 @@ __host__ __device__ size_t pivot_warp_bytes(int N, int d) {
   b = (b + 15) / 16 * 16 + 16 * (size_t)N;     // S: heights (i128)
   b += sizeof(TE) * (size_t)N;                 // G0
   b += sizeof(TE) * (size_t)d * (d + N);       // W
+  b += sizeof(float) * (size_t)N;              // Sf: the heights in single precision
   return (b + 15) / 16 * 16;
 }
 
@@ -371,6 +372,8 @@ __global__ void __launch_bounds__(32 * kPivotMaxWarps) k_pivot(const int64_t* pt
   TE* G0 = reinterpret_cast<TE*>(wb + at);
   at += sizeof(TE) * (size_t)N;
   TE* W = reinterpret_cast<TE*>(wb + at);
+  at += sizeof(TE) * (size_t)d * (d + N);
+  float* Sf = reinterpret_cast<float*>(wb + at);
   PivotWarp tm;
   bd::PivotAcc acc{};
   int flags = 0;
@@ -379,7 +382,7 @@ __global__ void __launch_bounds__(32 * kPivotMaxWarps) k_pivot(const int64_t* pt
   const unsigned long long nw = (unsigned long long)gridDim.x * wpb;
   for (unsigned long long c = gw; c < ncur; c += nw) {
     flags |= bd::pivot_cell<TE>(
-        tm, P, L, N, d, cur[c], W, S, G0, sc, acc,
+        tm, P, L, N, d, cur[c], W, S, Sf, G0, sc, acc,
         [&](Mask m) { return table.claim(cap, m, &dv->claimed, &dv->flags); },
         [&](Mask m) { frontier_push(next, cap, m, dv); }, budget);
   }
@@ -538,6 +541,7 @@ int host_pivot(const int64_t* pts, const int64_t* lifts, int N, int d, Mask star
     for (int p = 0; p < N; ++p) P[(size_t)r * N + p] = pts[p * d + r];
   std::vector<TE> W((size_t)d * (d + N)), G0(N);
   std::vector<i128> S(N);
+  std::vector<float> Sf(N);
   bd::PivotScratch<TE> sc{};
   std::unordered_set<Mask, MaskHash> seen{start};
   std::vector<Mask> cur{start}, next;
@@ -547,7 +551,7 @@ int host_pivot(const int64_t* pts, const int64_t* lifts, int N, int d, Mask star
   auto step = [&](auto tm) {  // neighbours go to `next` under the mutex
     for (const Mask m : cur) {
       const int f = bd::pivot_cell<TE>(
-          tm, P.data(), lifts, N, d, m, W.data(), S.data(), G0.data(), &sc, acc,
+          tm, P.data(), lifts, N, d, m, W.data(), S.data(), Sf.data(), G0.data(), &sc, acc,
           [&](Mask nb) {
             std::lock_guard<std::mutex> g(mu);  // lanes of a lockstep team claim concurrently
             return seen.insert(nb).second;

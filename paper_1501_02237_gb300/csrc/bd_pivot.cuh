@@ -128,6 +128,16 @@ BD_HD float approx_f(i128 x) {
   return neg ? -f : f;
 }
 
+// a / b in single precision: the device's fast division (within 2 ulp for |b| below 2^126),
+// the host's IEEE division (within half an ulp)
+BD_HD float ratio_f(float a, float b) {
+#ifdef __CUDA_ARCH__
+  return __fdividef(a, b);
+#else
+  return a / b;
+#endif
+}
+
 // merge candidate B into A (both for the same ridge); sets *tie on equal ratios
 template <class TE>
 BD_HD void pivot_merge(PivotCand<TE>& A, const PivotCand<TE>& B, int32_t* flags) {
@@ -160,8 +170,8 @@ struct PivotAcc {
 // either entered in place (one rank-one pivot of the tableau, Sec. 4.2's pivot taken literally;
 // one more pivot leads back) or, past the budget or the stack depth, handed to push(mask) for a
 // later launch.  claim and push are called by any lane, concurrently.  P holds the points coordinate-major
-// (P[r * N + p]), L the lifts.  Per team: W, d x (d+N) entries; S, N heights; G0, N values of g_0;
-// sc, the scratch.  Rows 1..d of the tableau are W's right block, row 0 is G0.  TE is int64_t
+// (P[r * N + p]), L the lifts.  Per team: W, d x (d+N) entries; S, N heights and Sf, their
+// single-precision values; G0, N values of g_0; sc, the scratch.  Rows 1..d of the tableau are W's right block, row 0 is G0.  TE is int64_t
 // (cell minors below 2^62) or i128 (below 2^126; the host checks the bounds).  Returns PV_OK,
 // or PV_TIE / PV_INVALID bits.
 #ifdef __CUDACC__
@@ -169,7 +179,7 @@ struct PivotAcc {
 #endif
 template <class TE, class Team, class Mask, class Claim, class Push>
 BD_HD int pivot_cell(Team tm, const int64_t* P, const int64_t* L, int N, int d, Mask mask, TE* W, i128* S,
-                     TE* G0, PivotScratch<TE>* sc, PivotAcc& acc, Claim claim, Push push, int budget) {
+                     float* Sf, TE* G0, PivotScratch<TE>* sc, PivotAcc& acc, Claim claim, Push push, int budget) {
   typedef typename DivOf<TE>::type Div;
   const int lane = tm.lane(), nl = tm.lanes(), width = d + N;
   tm.sync();  // the previous cell's readers are done with the scratch
@@ -228,6 +238,7 @@ BD_HD int pivot_cell(Team tm, const int64_t* P, const int64_t* L, int N, int d, 
       s -= (i128)g * (L[sc->cidx[j + 1]] - L[s0]);
     }
     S[p] = s;
+    Sf[p] = approx_f(s);
     G0[p] = (TE)((i128)Dv - gs);  // itself a minor: fits
     if (!mhas(mask, p)) {
       const int sg = (s > 0) - (s < 0);
@@ -268,6 +279,7 @@ BD_HD int pivot_cell(Team tm, const int64_t* P, const int64_t* L, int N, int d, 
       for (int r = 0; r <= d; ++r)
         if (r != i) T(r, p) = bareiss(T(r, p), piv, sc->colq[r], ti, Dd);
       S[p] = bareiss(S[p], (i128)piv, sq, (i128)ti, Dw);
+      Sf[p] = approx_f(S[p]);
     }
     tm.sync();
     if (lane == 0) {
@@ -283,28 +295,33 @@ BD_HD int pivot_cell(Team tm, const int64_t* P, const int64_t* L, int N, int d, 
     const int sd = sc->D > 0 ? 1 : -1;
     uint64_t fresh = 0;
     for (int r = lane; r <= d; r += nl) {
-      PivotCand<TE> best{0, 0, -1, 0};
-      float bf = 0.f;  // best's ratio in single precision
+      int bp = -1;     // the best candidate so far: its point, g_r and ratio in single precision
+      TE bg = 0;
+      float bf = 0.f;
       for (int p = 0; p < N; ++p) {
         if (mhas(mask, p)) continue;
         const TE gi = T(r, p);
         if (gi == 0 || (gi > 0 ? 1 : -1) == sd) continue;  // not beyond the ridge
-        PivotCand<TE> c{S[p], gi, p, 0};
-        // Ratios in single precision first: each operand within 2^-23.9 of its value, the
-        // quotient rounded once, so a ratio is within 2^-22.3 of the exact one and ratios apart
-        // by more than 2^-16 of their size are ordered correctly.  Closer ones: exact test.
-        const float cf = approx_f(c.s) / approx_f((TE)-gi);
-        if (best.p < 0 || cf < bf * (1.f - 0x1p-16f)) {
-          best = c;
+        // Ratios in single precision first: the height within 2^-23.9 of its value (Sf, formed
+        // once per cell), g_r within 2^-23.9, the quotient within 2 ulp (2^-22), so a ratio is
+        // within 2^-21.2 of the exact one and ratios apart by more than 2^-16 of their size are
+        // ordered correctly.  Closer ones: the exact test.
+        const float cf = ratio_f(Sf[p], approx_f((TE)-gi));
+        if (bp < 0 || cf < bf * (1.f - 0x1p-16f)) {
+          bp = p;
+          bg = gi;
           bf = cf;
           continue;
         }
         if (cf > bf * (1.f + 0x1p-16f)) continue;
-        pivot_merge(best, c, &sc->flags);
-        bf = approx_f(best.s) / approx_f((TE)-best.g);
+        PivotCand<TE> best{S[bp], bg, bp, 0};
+        pivot_merge(best, PivotCand<TE>{S[p], gi, p, 0}, &sc->flags);
+        bp = best.p;
+        bg = best.g;
+        bf = ratio_f(Sf[bp], approx_f((TE)-bg));
       }
-      sc->nbr[lvl][r] = best.p < 0 ? (uint8_t)255 : (uint8_t)best.p;
-      if (best.p >= 0 && claim(mswap(mask, sc->cidx[r], best.p))) fresh |= 1ull << r;
+      sc->nbr[lvl][r] = bp < 0 ? (uint8_t)255 : (uint8_t)bp;
+      if (bp >= 0 && claim(mswap(mask, sc->cidx[r], bp))) fresh |= 1ull << r;
     }
     fresh = tm.or_all(fresh);
     tm.sync();  // the neighbours are visible to every lane
