@@ -517,8 +517,8 @@ int bd_host_mixed_volume_lifted(const int64_t* points, const int32_t* counts, in
  * bound on them (bound_bits) stays below 2^62, 128-bit above (fewer warps per SM, slower pivots).
  * Errors: BD_ERR_ARG, BD_ERR_OVERFLOW (heights D h(p), a minor times a 41-bit lift difference
  * summed over k+1 terms, may leave 127 bits: bound_bits above about 84; or the start cell's
- * support function left 128 bits), BD_ERR_TIES, BD_ERR_CUDA, BD_ERR_NOMEM (more than 2^30
- * cells).
+ * support function, reduced by the gcd of its coefficients, left 128 bits), BD_ERR_TIES,
+ * BD_ERR_CUDA, BD_ERR_NOMEM (more than 2^30 cells).
  */
 int bd_volume_pivot(const int64_t* points, int32_t npts, int32_t k, uint64_t seed, bd_volume_out* out,
                     double* device_ms);

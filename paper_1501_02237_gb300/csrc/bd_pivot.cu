@@ -67,6 +67,123 @@ i128 gcd128(i128 a, i128 b) {
 bool mul_ok(i128 a, i128 b, i128& r) { return !__builtin_mul_overflow(a, b, &r); }
 bool add_ok(i128 a, i128 b, i128& r) { return !__builtin_add_overflow(a, b, &r); }
 
+// Signed 256-bit values as sign and magnitude, for the start cell's support function: the
+// coefficients of one extension step are formed exactly in 256 bits and reduced by their gcd
+// before they are stored back in 128 bits.
+struct U256 {
+  u128 lo = 0, hi = 0;
+};
+struct S256 {
+  bool neg = false;
+  U256 m;
+};
+
+bool u_zero(const U256& a) { return a.lo == 0 && a.hi == 0; }
+bool u_less(const U256& a, const U256& b) { return a.hi != b.hi ? a.hi < b.hi : a.lo < b.lo; }
+U256 u_add(const U256& a, const U256& b) {  // the callers keep the sum below 2^256
+  U256 r;
+  r.lo = a.lo + b.lo;
+  r.hi = a.hi + b.hi + (r.lo < a.lo ? 1 : 0);
+  return r;
+}
+U256 u_sub(const U256& a, const U256& b) {  // a >= b
+  U256 r;
+  r.lo = a.lo - b.lo;
+  r.hi = a.hi - b.hi - (a.lo < b.lo ? 1 : 0);
+  return r;
+}
+U256 u_shr(const U256& a, int k) {  // 0 <= k < 256
+  if (k == 0) return a;
+  U256 r;
+  if (k >= 128) {
+    r.lo = a.hi >> (k - 128);
+  } else {
+    r.lo = (a.lo >> k) | (a.hi << (128 - k));
+    r.hi = a.hi >> k;
+  }
+  return r;
+}
+U256 u_shl(const U256& a, int k) {  // 0 <= k < 256, no bit shifted out
+  if (k == 0) return a;
+  U256 r;
+  if (k >= 128) {
+    r.hi = a.lo << (k - 128);
+  } else {
+    r.hi = (a.hi << k) | (a.lo >> (128 - k));
+    r.lo = a.lo << k;
+  }
+  return r;
+}
+int u_ctz(const U256& a) { return a.lo ? bd::ctz128(a.lo) : 128 + bd::ctz128(a.hi); }
+U256 u_mul(u128 a, u128 b) {  // the full product of two 128-bit magnitudes
+  const u128 a0 = (uint64_t)a, a1 = a >> 64, b0 = (uint64_t)b, b1 = b >> 64;
+  const u128 p00 = a0 * b0, p01 = a0 * b1, p10 = a1 * b0, p11 = a1 * b1;
+  const u128 mid = (p00 >> 64) + (uint64_t)p01 + (uint64_t)p10;
+  U256 r;
+  r.lo = (u128)(uint64_t)p00 | (mid << 64);
+  r.hi = p11 + (p01 >> 64) + (p10 >> 64) + (mid >> 64);
+  return r;
+}
+u128 uabs128(i128 x) { return x < 0 ? (u128)0 - (u128)x : (u128)x; }
+S256 s_mul(i128 a, i128 b) {
+  S256 r;
+  r.m = u_mul(uabs128(a), uabs128(b));
+  r.neg = !u_zero(r.m) && ((a < 0) != (b < 0));
+  return r;
+}
+S256 s_add(const S256& a, const S256& b) {  // magnitudes below 2^255
+  S256 r;
+  if (a.neg == b.neg) {
+    r.neg = a.neg;
+    r.m = u_add(a.m, b.m);
+  } else if (u_less(a.m, b.m)) {
+    r.neg = b.neg;
+    r.m = u_sub(b.m, a.m);
+  } else {
+    r.neg = a.neg;
+    r.m = u_sub(a.m, b.m);
+  }
+  if (u_zero(r.m)) r.neg = false;
+  return r;
+}
+S256 s_negate(S256 a) {
+  if (!u_zero(a.m)) a.neg = !a.neg;
+  return a;
+}
+U256 u_gcd(U256 a, U256 b) {  // binary gcd
+  if (u_zero(a)) return b;
+  if (u_zero(b)) return a;
+  const int za = u_ctz(a), zb = u_ctz(b), sh = za < zb ? za : zb;
+  a = u_shr(a, za);
+  while (!u_zero(b)) {
+    b = u_shr(b, u_ctz(b));
+    if (u_less(b, a)) std::swap(a, b);
+    b = u_sub(b, a);
+  }
+  return u_shl(a, sh);
+}
+U256 u_div(const U256& x, const U256& g) {  // floor(x / g), g != 0, by binary long division
+  U256 q, r;
+  for (int i = 255; i >= 0; --i) {
+    r = u_shl(r, 1);  // r < g < 2^256 before the shift: r stays below 2^256 while g < 2^255
+    const bool bit = i >= 128 ? ((x.hi >> (i - 128)) & 1) : ((x.lo >> i) & 1);
+    if (bit) r.lo |= 1;
+    if (!u_less(r, g)) {
+      r = u_sub(r, g);
+      if (i >= 128) q.hi |= (u128)1 << (i - 128);
+      else q.lo |= (u128)1 << i;
+    }
+  }
+  return q;
+}
+// v / g as a 128-bit integer; false if it does not fit
+bool s_div_fit(const S256& v, const U256& g, i128& out) {
+  const U256 q = u_div(v.m, g);
+  if (q.hi != 0 || (q.lo >> 127) != 0) return false;
+  out = v.neg ? -(i128)q.lo : (i128)q.lo;
+  return true;
+}
+
 // A lower facet to start from, by extension (the paper's extension process, Sec. 4.1, done
 // here without a linear program): from the lowest lifted point, a lower face F with an integer
 // support function H(p) = c w_p - <A, a_p> - B (>= 0 on all points, 0 exactly on F) is tilted
@@ -138,8 +255,9 @@ int start_cell(const int64_t* pts, const int64_t* lifts, int N, int d, Mask& mas
       std::vector<i128> w(N);
       bool pos = false, neg = false;
       for (int p = 0; p < N; ++p) {
-        i128 s = 0;
-        for (int e = 0; e < d; ++e) s += u[e] * ((i128)pts[p * d + e] - pts[f0 * d + e]);
+        i128 s = 0, t;
+        for (int e = 0; e < d; ++e)
+          if (!mul_ok(u[e], (i128)pts[p * d + e] - pts[f0 * d + e], t) || !add_ok(s, t, s)) return START_OVERFLOW;
         w[p] = s;
         pos |= s > 0;
         neg |= s < 0;
@@ -158,22 +276,22 @@ int start_cell(const int64_t* pts, const int64_t* lifts, int N, int d, Mask& mas
         if (bd::prod_equal(H[p], sg * w[q], H[q], sg * w[p])) return START_TIE;
         if (bd::prod_greater(H[q], sg * w[p], H[p], sg * w[q])) q = p;
       }
-      const i128 wq = sg * w[q], hq = H[q];
-      i128 nc, t, t2;
-      if (!mul_ok(wq, c, nc)) return START_OVERFLOW;
-      std::vector<i128> nA(d);
-      for (int e = 0; e < d; ++e) {
-        if (!mul_ok(wq, A[e], t) || !mul_ok(hq * sg, u[e], t2) || !add_ok(t, t2, nA[e])) return START_OVERFLOW;
-      }
-      i128 uf0 = 0;
-      for (int e = 0; e < d; ++e) uf0 += u[e] * (i128)pts[f0 * d + e];
-      i128 nB;
-      if (!mul_ok(wq, B, t) || !mul_ok(hq * sg, uf0, t2) || __builtin_sub_overflow(t, t2, &nB)) return START_OVERFLOW;
-      i128 gg = gcd128(nc, nB);
-      for (int e = 0; e < d; ++e) gg = gcd128(gg, nA[e]);
-      c = nc / gg;
-      B = nB / gg;
-      for (int e = 0; e < d; ++e) A[e] = nA[e] / gg;
+      // H' = wq H - hq sg <u, a - a_f0>, formed exactly in 256 bits, then divided by the gcd of
+      // its coefficients (the products overflow 128 bits on large coordinates long before the
+      // reduced support function does)
+      const i128 wq = sg * w[q], hq = H[q];  // wq > 0, hq > 0
+      i128 uf0 = 0, t;
+      for (int e = 0; e < d; ++e)
+        if (!mul_ok(u[e], (i128)pts[f0 * d + e], t) || !add_ok(uf0, t, uf0)) return START_OVERFLOW;
+      const S256 nc = s_mul(wq, c);
+      std::vector<S256> nA(d);
+      for (int e = 0; e < d; ++e) nA[e] = s_add(s_mul(wq, A[e]), s_mul(hq * sg, u[e]));
+      const S256 nB = s_add(s_mul(wq, B), s_negate(s_mul(hq * sg, uf0)));
+      U256 gg = u_gcd(nc.m, nB.m);
+      for (int e = 0; e < d; ++e) gg = u_gcd(gg, nA[e].m);
+      if (!s_div_fit(nc, gg, c) || !s_div_fit(nB, gg, B)) return START_OVERFLOW;
+      for (int e = 0; e < d; ++e)
+        if (!s_div_fit(nA[e], gg, A[e])) return START_OVERFLOW;
       F.push_back(q);
       extended = true;
     }

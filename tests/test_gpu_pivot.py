@@ -155,3 +155,18 @@ def test_gpu_pivot_forced_wide_tableau_two_word_masks(seed):
     assert wide["flags"] & bd.BD_FLAG_INT128 and not narrow["flags"] & bd.BD_FLAG_INT128
     assert (wide["nvol"], wide["cells"], wide["relifts"]) == (narrow["nvol"], narrow["cells"], narrow["relifts"])
     assert wide["nvol"] == nvol_placing(pts)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_gpu_pivot_random_large_coordinates(seed):
+    # random coordinates up to 2^16 (Z^4) and 2^13 (Z^5): bounds past 2^62 and start cells formed
+    # in 256-bit steps; exact against the oracle's placing volume
+    rng = random.Random(8980 + seed)
+    k, bits, n = [(4, 16, 40), (5, 13, 30), (4, 17, 70)][seed]
+    pts = set()
+    while len(pts) < n:
+        pts.add(tuple(rng.randint(-(1 << bits) + 1, (1 << bits) - 1) for _ in range(k)))
+    pts = sorted(pts)
+    r = bd.volume_pivot(np.array(pts), seed=seed)
+    assert r["flags"] & bd.BD_FLAG_INT128 and r["bound_bits"] > 62
+    assert r["nvol"] == nvol_placing(pts)

@@ -168,9 +168,8 @@ def hadamard_bits(pts):
 
 @pytest.mark.parametrize("seed", range(5))
 def test_host_pivot_wide_tableau_matches_placing(seed):
-    # cell-minor bounds past 2^62: random points with coordinates in [-6, 6] multiplied by 2^12..2^16
-    # (the start cell's support function stays within 128 bits for such sets; random coordinates
-    # near 2^16 overflow it and are refused).  The tableau takes 128-bit entries (BD_FLAG_INT128);
+    # cell-minor bounds past 2^62: random points with coordinates in [-6, 6] multiplied by
+    # 2^12..2^16.  The tableau takes 128-bit entries (BD_FLAG_INT128);
     # the volume equals the oracle's placing volume of the given points and, for the smallest
     # sets, the cells equal the oracle's lower facets of the same lifting; one lane and a 7-lane
     # lockstep team, every cell eliminated or walked into in place
@@ -192,6 +191,21 @@ def test_host_pivot_wide_tableau_matches_placing(seed):
         assert r["subsets"] == (k + 1) * r["cells"]
         if ref is not None:
             assert set(r["cell_list"]) == {tuple(sorted(c[0])) for c in ref}
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_host_pivot_random_large_coordinates(seed):
+    # random coordinates up to 2^17 in Z^4, 2^14 in Z^5, 2^11 in Z^6: bounds past 2^62, and
+    # start cells whose extension steps pass 2^128 before their gcd reduction (formed in 256
+    # bits); exact against the oracle's placing volume
+    rng = random.Random(8660 + seed)
+    k, bits = [(4, 16), (4, 17), (5, 13), (5, 14), (6, 11), (4, 16)][seed]
+    n = [20, 30, 16, 24, 14, 64][seed]
+    pts = big_coordinate_set(rng, n, k, bits)
+    assert hadamard_bits(pts) > 62
+    r = bd.host_volume_pivot(np.array(pts), oracle_lifts(n, seed), team_width=1 if n > 30 else 7)
+    assert r["status"] == 0 and r["flags"] & bd.BD_FLAG_INT128
+    assert r["nvol"] == nvol_placing(pts)
 
 
 @pytest.mark.parametrize("seed", range(4))
