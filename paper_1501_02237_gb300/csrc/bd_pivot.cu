@@ -340,9 +340,14 @@ __host__ __device__ size_t pivot_warp_bytes(int N, int d) {
   return (b + 15) / 16 * 16;
 }
 
+// the block's points: 32-bit coordinates (below 2^20), coordinate-major, then the 64-bit lifts
+__host__ __device__ size_t pivot_points_bytes(int N, int d) {
+  return (4 * (size_t)d * N + 15) / 16 * 16 + (8 * (size_t)N + 15) / 16 * 16;
+}
+
 template <class TE>
 size_t pivot_smem(int N, int d, int warps) {
-  return ((8 * (size_t)(d + 1) * N + 15) / 16 * 16) + warps * pivot_warp_bytes<TE>(N, d);
+  return pivot_points_bytes(N, d) + warps * pivot_warp_bytes<TE>(N, d);
 }
 
 struct PivotDev {
@@ -476,13 +481,13 @@ __global__ void __launch_bounds__(32 * kPivotMaxWarps) k_pivot(const int64_t* pt
                                                             CellTable<Mask> table, unsigned long long cap,
                                                             int budget, Mask* next, PivotDev* dv) {
   extern __shared__ __align__(16) unsigned char smem[];
-  int64_t* P = reinterpret_cast<int64_t*>(smem);  // coordinate-major, then the lifts
-  int64_t* L = P + (size_t)d * N;
-  for (int i = threadIdx.x; i < d * N; i += blockDim.x) P[i] = pts[(i % N) * d + i / N];
+  int32_t* P = reinterpret_cast<int32_t*>(smem);  // coordinate-major, then the lifts
+  int64_t* L = reinterpret_cast<int64_t*>(smem + (4 * (size_t)d * N + 15) / 16 * 16);
+  for (int i = threadIdx.x; i < d * N; i += blockDim.x) P[i] = (int32_t)pts[(i % N) * d + i / N];
   for (int i = threadIdx.x; i < N; i += blockDim.x) L[i] = lifts[i];
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  unsigned char* wb = smem + ((8 * (size_t)(d + 1) * N + 15) / 16 * 16) + warp * pivot_warp_bytes<TE>(N, d);
+  unsigned char* wb = smem + pivot_points_bytes(N, d) + warp * pivot_warp_bytes<TE>(N, d);
   auto* sc = reinterpret_cast<bd::PivotScratch<TE>*>(wb);
   size_t at = (sizeof(bd::PivotScratch<TE>) + 15) / 16 * 16;
   i128* S = reinterpret_cast<i128*>(wb + at);
@@ -654,9 +659,9 @@ struct MaskHash {
 template <class Mask, class TE>
 int host_pivot(const int64_t* pts, const int64_t* lifts, int N, int d, Mask start, int width, int budget,
                PivotRun& run) {
-  std::vector<int64_t> P((size_t)d * N);
+  std::vector<int32_t> P((size_t)d * N);
   for (int r = 0; r < d; ++r)
-    for (int p = 0; p < N; ++p) P[(size_t)r * N + p] = pts[p * d + r];
+    for (int p = 0; p < N; ++p) P[(size_t)r * N + p] = (int32_t)pts[p * d + r];
   std::vector<TE> W((size_t)d * (d + N)), G0(N);
   std::vector<i128> S(N);
   std::vector<float> Sf(N);

@@ -76,7 +76,12 @@ struct PivotCand {
 };
 
 // per-warp scratch of the pivoting stage
-constexpr int kWalkDepth = 64;  // deepest in-place walk below an eliminated cell
+// deepest in-place walk below an eliminated cell: 32 levels keep the per-warp stack at ~1.2 KB
+// (W4,5 walks at 12 instead of 10 warps per SM: 4.11 -> 3.44 s; 64 levels gained nothing)
+#ifndef BD_WALK_DEPTH
+#define BD_WALK_DEPTH 32
+#endif
+constexpr int kWalkDepth = BD_WALK_DEPTH;
 
 template <class TE>
 struct PivotScratch {
@@ -170,7 +175,7 @@ struct PivotAcc {
 // either entered in place (one rank-one pivot of the tableau, Sec. 4.2's pivot taken literally;
 // one more pivot leads back) or, past the budget or the stack depth, handed to push(mask) for a
 // later launch.  claim and push are called by any lane, concurrently.  P holds the points coordinate-major
-// (P[r * N + p]), L the lifts.  Per team: W, d x (d+N) entries; S, N heights and Sf, their
+// (P[r * N + p], 32-bit: the pivoting path takes coordinates below 2^20), L the lifts.  Per team: W, d x (d+N) entries; S, N heights and Sf, their
 // single-precision values; G0, N values of g_0; sc, the scratch.  Rows 1..d of the tableau are W's right block, row 0 is G0.  TE is int64_t
 // (cell minors below 2^62) or i128 (below 2^126; the host checks the bounds).  Returns PV_OK,
 // or PV_TIE / PV_INVALID bits.
@@ -178,7 +183,7 @@ struct PivotAcc {
 #pragma nv_exec_check_disable  // instantiated with host-only teams by the host emulation
 #endif
 template <class TE, class Team, class Mask, class Claim, class Push>
-BD_HD int pivot_cell(Team tm, const int64_t* P, const int64_t* L, int N, int d, Mask mask, TE* W, i128* S,
+BD_HD int pivot_cell(Team tm, const int32_t* P, const int64_t* L, int N, int d, Mask mask, TE* W, i128* S,
                      float* Sf, TE* G0, PivotScratch<TE>* sc, PivotAcc& acc, Claim claim, Push push, int budget) {
   typedef typename DivOf<TE>::type Div;
   const int lane = tm.lane(), nl = tm.lanes(), width = d + N;
@@ -191,7 +196,7 @@ BD_HD int pivot_cell(Team tm, const int64_t* P, const int64_t* L, int N, int d, 
   // W = [M^T | a_p - a_{s_0}]: row r holds coordinate r
   for (int c = lane; c < width; c += nl) {
     const int src = c < d ? sc->cidx[c + 1] : c - d;
-    for (int r = 0; r < d; ++r) W[r * width + c] = P[r * N + src] - P[r * N + s0];
+    for (int r = 0; r < d; ++r) W[r * width + c] = (TE)(P[r * N + src] - P[r * N + s0]);
   }
   tm.sync();
   // fraction-free Gauss-Jordan: after step k, rows i != k have no entry in column k
