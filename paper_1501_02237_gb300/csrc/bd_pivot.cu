@@ -335,7 +335,7 @@ __host__ __device__ size_t pivot_warp_bytes(int N, int d) {
   size_t b = sizeof(bd::PivotScratch<TE>);
   b = (b + 15) / 16 * 16 + 16 * (size_t)N;     // S: heights (i128)
   b += sizeof(TE) * (size_t)N;                 // G0
-  b += sizeof(TE) * (size_t)d * (d + N);       // W
+  b += sizeof(TE) * (size_t)d * N;             // W: the d x N tableau rows
   b += sizeof(float) * (size_t)N;              // Sf: the heights in single precision
   return (b + 15) / 16 * 16;
 }
@@ -495,7 +495,7 @@ __global__ void __launch_bounds__(32 * kPivotMaxWarps) k_pivot(const int64_t* pt
   TE* G0 = reinterpret_cast<TE*>(wb + at);
   at += sizeof(TE) * (size_t)N;
   TE* W = reinterpret_cast<TE*>(wb + at);
-  at += sizeof(TE) * (size_t)d * (d + N);
+  at += sizeof(TE) * (size_t)d * N;
   float* Sf = reinterpret_cast<float*>(wb + at);
   PivotWarp tm;
   bd::PivotAcc acc{};
@@ -662,7 +662,7 @@ int host_pivot(const int64_t* pts, const int64_t* lifts, int N, int d, Mask star
   std::vector<int32_t> P((size_t)d * N);
   for (int r = 0; r < d; ++r)
     for (int p = 0; p < N; ++p) P[(size_t)r * N + p] = (int32_t)pts[p * d + r];
-  std::vector<TE> W((size_t)d * (d + N)), G0(N);
+  std::vector<TE> W((size_t)d * N), G0(N);
   std::vector<i128> S(N);
   std::vector<float> Sf(N);
   bd::PivotScratch<TE> sc{};

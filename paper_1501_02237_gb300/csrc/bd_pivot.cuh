@@ -175,7 +175,7 @@ struct PivotAcc {
 // either entered in place (one rank-one pivot of the tableau, Sec. 4.2's pivot taken literally;
 // one more pivot leads back) or, past the budget or the stack depth, handed to push(mask) for a
 // later launch.  claim and push are called by any lane, concurrently.  P holds the points coordinate-major
-// (P[r * N + p], 32-bit: the pivoting path takes coordinates below 2^20), L the lifts.  Per team: W, d x (d+N) entries; S, N heights and Sf, their
+// (P[r * N + p], 32-bit: the pivoting path takes coordinates below 2^20), L the lifts.  Per team: W, d x N entries; S, N heights and Sf, their
 // single-precision values; G0, N values of g_0; sc, the scratch.  Rows 1..d of the tableau are W's right block, row 0 is G0.  TE is int64_t
 // (cell minors below 2^62) or i128 (below 2^126; the host checks the bounds).  Returns PV_OK,
 // or PV_TIE / PV_INVALID bits.
@@ -186,25 +186,26 @@ template <class TE, class Team, class Mask, class Claim, class Push>
 BD_HD int pivot_cell(Team tm, const int32_t* P, const int64_t* L, int N, int d, Mask mask, TE* W, i128* S,
                      float* Sf, TE* G0, PivotScratch<TE>* sc, PivotAcc& acc, Claim claim, Push push, int budget) {
   typedef typename DivOf<TE>::type Div;
-  const int lane = tm.lane(), nl = tm.lanes(), width = d + N;
+  const int lane = tm.lane(), nl = tm.lanes();
   tm.sync();  // the previous cell's readers are done with the scratch
   if (lane == 0) sc->flags = 0;
   for (int b = lane; b < N; b += nl)
     if (mhas(mask, b)) sc->cidx[mrank(mask, b)] = (uint8_t)b;
   tm.sync();
   const int s0 = sc->cidx[0];
-  // W = [M^T | a_p - a_{s_0}]: row r holds coordinate r
-  for (int c = lane; c < width; c += nl) {
-    const int src = c < d ? sc->cidx[c + 1] : c - d;
-    for (int r = 0; r < d; ++r) W[r * width + c] = (TE)(P[r * N + src] - P[r * N + s0]);
-  }
+  // W = [a_p - a_{s_0}] for every point p (row r: coordinate r; d x N, row stride N).  The
+  // columns of the cell's own points s_1 .. s_d are M^T, so fraction-free Gauss-Jordan runs on W
+  // alone: step k pivots on the column of s_{k+1}, which then holds p_k e_k, and at the end
+  // every column is D lambda(p) (the cell's own columns D e_j)
+  for (int p = lane; p < N; p += nl)
+    for (int r = 0; r < d; ++r) W[r * N + p] = (TE)(P[r * N + p] - P[r * N + s0]);
   tm.sync();
-  // fraction-free Gauss-Jordan: after step k, rows i != k have no entry in column k
   TE prev = 1;
   for (int k = 0; k < d; ++k) {
+    const int kc = sc->cidx[k + 1];  // the pivot column
     if (lane == 0) {
       int r = k;
-      while (r < d && W[r * width + k] == 0) ++r;
+      while (r < d && W[r * N + kc] == 0) ++r;
       sc->piv = r;
     }
     tm.sync();
@@ -215,20 +216,23 @@ BD_HD int pivot_cell(Team tm, const int32_t* P, const int64_t* L, int N, int d, 
       return sc->flags;
     }
     if (pr != k) {
-      for (int c = lane; c < width; c += nl) {
-        const TE t = W[k * width + c];
-        W[k * width + c] = W[pr * width + c];
-        W[pr * width + c] = t;
+      for (int c = lane; c < N; c += nl) {
+        const TE t = W[k * N + c];
+        W[k * N + c] = W[pr * N + c];
+        W[pr * N + c] = t;
       }
       tm.sync();
     }
-    const TE pk = W[k * width + k];
+    const TE pk = W[k * N + kc];
     const Div D = make_div(prev);
-    for (int c = k + 1 + lane; c < width; c += nl) {
-      const TE top = W[k * width + c];
+    for (int c = lane; c < N; c += nl) {
+      if (c == kc) continue;  // the multipliers: read by every lane, rewritten below
+      const TE top = W[k * N + c];
       for (int i = 0; i < d; ++i)
-        if (i != k) W[i * width + c] = bareiss(W[i * width + c], pk, W[i * width + k], top, D);
+        if (i != k) W[i * N + c] = bareiss(W[i * N + c], pk, W[i * N + kc], top, D);
     }
+    tm.sync();
+    for (int i = lane; i < d; i += nl) W[i * N + kc] = i == k ? pk : (TE)0;
     tm.sync();
     prev = pk;
   }
@@ -238,7 +242,7 @@ BD_HD int pivot_cell(Team tm, const int32_t* P, const int64_t* L, int N, int d, 
   for (int p = lane; p < N; p += nl) {
     i128 s = (i128)Dv * (L[p] - L[s0]), gs = 0;
     for (int j = 0; j < d; ++j) {
-      const TE g = W[j * width + d + p];
+      const TE g = W[j * N + p];
       gs += g;
       s -= (i128)g * (L[sc->cidx[j + 1]] - L[s0]);
     }
@@ -267,7 +271,7 @@ BD_HD int pivot_cell(Team tm, const int32_t* P, const int64_t* L, int N, int d, 
     acc.nvol += (u128)(Dv < 0 ? -Dv : Dv);
     ++acc.cells;
   }
-  auto T = [&](int r, int p) -> TE& { return r == 0 ? G0[p] : W[(r - 1) * width + d + p]; };
+  auto T = [&](int r, int p) -> TE& { return r == 0 ? G0[p] : W[(r - 1) * N + p]; };
   // Pivot row i onto point q: T'[r][p] = (T[r][p] T[i][q] - T[r][q] T[i][p]) / D for r != i,
   // T'[i][p] = T[i][p], S'[p] = (S[p] T[i][q] - S[q] T[i][p]) / D, D' = T[i][q] (every entry
   // again a minor, or D' times a height, of the new cell).
